@@ -1,0 +1,286 @@
+"""CPU oracle for the l2T-MD electronic heat-conduction step (arXiv 1810.12357).
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It is a plain FP64
+restatement of the paper's equations (C loops in ``ehc_oracle.c`` plus the
+bookkeeping below in numpy) and shares no code with the CUDA library.
+
+Pins (tests/test_oracle_*.py) tie each function to something other than
+itself: brute-force neighbour search, the perfect-FCC neighbour count, flux
+antisymmetry and the uniform fixed point (Eq. HeatTransport), the Fourier-law
+decay rate implied by Eq. Kij, exact electron/lattice energy balance
+(Eqs. RateExchange, WorkDone, Xi), the two-bath equilibrium of the 1-D bar
+(Sec. 3.1), and published Philox4x32-10 known-answer vectors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# CODATA 2018
+KB_EV = 8.617333262e-5
+KB_J = 1.380649e-23
+EV_J = 1.602176634e-19
+AMU_KG = 1.66053906660e-27
+MVV_EV = AMU_KG * 1.0e10 / EV_J
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        u64 = ctypes.c_uint64
+        L.oracle_quantize.argtypes = [i64, P, P, P, P, P]
+        L.oracle_quantize.restype = ctypes.c_int
+        for f in (L.oracle_neighbors_brute, L.oracle_neighbors_cells):
+            f.argtypes = [i64, P, P, P, i64, P, P, i64]
+            f.restype = i64
+        L.oracle_lattice_temperature.argtypes = [i64, P, P, P, P, ctypes.c_int, P, P]
+        L.oracle_lattice_temperature.restype = None
+        L.oracle_pair_flux.argtypes = [dbl, dbl]
+        L.oracle_pair_flux.restype = dbl
+        L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
+                                      dbl, P, P, dbl, dbl, dbl, P]
+        L.oracle_substeps.restype = ctypes.c_int
+        L.oracle_philox4x32_10.argtypes = [P, P, P]
+        L.oracle_philox4x32_10.restype = None
+        L.oracle_gauss3.argtypes = [u64, u64, u64, P]
+        L.oracle_gauss3.restype = None
+        L.oracle_couple.argtypes = [i64, P, P, P, P, P, ctypes.c_int, ctypes.c_int, u64, u64,
+                                    dbl, dbl, dbl, P]
+        L.oracle_couple.restype = i64
+        L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+# --------------------------------------------------------------------------
+# neighbour lists (Sec. 2: j with |x_j - x_i| <= r_c)
+
+def quantize(x: np.ndarray, box, periodic):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    q = np.empty((x.shape[0], 3), dtype=np.int32)
+    Lq = np.empty(3, dtype=np.int64)
+    rc = lib().oracle_quantize(x.shape[0], _p(x), _p(box), _p(per), _p(q), _p(Lq))
+    if rc != 0:
+        raise ValueError(f"oracle_quantize failed ({rc})")
+    return q, Lq
+
+
+def rc_fixed(rc_A: float) -> int:
+    return int(np.rint(rc_A * 1048576.0))
+
+
+def neighbors(x: np.ndarray, box, periodic, rc_A: float, method: str = "cells",
+              cap_per_atom: int = 64):
+    """Full neighbour list in original ids: (rowptr int64 [N+1], col int32)."""
+    q, Lq = quantize(x, box, periodic)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    n = q.shape[0]
+    cap = max(1, n * cap_per_atom)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.empty(cap, dtype=np.int32)
+    f = lib().oracle_neighbors_brute if method == "brute" else lib().oracle_neighbors_cells
+    nnz = f(n, _p(q), _p(Lq), _p(per), rc_fixed(rc_A), _p(rowptr), _p(col), cap)
+    if nnz < 0:
+        raise ValueError(f"neighbour list capacity exceeded ({nnz})")
+    return rowptr, col[:nnz].copy()
+
+
+# --------------------------------------------------------------------------
+# local lattice temperature (Sec. 2)
+
+def lattice_temperature(rowptr, col, v, mass_of_atom, dof_mode: int = 0):
+    n = rowptr.shape[0] - 1
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    m = np.ascontiguousarray(mass_of_atom, dtype=np.float64)
+    Tl = np.empty(n)
+    Ks = np.empty(n)
+    lib().oracle_lattice_temperature(n, _p(rowptr), _p(col), _p(v), _p(m), int(dof_mode),
+                                     _p(Tl), _p(Ks))
+    return Tl, Ks
+
+
+def pair_flux(a: float, b: float) -> float:
+    return float(lib().oracle_pair_flux(float(a), float(b)))
+
+
+def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=None,
+             source=None, Ce_SI=1.0, vatom_A3=1.0, t_start=0.0):
+    """In place on T and A; returns (status, E_src increment)."""
+    n = rowptr.shape[0] - 1
+    esrc = np.zeros(1)
+    src = None
+    if source is not None:
+        src = np.ascontiguousarray([1.0, source["fluence_Jm2"], source["lp_A"], source["t0_fs"],
+                                    source["sigma_fs"]], dtype=np.float64)
+        depth = np.ascontiguousarray(depth, dtype=np.float64)
+    st = lib().oracle_substeps(n, _p(rowptr), _p(col), _p(T), _p(Tl), _p(chi), _p(A), int(n_sub),
+                               float(dt), float(Tmax), float(K), float(cG), float(VG),
+                               _p(depth) if depth is not None else None,
+                               _p(src) if src is not None else None, float(Ce_SI),
+                               float(vatom_A3), float(t_start), _p(esrc))
+    return st, float(esrc[0])
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.empty(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def gauss3(atom_id: int, step: int, seed: int):
+    g = np.empty(3)
+    lib().oracle_gauss3(int(atom_id), int(step), int(seed), _p(g))
+    return g
+
+
+def couple(v, mass_of_atom, A, T, chi, *, mode, frozen, seed, md_step, dt_md, gamma_fs, VC):
+    n = T.shape[0]
+    dKE = np.empty(n)
+    stopped = lib().oracle_couple(n, _p(v), _p(mass_of_atom), _p(A), _p(T), _p(chi), int(mode),
+                                  int(frozen), int(seed), int(md_step), float(dt_md),
+                                  float(gamma_fs), float(VC), _p(dKE))
+    return dKE, int(stopped)
+
+
+# --------------------------------------------------------------------------
+# material law and derived per-step scalars (Sec. 2, Eq. Kij)
+
+def ce_integral(T: np.ndarray, gamma: float, cap: float) -> np.ndarray:
+    """int_0^T C_e(T') dT' per unit volume for C_e = min(gamma T, cap) [J m^-3]."""
+    T = np.asarray(T, dtype=np.float64)
+    if cap <= 0:
+        return 0.5 * gamma * T * T
+    Tc = cap / gamma
+    return np.where(T <= Tc, 0.5 * gamma * T * T, 0.5 * cap * Tc + cap * (T - Tc))
+
+
+class OracleSim:
+    """MD-step driver around the oracle primitives, with the same call sequence
+    as the library: set_te -> per MD step [build(x, v) -> substeps(n) ->
+    couple(v, dt_md)] -> energy().  All arrays in original atom order, FP64.
+
+    p: dict with keys rc, dt_sub, Tmax, gamma_Ce, Ce_cap_kB, kappa0,
+    kappa_mode, G, eps_ke, dim_d, zb2, couple_mode, frozen, seed, dof_mode,
+    vatom (<= 0: box volume / N), and optionally 'laser' (dict with
+    fluence_Jm2, lp_A, t0_fs, sigma_fs) with `depth` per atom.
+    """
+
+    def __init__(self, p: dict, box, periodic, mass_amu, types, depth=None):
+        self.p = dict(p)
+        self.box = np.asarray(box, dtype=np.float64)
+        self.per = np.asarray(periodic, dtype=np.int32)
+        self.mass = np.asarray(mass_amu, dtype=np.float64)[np.asarray(types)]
+        self.mass = np.ascontiguousarray(self.mass)
+        self.n = self.mass.shape[0]
+        v = self.p.get("vatom", 0.0)
+        self.vatom = float(v) if v and v > 0 else float(np.prod(self.box)) / self.n
+        self.depth = depth
+        self.md_step = 0
+        self.T = None
+        self.A = np.zeros(self.n)
+        self.E_lat = 0.0
+        self.E_src = 0.0
+        self.n_stopped = 0
+        self.VC = None
+
+    # electronic temperature ------------------------------------------------
+    def set_te(self, Te):
+        self.T = np.ascontiguousarray(Te, dtype=np.float64).copy()
+        cap = self.cap_SI()
+        self.E_e0 = float((ce_integral(self.T, self.p["gamma_Ce"], cap)
+                           * self.vatom * 1e-30 / EV_J).sum())
+        self.E_base = self.E_e0
+        self.ST_base = float(self.T.sum())
+
+    def cap_SI(self) -> float:
+        c = self.p.get("Ce_cap_kB", 0.0)
+        return c * KB_J / (self.vatom * 1e-30) if c and c > 0 else 0.0
+
+    # per MD step -------------------------------------------------------------
+    def build(self, x, v):
+        p = self.p
+        if self.VC is not None:
+            s = float(self.T.sum())
+            self.E_base += self.VC * (s - self.ST_base)
+            self.ST_base = s
+        self.rowptr, self.col = neighbors(x, self.box, self.per, p["rc"])
+        self.Tl, self.Kself = lattice_temperature(self.rowptr, self.col, v, self.mass,
+                                                  p.get("dof_mode", 0))
+        self.chi = np.ascontiguousarray((self.Kself >= p["eps_ke"]).astype(np.uint8))
+        # global means: mean electronic temperature and the classical lattice
+        # temperature K / ((3/2) k_B N) (Sec. 2)
+        self.Te_mean = float(self.T.mean())
+        ke = 0.5 * self.mass * (v * v).sum(axis=1) * MVV_EV
+        self.Tlat = float(ke.sum() / (1.5 * KB_EV * self.n))
+        Ce = p["gamma_Ce"] * self.Te_mean
+        cap = self.cap_SI()
+        if cap > 0:
+            Ce = min(Ce, cap)
+        kappa = p["kappa0"] * (self.Te_mean / self.Tlat if p["kappa_mode"] == 1 else 1.0)
+        self.Ce = Ce
+        self.K = 2.0 * p["dim_d"] * kappa / (Ce * p["zb2"] * 1e-20) * 1e-15
+        self.cG = p["G"] / Ce * 1e-15
+        self.VG = p["G"] * self.vatom * 1e-30 / EV_J * 1e-15
+        self.VC = self.vatom * 1e-30 * Ce / EV_J
+        self.gamma_L = p["G"] * self.vatom * 1e-30 / (3.0 * KB_J) * 1e-15
+        nmax = int(np.diff(self.rowptr).max()) if self.n else 0
+        self.stability = p["dt_sub"] * (2.0 * nmax * self.K + self.cG)
+
+    def substeps(self, n_sub: int, t_start: float = 0.0):
+        if self.stability > 2.0:
+            raise ValueError("unstable substep")
+        p = self.p
+        st, es = substeps(self.rowptr, self.col, self.T, self.Tl, self.chi, self.A, n_sub,
+                          p["dt_sub"], p["Tmax"], self.K, self.cG, self.VG, depth=self.depth,
+                          source=p.get("laser"), Ce_SI=self.Ce, vatom_A3=self.vatom,
+                          t_start=t_start)
+        if st < 0:
+            raise FloatingPointError(f"theta left [0,1] at substep {-st - 1}")
+        self.E_src += es
+
+    def couple(self, v, dt_md: float):
+        p = self.p
+        dKE, stopped = couple(v, self.mass, self.A, self.T, self.chi, mode=p["couple_mode"],
+                              frozen=p["frozen"], seed=p["seed"], md_step=self.md_step,
+                              dt_md=dt_md, gamma_fs=self.gamma_L, VC=self.VC)
+        self.E_lat += float(dKE.sum())
+        self.n_stopped += stopped
+        self.md_step += 1
+        return dKE
+
+    def energy(self) -> dict:
+        s = float(self.T.sum())
+        E_e = self.E_base + self.VC * (s - self.ST_base) if self.VC is not None else self.E_base
+        return {"E_e": E_e, "E_lat": self.E_lat, "E_src": self.E_src, "E_e0": self.E_e0,
+                "sum_T": s, "max_T": float(self.T.max()),
+                "drift": (E_e + self.E_lat - self.E_src - self.E_e0) / self.E_e0}

@@ -1,0 +1,428 @@
+/*
+ * ehc_oracle.c -- plain, slow FP64 CPU oracle of the l2T-MD electronic
+ * heat-conduction step (Ullah & Ponga, arXiv 1810.12357).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark use it.  It shares no code, header, table or
+ * constant with the CUDA library; it is written from the paper's equations.
+ *
+ * Compiled with -O2 -fno-fast-math -ffp-contract=off, so every expression is
+ * evaluated as written in IEEE double precision.  Loops over atoms may run in
+ * parallel (OpenMP); each atom's sum is taken over its neighbour row in
+ * ascending original-id order, so results do not depend on the thread count.
+ *
+ * Units: Angstrom, fs, eV, amu, K.  Positions are mapped to a 2^-20 Angstrom
+ * fixed-point grid so that the neighbour test is exact integer arithmetic.
+ *
+ * Parity status of each function: see the pins listed beside it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 */
+static const double O_KB = 8.617333262e-5;          /* eV / K */
+static const double O_AMU = 1.66053906660e-27;      /* kg */
+static const double O_EV = 1.602176634e-19;         /* J */
+
+static double o_mvv_ev(void) { return O_AMU * 1.0e10 / O_EV; } /* amu*(A/fs)^2 in eV */
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fixed-point positions.  Neighbour selection "x_j - x_i <= r_c" (Sec. 2,
+ * lattice-temperature definition) evaluated exactly on integers.
+ * q = round-half-even(x * 2^20); periodic axes wrapped into [0, Lq).
+ * Pins: brute-force vs cell search; 18 neighbours per atom in perfect FCC Cu. */
+int oracle_quantize(int64_t n, const double *x, const double *box, const int32_t *periodic,
+                    int32_t *q, int64_t *Lq_out) {
+  int64_t Lq[3];
+  for (int k = 0; k < 3; ++k) {
+    Lq[k] = llrint(box[k] * 1048576.0);
+    Lq_out[k] = Lq[k];
+    if (Lq[k] <= 0 || Lq[k] >= 2147483647LL) return -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      int64_t v = llrint(x[3 * i + k] * 1048576.0);
+      if (periodic[k]) {
+        v %= Lq[k];
+        if (v < 0) v += Lq[k];
+      } else if (v < 0 || v >= Lq[k]) {
+        return -2; /* atoms must lie inside non-periodic extents */
+      }
+      q[3 * i + k] = (int32_t)v;
+    }
+  }
+  return 0;
+}
+
+/* Minimum-image displacement on the integer grid; a displacement of exactly
+ * half the box keeps its sign. */
+static int64_t o_disp(int64_t d, int64_t L, int per) {
+  if (per) {
+    if (2 * d > L) d -= L;
+    else if (2 * d < -L) d += L;
+  }
+  return d;
+}
+
+static int o_within(const int32_t *qi, const int32_t *qj, const int64_t *Lq, const int32_t *per,
+                    int64_t rcq) {
+  int64_t s = 0;
+  for (int k = 0; k < 3; ++k) {
+    int64_t d = o_disp((int64_t)qj[k] - (int64_t)qi[k], Lq[k], per[k]);
+    if (d > rcq || d < -rcq) return 0;
+    s += d * d;
+  }
+  return s <= rcq * rcq;
+}
+
+/* O(N^2) reference search: row i lists every j != i with |x_j - x_i| <= r_c,
+ * ascending j.  Returns the number of entries, or -1 if cap is exceeded. */
+int64_t oracle_neighbors_brute(int64_t n, const int32_t *q, const int64_t *Lq,
+                               const int32_t *periodic, int64_t rcq, int64_t *rowptr,
+                               int32_t *col, int64_t cap) {
+  int64_t nnz = 0;
+  rowptr[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      if (o_within(q + 3 * i, q + 3 * j, Lq, periodic, rcq)) {
+        if (nnz >= cap) return -1;
+        col[nnz++] = (int32_t)j;
+      }
+    }
+    rowptr[i + 1] = nnz;
+  }
+  return nnz;
+}
+
+static int o_cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* Same list by a linked cell search: cells of width >= r_c, each atom looks at
+ * the (deduplicated) 3x3x3 block of cells around its own.  Rows are sorted
+ * ascending by original id.  Two passes: counts, then fill. */
+int64_t oracle_neighbors_cells(int64_t n, const int32_t *q, const int64_t *Lq,
+                               const int32_t *periodic, int64_t rcq, int64_t *rowptr,
+                               int32_t *col, int64_t cap) {
+  int64_t nc[3];
+  for (int k = 0; k < 3; ++k) {
+    nc[k] = Lq[k] / rcq;
+    if (nc[k] < 1) nc[k] = 1;
+    if (nc[k] > 1024) nc[k] = 1024;
+  }
+  int64_t ncell = nc[0] * nc[1] * nc[2];
+  int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
+  int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  int64_t *cellof = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  if (!head || !next || !cellof) { free(head); free(next); free(cellof); return -2; }
+  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+  /* insert in descending id so every cell chain is ascending */
+  for (int64_t i = n - 1; i >= 0; --i) {
+    int64_t c3[3];
+    for (int k = 0; k < 3; ++k) {
+      int64_t c = ((int64_t)q[3 * i + k] * nc[k]) / Lq[k];
+      if (c >= nc[k]) c = nc[k] - 1;
+      c3[k] = c;
+    }
+    int64_t c = c3[0] + nc[0] * (c3[1] + nc[1] * c3[2]);
+    cellof[i] = c;
+    next[i] = head[c];
+    head[c] = i;
+  }
+  int64_t *cnt = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int64_t overflow = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : overflow)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t ci[3];
+      int64_t c = cellof[i];
+      ci[0] = c % nc[0];
+      ci[1] = (c / nc[0]) % nc[1];
+      ci[2] = c / (nc[0] * nc[1]);
+      /* candidate cell offsets per axis, without repeats */
+      int64_t off[3][3];
+      int noff[3];
+      for (int k = 0; k < 3; ++k) {
+        noff[k] = 0;
+        for (int64_t d = -1; d <= 1; ++d) {
+          int64_t cc = ci[k] + d;
+          if (periodic[k]) {
+            cc = ((cc % nc[k]) + nc[k]) % nc[k];
+          } else if (cc < 0 || cc >= nc[k]) {
+            continue;
+          }
+          int dup = 0;
+          for (int m = 0; m < noff[k]; ++m) dup |= (off[k][m] == cc);
+          if (!dup) off[k][noff[k]++] = cc;
+        }
+      }
+      int64_t m = 0;
+      int64_t base = pass ? rowptr[i] : 0;
+      for (int a = 0; a < noff[2]; ++a)
+        for (int b = 0; b < noff[1]; ++b)
+          for (int d = 0; d < noff[0]; ++d) {
+            int64_t cell = off[0][d] + nc[0] * (off[1][b] + nc[1] * off[2][a]);
+            for (int64_t j = head[cell]; j >= 0; j = next[j]) {
+              if (j == i) continue;
+              if (o_within(q + 3 * i, q + 3 * j, Lq, periodic, rcq)) {
+                if (pass) {
+                  if (base + m < cap) col[base + m] = (int32_t)j;
+                  else overflow += 1;
+                }
+                ++m;
+              }
+            }
+          }
+      if (!pass) cnt[i] = m;
+      else if (base + m <= cap) qsort(col + base, (size_t)m, sizeof(int32_t), o_cmp_i32);
+    }
+    if (!pass) {
+      rowptr[0] = 0;
+      for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + cnt[i];
+    }
+  }
+  free(head); free(next); free(cellof); free(cnt);
+  if (overflow || rowptr[n] > cap) return -1;
+  return rowptr[n];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local lattice temperature (Sec. 2, T_i^lat definition): over the set S of
+ * atom i and its neighbours within r_c, with the centre-of-mass velocity of S
+ * removed, T_i = sum_S (1/2) m |v - v_com|^2 / ((3/2) k_B N_j), N_j = |S|.
+ * dof_mode 1 divides by (3/2) k_B (N_j - 1) instead.
+ * Also returns each atom's own raw kinetic energy K_i = (1/2) m v_i.v_i [eV]
+ * (Eq. Xi), used by the epsilon guard.
+ * Pins: a uniform-velocity set gives exactly 0; a two-atom closed form. */
+void oracle_lattice_temperature(int64_t n, const int64_t *rowptr, const int32_t *col,
+                                const double *v, const double *mass_of_atom, int dof_mode,
+                                double *Tl, double *Kself) {
+  const double mvv = o_mvv_ev();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t len = rowptr[i + 1] - rowptr[i] + 1;
+    double msum = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+    for (int64_t t = -1; t < len - 1; ++t) {
+      int64_t j = (t < 0) ? i : col[rowptr[i] + t];
+      double m = mass_of_atom[j];
+      msum += m;
+      px += m * v[3 * j + 0];
+      py += m * v[3 * j + 1];
+      pz += m * v[3 * j + 2];
+    }
+    double vcx = px / msum, vcy = py / msum, vcz = pz / msum;
+    double ke = 0.0;
+    for (int64_t t = -1; t < len - 1; ++t) {
+      int64_t j = (t < 0) ? i : col[rowptr[i] + t];
+      double dx = v[3 * j + 0] - vcx, dy = v[3 * j + 1] - vcy, dz = v[3 * j + 2] - vcz;
+      ke += 0.5 * mass_of_atom[j] * (dx * dx + dy * dy + dz * dz) * mvv;
+    }
+    double dof_n = (dof_mode == 1) ? (double)(len - 1) : (double)len;
+    Tl[i] = (dof_n > 0.0) ? ke / (1.5 * O_KB * dof_n) : 0.0;
+    double vi2 = v[3 * i + 0] * v[3 * i + 0] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+    Kself[i] = 0.5 * mass_of_atom[i] * vi2 * mvv;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair term of Eq. HeatTransport, literally: with theta_i = a, theta_j = b,
+ * Delta e_ji = -(theta_j - theta_i) and Delta e_ij = -(theta_i - theta_j),
+ *   f(a, b) = b (1 - a) exp(a - b) - a (1 - b) exp(b - a).
+ * Evaluating f(b, a) performs the same two products in swapped roles, so
+ * f(b, a) == -f(a, b) bit for bit.  Pins: antisymmetry, f(a, a) == 0,
+ * linearisation slope 1 - 2a(1 - a). */
+double oracle_pair_flux(double a, double b) {
+  double gain = b * (1.0 - a) * exp(a - b);
+  double loss = a * (1.0 - b) * exp(b - a);
+  return gain - loss;
+}
+
+/* Optional time-dependent source (Sec. 5, Eq. LaserIntesity), a Gaussian pulse
+ * absorbed with exponential decay below the irradiated surface:
+ *   S(depth, t) = (F / l_p) exp(-depth / l_p) exp(-(t - t0)^2 / (2 s^2)) / (s sqrt(2 pi))
+ * [W m^-3], which raises T at rate S / C_e. */
+typedef struct {
+  int on;
+  double fluence_Jm2, lp_A, t0_fs, sigma_fs;
+} oracle_source;
+
+/* n_sub explicit forward-Euler substeps of Eq. HeatTransport (Jacobi: every
+ * atom reads the same snapshot theta^n), dt in fs:
+ *   T_i += dt * ( Tmax * K * F_i - chi_i * (G/C_e) * (T_i - T_l,i) + q_i(t) )
+ * with F_i = sum_j f(theta_i, theta_j) over row i in order, theta = T / Tmax
+ * (T_min = 0, Sec. 2).  K is the pair rate of Eq. Kij [1/fs]; cG = G/C_e [1/fs].
+ * The energy the electrons hand to atom i's lattice (Eq. RateExchange) is
+ * accumulated as A_i += dt * chi_i * VG * (T_i - T_l,i), VG = G * V_atom
+ * [eV / (K fs)], using T_i before the update.  E_src (if non-null) receives the
+ * source energy V_atom * C_e * q_i * dt summed over atoms and substeps.
+ * chi_i = 0 switches the coupling off for atom i (Eq. Xi guard).
+ * Returns the number of substeps done, or -(substep+1) if some theta left
+ * [0, 1] or became NaN. */
+int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double *T,
+                    const double *Tl, const uint8_t *chi, double *A, int n_sub, double dt,
+                    double Tmax, double K, double cG, double VG, const double *depth,
+                    const double *src, double Ce_SI, double vatom_A3, double t_start,
+                    double *E_src) {
+  double *theta = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *Tn = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  if (!theta || !Tn) { free(theta); free(Tn); return -1000000; }
+  oracle_source S = {0, 0, 0, 0, 0};
+  if (src) { S.on = (src[0] != 0.0); S.fluence_Jm2 = src[1]; S.lp_A = src[2]; S.t0_fs = src[3]; S.sigma_fs = src[4]; }
+  double esrc = 0.0;
+  int status = n_sub;
+  for (int s = 0; s < n_sub; ++s) {
+    double t = t_start + dt * (double)s;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      theta[i] = T[i] / Tmax;
+      if (!(theta[i] >= 0.0 && theta[i] <= 1.0)) bad = 1;
+    }
+    if (bad) { status = -(s + 1); break; }
+    double pulse = 0.0;
+    if (S.on) {
+      double sig_s = S.sigma_fs * 1.0e-15;
+      double dtp = (t - S.t0_fs) / S.sigma_fs;
+      /* W m^-3 at depth 0 */
+      pulse = S.fluence_Jm2 / (S.lp_A * 1.0e-10) * exp(-0.5 * dtp * dtp) /
+              (sig_s * sqrt(2.0 * M_PI));
+    }
+    double esrc_step = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : esrc_step)
+    for (int64_t i = 0; i < n; ++i) {
+      double F = 0.0;
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) F += oracle_pair_flux(theta[i], theta[col[p]]);
+      double dTdt = Tmax * K * F;
+      if (chi[i]) {
+        dTdt -= cG * (T[i] - Tl[i]);
+        A[i] += dt * VG * (T[i] - Tl[i]);
+      }
+      if (S.on) {
+        double Sw = pulse * exp(-depth[i] / S.lp_A);        /* W m^-3 */
+        dTdt += Sw / Ce_SI * 1.0e-15;                        /* K / fs */
+        esrc_step += Sw * vatom_A3 * 1.0e-30 * dt * 1.0e-15 / O_EV; /* eV */
+      }
+      Tn[i] = T[i] + dt * dTdt;
+    }
+    esrc += esrc_step;
+    memcpy(T, Tn, sizeof(double) * (size_t)n);
+  }
+  if (E_src) *E_src += esrc;
+  free(theta); free(Tn);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator, from its published definition
+ * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11): ten rounds of two 32x32->64 multiplications with the round keys
+ * bumped by the Weyl constants.  Pins: published known-answer vectors. */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Three standard normals for atom `id` at MD step `step`: counter
+ * (id lo, id hi, step lo, step hi), key (seed lo, seed hi); uniforms
+ * u = (x + 1/2) / 2^32 in (0, 1); Box-Muller in double precision. */
+void oracle_gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
+  uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
+  uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  oracle_philox4x32_10(c, k, r);
+  double u[4];
+  for (int m = 0; m < 4; ++m) u[m] = ((double)r[m] + 0.5) / 4294967296.0;
+  double r1 = sqrt(-2.0 * log(u[0]));
+  double r2 = sqrt(-2.0 * log(u[2]));
+  g[0] = r1 * cos(2.0 * M_PI * u[1]);
+  g[1] = r1 * sin(2.0 * M_PI * u[1]);
+  g[2] = r2 * cos(2.0 * M_PI * u[3]);
+}
+
+/* Electron -> lattice hand-over once per MD step (Eqs. Motion, WorkDone, Xi).
+ * Arrays in original atom order.  For each atom with chi_i = 1 the lattice
+ * receives exactly the energy A_i the electrons gave up:
+ *   mode 0 (damping, the paper's choice): v_i <- s v_i, s^2 = (K_i + A_i) / K_i.
+ *     Integrating m dv/dt = xi m v with xi of Eq. Xi over the step gives this
+ *     scaling; it transfers A_i exactly.
+ *   mode 1 (Langevin): trial v* = v e^{-g dt} + sqrt(kB T_e,i (1 - e^{-2 g dt}) / m) eta,
+ *     g = G V_atom / (3 kB), eta from oracle_gauss3; then v_i <- v* sqrt((K_i + A_i) / K*),
+ *     so the random force and friction act and the exchanged energy is A_i.
+ * If K_i + A_i < 0 the atom is stopped (lattice hands over only K_i) and the
+ * difference is returned to the electrons: T_i += (A_i - dKE_i) / VC,
+ * VC = V_atom C_e [eV/K].  frozen != 0 leaves v untouched (the lattice is a
+ * bookkeeping sink) and reports dKE_i = A_i.  A is reset to zero.
+ * dKE (out) holds each atom's kinetic-energy change.  Returns the number of
+ * atoms that had to be stopped. */
+int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *A, double *T,
+                      const uint8_t *chi, int mode, int frozen, uint64_t seed, uint64_t md_step,
+                      double dt_md, double gamma_fs, double VC, double *dKE) {
+  const double mvv = o_mvv_ev();
+  int64_t stopped = 0;
+#pragma omp parallel for schedule(static) reduction(+ : stopped)
+  for (int64_t i = 0; i < n; ++i) {
+    dKE[i] = 0.0;
+    if (!chi[i]) { A[i] = 0.0; continue; }
+    if (frozen) { dKE[i] = A[i]; A[i] = 0.0; continue; }
+    double m = mass_of_atom[i];
+    double *vi = v + 3 * i;
+    double K0 = 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * mvv;
+    double target = K0 + A[i];
+    if (target < 0.0) { target = 0.0; stopped += 1; }
+    double w[3] = {vi[0], vi[1], vi[2]};
+    if (mode == 1) {
+      double g[3];
+      oracle_gauss3((uint64_t)i, md_step, seed, g);
+      double e1 = exp(-gamma_fs * dt_md);
+      double e2 = exp(-2.0 * gamma_fs * dt_md);
+      double sig = sqrt(O_KB * T[i] * (1.0 - e2) / (m * mvv));
+      for (int k = 0; k < 3; ++k) w[k] = vi[k] * e1 + sig * g[k];
+    }
+    double Kw = 0.5 * m * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * mvv;
+    double s = (Kw > 0.0) ? sqrt(target / Kw) : 0.0;
+    for (int k = 0; k < 3; ++k) vi[k] = w[k] * s;
+    double K1 = 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * mvv;
+    dKE[i] = K1 - K0;
+    if (target == 0.0) T[i] += (A[i] - dKE[i]) / VC;
+    A[i] = 0.0;
+  }
+  return stopped;
+}
