@@ -1,0 +1,334 @@
+"""Throughput of the electronic heat-conduction path (l2T-MD, arXiv 1810.12357)
+on GB300: atom-substeps per second on the 4,000,000-atom swift-ion track.
+
+One step = one MD step of the whole path: fixed-point binning and the
+neighbour list, the local lattice temperature and per-step C_e, kappa_e and K,
+100 electronic substeps (FP32 pair flux, FP64 state and ledger), the Langevin
+hand-over to the atoms, and the free-flight drift that stands in for the MD
+integrator.  Inputs: FCC Cu 100^3 cells, 300 K Maxwell velocities, radial
+Gaussian T_e (20,000 K peak, r0 = 2 nm) on 300 K.  The working set (~0.9 GB)
+is far larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--cells C]
+
+N > 1 (launched by torch.distributed.run): every rank advances its own
+independent replica (weak scaling, no collective on the data path); the step
+time is the maximum over ranks.  --impl reference times the CPU oracle, as it
+stands, on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom·substeps/s, 4M-atom track: plain vs learned propagator @≤1% T_e err"
+UNIT = "atom·substeps/s"
+N_SUB = 100            # substeps per MD step (1 fs MD step / 100 substeps)
+DT_MD = 1.0            # fs
+N_NB = 18              # neighbours per atom in FCC Cu at r_c = 4.0 A
+B_ALG = 4 * N_NB + 44  # algorithmic bytes per atom-substep of the substep kernel
+# kernels launched per MD step: bin + 3-phase scan + scatter + cell sort + gather
+# + neighbour list + lattice temperature + 2 reduction kernels = 11; N_SUB substeps;
+# hand-over + 2 reduction kernels = 3; drift = 1
+LAUNCHES_PER_STEP = 11 + N_SUB + 3 + 1
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(cells: int):
+    from paper_1810_12357_gb300 import inputs as I
+    s = I.track_system(cells, seed=2)
+    p = I.params_track()
+    return s, p
+
+
+def config_dict(cells: int, n: int, extra=None, n_sub: int = N_SUB):
+    d = {"workload": f"swift-ion track, FCC Cu {cells}^3 cells ({n:,} atoms, periodic), 300 K Maxwell "
+                     f"velocities, T_e radial Gaussian 20,000 K peak r0=2 nm on 300 K, C_e=gamma*T_e capped "
+                     f"at 3 k_B/atom, K_e=K0*T_e/T_l, G=1e17, r_c=4.0 A, Langevin hand-over, free flight",
+         "n_atoms": n, "substeps_per_step": n_sub, "dt_sub_fs": 1.0e-3, "dt_md_fs": DT_MD,
+         "pair_flux": "fp32", "state_and_ledger": "fp64",
+         "l2": "inputs larger than L2 (~0.9 GB working set), no flush"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1810_12357_gb300 import Ehc
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    s, p = workload(args.cells)
+    n = s.n
+    sim = Ehc(p, s)
+    sim.set_te(s.Te)
+    x = torch.as_tensor(s.x, device=dev).contiguous()
+    v = torch.as_tensor(s.v, device=dev).contiguous()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t_fs = 0.0
+    sub_ev = []
+
+    def step(record: bool):
+        nonlocal t_fs
+        sim.build_neighbors(x, v)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        sim.substep(N_SUB, t_fs)
+        if record:
+            e1.record(stream)
+            sub_ev.append((e0, e1))
+        sim.couple(v, DT_MD)
+        sim.drift(x, v, DT_MD)
+        t_fs += DT_MD
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    sub_ms = [a.elapsed_time(b) for a, b in sub_ev]
+    e = sim.energy()
+
+    # end to end through the host-buffer entry point: inputs copied in, results copied out
+    xh = torch.as_tensor(s.x).clone().pin_memory()
+    vh = torch.as_tensor(s.v).clone().pin_memory()
+    Teh = torch.empty(n, dtype=torch.float64).pin_memory()
+    h = Ehc(p, s)
+    h.set_te(s.Te)
+    e2e_steps = max(1, min(args.steps, 10))
+    for k in range(2):
+        h.md_step_host(xh, vh, N_SUB, k * DT_MD, DT_MD, Teh)
+    barrier()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for k in range(e2e_steps):
+        h.md_step_host(xh, vh, N_SUB, (k + 2) * DT_MD, DT_MD, Teh)
+    a1.record(stream)
+    barrier()
+    e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    h.close()
+
+    if ws > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    ms_step = ms / args.steps
+    value = ws * n * N_SUB * args.steps / (ms * 1e-3)
+    sub_launch_ms = statistics.mean(sub_ms) / N_SUB
+    achieved = B_ALG * n / (sub_launch_ms * 1e-3) / 1e9
+    peak, kind = _peaks()
+    traffic = _traffic_from_profile(n)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair flux / f64 state", "data": "synthetic",
+        "config": config_dict(args.cells, n, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                              "path": "plain"}),
+        "e2e": {"value": ws * n * N_SUB / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "substep_f32_kernel", "bytes_per_atom_substep": B_ALG,
+                     "peak_kind": kind, "substep_ms": sub_launch_ms},
+        "clocks": clocks,
+        "energy_drift": e["drift"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cells)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profile(n):
+    """DRAM bytes per substep launch from the committed ncu summary, scaled to n atoms."""
+    path = os.path.join(ROOT, "profiles", "substep_f32_track.json")
+    try:
+        d = json.load(open(path))
+        return d["dram_bytes_per_launch"] * n / d["n_atoms"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def cpu_baseline(cells: int, n_sub: int = N_SUB):
+    """One MD step of the same workload through the CPU oracle (neighbour build,
+    lattice temperature, n_sub substeps, Langevin hand-over), all host cores."""
+    import oracle
+    s, p = workload(cells)
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    v = s.v.copy()
+    t0 = time.perf_counter()
+    sim.build(s.x, v)
+    sim.substeps(n_sub, 0.0)
+    sim.couple(v, DT_MD)
+    dt = time.perf_counter() - t0
+    return {"value": s.n * n_sub / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one MD step ({n_sub} substeps, neighbour build, lattice temperature, hand-over) "
+                      f"of the {s.n:,}-atom track, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    s, p = workload(args.cells)
+    n_sub = args.ref_substeps
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    x = s.x.copy()
+    v = s.v.copy()
+    from paper_1810_12357_gb300 import inputs as I
+
+    def step():
+        sim.build(x, v)
+        sim.substeps(n_sub, 0.0)
+        sim.couple(v, DT_MD)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = s.n * n_sub * args.steps / dt
+    sample = (f"{args.steps} MD steps of {n_sub} substeps each (neighbour build, lattice temperature, "
+              f"substeps, hand-over) of the {s.n:,}-atom track")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args.cells, s.n, {"path": "CPU oracle"}, n_sub),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ehc", choices=["ehc", "reference"])
+    ap.add_argument("--cells", type=int, default=100)
+    ap.add_argument("--ref-substeps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ehc":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ehc.h -- C ABI of libehc: per-atom electronic heat conduction for
+ * two-temperature molecular dynamics on one GB300 GPU (sm_103a).
+ *
+ * Method: Ullah & Ponga, "A new approach for electronic heat conduction in
+ * molecular dynamics simulations" (arXiv 1810.12357), Sec. 2.  Every atom
+ * carries an electronic temperature T_i; between two MD steps the library
+ * advances it by explicit substeps of the master equation (Eq. HeatTransport)
+ * with the pair rate of Eq. Kij, couples it to a local lattice temperature
+ * (Sec. 2, T_i^lat) through the constant G, and hands the exchanged energy to
+ * the atoms (Eqs. RateExchange, Motion, WorkDone, Xi).
+ *
+ * Conventions shared by every call:
+ *  - Units: Angstrom, fs, eV, amu, K on the atom side; material constants in SI
+ *    (J, W, m, K) as the paper states them; converted once in ehc_create.
+ *  - Per-atom arrays the caller passes are in the caller's ("original") atom
+ *    order, FP64, and live in device memory unless a name ends in _host.
+ *    The library only borrows them for the duration of the call.
+ *  - All GPU work is queued on the CUDA stream given to ehc_create (NULL: the
+ *    legacy default stream) and is asynchronous unless a call says it syncs.
+ *  - Return value: EHC_OK (0) or a negative EHC_E_* code.  Errors found on the
+ *    device (theta outside [0,1], NaN, neighbour-list overflow, atoms outside a
+ *    non-periodic box) are sticky in a device word and are returned by the next
+ *    call that synchronises (ehc_build_neighbors, ehc_energy, ehc_sync).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef EHC_H
+#define EHC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EHC_OK 0
+#define EHC_E_INVAL (-1)        /* bad argument or size */
+#define EHC_E_NOMEM (-2)        /* device or host allocation failed */
+#define EHC_E_CUDA (-3)         /* CUDA runtime error */
+#define EHC_E_UNSTABLE (-4)     /* substep violates dt (2 n_max K + G/C_e) <= 2 */
+#define EHC_E_RANGE (-5)        /* theta = T/T_max left [0,1] or became NaN */
+#define EHC_E_NBR_OVERFLOW (-6) /* an atom has more neighbours than max_neighbors */
+#define EHC_E_TIMEOUT (-7)      /* a bounded device wait gave up */
+#define EHC_E_STATE (-8)        /* call order violated (e.g. substep before build) */
+#define EHC_E_BOUNDS (-9)       /* atom outside the extent of a non-periodic axis */
+
+/* Parameters of one system.  Paper references:
+ *   Tmax_K          T^e_max of the normalisation theta = T/T_max, T_min = 0 (Sec. 2)
+ *   gamma_Ce        C_e = gamma T_e (Sec. 2) [J m^-3 K^-2]; Ce_cap_kB > 0 caps C_e at
+ *                   Ce_cap_kB * k_B per atomic volume
+ *   kappa0, kappa_mode  kappa_e = kappa0 (mode 0) or kappa0 <T_e>/<T_lat> (mode 1, Sec. 2);
+ *                   C_e and kappa_e use the system means at the start of each MD step
+ *   dim_d, zb2_A2   d and Z b^2 of Eq. Kij: K = 2 kappa_e d / (C_e Z b^2) [1/fs]
+ *   G               electron-phonon coupling of Eq. HeatTransport [W m^-3 K^-1]
+ *   eps_ke_eV       atoms with own kinetic energy below this do not exchange (Eq. Xi guard)
+ *   rc_A            neighbour cutoff, inclusive (Sec. 2 T_i^lat and Sec. 2.1)
+ *   dt_sub_fs       electronic substep (Sec. 2.1 sub-stepping)
+ *   vatom_A3        V_atom = V/N (Eq. RateExchange); <= 0 means box volume / N
+ *   couple_mode     0: damping of Eq. Motion (paper); 1: Langevin friction + random
+ *                   force with the same exact energy hand-over
+ *   frozen          1: velocities are never changed (the lattice is a bookkeeping sink)
+ *   dof_mode        0: T_lat divisor (3/2) k_B N_j (paper); 1: (3/2) k_B (N_j - 1)
+ *   flux_prec       0: pair flux in FP32 on the (T - Tref)/Tmax mirror, state in FP64;
+ *                   1: pair flux in FP64
+ *   Tref_K          reference temperature of the FP32 mirror
+ *   laser_*         optional source of Eq. LaserIntesity (Sec. 5): absorbed fluence,
+ *                   penetration length, pulse centre and standard deviation
+ *   seed            Philox4x32-10 key of the Langevin random force
+ *   max_neighbors   width of the neighbour table (<= 0: 32, at most 64)
+ *   use_graph       1: replay substep loops from a captured CUDA graph */
+typedef struct ehc_params {
+  double rc_A;
+  double dt_sub_fs;
+  double Tmax_K;
+  double Tref_K;
+  double gamma_Ce;
+  double Ce_cap_kB;
+  double kappa0;
+  double G;
+  double eps_ke_eV;
+  double zb2_A2;
+  double vatom_A3;
+  double laser_fluence_Jm2;
+  double laser_lp_A;
+  double laser_t0_fs;
+  double laser_sigma_fs;
+  uint64_t seed;
+  int32_t dim_d;
+  int32_t kappa_mode;
+  int32_t couple_mode;
+  int32_t frozen;
+  int32_t dof_mode;
+  int32_t flux_prec;
+  int32_t laser_on;
+  int32_t max_neighbors;
+  int32_t use_graph;
+  int32_t reserved[7];
+} ehc_params;
+
+/* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked
+ * incrementally: E_e0 = sum_i V_atom int_0^{T_i} C_e(T) dT at ehc_set_te, then
+ * each MD step adds V_atom C_e sum_i dT_i with that step's C_e.  E_lat is the
+ * kinetic energy the lattice received, E_src the energy of the source term.
+ * drift = (E_e + E_lat - E_src - E_e0) / E_e0. */
+typedef struct ehc_energy_t {
+  double E_e, E_lat, E_src, E_e0, drift;
+  double sum_T, max_T, mean_T;
+  double Te_mean_step, Tlat_step;   /* system means used for C_e, kappa_e this MD step */
+  double Ce_SI, K_per_fs, stability; /* stability = dt (2 n_max K + G/C_e), must be <= 2 */
+  int64_t n_stopped;                /* atoms whose kinetic energy could not pay A_i */
+  int64_t md_step;
+  int32_t max_count;                /* largest neighbour count */
+  int32_t device_error;             /* bit set of device-side error flags */
+} ehc_energy_t;
+
+typedef struct ehc_ctx ehc_ctx;
+
+/* Create a context for n_atoms atoms in an orthorhombic box [0, box_A[k]).
+ * periodic[k] != 0 makes axis k periodic (box_A[k] must then exceed 2 r_c).
+ * mass_amu_host: n_types masses (host memory, 1 <= n_types <= 16).
+ * type_dev: per-atom type index in original order (device, int32), or NULL when
+ * n_types == 1.  stream: a cudaStream_t or NULL.  Allocates all device memory
+ * the context will use; no later call allocates.  *out receives the context. */
+int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3],
+               const int32_t periodic[3], const double *mass_amu_host, int32_t n_types,
+               const int32_t *type_dev, void *stream, ehc_ctx **out);
+
+/* Copy the initial electronic temperatures Te_dev [N] (original order, device)
+ * into the context and reset the energy ledger (E_e0). */
+int ehc_set_te(ehc_ctx *c, const double *Te_dev);
+
+/* Per-atom depth below the irradiated surface [A] (device, original order), used
+ * by the laser source of Eq. LaserIntesity.  Kept until replaced. */
+int ehc_set_depth(ehc_ctx *c, const double *depth_dev);
+
+/* Start of an MD step: bin atoms into cells, build the full neighbour list
+ * (all j != i with |x_j - x_i| <= r_c on a 2^-20 A fixed-point grid, minimum
+ * image on periodic axes; Sec. 2), compute the local lattice temperature of
+ * every atom from its neighbours' velocities (Sec. 2, T_i^lat, centre-of-mass
+ * velocity removed), the system means <T_e> and T_lat = K/((3/2) k_B N), and from
+ * them C_e, kappa_e and K of Eq. Kij for this step.  x_dev, v_dev: [N,3].
+ * Synchronises the stream once (reads back a few scalars). */
+int ehc_build_neighbors(ehc_ctx *c, const double *x_dev, const double *v_dev);
+
+/* n_sub explicit Euler substeps of Eq. HeatTransport (all atoms read the same
+ * snapshot), starting at time t_fs (used by the laser source).  Returns
+ * EHC_E_UNSTABLE without launching if dt (2 n_max K + G/C_e) > 2.  Allocates
+ * nothing; asynchronous. */
+int ehc_substep(ehc_ctx *c, int32_t n_sub, double t_fs);
+
+/* End of an MD step: hand the energy each atom's electrons gave up during the
+ * substeps to its velocity (Eqs. RateExchange, WorkDone, Xi), in place on v_dev
+ * [N,3].  dt_md_fs is the MD step (Langevin friction and noise amplitude). */
+int ehc_couple(ehc_ctx *c, double *v_dev, double dt_md_fs);
+
+/* Free flight x += v dt, wrapped into the box on periodic axes: the stand-in
+ * for the host MD integrator when no interatomic forces are available. */
+int ehc_drift(ehc_ctx *c, double *x_dev, const double *v_dev, double dt_fs);
+
+/* One whole MD step with HOST buffers: copies x_host, v_host [N,3] to the
+ * device, runs build, n_sub substeps from t_fs, couple and drift, and copies
+ * x, v and the electronic temperatures back (Te_host_out [N]).  Host buffers
+ * should be page-locked for full copy speed.  Synchronises. */
+int ehc_md_step_host(ehc_ctx *c, double *x_host, double *v_host, int32_t n_sub,
+                     double t_fs, double dt_md_fs, double *Te_host_out);
+
+/* Energy ledger and diagnostics; synchronises and returns any sticky device
+ * error as its EHC_E_* code (the ledger is filled in either way). */
+int ehc_energy(ehc_ctx *c, ehc_energy_t *out);
+
+/* Wait for queued work; return a sticky device error if one was raised. */
+int ehc_sync(ehc_ctx *c);
+
+/* Electronic temperatures [N] (original order) into Te_dev_out (device). */
+int ehc_get_te(ehc_ctx *c, double *Te_dev_out);
+
+/* Local lattice temperatures of the current MD step [N] (original order, device);
+ * atoms below the kinetic-energy guard are reported as -1. */
+int ehc_get_lattice_temperature(ehc_ctx *c, double *Tl_dev_out);
+
+/* Current neighbour list in canonical form: rows in original atom order, each
+ * row's original ids ascending.  rowptr_host [N+1]; col_host has room for cap
+ * entries.  Returns EHC_E_INVAL if cap is too small.  Synchronises. */
+int ehc_export_neighbors(ehc_ctx *c, int64_t *rowptr_host, int32_t *col_host, int64_t cap);
+
+/* Three standard normals per listed atom from the Philox4x32-10 stream the
+ * Langevin hand-over uses: counter (id, md_step), key seed; out_dev [n,3]. */
+int ehc_philox_normals(const int64_t *ids_dev, int64_t n, uint64_t md_step, uint64_t seed,
+                       double *out_dev, void *stream);
+
+/* Checkpoint: electronic temperatures, pending exchange energies, ledger,
+ * step counter and Philox key to a file; ehc_load restores them into a context
+ * created with the same parameters and atom count. */
+int ehc_save(ehc_ctx *c, const char *path);
+int ehc_load(ehc_ctx *c, const char *path);
+
+void ehc_destroy(ehc_ctx *c);
+const char *ehc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EHC_H */

@@ -1,0 +1,286 @@
+"""Python binding of libehc (include/ehc.h): electronic heat conduction for
+two-temperature molecular dynamics (Ullah & Ponga, arXiv 1810.12357) on one
+GB300 GPU.
+
+The binding only marshals arguments: every computation runs in the CUDA
+kernels of ``libehc.so``.  PyTorch supplies device memory and the stream.
+There is no CPU fallback: if the library or a GPU is missing, calls raise.
+
+    from paper_1810_12357_gb300 import Ehc, inputs
+    s = inputs.track_system(20, seed=2)
+    sim = Ehc(inputs.params_track(), s)          # ehc_create
+    sim.set_te(s.Te)                             # ehc_set_te
+    sim.build_neighbors(x, v)                    # per MD step
+    sim.substep(100, t_fs)
+    sim.couple(v, 1.0)
+    sim.energy()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libehc.so")
+
+EHC_OK = 0
+ERRORS = {-1: "INVAL", -2: "NOMEM", -3: "CUDA", -4: "UNSTABLE", -5: "RANGE", -6: "NBR_OVERFLOW",
+          -7: "TIMEOUT", -8: "STATE", -9: "BOUNDS"}
+
+
+class EhcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.ehc_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class ehc_params(ctypes.Structure):
+    _fields_ = [
+        ("rc_A", ctypes.c_double), ("dt_sub_fs", ctypes.c_double), ("Tmax_K", ctypes.c_double),
+        ("Tref_K", ctypes.c_double), ("gamma_Ce", ctypes.c_double), ("Ce_cap_kB", ctypes.c_double),
+        ("kappa0", ctypes.c_double), ("G", ctypes.c_double), ("eps_ke_eV", ctypes.c_double),
+        ("zb2_A2", ctypes.c_double), ("vatom_A3", ctypes.c_double),
+        ("laser_fluence_Jm2", ctypes.c_double), ("laser_lp_A", ctypes.c_double),
+        ("laser_t0_fs", ctypes.c_double), ("laser_sigma_fs", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("dim_d", ctypes.c_int32), ("kappa_mode", ctypes.c_int32),
+        ("couple_mode", ctypes.c_int32), ("frozen", ctypes.c_int32), ("dof_mode", ctypes.c_int32),
+        ("flux_prec", ctypes.c_int32), ("laser_on", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+class ehc_energy_t(ctypes.Structure):
+    _fields_ = [
+        ("E_e", ctypes.c_double), ("E_lat", ctypes.c_double), ("E_src", ctypes.c_double),
+        ("E_e0", ctypes.c_double), ("drift", ctypes.c_double), ("sum_T", ctypes.c_double),
+        ("max_T", ctypes.c_double), ("mean_T", ctypes.c_double), ("Te_mean_step", ctypes.c_double),
+        ("Tlat_step", ctypes.c_double), ("Ce_SI", ctypes.c_double), ("K_per_fs", ctypes.c_double),
+        ("stability", ctypes.c_double), ("n_stopped", ctypes.c_int64), ("md_step", ctypes.c_int64),
+        ("max_count", ctypes.c_int32), ("device_error", ctypes.c_int32),
+    ]
+
+
+# every entry point of include/ehc.h with its ctypes signature
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "ehc_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P, _P,
+                        ctypes.POINTER(_P)]),
+    "ehc_set_te": (_I, [_P, _P]),
+    "ehc_set_depth": (_I, [_P, _P]),
+    "ehc_build_neighbors": (_I, [_P, _P, _P]),
+    "ehc_substep": (_I, [_P, ctypes.c_int32, ctypes.c_double]),
+    "ehc_couple": (_I, [_P, _P, ctypes.c_double]),
+    "ehc_drift": (_I, [_P, _P, _P, ctypes.c_double]),
+    "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
+    "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
+    "ehc_sync": (_I, [_P]),
+    "ehc_get_te": (_I, [_P, _P]),
+    "ehc_get_lattice_temperature": (_I, [_P, _P]),
+    "ehc_export_neighbors": (_I, [_P, _P, _P, ctypes.c_int64]),
+    "ehc_philox_normals": (_I, [_P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, _P, _P]),
+    "ehc_save": (_I, [_P, ctypes.c_char_p]),
+    "ehc_load": (_I, [_P, ctypes.c_char_p]),
+    "ehc_destroy": (None, [_P]),
+    "ehc_strerror": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libehc.so (raises if it has not been built: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libehc.so not built ({p}); run __graft_entry__.build()")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != EHC_OK:
+        raise EhcError(code, where)
+
+
+def make_params(p: dict) -> ehc_params:
+    """Marshal a parameter dict (see inputs.params_*) into the C struct."""
+    q = ehc_params()
+    q.rc_A = p["rc"]
+    q.dt_sub_fs = p["dt_sub"]
+    q.Tmax_K = p["Tmax"]
+    q.Tref_K = p.get("Tref", 300.0)
+    q.gamma_Ce = p["gamma_Ce"]
+    q.Ce_cap_kB = p.get("Ce_cap_kB", 0.0)
+    q.kappa0 = p["kappa0"]
+    q.G = p["G"]
+    q.eps_ke_eV = p["eps_ke"]
+    q.zb2_A2 = p["zb2"]
+    q.vatom_A3 = p.get("vatom", 0.0)
+    las = p.get("laser")
+    if las:
+        q.laser_on = 1
+        q.laser_fluence_Jm2 = las["fluence_Jm2"]
+        q.laser_lp_A = las["lp_A"]
+        q.laser_t0_fs = las["t0_fs"]
+        q.laser_sigma_fs = las["sigma_fs"]
+    q.seed = int(p.get("seed", 0))
+    q.dim_d = int(p["dim_d"])
+    q.kappa_mode = int(p["kappa_mode"])
+    q.couple_mode = int(p["couple_mode"])
+    q.frozen = int(p["frozen"])
+    q.dof_mode = int(p.get("dof_mode", 0))
+    q.flux_prec = int(p.get("flux_prec", 0))
+    q.max_neighbors = int(p.get("max_neighbors", 0))
+    q.use_graph = int(p.get("use_graph", 1))
+    return q
+
+
+def _ptr(t) -> int:
+    import torch
+    if t is None:
+        return None
+    assert t.is_contiguous(), "tensors passed to libehc must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream() -> int:
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Ehc:
+    """One system behind an ehc_ctx.  Arrays are torch tensors (float64,
+    original atom order) on the CUDA device, or numpy arrays that are copied
+    to the device first."""
+
+    def __init__(self, params: dict, system=None, *, n=None, box=None, periodic=None, mass_amu=None,
+                 types=None, device="cuda"):
+        import torch
+        L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libehc needs a CUDA device; there is no CPU path")
+        self.device = torch.device(device)
+        if system is not None:
+            n, box, periodic, mass_amu, types = (system.n, system.box, system.periodic, system.mass_amu,
+                                                 system.type)
+        self.n = int(n)
+        self.params = dict(params)
+        self._p = make_params(params)
+        box_a = np.ascontiguousarray(box, dtype=np.float64)
+        per_a = np.ascontiguousarray(periodic, dtype=np.int32)
+        m_a = np.ascontiguousarray(mass_amu, dtype=np.float64)
+        self._types = None
+        nt = int(m_a.shape[0])
+        if nt > 1:
+            self._types = torch.as_tensor(np.asarray(types, dtype=np.int32), device=self.device).contiguous()
+        h = ctypes.c_void_p()
+        _check(L.ehc_create(ctypes.byref(self._p), self.n, box_a.ctypes.data_as(_P), per_a.ctypes.data_as(_P),
+                            m_a.ctypes.data_as(_P), nt, _ptr(self._types) if self._types is not None else None,
+                            _stream(), ctypes.byref(h)), "ehc_create")
+        self._h = h
+        self._lib = L
+
+    # ---------------------------------------------------------------- helpers
+    def _dev(self, a):
+        import torch
+        if isinstance(a, torch.Tensor):
+            t = a if a.device == self.device else a.to(self.device)
+            return t.to(torch.float64).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=self.device)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.ehc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- C-ABI calls
+    def set_te(self, Te):
+        t = self._dev(Te)
+        _check(self._lib.ehc_set_te(self._h, _ptr(t)), "ehc_set_te")
+
+    def set_depth(self, depth):
+        t = self._dev(depth)
+        _check(self._lib.ehc_set_depth(self._h, _ptr(t)), "ehc_set_depth")
+
+    def build_neighbors(self, x, v):
+        _check(self._lib.ehc_build_neighbors(self._h, _ptr(x), _ptr(v)), "ehc_build_neighbors")
+
+    def substep(self, n_sub: int, t_fs: float = 0.0):
+        _check(self._lib.ehc_substep(self._h, int(n_sub), float(t_fs)), "ehc_substep")
+
+    def couple(self, v, dt_md_fs: float):
+        _check(self._lib.ehc_couple(self._h, _ptr(v), float(dt_md_fs)), "ehc_couple")
+
+    def drift(self, x, v, dt_fs: float):
+        _check(self._lib.ehc_drift(self._h, _ptr(x), _ptr(v), float(dt_fs)), "ehc_drift")
+
+    def md_step_host(self, x_host, v_host, n_sub: int, t_fs: float, dt_md_fs: float, Te_host_out):
+        """Whole MD step on host buffers (torch CPU tensors, ideally pinned)."""
+        _check(self._lib.ehc_md_step_host(self._h, ctypes.c_void_p(x_host.data_ptr()),
+                                          ctypes.c_void_p(v_host.data_ptr()), int(n_sub), float(t_fs),
+                                          float(dt_md_fs), ctypes.c_void_p(Te_host_out.data_ptr())),
+               "ehc_md_step_host")
+
+    def energy(self, check: bool = True) -> dict:
+        e = ehc_energy_t()
+        code = self._lib.ehc_energy(self._h, ctypes.byref(e))
+        if check:
+            _check(code, "ehc_energy")
+        d = {f: getattr(e, f) for f, _ in ehc_energy_t._fields_}
+        d["status"] = code
+        return d
+
+    def sync(self):
+        _check(self._lib.ehc_sync(self._h), "ehc_sync")
+
+    def get_te(self):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(self._lib.ehc_get_te(self._h, _ptr(out)), "ehc_get_te")
+        return out
+
+    def get_lattice_temperature(self):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(self._lib.ehc_get_lattice_temperature(self._h, _ptr(out)), "ehc_get_lattice_temperature")
+        return out
+
+    def export_neighbors(self, cap_per_atom: int = 64):
+        rowptr = np.zeros(self.n + 1, dtype=np.int64)
+        col = np.empty(max(1, self.n * cap_per_atom), dtype=np.int32)
+        _check(self._lib.ehc_export_neighbors(self._h, rowptr.ctypes.data_as(_P), col.ctypes.data_as(_P),
+                                              col.shape[0]), "ehc_export_neighbors")
+        return rowptr, col[: rowptr[-1]].copy()
+
+    def save(self, path: str):
+        _check(self._lib.ehc_save(self._h, path.encode()), "ehc_save")
+
+    def load(self, path: str):
+        _check(self._lib.ehc_load(self._h, path.encode()), "ehc_load")
+
+
+def philox_normals(ids, md_step: int, seed: int):
+    """Three standard normals per id from the Langevin Philox stream (device)."""
+    import torch
+    L = load_library()
+    ids_t = torch.as_tensor(np.asarray(ids, dtype=np.int64), device="cuda")
+    out = torch.empty((ids_t.shape[0], 3), dtype=torch.float64, device="cuda")
+    _check(L.ehc_philox_normals(_ptr(ids_t), ids_t.shape[0], int(md_step), int(seed), _ptr(out), _stream()),
+           "ehc_philox_normals")
+    return out

@@ -1,0 +1,618 @@
+// ehc_api.cu -- the C ABI of libehc (declared in include/ehc.h): argument
+// checks, unit conversion, device memory, per-MD-step scalars, substep loops
+// replayed from CUDA graphs, and the FP64 energy ledger.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ehc_internal.cuh"
+
+using namespace ehc;
+
+struct ehc_ctx {
+  Ctx c;
+};
+
+namespace {
+
+// CODATA 2018
+constexpr double kKB_EV = 8.617333262e-5;
+constexpr double kKB_J = 1.380649e-23;
+constexpr double kEV_J = 1.602176634e-19;
+constexpr double kPI = 3.14159265358979323846;
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return EHC_E_CUDA;     \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+int err_code(int32_t bits) {
+  if (bits & ERR_BOUNDS) return EHC_E_BOUNDS;
+  if (bits & ERR_NBR_OVERFLOW) return EHC_E_NBR_OVERFLOW;
+  if (bits & ERR_RANGE) return EHC_E_RANGE;
+  if (bits & ERR_TIMEOUT) return EHC_E_TIMEOUT;
+  return EHC_OK;
+}
+
+void free_all(Ctx &c) {
+  cudaStream_t st = c.stream;
+  cudaStreamSynchronize(st);
+  void *dev[] = {c.type_orig, c.type_s, c.q_orig, c.cell_count, c.cell_start, c.cell_fill, c.scan_tmp,
+                 c.perm, c.inv_perm[0], c.inv_perm[1], c.q_s, c.v_s, c.nbr, c.cnt, c.T[0], c.T[1],
+                 c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
+                 c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (c.pulse_host) cudaFreeHost(c.pulse_host);
+  if (c.scal_host) cudaFreeHost(c.scal_host);
+  if (c.coef_host) cudaFreeHost(c.coef_host);
+  for (int i = 0; i < c.n_graphs; ++i) cudaGraphExecDestroy(c.graphs[i].exec);
+  c.n_graphs = 0;
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  if (c.pulse_ev) cudaEventDestroy(c.pulse_ev);
+}
+
+// read back scal[0..15] and the error word; synchronises the stream
+int readback(Ctx &c) {
+  CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  int32_t w[2];
+  std::memcpy(w, c.scal_host + 16, sizeof(w));
+  c.dev_err = w[0];
+  return EHC_OK;
+}
+
+double cap_SI(const Ctx &c) {
+  return c.p.Ce_cap_kB > 0 ? c.p.Ce_cap_kB * kKB_J / (c.vatom * 1e-30) : 0.0;
+}
+
+int run_substeps(Ctx &c, int32_t n_sub) {
+  const int p0 = (c.p.flux_prec == 1) ? c.tcur : c.parity;
+  const int ab = (c.A == c.abuf[0]) ? 0 : 1;
+  bool use_graph = c.p.use_graph && n_sub >= 4;
+  if (use_graph) {
+    int hit = -1;
+    for (int i = 0; i < c.n_graphs; ++i) {
+      const auto &e = c.graphs[i];
+      if (e.n_sub == n_sub && e.parity == p0 && e.tcur == c.tcur && e.abuf == ab) hit = i;
+    }
+    if (hit < 0) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t le = cudaSuccess;
+      for (int k = 0; k < n_sub && le == cudaSuccess; ++k) le = launch_substep(c, k, p0 ^ (k & 1), c.cap_stream);
+      cudaError_t ee = cudaStreamEndCapture(c.cap_stream, &graph);
+      if (le != cudaSuccess || ee != cudaSuccess) return EHC_E_CUDA;
+      cudaGraphExec_t exec;
+      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return EHC_E_CUDA;
+      if (c.n_graphs == 8) {
+        int lru = 0;
+        for (int i = 1; i < 8; ++i)
+          if (c.graphs[i].last_use < c.graphs[lru].last_use) lru = i;
+        cudaGraphExecDestroy(c.graphs[lru].exec);
+        c.graphs[lru] = c.graphs[7];
+        c.n_graphs = 7;
+      }
+      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, exec, 0};
+      hit = c.n_graphs++;
+    }
+    c.graphs[hit].last_use = ++c.use_clock;
+    CK(cudaGraphLaunch(c.graphs[hit].exec, c.stream));
+  } else {
+    for (int k = 0; k < n_sub; ++k) CK(launch_substep(c, k, p0 ^ (k & 1), c.stream));
+  }
+  const int p1 = p0 ^ (n_sub & 1);
+  if (c.p.flux_prec == 1) c.tcur = p1;
+  else c.parity = p1;
+  return EHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ehc_strerror(int code) {
+  switch (code) {
+    case EHC_OK: return "ok";
+    case EHC_E_INVAL: return "invalid argument";
+    case EHC_E_NOMEM: return "out of memory";
+    case EHC_E_CUDA: return "CUDA runtime error";
+    case EHC_E_UNSTABLE: return "substep unstable: dt (2 n_max K + G/C_e) > 2";
+    case EHC_E_RANGE: return "normalised temperature left [0,1] (raise Tmax) or became NaN";
+    case EHC_E_NBR_OVERFLOW: return "neighbour count exceeds max_neighbors";
+    case EHC_E_TIMEOUT: return "bounded device wait timed out";
+    case EHC_E_STATE: return "call out of order";
+    case EHC_E_BOUNDS: return "atom outside a non-periodic box extent";
+    default: return "unknown error";
+  }
+}
+
+int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], const int32_t periodic[3],
+               const double *mass_amu_host, int32_t n_types, const int32_t *type_dev, void *stream,
+               ehc_ctx **out) {
+  if (!p || !box_A || !periodic || !mass_amu_host || !out) return EHC_E_INVAL;
+  *out = nullptr;
+  if (n_atoms < 0 || n_atoms >= (int64_t)INT32_MAX / 2) return EHC_E_INVAL;
+  if (n_types < 1 || n_types > kMaxTypes || (n_types > 1 && !type_dev)) return EHC_E_INVAL;
+  if (!(p->rc_A > 0) || !(p->dt_sub_fs > 0) || !(p->Tmax_K > 0) || !(p->zb2_A2 > 0) || p->dim_d < 1 ||
+      !(p->gamma_Ce > 0) || !(p->kappa0 >= 0) || !(p->G >= 0) || p->Tref_K < 0 || p->Tref_K > p->Tmax_K)
+    return EHC_E_INVAL;
+  if (p->flux_prec != 0 && p->flux_prec != 1) return EHC_E_INVAL;
+  if (p->couple_mode != 0 && p->couple_mode != 1) return EHC_E_INVAL;
+  if (p->laser_on && (!(p->laser_lp_A > 0) || !(p->laser_sigma_fs > 0))) return EHC_E_INVAL;
+  int32_t W = p->max_neighbors <= 0 ? 32 : p->max_neighbors;
+  if (W > kMaxWidth || W > 255) return EHC_E_INVAL;
+  for (int t = 0; t < n_types; ++t)
+    if (!(mass_amu_host[t] > 0)) return EHC_E_INVAL;
+
+  ehc_ctx *h = new (std::nothrow) ehc_ctx();
+  if (!h) return EHC_E_NOMEM;
+  Ctx &c = h->c;
+  c.p = *p;
+  c.n = n_atoms;
+  c.W = W;
+  c.stream = (cudaStream_t)stream;
+  c.g.rcq = llrint(p->rc_A * 1048576.0);
+  int64_t ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    c.box[k] = box_A[k];
+    if (!(box_A[k] > 0)) { delete h; return EHC_E_INVAL; }
+    c.g.Lq[k] = llrint(box_A[k] * 1048576.0);
+    if (c.g.Lq[k] <= 0 || c.g.Lq[k] >= INT32_MAX) { delete h; return EHC_E_INVAL; }
+    c.g.per[k] = periodic[k] ? 1 : 0;
+    if (c.g.per[k] && c.g.Lq[k] <= 2 * c.g.rcq) { delete h; return EHC_E_INVAL; }
+    int64_t nc = c.g.Lq[k] / c.g.rcq;
+    if (nc < 1) nc = 1;
+    if (nc > 1024) nc = 1024;
+    c.g.nc[k] = (int32_t)nc;
+    ncell *= nc;
+  }
+  // very large, sparse boxes: coarser cells (still at least r_c wide) keep the cell arrays bounded
+  while (ncell > (int64_t(1) << 26)) {
+    int k = 0;
+    for (int j = 1; j < 3; ++j)
+      if (c.g.nc[j] > c.g.nc[k]) k = j;
+    ncell /= c.g.nc[k];
+    c.g.nc[k] = (c.g.nc[k] + 1) / 2;
+    ncell *= c.g.nc[k];
+  }
+  c.g.ncell = ncell;
+  c.mt.n_types = n_types;
+  for (int t = 0; t < kMaxTypes; ++t) c.mt.m[t] = t < n_types ? mass_amu_host[t] : mass_amu_host[0];
+  c.vatom = p->vatom_A3 > 0 ? p->vatom_A3 : (n_atoms > 0 ? box_A[0] * box_A[1] * box_A[2] / (double)n_atoms : 1.0);
+  c.max_sub = 65536;
+
+  const int64_t n = n_atoms;
+  const int64_t ntiles = (ncell + 4095) / 4096;
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  if (n_types > 1) A(dalloc(&c.type_orig, n));
+  A(dalloc(&c.type_s, n));
+  A(dalloc(&c.q_orig, n));
+  A(dalloc(&c.cell_count, ncell + 1));
+  A(dalloc(&c.cell_start, ncell + 1));
+  A(dalloc(&c.cell_fill, ncell));
+  A(dalloc(&c.scan_tmp, ntiles + 1));
+  A(dalloc(&c.perm, n));
+  A(dalloc(&c.inv_perm[0], n));
+  A(dalloc(&c.inv_perm[1], n));
+  A(dalloc(&c.q_s, n));
+  A(dalloc(&c.v_s, 3 * n));
+  A(dalloc(&c.nbr, (size_t)W * n));
+  A(dalloc(&c.cnt, n));
+  A(dalloc(&c.T[0], n));
+  A(dalloc(&c.T[1], n));
+  A(dalloc(&c.dmir[0], n));
+  A(dalloc(&c.dmir[1], n));
+  A(dalloc(&c.abuf[0], n));
+  A(dalloc(&c.abuf[1], n));
+  A(dalloc(&c.Tl_f, n));
+  A(dalloc(&c.Tl_d, n));
+  A(dalloc(&c.depth_orig, n));
+  A(dalloc(&c.srcw, n));
+  A(dalloc(&c.pulse, c.max_sub));
+  A(dalloc(&c.dKE, n));
+  A(dalloc(&c.partials, kRedBlocks * 4));
+  A(dalloc(&c.scal, 16));
+  A(dalloc(&c.err, 2));
+  A(dalloc(&c.coef, 1));
+  A(dalloc(&c.x_dev, 3 * n));
+  A(dalloc(&c.v_dev, 3 * n));
+  A(dalloc(&c.T_out, n));
+  A(cudaMallocHost((void **)&c.pulse_host, sizeof(double) * c.max_sub));
+  A(cudaMallocHost((void **)&c.scal_host, sizeof(double) * 24));
+  A(cudaMallocHost((void **)&c.coef_host, sizeof(StepCoef)));
+  A(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  A(cudaEventCreateWithFlags(&c.pulse_ev, cudaEventDisableTiming));
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    delete h;
+    return EHC_E_NOMEM;
+  }
+  c.A = c.abuf[0];
+  c.A_tmp = c.abuf[1];
+  cudaError_t e = cudaSuccess;
+  if (n_types > 1 && n > 0)
+    e = cudaMemcpyAsync(c.type_orig, type_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.scal, 0, sizeof(double) * 16, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 2, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.abuf[0], 0, sizeof(double) * (n > 0 ? n : 1), c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.srcw, 0, sizeof(float) * (n > 0 ? n : 1), c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete h;
+    return EHC_E_CUDA;
+  }
+  *out = h;
+  return EHC_OK;
+}
+
+void ehc_destroy(ehc_ctx *h) {
+  if (!h) return;
+  free_all(h->c);
+  delete h;
+}
+
+int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
+  if (!h || (!Te_dev && h->c.n > 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (c.n > 0) {
+    CK(cudaMemcpyAsync(c.T[c.tcur], Te_dev, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+    CK(cudaMemsetAsync(c.A, 0, sizeof(double) * c.n, c.stream));
+  }
+  CK(cudaMemsetAsync(c.scal, 0, sizeof(double) * 16, c.stream));
+  CK(launch_seed(c, cap_SI(c)));
+  int r = readback(c);
+  if (r) return r;
+  c.te_orig_order = true;
+  c.have_te = true;
+  c.built = false;
+  c.E_e0 = c.scal_host[2] * c.vatom * 1e-30 / kEV_J;
+  c.E_base = c.E_e0;
+  c.ST_base = c.scal_host[0];
+  c.VC_prev = -1;
+  c.E_src = 0;
+  c.md_step = 0;
+  return EHC_OK;
+}
+
+int ehc_set_depth(ehc_ctx *h, const double *depth_dev) {
+  if (!h || (!depth_dev && h->c.n > 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (c.n > 0)
+    CK(cudaMemcpyAsync(c.depth_orig, depth_dev, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+  c.have_depth = true;
+  return EHC_OK;
+}
+
+int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
+  if (!h) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  if (c.n > 0 && (!x_dev || !v_dev)) return EHC_E_INVAL;
+  CK(launch_bin(c, x_dev));
+  CK(launch_sort_cells(c));
+  CK(launch_gather(c, v_dev, c.te_orig_order));
+  c.te_orig_order = false;
+  CK(launch_neighbors(c));
+  CK(launch_lattice_temperature(c));
+  CK(launch_globals(c));
+  int r = readback(c);
+  if (r) return r;
+  int32_t w[2];
+  std::memcpy(w, c.scal_host + 16, sizeof(w));
+  c.n_max = w[1];
+  const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
+  c.wsum = c.scal_host[3];
+  // ledger: close the previous MD step with its own C_e
+  if (c.VC_prev > 0) {
+    c.E_base += c.VC_prev * (sumT - c.ST_base);
+    c.ST_base = sumT;
+  }
+  const double N = (double)(c.n > 0 ? c.n : 1);
+  // system means (Sec. 2): mean electronic temperature, classical T_lat = K / ((3/2) k_B N)
+  c.Te_mean = sumT / N;
+  c.Tlat = sumKE / (1.5 * kKB_EV * N);
+  double Ce = c.p.gamma_Ce * c.Te_mean;
+  const double cap = cap_SI(c);
+  if (cap > 0 && Ce > cap) Ce = cap;
+  if (c.n == 0) Ce = c.p.gamma_Ce;   // nothing to advance; keep the coefficients finite
+  if (!(Ce > 0)) return EHC_E_RANGE;
+  double kappa = c.p.kappa0;
+  if (c.p.kappa_mode == 1) kappa = c.Tlat > 0 ? c.p.kappa0 * c.Te_mean / c.Tlat : c.p.kappa0;
+  c.Ce = Ce;
+  // Eq. Kij, K = 2 kappa_e d / (C_e Z b^2): m^2/s over A^2 -> 1/fs
+  c.K = 2.0 * c.p.dim_d * kappa / (Ce * c.p.zb2_A2 * 1e-20) * 1e-15;
+  c.cG = c.p.G / Ce * 1e-15;
+  c.VG = c.p.G * c.vatom * 1e-30 / kEV_J * 1e-15;
+  c.VC = c.vatom * 1e-30 * Ce / kEV_J;
+  c.gammaL = c.p.G * c.vatom * 1e-30 / (3.0 * kKB_J) * 1e-15;
+  c.stability = c.p.dt_sub_fs * (2.0 * c.n_max * c.K + c.cG);
+  c.VC_prev = c.VC;
+  StepCoef &cf = *c.coef_host;
+  cf.dt = c.p.dt_sub_fs;
+  cf.dtTK = c.p.dt_sub_fs * c.p.Tmax_K * c.K;
+  cf.dtcG = c.p.dt_sub_fs * c.cG;
+  cf.dtVG = c.p.dt_sub_fs * c.VG;
+  cf.invTmax = 1.0 / c.p.Tmax_K;
+  cf.Tref = c.p.Tref_K;
+  cf.th_ref = (float)(c.p.Tref_K / c.p.Tmax_K);
+  cf.pad = 0.f;
+  CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
+  c.built = true;
+  return err_code(c.dev_err);
+}
+
+int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
+  if (!h || n_sub < 0) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  if (n_sub == 0 || c.n == 0) return EHC_OK;
+  if (!(c.stability <= 2.0)) return EHC_E_UNSTABLE;
+  const bool laser = c.p.laser_on && c.have_depth;
+  int32_t done = 0;
+  while (done < n_sub) {
+    int32_t chunk = n_sub - done;
+    if (laser && chunk > c.max_sub) chunk = c.max_sub;
+    if (laser) {
+      CK(cudaEventSynchronize(c.pulse_ev));  // previous copy out of the staging buffer finished
+      const double sig = c.p.laser_sigma_fs;
+      const double S0 = c.p.laser_fluence_Jm2 / (c.p.laser_lp_A * 1e-10) / (sig * 1e-15 * std::sqrt(2.0 * kPI));
+      for (int k = 0; k < chunk; ++k) {
+        const double t = t_fs + c.p.dt_sub_fs * (double)(done + k);
+        const double u = (t - c.p.laser_t0_fs) / sig;
+        const double rate = S0 * std::exp(-0.5 * u * u) / c.Ce * 1e-15;  // K / fs at depth 0
+        c.pulse_host[k] = rate;
+        c.E_src += c.VC * c.p.dt_sub_fs * rate * c.wsum;
+      }
+      CK(cudaMemcpyAsync(c.pulse, c.pulse_host, sizeof(double) * chunk, cudaMemcpyHostToDevice, c.stream));
+      CK(cudaEventRecord(c.pulse_ev, c.stream));
+    }
+    int r = run_substeps(c, chunk);
+    if (r) return r;
+    done += chunk;
+  }
+  return EHC_OK;
+}
+
+int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
+  if (!h) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  if (c.n > 0 && !v_dev && !c.p.frozen) return EHC_E_INVAL;
+  CK(launch_couple(c, v_dev, dt_md_fs));
+  c.md_step += 1;
+  return EHC_OK;
+}
+
+int ehc_drift(ehc_ctx *h, double *x_dev, const double *v_dev, double dt_fs) {
+  if (!h || (h->c.n > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
+  CK(launch_drift(h->c, x_dev, v_dev, dt_fs));
+  return EHC_OK;
+}
+
+int ehc_sync(ehc_ctx *h) {
+  if (!h) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  int32_t w[2];
+  std::memcpy(w, c.scal_host + 16, sizeof(w));
+  c.dev_err = w[0];
+  return err_code(c.dev_err);
+}
+
+int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
+  if (!h || !out) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  CK(launch_ledger(c));
+  int r = readback(c);
+  if (r) return r;
+  const double sumT = c.scal_host[0];
+  std::memset(out, 0, sizeof(*out));
+  out->E_e = c.E_base + (c.VC_prev > 0 ? c.VC_prev * (sumT - c.ST_base) : 0.0);
+  out->E_lat = c.scal_host[8];
+  out->E_src = c.E_src;
+  out->E_e0 = c.E_e0;
+  out->drift = c.E_e0 != 0 ? (out->E_e + out->E_lat - out->E_src - out->E_e0) / c.E_e0 : 0.0;
+  out->sum_T = sumT;
+  out->max_T = c.scal_host[1];
+  out->mean_T = c.n > 0 ? sumT / (double)c.n : 0.0;
+  out->Te_mean_step = c.Te_mean;
+  out->Tlat_step = c.Tlat;
+  out->Ce_SI = c.Ce;
+  out->K_per_fs = c.K;
+  out->stability = c.stability;
+  uint64_t ns;
+  std::memcpy(&ns, c.scal_host + 9, sizeof(ns));
+  out->n_stopped = (int64_t)ns;
+  out->md_step = c.md_step;
+  out->max_count = c.n_max;
+  out->device_error = c.dev_err;
+  return err_code(c.dev_err);
+}
+
+int ehc_get_te(ehc_ctx *h, double *Te_dev_out) {
+  if (!h || (!Te_dev_out && h->c.n > 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  CK(launch_unpermute(c, c.T[c.tcur], Te_dev_out, c.te_orig_order ? 1 : 0));
+  return EHC_OK;
+}
+
+int ehc_get_lattice_temperature(ehc_ctx *h, double *Tl_dev_out) {
+  if (!h || (!Tl_dev_out && h->c.n > 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  CK(launch_unpermute(c, c.Tl_d, Tl_dev_out, 0));
+  return EHC_OK;
+}
+
+int ehc_export_neighbors(ehc_ctx *h, int64_t *rowptr, int32_t *col, int64_t cap) {
+  if (!h || !rowptr || (!col && cap > 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  const int64_t n = c.n;
+  const int32_t w = c.n_max < c.W ? c.n_max : c.W;
+  std::vector<uint8_t> cnt(n);
+  std::vector<int32_t> perm(n), nbr((size_t)w * n);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(cnt.data(), c.cnt, n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(perm.data(), c.perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c.stream));
+    if (w > 0)
+      CK(cudaMemcpyAsync(nbr.data(), c.nbr, sizeof(int32_t) * (size_t)w * n, cudaMemcpyDeviceToHost, c.stream));
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  std::vector<int32_t> inv(n);
+  for (int64_t s = 0; s < n; ++s) inv[perm[s]] = (int32_t)s;
+  rowptr[0] = 0;
+  for (int64_t o = 0; o < n; ++o) rowptr[o + 1] = rowptr[o] + cnt[inv[o]];
+  if (rowptr[n] > cap) return EHC_E_INVAL;
+  for (int64_t o = 0; o < n; ++o) {
+    const int64_t s = inv[o];
+    int64_t b = rowptr[o];
+    for (int k = 0; k < cnt[s]; ++k) col[b + k] = perm[nbr[(size_t)k * n + s]];
+  }
+  return EHC_OK;
+}
+
+int ehc_md_step_host(ehc_ctx *h, double *x_host, double *v_host, int32_t n_sub, double t_fs, double dt_md_fs,
+                     double *Te_host_out) {
+  if (!h || (h->c.n > 0 && (!x_host || !v_host || !Te_host_out))) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  const size_t b3 = sizeof(double) * 3 * (size_t)c.n;
+  if (c.n > 0) {
+    CK(cudaMemcpyAsync(c.x_dev, x_host, b3, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.v_dev, v_host, b3, cudaMemcpyHostToDevice, c.stream));
+  }
+  int r = ehc_build_neighbors(h, c.x_dev, c.v_dev);
+  if (r) return r;
+  r = ehc_substep(h, n_sub, t_fs);
+  if (r) return r;
+  r = ehc_couple(h, c.v_dev, dt_md_fs);
+  if (r) return r;
+  r = ehc_drift(h, c.x_dev, c.v_dev, dt_md_fs);
+  if (r) return r;
+  r = ehc_get_te(h, c.T_out);
+  if (r) return r;
+  if (c.n > 0) {
+    CK(cudaMemcpyAsync(x_host, c.x_dev, b3, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(v_host, c.v_dev, b3, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(Te_host_out, c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+  }
+  return ehc_sync(h);
+}
+
+int ehc_philox_normals(const int64_t *ids_dev, int64_t n, uint64_t md_step, uint64_t seed, double *out_dev,
+                       void *stream) {
+  if (n < 0 || (n > 0 && (!ids_dev || !out_dev))) return EHC_E_INVAL;
+  CK(launch_philox_normals(ids_dev, n, md_step, seed, out_dev, (cudaStream_t)stream));
+  return EHC_OK;
+}
+
+// checkpoint file: magic, version, n, md_step, ledger scalars, T and A in caller order
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int64_t version, n, md_step;
+  double E_e0, E_base, ST_base, VC_prev, E_src, E_lat;
+  uint64_t n_stopped, seed;
+  int64_t flux_prec;
+};
+}  // namespace
+
+int ehc_save(ehc_ctx *h, const char *path) {
+  if (!h || !path) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  std::vector<double> T(c.n), A(c.n);
+  int r = ehc_get_te(h, c.T_out);
+  if (r) return r;
+  if (c.n > 0) {
+    CK(cudaMemcpyAsync(T.data(), c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+    CK(launch_unpermute(c, c.A, c.T_out, c.te_orig_order ? 1 : 0));
+    CK(cudaMemcpyAsync(A.data(), c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+  }
+  r = readback(c);
+  if (r) return r;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "EHCCKPT1", 8);
+  hd.version = 1;
+  hd.n = c.n;
+  hd.md_step = c.md_step;
+  hd.E_e0 = c.E_e0;
+  hd.E_base = c.E_base;
+  hd.ST_base = c.ST_base;
+  hd.VC_prev = c.VC_prev;
+  hd.E_src = c.E_src;
+  hd.E_lat = c.scal_host[8];
+  std::memcpy(&hd.n_stopped, c.scal_host + 9, sizeof(uint64_t));
+  hd.seed = c.p.seed;
+  hd.flux_prec = c.p.flux_prec;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return EHC_E_INVAL;
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  if (c.n > 0) {
+    ok = ok && std::fwrite(T.data(), sizeof(double), c.n, f) == (size_t)c.n;
+    ok = ok && std::fwrite(A.data(), sizeof(double), c.n, f) == (size_t)c.n;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? EHC_OK : EHC_E_INVAL;
+}
+
+int ehc_load(ehc_ctx *h, const char *path) {
+  if (!h || !path) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return EHC_E_INVAL;
+  CkptHeader hd;
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, "EHCCKPT1", 8) == 0 && hd.n == c.n &&
+            hd.version == 1;
+  std::vector<double> T(c.n), A(c.n);
+  if (ok && c.n > 0) {
+    ok = std::fread(T.data(), sizeof(double), c.n, f) == (size_t)c.n;
+    ok = ok && std::fread(A.data(), sizeof(double), c.n, f) == (size_t)c.n;
+  }
+  std::fclose(f);
+  if (!ok) return EHC_E_INVAL;
+  if (c.n > 0) {
+    CK(cudaMemcpyAsync(c.T[c.tcur], T.data(), sizeof(double) * c.n, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.A, A.data(), sizeof(double) * c.n, cudaMemcpyHostToDevice, c.stream));
+  }
+  c.scal_host[8] = hd.E_lat;
+  std::memcpy(c.scal_host + 9, &hd.n_stopped, sizeof(uint64_t));
+  CK(cudaMemcpyAsync(c.scal + 8, c.scal_host + 8, sizeof(double) * 2, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  c.md_step = hd.md_step;
+  c.E_e0 = hd.E_e0;
+  c.E_base = hd.E_base;
+  c.ST_base = hd.ST_base;
+  c.VC_prev = hd.VC_prev;
+  c.E_src = hd.E_src;
+  c.p.seed = hd.seed;
+  c.have_te = true;
+  c.te_orig_order = true;
+  c.built = false;
+  return EHC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// ehc_internal.cuh -- device data layout and kernel launchers of libehc.
+//
+// Layout in HBM (N atoms, W = neighbour-table width):
+//   atoms are kept in a cell-sorted order s (cells x-fastest, within a cell by
+//   original id); perm[s] = original id, inv_perm[original] = s.
+//   nbr   int32 [W][N]  slot-major: nbr[k*N + s] = k-th neighbour of s (sorted index),
+//                       a row lists its neighbours by ascending original id
+//   cnt   uint8 [N]     neighbour count of s
+//   T     double[N]     electronic temperature (FP64 state), sorted order
+//   dmir  float [2][N]  (T - Tref)/Tmax mirror, double-buffered across substeps
+//   A     double[N]     energy handed from electrons to the lattice this MD step [eV]
+//   Tl_f  float [N]     local lattice temperature (negative: atom below the guard)
+//   Tl_d  double[N]     same in FP64 (for the FP64 flux path and diagnostics)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ehc.h"
+
+namespace ehc {
+
+constexpr int kMaxTypes = 16;
+constexpr int kMaxWidth = 64;
+
+enum DevErr : int32_t {
+  ERR_RANGE = 1,         // theta outside [0,1] or NaN
+  ERR_NBR_OVERFLOW = 2,  // more neighbours than the table width
+  ERR_BOUNDS = 4,        // atom outside a non-periodic extent
+  ERR_TIMEOUT = 8,       // bounded wait gave up
+  ERR_NEG_KE = 16,       // (informational) kinetic energy could not pay A_i
+};
+
+struct MassTable {
+  double m[kMaxTypes];
+  int32_t n_types;
+};
+
+struct Grid {
+  int64_t Lq[3];   // box on the 2^-20 A grid
+  int32_t nc[3];   // cells per axis
+  int32_t per[3];  // periodic flags
+  int64_t rcq;     // cutoff on the grid
+  int64_t ncell;
+};
+
+// Per-MD-step coefficients read by the substep kernels through a pointer, so
+// that captured graphs stay valid when the values change.
+struct StepCoef {
+  double dtTK;     // dt * Tmax * K
+  double dtcG;     // dt * G / C_e
+  double dtVG;     // dt * G * V_atom [eV/K]
+  double dt;       // substep [fs]
+  double invTmax;  // 1 / Tmax
+  double Tref;     // mirror reference
+  float th_ref;    // Tref / Tmax
+  float pad;
+};
+
+// Deterministic block-partial reductions.
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+struct Ctx;
+
+// kernels_build.cu
+cudaError_t launch_bin(Ctx &c, const double *x);
+cudaError_t launch_sort_cells(Ctx &c);
+cudaError_t launch_gather(Ctx &c, const double *v, bool first);
+cudaError_t launch_neighbors(Ctx &c);
+cudaError_t launch_lattice_temperature(Ctx &c);
+cudaError_t launch_globals(Ctx &c);
+cudaError_t launch_unpermute(Ctx &c, const double *src_sorted, double *dst_orig, int mode);
+cudaError_t launch_seed(Ctx &c, double cap_SI);
+cudaError_t launch_ledger(Ctx &c);
+// kernels_substep.cu
+cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t s);
+// kernels_couple.cu
+cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
+cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);
+cudaError_t launch_philox_normals(const int64_t *ids, int64_t n, uint64_t step, uint64_t seed,
+                                  double *out, cudaStream_t s);
+
+struct Ctx {
+  ehc_params p;
+  int64_t n = 0;
+  int32_t W = 32;
+  double box[3];
+  Grid g;
+  MassTable mt;
+  double vatom = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t pulse_ev = nullptr;
+
+  // device buffers
+  int32_t *type_orig = nullptr;  // caller's type index per atom (original order), or null
+  int8_t *type_s = nullptr;
+  int4 *q_orig = nullptr;        // quantised position + cell id, original order
+  int32_t *cell_count = nullptr; // [ncell + 1]
+  int32_t *cell_start = nullptr; // [ncell + 1]
+  int32_t *cell_fill = nullptr;  // [ncell]
+  int32_t *scan_tmp = nullptr;   // block sums of the scan
+  int32_t *perm = nullptr;
+  int32_t *inv_perm[2] = {nullptr, nullptr};
+  int cur_inv = 0;
+  int4 *q_s = nullptr;           // sorted positions + cell id
+  double *v_s = nullptr;         // sorted velocities [3N]
+  int32_t *nbr = nullptr;        // [W][N]
+  uint8_t *cnt = nullptr;
+  double *T[2] = {nullptr, nullptr};   // T[tcur] is the state
+  int tcur = 0;
+  float *dmir[2] = {nullptr, nullptr};
+  double *abuf[2] = {nullptr, nullptr};
+  double *A = nullptr;           // one of abuf
+  double *A_tmp = nullptr;       // the other
+  float *Tl_f = nullptr;
+  double *Tl_d = nullptr;
+  double *depth_orig = nullptr;
+  float *srcw = nullptr;         // exp(-depth / l_p), sorted
+  double *pulse = nullptr;       // per-substep source rate factors [max_sub]
+  double *pulse_host = nullptr;  // pinned staging
+  int32_t max_sub = 0;
+  double *dKE = nullptr;
+  double *partials = nullptr;    // [kRedBlocks * 4]
+  double *scal = nullptr;        // device scalars [16]
+  double *scal_host = nullptr;   // pinned mirror [16]
+  int32_t *err = nullptr;        // device error word
+  int32_t *maxcnt = nullptr;     // device max count (adjacent to err)
+  StepCoef *coef = nullptr;      // device
+  StepCoef *coef_host = nullptr; // pinned
+  double *x_dev = nullptr, *v_dev = nullptr, *T_out = nullptr;  // staging of the host-buffer step
+
+  // state
+  bool have_te = false;
+  bool te_orig_order = false;    // T[tcur] still in caller order (before the first build)
+  bool built = false;
+  bool have_depth = false;
+  int parity = 0;                // mirror buffer holding the current snapshot
+  int64_t md_step = 0;
+  int32_t n_max = 0;             // largest neighbour count this MD step
+  int32_t dev_err = 0;
+
+  // per-step scalars
+  double Te_mean = 0, Tlat = 0, Ce = 0, K = 0, cG = 0, VG = 0, VC = 0, gammaL = 0;
+  double stability = 0, wsum = 0;
+
+  // ledger (host, FP64)
+  double E_e0 = 0, E_base = 0, ST_base = 0, VC_prev = -1, E_src = 0;
+
+  // captured substep loops, keyed by everything a launch bakes in
+  struct GraphEntry {
+    int n_sub, parity, tcur, abuf;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+  };
+  GraphEntry graphs[8];
+  int n_graphs = 0;
+  uint64_t use_clock = 0;
+};
+
+}  // namespace ehc

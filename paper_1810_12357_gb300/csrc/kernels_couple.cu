@@ -1,0 +1,198 @@
+// kernels_couple.cu -- once-per-MD-step hand-over of the exchanged energy to
+// the atoms, the free-flight drift, and the Philox4x32-10 generator.
+//
+// Energy balance (Eqs. RateExchange, WorkDone, Xi): during the substeps the
+// electrons of atom i gave up A_i = dt sum_n G V_atom (T_i - T_l,i).  The
+// damping force xi_i m v_i of Eq. Motion, with xi_i of Eq. Xi, integrated over
+// the MD step scales the velocity by s with s^2 = (K_i + A_i) / K_i, which
+// moves exactly A_i into the atom's kinetic energy K_i.  The Langevin variant
+// first applies friction e^{-g dt} and a Gaussian random force of variance
+// k_B T_e,i (1 - e^{-2 g dt}) / m (g = G V_atom / (3 k_B)), then rescales to the
+// same kinetic energy K_i + A_i, so the hand-over stays exact.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "ehc_internal.cuh"
+
+namespace ehc {
+
+namespace {
+
+constexpr double kMVV = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;  // amu (A/fs)^2 -> eV
+constexpr double kKB = 8.617333262e-5;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplications (high and low halves) with Weyl-sequence key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// counter (id lo, id hi, step lo, step hi), key (seed lo, seed hi);
+// u = (x + 1/2) 2^-32; Box-Muller in double precision.
+__device__ __forceinline__ void gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step,
+                                           (uint32_t)(step >> 32)),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double s = 1.0 / 4294967296.0;
+  const double u0 = ((double)r.x + 0.5) * s, u1 = ((double)r.y + 0.5) * s;
+  const double u2 = ((double)r.z + 0.5) * s, u3 = ((double)r.w + 0.5) * s;
+  const double r1 = sqrt(-2.0 * log(u0));
+  const double r2 = sqrt(-2.0 * log(u2));
+  const double twopi = 6.283185307179586;
+  g[0] = r1 * cos(twopi * u1);
+  g[1] = r1 * sin(twopi * u1);
+  g[2] = r2 * cos(twopi * u3);
+}
+
+__global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ type_s,
+                              MassTable mt, const double *__restrict__ Tl, double *__restrict__ A,
+                              double *__restrict__ T, double *__restrict__ v, double *__restrict__ dKE,
+                              int mode, int frozen, uint64_t seed, uint64_t md_step, double e1,
+                              double one_m_e2, double inv_VC, unsigned long long *__restrict__ n_stopped) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double Ai = A[s];
+  A[s] = 0.0;
+  if (!(Tl[s] >= 0.0)) {
+    dKE[s] = 0.0;
+    return;
+  }
+  if (frozen) {
+    dKE[s] = Ai;
+    return;
+  }
+  const int64_t o = perm[s];
+  const double m = mt.m[type_s[s]];
+  double *vi = v + 3 * o;
+  const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
+  const double K0 = 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2) * kMVV;
+  double target = K0 + Ai;
+  if (target < 0.0) {
+    target = 0.0;
+    atomicAdd(n_stopped, 1ull);
+  }
+  double w0 = v0, w1 = v1, w2 = v2;
+  if (mode == 1) {
+    double g[3];
+    gauss3((uint64_t)o, md_step, seed, g);
+    const double sig = sqrt(kKB * T[s] * one_m_e2 / (m * kMVV));
+    w0 = v0 * e1 + sig * g[0];
+    w1 = v1 * e1 + sig * g[1];
+    w2 = v2 * e1 + sig * g[2];
+  }
+  const double Kw = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
+  const double sc = Kw > 0.0 ? sqrt(target / Kw) : 0.0;
+  w0 *= sc;
+  w1 *= sc;
+  w2 *= sc;
+  vi[0] = w0;
+  vi[1] = w1;
+  vi[2] = w2;
+  const double K1 = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
+  const double d = K1 - K0;
+  dKE[s] = d;
+  if (target == 0.0) T[s] += (Ai - d) * inv_VC;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+__global__ void sum_partial(int64_t n, const double *__restrict__ x, double *__restrict__ part) {
+  __shared__ double sh[32];
+  double a = 0;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    a += x[s];
+  double r = block_sum(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void sum_final_accumulate(int nb, const double *__restrict__ part, double *__restrict__ acc) {
+  __shared__ double sh[32];
+  double a = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[b];
+  double r = block_sum(a, sh);
+  if (threadIdx.x == 0) *acc += r;
+}
+
+__global__ void drift_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ v, double dt,
+                             double L0, double L1, double L2, int p0, int p1, int p2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  const int k = (int)(i % 3);
+  const double L = k == 0 ? L0 : (k == 1 ? L1 : L2);
+  const int per = k == 0 ? p0 : (k == 1 ? p1 : p2);
+  // no contraction: x + v dt rounds the product and the sum separately
+  double y = __dadd_rn(x[i], __dmul_rn(v[i], dt));
+  if (per) {
+    y = fmod(y, L);
+    if (y < 0.0) y += L;
+  }
+  x[i] = y;
+}
+
+__global__ void philox_normals_kernel(const int64_t *__restrict__ ids, int64_t n, uint64_t step, uint64_t seed,
+                                      double *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double g[3];
+  gauss3((uint64_t)ids[i], step, seed, g);
+  out[3 * i + 0] = g[0];
+  out[3 * i + 1] = g[1];
+  out[3 * i + 2] = g[2];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// scal[8] accumulates E_lat; scal[9] holds the stopped-atom counter (as u64 bits)
+cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
+  const double gdt = c.gammaL * dt_md;
+  const double e1 = std::exp(-gdt);
+  const double one_m_e2 = 1.0 - std::exp(-2.0 * gdt);
+  if (c.n > 0)
+    couple_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
+        c.n, c.perm, c.type_s, c.mt, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode, c.p.frozen, c.p.seed,
+        (uint64_t)c.md_step, e1, one_m_e2, 1.0 / c.VC, reinterpret_cast<unsigned long long *>(c.scal + 9));
+  sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
+  sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt) {
+  if (c.n > 0)
+    drift_kernel<<<nblk(3 * c.n, 256), 256, 0, c.stream>>>(c.n, x, v, dt, c.box[0], c.box[1], c.box[2],
+                                                           c.g.per[0], c.g.per[1], c.g.per[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_normals(const int64_t *ids, int64_t n, uint64_t step, uint64_t seed, double *out,
+                                  cudaStream_t s) {
+  if (n > 0) philox_normals_kernel<<<nblk(n, 256), 256, 0, s>>>(ids, n, step, seed, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ehc
