@@ -247,6 +247,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   }
   c.A = c.abuf[0];
   c.A_tmp = c.abuf[1];
+  c.maxcnt = c.err + 1;
   cudaError_t e = cudaSuccess;
   if (n_types > 1 && n > 0)
     e = cudaMemcpyAsync(c.type_orig, type_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.stream);

@@ -8,8 +8,11 @@ import oracle
 from paper_1810_12357_gb300 import inputs as I
 
 
-def run_oracle(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float = 1.0, drift: bool = True,
-               t0: float = 0.0):
+def run_oracle(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float | None = None,
+               drift: bool = True, t0: float = 0.0):
+    """The electrons and the lattice advance the same time per MD step unless
+    dt_md is given: dt_md = n_sub * dt_sub."""
+    dt_md = n_sub * p["dt_sub"] if dt_md is None else dt_md
     sim = oracle.OracleSim(p, system.box, system.periodic, system.mass_amu, system.type, depth=system.depth)
     sim.set_te(system.Te)
     x = system.x.copy()
@@ -25,8 +28,9 @@ def run_oracle(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float = 
     return sim, x, v
 
 
-def run_gpu(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float = 1.0, drift: bool = True,
-            t0: float = 0.0):
+def run_gpu(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float | None = None,
+            drift: bool = True, t0: float = 0.0):
+    dt_md = n_sub * p["dt_sub"] if dt_md is None else dt_md
     import torch
     from paper_1810_12357_gb300 import Ehc
     g = Ehc(p, system)

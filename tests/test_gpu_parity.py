@@ -42,10 +42,10 @@ def test_neighbor_list_bit_exact(case):
         s = I.hot_spot_system(10, 1)
         rc = 4.0
     elif case == "random_periodic":
-        s = I.random_box_system(3000, (25.0, 31.0, 22.5), 21)
+        s = I.random_box_system(1500, (25.0, 31.0, 22.5), 21)   # ~23 neighbours on average
         rc = 4.0
     elif case == "random_mixed":
-        s = I.random_box_system(2500, (40.0, 18.0, 15.0), 22, periodic=(1, 0, 1))
+        s = I.random_box_system(800, (40.0, 18.0, 15.0), 22, periodic=(1, 0, 1))   # ~28 on average
         rc = 4.5
     elif case == "few_cells":
         s = I.random_box_system(700, (8.5, 9.0, 30.0), 23, periodic=(1, 1, 0))
@@ -112,8 +112,8 @@ def test_fp64_hotspot_1000_substeps():
 
 
 def test_fp32_track_10k_substeps():
-    # track profile on 16^3 cells (16,384 atoms), FP32 flux, 100 MD steps x 100 substeps,
-    # Langevin coupling, free flight: T_e within 1e-4, energy drift within 1e-9
+    # track profile on 16^3 cells (16,384 atoms), FP32 flux, 100 MD steps x 100 substeps
+    # (0.1 fs each), Langevin coupling, free flight: T_e within 1e-4, energy drift within 1e-9
     s = I.track_system(16, 2, r0=10.0)
     p = I.params_track()
     sim, xo, vo = run_oracle(s, p, 100, 100)
@@ -123,7 +123,8 @@ def test_fp32_track_10k_substeps():
     assert err < 1e-4, err
     eg = g.energy()
     assert abs(eg["drift"]) < 1e-9
-    assert relerr(vg.cpu().numpy(), vo) < 1e-6
+    vg = vg.cpu().numpy()
+    assert np.abs(vg - vo).max() / np.abs(vo).max() < 1e-6
     print(f"track16 FP32: max rel T_e err {err:.3e}, drift {eg['drift']:.3e}")
 
 
@@ -207,8 +208,8 @@ def test_checkpoint_resume_bit_identical(tmp_path):
         for _ in range(n):
             g.build_neighbors(x, v)
             g.substep(50)
-            g.couple(v, 1.0)
-            g.drift(x, v, 1.0)
+            g.couple(v, 0.05)
+            g.drift(x, v, 0.05)
 
     g = Ehc(p, s)
     g.set_te(s.Te)
@@ -245,7 +246,7 @@ def test_host_buffer_step_matches_device_calls():
     vh = torch.as_tensor(s.v).clone().pin_memory()
     Te = torch.empty(s.n, dtype=torch.float64).pin_memory()
     for k in range(2):
-        h.md_step_host(xh, vh, 30, k * 30 * p["dt_sub"], 1.0, Te)
+        h.md_step_host(xh, vh, 30, k * 30 * p["dt_sub"], 30 * p["dt_sub"], Te)
     assert np.array_equal(Te.numpy(), g.get_te().cpu().numpy())
     assert np.array_equal(vh.numpy(), vg.cpu().numpy())
     assert np.array_equal(xh.numpy(), xg.cpu().numpy())
