@@ -60,8 +60,9 @@ extern "C" {
  *                   force with the same exact energy hand-over
  *   frozen          1: velocities are never changed (the lattice is a bookkeeping sink)
  *   dof_mode        0: T_lat divisor (3/2) k_B N_j (paper); 1: (3/2) k_B (N_j - 1)
- *   flux_prec       0: pair flux in FP32 on the (T - Tref)/Tmax mirror, state in FP64;
- *                   1: pair flux in FP64
+ *   flux_prec       0: pair flux in FP32 on the (T - Tref)/Tmax mirror, substep state as a
+ *                   float pair (about 48 bits), T kept in FP64 between calls, per-atom
+ *                   exchanged energy in FP64; 1: everything in FP64
  *   Tref_K          reference temperature of the FP32 mirror
  *   laser_*         optional source of Eq. LaserIntesity (Sec. 5): absorbed fluence,
  *                   penetration length, pulse centre and standard deviation
@@ -101,7 +102,7 @@ typedef struct ehc_params {
  * incrementally: E_e0 = sum_i V_atom int_0^{T_i} C_e(T) dT at ehc_set_te, then
  * each MD step adds V_atom C_e sum_i dT_i with that step's C_e.  E_lat is the
  * kinetic energy the lattice received, E_src the energy of the source term.
- * drift = (E_e + E_lat - E_src - E_e0) / E_e0. */
+ * drift = (E_e + E_lat - E_src - E_e0) / max(|E_e0|, |E_e|). */
 typedef struct ehc_energy_t {
   double E_e, E_lat, E_src, E_e0, drift;
   double sum_T, max_T, mean_T;

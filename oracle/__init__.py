@@ -283,4 +283,4 @@ class OracleSim:
         E_e = self.E_base + self.VC * (s - self.ST_base) if self.VC is not None else self.E_base
         return {"E_e": E_e, "E_lat": self.E_lat, "E_src": self.E_src, "E_e0": self.E_e0,
                 "sum_T": s, "max_T": float(self.T.max()),
-                "drift": (E_e + self.E_lat - self.E_src - self.E_e0) / self.E_e0}
+                "drift": (E_e + self.E_lat - self.E_src - self.E_e0) / max(abs(self.E_e0), abs(E_e))}

@@ -361,15 +361,16 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 }
 
 /* Three standard normals for atom `id` at MD step `step`: counter
- * (id lo, id hi, step lo, step hi), key (seed lo, seed hi); uniforms
- * u = (x + 1/2) / 2^32 in (0, 1); Box-Muller in double precision. */
+ * (id lo, id hi, step lo, step hi), key (seed lo, seed hi); uniforms from the
+ * top 24 bits of each word, u = (x + 1/2) / 2^24 in (0, 1); Box-Muller in
+ * double precision. */
 void oracle_gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
   uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
   uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t r[4];
   oracle_philox4x32_10(c, k, r);
   double u[4];
-  for (int m = 0; m < 4; ++m) u[m] = ((double)r[m] + 0.5) / 4294967296.0;
+  for (int m = 0; m < 4; ++m) u[m] = ((double)(r[m] >> 8) + 0.5) / 16777216.0;
   double r1 = sqrt(-2.0 * log(u[0]));
   double r2 = sqrt(-2.0 * log(u[2]));
   g[0] = r1 * cos(2.0 * M_PI * u[1]);

@@ -8,12 +8,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
 #include "ehc_internal.cuh"
 
 using namespace ehc;
+
 
 struct ehc_ctx {
   Ctx c;
@@ -52,12 +54,14 @@ void free_all(Ctx &c) {
   void *dev[] = {c.type_orig, c.type_s, c.q_orig, c.cell_count, c.cell_start, c.cell_fill, c.scan_tmp,
                  c.perm, c.inv_perm[0], c.inv_perm[1], c.q_s, c.v_s, c.nbr, c.cnt, c.T[0], c.T[1],
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
-                 c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out};
+                 c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
+                 c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
   if (c.scal_host) cudaFreeHost(c.scal_host);
   if (c.coef_host) cudaFreeHost(c.coef_host);
+  if (c.pulse_f_host) cudaFreeHost(c.pulse_f_host);
   for (int i = 0; i < c.n_graphs; ++i) cudaGraphExecDestroy(c.graphs[i].exec);
   c.n_graphs = 0;
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
@@ -67,33 +71,96 @@ void free_all(Ctx &c) {
 // read back scal[0..15] and the error word; synchronises the stream
 int readback(Ctx &c) {
   CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));
-  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
-  int32_t w[2];
+  int32_t w[4];
   std::memcpy(w, c.scal_host + 16, sizeof(w));
   c.dev_err = w[0];
   return EHC_OK;
+}
+
+// neighbour rows of every row (cy, cz): z offset outer, y offset inner, wrapped on
+// periodic axes, dropped outside non-periodic ones, duplicates removed, -1 padded
+void row_table(const Grid &g, std::vector<int32_t> &tab) {
+  const int64_t ny = g.nc[1], nz = g.nc[2];
+  tab.assign((size_t)(ny * nz * kRowNbr), -1);
+  for (int64_t cz = 0; cz < nz; ++cz)
+    for (int64_t cy = 0; cy < ny; ++cy) {
+      const int64_t R = cy + ny * cz;
+      int m = 0;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+          int64_t z = cz + dz, y = cy + dy;
+          if (g.per[2]) z = (z + nz) % nz;
+          else if (z < 0 || z >= nz) continue;
+          if (g.per[1]) y = (y + ny) % ny;
+          else if (y < 0 || y >= ny) continue;
+          const int32_t R2 = (int32_t)(y + ny * z);
+          bool dup = false;
+          for (int q = 0; q < m; ++q) dup |= tab[R * kRowNbr + q] == R2;
+          if (!dup) tab[R * kRowNbr + m++] = R2;
+        }
+    }
 }
 
 double cap_SI(const Ctx &c) {
   return c.p.Ce_cap_kB > 0 ? c.p.Ce_cap_kB * kKB_J / (c.vatom * 1e-30) : 0.0;
 }
 
+// n_sub substeps on the context stream.  The single-precision path splits T
+// into the float-float state first and merges it back at the end.  Loops of 4 or
+// more substeps are captured once into a CUDA graph and replayed; the key holds
+// everything a launch bakes in (buffer choice, path, pairs per atom).
+cudaError_t enqueue_substeps(Ctx &c, int32_t n_sub, int p0, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n_sub && e == cudaSuccess; ++k) e = launch_substep(c, k, p0 ^ (k & 1), st);
+  return e;
+}
+
+// The single-precision path keeps its float-float state between substep calls;
+// T (FP64) is rebuilt from it only when something reads T, and the state is
+// split from T again only after something changed T.
+int ensure_t(Ctx &c) {
+  if (c.t_stale) {
+    CK(launch_merge(c, c.parity, c.stream));
+    c.t_stale = false;
+  }
+  return EHC_OK;
+}
+
+int ensure_split(Ctx &c) {
+  if (c.p.flux_prec == 0 && !c.ff_valid) {
+    CK(launch_split(c, c.stream));
+    // row value ranges of this snapshot are unknown: the first substep takes the
+    // general polynomial everywhere
+    if (c.nrows > 0) {
+      CK(cudaMemsetAsync(c.rrange[c.parity], 0xfe, sizeof(float) * c.nrows, c.stream));
+      CK(cudaMemsetAsync(c.rrange[c.parity] + c.nrows, 0x7f, sizeof(float) * c.nrows, c.stream));
+    }
+    c.ff_valid = true;
+  }
+  return EHC_OK;
+}
+
 int run_substeps(Ctx &c, int32_t n_sub) {
   const int p0 = (c.p.flux_prec == 1) ? c.tcur : c.parity;
   const int ab = (c.A == c.abuf[0]) ? 0 : 1;
+  const int path = (c.p.flux_prec == 1) ? 2 : (tile_path(c) ? 1 : 0);
+  const int pairs = (c.n_max + 1) / 2;
+  const int tile = c.tile_floats;
   bool use_graph = c.p.use_graph && n_sub >= 4;
   if (use_graph) {
     int hit = -1;
     for (int i = 0; i < c.n_graphs; ++i) {
       const auto &e = c.graphs[i];
-      if (e.n_sub == n_sub && e.parity == p0 && e.tcur == c.tcur && e.abuf == ab) hit = i;
+      if (e.n_sub == n_sub && e.parity == p0 && e.tcur == c.tcur && e.abuf == ab && e.path == path &&
+          e.pairs == pairs && e.tile == tile)
+        hit = i;
     }
     if (hit < 0) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t le = cudaSuccess;
-      for (int k = 0; k < n_sub && le == cudaSuccess; ++k) le = launch_substep(c, k, p0 ^ (k & 1), c.cap_stream);
+      cudaError_t le = enqueue_substeps(c, n_sub, p0, c.cap_stream);
       cudaError_t ee = cudaStreamEndCapture(c.cap_stream, &graph);
       if (le != cudaSuccess || ee != cudaSuccess) return EHC_E_CUDA;
       cudaGraphExec_t exec;
@@ -108,17 +175,21 @@ int run_substeps(Ctx &c, int32_t n_sub) {
         c.graphs[lru] = c.graphs[7];
         c.n_graphs = 7;
       }
-      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, exec, 0};
+      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, path, pairs, tile, exec, 0};
       hit = c.n_graphs++;
     }
     c.graphs[hit].last_use = ++c.use_clock;
     CK(cudaGraphLaunch(c.graphs[hit].exec, c.stream));
   } else {
-    for (int k = 0; k < n_sub; ++k) CK(launch_substep(c, k, p0 ^ (k & 1), c.stream));
+    CK(enqueue_substeps(c, n_sub, p0, c.stream));
   }
   const int p1 = p0 ^ (n_sub & 1);
-  if (c.p.flux_prec == 1) c.tcur = p1;
-  else c.parity = p1;
+  if (c.p.flux_prec == 1) {
+    c.tcur = p1;
+  } else {
+    c.parity = p1;
+    c.t_stale = true;
+  }
   return EHC_OK;
 }
 
@@ -212,8 +283,14 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.inv_perm[0], n));
   A(dalloc(&c.inv_perm[1], n));
   A(dalloc(&c.q_s, n));
-  A(dalloc(&c.v_s, 3 * n));
+  A(dalloc(&c.v_s, n));
   A(dalloc(&c.nbr, (size_t)W * n));
+  A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * n));
+  A(dalloc(&c.dlo, n));
+  A(dalloc(&c.uTl, n));
+  A(dalloc(&c.pulse_f, c.max_sub));
+  c.nrows = (int64_t)c.g.nc[1] * c.g.nc[2];
+  A(dalloc(&c.row_nbr, c.nrows * kRowNbr));
   A(dalloc(&c.cnt, n));
   A(dalloc(&c.T[0], n));
   A(dalloc(&c.T[1], n));
@@ -225,11 +302,12 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.Tl_d, n));
   A(dalloc(&c.depth_orig, n));
   A(dalloc(&c.srcw, n));
+  A(dalloc(&c.srcw_d, n));
   A(dalloc(&c.pulse, c.max_sub));
   A(dalloc(&c.dKE, n));
   A(dalloc(&c.partials, kRedBlocks * 4));
   A(dalloc(&c.scal, 16));
-  A(dalloc(&c.err, 2));
+  A(dalloc(&c.err, 4));
   A(dalloc(&c.coef, 1));
   A(dalloc(&c.x_dev, 3 * n));
   A(dalloc(&c.v_dev, 3 * n));
@@ -237,6 +315,10 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(cudaMallocHost((void **)&c.pulse_host, sizeof(double) * c.max_sub));
   A(cudaMallocHost((void **)&c.scal_host, sizeof(double) * 24));
   A(cudaMallocHost((void **)&c.coef_host, sizeof(StepCoef)));
+  A(cudaMallocHost((void **)&c.pulse_f_host, sizeof(float) * c.max_sub));
+  A(dalloc(&c.rrange[0], 2 * c.nrows));
+  A(dalloc(&c.rrange[1], 2 * c.nrows));
+  A(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, 0));
   A(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   A(cudaEventCreateWithFlags(&c.pulse_ev, cudaEventDisableTiming));
   if (!ok) {
@@ -248,11 +330,16 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   c.A = c.abuf[0];
   c.A_tmp = c.abuf[1];
   c.maxcnt = c.err + 1;
+  c.maxstaged = c.err + 2;
+  std::vector<int32_t> rt;
+  row_table(c.g, rt);
   cudaError_t e = cudaSuccess;
   if (n_types > 1 && n > 0)
     e = cudaMemcpyAsync(c.type_orig, type_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.scal, 0, sizeof(double) * 16, c.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 2, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 4, c.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c.row_nbr, rt.data(), sizeof(int32_t) * rt.size(), cudaMemcpyHostToDevice, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.abuf[0], 0, sizeof(double) * (n > 0 ? n : 1), c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.srcw, 0, sizeof(float) * (n > 0 ? n : 1), c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
@@ -285,6 +372,8 @@ int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
   c.te_orig_order = true;
   c.have_te = true;
   c.built = false;
+  c.ff_valid = false;
+  c.t_stale = false;
   c.E_e0 = c.scal_host[2] * c.vatom * 1e-30 / kEV_J;
   c.E_base = c.E_e0;
   c.ST_base = c.scal_host[0];
@@ -308,6 +397,9 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   Ctx &c = h->c;
   if (!c.have_te) return EHC_E_STATE;
   if (c.n > 0 && (!x_dev || !v_dev)) return EHC_E_INVAL;
+  int r0 = ensure_t(c);
+  if (r0) return r0;
+  c.ff_valid = false;
   CK(launch_bin(c, x_dev));
   CK(launch_sort_cells(c));
   CK(launch_gather(c, v_dev, c.te_orig_order));
@@ -317,9 +409,20 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   CK(launch_globals(c));
   int r = readback(c);
   if (r) return r;
-  int32_t w[2];
+  int32_t w[4];
   std::memcpy(w, c.scal_host + 16, sizeof(w));
   c.n_max = w[1];
+  c.staged_max = w[2];
+  // size the row tiles with headroom for atoms drifting between cells
+  if (c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
+    const int32_t tb = ((c.staged_max + c.staged_max / 4 + 64 + 255) / 256) * 256;
+    int bps = 0;
+    if ((int64_t)tb * 2 * (int64_t)sizeof(float) <= kTileMaxBytes && tile_setup(tb, &bps) == cudaSuccess && bps > 0) {
+      c.tile_floats = tb;
+      c.tile_grid = bps * c.num_sms;
+    }
+    cudaGetLastError();
+  }
   const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
   c.wsum = c.scal_host[3];
   // ledger: close the previous MD step with its own C_e
@@ -355,7 +458,11 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   cf.invTmax = 1.0 / c.p.Tmax_K;
   cf.Tref = c.p.Tref_K;
   cf.th_ref = (float)(c.p.Tref_K / c.p.Tmax_K);
-  cf.pad = 0.f;
+  cf.omt = (float)(1.0 - c.p.Tref_K / c.p.Tmax_K);
+  cf.dtK_f = (float)(c.p.dt_sub_fs * c.K);
+  cf.dtcGn_f = (float)(c.p.dt_sub_fs * c.cG / c.p.Tmax_K);
+  cf.Tmax_f = (float)c.p.Tmax_K;
+  cf.pad[0] = cf.pad[1] = cf.pad[2] = 0.f;
   CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
   c.built = true;
   return err_code(c.dev_err);
@@ -381,12 +488,19 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
         const double u = (t - c.p.laser_t0_fs) / sig;
         const double rate = S0 * std::exp(-0.5 * u * u) / c.Ce * 1e-15;  // K / fs at depth 0
         c.pulse_host[k] = rate;
-        c.E_src += c.VC * c.p.dt_sub_fs * rate * c.wsum;
+        // the single-precision path adds the exact product of these two floats per atom
+        const float cf = (float)(c.p.dt_sub_fs * rate / c.p.Tmax_K);
+        c.pulse_f_host[k] = cf;
+        if (c.p.flux_prec == 1) c.E_src += c.VC * c.p.dt_sub_fs * rate * c.wsum;
+        else c.E_src += c.VC * c.p.Tmax_K * (double)cf * c.wsum;
       }
       CK(cudaMemcpyAsync(c.pulse, c.pulse_host, sizeof(double) * chunk, cudaMemcpyHostToDevice, c.stream));
+      CK(cudaMemcpyAsync(c.pulse_f, c.pulse_f_host, sizeof(float) * chunk, cudaMemcpyHostToDevice, c.stream));
       CK(cudaEventRecord(c.pulse_ev, c.stream));
     }
-    int r = run_substeps(c, chunk);
+    int r = ensure_split(c);
+    if (r) return r;
+    r = run_substeps(c, chunk);
     if (r) return r;
     done += chunk;
   }
@@ -398,7 +512,10 @@ int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
   Ctx &c = h->c;
   if (!c.built) return EHC_E_STATE;
   if (c.n > 0 && !v_dev && !c.p.frozen) return EHC_E_INVAL;
+  int r = ensure_t(c);
+  if (r) return r;
   CK(launch_couple(c, v_dev, dt_md_fs));
+  c.ff_valid = false;
   c.md_step += 1;
   return EHC_OK;
 }
@@ -412,9 +529,9 @@ int ehc_drift(ehc_ctx *h, double *x_dev, const double *v_dev, double dt_fs) {
 int ehc_sync(ehc_ctx *h) {
   if (!h) return EHC_E_INVAL;
   Ctx &c = h->c;
-  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
-  int32_t w[2];
+  int32_t w[4];
   std::memcpy(w, c.scal_host + 16, sizeof(w));
   c.dev_err = w[0];
   return err_code(c.dev_err);
@@ -424,6 +541,8 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   if (!h || !out) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.have_te) return EHC_E_STATE;
+  int r0 = ensure_t(c);
+  if (r0) return r0;
   CK(launch_ledger(c));
   int r = readback(c);
   if (r) return r;
@@ -433,7 +552,8 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   out->E_lat = c.scal_host[8];
   out->E_src = c.E_src;
   out->E_e0 = c.E_e0;
-  out->drift = c.E_e0 != 0 ? (out->E_e + out->E_lat - out->E_src - out->E_e0) / c.E_e0 : 0.0;
+  const double scale = std::max(std::fabs(c.E_e0), std::fabs(out->E_e));
+  out->drift = scale > 0 ? (out->E_e + out->E_lat - out->E_src - out->E_e0) / scale : 0.0;
   out->sum_T = sumT;
   out->max_T = c.scal_host[1];
   out->mean_T = c.n > 0 ? sumT / (double)c.n : 0.0;
@@ -455,6 +575,8 @@ int ehc_get_te(ehc_ctx *h, double *Te_dev_out) {
   if (!h || (!Te_dev_out && h->c.n > 0)) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.have_te) return EHC_E_STATE;
+  int r = ensure_t(c);
+  if (r) return r;
   CK(launch_unpermute(c, c.T[c.tcur], Te_dev_out, c.te_orig_order ? 1 : 0));
   return EHC_OK;
 }
@@ -491,6 +613,7 @@ int ehc_export_neighbors(ehc_ctx *h, int64_t *rowptr, int32_t *col, int64_t cap)
     const int64_t s = inv[o];
     int64_t b = rowptr[o];
     for (int k = 0; k < cnt[s]; ++k) col[b + k] = perm[nbr[(size_t)k * n + s]];
+    std::sort(col + b, col + b + cnt[s]);
   }
   return EHC_OK;
 }
@@ -613,6 +736,8 @@ int ehc_load(ehc_ctx *h, const char *path) {
   c.have_te = true;
   c.te_orig_order = true;
   c.built = false;
+  c.ff_valid = false;
+  c.t_stale = false;
   return EHC_OK;
 }
 

@@ -54,8 +54,19 @@ struct StepCoef {
   double invTmax;  // 1 / Tmax
   double Tref;     // mirror reference
   float th_ref;    // Tref / Tmax
-  float pad;
+  float omt;       // 1 - Tref / Tmax
+  float dtK_f;     // dt * K: flux increment of delta = (T - Tref) / Tmax
+  float dtcGn_f;   // dt * G / (C_e Tmax)
+  float Tmax_f;
+  float pad[3];
 };
+
+// Row tiles: a row is the run of cells with the same (cy, cz); its atoms are a
+// contiguous range of the sorted order.  Every neighbour of an atom lies in the
+// (at most 9, deduplicated) rows around its own, listed in a fixed order.
+constexpr int kRowNbr = 9;
+constexpr int kTileThreads = 512;
+constexpr int kTileMaxBytes = 200 * 1024;   // two tile buffers must fit in this much shared memory
 
 // Deterministic block-partial reductions.
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
@@ -75,6 +86,10 @@ cudaError_t launch_seed(Ctx &c, double cap_SI);
 cudaError_t launch_ledger(Ctx &c);
 // kernels_substep.cu
 cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t s);
+cudaError_t launch_split(Ctx &c, cudaStream_t s);
+cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
+bool tile_path(const Ctx &c);
+cudaError_t tile_setup(int tb, int *blocks_per_sm);
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);
@@ -105,28 +120,42 @@ struct Ctx {
   int32_t *inv_perm[2] = {nullptr, nullptr};
   int cur_inv = 0;
   int4 *q_s = nullptr;           // sorted positions + cell id
-  double *v_s = nullptr;         // sorted velocities [3N]
+  double4_32a *v_s = nullptr;        // sorted velocities and |v|^2
   int32_t *nbr = nullptr;        // [W][N]
+  uint32_t *pidx = nullptr;      // [W/2][N] pairs of 16-bit tile-local neighbour indices
+  int32_t *row_nbr = nullptr;    // [nrows][9] neighbour rows, -1 padded
+  int64_t nrows = 0;
   uint8_t *cnt = nullptr;
   double *T[2] = {nullptr, nullptr};   // T[tcur] is the state
   int tcur = 0;
-  float *dmir[2] = {nullptr, nullptr};
+  float *dmir[2] = {nullptr, nullptr};  // hi part of delta = (T - Tref)/Tmax, double-buffered
+  float *dlo = nullptr;          // lo part of delta (float-float state of the FP32 path)
+  float *uTl = nullptr;          // Tref - T_l,i (NaN: atom below the guard)
   double *abuf[2] = {nullptr, nullptr};
   double *A = nullptr;           // one of abuf
   double *A_tmp = nullptr;       // the other
   float *Tl_f = nullptr;
   double *Tl_d = nullptr;
   double *depth_orig = nullptr;
-  float *srcw = nullptr;         // exp(-depth / l_p), sorted
-  double *pulse = nullptr;       // per-substep source rate factors [max_sub]
+  float *srcw = nullptr;         // exp(-depth / l_p), sorted (single-precision path)
+  double *srcw_d = nullptr;      // the same in FP64 (double-precision path)
+  double *pulse = nullptr;       // per-substep source rate factors [max_sub] (K/fs, FP64 path)
   double *pulse_host = nullptr;  // pinned staging
+  float *pulse_f = nullptr;      // dt * rate / Tmax per substep (FP32 path)
+  float *pulse_f_host = nullptr;
   int32_t max_sub = 0;
   double *dKE = nullptr;
   double *partials = nullptr;    // [kRedBlocks * 4]
   double *scal = nullptr;        // device scalars [16]
   double *scal_host = nullptr;   // pinned mirror [16]
   int32_t *err = nullptr;        // device error word
-  int32_t *maxcnt = nullptr;     // device max count (adjacent to err)
+  int32_t *maxcnt = nullptr;     // device max count (err + 1)
+  int32_t *maxstaged = nullptr;  // largest staged row-tile size (err + 2)
+  int32_t staged_max = 0;
+  int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)
+  int32_t tile_grid = 0;         // resident CTAs of the row-tile kernel
+  int32_t num_sms = 0;
+  float *rrange[2] = {nullptr, nullptr};  // [min of every row | max of every row] of each mirror
   StepCoef *coef = nullptr;      // device
   StepCoef *coef_host = nullptr; // pinned
   double *x_dev = nullptr, *v_dev = nullptr, *T_out = nullptr;  // staging of the host-buffer step
@@ -136,6 +165,8 @@ struct Ctx {
   bool te_orig_order = false;    // T[tcur] still in caller order (before the first build)
   bool built = false;
   bool have_depth = false;
+  bool ff_valid = false;         // float-float substep state holds the current temperatures
+  bool t_stale = false;          // T[tcur] is behind the float-float state
   int parity = 0;                // mirror buffer holding the current snapshot
   int64_t md_step = 0;
   int32_t n_max = 0;             // largest neighbour count this MD step
@@ -150,7 +181,7 @@ struct Ctx {
 
   // captured substep loops, keyed by everything a launch bakes in
   struct GraphEntry {
-    int n_sub, parity, tcur, abuf;
+    int n_sub, parity, tcur, abuf, path, pairs, tile;
     cudaGraphExec_t exec;
     uint64_t last_use;
   };

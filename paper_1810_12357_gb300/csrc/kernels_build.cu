@@ -18,14 +18,6 @@ namespace {
 constexpr double kKB = 8.617333262e-5;          // eV/K (CODATA 2018)
 constexpr double kMVV = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;  // amu (A/fs)^2 -> eV
 
-__device__ __forceinline__ int64_t min_image(int64_t d, int64_t L, int per) {
-  if (per) {
-    if (2 * d > L) d -= L;
-    else if (2 * d < -L) d += L;
-  }
-  return d;
-}
-
 __global__ void bin_kernel(const double *__restrict__ x, int64_t n, Grid g, int4 *__restrict__ q,
                            int32_t *__restrict__ count, int32_t *__restrict__ err) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -159,19 +151,18 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
                               const int32_t *__restrict__ inv_old, int src_is_orig,
                               const double *__restrict__ T_old, const double *__restrict__ A_old,
                               int32_t *__restrict__ inv_new, int4 *__restrict__ q_s,
-                              double *__restrict__ v_s, int8_t *__restrict__ type_s,
+                              double4_32a *__restrict__ v_s, int8_t *__restrict__ type_s,
                               double *__restrict__ T_new, double *__restrict__ A_new,
                               float *__restrict__ dmir0, double Tref, double invTmax,
                               const double *__restrict__ depth, float *__restrict__ srcw,
-                              double inv_lp) {
+                              double *__restrict__ srcw_d, double inv_lp) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int32_t o = perm[s];
   q_s[s] = q[o];
   inv_new[o] = (int32_t)s;
-  v_s[3 * s + 0] = v[3 * (int64_t)o + 0];
-  v_s[3 * s + 1] = v[3 * (int64_t)o + 1];
-  v_s[3 * s + 2] = v[3 * (int64_t)o + 2];
+  const double vx = v[3 * (int64_t)o + 0], vy = v[3 * (int64_t)o + 1], vz = v[3 * (int64_t)o + 2];
+  v_s[s] = make_double4_32a(vx, vy, vz, vx * vx + vy * vy + vz * vz);
   int32_t ty = type_orig ? type_orig[o] : 0;
   type_s[s] = (int8_t)(ty < 0 ? 0 : (ty >= kMaxTypes ? kMaxTypes - 1 : ty));
   int64_t src = src_is_orig ? (int64_t)o : (int64_t)inv_old[o];
@@ -179,114 +170,157 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
   T_new[s] = T;
   A_new[s] = A_old[src];
   dmir0[s] = (float)((T - Tref) * invTmax);
-  if (srcw) srcw[s] = depth ? (float)exp(-depth[o] * inv_lp) : 0.0f;
+  const double w = depth ? exp(-depth[o] * inv_lp) : 0.0;
+  srcw[s] = (float)w;
+  srcw_d[s] = w;
 }
 
-template <int WMAX>
-__global__ void __launch_bounds__(128) neighbor_kernel(int64_t n, Grid g, const int4 *__restrict__ q_s,
+// One thread per atom.  Candidates come from the atom's (deduplicated) neighbour
+// rows and, within each row, the (deduplicated) cells cx-1, cx, cx+1.  All
+// arithmetic is on the integer grid: per-axis minimum image in int32, the
+// squared distance in int64, inclusive comparison with r_c^2.  Outputs:
+//   nbr  [W][N] sorted indices in visit order (row, cell, sorted index)
+//   pidx [W/2][N] the same neighbours as 16-bit indices into the row tile (the
+//        concatenation of the neighbour rows), two per word; unused slots up to
+//        W hold the atom's own tile index, whose pair term is exactly zero.
+__global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
                                                        const int32_t *__restrict__ start,
-                                                       const int32_t *__restrict__ perm, int32_t W,
-                                                       int32_t *__restrict__ nbr, uint8_t *__restrict__ cnt,
-                                                       int32_t *__restrict__ maxcnt, int32_t *__restrict__ err) {
-  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                                       const int32_t *__restrict__ row_nbr, int32_t W,
+                                                       int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
+                                                       uint8_t *__restrict__ cnt, int32_t *__restrict__ maxcnt,
+                                                       int32_t *__restrict__ maxstaged, int32_t *__restrict__ err) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 qi = q_s[s];
-  int32_t ci[3];
-  ci[0] = qi.w % g.nc[0];
-  ci[1] = (qi.w / g.nc[0]) % g.nc[1];
-  ci[2] = qi.w / (g.nc[0] * g.nc[1]);
-  // distinct neighbour cells per axis (an axis with fewer than 3 cells repeats otherwise)
-  int32_t off[3][3];
-  int nof[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    nof[k] = 0;
-    for (int d = -1; d <= 1; ++d) {
-      int32_t c = ci[k] + d;
-      if (g.per[k]) {
-        if (c < 0) c += g.nc[k];
-        if (c >= g.nc[k]) c -= g.nc[k];
-      } else if (c < 0 || c >= g.nc[k]) {
-        continue;
-      }
-      bool dup = false;
-      for (int m = 0; m < nof[k]; ++m) dup |= (off[k][m] == c);
-      if (!dup) off[k][nof[k]++] = c;
+  const int32_t ncx = g.nc[0];
+  const int32_t cx = qi.w % ncx;
+  const int32_t R = qi.w / ncx;
+  int32_t xo[3];
+  int nx = 0;
+  for (int d = -1; d <= 1; ++d) {
+    int32_t c = cx + d;
+    if (g.per[0]) {
+      if (c < 0) c += ncx;
+      if (c >= ncx) c -= ncx;
+    } else if (c < 0 || c >= ncx) {
+      continue;
     }
+    bool dup = false;
+    for (int m = 0; m < nx; ++m) dup |= (xo[m] == c);
+    if (!dup) xo[nx++] = c;
   }
+  const int32_t L0 = (int32_t)g.Lq[0], L1 = (int32_t)g.Lq[1], L2 = (int32_t)g.Lq[2];
+  const int32_t h0 = L0 >> 1, h1 = L1 >> 1, h2 = L2 >> 1;
+  const int32_t rcq = (int32_t)g.rcq;
   const int64_t rc2 = g.rcq * g.rcq;
-  int32_t ct[WMAX];
-  int32_t ck[WMAX];
   int32_t m = 0;
-  for (int a = 0; a < nof[2]; ++a)
-    for (int b = 0; b < nof[1]; ++b)
-      for (int d = 0; d < nof[0]; ++d) {
-        int32_t cell = off[0][d] + g.nc[0] * (off[1][b] + g.nc[1] * off[2][a]);
-        int32_t e = start[cell + 1];
-        for (int32_t t = start[cell]; t < e; ++t) {
-          if (t == (int32_t)s) continue;
-          int4 qj = q_s[t];
-          int64_t dx = min_image((int64_t)qj.x - qi.x, g.Lq[0], g.per[0]);
-          if (dx > g.rcq || dx < -g.rcq) continue;
-          int64_t dy = min_image((int64_t)qj.y - qi.y, g.Lq[1], g.per[1]);
-          if (dy > g.rcq || dy < -g.rcq) continue;
-          int64_t dz = min_image((int64_t)qj.z - qi.z, g.Lq[2], g.per[2]);
-          if (dz > g.rcq || dz < -g.rcq) continue;
-          if (dx * dx + dy * dy + dz * dz <= rc2) {
-            if (m < W) {
-              int32_t key = perm[t];
-              // insertion into the row, ascending original id
-              int32_t j = m - 1;
-              while (j >= 0 && ck[j] > key) {
-                ck[j + 1] = ck[j];
-                ct[j + 1] = ct[j];
-                --j;
-              }
-              ck[j + 1] = key;
-              ct[j + 1] = t;
-            }
-            ++m;
+  int32_t prefix = 0;   // tile offset of the current neighbour row
+  int32_t tend = 0;     // end of the tile so far
+  int32_t self_local = 0;
+  for (int r = 0; r < kRowNbr; ++r) {
+    const int32_t R2 = row_nbr[(int64_t)R * kRowNbr + r];
+    if (R2 < 0) break;
+    const int32_t rs = start[(int64_t)R2 * ncx];
+    const int32_t re = start[(int64_t)R2 * ncx + ncx];
+    // row placement in the tile: congruent to its first index modulo 4
+    prefix = tend + ((rs - tend) & 3);
+    if (R2 == R) self_local = prefix + (s - rs);
+    for (int ix = 0; ix < nx; ++ix) {
+      const int32_t cell = R2 * ncx + xo[ix];
+      const int32_t t1 = start[cell + 1];
+      for (int32_t t = start[cell]; t < t1; ++t) {
+        if (t == s) continue;
+        const int4 qj = q_s[t];
+        int32_t dx = qj.x - qi.x;
+        if (g.per[0]) dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
+        if (dx > rcq || dx < -rcq) continue;
+        int32_t dy = qj.y - qi.y;
+        if (g.per[1]) dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
+        if (dy > rcq || dy < -rcq) continue;
+        int32_t dz = qj.z - qi.z;
+        if (g.per[2]) dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+        if (dz > rcq || dz < -rcq) continue;
+        const int64_t d2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+        if (d2 <= rc2) {
+          if (m < W) {
+            nbr[(int64_t)m * n + s] = t;
+            pidx16[((int64_t)(m >> 1) * n + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
           }
+          ++m;
         }
       }
+    }
+    tend = prefix + (re - rs);
+  }
   if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
-  int32_t mm = m < W ? m : W;
-  for (int32_t k = 0; k < mm; ++k) nbr[(int64_t)k * n + s] = ct[k];
+  const int32_t mm = m < W ? m : W;
+  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * n + s) * 2 + (k & 1)] = (uint16_t)self_local;
   cnt[s] = (uint8_t)mm;
-  atomicMax(maxcnt, m);
+  // one atomic per warp for the two maxima
+  const unsigned act = __activemask();
+  const int32_t wm = __reduce_max_sync(act, m);
+  const int32_t ws = __reduce_max_sync(act, tend);
+  if ((threadIdx.x & 31) == (__ffs(act) - 1)) {
+    atomicMax(maxcnt, wm);
+    atomicMax(maxstaged, ws);
+  }
 }
 
-// Sec. 2: T_i^lat = sum_S (1/2) m |v - v_com|^2 / ((3/2) k_B N_j) over S = {i} + neighbours
-__global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr,
-                                    const uint8_t *__restrict__ cnt, const double *__restrict__ v_s,
-                                    const int8_t *__restrict__ type_s, MassTable mt, int dof_mode,
-                                    double eps_ke, double *__restrict__ Tl_d, float *__restrict__ Tl_f) {
-  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Sec. 2: T_i^lat = sum_S (1/2) m |v - v_com|^2 / ((3/2) k_B N_j) over S = {i} + neighbours.
+// With M = sum m, P = sum m v, W = sum m |v|^2:  sum (1/2) m |v - v_com|^2 = (W - |P|^2 / M) / 2.
+// One atom type: M = m N_j, P = m sum v, W = m sum |v|^2 (four FP64 additions per neighbour).
+template <bool ONE_TYPE>
+__global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
+                                    const double4_32a *__restrict__ v_s, const int8_t *__restrict__ type_s,
+                                    MassTable mt, int dof_mode, double eps_ke, double Tref,
+                                    double *__restrict__ Tl_d, float *__restrict__ Tl_f, float *__restrict__ uTl) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int c = cnt[s];
-  double M = 0, px = 0, py = 0, pz = 0;
-  for (int k = -1; k < c; ++k) {
-    int64_t t = (k < 0) ? s : (int64_t)nbr[(int64_t)k * n + s];
-    double m = mt.m[type_s[t]];
-    M += m;
-    px += m * v_s[3 * t + 0];
-    py += m * v_s[3 * t + 1];
-    pz += m * v_s[3 * t + 2];
+  const double4_32a vi = v_s[s];
+  double M, px, py, pz, W;
+  if (ONE_TYPE) {
+    double sx = vi.x, sy = vi.y, sz = vi.z, sw = vi.w;
+    for (int k = 0; k < c; ++k) {
+      const double4_32a vj = v_s[nbr[(int64_t)k * n + s]];
+      sx += vj.x;
+      sy += vj.y;
+      sz += vj.z;
+      sw += vj.w;
+    }
+    const double m = mt.m[0];
+    M = m * (double)(c + 1);
+    px = m * sx;
+    py = m * sy;
+    pz = m * sz;
+    W = m * sw;
+  } else {
+    const double mi = mt.m[type_s[s]];
+    M = mi;
+    px = mi * vi.x;
+    py = mi * vi.y;
+    pz = mi * vi.z;
+    W = mi * vi.w;
+    for (int k = 0; k < c; ++k) {
+      const int32_t t = nbr[(int64_t)k * n + s];
+      const double4_32a vj = v_s[t];
+      const double mj = mt.m[type_s[t]];
+      M += mj;
+      px += mj * vj.x;
+      py += mj * vj.y;
+      pz += mj * vj.z;
+      W += mj * vj.w;
+    }
   }
-  const double vx = px / M, vy = py / M, vz = pz / M;
-  double ke = 0;
-  for (int k = -1; k < c; ++k) {
-    int64_t t = (k < 0) ? s : (int64_t)nbr[(int64_t)k * n + s];
-    double dx = v_s[3 * t + 0] - vx, dy = v_s[3 * t + 1] - vy, dz = v_s[3 * t + 2] - vz;
-    ke += 0.5 * mt.m[type_s[t]] * (dx * dx + dy * dy + dz * dz) * kMVV;
-  }
+  const double ke = 0.5 * (W - (px * px + py * py + pz * pz) / M) * kMVV;
   const double dof = (dof_mode == 1) ? (double)c : (double)(c + 1);
   double T = dof > 0 ? ke / (1.5 * kKB * dof) : 0.0;
-  const double *vi = v_s + 3 * s;
-  double Ks = 0.5 * mt.m[type_s[s]] * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * kMVV;
-  if (!(Ks >= eps_ke)) T = -1.0;
+  const double Ks = 0.5 * mt.m[ONE_TYPE ? 0 : type_s[s]] * vi.w * kMVV;
+  const bool chi = Ks >= eps_ke;
+  if (!chi) T = -1.0;
   Tl_d[s] = T;
   Tl_f[s] = (float)T;
+  uTl[s] = chi ? (float)(Tref - T) : __int_as_float(0x7fc00000);
 }
 
 // Deterministic block reduction helpers: fixed thread-to-element map and a fixed
@@ -320,9 +354,10 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
 }
 
 // partial sums per block: [0] sum T, [1] max T, [2] sum KE (eV), [3] sum srcw
-__global__ void globals_partial(int64_t n, const double *__restrict__ T, const double *__restrict__ v_s,
+__global__ void globals_partial(int64_t n, const double *__restrict__ T, const double4_32a *__restrict__ v_s,
                                 const int8_t *__restrict__ type_s, MassTable mt,
-                                const float *__restrict__ srcw, double *__restrict__ part) {
+                                const float *__restrict__ srcw, const double *__restrict__ srcw_d,
+                                double *__restrict__ part) {
   __shared__ double sh[32];
   double sT = 0, mT = -1e300, sK = 0, sW = 0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
@@ -330,11 +365,9 @@ __global__ void globals_partial(int64_t n, const double *__restrict__ T, const d
     double t = T[s];
     sT += t;
     mT = fmax(mT, t);
-    if (v_s) {
-      const double *vi = v_s + 3 * s;
-      sK += 0.5 * mt.m[type_s[s]] * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * kMVV;
-    }
-    if (srcw) sW += (double)srcw[s];
+    if (v_s) sK += 0.5 * mt.m[type_s[s]] * v_s[s].w * kMVV;
+    if (srcw_d) sW += srcw_d[s];
+    else if (srcw) sW += (double)srcw[s];
   }
   double r0 = block_sum(sT, sh);
   double r1 = block_max(mT, sh);
@@ -435,7 +468,7 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
     gather_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
         c.n, c.perm, c.q_orig, v, c.type_orig, c.inv_perm[c.cur_inv], src_is_orig ? 1 : 0, c.T[c.tcur], c.A,
         c.inv_perm[nxt], c.q_s, c.v_s, c.type_s, c.T[tn], c.A_tmp, c.dmir[0], c.p.Tref_K, 1.0 / c.p.Tmax_K,
-        laser ? c.depth_orig : nullptr, c.srcw, laser ? 1.0 / c.p.laser_lp_A : 0.0);
+        laser ? c.depth_orig : nullptr, c.srcw, c.srcw_d, laser ? 1.0 / c.p.laser_lp_A : 0.0);
   c.cur_inv = nxt;
   c.tcur = tn;
   double *t = c.A;
@@ -446,35 +479,39 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
 }
 
 cudaError_t launch_neighbors(Ctx &c) {
-  cudaMemsetAsync(c.maxcnt, 0, sizeof(int32_t), c.stream);
+  cudaMemsetAsync(c.maxcnt, 0, sizeof(int32_t) * 2, c.stream);
   if (c.n == 0) return cudaGetLastError();
-  if (c.W <= 32)
-    neighbor_kernel<32><<<nblk(c.n, 128), 128, 0, c.stream>>>(c.n, c.g, c.q_s, c.cell_start, c.perm, c.W,
-                                                               c.nbr, c.cnt, c.maxcnt, c.err);
-  else
-    neighbor_kernel<64><<<nblk(c.n, 128), 128, 0, c.stream>>>(c.n, c.g, c.q_s, c.cell_start, c.perm, c.W,
-                                                               c.nbr, c.cnt, c.maxcnt, c.err);
+  neighbor_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W,
+                                                        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.cnt,
+                                                        c.maxcnt, c.maxstaged, c.err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lattice_temperature(Ctx &c) {
-  if (c.n > 0)
-    lattice_temp_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt,
-                                                              c.p.dof_mode, c.p.eps_ke_eV, c.Tl_d, c.Tl_f);
+  if (c.n == 0) return cudaGetLastError();
+  if (c.mt.n_types == 1)
+    lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt,
+                                                                    c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
+                                                                    c.Tl_d, c.Tl_f, c.uTl);
+  else
+    lattice_temp_kernel<false><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt,
+                                                                     c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
+                                                                     c.Tl_d, c.Tl_f, c.uTl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_globals(Ctx &c) {
-  globals_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.T[c.tcur], c.v_s, c.type_s, c.mt,
-                                                            (c.p.laser_on && c.have_depth) ? c.srcw : nullptr,
-                                                            c.partials);
+  const bool laser = c.p.laser_on && c.have_depth;
+  globals_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(
+      c.n, c.T[c.tcur], c.v_s, c.type_s, c.mt, (laser && c.p.flux_prec == 0) ? c.srcw : nullptr,
+      (laser && c.p.flux_prec == 1) ? c.srcw_d : nullptr, c.partials);
   globals_final<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ledger(Ctx &c) {
   globals_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.T[c.tcur], nullptr, nullptr, c.mt, nullptr,
-                                                            c.partials);
+                                                            nullptr, c.partials);
   globals_final<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal);
   return cudaGetLastError();
 }

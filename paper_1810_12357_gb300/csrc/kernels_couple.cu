@@ -39,21 +39,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// counter (id lo, id hi, step lo, step hi), key (seed lo, seed hi);
-// u = (x + 1/2) 2^-32; Box-Muller in double precision.
-__device__ __forceinline__ void gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
+// counter (id lo, id hi, step lo, step hi), key (seed lo, seed hi); the top
+// 24 bits of each output word give u = (x + 1/2) 2^-24 in (0, 1), exact in
+// single precision; Box-Muller in single precision.
+__device__ __forceinline__ void gauss3(uint64_t id, uint64_t step, uint64_t seed, float g[3]) {
   const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step,
                                            (uint32_t)(step >> 32)),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  const double s = 1.0 / 4294967296.0;
-  const double u0 = ((double)r.x + 0.5) * s, u1 = ((double)r.y + 0.5) * s;
-  const double u2 = ((double)r.z + 0.5) * s, u3 = ((double)r.w + 0.5) * s;
-  const double r1 = sqrt(-2.0 * log(u0));
-  const double r2 = sqrt(-2.0 * log(u2));
-  const double twopi = 6.283185307179586;
-  g[0] = r1 * cos(twopi * u1);
-  g[1] = r1 * sin(twopi * u1);
-  g[2] = r2 * cos(twopi * u3);
+  const float s = 5.9604644775390625e-08f;  // 2^-24
+  const float u0 = ((float)(r.x >> 8) + 0.5f) * s, u1 = ((float)(r.y >> 8) + 0.5f) * s;
+  const float u2 = ((float)(r.z >> 8) + 0.5f) * s, u3 = ((float)(r.w >> 8) + 0.5f) * s;
+  const float r1 = sqrtf(-2.0f * logf(u0));
+  const float r2 = sqrtf(-2.0f * logf(u2));
+  float sn, cs;
+  sincospif(2.0f * u1, &sn, &cs);
+  g[0] = r1 * cs;
+  g[1] = r1 * sn;
+  g[2] = r2 * cospif(2.0f * u3);
 }
 
 __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ type_s,
@@ -85,12 +87,13 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   }
   double w0 = v0, w1 = v1, w2 = v2;
   if (mode == 1) {
-    double g[3];
+    float g[3];
     gauss3((uint64_t)o, md_step, seed, g);
-    const double sig = sqrt(kKB * T[s] * one_m_e2 / (m * kMVV));
-    w0 = v0 * e1 + sig * g[0];
-    w1 = v1 * e1 + sig * g[1];
-    w2 = v2 * e1 + sig * g[2];
+    // noise amplitude in single precision (it multiplies a single-precision normal)
+    const float sig = sqrtf((float)(kKB * one_m_e2 / (m * kMVV) * T[s]));
+    w0 = v0 * e1 + (double)(sig * g[0]);
+    w1 = v1 * e1 + (double)(sig * g[1]);
+    w2 = v2 * e1 + (double)(sig * g[2]);
   }
   const double Kw = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
   const double sc = Kw > 0.0 ? sqrt(target / Kw) : 0.0;
@@ -140,24 +143,33 @@ __global__ void sum_final_accumulate(int nb, const double *__restrict__ part, do
 __global__ void drift_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ v, double dt,
                              double L0, double L1, double L2, int p0, int p1, int p2) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= 3 * n) return;
-  const int k = (int)(i % 3);
-  const double L = k == 0 ? L0 : (k == 1 ? L1 : L2);
-  const int per = k == 0 ? p0 : (k == 1 ? p1 : p2);
-  // no contraction: x + v dt rounds the product and the sum separately
-  double y = __dadd_rn(x[i], __dmul_rn(v[i], dt));
-  if (per) {
-    y = fmod(y, L);
-    if (y < 0.0) y += L;
+  if (i >= n) return;
+  double *xi = x + 3 * i;
+  const double *vi = v + 3 * i;
+  const double L[3] = {L0, L1, L2};
+  const int per[3] = {p0, p1, p2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // no contraction: x + v dt rounds the product and the sum separately
+    double y = __dadd_rn(xi[k], __dmul_rn(vi[k], dt));
+    if (per[k]) {
+      // one period at most per step; the same result as a floored modulo
+      if (y < 0.0) y += L[k];
+      else if (y >= L[k]) y -= L[k];
+      if (y < 0.0 || y > L[k]) {
+        y = fmod(y, L[k]);
+        if (y < 0.0) y += L[k];
+      }
+    }
+    xi[k] = y;
   }
-  x[i] = y;
 }
 
 __global__ void philox_normals_kernel(const int64_t *__restrict__ ids, int64_t n, uint64_t step, uint64_t seed,
                                       double *__restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double g[3];
+  float g[3];
   gauss3((uint64_t)ids[i], step, seed, g);
   out[3 * i + 0] = g[0];
   out[3 * i + 1] = g[1];
@@ -184,7 +196,7 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
 
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt) {
   if (c.n > 0)
-    drift_kernel<<<nblk(3 * c.n, 256), 256, 0, c.stream>>>(c.n, x, v, dt, c.box[0], c.box[1], c.box[2],
+    drift_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, x, v, dt, c.box[0], c.box[1], c.box[2],
                                                            c.g.per[0], c.g.per[1], c.g.per[2]);
   return cudaGetLastError();
 }
