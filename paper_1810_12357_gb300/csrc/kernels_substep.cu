@@ -243,52 +243,50 @@ __device__ __forceinline__ float row_atom(const TileArgs &t, const float *tile, 
 // PP = 9: exactly nine index words per atom (18-neighbour FCC shells); PP = 16:
 // any count up to 32 neighbours, t.P words
 template <bool LASER, int PP>
-__global__ void __launch_bounds__(kTileThreads, 2) substep_tile_kernel(const TileArgs t) {
+__global__ void __launch_bounds__(kTileThreads + 32, 2) substep_tile_kernel(const TileArgs t) {
   extern __shared__ float tiles[];
   __shared__ TileDesc desc[3];
-  __shared__ float wmin[kTileThreads / 32], wmax[kTileThreads / 32];
+  __shared__ float wmin[2][kTileThreads / 32], wmax[2][kTileThreads / 32];   // by iteration parity
   int R = blockIdx.x;
   if (R >= t.nrows) return;
   const StepCoef *cf = t.cf;
   const float th = cf->th_ref;
   const int warp = threadIdx.x >> 5;
+  const int aw = kTileThreads / 32;   // warps 0..aw-1 own atoms; warp aw prepares descriptors
   if (warp == 0) make_desc(t, R, &desc[0]);
   if (warp == 1 && R + (int)gridDim.x < t.nrows) make_desc(t, R + gridDim.x, &desc[1]);
   __syncthreads();
   stage_row(t, &desc[0], tiles);
   cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
   int it = 0;
+  // one barrier per row: at the end of an iteration every thread waits for its
+  // copies of the next tile, then the barrier makes them (and the descriptor of
+  // the row after next) visible and frees the consumed buffer for refilling.
   for (; R < t.nrows; R += gridDim.x, ++it) {
     const int dc = it % 3, dn = (it + 1) % 3, dnn = (it + 2) % 3;
     const int buf = it & 1;
     const int Rn = R + gridDim.x;
     if (Rn < t.nrows) stage_row(t, &desc[dn], tiles + (buf ^ 1) * t.tb);
     cp_async_commit();
-    // descriptor of the row after next, by the last warp, ahead of its atoms
-    if (warp == (int)(blockDim.x >> 5) - 1 && Rn + (int)gridDim.x < t.nrows) make_desc(t, Rn + gridDim.x, &desc[dnn]);
+    // descriptor of the row after next, by the warp without atoms
+    if (warp == aw && Rn + (int)gridDim.x < t.nrows) make_desc(t, Rn + gridDim.x, &desc[dnn]);
     const int row_len = desc[dc].row_len, row_s = desc[dc].row_s, sb = desc[dc].self_base;
     const int tier = desc[dc].tier;
     const float *tile = tiles + buf * t.tb;
     float vmin = 3.0e38f, vmax = -3.0e38f;
-    for (int q0 = 0; q0 < row_len; q0 += blockDim.x) {
+    for (int q0 = 0; q0 < row_len; q0 += kTileThreads) {
       const int q = q0 + threadIdx.x;
-      const bool act = q < row_len;
+      const bool act = q < row_len && warp < aw;
       const int32_t s = row_s + (act ? q : 0);
       uint32_t pv[PP];
-      const uint32_t *pp = t.pidx + s;
 #pragma unroll
       for (int m = 0; m < PP; ++m)
-        if (PP != 16 || m < t.P) {
-          pv[m] = act ? __ldg(pp) : 0u;
-          pp += t.n;
-        }
-      const float ui = act ? t.uTl[s] : 0.0f;
-      const float li = act ? t.lo[s] : 0.0f;
-      if (q0 == 0) {
-        cp_async_wait<1>();
-        __syncthreads();
-      }
+        if (PP != 16 || m < t.P) pv[m] = act ? __ldg(t.pidx + (m * t.n + s)) : 0u;
       if (act) {
+        const float ui = t.uTl[s];
+        const float li = t.lo[s];
         const float di = tile[sb + q];
         float h;
         if (tier == 2) h = row_atom<2, LASER, PP>(t, tile, cf, s, di, pv, ui, li, th);
@@ -298,30 +296,26 @@ __global__ void __launch_bounds__(kTileThreads, 2) substep_tile_kernel(const Til
         vmax = fmaxf(vmax, h);
       }
     }
-    if (row_len == 0) {
-      cp_async_wait<1>();
-      __syncthreads();
-    }
     for (int o = 16; o > 0; o >>= 1) {
       vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
       vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-      wmin[warp] = vmin;
-      wmax[warp] = vmax;
+    if ((threadIdx.x & 31) == 0 && warp < aw) {
+      wmin[buf][warp] = vmin;
+      wmax[buf][warp] = vmax;
     }
-    __syncthreads();  // tile consumed; warp ranges and the new descriptor are visible
+    cp_async_wait<0>();
+    __syncthreads();
     if (threadIdx.x == 0) {
-      float a = wmin[0], b = wmax[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        a = fminf(a, wmin[w]);
-        b = fmaxf(b, wmax[w]);
+      float a = wmin[buf][0], b = wmax[buf][0];
+      for (int w = 1; w < aw; ++w) {
+        a = fminf(a, wmin[buf][w]);
+        b = fmaxf(b, wmax[buf][w]);
       }
       t.rmin_out[R] = a;
       t.rmax_out[R] = b;
     }
   }
-  cp_async_wait<0>();
 }
 
 // general single-precision path: one thread per atom, int32 neighbour table,
@@ -477,11 +471,11 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     const size_t shm = sizeof(float) * 2 * (size_t)c.tile_floats;
     const unsigned grid = (unsigned)(c.nrows < c.tile_grid ? c.nrows : c.tile_grid);
     if (P == 9) {
-      if (laser) substep_tile_kernel<true, 9><<<grid, kTileThreads, shm, st>>>(t);
-      else substep_tile_kernel<false, 9><<<grid, kTileThreads, shm, st>>>(t);
+      if (laser) substep_tile_kernel<true, 9><<<grid, kTileThreads + 32, shm, st>>>(t);
+      else substep_tile_kernel<false, 9><<<grid, kTileThreads + 32, shm, st>>>(t);
     } else {
-      if (laser) substep_tile_kernel<true, 16><<<grid, kTileThreads, shm, st>>>(t);
-      else substep_tile_kernel<false, 16><<<grid, kTileThreads, shm, st>>>(t);
+      if (laser) substep_tile_kernel<true, 16><<<grid, kTileThreads + 32, shm, st>>>(t);
+      else substep_tile_kernel<false, 16><<<grid, kTileThreads + 32, shm, st>>>(t);
     }
   } else {
     if (laser)
@@ -506,10 +500,11 @@ cudaError_t tile_setup(int tb, int *blocks_per_sm) {
     if (e != cudaSuccess) return e;
   }
   int b9 = 0, b16 = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b9, substep_tile_kernel<false, 9>, kTileThreads,
-                                                                (size_t)bytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b9, substep_tile_kernel<false, 9>,
+                                                                kTileThreads + 32, (size_t)bytes);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, substep_tile_kernel<true, 16>, kTileThreads, (size_t)bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, substep_tile_kernel<true, 16>, kTileThreads + 32,
+                                                    (size_t)bytes);
   *blocks_per_sm = b9 < b16 ? b9 : b16;
   return e;
 }
