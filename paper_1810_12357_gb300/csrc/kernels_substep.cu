@@ -243,7 +243,7 @@ __device__ __forceinline__ float row_atom(const TileArgs &t, const float *tile, 
 // PP = 9: exactly nine index words per atom (18-neighbour FCC shells); PP = 16:
 // any count up to 32 neighbours, t.P words
 template <bool LASER, int PP>
-__global__ void __launch_bounds__(kTileThreads + 32, 2) substep_tile_kernel(const TileArgs t) {
+__global__ void __launch_bounds__(kTileThreads + 32, 4) substep_tile_kernel(const TileArgs t) {
   extern __shared__ float tiles[];
   __shared__ TileDesc desc[3];
   __shared__ float wmin[2][kTileThreads / 32], wmax[2][kTileThreads / 32];   // by iteration parity
