@@ -65,7 +65,8 @@ struct StepCoef {
 // contiguous range of the sorted order.  Every neighbour of an atom lies in the
 // (at most 9, deduplicated) rows around its own, listed in a fixed order.
 constexpr int kRowNbr = 9;
-constexpr int kTileThreads = 256;
+constexpr int kTileThreads = 256;   // threads that own atoms (plus one descriptor warp)
+constexpr int kTileMinBlocks = 4;
 constexpr int kTileMaxBytes = 200 * 1024;   // two tile buffers must fit in this much shared memory
 
 // Deterministic block-partial reductions.

@@ -207,22 +207,23 @@ __device__ __forceinline__ void make_desc(const TileArgs &t, int R, TileDesc *d)
   }
 }
 
-// warp w (< 9) copies neighbour row w into buf: unaligned head and tail in
-// 4-byte copies, the interior in 16-byte copies
+// warp w copies neighbour rows w, w + nwarps, ... into buf: unaligned head and
+// tail in 4-byte copies, the interior in 16-byte copies
 __device__ __forceinline__ void stage_row(const TileArgs &t, const TileDesc *d, float *buf) {
-  const int w = threadIdx.x >> 5;
-  if (w >= kRowNbr) return;
+  const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int32_t a = d->start[w], len = d->len[w];
-  float *dst = buf + d->off[w];
-  const float *src = t.hin + a;
-  int32_t head = (4 - (a & 3)) & 3;
-  if (head > len) head = len;
-  if (lane < head) cp_async4(dst + lane, src + lane);
-  const int32_t nb = (len - head) >> 2;
-  for (int32_t c = lane; c < nb; c += 32) cp_async16(dst + head + 4 * c, src + head + 4 * c);
-  const int32_t tail0 = head + 4 * nb;
-  if (lane < len - tail0) cp_async4(dst + tail0 + lane, src + tail0 + lane);
+  for (int w = threadIdx.x >> 5; w < kRowNbr; w += nw) {
+    const int32_t a = d->start[w], len = d->len[w];
+    float *dst = buf + d->off[w];
+    const float *src = t.hin + a;
+    int32_t head = (4 - (a & 3)) & 3;
+    if (head > len) head = len;
+    if (lane < head) cp_async4(dst + lane, src + lane);
+    const int32_t nb = (len - head) >> 2;
+    for (int32_t c = lane; c < nb; c += 32) cp_async16(dst + head + 4 * c, src + head + 4 * c);
+    const int32_t tail0 = head + 4 * nb;
+    if (lane < len - tail0) cp_async4(dst + tail0 + lane, src + tail0 + lane);
+  }
 }
 
 template <int TIER, bool LASER, int PP>
@@ -243,7 +244,7 @@ __device__ __forceinline__ float row_atom(const TileArgs &t, const float *tile, 
 // PP = 9: exactly nine index words per atom (18-neighbour FCC shells); PP = 16:
 // any count up to 32 neighbours, t.P words
 template <bool LASER, int PP>
-__global__ void __launch_bounds__(kTileThreads + 32, 4) substep_tile_kernel(const TileArgs t) {
+__global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks) substep_tile_kernel(const TileArgs t) {
   extern __shared__ float tiles[];
   __shared__ TileDesc desc[3];
   __shared__ float wmin[2][kTileThreads / 32], wmax[2][kTileThreads / 32];   // by iteration parity
