@@ -420,8 +420,7 @@ int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *
     double Kw = 0.5 * m * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * mvv;
     double s = (Kw > 0.0) ? sqrt(target / Kw) : 0.0;
     for (int k = 0; k < 3; ++k) vi[k] = w[k] * s;
-    double K1 = 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * mvv;
-    dKE[i] = K1 - K0;
+    dKE[i] = target - K0;   /* the kinetic energy after scaling is the target */
     if (target == 0.0) T[i] += (A[i] - dKE[i]) / VC;
     A[i] = 0.0;
   }

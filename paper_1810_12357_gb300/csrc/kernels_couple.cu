@@ -97,14 +97,11 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   }
   const double Kw = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
   const double sc = Kw > 0.0 ? sqrt(target / Kw) : 0.0;
-  w0 *= sc;
-  w1 *= sc;
-  w2 *= sc;
-  vi[0] = w0;
-  vi[1] = w1;
-  vi[2] = w2;
-  const double K1 = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
-  const double d = K1 - K0;
+  vi[0] = w0 * sc;
+  vi[1] = w1 * sc;
+  vi[2] = w2 * sc;
+  // the new kinetic energy is the target up to the rounding of the scaling
+  const double d = target - K0;
   dKE[s] = d;
   if (target == 0.0) T[s] += (Ai - d) * inv_VC;
 }
@@ -140,6 +137,13 @@ __global__ void sum_final_accumulate(int nb, const double *__restrict__ part, do
   if (threadIdx.x == 0) *acc += r;
 }
 
+// sign and ordering tests of doubles on the integer pipes: for y >= 0 the bit
+// patterns order like the values
+__device__ __forceinline__ bool neg_bits(double y) { return __double_as_longlong(y) < 0; }
+__device__ __forceinline__ bool ge_bits(double y, double L) {   // y >= L for y >= +0, L > 0
+  return __double_as_longlong(y) >= __double_as_longlong(L);
+}
+
 __global__ void drift_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ v, double dt,
                              double L0, double L1, double L2, int p0, int p1, int p2) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -154,9 +158,9 @@ __global__ void drift_kernel(int64_t n, double *__restrict__ x, const double *__
     double y = __dadd_rn(xi[k], __dmul_rn(vi[k], dt));
     if (per[k]) {
       // one period at most per step; the same result as a floored modulo
-      if (y < 0.0) y += L[k];
-      else if (y >= L[k]) y -= L[k];
-      if (y < 0.0 || y > L[k]) {
+      if (neg_bits(y) && y != 0.0) y += L[k];
+      else if (ge_bits(y, L[k])) y -= L[k];
+      if ((neg_bits(y) && y != 0.0) || (!neg_bits(y) && __double_as_longlong(y) > __double_as_longlong(L[k]))) {
         y = fmod(y, L[k]);
         if (y < 0.0) y += L[k];
       }
