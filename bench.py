@@ -248,7 +248,7 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "substep_f32_kernel", "bytes_per_atom_substep": B_ALG,
+                     "kernel": "substep_tile_kernel", "bytes_per_atom_substep": B_ALG,
                      "peak_kind": kind, "substep_ms": sub_launch_ms},
         "clocks": clocks,
         "energy_drift": e["drift"],
@@ -261,13 +261,16 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
 
 
 def _traffic_from_profile(n):
-    """DRAM bytes per substep launch from the committed ncu summary, scaled to n atoms."""
-    path = os.path.join(ROOT, "profiles", "substep_f32_track.json")
+    """DRAM bytes per substep launch from the committed ncu summary of the
+    current substep kernel (captured on a smaller track; scales with atoms)."""
+    path = os.path.join(ROOT, "profiles", "substep_tile_track_2M.md")
     try:
-        d = json.load(open(path))
-        return d["dram_bytes_per_launch"] * n / d["n_atoms"]
+        for line in open(path):
+            if line.startswith("| traffic_bytes_per_atom_substep |"):
+                return float(line.split("|")[2]) * n
     except Exception:
-        return None
+        pass
+    return None
 
 
 # ------------------------------------------------------------ CPU oracle arm
