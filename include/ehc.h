@@ -195,6 +195,24 @@ int ehc_philox_normals(const int64_t *ids_dev, int64_t n, uint64_t md_step, uint
 int ehc_save(ehc_ctx *c, const char *path);
 int ehc_load(ehc_ctx *c, const char *path);
 
+/* Electronic energy of a set of temperatures without allocating anything: the
+ * paper has no counterpart; this serves callers that cannot call cudaMalloc at
+ * the time they need the number (a callback that runs during CUDA graph capture,
+ * an application whose device memory pool is fixed at start-up, a loop that must
+ * not take the allocator's locks).  Te_dev [n] (device, any order); writes to
+ * out_dev (device, 3 doubles): sum of T [K], max T [K] and
+ * sum_i V_atom int_0^{T_i} C_e dT [eV] with C_e = min(gamma_Ce T, Ce_cap_kB k_B / V_atom)
+ * (Ce_cap_kB <= 0: no cap) -- the E_e0 that ehc_set_te computes.  Asynchronous on
+ * `stream`.  Scratch: a fixed 128 KB device array in the library, held by every
+ * GPU that loads it until the process exits; n may not exceed 16,777,216
+ * (EHC_E_INVAL beyond).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array and every call
+ * overwrites the part it uses, so calls that overlap on the GPU (different
+ * streams, or host threads) race; serialise them. */
+int ehc_electron_energy_noalloc(const double *Te_dev, int64_t n, double gamma_Ce, double Ce_cap_kB,
+                                double vatom_A3, double *out_dev, void *stream);
+
 void ehc_destroy(ehc_ctx *c);
 const char *ehc_strerror(int code);
 

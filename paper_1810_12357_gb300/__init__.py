@@ -84,6 +84,8 @@ _SIGS = {
     "ehc_philox_normals": (_I, [_P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, _P, _P]),
     "ehc_save": (_I, [_P, ctypes.c_char_p]),
     "ehc_load": (_I, [_P, ctypes.c_char_p]),
+    "ehc_electron_energy_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _P, _P]),
     "ehc_destroy": (None, [_P]),
     "ehc_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -283,4 +285,17 @@ def philox_normals(ids, md_step: int, seed: int):
     out = torch.empty((ids_t.shape[0], 3), dtype=torch.float64, device="cuda")
     _check(L.ehc_philox_normals(_ptr(ids_t), ids_t.shape[0], int(md_step), int(seed), _ptr(out), _stream()),
            "ehc_philox_normals")
+    return out
+
+
+def electron_energy_noalloc(Te, gamma_Ce: float, Ce_cap_kB: float, vatom_A3: float, out=None):
+    """ehc_electron_energy_noalloc: (sum T, max T, E_e0 [eV]) of device temperatures
+    without any device allocation by the library.  `out` (3 float64 on the device)
+    is the caller's; it is created here only when not given."""
+    import torch
+    L = load_library()
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=Te.device)
+    _check(L.ehc_electron_energy_noalloc(_ptr(Te), int(Te.numel()), float(gamma_Ce), float(Ce_cap_kB),
+                                         float(vatom_A3), _ptr(out), _stream()), "ehc_electron_energy_noalloc")
     return out
