@@ -55,7 +55,8 @@ void free_all(Ctx &c) {
                  c.perm, c.inv_perm[0], c.inv_perm[1], c.q_s, c.v_s, c.nbr, c.cnt, c.T[0], c.T[1],
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
-                 c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d};
+                 c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
+                 c.work};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -193,6 +194,33 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   return EHC_OK;
 }
 
+// refresh the device argument table of the row-tile kernel (P changes per build)
+cudaError_t upload_reps(Ctx &c) {
+  RepArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  ra.n = (int32_t)c.n;
+  ra.ncx = c.g.nc[0];
+  int32_t P = (c.n_max + 1) / 2;
+  if (P > (c.W + 1) / 2) P = (c.W + 1) / 2;
+  ra.P = P;
+  ra.nrows = (int32_t)c.nrows;
+  ra.start = c.cell_start;
+  ra.row_nbr = c.row_nbr;
+  ra.pidx = c.pidx;
+  ra.dmir[0] = c.dmir[0];
+  ra.dmir[1] = c.dmir[1];
+  ra.lo = c.dlo;
+  ra.A = c.A;
+  ra.uTl = c.uTl;
+  ra.srcw = c.srcw;
+  ra.pulse_f = c.pulse_f;
+  ra.rrange[0] = c.rrange[0];
+  ra.rrange[1] = c.rrange[1];
+  ra.cf = c.coef;
+  ra.err = c.err;
+  return cudaMemcpy(c.reps, &ra, sizeof(ra), cudaMemcpyHostToDevice);
+}
+
 }  // namespace
 
 extern "C" {
@@ -318,6 +346,8 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(cudaMallocHost((void **)&c.pulse_f_host, sizeof(float) * c.max_sub));
   A(dalloc(&c.rrange[0], 2 * c.nrows));
   A(dalloc(&c.rrange[1], 2 * c.nrows));
+  A(dalloc(&c.reps, 1));
+  A(dalloc(&c.work, c.nrows));
   A(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, 0));
   A(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   A(cudaEventCreateWithFlags(&c.pulse_ev, cudaEventDisableTiming));
@@ -340,6 +370,12 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 4, c.stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c.row_nbr, rt.data(), sizeof(int32_t) * rt.size(), cudaMemcpyHostToDevice, c.stream);
+  std::vector<int2> wl((size_t)c.nrows);
+  for (int64_t R = 0; R < c.nrows; ++R) wl[(size_t)R] = make_int2(0, (int)R);
+  c.nwork = (int32_t)c.nrows;
+  if (e == cudaSuccess && c.nrows > 0)
+    e = cudaMemcpyAsync(c.work, wl.data(), sizeof(int2) * wl.size(), cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = upload_reps(c);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.abuf[0], 0, sizeof(double) * (n > 0 ? n : 1), c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.srcw, 0, sizeof(float) * (n > 0 ? n : 1), c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
@@ -464,6 +500,7 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   cf.Tmax_f = (float)c.p.Tmax_K;
   cf.pad[0] = cf.pad[1] = cf.pad[2] = 0.f;
   CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
+  CK(upload_reps(c));
   c.built = true;
   return err_code(c.dev_err);
 }

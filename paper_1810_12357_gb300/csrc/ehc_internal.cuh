@@ -69,6 +69,22 @@ constexpr int kTileThreads = 256;   // threads that own atoms (plus one descript
 constexpr int kTileMinBlocks = 4;
 constexpr int kTileMaxBytes = 200 * 1024;   // two tile buffers must fit in this much shared memory
 
+// Arguments of one system for the row-tile substep kernel (device table; one
+// entry for a single system, one per replica for a batch).  Pointers stay
+// fixed for the life of a context; P is refreshed after every neighbour build.
+struct RepArgs {
+  int32_t n, ncx, P, nrows;
+  const int32_t *start, *row_nbr;
+  const uint32_t *pidx;
+  float *dmir[2];
+  float *lo;
+  double *A;
+  const float *uTl, *srcw, *pulse_f;
+  float *rrange[2];
+  const StepCoef *cf;
+  int32_t *err;
+};
+
 // Deterministic block-partial reductions.
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 constexpr int kRedThreads = 256;
@@ -156,6 +172,9 @@ struct Ctx {
   int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)
   int32_t tile_grid = 0;         // resident CTAs of the row-tile kernel
   int32_t num_sms = 0;
+  RepArgs *reps = nullptr;       // device table of the row-tile kernel (this system only)
+  int2 *work = nullptr;          // (system, row) work list of the row-tile kernel
+  int32_t nwork = 0;
   float *rrange[2] = {nullptr, nullptr};  // [min of every row | max of every row] of each mirror
   StepCoef *coef = nullptr;      // device
   StepCoef *coef_host = nullptr; // pinned

@@ -471,9 +471,8 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
         laser ? c.depth_orig : nullptr, c.srcw, c.srcw_d, laser ? 1.0 / c.p.laser_lp_A : 0.0);
   c.cur_inv = nxt;
   c.tcur = tn;
-  double *t = c.A;
-  c.A = c.A_tmp;
-  c.A_tmp = t;
+  // A keeps its address (captured substep graphs and the tile argument table hold it)
+  cudaMemcpyAsync(c.A, c.A_tmp, sizeof(double) * (c.n > 0 ? c.n : 1), cudaMemcpyDeviceToDevice, c.stream);
   c.parity = 0;
   return cudaGetLastError();
 }

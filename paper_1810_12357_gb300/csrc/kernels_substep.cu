@@ -134,47 +134,46 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-struct TileArgs {
-  int32_t n, ncx, P, nrows, tb;       // tb: floats per tile buffer
-  const int32_t *start, *row_nbr;
-  const uint32_t *pidx;
-  const float *hin;
-  float *hout, *lo;
-  double *A;
-  const float *uTl, *srcw, *pulse_f;
-  const float *rmin_in, *rmax_in;     // value range of every row of hin
-  float *rmin_out, *rmax_out;         // value range of every row of hout
-  int k;
-  const StepCoef *cf;
-  int32_t *err;
-};
-
 __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// Tile descriptor of the row tile around row R.  Neighbour row r is placed at
-// tile offset off[r], congruent to its first global index modulo 4, so that its
-// interior moves in 16-byte copies.
+// Tile descriptor of the row tile around row R of one system.  Neighbour row r
+// is placed at tile offset off[r], congruent to its first global index modulo
+// 4, so that its interior moves in 16-byte copies.  The system's arguments are
+// copied next to it, so every warp reads them from shared memory.
 struct TileDesc {
   int32_t start[kRowNbr], len[kRowNbr], off[kRowNbr];
-  int32_t self_base, row_s, row_len, tier;
+  int32_t self_base, row_s, row_len, tier, row;
+  int32_t pad[3];
+  RepArgs ra;
 };
 
 // computed by one warp: lane r < 9 handles neighbour row r
-__device__ __forceinline__ void make_desc(const TileArgs &t, int R, TileDesc *d) {
+__device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2 item, int parity, TileDesc *d) {
   const int lane = threadIdx.x & 31;
+  // copy the system's arguments (whole 8-byte words) into the descriptor
+  static_assert(sizeof(RepArgs) % 8 == 0, "RepArgs must be a whole number of 8-byte words");
+  const uint64_t *src = reinterpret_cast<const uint64_t *>(reps + item.x);
+  uint64_t *dst = reinterpret_cast<uint64_t *>(&d->ra);
+  for (int w = lane; w < (int)(sizeof(RepArgs) / 8); w += 32) dst[w] = __ldg(src + w);
+  __syncwarp();
+  const int R = item.y;
+  const int32_t ncx = d->ra.ncx;
+  const int32_t *row_nbr = d->ra.row_nbr;
+  const int32_t *start = d->ra.start;
+  const float *rr = d->ra.rrange[parity];
+  const int32_t nrows = d->ra.nrows;
   int32_t R2 = -1, a = 0, len = 0;
   float mn = 3.0e38f, mx = -3.0e38f;
   if (lane < kRowNbr) {
-    R2 = __ldg(t.row_nbr + (int64_t)R * kRowNbr + lane);
+    R2 = __ldg(row_nbr + (int64_t)R * kRowNbr + lane);
     if (R2 >= 0) {
-      a = __ldg(t.start + (int64_t)R2 * t.ncx);
-      len = __ldg(t.start + (int64_t)R2 * t.ncx + t.ncx) - a;
-      mn = t.rmin_in[R2];
-      mx = t.rmax_in[R2];
+      a = __ldg(start + (int64_t)R2 * ncx);
+      len = __ldg(start + (int64_t)R2 * ncx + ncx) - a;
+      mn = rr[R2];
+      mx = rr[nrows + R2];
     }
   }
   // aligned placement, sequential over the 9 rows (same rule as the neighbour build)
@@ -202,20 +201,21 @@ __device__ __forceinline__ void make_desc(const TileArgs &t, int R, TileDesc *d)
     d->self_base = off;
     d->row_s = a;
     d->row_len = len;
+    d->row = R;
     const float spread = mx - mn;
     d->tier = spread < 0.02f ? 2 : (spread < 0.12f ? 1 : 0);
   }
 }
 
-// warp w copies neighbour rows w, w + nwarps, ... into buf: unaligned head and
-// tail in 4-byte copies, the interior in 16-byte copies
-__device__ __forceinline__ void stage_row(const TileArgs &t, const TileDesc *d, float *buf) {
+// warp w copies neighbour rows w, w + nwarps, ... of hin into buf: unaligned
+// head and tail in 4-byte copies, the interior in 16-byte copies
+__device__ __forceinline__ void stage_row(const TileDesc *d, const float *hin, float *buf) {
   const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31;
   for (int w = threadIdx.x >> 5; w < kRowNbr; w += nw) {
     const int32_t a = d->start[w], len = d->len[w];
     float *dst = buf + d->off[w];
-    const float *src = t.hin + a;
+    const float *src = hin + a;
     int32_t head = (4 - (a & 3)) & 3;
     if (head > len) head = len;
     if (lane < head) cp_async4(dst + lane, src + lane);
@@ -227,72 +227,80 @@ __device__ __forceinline__ void stage_row(const TileArgs &t, const TileDesc *d, 
 }
 
 template <int TIER, bool LASER, int PP>
-__device__ __forceinline__ float row_atom(const TileArgs &t, const float *tile, const StepCoef *cf, int32_t s,
-                                          float di, const uint32_t *pv, float ui, float li, float th) {
+__device__ __forceinline__ float row_atom(const RepArgs &ra, int parity, int k, const float *tile, int32_t s,
+                                          float di, const uint32_t *pv, float ui, float li) {
+  const StepCoef *cf = ra.cf;
+  const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
   float F = 0.0f;
 #pragma unroll
   for (int m = 0; m < PP; ++m)
-    if (PP != 16 || m < t.P) {
+    if (PP != 16 || m < ra.P) {
       F = pair_acc<TIER>(F, di, tile[pv[m] & 0xffffu], th, ai, m2ai);
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
-  return update_atom<LASER>(s, di, li, ui, F, cf, t.hout, t.lo, t.A, t.srcw, t.pulse_f, t.k, t.err);
+  return update_atom<LASER>(s, di, li, ui, F, cf, ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, k,
+                            ra.err);
 }
 
-// PP = 9: exactly nine index words per atom (18-neighbour FCC shells); PP = 16:
-// any count up to 32 neighbours, t.P words
+// Persistent row-tile kernel over a work list of (system, row) items: each CTA
+// walks items blockIdx.x, +gridDim.x, ... and double-buffers the tiles: the
+// next item's tile is copied (cp.async) while the current one is computed.
+// PP = 9: exactly nine index words per atom (18-neighbour FCC shells) in every
+// system; PP = 16: any count up to 32 neighbours, ra.P words.
 template <bool LASER, int PP>
-__global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks) substep_tile_kernel(const TileArgs t) {
+__global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
+    substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
+                        int parity, int k) {
   extern __shared__ float tiles[];
   __shared__ TileDesc desc[3];
   __shared__ float wmin[2][kTileThreads / 32], wmax[2][kTileThreads / 32];   // by iteration parity
-  int R = blockIdx.x;
-  if (R >= t.nrows) return;
-  const StepCoef *cf = t.cf;
-  const float th = cf->th_ref;
+  int it_item = blockIdx.x;
+  if (it_item >= nwork) return;
   const int warp = threadIdx.x >> 5;
   const int aw = kTileThreads / 32;   // warps 0..aw-1 own atoms; warp aw prepares descriptors
-  if (warp == 0) make_desc(t, R, &desc[0]);
-  if (warp == 1 && R + (int)gridDim.x < t.nrows) make_desc(t, R + gridDim.x, &desc[1]);
+  if (warp == 0) make_desc(reps, work[it_item], parity, &desc[0]);
+  if (warp == 1 && it_item + (int)gridDim.x < nwork) make_desc(reps, work[it_item + gridDim.x], parity, &desc[1]);
   __syncthreads();
-  stage_row(t, &desc[0], tiles);
+  stage_row(&desc[0], desc[0].ra.dmir[parity], tiles);
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
   int it = 0;
-  // one barrier per row: at the end of an iteration every thread waits for its
+  // one barrier per item: at the end of an iteration every thread waits for its
   // copies of the next tile, then the barrier makes them (and the descriptor of
-  // the row after next) visible and frees the consumed buffer for refilling.
-  for (; R < t.nrows; R += gridDim.x, ++it) {
+  // the item after next) visible and frees the consumed buffer for refilling.
+  for (; it_item < nwork; it_item += gridDim.x, ++it) {
     const int dc = it % 3, dn = (it + 1) % 3, dnn = (it + 2) % 3;
     const int buf = it & 1;
-    const int Rn = R + gridDim.x;
-    if (Rn < t.nrows) stage_row(t, &desc[dn], tiles + (buf ^ 1) * t.tb);
+    const int nxt = it_item + gridDim.x;
+    if (nxt < nwork) stage_row(&desc[dn], desc[dn].ra.dmir[parity], tiles + (buf ^ 1) * tb);
     cp_async_commit();
-    // descriptor of the row after next, by the warp without atoms
-    if (warp == aw && Rn + (int)gridDim.x < t.nrows) make_desc(t, Rn + gridDim.x, &desc[dnn]);
-    const int row_len = desc[dc].row_len, row_s = desc[dc].row_s, sb = desc[dc].self_base;
-    const int tier = desc[dc].tier;
-    const float *tile = tiles + buf * t.tb;
+    if (warp == aw && nxt + (int)gridDim.x < nwork) make_desc(reps, work[nxt + gridDim.x], parity, &desc[dnn]);
+    const TileDesc &D = desc[dc];
+    const int row_len = D.row_len, row_s = D.row_s, sb = D.self_base;
+    const int tier = D.tier;
+    const float *tile = tiles + buf * tb;
     float vmin = 3.0e38f, vmax = -3.0e38f;
     for (int q0 = 0; q0 < row_len; q0 += kTileThreads) {
       const int q = q0 + threadIdx.x;
       const bool act = q < row_len && warp < aw;
       const int32_t s = row_s + (act ? q : 0);
+      const int32_t n = D.ra.n;
+      const uint32_t *pidx = D.ra.pidx;
       uint32_t pv[PP];
 #pragma unroll
       for (int m = 0; m < PP; ++m)
-        if (PP != 16 || m < t.P) pv[m] = act ? __ldg(t.pidx + (m * t.n + s)) : 0u;
+        if (PP != 16 || m < D.ra.P) pv[m] = act ? __ldg(pidx + (m * n + s)) : 0u;
       if (act) {
-        const float ui = t.uTl[s];
-        const float li = t.lo[s];
+        const float ui = D.ra.uTl[s];
+        const float li = D.ra.lo[s];
         const float di = tile[sb + q];
         float h;
-        if (tier == 2) h = row_atom<2, LASER, PP>(t, tile, cf, s, di, pv, ui, li, th);
-        else if (tier == 1) h = row_atom<1, LASER, PP>(t, tile, cf, s, di, pv, ui, li, th);
-        else h = row_atom<0, LASER, PP>(t, tile, cf, s, di, pv, ui, li, th);
+        if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+        else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+        else h = row_atom<0, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
         vmin = fminf(vmin, h);
         vmax = fmaxf(vmax, h);
       }
@@ -313,8 +321,9 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks) substep_til
         a = fminf(a, wmin[buf][w]);
         b = fmaxf(b, wmax[buf][w]);
       }
-      t.rmin_out[R] = a;
-      t.rmax_out[R] = b;
+      float *rr = D.ra.rrange[parity ^ 1];
+      rr[D.row] = a;
+      rr[D.ra.nrows + D.row] = b;
     }
   }
 }
@@ -412,7 +421,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // the row-tile kernel applies when two tiles fit in shared memory and the table
 // holds at most 32 neighbours per atom
 bool tile_path(const Ctx &c) {
-  return c.p.flux_prec == 0 && c.W <= 32 && c.nrows > 0 && c.staged_max <= c.tile_floats;
+  return c.p.flux_prec == 0 && c.W <= 32 && c.nwork > 0 && c.staged_max <= c.tile_floats;
 }
 
 cudaError_t launch_split(Ctx &c, cudaStream_t st) {
@@ -444,39 +453,15 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
       substep_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
                                                               c.pulse, k, c.coef, c.err);
   } else if (tile_path(c)) {
-    int32_t P = (c.n_max + 1) / 2;
-    if (P > (c.W + 1) / 2) P = (c.W + 1) / 2;
-    TileArgs t;
-    t.n = n;
-    t.ncx = c.g.nc[0];
-    t.P = P;
-    t.nrows = (int32_t)c.nrows;
-    t.tb = c.tile_floats;
-    t.start = c.cell_start;
-    t.row_nbr = c.row_nbr;
-    t.pidx = c.pidx;
-    t.hin = c.dmir[parity];
-    t.hout = c.dmir[parity ^ 1];
-    t.lo = c.dlo;
-    t.A = c.A;
-    t.uTl = c.uTl;
-    t.srcw = c.srcw;
-    t.pulse_f = c.pulse_f;
-    t.rmin_in = c.rrange[parity];
-    t.rmax_in = c.rrange[parity] + c.nrows;
-    t.rmin_out = c.rrange[parity ^ 1];
-    t.rmax_out = c.rrange[parity ^ 1] + c.nrows;
-    t.k = k;
-    t.cf = c.coef;
-    t.err = c.err;
+    const int32_t P = (c.n_max + 1) / 2;
     const size_t shm = sizeof(float) * 2 * (size_t)c.tile_floats;
-    const unsigned grid = (unsigned)(c.nrows < c.tile_grid ? c.nrows : c.tile_grid);
+    const unsigned grid = (unsigned)(c.nwork < c.tile_grid ? c.nwork : c.tile_grid);
     if (P == 9) {
-      if (laser) substep_tile_kernel<true, 9><<<grid, kTileThreads + 32, shm, st>>>(t);
-      else substep_tile_kernel<false, 9><<<grid, kTileThreads + 32, shm, st>>>(t);
+      if (laser) substep_tile_kernel<true, 9><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
+      else substep_tile_kernel<false, 9><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
     } else {
-      if (laser) substep_tile_kernel<true, 16><<<grid, kTileThreads + 32, shm, st>>>(t);
-      else substep_tile_kernel<false, 16><<<grid, kTileThreads + 32, shm, st>>>(t);
+      if (laser) substep_tile_kernel<true, 16><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
+      else substep_tile_kernel<false, 16><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
     }
   } else {
     if (laser)
