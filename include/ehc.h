@@ -216,6 +216,36 @@ int ehc_electron_energy_noalloc(const double *Te_dev, int64_t n, double gamma_Ce
 void ehc_destroy(ehc_ctx *c);
 const char *ehc_strerror(int code);
 
+/* ---- Batched replicas --------------------------------------------------------
+ * Independent systems (e.g. repeated cascades of different sizes, Sec. 4) that
+ * share one parameter set are advanced together: each replica keeps its own
+ * neighbour list, per-step C_e / kappa_e / K and energy ledger exactly as a
+ * single context would, and the substeps of all replicas run as one launch per
+ * substep over a work list of (replica, row) tiles, replayed from a CUDA graph.
+ * Per-atom arrays are the replicas' arrays concatenated in replica order
+ * (positions and velocities [sum n, 3]); ehc_batch_size gives the offsets.
+ * Single-precision flux only (flux_prec 0), no laser source, one atom type.
+ * The results of a replica are those a single context gives for it. */
+typedef struct ehc_batch ehc_batch;
+
+/* n_rep replicas with n_atoms_host[r] atoms in boxes boxes_host[3 r .. 3 r + 2]
+ * (host memory), all with the same periodic flags and the one atom mass. */
+int ehc_batch_create(const ehc_params *p, int32_t n_rep, const int64_t *n_atoms_host,
+                     const double *boxes_host, const int32_t periodic[3], const double *mass_amu_host,
+                     void *stream, ehc_batch **out);
+/* total atom count and the first atom of every replica (offsets_host [n_rep], may be NULL) */
+int ehc_batch_size(const ehc_batch *b, int64_t *n_total, int64_t *offsets_host);
+int ehc_batch_set_te(ehc_batch *b, const double *Te_dev);
+/* one neighbour build for every replica; synchronises the stream once */
+int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v_dev);
+int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs);
+int ehc_batch_couple(ehc_batch *b, double *v_dev, double dt_md_fs);
+int ehc_batch_drift(ehc_batch *b, double *x_dev, const double *v_dev, double dt_fs);
+int ehc_batch_get_te(ehc_batch *b, double *Te_dev_out);
+/* ledger of replica r */
+int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out);
+void ehc_batch_destroy(ehc_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

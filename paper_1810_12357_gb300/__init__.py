@@ -86,6 +86,17 @@ _SIGS = {
     "ehc_load": (_I, [_P, ctypes.c_char_p]),
     "ehc_electron_energy_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, _P, _P]),
+    "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
+                              ctypes.POINTER(_P)]),
+    "ehc_batch_size": (_I, [_P, _P, _P]),
+    "ehc_batch_set_te": (_I, [_P, _P]),
+    "ehc_batch_build_neighbors": (_I, [_P, _P, _P]),
+    "ehc_batch_substep": (_I, [_P, ctypes.c_int32, ctypes.c_double]),
+    "ehc_batch_couple": (_I, [_P, _P, ctypes.c_double]),
+    "ehc_batch_drift": (_I, [_P, _P, _P, ctypes.c_double]),
+    "ehc_batch_get_te": (_I, [_P, _P]),
+    "ehc_batch_energy": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ehc_energy_t)]),
+    "ehc_batch_destroy": (None, [_P]),
     "ehc_destroy": (None, [_P]),
     "ehc_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -299,3 +310,70 @@ def electron_energy_noalloc(Te, gamma_Ce: float, Ce_cap_kB: float, vatom_A3: flo
     _check(L.ehc_electron_energy_noalloc(_ptr(Te), int(Te.numel()), float(gamma_Ce), float(Ce_cap_kB),
                                          float(vatom_A3), _ptr(out), _stream()), "ehc_electron_energy_noalloc")
     return out
+
+
+class EhcBatch:
+    """Independent replicas advanced together (ehc_batch_*).  `systems` is a
+    list of inputs.System sharing one parameter set; per-atom arrays are the
+    replicas' arrays concatenated in order (see `offsets`)."""
+
+    def __init__(self, params: dict, systems):
+        import torch
+        L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libehc needs a CUDA device; there is no CPU path")
+        self._lib = L
+        self.params = dict(params)
+        self._p = make_params(params)
+        n = np.ascontiguousarray([s.n for s in systems], dtype=np.int64)
+        boxes = np.ascontiguousarray(np.concatenate([s.box for s in systems]), dtype=np.float64)
+        per = np.ascontiguousarray(systems[0].periodic, dtype=np.int32)
+        m = np.ascontiguousarray(systems[0].mass_amu[:1], dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(L.ehc_batch_create(ctypes.byref(self._p), len(systems), n.ctypes.data_as(_P),
+                                  boxes.ctypes.data_as(_P), per.ctypes.data_as(_P), m.ctypes.data_as(_P),
+                                  _stream(), ctypes.byref(h)), "ehc_batch_create")
+        self._h = h
+        self.n_rep = len(systems)
+        tot = ctypes.c_int64()
+        off = np.zeros(self.n_rep, dtype=np.int64)
+        _check(L.ehc_batch_size(h, ctypes.byref(tot), off.ctypes.data_as(_P)), "ehc_batch_size")
+        self.n = int(tot.value)
+        self.offsets = off
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.ehc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_te(self, Te):
+        _check(self._lib.ehc_batch_set_te(self._h, _ptr(Te)), "ehc_batch_set_te")
+
+    def build_neighbors(self, x, v):
+        _check(self._lib.ehc_batch_build_neighbors(self._h, _ptr(x), _ptr(v)), "ehc_batch_build_neighbors")
+
+    def substep(self, n_sub: int, t_fs: float = 0.0):
+        _check(self._lib.ehc_batch_substep(self._h, int(n_sub), float(t_fs)), "ehc_batch_substep")
+
+    def couple(self, v, dt_md_fs: float):
+        _check(self._lib.ehc_batch_couple(self._h, _ptr(v), float(dt_md_fs)), "ehc_batch_couple")
+
+    def drift(self, x, v, dt_fs: float):
+        _check(self._lib.ehc_batch_drift(self._h, _ptr(x), _ptr(v), float(dt_fs)), "ehc_batch_drift")
+
+    def get_te(self):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(self._lib.ehc_batch_get_te(self._h, _ptr(out)), "ehc_batch_get_te")
+        return out
+
+    def energy(self, r: int) -> dict:
+        e = ehc_energy_t()
+        _check(self._lib.ehc_batch_energy(self._h, int(r), ctypes.byref(e)), "ehc_batch_energy")
+        return {f: getattr(e, f) for f, _ in ehc_energy_t._fields_}

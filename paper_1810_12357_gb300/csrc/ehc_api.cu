@@ -194,8 +194,16 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   return EHC_OK;
 }
 
+// the row-tile kernel's arguments of one system
+RepArgs rep_args(const Ctx &c);
+
 // refresh the device argument table of the row-tile kernel (P changes per build)
 cudaError_t upload_reps(Ctx &c) {
+  const RepArgs ra = rep_args(c);
+  return cudaMemcpy(c.reps, &ra, sizeof(ra), cudaMemcpyHostToDevice);
+}
+
+RepArgs rep_args(const Ctx &c) {
   RepArgs ra;
   std::memset(&ra, 0, sizeof(ra));
   ra.n = (int32_t)c.n;
@@ -218,7 +226,7 @@ cudaError_t upload_reps(Ctx &c) {
   ra.rrange[1] = c.rrange[1];
   ra.cf = c.coef;
   ra.err = c.err;
-  return cudaMemcpy(c.reps, &ra, sizeof(ra), cudaMemcpyHostToDevice);
+  return ra;
 }
 
 }  // namespace
@@ -428,9 +436,13 @@ int ehc_set_depth(ehc_ctx *h, const double *depth_dev) {
   return EHC_OK;
 }
 
-int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
-  if (!h) return EHC_E_INVAL;
-  Ctx &c = h->c;
+}  // extern "C"
+
+namespace {
+
+// first half of a neighbour build: queue every kernel and the copies of the
+// per-step scalars to pinned host memory (no synchronisation)
+int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev) {
   if (!c.have_te) return EHC_E_STATE;
   if (c.n > 0 && (!x_dev || !v_dev)) return EHC_E_INVAL;
   int r0 = ensure_t(c);
@@ -443,14 +455,21 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   CK(launch_neighbors(c));
   CK(launch_lattice_temperature(c));
   CK(launch_globals(c));
-  int r = readback(c);
-  if (r) return r;
+  CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c.stream));
+  return EHC_OK;
+}
+
+// second half, after the stream has been synchronised: per-step scalars (Sec. 2
+// means, C_e, kappa_e, Eq. Kij), ledger, stability, coefficient upload
+int build_finish(Ctx &c, bool own_tiles) {
   int32_t w[4];
   std::memcpy(w, c.scal_host + 16, sizeof(w));
+  c.dev_err = w[0];
   c.n_max = w[1];
   c.staged_max = w[2];
   // size the row tiles with headroom for atoms drifting between cells
-  if (c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
+  if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
     const int32_t tb = ((c.staged_max + c.staged_max / 4 + 64 + 255) / 256) * 256;
     int bps = 0;
     if ((int64_t)tb * 2 * (int64_t)sizeof(float) <= kTileMaxBytes && tile_setup(tb, &bps) == cudaSuccess && bps > 0) {
@@ -504,6 +523,20 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
   c.built = true;
   return err_code(c.dev_err);
 }
+
+}  // namespace
+
+extern "C" {
+
+int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
+  if (!h) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  int r = build_enqueue(c, x_dev, v_dev);
+  if (r) return r;
+  CK(cudaStreamSynchronize(c.stream));
+  return build_finish(c, true);
+}
+
 
 int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
   if (!h || n_sub < 0) return EHC_E_INVAL;
@@ -776,6 +809,238 @@ int ehc_load(ehc_ctx *h, const char *path) {
   c.ff_valid = false;
   c.t_stale = false;
   return EHC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched replicas: independent systems advanced together.  Every replica keeps
+// its own context (neighbour list, coefficients, ledger); the substeps of all
+// replicas run as one launch of the row-tile kernel per substep over a work list
+// of (replica, row) items, replayed from a CUDA graph.
+
+struct ehc_batch {
+  std::vector<ehc_ctx *> rep;
+  std::vector<int64_t> off;      // first atom of each replica in the concatenated arrays
+  int64_t n_total = 0;
+  ehc_params p;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  RepArgs *reps_dev = nullptr;
+  int2 *work = nullptr;
+  int32_t nwork = 0, tile_floats = 0, tile_grid = 0, num_sms = 0;
+  int parity = 0;
+  struct G {
+    int n_sub, parity, pairs, tile;
+    cudaGraphExec_t exec;
+  };
+  std::vector<G> graphs;
+};
+
+namespace {
+
+int batch_pairs(const ehc_batch &b) {
+  int pairs = 9;
+  for (auto *h : b.rep) {
+    const int P = (h->c.n_max + 1) / 2;
+    if (P != 9) pairs = 16;
+  }
+  return pairs;
+}
+
+bool batch_tile_ok(const ehc_batch &b) {
+  if (b.tile_floats <= 0 || b.nwork <= 0) return false;
+  for (auto *h : b.rep)
+    if (h->c.W > 32 || h->c.staged_max > b.tile_floats || h->c.p.flux_prec != 0) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ehc_batch_create(const ehc_params *p, int32_t n_rep, const int64_t *n_atoms_host, const double *boxes_host,
+                     const int32_t periodic[3], const double *mass_amu_host, void *stream, ehc_batch **out) {
+  if (!p || n_rep <= 0 || !n_atoms_host || !boxes_host || !periodic || !mass_amu_host || !out) return EHC_E_INVAL;
+  *out = nullptr;
+  if (p->laser_on || p->flux_prec != 0) return EHC_E_INVAL;   // batches use the single-precision path, no source
+  ehc_batch *b = new (std::nothrow) ehc_batch();
+  if (!b) return EHC_E_NOMEM;
+  b->p = *p;
+  b->stream = (cudaStream_t)stream;
+  std::vector<int2> wl;
+  for (int32_t r = 0; r < n_rep; ++r) {
+    ehc_ctx *h = nullptr;
+    int e = ehc_create(p, n_atoms_host[r], boxes_host + 3 * r, periodic, mass_amu_host, 1, nullptr, stream, &h);
+    if (e != EHC_OK) {
+      ehc_batch_destroy(b);
+      return e;
+    }
+    b->rep.push_back(h);
+    b->off.push_back(b->n_total);
+    b->n_total += n_atoms_host[r];
+    for (int64_t R = 0; R < h->c.nrows; ++R) wl.push_back(make_int2(r, (int)R));
+  }
+  b->nwork = (int32_t)wl.size();
+  bool ok = cudaMalloc((void **)&b->reps_dev, sizeof(RepArgs) * n_rep) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&b->work, sizeof(int2) * (wl.empty() ? 1 : wl.size())) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, 0) == cudaSuccess;
+  if (ok && !wl.empty())
+    ok = cudaMemcpy(b->work, wl.data(), sizeof(int2) * wl.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ehc_batch_destroy(b);
+    return EHC_E_NOMEM;
+  }
+  *out = b;
+  return EHC_OK;
+}
+
+void ehc_batch_destroy(ehc_batch *b) {
+  if (!b) return;
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto *h : b->rep) ehc_destroy(h);
+  if (b->reps_dev) cudaFree(b->reps_dev);
+  if (b->work) cudaFree(b->work);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+int ehc_batch_size(const ehc_batch *b, int64_t *n_total, int64_t *offsets_host) {
+  if (!b) return EHC_E_INVAL;
+  if (n_total) *n_total = b->n_total;
+  if (offsets_host)
+    for (size_t r = 0; r < b->off.size(); ++r) offsets_host[r] = b->off[r];
+  return EHC_OK;
+}
+
+int ehc_batch_set_te(ehc_batch *b, const double *Te_dev) {
+  if (!b || (!Te_dev && b->n_total > 0)) return EHC_E_INVAL;
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    int e = ehc_set_te(b->rep[r], Te_dev + b->off[r]);
+    if (e) return e;
+  }
+  b->parity = 0;
+  return EHC_OK;
+}
+
+int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v_dev) {
+  if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    int e = build_enqueue(b->rep[r]->c, x_dev + 3 * b->off[r], v_dev + 3 * b->off[r]);
+    if (e) return e;
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  int first_err = EHC_OK;
+  int32_t staged = 0;
+  std::vector<RepArgs> tab(b->rep.size());
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    Ctx &c = b->rep[r]->c;
+    int e = build_finish(c, false);
+    if (e && !first_err) first_err = e;
+    staged = std::max(staged, c.staged_max);
+    tab[r] = rep_args(c);
+  }
+  if (staged > b->tile_floats) {
+    const int32_t tb = ((staged + staged / 4 + 64 + 255) / 256) * 256;
+    int bps = 0;
+    if ((int64_t)tb * 2 * (int64_t)sizeof(float) <= kTileMaxBytes && tile_setup(tb, &bps) == cudaSuccess && bps > 0) {
+      b->tile_floats = tb;
+      b->tile_grid = bps * b->num_sms;
+    }
+    cudaGetLastError();
+  }
+  CK(cudaMemcpy(b->reps_dev, tab.data(), sizeof(RepArgs) * tab.size(), cudaMemcpyHostToDevice));
+  b->parity = 0;
+  return first_err;
+}
+
+int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
+  if (!b || n_sub < 0) return EHC_E_INVAL;
+  for (auto *h : b->rep) {
+    if (!h->c.built) return EHC_E_STATE;
+    if (h->c.n > 0 && !(h->c.stability <= 2.0)) return EHC_E_UNSTABLE;
+  }
+  if (n_sub == 0) return EHC_OK;
+  if (!batch_tile_ok(*b)) {
+    // some replica does not fit the row tiles: advance each on its own
+    for (auto *h : b->rep) {
+      int e = ehc_substep(h, n_sub, t_fs);
+      if (e) return e;
+    }
+    return EHC_OK;
+  }
+  for (auto *h : b->rep) {
+    h->c.parity = b->parity;
+    int e = ensure_split(h->c);
+    if (e) return e;
+  }
+  const int p0 = b->parity;
+  const int pairs = batch_pairs(*b);
+  int hit = -1;
+  for (size_t i = 0; i < b->graphs.size(); ++i) {
+    const auto &g = b->graphs[i];
+    if (g.n_sub == n_sub && g.parity == p0 && g.pairs == pairs && g.tile == b->tile_floats) hit = (int)i;
+  }
+  if (hit < 0) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < n_sub && le == cudaSuccess; ++k)
+      le = launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats, b->tile_grid, pairs, p0 ^ (k & 1), k,
+                                b->cap_stream);
+    cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (le != cudaSuccess || ee != cudaSuccess) return EHC_E_CUDA;
+    cudaGraphExec_t exec;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return EHC_E_CUDA;
+    if (b->graphs.size() >= 8) {
+      cudaGraphExecDestroy(b->graphs.front().exec);
+      b->graphs.erase(b->graphs.begin());
+    }
+    b->graphs.push_back({n_sub, p0, pairs, b->tile_floats, exec});
+    hit = (int)b->graphs.size() - 1;
+  }
+  CK(cudaGraphLaunch(b->graphs[hit].exec, b->stream));
+  b->parity = p0 ^ (n_sub & 1);
+  for (auto *h : b->rep) {
+    h->c.parity = b->parity;
+    h->c.t_stale = true;
+  }
+  return EHC_OK;
+}
+
+int ehc_batch_couple(ehc_batch *b, double *v_dev, double dt_md_fs) {
+  if (!b || (b->n_total > 0 && !v_dev)) return EHC_E_INVAL;
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    int e = ehc_couple(b->rep[r], v_dev + 3 * b->off[r], dt_md_fs);
+    if (e) return e;
+  }
+  return EHC_OK;
+}
+
+int ehc_batch_drift(ehc_batch *b, double *x_dev, const double *v_dev, double dt_fs) {
+  if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    int e = ehc_drift(b->rep[r], x_dev + 3 * b->off[r], v_dev + 3 * b->off[r], dt_fs);
+    if (e) return e;
+  }
+  return EHC_OK;
+}
+
+int ehc_batch_get_te(ehc_batch *b, double *Te_dev_out) {
+  if (!b || (b->n_total > 0 && !Te_dev_out)) return EHC_E_INVAL;
+  for (size_t r = 0; r < b->rep.size(); ++r) {
+    int e = ehc_get_te(b->rep[r], Te_dev_out + b->off[r]);
+    if (e) return e;
+  }
+  return EHC_OK;
+}
+
+int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
+  if (!b || r < 0 || r >= (int32_t)b->rep.size()) return EHC_E_INVAL;
+  return ehc_energy(b->rep[r], out);
 }
 
 }  // extern "C"

@@ -107,6 +107,8 @@ cudaError_t launch_split(Ctx &c, cudaStream_t s);
 cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
 bool tile_path(const Ctx &c);
 cudaError_t tile_setup(int tb, int *blocks_per_sm);
+cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
+                                 int pairs, int parity, int k, cudaStream_t st);
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);

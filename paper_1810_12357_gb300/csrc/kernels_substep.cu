@@ -475,6 +475,17 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// one substep of the row-tile kernel over an explicit work list (batched systems)
+cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
+                                 int pairs, int parity, int k, cudaStream_t st) {
+  const size_t shm = sizeof(float) * 2 * (size_t)tb;
+  const unsigned g = (unsigned)(nwork < grid ? nwork : grid);
+  if (g == 0) return cudaSuccess;
+  if (pairs == 9) substep_tile_kernel<false, 9><<<g, kTileThreads + 32, shm, st>>>(reps, work, nwork, tb, parity, k);
+  else substep_tile_kernel<false, 16><<<g, kTileThreads + 32, shm, st>>>(reps, work, nwork, tb, parity, k);
+  return cudaGetLastError();
+}
+
 // shared memory opt-in and resident CTAs per SM of the tile kernel for two
 // buffers of tb floats
 cudaError_t tile_setup(int tb, int *blocks_per_sm) {

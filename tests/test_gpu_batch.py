@@ -1,0 +1,66 @@
+"""Batched replicas (ehc_batch_*): one substep launch over the (replica, row)
+work list of all replicas must give each replica exactly what a single context
+gives it, and agree with the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_12357_gb300 import inputs as I
+
+from _drive import run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _concat(systems):
+    x = np.concatenate([s.x for s in systems])
+    v = np.concatenate([s.v for s in systems])
+    Te = np.concatenate([s.Te for s in systems])
+    return x, v, Te
+
+
+def _run_batch(systems, p, n_md, n_sub):
+    import torch
+    from paper_1810_12357_gb300 import EhcBatch
+    b = EhcBatch(p, systems)
+    x, v, Te = _concat(systems)
+    x = torch.as_tensor(x, device="cuda").contiguous()
+    v = torch.as_tensor(v, device="cuda").contiguous()
+    b.set_te(torch.as_tensor(Te, device="cuda"))
+    dt_md = n_sub * p["dt_sub"]
+    for step in range(n_md):
+        b.build_neighbors(x, v)
+        b.substep(n_sub, step * dt_md)
+        b.couple(v, dt_md)
+        b.drift(x, v, dt_md)
+    torch.cuda.synchronize()
+    return b, x, v
+
+
+@pytest.mark.parametrize("couple_mode", [0, 1])
+def test_batch_equals_single_contexts(couple_mode):
+    systems = I.batch_replicas(5, 41, n_min=1500, n_max=12000)
+    p = dict(I.params_track(), couple_mode=couple_mode, Tmax=1e5)
+    b, xb, vb = _run_batch(systems, p, 3, 40)
+    Tb = b.get_te().cpu().numpy()
+    vb = vb.cpu().numpy()
+    for r, s in enumerate(systems):
+        g, xg, vg = run_gpu(s, p, 3, 40)
+        lo, hi = b.offsets[r], b.offsets[r] + s.n
+        assert np.array_equal(Tb[lo:hi], g.get_te().cpu().numpy())
+        assert np.array_equal(vb[lo:hi], vg.cpu().numpy())
+        eb, eg = b.energy(r), g.energy()
+        assert eb["E_e"] == eg["E_e"] and eb["E_lat"] == eg["E_lat"]
+
+
+def test_batch_replica_matches_oracle():
+    systems = I.batch_replicas(4, 42, n_min=2000, n_max=8000)
+    p = I.params_track()
+    b, _, _ = _run_batch(systems, p, 2, 50)
+    Tb = b.get_te().cpu().numpy()
+    for r, s in enumerate(systems):
+        sim, _, _ = run_oracle(s, p, 2, 50)
+        lo = b.offsets[r]
+        err = float(np.max(np.abs(Tb[lo:lo + s.n] - sim.T) / sim.T))
+        assert err < 1e-4, (r, err)
+        assert abs(b.energy(r)["drift"]) < 1e-8
