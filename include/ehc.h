@@ -216,6 +216,43 @@ int ehc_electron_energy_noalloc(const double *Te_dev, int64_t n, double gamma_Ce
 void ehc_destroy(ehc_ctx *c);
 const char *ehc_strerror(int code);
 
+/* ---- Learned window propagator ------------------------------------------------
+ * A small message-passing network over the context's neighbour list stands in
+ * for n_window explicit substeps of Eq. HeatTransport (pair-flux part); the
+ * coupling term of the window is applied in closed form.  Two layers of hidden
+ * width H (8 or 16), every pair term odd under i <-> j (pair fluxes conserve
+ * sum_i T_i).  With delta = (T - Tref)/Tmax, D = (delta_j - delta_i)/sigma,
+ * q = D^2/(1+D^2), s = theta_i + theta_j:
+ *   h_i = sum_j D relu(W1 [q, s] + b1),
+ *   phi_ij = D (c0 + w . relu(W2 [q, s] + b2)) + u . (h_j - h_i),
+ *   T^_i = T_i + sigma Tmax (n_window dt K) sum_j phi_ij.
+ * Parameters (8H + 1 floats): [W1 (H x 2) | b1 | W2 (H x 2) | b2 | w | u | c0];
+ * BF16 weights and hidden vectors in the forward, FP32 arithmetic and
+ * accumulation, FP32 master weights and Adam for training.  The network is
+ * bound to the atom count of the context it was created with; single-precision
+ * flux, no laser source. */
+typedef struct ehc_nn ehc_nn;
+int ehc_nn_create(ehc_ctx *c, int32_t hidden, int32_t n_window, double sigma, ehc_nn **out);
+int ehc_nn_set_params(ehc_nn *nn, ehc_ctx *c, const float *params_host);
+int ehc_nn_get_params(ehc_nn *nn, ehc_ctx *c, float *params_host);
+/* One training step on a window: Tin_dev -> Ttar_dev (caller order, device;
+ * the target is the state after n_window plain substeps without coupling) on the
+ * context's current neighbour list and K.  Loss mean(((T^ - T*)/(sigma Tmax))^2)
+ * to *loss_host; the gradient (8H + 1) to grad_host if not NULL; an Adam step of
+ * rate lr if lr > 0.  Synchronises. */
+int ehc_nn_train_step(ehc_nn *nn, ehc_ctx *c, const double *Tin_dev, const double *Ttar_dev, float lr,
+                      float *loss_host, float *grad_host);
+/* Flux-only prediction of one window from Tin_dev into Tout_dev (caller order). */
+int ehc_nn_predict(ehc_nn *nn, ehc_ctx *c, const double *Tin_dev, double *Tout_dev);
+/* Advance the context by one window: predict, apply the window's coupling, and
+ * form the a-posteriori residual rho = max_i |T^_i - T_i - tau_w (R(T)_i + R(T^)_i)/2|
+ * / max(1 K, 1e-3 T_i) with R the right-hand side of Eq. HeatTransport and tau_w the
+ * window length.  rho <= tau: the prediction is kept (and its coupling energy
+ * handed to the lattice ledger); otherwise the window is redone with n_window
+ * plain substeps (*fell_back = 1).  Synchronises once. */
+int ehc_nn_step(ehc_nn *nn, ehc_ctx *c, double tau, double t_fs, int32_t *fell_back, double *rho_out);
+void ehc_nn_destroy(ehc_nn *nn);
+
 /* ---- Batched replicas --------------------------------------------------------
  * Independent systems (e.g. repeated cascades of different sizes, Sec. 4) that
  * share one parameter set are advanced together: each replica keeps its own

@@ -86,6 +86,13 @@ _SIGS = {
     "ehc_load": (_I, [_P, ctypes.c_char_p]),
     "ehc_electron_energy_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, _P, _P]),
+    "ehc_nn_create": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_P)]),
+    "ehc_nn_set_params": (_I, [_P, _P, _P]),
+    "ehc_nn_get_params": (_I, [_P, _P, _P]),
+    "ehc_nn_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, _P, _P]),
+    "ehc_nn_predict": (_I, [_P, _P, _P, _P]),
+    "ehc_nn_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
+    "ehc_nn_destroy": (None, [_P]),
     "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
                               ctypes.POINTER(_P)]),
     "ehc_batch_size": (_I, [_P, _P, _P]),
@@ -377,3 +384,63 @@ class EhcBatch:
         e = ehc_energy_t()
         _check(self._lib.ehc_batch_energy(self._h, int(r), ctypes.byref(e)), "ehc_batch_energy")
         return {f: getattr(e, f) for f, _ in ehc_energy_t._fields_}
+
+
+class EhcNN:
+    """Learned window propagator bound to a context (ehc_nn_*)."""
+
+    def __init__(self, ctx: "Ehc", hidden: int = 8, n_window: int = 16, sigma: float = 1e-3, params=None):
+        L = load_library()
+        self._lib = L
+        self.ctx = ctx
+        self.H = int(hidden)
+        self.n_window = int(n_window)
+        self.sigma = float(sigma)
+        self.np = 8 * self.H + 1
+        h = ctypes.c_void_p()
+        _check(L.ehc_nn_create(ctx._h, self.H, self.n_window, self.sigma, ctypes.byref(h)), "ehc_nn_create")
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.ehc_nn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.shape == (self.np,)
+        _check(self._lib.ehc_nn_set_params(self._h, self.ctx._h, a.ctypes.data_as(_P)), "ehc_nn_set_params")
+
+    def get_params(self):
+        a = np.empty(self.np, dtype=np.float32)
+        _check(self._lib.ehc_nn_get_params(self._h, self.ctx._h, a.ctypes.data_as(_P)), "ehc_nn_get_params")
+        return a
+
+    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False):
+        loss = ctypes.c_float()
+        g = np.empty(self.np, dtype=np.float32) if want_grad else None
+        _check(self._lib.ehc_nn_train_step(self._h, self.ctx._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr),
+                                           ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
+               "ehc_nn_train_step")
+        return (float(loss.value), g) if want_grad else float(loss.value)
+
+    def predict(self, Tin):
+        import torch
+        out = torch.empty_like(Tin)
+        _check(self._lib.ehc_nn_predict(self._h, self.ctx._h, _ptr(Tin), _ptr(out)), "ehc_nn_predict")
+        return out
+
+    def step(self, tau: float, t_fs: float = 0.0):
+        fb = ctypes.c_int32()
+        rho = ctypes.c_double()
+        _check(self._lib.ehc_nn_step(self._h, self.ctx._h, float(tau), float(t_fs), ctypes.byref(fb),
+                                     ctypes.byref(rho)), "ehc_nn_step")
+        return bool(fb.value), float(rho.value)

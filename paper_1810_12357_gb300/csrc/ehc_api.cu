@@ -1044,3 +1044,165 @@ int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned window propagator
+
+struct ehc_nn {
+  int H = 8, n_w = 16, np = 0;
+  double sigma = 1e-3;
+  int64_t n = 0;
+  int t = 0;                       // Adam steps taken
+  float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+  __nv_bfloat16 *pb = nullptr, *h = nullptr;
+  float *gphi = nullptr, *p1 = nullptr, *p2 = nullptr, *dm0 = nullptr, *dm1 = nullptr, *rpart = nullptr, *rho = nullptr;
+  double *T0 = nullptr, *T1 = nullptr, *Ttar = nullptr;
+  float *host = nullptr;           // pinned: loss, rho, gradient
+  int64_t fallbacks = 0, windows = 0;
+};
+
+extern "C" {
+
+int ehc_nn_create(ehc_ctx *hc, int32_t hidden, int32_t n_window, double sigma, ehc_nn **out) {
+  if (!hc || !out || (hidden != 8 && hidden != 16) || n_window < 1 || !(sigma > 0)) return EHC_E_INVAL;
+  *out = nullptr;
+  Ctx &c = hc->c;
+  if (c.p.flux_prec != 0 || c.p.laser_on) return EHC_E_INVAL;
+  ehc_nn *nn = new (std::nothrow) ehc_nn();
+  if (!nn) return EHC_E_NOMEM;
+  nn->H = hidden;
+  nn->n_w = n_window;
+  nn->sigma = sigma;
+  nn->n = c.n;
+  nn->np = 8 * hidden + 1;
+  const int64_t n = c.n > 0 ? c.n : 1;
+  const int nb = nn_blocks(n);
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dalloc(&nn->p, nn->np));
+  A(dalloc(&nn->m, nn->np));
+  A(dalloc(&nn->v, nn->np));
+  A(dalloc(&nn->grad, nn->np));
+  A(dalloc(&nn->loss, 1));
+  A(dalloc(&nn->pb, nn->np));
+  A(dalloc(&nn->h, n * hidden));
+  A(dalloc(&nn->gphi, n));
+  A(dalloc(&nn->p2, (int64_t)nb * (5 * hidden + 2)));
+  A(dalloc(&nn->p1, (int64_t)nb * (3 * hidden)));
+  A(dalloc(&nn->dm0, n));
+  A(dalloc(&nn->dm1, n));
+  A(dalloc(&nn->rpart, nb));
+  A(dalloc(&nn->rho, 1));
+  A(dalloc(&nn->T0, n));
+  A(dalloc(&nn->T1, n));
+  A(dalloc(&nn->Ttar, n));
+  A(cudaMallocHost((void **)&nn->host, sizeof(float) * (nn->np + 4)));
+  if (ok) {
+    A(cudaMemsetAsync(nn->p, 0, sizeof(float) * nn->np, c.stream));
+    A(cudaMemsetAsync(nn->m, 0, sizeof(float) * nn->np, c.stream));
+    A(cudaMemsetAsync(nn->v, 0, sizeof(float) * nn->np, c.stream));
+    A(cudaStreamSynchronize(c.stream));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    ehc_nn_destroy(nn);
+    return EHC_E_NOMEM;
+  }
+  *out = nn;
+  return EHC_OK;
+}
+
+void ehc_nn_destroy(ehc_nn *nn) {
+  if (!nn) return;
+  void *d[] = {nn->p, nn->m, nn->v, nn->grad, nn->loss, nn->pb, nn->h, nn->gphi, nn->p1, nn->p2,
+               nn->dm0, nn->dm1, nn->rpart, nn->rho, nn->T0, nn->T1, nn->Ttar};
+  for (void *q : d)
+    if (q) cudaFree(q);
+  if (nn->host) cudaFreeHost(nn->host);
+  delete nn;
+}
+
+int ehc_nn_set_params(ehc_nn *nn, ehc_ctx *hc, const float *params_host) {
+  if (!nn || !hc || !params_host) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  CK(cudaMemcpyAsync(nn->p, params_host, sizeof(float) * nn->np, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemsetAsync(nn->m, 0, sizeof(float) * nn->np, c.stream));
+  CK(cudaMemsetAsync(nn->v, 0, sizeof(float) * nn->np, c.stream));
+  CK(nn_params_to_bf16(c.stream, nn->np, nn->p, nn->pb));
+  CK(cudaStreamSynchronize(c.stream));
+  nn->t = 0;
+  return EHC_OK;
+}
+
+int ehc_nn_get_params(ehc_nn *nn, ehc_ctx *hc, float *params_host) {
+  if (!nn || !hc || !params_host) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  CK(cudaMemcpyAsync(params_host, nn->p, sizeof(float) * nn->np, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  return EHC_OK;
+}
+
+int ehc_nn_train_step(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
+                      float *loss_host, float *grad_host) {
+  if (!nn || !hc || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || hc->c.n != nn->n) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  CK(nn_gather(c, Tin_dev, Ttar_dev, nn->T0, nn->Ttar, nn->dm0));
+  CK(nn_grad(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->Ttar, nn->gphi, nn->p2, nn->p1,
+             nn->grad, nn->loss));
+  CK(cudaMemcpyAsync(nn->host, nn->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+  if (grad_host)
+    CK(cudaMemcpyAsync(nn->host + 4, nn->grad, sizeof(float) * nn->np, cudaMemcpyDeviceToHost, c.stream));
+  if (lr > 0.0f) {
+    nn->t += 1;
+    CK(nn_adam(c.stream, nn->np, nn->p, nn->m, nn->v, nn->grad, lr, nn->t, nn->pb));
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  if (loss_host) *loss_host = nn->host[0];
+  if (grad_host) std::memcpy(grad_host, nn->host + 4, sizeof(float) * nn->np);
+  return EHC_OK;
+}
+
+int ehc_nn_predict(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, double *Tout_dev) {
+  if (!nn || !hc || (hc->c.n > 0 && (!Tin_dev || !Tout_dev)) || hc->c.n != nn->n) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  CK(nn_gather(c, Tin_dev, nullptr, nn->T0, nullptr, nn->dm0));
+  CK(nn_forward(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->T1, nn->dm1));
+  CK(launch_unpermute(c, nn->T1, Tout_dev, 0));
+  return EHC_OK;
+}
+
+int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_back, double *rho_out) {
+  if (!nn || !hc || hc->c.n != nn->n) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  if (!(c.stability <= 2.0)) return EHC_E_UNSTABLE;
+  int r = ensure_t(c);
+  if (r) return r;
+  if (c.n == 0) return EHC_OK;
+  // the window's state in sorted order: T0 and its mirror
+  CK(nn_gather(c, c.T[c.tcur], nullptr, nn->T0, nullptr, nn->dm0));
+  CK(nn_forward(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->T1, nn->dm1));
+  CK(nn_couple_window(c, nn->T0, nn->T1, nn->dm1, nn->Ttar, nn->n_w));
+  CK(nn_residual(c, nn->dm0, nn->dm1, nn->T0, nn->T1, (double)nn->n_w * c.p.dt_sub_fs, nn->rpart, nn->rho));
+  CK(cudaMemcpyAsync(nn->host + 1, nn->rho, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  const double rho = nn->host[1];
+  nn->windows += 1;
+  if (rho_out) *rho_out = rho;
+  if (rho <= tau) {
+    CK(nn_accept(c, nn->Ttar));
+    CK(cudaMemcpyAsync(c.T[c.tcur], nn->T1, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+    c.ff_valid = false;
+    c.t_stale = false;
+    if (fell_back) *fell_back = 0;
+    return EHC_OK;
+  }
+  // residual above threshold: advance the window with the plain substeps
+  nn->fallbacks += 1;
+  if (fell_back) *fell_back = 1;
+  return ehc_substep(hc, nn->n_w, t_fs);
+}
+
+}  // extern "C"

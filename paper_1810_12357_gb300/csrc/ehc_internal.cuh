@@ -13,6 +13,7 @@
 //   Tl_d  double[N]     same in FP64 (for the FP64 flux path and diagnostics)
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -109,6 +110,21 @@ bool tile_path(const Ctx &c);
 cudaError_t tile_setup(int tb, int *blocks_per_sm);
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
                                  int pairs, int parity, int k, cudaStream_t st);
+// kernels_nn.cu (learned window propagator)
+int nn_blocks(int64_t n);
+cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm);
+cudaError_t nn_forward(Ctx &c, int H, const __nv_bfloat16 *pb, double sigma, int n_w, const float *dm,
+                       __nv_bfloat16 *h, const double *Tin, double *Tout, float *dm_out);
+cudaError_t nn_grad(Ctx &c, int H, const __nv_bfloat16 *pb, double sigma, int n_w, const float *dm,
+                    __nv_bfloat16 *h, const double *Tin, const double *Ttar, float *gphi, float *p2, float *p1,
+                    float *grad, float *loss);
+cudaError_t nn_adam(cudaStream_t st, int np, float *p, float *m, float *v, const float *g, float lr, int t,
+                    __nv_bfloat16 *pb);
+cudaError_t nn_params_to_bf16(cudaStream_t st, int np, const float *p, __nv_bfloat16 *pb);
+cudaError_t nn_residual(Ctx &c, const float *d0, const float *d1, const double *T0, const double *T1, double tau,
+                        float *part, float *out);
+cudaError_t nn_couple_window(Ctx &c, const double *T0, double *T1, float *d1, double *dTc, int n_w);
+cudaError_t nn_accept(Ctx &c, const double *dTc);
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);

@@ -1,0 +1,71 @@
+"""Training and evaluation of the learned window propagator (ehc_nn_*).
+
+Training windows come from the plain method itself: a context runs n_w
+explicit substeps of Eq. HeatTransport with the coupling switched off (G = 0),
+and each (state, state n_w substeps later) pair is one window.  The network is
+trained on the GPU by the library's own forward/backward kernels and Adam.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import Ehc, EhcNN
+
+
+def generate_windows(system, params: dict, n_windows: int, n_w: int = 16, stride: int = 1):
+    """(T_in, T_out) device tensor pairs from a frozen-atom, flux-only run of the
+    plain method (caller order).  `stride` windows are skipped between samples."""
+    import torch
+    p = dict(params, G=0.0, frozen=1)
+    g = Ehc(p, system)
+    g.set_te(system.Te)
+    x = torch.as_tensor(system.x, device="cuda")
+    v = torch.as_tensor(system.v, device="cuda")
+    g.build_neighbors(x, v)
+    pairs = []
+    for w in range(n_windows):
+        for _ in range(stride - 1):
+            g.substep(n_w)
+        t0 = g.get_te()
+        g.substep(n_w)
+        t1 = g.get_te()
+        pairs.append((t0, t1))
+    return g, pairs
+
+
+def train(nn: EhcNN, pairs, steps: int, lr: float = 3e-3, log_every: int = 0):
+    """Adam steps cycling through the windows; returns the loss history."""
+    hist = []
+    for k in range(steps):
+        t0, t1 = pairs[k % len(pairs)]
+        loss = nn.train_step(t0, t1, lr)
+        hist.append(loss)
+        if log_every and k % log_every == 0:
+            print(f"step {k} loss {loss:.4e}")
+    return hist
+
+
+def window_error(nn: EhcNN, pairs):
+    """Max relative and RMS absolute error of flux-only predictions on windows."""
+    import torch
+    mx, ms = 0.0, 0.0
+    for t0, t1 in pairs:
+        p = nn.predict(t0)
+        d = (p - t1).abs()
+        mx = max(mx, float((d / t1).max()))
+        ms = max(ms, float(torch.sqrt((d * d).mean())))
+    return mx, ms
+
+
+def init_params(H: int, seed: int = 0) -> np.ndarray:
+    """c0 = 1 (one Euler step of the whole window), small hidden weights."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(8 * H + 1, dtype=np.float32)
+    p[0:2 * H] = rng.normal(0, 0.3, size=2 * H)          # W1
+    p[2 * H:3 * H] = 0.1                                  # b1
+    p[3 * H:5 * H] = rng.normal(0, 0.3, size=2 * H)      # W2
+    p[5 * H:6 * H] = 0.1                                  # b2
+    p[6 * H:7 * H] = rng.normal(0, 0.01, size=H)         # w
+    p[7 * H:8 * H] = rng.normal(0, 0.01, size=H)         # u
+    p[8 * H] = 1.0                                        # c0
+    return p
