@@ -398,6 +398,94 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned window propagator on the 4,000,000-atom track: windows of 16
+    substeps advanced by the network (with the a-posteriori residual check and
+    fallback to plain substeps), against the plain path from the same state."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc, EhcNN, learned
+    from paper_1810_12357_gb300 import inputs as I
+    H, n_w, sigma, tau = args.hidden, 16, 1e-3, args.tau
+    p = I.params_track()
+    # training windows: 256,000-atom track and hot-spot cells (40^3 cells), plain method
+    t_train0 = time.perf_counter()
+    train_sys = [I.track_system(40, 100 + k, peak=5000.0 + 3000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
+    train_sys += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 4000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
+                  for k in range(3)]
+    ctxs, pairs = [], []
+    for s in train_sys:
+        g, pr = learned.generate_windows(s, p, args.train_windows // len(train_sys), n_w)
+        ctxs.append(g)
+        pairs.append(pr)
+    net = EhcNN(ctxs[0], hidden=H, n_window=n_w, sigma=sigma, params=learned.init_params(H, 0))
+    for k in range(args.train_steps):
+        c = k % len(ctxs)
+        t0, t1 = pairs[c][(k // len(ctxs)) % len(pairs[c])]
+        net.train_step(t0, t1, 3e-3 if k < args.train_steps * 3 // 4 else 1e-3, ctx=ctxs[c])
+    params = net.get_params()
+    t_train = time.perf_counter() - t_train0
+    # held-out check on a training-size system: error of the flux-only window
+    held_g, held = learned.generate_windows(I.track_system(40, 199, peak=12000.0, r0=15.0), p, 8, n_w)
+    held_net = EhcNN(held_g, hidden=H, n_window=n_w, sigma=sigma, params=params)
+    held_err = learned.window_error(held_net, held)
+    base_net = EhcNN(held_g, hidden=H, n_window=n_w, sigma=sigma, params=learned.init_params(H, 0))
+    base_err = learned.window_error(base_net, held)
+    del pairs
+
+    # evaluation on the 4M-atom track: learned windows vs the plain path
+    s, _ = workload(args.cells)
+    n = s.n
+    a = Ehc(p, s)
+    b = Ehc(p, s)
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    for c in (a, b):
+        c.set_te(s.Te)
+        c.build_neighbors(x, v)
+    ev = EhcNN(a, hidden=H, n_window=n_w, sigma=sigma, params=params)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):   # warm-up windows
+        ev.step(tau)
+        b.substep(n_w)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fb = 0
+    rhos = []
+    for _ in range(args.windows):
+        f, rho = ev.step(tau)
+        fb += int(f)
+        rhos.append(rho)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_l = e0.elapsed_time(e1)
+    e0.record(stream)
+    for _ in range(args.windows):
+        b.substep(n_w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    Ta = a.get_te()
+    Tb = b.get_te()
+    err = float(((Ta - Tb).abs() / Tb).max())
+    value = n * n_w * args.windows / (ms_l * 1e-3)
+    plain = n * n_w * args.windows / (ms_p * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.windows, "warmup": 2,
+            "ms_per_step": ms_l / args.windows, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 weights / f32 accumulate", "data": "synthetic",
+            "config": config_dict(args.cells, n, {"path": "learned", "window_substeps": n_w, "hidden": H,
+                                                 "residual_tau": tau, "coupling": "closed form per window"}),
+            "learned": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
+                        "fallbacks": fb, "windows": args.windows, "rho_median": float(np.median(rhos)),
+                        "rho_max": float(np.max(rhos)), "train_s": t_train,
+                        "heldout_256k_window_err": {"trained_max_rel": held_err[0], "trained_rms_K": held_err[1],
+                                                    "untrained_max_rel": base_err[0],
+                                                    "untrained_rms_K": base_err[1]},
+                        "train_windows": args.train_windows, "train_steps": args.train_steps}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,7 +496,12 @@ def main():
     ap.add_argument("--ref-substeps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="track", choices=["track", "batch"])
+    ap.add_argument("--workload", default="track", choices=["track", "batch", "learned"])
+    ap.add_argument("--hidden", type=int, default=8)
+    ap.add_argument("--tau", type=float, default=0.05)
+    ap.add_argument("--windows", type=int, default=20)
+    ap.add_argument("--train-windows", type=int, default=480)
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--replicas", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ehc":
@@ -417,6 +510,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

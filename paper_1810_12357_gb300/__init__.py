@@ -424,10 +424,13 @@ class EhcNN:
         _check(self._lib.ehc_nn_get_params(self._h, self.ctx._h, a.ctypes.data_as(_P)), "ehc_nn_get_params")
         return a
 
-    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False):
+    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False, ctx=None):
+        """One Adam step on a window; `ctx` (same atom count) supplies the
+        neighbour list and K, default the context the network was created on."""
         loss = ctypes.c_float()
         g = np.empty(self.np, dtype=np.float32) if want_grad else None
-        _check(self._lib.ehc_nn_train_step(self._h, self.ctx._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr),
+        c = ctx if ctx is not None else self.ctx
+        _check(self._lib.ehc_nn_train_step(self._h, c._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr),
                                            ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
                "ehc_nn_train_step")
         return (float(loss.value), g) if want_grad else float(loss.value)

@@ -1147,7 +1147,7 @@ int ehc_nn_train_step(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, const doub
   if (!nn || !hc || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || hc->c.n != nn->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
-  CK(nn_gather(c, Tin_dev, Ttar_dev, nn->T0, nn->Ttar, nn->dm0));
+  CK(nn_gather(c, Tin_dev, Ttar_dev, nn->T0, nn->Ttar, nn->dm0, false));
   CK(nn_grad(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->Ttar, nn->gphi, nn->p2, nn->p1,
              nn->grad, nn->loss));
   CK(cudaMemcpyAsync(nn->host, nn->loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
@@ -1167,7 +1167,7 @@ int ehc_nn_predict(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, double *Tout_
   if (!nn || !hc || (hc->c.n > 0 && (!Tin_dev || !Tout_dev)) || hc->c.n != nn->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
-  CK(nn_gather(c, Tin_dev, nullptr, nn->T0, nullptr, nn->dm0));
+  CK(nn_gather(c, Tin_dev, nullptr, nn->T0, nullptr, nn->dm0, false));
   CK(nn_forward(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->T1, nn->dm1));
   CK(launch_unpermute(c, nn->T1, Tout_dev, 0));
   return EHC_OK;
@@ -1182,7 +1182,7 @@ int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_
   if (r) return r;
   if (c.n == 0) return EHC_OK;
   // the window's state in sorted order: T0 and its mirror
-  CK(nn_gather(c, c.T[c.tcur], nullptr, nn->T0, nullptr, nn->dm0));
+  CK(nn_gather(c, c.T[c.tcur], nullptr, nn->T0, nullptr, nn->dm0, true));
   CK(nn_forward(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->T1, nn->dm1));
   CK(nn_couple_window(c, nn->T0, nn->T1, nn->dm1, nn->Ttar, nn->n_w));
   CK(nn_residual(c, nn->dm0, nn->dm1, nn->T0, nn->T1, (double)nn->n_w * c.p.dt_sub_fs, nn->rpart, nn->rho));

@@ -112,7 +112,8 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
                                  int pairs, int parity, int k, cudaStream_t st);
 // kernels_nn.cu (learned window propagator)
 int nn_blocks(int64_t n);
-cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm);
+cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm,
+                      bool sorted);
 cudaError_t nn_forward(Ctx &c, int H, const __nv_bfloat16 *pb, double sigma, int n_w, const float *dm,
                        __nv_bfloat16 *h, const double *Tin, double *Tout, float *dm_out);
 cudaError_t nn_grad(Ctx &c, int H, const __nv_bfloat16 *pb, double sigma, int n_w, const float *dm,

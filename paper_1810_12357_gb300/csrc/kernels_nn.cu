@@ -398,10 +398,12 @@ cudaError_t nn_accept(Ctx &c, const double *dTc) {
 
 int nn_blocks(int64_t n) { return (int)nblk(n, kNnThreads); }
 
-cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm) {
+// sorted == true: Tin (and Ttar) are already in the context's sorted order
+cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm,
+                      bool sorted) {
   if (c.n > 0)
-    nn_gather_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.inv_perm[c.cur_inv], Tin, Ttar, c.p.Tref_K,
-                                                           1.0 / c.p.Tmax_K, Ts, Ttar_s, dm);
+    nn_gather_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, sorted ? nullptr : c.inv_perm[c.cur_inv], Tin, Ttar,
+                                                           c.p.Tref_K, 1.0 / c.p.Tmax_K, Ts, Ttar_s, dm);
   return cudaGetLastError();
 }
 
