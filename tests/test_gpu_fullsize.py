@@ -1,0 +1,107 @@
+"""Parity at the full size of the benchmark: the 4,000,000-atom swift-ion track
+in the launch configuration bench.py times (row-tile kernel, graph replay).
+
+* the neighbour list of all 4 M atoms equals the oracle's, bit for bit;
+* after 10 substeps, sampled atoms equal the oracle run on their 10-hop
+  neighbourhood (information travels one hop per substep, so the centre of a
+  10-hop ball is exact after 10 substeps): T_e within 1e-4 relative;
+* after a whole MD step (100 substeps, Langevin hand-over) the energy ledger
+  closes to 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_12357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N_SUB_SAMPLE = 10
+
+
+def _ball(rowptr, col, seed, hops):
+    """Atoms within `hops` neighbour hops of `seed`, and the neighbour list
+    restricted to them (local ids; links leaving the ball are dropped, which
+    only the outermost shell feels)."""
+    n = rowptr.shape[0] - 1
+    inball = np.zeros(n, dtype=bool)
+    inball[seed] = True
+    front = np.array([seed], dtype=np.int64)
+    for _ in range(hops):
+        cnt = rowptr[front + 1] - rowptr[front]
+        idx = np.repeat(rowptr[front] - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
+        nb = np.unique(col[idx])
+        front = nb[~inball[nb]]
+        inball[front] = True
+    ball = np.flatnonzero(inball)
+    loc = -np.ones(n, dtype=np.int64)
+    loc[ball] = np.arange(ball.size)
+    cnt = rowptr[ball + 1] - rowptr[ball]
+    idx = np.repeat(rowptr[ball] - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
+    lj = loc[col[idx]]
+    li = np.repeat(np.arange(ball.size), cnt)
+    keep = lj >= 0
+    li, lj = li[keep], lj[keep]
+    rp = np.zeros(ball.size + 1, dtype=np.int64)
+    np.add.at(rp, li + 1, 1)
+    return ball, loc, np.cumsum(rp), lj.astype(np.int32)
+
+
+@pytest.fixture(scope="module")
+def track():
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.track_system(100, 2)
+    p = I.params_track()
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    g.build_neighbors(x, v)
+    return s, p, g, x, v
+
+
+def test_fullsize_neighbor_list_bit_exact(track):
+    s, p, g, x, v = track
+    rg, cg = g.export_neighbors(cap_per_atom=24)
+    ro, co = oracle.neighbors(s.x, s.box, s.periodic, p["rc"], cap_per_atom=24)
+    assert np.array_equal(rg, ro)
+    assert np.array_equal(cg, co)
+
+
+def test_fullsize_sampled_substeps(track):
+    s, p, g, x, v = track
+    g.substep(N_SUB_SAMPLE, 0.0)
+    Tg = g.get_te().cpu().numpy()
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    rng = np.random.default_rng(7)
+    # samples across the track core, its flank and the far field
+    rho = np.hypot(s.x[:, 0] - 0.5 * s.box[0], s.x[:, 1] - 0.5 * s.box[1])
+    picks = np.concatenate([rng.choice(np.flatnonzero(rho < 8.0), 4, replace=False),
+                            rng.choice(np.flatnonzero((rho > 15.0) & (rho < 40.0)), 4, replace=False),
+                            rng.choice(np.flatnonzero(rho > 80.0), 4, replace=False)])
+    worst = 0.0
+    for a in picks:
+        ball, loc, rp, col = _ball(sim.rowptr, sim.col, a, N_SUB_SAMPLE)
+        T = s.Te[ball].copy()
+        Tl = sim.Tl[ball].copy()
+        chi = sim.chi[ball].copy()
+        Aacc = np.zeros(ball.size)
+        st, _ = oracle.substeps(rp, col, T, Tl, chi, Aacc, N_SUB_SAMPLE, p["dt_sub"], p["Tmax"], sim.K, sim.cG,
+                                sim.VG)
+        assert st == N_SUB_SAMPLE
+        err = abs(Tg[a] - T[loc[a]]) / T[loc[a]]
+        worst = max(worst, err)
+    assert worst < 1e-4, worst
+    print(f"full-size sampled T_e max rel err {worst:.3e}")
+
+
+def test_fullsize_md_step_ledger(track):
+    s, p, g, x, v = track
+    g.substep(100 - N_SUB_SAMPLE, N_SUB_SAMPLE * p["dt_sub"])
+    g.couple(v, 100 * p["dt_sub"])
+    e = g.energy()
+    assert abs(e["drift"]) < 1e-9
+    assert e["n_stopped"] == 0
