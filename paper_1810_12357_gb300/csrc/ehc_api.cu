@@ -212,6 +212,7 @@ RepArgs rep_args(const Ctx &c) {
   if (P > (c.W + 1) / 2) P = (c.W + 1) / 2;
   ra.P = P;
   ra.nrows = (int32_t)c.nrows;
+  ra.ps = (int32_t)c.ps;
   ra.start = c.cell_start;
   ra.row_nbr = c.row_nbr;
   ra.pidx = c.pidx;
@@ -321,7 +322,8 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.q_s, n));
   A(dalloc(&c.v_s, n));
   A(dalloc(&c.nbr, (size_t)W * n));
-  A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * n));
+  c.ps = (n + 3) / 4 * 4;
+  A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * (size_t)(c.ps > 0 ? c.ps : 4)));
   A(dalloc(&c.dlo, n));
   A(dalloc(&c.uTl, n));
   A(dalloc(&c.pulse_f, c.max_sub));
@@ -330,8 +332,8 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.cnt, n));
   A(dalloc(&c.T[0], n));
   A(dalloc(&c.T[1], n));
-  A(dalloc(&c.dmir[0], n));
-  A(dalloc(&c.dmir[1], n));
+  A(dalloc(&c.dmir[0], c.ps > 0 ? c.ps : 4));   // padded: tiles are copied in 16-byte aligned supersets
+  A(dalloc(&c.dmir[1], c.ps > 0 ? c.ps : 4));
   A(dalloc(&c.abuf[0], n));
   A(dalloc(&c.abuf[1], n));
   A(dalloc(&c.Tl_f, n));
@@ -369,6 +371,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   c.A_tmp = c.abuf[1];
   c.maxcnt = c.err + 1;
   c.maxstaged = c.err + 2;
+  c.maxrow = c.err + 3;
   std::vector<int32_t> rt;
   row_table(c.g, rt);
   cudaError_t e = cudaSuccess;
@@ -468,15 +471,15 @@ int build_finish(Ctx &c, bool own_tiles) {
   c.dev_err = w[0];
   c.n_max = w[1];
   c.staged_max = w[2];
-  // size the row tiles with headroom for atoms drifting between cells
+  c.row_max = w[3];
+  // size the row-tile buffers (grown only when a build outgrows them)
   if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
-    const int32_t tb = ((c.staged_max + c.staged_max / 4 + 64 + 255) / 256) * 256;
-    int bps = 0;
-    if ((int64_t)tb * 2 * (int64_t)sizeof(float) <= kTileMaxBytes && tile_setup(tb, &bps) == cudaSuccess && bps > 0) {
+    int32_t tb = 0, grid[2] = {0, 0};
+    if (tile_size(c.staged_max, c.num_sms, &tb, grid)) {
       c.tile_floats = tb;
-      c.tile_grid = bps * c.num_sms;
+      c.tile_grid[0] = grid[0];
+      c.tile_grid[1] = grid[1];
     }
-    cudaGetLastError();
   }
   const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
   c.wsum = c.scal_host[3];
@@ -827,7 +830,8 @@ struct ehc_batch {
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   RepArgs *reps_dev = nullptr;
   int2 *work = nullptr;
-  int32_t nwork = 0, tile_floats = 0, tile_grid = 0, num_sms = 0;
+  int32_t nwork = 0, tile_floats = 0, num_sms = 0;
+  int32_t tile_grid[2] = {0, 0};
   int parity = 0;
   struct G {
     int n_sub, parity, pairs, tile;
@@ -848,7 +852,7 @@ int batch_pairs(const ehc_batch &b) {
 }
 
 bool batch_tile_ok(const ehc_batch &b) {
-  if (b.tile_floats <= 0 || b.nwork <= 0) return false;
+  if (b.tile_floats <= 0 || b.nwork <= 0 || b.tile_grid[batch_pairs(b) == 9 ? 0 : 1] <= 0) return false;
   for (auto *h : b.rep)
     if (h->c.W > 32 || h->c.staged_max > b.tile_floats || h->c.p.flux_prec != 0) return false;
   return true;
@@ -942,13 +946,12 @@ int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v
     tab[r] = rep_args(c);
   }
   if (staged > b->tile_floats) {
-    const int32_t tb = ((staged + staged / 4 + 64 + 255) / 256) * 256;
-    int bps = 0;
-    if ((int64_t)tb * 2 * (int64_t)sizeof(float) <= kTileMaxBytes && tile_setup(tb, &bps) == cudaSuccess && bps > 0) {
+    int32_t tb = 0, grid[2] = {0, 0};
+    if (tile_size(staged, b->num_sms, &tb, grid)) {
       b->tile_floats = tb;
-      b->tile_grid = bps * b->num_sms;
+      b->tile_grid[0] = grid[0];
+      b->tile_grid[1] = grid[1];
     }
-    cudaGetLastError();
   }
   CK(cudaMemcpy(b->reps_dev, tab.data(), sizeof(RepArgs) * tab.size(), cudaMemcpyHostToDevice));
   b->parity = 0;
@@ -987,7 +990,8 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < n_sub && le == cudaSuccess; ++k)
-      le = launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats, b->tile_grid, pairs, p0 ^ (k & 1), k,
+      le = launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats, b->tile_grid[pairs == 9 ? 0 : 1],
+                                pairs, p0 ^ (k & 1), k,
                                 b->cap_stream);
     cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
     if (le != cudaSuccess || ee != cudaSuccess) return EHC_E_CUDA;

@@ -5,6 +5,8 @@
 //   original id); perm[s] = original id, inv_perm[original] = s.
 //   nbr   int32 [W][N]  slot-major: nbr[k*N + s] = k-th neighbour of s (sorted index),
 //                       a row lists its neighbours by ascending original id
+//   pidx  u32 [W/2][ps] the same neighbours as 16-bit indices into the row tile,
+//                       two per word; ps = N rounded up to a multiple of 4
 //   cnt   uint8 [N]     neighbour count of s
 //   T     double[N]     electronic temperature (FP64 state), sorted order
 //   dmir  float [2][N]  (T - Tref)/Tmax mirror, double-buffered across substeps
@@ -68,13 +70,15 @@ struct StepCoef {
 constexpr int kRowNbr = 9;
 constexpr int kTileThreads = 256;   // threads that own atoms (plus one descriptor warp)
 constexpr int kTileMinBlocks = 4;
-constexpr int kTileMaxBytes = 200 * 1024;   // two tile buffers must fit in this much shared memory
+constexpr int kTileMaxBytes = 200 * 1024;   // the tile buffers must fit in this much shared memory
+
 
 // Arguments of one system for the row-tile substep kernel (device table; one
 // entry for a single system, one per replica for a batch).  Pointers stay
 // fixed for the life of a context; P is refreshed after every neighbour build.
 struct RepArgs {
   int32_t n, ncx, P, nrows;
+  int32_t ps, rsv;               // plane stride of pidx (words, a multiple of 4)
   const int32_t *start, *row_nbr;
   const uint32_t *pidx;
   float *dmir[2];
@@ -107,7 +111,10 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t s);
 cudaError_t launch_split(Ctx &c, cudaStream_t s);
 cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
 bool tile_path(const Ctx &c);
-cudaError_t tile_setup(int tb, int *blocks_per_sm);
+// tile capacity tb with headroom for the largest staged tile, the shared-memory
+// opt-in and the resident grid of each index width (9 and 16 words); false:
+// the buffers do not fit
+bool tile_size(int32_t staged, int num_sms, int32_t *tb, int32_t grid[2]);
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
                                  int pairs, int parity, int k, cudaStream_t st);
 // kernels_nn.cu (learned window propagator)
@@ -158,7 +165,8 @@ struct Ctx {
   int4 *q_s = nullptr;           // sorted positions + cell id
   double4_32a *v_s = nullptr;        // sorted velocities and |v|^2
   int32_t *nbr = nullptr;        // [W][N]
-  uint32_t *pidx = nullptr;      // [W/2][N] pairs of 16-bit tile-local neighbour indices
+  uint32_t *pidx = nullptr;      // [W/2][ps] pairs of 16-bit tile-local neighbour indices
+  int64_t ps = 0;                // plane stride of pidx: N rounded up to a multiple of 4
   int32_t *row_nbr = nullptr;    // [nrows][9] neighbour rows, -1 padded
   int64_t nrows = 0;
   uint8_t *cnt = nullptr;
@@ -187,9 +195,11 @@ struct Ctx {
   int32_t *err = nullptr;        // device error word
   int32_t *maxcnt = nullptr;     // device max count (err + 1)
   int32_t *maxstaged = nullptr;  // largest staged row-tile size (err + 2)
+  int32_t *maxrow = nullptr;     // longest row (err + 3)
   int32_t staged_max = 0;
+  int32_t row_max = 0;
   int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)
-  int32_t tile_grid = 0;         // resident CTAs of the row-tile kernel
+  int32_t tile_grid[2] = {0, 0};  // resident CTAs of the row-tile kernel (9 / 16 index words)
   int32_t num_sms = 0;
   RepArgs *reps = nullptr;       // device table of the row-tile kernel (this system only)
   int2 *work = nullptr;          // (system, row) work list of the row-tile kernel

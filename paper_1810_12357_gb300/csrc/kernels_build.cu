@@ -180,15 +180,16 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
 // arithmetic is on the integer grid: per-axis minimum image in int32, the
 // squared distance in int64, inclusive comparison with r_c^2.  Outputs:
 //   nbr  [W][N] sorted indices in visit order (row, cell, sorted index)
-//   pidx [W/2][N] the same neighbours as 16-bit indices into the row tile (the
+//   pidx [W/2][ps] the same neighbours as 16-bit indices into the row tile (the
 //        concatenation of the neighbour rows), two per word; unused slots up to
 //        W hold the atom's own tile index, whose pair term is exactly zero.
 __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
                                                        const int32_t *__restrict__ start,
                                                        const int32_t *__restrict__ row_nbr, int32_t W,
                                                        int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
-                                                       uint8_t *__restrict__ cnt, int32_t *__restrict__ maxcnt,
-                                                       int32_t *__restrict__ maxstaged, int32_t *__restrict__ err) {
+                                                       int64_t ps, uint8_t *__restrict__ cnt,
+                                                       int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
+                                                       int32_t *__restrict__ maxrow, int32_t *__restrict__ err) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 qi = q_s[s];
@@ -217,14 +218,20 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
   int32_t prefix = 0;   // tile offset of the current neighbour row
   int32_t tend = 0;     // end of the tile so far
   int32_t self_local = 0;
+  int32_t own_len = 0;
   for (int r = 0; r < kRowNbr; ++r) {
     const int32_t R2 = row_nbr[(int64_t)R * kRowNbr + r];
     if (R2 < 0) break;
     const int32_t rs = start[(int64_t)R2 * ncx];
     const int32_t re = start[(int64_t)R2 * ncx + ncx];
-    // row placement in the tile: congruent to its first index modulo 4
-    prefix = tend + ((rs - tend) & 3);
-    if (R2 == R) self_local = prefix + (s - rs);
+    // row placement in the tile: after the previous row rounded up to 4 words,
+    // congruent to its first index modulo 4, so that the 16-byte aligned
+    // superset of every row lands on free words
+    prefix = ((tend + 3) & ~3) + (rs & 3);
+    if (R2 == R) {
+      self_local = prefix + (s - rs);
+      own_len = re - rs;
+    }
     for (int ix = 0; ix < nx; ++ix) {
       const int32_t cell = R2 * ncx + xo[ix];
       const int32_t t1 = start[cell + 1];
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
         if (d2 <= rc2) {
           if (m < W) {
             nbr[(int64_t)m * n + s] = t;
-            pidx16[((int64_t)(m >> 1) * n + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+            pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
           }
           ++m;
         }
@@ -254,15 +261,17 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
   }
   if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
   const int32_t mm = m < W ? m : W;
-  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * n + s) * 2 + (k & 1)] = (uint16_t)self_local;
+  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
   cnt[s] = (uint8_t)mm;
-  // one atomic per warp for the two maxima
+  // one atomic per warp for each of the three maxima
   const unsigned act = __activemask();
   const int32_t wm = __reduce_max_sync(act, m);
-  const int32_t ws = __reduce_max_sync(act, tend);
+  const int32_t ws = __reduce_max_sync(act, (tend + 3) & ~3);
+  const int32_t wr = __reduce_max_sync(act, own_len);
   if ((threadIdx.x & 31) == (__ffs(act) - 1)) {
     atomicMax(maxcnt, wm);
     atomicMax(maxstaged, ws);
+    atomicMax(maxrow, wr);
   }
 }
 
@@ -478,11 +487,11 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
 }
 
 cudaError_t launch_neighbors(Ctx &c) {
-  cudaMemsetAsync(c.maxcnt, 0, sizeof(int32_t) * 2, c.stream);
+  cudaMemsetAsync(c.maxcnt, 0, sizeof(int32_t) * 3, c.stream);
   if (c.n == 0) return cudaGetLastError();
   neighbor_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W,
-                                                        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.cnt,
-                                                        c.maxcnt, c.maxstaged, c.err);
+                                                        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt,
+                                                        c.maxcnt, c.maxstaged, c.maxrow, c.err);
   return cudaGetLastError();
 }
 

@@ -24,10 +24,14 @@
 //    FP32 error is relative to the local temperature difference Delta.
 //    cosh and sinh(Delta)/Delta come from their Taylor series in Delta^2, with
 //    the order set per tile from the largest value spread of its rows (previous
-//    substep): spread < 0.02 -> to Delta^2; < 0.12 -> to Delta^4; otherwise to
-//    Delta^10 (|Delta| <= 1).  Truncation stays below 3e-8 of B in every tier.
-//  * Row tiles: one CTA per row of cells; the rows around it (at most 9) are
-//    copied into shared memory and neighbours are 16-bit indices into that tile.
+//    substep): spread < 1.2e-4 -> B = 1 - P; < 0.02 -> to Delta^2; < 0.12 -> to
+//    Delta^4; otherwise to Delta^10 (|Delta| <= 1).  Truncation stays below 3e-8
+//    of B in every tier.  Two atoms whose rows use different tiers differ in B
+//    by at most that bound; within a tier B is bit-identical on both sides.
+//  * Row tiles: a CTA takes one row of cells at a time; the rows around it (at
+//    most 9) are copied into shared memory by bulk copies (one producer warp,
+//    mbarrier completion, two buffers) and neighbours are 16-bit indices into
+//    that tile.
 //
 // Double-precision path (flux_prec = 1): gathers T itself and evaluates the pair
 // term as written in the paper with one exponential, E = e^{theta_lo - theta_hi}:
@@ -45,6 +49,11 @@ namespace {
 template <int TIER>
 __device__ __forceinline__ float pair_acc(float F, float di, float dj, float th, float ai, float m2ai) {
   const float D = dj - di;
+  if (TIER == 3) {                                                  // B = 1 - P
+    const float b = th + dj;
+    const float P = fmaf(m2ai, b, ai + b);
+    return fmaf(D, 1.0f - P, F);
+  }
   const float x = D * D;
   float S, C;
   if (TIER == 2) {
@@ -96,57 +105,69 @@ __device__ __forceinline__ void ff_add(float &h, float &l, float x) {
   h = hn;
 }
 
-// state update of one atom (single-precision path); returns the new hi
+// coefficients of the single-precision update, read once per item into registers
+struct CoefF {
+  double dtVG;
+  float dtK, dtcGn, Tmax, th;
+};
+
+__device__ __forceinline__ CoefF load_coef(const StepCoef *__restrict__ cf) {
+  CoefF c;
+  c.dtVG = cf->dtVG;
+  c.dtK = cf->dtK_f;
+  c.dtcGn = cf->dtcGn_f;
+  c.Tmax = cf->Tmax_f;
+  c.th = cf->th_ref;
+  return c;
+}
+
+// where the results of one system go
+struct OutPtrs {
+  float *hout, *lo;
+  double *A;
+  const float *srcw, *pulse_f;
+  int32_t *err;
+};
+
+// state update of one atom (single-precision path); Ai is the atom's exchanged
+// energy before this substep; returns the new hi
 template <bool LASER>
-__device__ __forceinline__ float update_atom(int64_t s, float di, float li, float ui, float F,
-                                             const StepCoef *__restrict__ cf, float *__restrict__ hout,
-                                             float *__restrict__ lo, double *__restrict__ A,
-                                             const float *__restrict__ srcw, const float *__restrict__ pulse_f, int k,
-                                             int32_t *__restrict__ err) {
-  float inc = cf->dtK_f * F;
+__device__ __forceinline__ float update_atom(int64_t s, float di, float li, float ui, double Ai, float F,
+                                             const CoefF &cf, const OutPtrs &o, int k) {
+  float inc = cf.dtK * F;
   const bool chi = (ui == ui);
   float d = 0.0f;
   if (chi) {
-    d = fmaf(cf->Tmax_f, di, ui);        // T_i - T_l,i
-    inc = fmaf(-cf->dtcGn_f, d, inc);
+    d = fmaf(cf.Tmax, di, ui);           // T_i - T_l,i
+    inc = fmaf(-cf.dtcGn, d, inc);
   }
   float h = di, l = li;
   ff_add(h, l, inc);
   if (LASER) {
-    const float c = pulse_f[k], w = srcw[s];
+    const float c = o.pulse_f[k], w = o.srcw[s];
     const float p = c * w;
     const float e = fmaf(c, w, -p);      // p + e == c * w exactly
     ff_add(h, l, p);
     ff_add(h, l, e);
   }
-  hout[s] = h;
-  lo[s] = l;
-  if (chi) A[s] = fma(cf->dtVG, f2d(d), A[s]);
-  const float th = cf->th_ref + h;
-  if (!(th >= 0.0f && th <= 1.0f)) atomicOr(err, ERR_RANGE);
+  o.hout[s] = h;
+  o.lo[s] = l;
+  if (chi) o.A[s] = fma(cf.dtVG, f2d(d), Ai);
+  const float th = cf.th + h;
+  if (!(th >= 0.0f && th <= 1.0f)) atomicOr(o.err, ERR_RANGE);
   return h;
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-
 // Tile descriptor of the row tile around row R of one system.  Neighbour row r
-// is placed at tile offset off[r], congruent to its first global index modulo
-// 4, so that its interior moves in 16-byte copies.  The system's arguments are
-// copied next to it, so every warp reads them from shared memory.
+// is placed at tile offset off[r]: after the previous row rounded up to 4
+// words, congruent to its first global index modulo 4, so that each row moves
+// as one 16-byte aligned bulk copy of its aligned superset.  The system's
+// arguments are copied next to it, so every warp reads them from shared memory.
 struct TileDesc {
   int32_t start[kRowNbr], len[kRowNbr], off[kRowNbr];
   int32_t self_base, row_s, row_len, tier, row;
-  int32_t pad[3];
+  int32_t staged;   // words the tile occupies
+  int32_t pad[2];
   RepArgs ra;
 };
 
@@ -176,12 +197,12 @@ __device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2
       mx = rr[nrows + R2];
     }
   }
-  // aligned placement, sequential over the 9 rows (same rule as the neighbour build)
+  // placement, sequential over the 9 rows (same rule as the neighbour build)
   int32_t off = 0, end = 0;
   for (int r = 0; r < kRowNbr; ++r) {
     const int32_t ar = __shfl_sync(0xffffffffu, a, r);
     const int32_t lr = __shfl_sync(0xffffffffu, len, r);
-    const int32_t o = end + ((ar - end) & 3);
+    const int32_t o = ((end + 3) & ~3) + (ar & 3);
     if (lane == r) off = o;
     end = o + lr;
   }
@@ -202,28 +223,52 @@ __device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2
     d->row_s = a;
     d->row_len = len;
     d->row = R;
+    d->staged = (end + 3) & ~3;
     const float spread = mx - mn;
-    d->tier = spread < 0.02f ? 2 : (spread < 0.12f ? 1 : 0);
+    d->tier = spread < 1.2e-4f ? 3 : (spread < 0.02f ? 2 : (spread < 0.12f ? 1 : 0));
   }
+  __syncwarp();
 }
 
-// warp w copies neighbour rows w, w + nwarps, ... of hin into buf: unaligned
-// head and tail in 4-byte copies, the interior in 16-byte copies
-__device__ __forceinline__ void stage_row(const TileDesc *d, const float *hin, float *buf) {
-  const int nw = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31;
-  for (int w = threadIdx.x >> 5; w < kRowNbr; w += nw) {
-    const int32_t a = d->start[w], len = d->len[w];
-    float *dst = buf + d->off[w];
-    const float *src = hin + a;
-    int32_t head = (4 - (a & 3)) & 3;
-    if (head > len) head = len;
-    if (lane < head) cp_async4(dst + lane, src + lane);
-    const int32_t nb = (len - head) >> 2;
-    for (int32_t c = lane; c < nb; c += 32) cp_async16(dst + head + 4 * c, src + head + 4 * c);
-    const int32_t tail0 = head + 4 * nb;
-    if (lane < len - tail0) cp_async4(dst + tail0 + lane, src + tail0 + lane);
-  }
+// ---- mbarrier and bulk-copy primitives (CTA scope) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+// arrive once and add `bytes` to the transaction count of the current phase
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the completion of the phase with the given parity; gives up (false)
+// after a bounded number of polls, each of which may suspend the thread briefly
+constexpr uint32_t kMaxPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+  for (uint32_t i = 0; i < kMaxPolls; ++i)
+    if (mbar_test(b, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+// that completes `bytes` transactions on barrier `bar`
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
 }
 
 template <int TIER, bool LASER, int PP>
@@ -240,91 +285,164 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, int parity, int k, 
       F = pair_acc<TIER>(F, di, tile[pv[m] & 0xffffu], th, ai, m2ai);
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
-  return update_atom<LASER>(s, di, li, ui, F, cf, ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, k,
-                            ra.err);
+  const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err};
+  return update_atom<LASER>(s, di, li, ui, ra.A[s], F, load_coef(cf), o, k);
 }
 
-// Persistent row-tile kernel over a work list of (system, row) items: each CTA
-// walks items blockIdx.x, +gridDim.x, ... and double-buffers the tiles: the
-// next item's tile is copied (cp.async) while the current one is computed.
+constexpr int kTileBufs = 2;   // tiles in flight per CTA
+
+struct TilePipe {
+  uint64_t full[kTileBufs];    // tile b holds its item (one arrival + the copied bytes)
+  uint64_t empty[kTileBufs];   // every compute warp is done with tile b
+  TileDesc desc[kTileBufs];
+  float wmin[kTileBufs][kTileThreads / 32], wmax[kTileBufs][kTileThreads / 32];
+};
+
+// producer side, after the compute warps released tile b: the row's value
+// range for the tier choice of the next substep
+__device__ __forceinline__ void close_item(TilePipe &sp, int b, int parity) {
+  if ((threadIdx.x & 31) == 0) {
+    float a = sp.wmin[b][0], c = sp.wmax[b][0];
+    for (int w = 1; w < kTileThreads / 32; ++w) {
+      a = fminf(a, sp.wmin[b][w]);
+      c = fmaxf(c, sp.wmax[b][w]);
+    }
+    const TileDesc &D = sp.desc[b];
+    float *rr = D.ra.rrange[parity ^ 1];
+    rr[D.row] = a;
+    rr[D.ra.nrows + D.row] = c;
+  }
+  __syncwarp();
+}
+
+// Persistent row-tile kernel over a work list of (system, row) items; CTA c
+// takes items c, c + gridDim.x, ...  Warp-specialised pipeline on two tile
+// buffers: the last warp writes each item's descriptor and fetches its 9 rows
+// with bulk copies (one lane, completion counted on full[b]); the compute warps
+// wait on full[b], sweep the row's atoms and arrive on empty[b], which the
+// producer waits for before reusing the buffer.  No CTA-wide barrier inside the
+// loop, so fast warps run ahead by up to one item.  Every wait is bounded: on
+// a timeout the warp records ERR_TIMEOUT and stops, and the producer waits
+// (bounded) for its copies in flight before leaving.
 // PP = 9: exactly nine index words per atom (18-neighbour FCC shells) in every
 // system; PP = 16: any count up to 32 neighbours, ra.P words.
 template <bool LASER, int PP>
 __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
     substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
                         int parity, int k) {
-  extern __shared__ float tiles[];
-  __shared__ TileDesc desc[3];
-  __shared__ float wmin[2][kTileThreads / 32], wmax[2][kTileThreads / 32];   // by iteration parity
-  int it_item = blockIdx.x;
-  if (it_item >= nwork) return;
-  const int warp = threadIdx.x >> 5;
-  const int aw = kTileThreads / 32;   // warps 0..aw-1 own atoms; warp aw prepares descriptors
-  if (warp == 0) make_desc(reps, work[it_item], parity, &desc[0]);
-  if (warp == 1 && it_item + (int)gridDim.x < nwork) make_desc(reps, work[it_item + gridDim.x], parity, &desc[1]);
+  extern __shared__ __align__(128) float tiles[];   // kTileBufs x tb words
+  __shared__ TilePipe sp;
+  if ((int)blockIdx.x >= nwork) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int aw = kTileThreads / 32;   // warps 0..aw-1 compute; warp aw produces
+  const int n_it = (nwork - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kTileBufs; ++b) {
+      mbar_init(&sp.full[b], 1);
+      mbar_init(&sp.empty[b], aw);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
   __syncthreads();
-  stage_row(&desc[0], desc[0].ra.dmir[parity], tiles);
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncthreads();
-  int it = 0;
-  // one barrier per item: at the end of an iteration every thread waits for its
-  // copies of the next tile, then the barrier makes them (and the descriptor of
-  // the item after next) visible and frees the consumed buffer for refilling.
-  for (; it_item < nwork; it_item += gridDim.x, ++it) {
-    const int dc = it % 3, dn = (it + 1) % 3, dnn = (it + 2) % 3;
-    const int buf = it & 1;
-    const int nxt = it_item + gridDim.x;
-    if (nxt < nwork) stage_row(&desc[dn], desc[dn].ra.dmir[parity], tiles + (buf ^ 1) * tb);
-    cp_async_commit();
-    if (warp == aw && nxt + (int)gridDim.x < nwork) make_desc(reps, work[nxt + gridDim.x], parity, &desc[dnn]);
-    const TileDesc &D = desc[dc];
+  if (warp == aw) {
+    int32_t *err = nullptr;
+    int issued = 0;
+    bool ok = true;
+    for (int it = 0; it < n_it && ok; ++it) {
+      const int b = it % kTileBufs;
+      const uint32_t use = (uint32_t)(it / kTileBufs);
+      if (use > 0) {
+        ok = mbar_wait(&sp.empty[b], (use - 1) & 1);
+        if (!ok) break;
+        close_item(sp, b, parity);
+      }
+      TileDesc *d = &sp.desc[b];
+      make_desc(reps, work[blockIdx.x + (int64_t)it * gridDim.x], parity, d);
+      err = d->ra.err;
+      if (lane == 0) {
+        const float *hin = d->ra.dmir[parity];
+        float *dst = tiles + (int64_t)b * tb;
+        // an empty row has nothing to update (and its tile is not covered by
+        // the build's largest-tile figure): copy nothing.  A row whose tile
+        // exceeds the buffer cannot occur after a build; if it did, it is
+        // skipped and reported.
+        if (d->row_len > 0 && d->staged > tb) {
+          atomicOr(d->ra.err, ERR_NBR_OVERFLOW);
+          d->row_len = 0;
+        }
+        const bool copy = d->row_len > 0;
+        uint32_t bytes = 0;
+        for (int r = 0; r < kRowNbr && copy; ++r) {
+          const int32_t a = d->start[r], len = d->len[r];
+          if (len > 0) bytes += (uint32_t)(((a + len + 3) & ~3) - (a & ~3)) * 4u;
+        }
+        mbar_arrive_expect(&sp.full[b], bytes);
+        for (int r = 0; r < kRowNbr && copy; ++r) {
+          const int32_t a = d->start[r], len = d->len[r];
+          if (len <= 0) continue;
+          const int32_t a0 = a & ~3, a1 = (a + len + 3) & ~3;
+          bulk_copy(dst + (d->off[r] - (a & 3)), hin + a0, (uint32_t)(a1 - a0) * 4u, &sp.full[b]);
+        }
+      }
+      __syncwarp();
+      issued = it + 1;
+    }
+    // release the last items: their row ranges
+    for (int it = (issued > kTileBufs ? issued - kTileBufs : 0); it < issued && ok; ++it) {
+      const int b = it % kTileBufs;
+      ok = mbar_wait(&sp.empty[b], (uint32_t)(it / kTileBufs) & 1);
+      if (ok) close_item(sp, b, parity);
+    }
+    if (!ok) {
+      if (lane == 0 && err) atomicOr(err, ERR_TIMEOUT);
+      // no copy may still be landing when the CTA leaves
+      for (int it = (issued > kTileBufs ? issued - kTileBufs : 0); it < issued; ++it)
+        mbar_wait(&sp.full[it % kTileBufs], (uint32_t)(it / kTileBufs) & 1);
+    }
+    return;
+  }
+  // compute warps
+  for (int it = 0; it < n_it; ++it) {
+    const int b = it % kTileBufs;
+    if (!mbar_wait(&sp.full[b], (uint32_t)(it / kTileBufs) & 1)) {
+      if (lane == 0) atomicOr(reps[0].err, ERR_TIMEOUT);
+      return;
+    }
+    const TileDesc &D = sp.desc[b];
     const int row_len = D.row_len, row_s = D.row_s, sb = D.self_base;
     const int tier = D.tier;
-    const float *tile = tiles + buf * tb;
+    const float *tile = tiles + (int64_t)b * tb;
+    const int64_t ps = D.ra.ps;
+    const uint32_t *pidx = D.ra.pidx;
     float vmin = 3.0e38f, vmax = -3.0e38f;
-    for (int q0 = 0; q0 < row_len; q0 += kTileThreads) {
-      const int q = q0 + threadIdx.x;
-      const bool act = q < row_len && warp < aw;
-      const int32_t s = row_s + (act ? q : 0);
-      const int32_t n = D.ra.n;
-      const uint32_t *pidx = D.ra.pidx;
+    for (int q = threadIdx.x; q < row_len; q += kTileThreads) {
+      const int32_t s = row_s + q;
       uint32_t pv[PP];
 #pragma unroll
       for (int m = 0; m < PP; ++m)
-        if (PP != 16 || m < D.ra.P) pv[m] = act ? __ldg(pidx + (m * n + s)) : 0u;
-      if (act) {
-        const float ui = D.ra.uTl[s];
-        const float li = D.ra.lo[s];
-        const float di = tile[sb + q];
-        float h;
-        if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-        else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-        else h = row_atom<0, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-        vmin = fminf(vmin, h);
-        vmax = fmaxf(vmax, h);
-      }
+        if (PP != 16 || m < D.ra.P) pv[m] = __ldg(pidx + (m * ps + s));
+      const float ui = D.ra.uTl[s];
+      const float li = D.ra.lo[s];
+      const float di = tile[sb + q];
+      float h;
+      if (tier == 3) h = row_atom<3, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+      else if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+      else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+      else h = row_atom<0, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+      vmin = fminf(vmin, h);
+      vmax = fmaxf(vmax, h);
     }
     for (int o = 16; o > 0; o >>= 1) {
       vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
       vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     }
-    if ((threadIdx.x & 31) == 0 && warp < aw) {
-      wmin[buf][warp] = vmin;
-      wmax[buf][warp] = vmax;
+    if (lane == 0) {
+      sp.wmin[b][warp] = vmin;
+      sp.wmax[b][warp] = vmax;
+      mbar_arrive(&sp.empty[b]);
     }
-    cp_async_wait<0>();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float a = wmin[buf][0], b = wmax[buf][0];
-      for (int w = 1; w < aw; ++w) {
-        a = fminf(a, wmin[buf][w]);
-        b = fmaxf(b, wmax[buf][w]);
-      }
-      float *rr = D.ra.rrange[parity ^ 1];
-      rr[D.row] = a;
-      rr[D.ra.nrows + D.row] = b;
-    }
+    __syncwarp();
   }
 }
 
@@ -356,7 +474,8 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
     for (int u = 0; u < 6; ++u) F = pair_acc<0>(F, di, dj[u], th, ai, m2ai);
   }
   for (; j < c; ++j) F = pair_acc<0>(F, di, __ldg(hin + __ldg(np + (int64_t)j * n)), th, ai, m2ai);
-  update_atom<LASER>(s, di, lo[s], uTl[s], F, cf, hout, lo, A, srcw, pulse_f, k, err);
+  const OutPtrs o = {hout, lo, A, srcw, pulse_f, err};
+  update_atom<LASER>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k);
 }
 
 // T (FP64) -> hi + lo of delta = (T - Tref) / Tmax
@@ -418,10 +537,11 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-// the row-tile kernel applies when two tiles fit in shared memory and the table
-// holds at most 32 neighbours per atom
+// the row-tile kernel applies when two buffers fit in shared memory and the
+// table holds at most 32 neighbours per atom
 bool tile_path(const Ctx &c) {
-  return c.p.flux_prec == 0 && c.W <= 32 && c.nwork > 0 && c.staged_max <= c.tile_floats;
+  const int w = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
+  return c.p.flux_prec == 0 && c.W <= 32 && c.nwork > 0 && c.staged_max <= c.tile_floats && c.tile_grid[w] > 0;
 }
 
 cudaError_t launch_split(Ctx &c, cudaStream_t st) {
@@ -454,14 +574,17 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
                                                               c.pulse, k, c.coef, c.err);
   } else if (tile_path(c)) {
     const int32_t P = (c.n_max + 1) / 2;
-    const size_t shm = sizeof(float) * 2 * (size_t)c.tile_floats;
-    const unsigned grid = (unsigned)(c.nwork < c.tile_grid ? c.nwork : c.tile_grid);
+    const int32_t tb = c.tile_floats;
+    const int32_t tg = c.tile_grid[P == 9 ? 0 : 1];
+    const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
+    const unsigned nt = kTileThreads + 32;
+    const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
     if (P == 9) {
-      if (laser) substep_tile_kernel<true, 9><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
-      else substep_tile_kernel<false, 9><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
+      if (laser) substep_tile_kernel<true, 9><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
+      else substep_tile_kernel<false, 9><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
     } else {
-      if (laser) substep_tile_kernel<true, 16><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
-      else substep_tile_kernel<false, 16><<<grid, kTileThreads + 32, shm, st>>>(c.reps, c.work, c.nwork, c.tile_floats, parity, k);
+      if (laser) substep_tile_kernel<true, 16><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
+      else substep_tile_kernel<false, 16><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
     }
   } else {
     if (laser)
@@ -478,32 +601,45 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
 // one substep of the row-tile kernel over an explicit work list (batched systems)
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
                                  int pairs, int parity, int k, cudaStream_t st) {
-  const size_t shm = sizeof(float) * 2 * (size_t)tb;
   const unsigned g = (unsigned)(nwork < grid ? nwork : grid);
   if (g == 0) return cudaSuccess;
-  if (pairs == 9) substep_tile_kernel<false, 9><<<g, kTileThreads + 32, shm, st>>>(reps, work, nwork, tb, parity, k);
-  else substep_tile_kernel<false, 16><<<g, kTileThreads + 32, shm, st>>>(reps, work, nwork, tb, parity, k);
+  const unsigned nt = kTileThreads + 32;
+  const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
+  if (pairs == 9) substep_tile_kernel<false, 9><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k);
+  else substep_tile_kernel<false, 16><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k);
   return cudaGetLastError();
 }
 
-// shared memory opt-in and resident CTAs per SM of the tile kernel for two
-// buffers of tb floats
-cudaError_t tile_setup(int tb, int *blocks_per_sm) {
-  const int bytes = (int)(sizeof(float) * 2 * (size_t)tb);
-  const void *fns[4] = {(const void *)substep_tile_kernel<true, 9>, (const void *)substep_tile_kernel<false, 9>,
-                        (const void *)substep_tile_kernel<true, 16>, (const void *)substep_tile_kernel<false, 16>};
-  for (const void *f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
+// Tile capacity with headroom for atoms drifting between cells (tiles are
+// resized only when a build outgrows them), the shared-memory opt-in of every
+// instance and the resident grid of each width (grid[0]: 9 index words,
+// grid[1]: 16).
+bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2]) {
+  const int32_t tb = ((staged + staged / 8 + 64 + 255) / 256) * 256;
+  const int64_t bytes = (int64_t)sizeof(float) * kTileBufs * tb;
+  if (bytes > kTileMaxBytes) return false;
+  const void *inst[2][2] = {{(const void *)substep_tile_kernel<true, 9>, (const void *)substep_tile_kernel<false, 9>},
+                            {(const void *)substep_tile_kernel<true, 16>, (const void *)substep_tile_kernel<false, 16>}};
+  int32_t g[2] = {0, 0};
+  for (int w = 0; w < 2; ++w) {
+    int bps = 1 << 30;
+    bool ok = true;
+    for (int l = 0; l < 2 && ok; ++l) {
+      int b = 0;
+      ok = cudaFuncSetAttribute(inst[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inst[w][l], kTileThreads + 32, (size_t)bytes) ==
+               cudaSuccess &&
+           b > 0;
+      bps = b < bps ? b : bps;
+    }
+    if (ok) g[w] = bps * num_sms;
   }
-  int b9 = 0, b16 = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b9, substep_tile_kernel<false, 9>,
-                                                                kTileThreads + 32, (size_t)bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, substep_tile_kernel<true, 16>, kTileThreads + 32,
-                                                    (size_t)bytes);
-  *blocks_per_sm = b9 < b16 ? b9 : b16;
-  return e;
+  cudaGetLastError();
+  if (g[0] == 0 && g[1] == 0) return false;
+  *tb_out = tb;
+  grid[0] = g[0];
+  grid[1] = g[1];
+  return true;
 }
 
 }  // namespace ehc
