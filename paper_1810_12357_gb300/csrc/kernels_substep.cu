@@ -290,24 +290,27 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, int parity, int k, 
 }
 
 constexpr int kTileBufs = 2;   // tiles in flight per CTA
+constexpr int kDescAhead = 2;  // descriptors are prepared this many items ahead of their copies
+constexpr int kDescRing = kTileBufs + kDescAhead + 1;
 
 struct TilePipe {
   uint64_t full[kTileBufs];    // tile b holds its item (one arrival + the copied bytes)
   uint64_t empty[kTileBufs];   // every compute warp is done with tile b
-  TileDesc desc[kTileBufs];
+  TileDesc desc[kDescRing];    // item it uses slot it % kDescRing
   float wmin[kTileBufs][kTileThreads / 32], wmax[kTileBufs][kTileThreads / 32];
 };
 
-// producer side, after the compute warps released tile b: the row's value
-// range for the tier choice of the next substep
-__device__ __forceinline__ void close_item(TilePipe &sp, int b, int parity) {
+// producer side, after the compute warps released tile b of item it: the row's
+// value range for the tier choice of the next substep
+__device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity) {
+  const int b = it % kTileBufs;
   if ((threadIdx.x & 31) == 0) {
     float a = sp.wmin[b][0], c = sp.wmax[b][0];
     for (int w = 1; w < kTileThreads / 32; ++w) {
       a = fminf(a, sp.wmin[b][w]);
       c = fmaxf(c, sp.wmax[b][w]);
     }
-    const TileDesc &D = sp.desc[b];
+    const TileDesc &D = sp.desc[it % kDescRing];
     float *rr = D.ra.rrange[parity ^ 1];
     rr[D.row] = a;
     rr[D.ra.nrows + D.row] = c;
@@ -317,8 +320,10 @@ __device__ __forceinline__ void close_item(TilePipe &sp, int b, int parity) {
 
 // Persistent row-tile kernel over a work list of (system, row) items; CTA c
 // takes items c, c + gridDim.x, ...  Warp-specialised pipeline on two tile
-// buffers: the last warp writes each item's descriptor and fetches its 9 rows
-// with bulk copies (one lane, completion counted on full[b]); the compute warps
+// buffers: the last warp writes each item's descriptor (two items ahead, so its
+// chain of dependent loads is off the critical path) and fetches the item's 9
+// rows with bulk copies as soon as a buffer frees (one lane, completion counted
+// on full[b]); the compute warps
 // wait on full[b], sweep the row's atoms and arrive on empty[b], which the
 // producer waits for before reusing the buffer.  No CTA-wide barrier inside the
 // loop, so fast warps run ahead by up to one item.  Every wait is bounded: on
@@ -349,16 +354,17 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
     int32_t *err = nullptr;
     int issued = 0;
     bool ok = true;
+    make_desc(reps, work[blockIdx.x], parity, &sp.desc[0]);
+    int made = 1;
     for (int it = 0; it < n_it && ok; ++it) {
       const int b = it % kTileBufs;
       const uint32_t use = (uint32_t)(it / kTileBufs);
       if (use > 0) {
         ok = mbar_wait(&sp.empty[b], (use - 1) & 1);
         if (!ok) break;
-        close_item(sp, b, parity);
+        close_item(sp, it - kTileBufs, parity);
       }
-      TileDesc *d = &sp.desc[b];
-      make_desc(reps, work[blockIdx.x + (int64_t)it * gridDim.x], parity, d);
+      TileDesc *d = &sp.desc[it % kDescRing];
       err = d->ra.err;
       if (lane == 0) {
         const float *hin = d->ra.dmir[parity];
@@ -387,12 +393,15 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       }
       __syncwarp();
       issued = it + 1;
+      // descriptors ahead: one after the first item's copies, then up to kDescAhead
+      const int want = (it == 0) ? 2 : it + 1 + kDescAhead;
+      for (; made < want && made < n_it; ++made)
+        make_desc(reps, work[blockIdx.x + (int64_t)made * gridDim.x], parity, &sp.desc[made % kDescRing]);
     }
     // release the last items: their row ranges
     for (int it = (issued > kTileBufs ? issued - kTileBufs : 0); it < issued && ok; ++it) {
-      const int b = it % kTileBufs;
-      ok = mbar_wait(&sp.empty[b], (uint32_t)(it / kTileBufs) & 1);
-      if (ok) close_item(sp, b, parity);
+      ok = mbar_wait(&sp.empty[it % kTileBufs], (uint32_t)(it / kTileBufs) & 1);
+      if (ok) close_item(sp, it, parity);
     }
     if (!ok) {
       if (lane == 0 && err) atomicOr(err, ERR_TIMEOUT);
@@ -409,7 +418,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       if (lane == 0) atomicOr(reps[0].err, ERR_TIMEOUT);
       return;
     }
-    const TileDesc &D = sp.desc[b];
+    const TileDesc &D = sp.desc[it % kDescRing];
     const int row_len = D.row_len, row_s = D.row_s, sb = D.self_base;
     const int tier = D.tier;
     const float *tile = tiles + (int64_t)b * tb;
