@@ -183,6 +183,17 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
 //   pidx [W/2][ps] the same neighbours as 16-bit indices into the row tile (the
 //        concatenation of the neighbour rows), two per word; unused slots up to
 //        W hold the atom's own tile index, whose pair term is exactly zero.
+// FAST: every periodic axis has at least 3 cells.  Cells are at least r_c wide,
+// so a pair within r_c sits in adjacent cells and its minimum image is the
+// image of that cell offset: the shift (0 or +-L) is fixed per neighbour row
+// (y, z) and per cell (x), and the per-pair test is branch-free (the unsigned
+// 64-bit sum of squares cannot overflow).  Otherwise each difference takes its
+// minimum image separately, as in the oracle.
+__device__ __forceinline__ uint32_t wrap_shift(int32_t dcell, int64_t L) {
+  return dcell > 1 ? (uint32_t)(-L) : (dcell < -1 ? (uint32_t)L : 0u);
+}
+
+template <bool FAST>
 __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
                                                        const int32_t *__restrict__ start,
                                                        const int32_t *__restrict__ row_nbr, int32_t W,
@@ -232,28 +243,56 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
       self_local = prefix + (s - rs);
       own_len = re - rs;
     }
-    for (int ix = 0; ix < nx; ++ix) {
-      const int32_t cell = R2 * ncx + xo[ix];
-      const int32_t t1 = start[cell + 1];
-      for (int32_t t = start[cell]; t < t1; ++t) {
-        if (t == s) continue;
-        const int4 qj = q_s[t];
-        int32_t dx = qj.x - qi.x;
-        if (g.per[0]) dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
-        if (dx > rcq || dx < -rcq) continue;
-        int32_t dy = qj.y - qi.y;
-        if (g.per[1]) dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
-        if (dy > rcq || dy < -rcq) continue;
-        int32_t dz = qj.z - qi.z;
-        if (g.per[2]) dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
-        if (dz > rcq || dz < -rcq) continue;
-        const int64_t d2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
-        if (d2 <= rc2) {
-          if (m < W) {
-            nbr[(int64_t)m * n + s] = t;
-            pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+    if (FAST) {
+      const int32_t ny = g.nc[1];
+      // dx = qj.x + ox (mod 2^32) is the minimum-image difference for every pair within r_c
+      const uint32_t oy = wrap_shift(R2 % ny - R % ny, g.Lq[1]) - (uint32_t)qi.y;
+      const uint32_t oz = wrap_shift(R2 / ny - R / ny, g.Lq[2]) - (uint32_t)qi.z;
+      const uint64_t rc2u = (uint64_t)rc2;
+      for (int ix = 0; ix < nx; ++ix) {
+        const int32_t cell = R2 * ncx + xo[ix];
+        const uint32_t ox = wrap_shift(xo[ix] - cx, g.Lq[0]) - (uint32_t)qi.x;
+        const int32_t t1 = start[cell + 1];
+        for (int32_t t = start[cell]; t < t1; ++t) {
+          const int4 qj = q_s[t];
+          const int32_t dx = (int32_t)((uint32_t)qj.x + ox);
+          const int32_t dy = (int32_t)((uint32_t)qj.y + oy);
+          const int32_t dz = (int32_t)((uint32_t)qj.z + oz);
+          const uint64_t d2 = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                              (uint64_t)((int64_t)dz * dz);
+          if (d2 <= rc2u && t != s) {
+            if (m < W) {
+              nbr[(int64_t)m * n + s] = t;
+              pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+            }
+            ++m;
           }
-          ++m;
+        }
+      }
+    } else {
+      for (int ix = 0; ix < nx; ++ix) {
+        const int32_t cell = R2 * ncx + xo[ix];
+        const int32_t t1 = start[cell + 1];
+        for (int32_t t = start[cell]; t < t1; ++t) {
+          if (t == s) continue;
+          const int4 qj = q_s[t];
+          int32_t dx = qj.x - qi.x;
+          if (g.per[0]) dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
+          if (dx > rcq || dx < -rcq) continue;
+          int32_t dy = qj.y - qi.y;
+          if (g.per[1]) dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
+          if (dy > rcq || dy < -rcq) continue;
+          int32_t dz = qj.z - qi.z;
+          if (g.per[2]) dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+          if (dz > rcq || dz < -rcq) continue;
+          const int64_t d2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+          if (d2 <= rc2) {
+            if (m < W) {
+              nbr[(int64_t)m * n + s] = t;
+              pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+            }
+            ++m;
+          }
         }
       }
     }
@@ -489,9 +528,12 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
 cudaError_t launch_neighbors(Ctx &c) {
   cudaMemsetAsync(c.maxcnt, 0, sizeof(int32_t) * 3, c.stream);
   if (c.n == 0) return cudaGetLastError();
-  neighbor_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W,
-                                                        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt,
-                                                        c.maxcnt, c.maxstaged, c.maxrow, c.err);
+  bool fast = true;
+  for (int k = 0; k < 3; ++k) fast = fast && (!c.g.per[k] || c.g.nc[k] >= 3);
+  auto kern = fast ? neighbor_kernel<true> : neighbor_kernel<false>;
+  kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
+                                             reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt,
+                                             c.maxstaged, c.maxrow, c.err);
   return cudaGetLastError();
 }
 
