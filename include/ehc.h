@@ -38,7 +38,8 @@ extern "C" {
 #define EHC_E_NOMEM (-2)        /* device or host allocation failed */
 #define EHC_E_CUDA (-3)         /* CUDA runtime error */
 #define EHC_E_UNSTABLE (-4)     /* substep violates dt (2 n_max K + G/C_e) <= 2 */
-#define EHC_E_RANGE (-5)        /* theta = T/T_max left [0,1] or became NaN */
+#define EHC_E_RANGE (-5)        /* theta = T/T_max left [0,1] or became NaN, or a velocity
+                                   component reached 256 A/fs (or NaN) at a build */
 #define EHC_E_NBR_OVERFLOW (-6) /* an atom has more neighbours than max_neighbors */
 #define EHC_E_TIMEOUT (-7)      /* a bounded device wait gave up */
 #define EHC_E_STATE (-8)        /* call order violated (e.g. substep before build) */

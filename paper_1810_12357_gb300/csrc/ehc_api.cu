@@ -43,7 +43,7 @@ cudaError_t dalloc(T **p, size_t count) {
 int err_code(int32_t bits) {
   if (bits & ERR_BOUNDS) return EHC_E_BOUNDS;
   if (bits & ERR_NBR_OVERFLOW) return EHC_E_NBR_OVERFLOW;
-  if (bits & ERR_RANGE) return EHC_E_RANGE;
+  if (bits & (ERR_RANGE | ERR_SPEED)) return EHC_E_RANGE;
   if (bits & ERR_TIMEOUT) return EHC_E_TIMEOUT;
   return EHC_OK;
 }

@@ -13,6 +13,7 @@
 //   A     double[N]     energy handed from electrons to the lattice this MD step [eV]
 //   Tl_f  float [N]     local lattice temperature (negative: atom below the guard)
 //   Tl_d  double[N]     same in FP64 (for the FP64 flux path and diagnostics)
+//   v_s   VelQ  [N]     velocity on a 2^-48 A/fs integer grid and |v|^2 (FP64), sorted
 #pragma once
 
 #include <cuda_bf16.h>
@@ -32,6 +33,25 @@ enum DevErr : int32_t {
   ERR_BOUNDS = 4,        // atom outside a non-periodic extent
   ERR_TIMEOUT = 8,       // bounded wait gave up
   ERR_NEG_KE = 16,       // (informational) kinetic energy could not pay A_i
+  ERR_SPEED = 32,        // a velocity component outside the fixed-point range (|v| >= 256 A/fs or NaN)
+};
+
+// Sorted velocity of one atom: components on a fixed-point grid of 2^-48 A/fs
+// (|v| < 256 A/fs, so sums over an atom and up to 64 neighbours stay exact in
+// int64) and |v|^2 in FP64.
+constexpr double kVelScale = 281474976710656.0;   // 2^48
+constexpr double kVelUnit = 1.0 / kVelScale;
+constexpr double kVelMax = 256.0;
+struct __align__(32) VelQ {
+  long long x, y, z;
+  double w;
+};
+
+// exact reciprocals of 1..kMaxWidth+1 and of (3/2) k_B times the same counts,
+// for the lattice temperature (one rounding instead of a division per atom)
+struct RecipTab {
+  double inv_n[kMaxWidth + 2];
+  double inv_dof[kMaxWidth + 2];
 };
 
 struct MassTable {
@@ -163,7 +183,7 @@ struct Ctx {
   int32_t *inv_perm[2] = {nullptr, nullptr};
   int cur_inv = 0;
   int4 *q_s = nullptr;           // sorted positions + cell id
-  double4_32a *v_s = nullptr;        // sorted velocities and |v|^2
+  VelQ *v_s = nullptr;           // sorted velocities (fixed point) and |v|^2
   int32_t *nbr = nullptr;        // [W][N]
   uint32_t *pidx = nullptr;      // [W/2][ps] pairs of 16-bit tile-local neighbour indices
   int64_t ps = 0;                // plane stride of pidx: N rounded up to a multiple of 4

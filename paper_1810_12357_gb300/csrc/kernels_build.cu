@@ -151,18 +151,24 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
                               const int32_t *__restrict__ inv_old, int src_is_orig,
                               const double *__restrict__ T_old, const double *__restrict__ A_old,
                               int32_t *__restrict__ inv_new, int4 *__restrict__ q_s,
-                              double4_32a *__restrict__ v_s, int8_t *__restrict__ type_s,
+                              VelQ *__restrict__ v_s, int8_t *__restrict__ type_s,
                               double *__restrict__ T_new, double *__restrict__ A_new,
                               float *__restrict__ dmir0, double Tref, double invTmax,
                               const double *__restrict__ depth, float *__restrict__ srcw,
-                              double *__restrict__ srcw_d, double inv_lp) {
+                              double *__restrict__ srcw_d, double inv_lp, int32_t *__restrict__ err) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int32_t o = perm[s];
   q_s[s] = q[o];
   inv_new[o] = (int32_t)s;
   const double vx = v[3 * (int64_t)o + 0], vy = v[3 * (int64_t)o + 1], vz = v[3 * (int64_t)o + 2];
-  v_s[s] = make_double4_32a(vx, vy, vz, vx * vx + vy * vy + vz * vz);
+  if (!(fabs(vx) < kVelMax && fabs(vy) < kVelMax && fabs(vz) < kVelMax)) atomicOr(err, ERR_SPEED);
+  VelQ vq;
+  vq.x = __double2ll_rn(vx * kVelScale);
+  vq.y = __double2ll_rn(vy * kVelScale);
+  vq.z = __double2ll_rn(vz * kVelScale);
+  vq.w = vx * vx + vy * vy + vz * vz;
+  v_s[s] = vq;
   int32_t ty = type_orig ? type_orig[o] : 0;
   type_s[s] = (int8_t)(ty < 0 ? 0 : (ty >= kMaxTypes ? kMaxTypes - 1 : ty));
   int64_t src = src_is_orig ? (int64_t)o : (int64_t)inv_old[o];
@@ -316,53 +322,52 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
 
 // Sec. 2: T_i^lat = sum_S (1/2) m |v - v_com|^2 / ((3/2) k_B N_j) over S = {i} + neighbours.
 // With M = sum m, P = sum m v, W = sum m |v|^2:  sum (1/2) m |v - v_com|^2 = (W - |P|^2 / M) / 2.
-// One atom type: M = m N_j, P = m sum v, W = m sum |v|^2 (four FP64 additions per neighbour).
+// One atom type: M = m N_j, P = m sum v with sum v exact on the 2^-48 grid
+// (int64), W = m sum |v|^2 (one FP64 addition per neighbour).  Several types:
+// FP64 sums of m v and m |v|^2.
 template <bool ONE_TYPE>
 __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
-                                    const double4_32a *__restrict__ v_s, const int8_t *__restrict__ type_s,
-                                    MassTable mt, int dof_mode, double eps_ke, double Tref,
+                                    const VelQ *__restrict__ v_s, const int8_t *__restrict__ type_s,
+                                    MassTable mt, RecipTab rt, int dof_mode, double eps_ke, double Tref,
                                     double *__restrict__ Tl_d, float *__restrict__ Tl_f, float *__restrict__ uTl) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int c = cnt[s];
-  const double4_32a vi = v_s[s];
-  double M, px, py, pz, W;
+  const VelQ vi = v_s[s];
+  double ke;
   if (ONE_TYPE) {
-    double sx = vi.x, sy = vi.y, sz = vi.z, sw = vi.w;
+    long long qx = vi.x, qy = vi.y, qz = vi.z;
+    double sw = vi.w;
     for (int k = 0; k < c; ++k) {
-      const double4_32a vj = v_s[nbr[(int64_t)k * n + s]];
-      sx += vj.x;
-      sy += vj.y;
-      sz += vj.z;
+      const VelQ vj = v_s[nbr[(int64_t)k * n + s]];
+      qx += vj.x;
+      qy += vj.y;
+      qz += vj.z;
       sw += vj.w;
     }
-    const double m = mt.m[0];
-    M = m * (double)(c + 1);
-    px = m * sx;
-    py = m * sy;
-    pz = m * sz;
-    W = m * sw;
+    const double sx = (double)qx * kVelUnit, sy = (double)qy * kVelUnit, sz = (double)qz * kVelUnit;
+    ke = 0.5 * mt.m[0] * (sw - (sx * sx + sy * sy + sz * sz) * rt.inv_n[c + 1]) * kMVV;
   } else {
     const double mi = mt.m[type_s[s]];
-    M = mi;
-    px = mi * vi.x;
-    py = mi * vi.y;
-    pz = mi * vi.z;
-    W = mi * vi.w;
+    double M = mi;
+    double px = mi * ((double)vi.x * kVelUnit);
+    double py = mi * ((double)vi.y * kVelUnit);
+    double pz = mi * ((double)vi.z * kVelUnit);
+    double W = mi * vi.w;
     for (int k = 0; k < c; ++k) {
       const int32_t t = nbr[(int64_t)k * n + s];
-      const double4_32a vj = v_s[t];
+      const VelQ vj = v_s[t];
       const double mj = mt.m[type_s[t]];
       M += mj;
-      px += mj * vj.x;
-      py += mj * vj.y;
-      pz += mj * vj.z;
+      px += mj * ((double)vj.x * kVelUnit);
+      py += mj * ((double)vj.y * kVelUnit);
+      pz += mj * ((double)vj.z * kVelUnit);
       W += mj * vj.w;
     }
+    ke = 0.5 * (W - (px * px + py * py + pz * pz) / M) * kMVV;
   }
-  const double ke = 0.5 * (W - (px * px + py * py + pz * pz) / M) * kMVV;
-  const double dof = (dof_mode == 1) ? (double)c : (double)(c + 1);
-  double T = dof > 0 ? ke / (1.5 * kKB * dof) : 0.0;
+  const int dof = (dof_mode == 1) ? c : c + 1;
+  double T = dof > 0 ? ke * rt.inv_dof[dof] : 0.0;
   const double Ks = 0.5 * mt.m[ONE_TYPE ? 0 : type_s[s]] * vi.w * kMVV;
   const bool chi = Ks >= eps_ke;
   if (!chi) T = -1.0;
@@ -402,7 +407,7 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
 }
 
 // partial sums per block: [0] sum T, [1] max T, [2] sum KE (eV), [3] sum srcw
-__global__ void globals_partial(int64_t n, const double *__restrict__ T, const double4_32a *__restrict__ v_s,
+__global__ void globals_partial(int64_t n, const double *__restrict__ T, const VelQ *__restrict__ v_s,
                                 const int8_t *__restrict__ type_s, MassTable mt,
                                 const float *__restrict__ srcw, const double *__restrict__ srcw_d,
                                 double *__restrict__ part) {
@@ -516,7 +521,7 @@ cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
     gather_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
         c.n, c.perm, c.q_orig, v, c.type_orig, c.inv_perm[c.cur_inv], src_is_orig ? 1 : 0, c.T[c.tcur], c.A,
         c.inv_perm[nxt], c.q_s, c.v_s, c.type_s, c.T[tn], c.A_tmp, c.dmir[0], c.p.Tref_K, 1.0 / c.p.Tmax_K,
-        laser ? c.depth_orig : nullptr, c.srcw, c.srcw_d, laser ? 1.0 / c.p.laser_lp_A : 0.0);
+        laser ? c.depth_orig : nullptr, c.srcw, c.srcw_d, laser ? 1.0 / c.p.laser_lp_A : 0.0, c.err);
   c.cur_inv = nxt;
   c.tcur = tn;
   // A keeps its address (captured substep graphs and the tile argument table hold it)
@@ -539,12 +544,17 @@ cudaError_t launch_neighbors(Ctx &c) {
 
 cudaError_t launch_lattice_temperature(Ctx &c) {
   if (c.n == 0) return cudaGetLastError();
+  RecipTab rt;
+  for (int k = 0; k < kMaxWidth + 2; ++k) {
+    rt.inv_n[k] = k > 0 ? 1.0 / (double)k : 0.0;
+    rt.inv_dof[k] = k > 0 ? 1.0 / (1.5 * kKB * (double)k) : 0.0;
+  }
   if (c.mt.n_types == 1)
-    lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt,
+    lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,
                                                                     c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
                                                                     c.Tl_d, c.Tl_f, c.uTl);
   else
-    lattice_temp_kernel<false><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt,
+    lattice_temp_kernel<false><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,
                                                                      c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
                                                                      c.Tl_d, c.Tl_f, c.uTl);
   return cudaGetLastError();

@@ -58,11 +58,28 @@ __device__ __forceinline__ void gauss3(uint64_t id, uint64_t step, uint64_t seed
   g[2] = r2 * cospif(2.0f * u3);
 }
 
+// s = sqrt(target / Kw) without an FP64 division or square root: Newton's
+// method for f(y) = Kw y^2 - target, started from the single-precision root and
+// stepped twice in FP64 with a single-precision 1 / f'(y0) (each step squares
+// the relative error, 1e-7 -> 1e-14 -> rounding).  Outside the normal
+// single-precision range the plain FP64 expression is used.
+__device__ __forceinline__ double scale_root(double target, double Kw) {
+  if (!(target > 1.0e-30 && target < 1.0e30 && Kw > 1.0e-30 && Kw < 1.0e30)) return sqrt(target / Kw);
+  const float kf = (float)Kw;
+  const float yf = sqrtf((float)target / kf);
+  const double c = (double)(0.5f / (kf * yf));   // ~ 1 / (2 Kw y)
+  double y = (double)yf;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = fma(fma(-Kw * y, y, target), c, y);
+  return y;
+}
+
 __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ type_s,
-                              MassTable mt, const double *__restrict__ Tl, double *__restrict__ A,
+                              MassTable mt, double kv, double kv0, const double *__restrict__ Tl,
+                              double *__restrict__ A,
                               double *__restrict__ T, double *__restrict__ v, double *__restrict__ dKE,
-                              int mode, int frozen, uint64_t seed, uint64_t md_step, double e1,
-                              double one_m_e2, double inv_VC, unsigned long long *__restrict__ n_stopped) {
+                              int mode, int frozen, uint64_t seed, uint64_t md_step, double e1, double inv_VC,
+                              unsigned long long *__restrict__ n_stopped) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double Ai = A[s];
@@ -76,7 +93,8 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
     return;
   }
   const int64_t o = perm[s];
-  const double m = mt.m[type_s[s]];
+  const int ty = type_s[s];
+  const double m = mt.m[ty];
   double *vi = v + 3 * o;
   const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
   const double K0 = 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2) * kMVV;
@@ -90,13 +108,15 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
     float g[3];
     gauss3((uint64_t)o, md_step, seed, g);
     // noise amplitude in single precision (it multiplies a single-precision normal)
-    const float sig = sqrtf((float)(kKB * one_m_e2 / (m * kMVV) * T[s]));
+    // variance factor k_B (1 - e^{-2 g dt}) / (m kMVV) = kv / (m kMVV), for type 0 from the host
+    const double cv = (ty == 0) ? kv0 : kv / (m * kMVV);
+    const float sig = sqrtf((float)(cv * T[s]));
     w0 = v0 * e1 + (double)(sig * g[0]);
     w1 = v1 * e1 + (double)(sig * g[1]);
     w2 = v2 * e1 + (double)(sig * g[2]);
   }
   const double Kw = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
-  const double sc = Kw > 0.0 ? sqrt(target / Kw) : 0.0;
+  const double sc = (Kw > 0.0 && target > 0.0) ? scale_root(target, Kw) : 0.0;
   vi[0] = w0 * sc;
   vi[1] = w1 * sc;
   vi[2] = w2 * sc;
@@ -144,29 +164,26 @@ __device__ __forceinline__ bool ge_bits(double y, double L) {   // y >= L for y 
   return __double_as_longlong(y) >= __double_as_longlong(L);
 }
 
-__global__ void drift_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ v, double dt,
+// one thread per coordinate (coalesced over the flat [N][3] arrays)
+__global__ void drift_kernel(int64_t n3, double *__restrict__ x, const double *__restrict__ v, double dt,
                              double L0, double L1, double L2, int p0, int p1, int p2) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double *xi = x + 3 * i;
-  const double *vi = v + 3 * i;
-  const double L[3] = {L0, L1, L2};
-  const int per[3] = {p0, p1, p2};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    // no contraction: x + v dt rounds the product and the sum separately
-    double y = __dadd_rn(xi[k], __dmul_rn(vi[k], dt));
-    if (per[k]) {
-      // one period at most per step; the same result as a floored modulo
-      if (neg_bits(y) && y != 0.0) y += L[k];
-      else if (ge_bits(y, L[k])) y -= L[k];
-      if ((neg_bits(y) && y != 0.0) || (!neg_bits(y) && __double_as_longlong(y) > __double_as_longlong(L[k]))) {
-        y = fmod(y, L[k]);
-        if (y < 0.0) y += L[k];
-      }
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n3) return;
+  const int k = (int)(j % 3);
+  const double L = k == 0 ? L0 : (k == 1 ? L1 : L2);
+  const int per = k == 0 ? p0 : (k == 1 ? p1 : p2);
+  // no contraction: x + v dt rounds the product and the sum separately
+  double y = __dadd_rn(x[j], __dmul_rn(v[j], dt));
+  if (per) {
+    // one period at most per step; the same result as a floored modulo
+    if (neg_bits(y) && y != 0.0) y += L;
+    else if (ge_bits(y, L)) y -= L;
+    if ((neg_bits(y) && y != 0.0) || (!neg_bits(y) && __double_as_longlong(y) > __double_as_longlong(L))) {
+      y = fmod(y, L);
+      if (y < 0.0) y += L;
     }
-    xi[k] = y;
   }
+  x[j] = y;
 }
 
 __global__ void philox_normals_kernel(const int64_t *__restrict__ ids, int64_t n, uint64_t step, uint64_t seed,
@@ -189,10 +206,12 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
   const double gdt = c.gammaL * dt_md;
   const double e1 = std::exp(-gdt);
   const double one_m_e2 = 1.0 - std::exp(-2.0 * gdt);
+  const double kv = kKB * one_m_e2;
+  const double kv0 = kv / (c.mt.m[0] * kMVV);
   if (c.n > 0)
     couple_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
-        c.n, c.perm, c.type_s, c.mt, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode, c.p.frozen, c.p.seed,
-        (uint64_t)c.md_step, e1, one_m_e2, 1.0 / c.VC, reinterpret_cast<unsigned long long *>(c.scal + 9));
+        c.n, c.perm, c.type_s, c.mt, kv, kv0, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode, c.p.frozen, c.p.seed,
+        (uint64_t)c.md_step, e1, 1.0 / c.VC, reinterpret_cast<unsigned long long *>(c.scal + 9));
   sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
   sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
   return cudaGetLastError();
@@ -200,8 +219,8 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
 
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt) {
   if (c.n > 0)
-    drift_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, x, v, dt, c.box[0], c.box[1], c.box[2],
-                                                           c.g.per[0], c.g.per[1], c.g.per[2]);
+    drift_kernel<<<nblk(3 * c.n, 256), 256, 0, c.stream>>>(3 * c.n, x, v, dt, c.box[0], c.box[1], c.box[2],
+                                                               c.g.per[0], c.g.per[1], c.g.per[2]);
   return cudaGetLastError();
 }
 

@@ -353,3 +353,16 @@ def test_laser_slab_source(flux_prec):
     assert eg["E_src"] == pytest.approx(eo["E_src"], rel=1e-6 if flux_prec == 0 else 1e-12)
     assert abs(eg["drift"]) < 1e-9
     assert abs(eo["drift"]) < 1e-12
+
+
+def test_speed_outside_fixed_point_range_refused():
+    # velocity components are summed exactly on a 2^-48 A/fs grid, which holds |v| < 256 A/fs
+    torch = _torch()
+    from paper_1810_12357_gb300 import Ehc, EhcError
+    s = I.hot_spot_system(4, 2)
+    s.v[7, 1] = -300.0
+    g = Ehc(I.params_hotspot_fp64(), s)
+    g.set_te(s.Te)
+    with pytest.raises(EhcError) as e:
+        g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
+    assert e.value.code == -5
