@@ -176,9 +176,11 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
   T_new[s] = T;
   A_new[s] = A_old[src];
   dmir0[s] = (float)((T - Tref) * invTmax);
-  const double w = depth ? exp(-depth[o] * inv_lp) : 0.0;
-  srcw[s] = (float)w;
-  srcw_d[s] = w;
+  if (depth) {   // source weights only with a laser source (nothing reads them otherwise)
+    const double w = exp(-depth[o] * inv_lp);
+    srcw[s] = (float)w;
+    srcw_d[s] = w;
+  }
 }
 
 // One thread per atom.  Candidates come from the atom's (deduplicated) neighbour
@@ -213,8 +215,9 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
   const int32_t ncx = g.nc[0];
   const int32_t cx = qi.w % ncx;
   const int32_t R = qi.w / ncx;
-  int32_t xo[3];
+  int32_t xo[3] = {0, 0, 0};
   int nx = 0;
+#pragma unroll
   for (int d = -1; d <= 1; ++d) {
     int32_t c = cx + d;
     if (g.per[0]) {
@@ -226,6 +229,33 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
     bool dup = false;
     for (int m = 0; m < nx; ++m) dup |= (xo[m] == c);
     if (!dup) xo[nx++] = c;
+  }
+  // FAST: the cells xo[] in visit order form at most two runs of consecutive
+  // cell indices (the second after a periodic wrap), i.e. at most two
+  // contiguous atom ranges per neighbour row, each with one x image shift
+  int nseg = 0;
+  int32_t seg_lo[2] = {0, 0}, seg_hi[2] = {-1, -1};
+  uint32_t seg_shift[2] = {0u, 0u};
+  if (FAST) {
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      if (ix >= nx) break;
+      const int32_t c = xo[ix];
+      if (ix > 0 && c == xo[ix - 1] + 1) {
+        if (nseg == 1) seg_hi[0] = c;
+        else seg_hi[1] = c;
+      } else {
+        const uint32_t sh = wrap_shift(c - cx, g.Lq[0]);
+        if (nseg == 0) {
+          seg_lo[0] = seg_hi[0] = c;
+          seg_shift[0] = sh;
+        } else {
+          seg_lo[1] = seg_hi[1] = c;
+          seg_shift[1] = sh;
+        }
+        ++nseg;
+      }
+    }
   }
   const int32_t L0 = (int32_t)g.Lq[0], L1 = (int32_t)g.Lq[1], L2 = (int32_t)g.Lq[2];
   const int32_t h0 = L0 >> 1, h1 = L1 >> 1, h2 = L2 >> 1;
@@ -255,11 +285,13 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
       const uint32_t oy = wrap_shift(R2 % ny - R % ny, g.Lq[1]) - (uint32_t)qi.y;
       const uint32_t oz = wrap_shift(R2 / ny - R / ny, g.Lq[2]) - (uint32_t)qi.z;
       const uint64_t rc2u = (uint64_t)rc2;
-      for (int ix = 0; ix < nx; ++ix) {
-        const int32_t cell = R2 * ncx + xo[ix];
-        const uint32_t ox = wrap_shift(xo[ix] - cx, g.Lq[0]) - (uint32_t)qi.x;
-        const int32_t t1 = start[cell + 1];
-        for (int32_t t = start[cell]; t < t1; ++t) {
+      const int32_t *rowst = start + (int64_t)R2 * ncx;
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        if (sg >= nseg) break;
+        const uint32_t ox = seg_shift[sg] - (uint32_t)qi.x;
+        const int32_t t1 = rowst[seg_hi[sg] + 1];
+        for (int32_t t = rowst[seg_lo[sg]]; t < t1; ++t) {
           const int4 qj = q_s[t];
           const int32_t dx = (int32_t)((uint32_t)qj.x + ox);
           const int32_t dy = (int32_t)((uint32_t)qj.y + oy);
