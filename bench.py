@@ -220,18 +220,30 @@ def _e2e(args, s, p, n, barrier, stream):
     return e2e_ms
 
 
-def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
+def max_over_ranks(vals, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    replica sets the job time)."""
     import torch
+    t = torch.tensor(list(vals), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_value(ws, n_atoms, n_sub, steps, ms):
+    """Whole-job atom-substeps/s: every replica advanced n_atoms atoms by
+    n_sub substeps per step for `steps` steps within `ms` milliseconds."""
+    return ws * n_atoms * n_sub * steps / (ms * 1e-3)
+
+
+def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
     if ws > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+        ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, dev)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
     ms_step = ms / args.steps
-    value = ws * n * N_SUB * args.steps / (ms * 1e-3)
+    value = job_value(ws, n, N_SUB, args.steps, ms)
     sub_launch_ms = statistics.mean(sub_ms) / N_SUB
     achieved = B_ALG * n / (sub_launch_ms * 1e-3) / 1e9
     peak, kind = _peaks()
@@ -242,7 +254,7 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "vs_baseline": None, "dtype": "f32 pair flux / f64 state", "data": "synthetic",
         "config": config_dict(args.cells, n, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                               "path": "plain"}),
-        "e2e": ({"value": ws * n * N_SUB / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
