@@ -169,6 +169,7 @@ struct TileDesc {
   int32_t staged;   // words the tile occupies
   int32_t pad[2];
   RepArgs ra;
+  StepCoef cf;      // the system's step coefficients (a copy, read from shared memory)
 };
 
 // computed by one warp: lane r < 9 handles neighbour row r
@@ -180,6 +181,12 @@ __device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2
   uint64_t *dst = reinterpret_cast<uint64_t *>(&d->ra);
   for (int w = lane; w < (int)(sizeof(RepArgs) / 8); w += 32) dst[w] = __ldg(src + w);
   __syncwarp();
+  static_assert(sizeof(StepCoef) % 8 == 0, "StepCoef must be a whole number of 8-byte words");
+  {
+    const uint64_t *cs = reinterpret_cast<const uint64_t *>(d->ra.cf);
+    uint64_t *cd = reinterpret_cast<uint64_t *>(&d->cf);
+    for (int w = lane; w < (int)(sizeof(StepCoef) / 8); w += 32) cd[w] = __ldg(cs + w);
+  }
   const int R = item.y;
   const int32_t ncx = d->ra.ncx;
   const int32_t *row_nbr = d->ra.row_nbr;
@@ -272,9 +279,9 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 }
 
 template <int TIER, bool LASER, int PP>
-__device__ __forceinline__ float row_atom(const RepArgs &ra, int parity, int k, const float *tile, int32_t s,
-                                          float di, const uint32_t *pv, float ui, float li) {
-  const StepCoef *cf = ra.cf;
+__device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, int parity, int k,
+                                          const float *tile, int32_t s, float di, const uint32_t *pv, float ui,
+                                          float li, double Ai) {
   const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
@@ -286,7 +293,7 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, int parity, int k, 
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
   const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err};
-  return update_atom<LASER>(s, di, li, ui, ra.A[s], F, load_coef(cf), o, k);
+  return update_atom<LASER>(s, di, li, ui, Ai, F, load_coef(cf), o, k);
 }
 
 constexpr int kTileBufs = 2;   // tiles in flight per CTA
@@ -433,12 +440,13 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
         if (PP != 16 || m < D.ra.P) pv[m] = __ldg(pidx + (m * ps + s));
       const float ui = D.ra.uTl[s];
       const float li = D.ra.lo[s];
+      const double Ai = D.ra.A[s];
       const float di = tile[sb + q];
       float h;
-      if (tier == 3) h = row_atom<3, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-      else if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-      else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
-      else h = row_atom<0, LASER, PP>(D.ra, parity, k, tile, s, di, pv, ui, li);
+      if (tier == 3) h = row_atom<3, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
+      else if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
+      else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
+      else h = row_atom<0, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
       vmin = fminf(vmin, h);
       vmax = fmaxf(vmax, h);
     }
