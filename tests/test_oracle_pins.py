@@ -280,3 +280,81 @@ def test_langevin_mode_moves_directions_not_energies():
     sim = out[1][1]
     cosang = (v0 * v1).sum(1) / np.sqrt(k0 * k1)
     assert np.median(cosang) > 0.95
+
+
+# ------------------------------------------------------------- stability bound
+
+def test_stability_bound_at_the_l_point():
+    # FCC Cu at r_c = 4.0 A: 12 first and 6 second neighbours.  The mode
+    # cos(pi (x + y + z) / a) (the L point) flips sign across all 6 second and
+    # 6 of the 12 first neighbours, so its linearised rate is
+    # lambda_L = K c(theta) sum_j (1 - cos k.r_j) = 24 K c(theta), the largest of
+    # the lattice; forward Euler multiplies its amplitude by 1 - dt lambda_L per
+    # substep, which stays bounded for dt lambda_L < 2 and grows above.
+    a = I.CU_A
+    x = I.fcc_lattice(4, 4, 4, a)
+    n = x.shape[0]
+    box = np.array([4 * a] * 3)
+    per = np.array([1, 1, 1], dtype=np.int32)
+    rowptr, col = oracle.neighbors(x, box, per, 4.0)
+    assert np.all(np.diff(rowptr) == 18)
+    mode = np.cos(np.pi * x.sum(axis=1) / a)
+    assert np.allclose(np.abs(mode), 1.0) and abs(mode.sum()) < 1e-9
+    shell = I.fcc_shell_vectors(a, 4.0)
+    kvec = np.array([np.pi / a] * 3)
+    assert float((1.0 - np.cos(shell @ kvec)).sum()) == pytest.approx(24.0, abs=1e-12)
+    T0, amp, Tmax, K = 300.0, 1e-3, 1.0e5, 1.0
+    th = T0 / Tmax
+    lam = 24.0 * K * (1.0 - 2.0 * th * (1.0 - th))
+    n_sub = 60
+    for r in (0.95, 1.05):
+        dt = r * 2.0 / lam
+        T = T0 + amp * mode
+        Tl = np.full(n, T0)
+        chi = np.zeros(n, dtype=np.uint8)
+        A = np.zeros(n)
+        st, _ = oracle.substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, 0.0, 0.0)
+        assert st == n_sub
+        a1 = float((T - T0) @ mode / n)
+        pred = amp * (1.0 - dt * lam) ** n_sub
+        assert a1 == pytest.approx(pred, rel=1e-4)
+        if r < 1:
+            assert abs(a1) < 0.01 * amp
+        else:
+            assert abs(a1) > 100 * amp
+
+
+# ------------------------------------------------------- Langevin statistics
+
+def test_langevin_lattice_reaches_the_electron_temperature():
+    # uniform T_e held fixed (a very large electronic heat capacity), strong
+    # coupling, atoms at rest in space: the Langevin hand-over drives the lattice
+    # to <KE> = (3/2) k_B T_e per atom (with the 3 (N_j - 1) degrees of freedom of
+    # the centre-of-mass-free local temperature); statistical check at 3 sigma
+    s = I.hot_spot_system(6, 5, peak=300.0)
+    n = s.n
+    Te = 900.0
+    s.Te[:] = Te
+    p = I.params_hotspot_fp64()
+    p.update(frozen=0, couple_mode=1, G=3e18, gamma_Ce=1e12, dof_mode=1, dt_sub=1.0, Tmax=2.0e4)
+    sim = _sim(s, p)
+    v = s.v.copy()
+    ke = lambda vv: 0.5 * sim.mass * (vv * vv).sum(1) * oracle.MVV_EV
+    samples = []
+    for step in range(600):
+        if step:
+            sim.build(s.x, v)
+        sim.substeps(10)
+        sim.couple(v, 10.0)
+        if step >= 300:
+            samples.append(float(ke(v).mean()))
+    target = 1.5 * oracle.KB_EV * Te
+    m = float(np.mean(samples))
+    # per-atom kinetic energies are Gamma(3/2)-distributed: relative spread
+    # sqrt(2/3) per atom; the 300 samples are correlated, count them as 5.
+    # (3 N_j degrees of freedom would give 19/18 of the target, 5.6 % above,
+    # outside this band.)
+    sigma = target * math.sqrt(2.0 / 3.0) / math.sqrt(n * 5)
+    assert abs(m - target) < 3.0 * sigma, (m, target, sigma)
+    assert 19.0 / 18.0 * target - m > 3.0 * sigma
+    assert abs(np.mean(sim.T) - Te) < 1e-3 * Te
