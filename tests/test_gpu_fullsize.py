@@ -6,7 +6,9 @@ in the launch configuration bench.py times (row-tile kernel, graph replay).
   neighbourhood (information travels one hop per substep, so the centre of a
   10-hop ball is exact after 10 substeps): T_e within 1e-4 relative;
 * after a whole MD step (100 substeps, Langevin hand-over) the energy ledger
-  closes to 1e-9.
+  closes to 1e-9;
+and the same workload on 256,000 atoms over 100 MD steps (10,000 substeps)
+against the oracle run of the whole sequence.
 """
 import numpy as np
 import pytest
@@ -105,3 +107,23 @@ def test_fullsize_md_step_ledger(track):
     e = g.energy()
     assert abs(e["drift"]) < 1e-9
     assert e["n_stopped"] == 0
+
+
+def test_256k_track_10k_substeps():
+    # the track profile on 40^3 cells (256,000 atoms), FP32 flux, 100 MD steps x
+    # 100 substeps of 1e-3 fs, Langevin coupling, free flight, against the oracle
+    # run of the same sequence: T_e within 1e-4, ledger drift within 1e-9
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _drive import run_gpu, run_oracle
+    s = I.track_system(40, 2)
+    p = I.params_track()
+    sim, xo, vo = run_oracle(s, p, 100, 100)
+    g, xg, vg = run_gpu(s, p, 100, 100)
+    Tg = g.get_te().cpu().numpy()
+    err = float(np.max(np.abs(Tg - sim.T) / sim.T))
+    assert err < 1e-4, err
+    e = g.energy()
+    assert abs(e["drift"]) < 1e-9
+    assert e["n_stopped"] == sim.n_stopped
+    print(f"track40 (256k atoms) FP32, 10k substeps: max rel T_e err {err:.3e}, drift {e['drift']:.3e}")
