@@ -522,7 +522,7 @@ int build_finish(Ctx &c, bool own_tiles) {
   cf.Tmax_f = (float)c.p.Tmax_K;
   cf.pad[0] = cf.pad[1] = cf.pad[2] = 0.f;
   CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
-  CK(upload_reps(c));
+  if (own_tiles) CK(upload_reps(c));   // a batch keeps its own table of every replica
   c.built = true;
   return err_code(c.dev_err);
 }
@@ -828,6 +828,11 @@ struct ehc_batch {
   int64_t n_total = 0;
   ehc_params p;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
+  // per-replica work (builds, hand-over, drift) runs on kRepStreams streams,
+  // replica r on rs[r % kRepStreams], forked from and joined back to `stream`
+  std::vector<cudaStream_t> rs;
+  std::vector<cudaEvent_t> rev;
+  cudaEvent_t fork_ev = nullptr;
   RepArgs *reps_dev = nullptr;
   int2 *work = nullptr;
   int32_t nwork = 0, tile_floats = 0, num_sms = 0;
@@ -841,6 +846,25 @@ struct ehc_batch {
 };
 
 namespace {
+
+constexpr int kRepStreams = 16;
+
+// the replica streams wait for everything queued on the batch stream so far
+cudaError_t batch_fork(ehc_batch &b) {
+  cudaError_t e = cudaEventRecord(b.fork_ev, b.stream);
+  for (size_t k = 0; k < b.rs.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b.rs[k], b.fork_ev, 0);
+  return e;
+}
+
+// the batch stream waits for everything queued on the replica streams
+cudaError_t batch_join(ehc_batch &b) {
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < b.rs.size() && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b.rev[k], b.rs[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b.stream, b.rev[k], 0);
+  }
+  return e;
+}
 
 int batch_pairs(const ehc_batch &b) {
   int pairs = 9;
@@ -871,10 +895,26 @@ int ehc_batch_create(const ehc_params *p, int32_t n_rep, const int64_t *n_atoms_
   if (!b) return EHC_E_NOMEM;
   b->p = *p;
   b->stream = (cudaStream_t)stream;
+  const int ns = n_rep < kRepStreams ? n_rep : kRepStreams;
+  bool sok = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < ns && sok; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    sok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    if (sok) b->rs.push_back(st);
+    sok = sok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (sok) b->rev.push_back(ev);
+  }
+  if (!sok) {
+    cudaGetLastError();
+    ehc_batch_destroy(b);
+    return EHC_E_NOMEM;
+  }
   std::vector<int2> wl;
   for (int32_t r = 0; r < n_rep; ++r) {
     ehc_ctx *h = nullptr;
-    int e = ehc_create(p, n_atoms_host[r], boxes_host + 3 * r, periodic, mass_amu_host, 1, nullptr, stream, &h);
+    int e = ehc_create(p, n_atoms_host[r], boxes_host + 3 * r, periodic, mass_amu_host, 1, nullptr,
+                       b->rs[r % ns], &h);
     if (e != EHC_OK) {
       ehc_batch_destroy(b);
       return e;
@@ -907,6 +947,9 @@ void ehc_batch_destroy(ehc_batch *b) {
   if (b->reps_dev) cudaFree(b->reps_dev);
   if (b->work) cudaFree(b->work);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto st : b->rs) cudaStreamDestroy(st);
+  for (auto ev : b->rev) cudaEventDestroy(ev);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   delete b;
 }
 
@@ -920,20 +963,24 @@ int ehc_batch_size(const ehc_batch *b, int64_t *n_total, int64_t *offsets_host) 
 
 int ehc_batch_set_te(ehc_batch *b, const double *Te_dev) {
   if (!b || (!Te_dev && b->n_total > 0)) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
     int e = ehc_set_te(b->rep[r], Te_dev + b->off[r]);
     if (e) return e;
   }
+  CK(batch_join(*b));
   b->parity = 0;
   return EHC_OK;
 }
 
 int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v_dev) {
   if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
     int e = build_enqueue(b->rep[r]->c, x_dev + 3 * b->off[r], v_dev + 3 * b->off[r]);
     if (e) return e;
   }
+  CK(batch_join(*b));
   CK(cudaStreamSynchronize(b->stream));
   int first_err = EHC_OK;
   int32_t staged = 0;
@@ -954,6 +1001,7 @@ int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v
     }
   }
   CK(cudaMemcpy(b->reps_dev, tab.data(), sizeof(RepArgs) * tab.size(), cudaMemcpyHostToDevice));
+  CK(batch_join(*b));   // the coefficient uploads of build_finish
   b->parity = 0;
   return first_err;
 }
@@ -965,12 +1013,14 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
     if (h->c.n > 0 && !(h->c.stability <= 2.0)) return EHC_E_UNSTABLE;
   }
   if (n_sub == 0) return EHC_OK;
+  CK(batch_fork(*b));
   if (!batch_tile_ok(*b)) {
     // some replica does not fit the row tiles: advance each on its own
     for (auto *h : b->rep) {
       int e = ehc_substep(h, n_sub, t_fs);
       if (e) return e;
     }
+    CK(batch_join(*b));
     return EHC_OK;
   }
   for (auto *h : b->rep) {
@@ -978,6 +1028,7 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
     int e = ensure_split(h->c);
     if (e) return e;
   }
+  CK(batch_join(*b));
   const int p0 = b->parity;
   const int pairs = batch_pairs(*b);
   int hit = -1;
@@ -1017,33 +1068,40 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
 
 int ehc_batch_couple(ehc_batch *b, double *v_dev, double dt_md_fs) {
   if (!b || (b->n_total > 0 && !v_dev)) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
     int e = ehc_couple(b->rep[r], v_dev + 3 * b->off[r], dt_md_fs);
     if (e) return e;
   }
+  CK(batch_join(*b));
   return EHC_OK;
 }
 
 int ehc_batch_drift(ehc_batch *b, double *x_dev, const double *v_dev, double dt_fs) {
   if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
     int e = ehc_drift(b->rep[r], x_dev + 3 * b->off[r], v_dev + 3 * b->off[r], dt_fs);
     if (e) return e;
   }
+  CK(batch_join(*b));
   return EHC_OK;
 }
 
 int ehc_batch_get_te(ehc_batch *b, double *Te_dev_out) {
   if (!b || (b->n_total > 0 && !Te_dev_out)) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
     int e = ehc_get_te(b->rep[r], Te_dev_out + b->off[r]);
     if (e) return e;
   }
+  CK(batch_join(*b));
   return EHC_OK;
 }
 
 int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
   if (!b || r < 0 || r >= (int32_t)b->rep.size()) return EHC_E_INVAL;
+  CK(batch_fork(*b));
   return ehc_energy(b->rep[r], out);
 }
 
