@@ -49,6 +49,8 @@ def lib():
         L.oracle_lattice_temperature.restype = None
         L.oracle_pair_flux.argtypes = [dbl, dbl]
         L.oracle_pair_flux.restype = dbl
+        L.oracle_flux_sum.argtypes = [i64, P, P, P, P]
+        L.oracle_flux_sum.restype = None
         L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
                                       dbl, P, P, dbl, dbl, dbl, P]
         L.oracle_substeps.restype = ctypes.c_int
@@ -129,6 +131,16 @@ def lattice_temperature(rowptr, col, v, mass_of_atom, dof_mode: int = 0):
 
 def pair_flux(a: float, b: float) -> float:
     return float(lib().oracle_pair_flux(float(a), float(b)))
+
+
+def flux_sum(rowptr, col, theta):
+    """F_i = sum_j f(theta_i, theta_j) over the list (Eq. HeatTransport, flux part)."""
+    n = rowptr.shape[0] - 1
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    F = np.empty(n)
+    lib().oracle_flux_sum(n, _p(np.ascontiguousarray(rowptr, dtype=np.int64)),
+                          _p(np.ascontiguousarray(col, dtype=np.int32)), _p(th), _p(F))
+    return F
 
 
 def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=None,

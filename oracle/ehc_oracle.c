@@ -261,6 +261,17 @@ double oracle_pair_flux(double a, double b) {
   return gain - loss;
 }
 
+/* The pair-flux sum of Eq. HeatTransport for every atom, in list order:
+ * F_i = sum_j f(theta_i, theta_j), so that d theta_i / dt = K F_i (flux part). */
+void oracle_flux_sum(int64_t n, const int64_t *rowptr, const int32_t *col, const double *theta, double *F) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double acc = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += oracle_pair_flux(theta[i], theta[col[e]]);
+    F[i] = acc;
+  }
+}
+
 /* Optional time-dependent source (Sec. 5, Eq. LaserIntesity), a Gaussian pulse
  * absorbed with exponential decay below the irradiated surface:
  *   S(depth, t) = (F / l_p) exp(-depth / l_p) exp(-(t - t0)^2 / (2 s^2)) / (s sqrt(2 pi))

@@ -1,0 +1,138 @@
+"""Pins of the FP64 Chebyshev window reference (oracle/window.py) against
+closed forms: the Chebyshev polynomials cos(s arccos x) / cosh(s arccosh x),
+the stability polynomial of the recurrence on a linear lattice mode, the sum
+of temperatures (Eq. HeatTransport conserves it) and the uniform fixed point."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import window as W
+from paper_1810_12357_gb300 import inputs as I
+
+
+def T_closed(s, x):
+    if abs(x) <= 1.0:
+        return math.cos(s * math.acos(x))
+    if x > 1.0:
+        return math.cosh(s * math.acosh(x))
+    return (-1.0) ** s * math.cosh(s * math.acosh(-x))
+
+
+def P_closed(s, eps, z):
+    w0 = 1.0 + eps / (s * s)
+    # w1 = T_s(w0) / T_s'(w0) with T_s'(x) = s sinh(s arccosh x) / sinh(arccosh x) for x > 1
+    a = math.acosh(w0)
+    w1 = math.cosh(s * a) * math.sinh(a) / (s * math.sinh(s * a))
+    return T_closed(s, w0 + w1 * z) / T_closed(s, w0)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 6])
+def test_recurrence_matches_closed_form(s):
+    for x in (-0.9, -0.3, 0.2, 0.95, 1.0, 1.02, 1.3):
+        assert W.cheb(s, x) == pytest.approx(T_closed(s, x), rel=1e-12, abs=1e-12)
+    w0, w1, mu, nu, mut = W.coefficients(s, 0.05)
+    a = math.acosh(w0)
+    assert w1 == pytest.approx(math.cosh(s * a) * math.sinh(a) / (s * math.sinh(s * a)), rel=1e-12)
+    for j in range(2, s + 1):
+        assert mu[j] + nu[j] == pytest.approx(1.0, abs=1e-14)   # affine: the sum of theta is kept
+
+
+@pytest.mark.parametrize("s", [3, 4, 5])
+def test_stability_polynomial(s):
+    eps = 0.05
+    # first order: P(0) = 1, P'(0) = 1
+    h = 1e-5
+    assert P_closed(s, eps, 0.0) == pytest.approx(1.0, abs=1e-14)
+    assert (P_closed(s, eps, h) - P_closed(s, eps, -h)) / (2 * h) == pytest.approx(1.0, rel=1e-8)
+    b = W.beta(s, eps)
+    assert b == pytest.approx((2.0 - 4.0 * eps / 3.0) * s * s, rel=0.02)
+    zs = np.linspace(-b, 0.0, 2001)
+    assert max(abs(P_closed(s, eps, z)) for z in zs) <= 1.0 + 1e-12
+    assert abs(P_closed(s, eps, -1.05 * b)) > 1.0
+
+
+def _fcc(nc):
+    a = I.CU_A
+    x = I.fcc_lattice(nc, nc, nc, a)
+    box = np.array([nc * a] * 3)
+    per = np.array([1, 1, 1], dtype=np.int32)
+    rowptr, col = oracle.neighbors(x, box, per, 4.0)
+    return a, x, rowptr, col
+
+
+def test_linear_mode_follows_the_stability_polynomial():
+    # a small sin(k x) mode on the perfect lattice decays over one window by
+    # exactly P_s(-tau lambda_k), lambda_k = K c(theta) sum_j (1 - cos k.r_j)
+    a, x, rowptr, col = _fcc(6)
+    shell = I.fcc_shell_vectors(a, 4.0)
+    th0, amp, K = 0.003, 1e-9, 1.0
+    c = 1.0 - 2.0 * th0 * (1.0 - th0)
+    s, eps = 4, 0.05
+    for kc in (6, 3, 2):                      # k = 2 pi / (kc a): long to short waves
+        k = 2.0 * math.pi / (kc * a)
+        lam = K * c * float((1.0 - np.cos(k * shell[:, 0])).sum())
+        mode = np.sin(k * x[:, 0])
+        for tau in (0.02, 0.5, 0.9 * W.beta(s, eps) / lam):
+            y, _ = W.window(rowptr, col, th0 + amp * mode, K, tau, s, eps)
+            a1 = float((y - th0) @ mode / (mode @ mode))
+            assert a1 == pytest.approx(amp * P_closed(s, eps, -tau * lam), rel=2e-5, abs=1e-17)
+
+
+def test_conservation_and_fixed_point():
+    s = I.hot_spot_system(5, 3, peak=9000.0)
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, 4.0)
+    th = s.Te / 2.0e4
+    y, F0 = W.window(rowptr, col, th, 20.0, 0.02, 4, 0.05)
+    assert abs(y.sum() - th.sum()) < 1e-13 * th.sum()
+    assert abs(F0.sum()) < 1e-12
+    assert y.max() < th.max()
+    u = np.full(s.n, 0.0617)
+    yu, _ = W.window(rowptr, col, u, 20.0, 0.02, 4, 0.05)
+    assert np.all(yu == u)
+
+
+def test_l_point_mode_bounded_inside_the_interval():
+    # the most unstable lattice mode (rate 24 K c) stays bounded while
+    # tau lambda_L <= beta and grows beyond it
+    a, x, rowptr, col = _fcc(4)
+    mode = np.cos(np.pi * x.sum(axis=1) / a)
+    th0, amp, K = 0.003, 1e-9, 1.0
+    lam = 24.0 * K * (1.0 - 2.0 * th0 * (1.0 - th0))
+    s, eps = 4, 0.05
+    b = W.beta(s, eps)
+    for r, bounded in ((0.98, True), (1.10, False)):
+        y = th0 + amp * mode
+        for _ in range(20):
+            y, _ = W.window(rowptr, col, y, K, r * b / lam, s, eps)
+        a1 = float((y - th0) @ mode / (mode @ mode))
+        assert (abs(a1) <= amp) == bounded
+
+
+def test_window_against_plain_substeps_on_the_track():
+    # how far one Chebyshev window (4 stages, 16 substeps of the bench's dt) is
+    # from the 16 explicit substeps it replaces, along the plain trajectory of
+    # the track profile: several per cent in the first window (the heat front
+    # moves by ~70 % of the local temperature within one window, where the two
+    # first-order maps differ in their error constants), well under 1 % once the
+    # profile has spread
+    s = I.track_system(24, 2, r0=20.0)
+    p = I.params_track()
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    K, Tmax, dt = sim.K, p["Tmax"], p["dt_sub"]
+    T = s.Te.copy()
+    errs = []
+    for w in range(20):
+        y, _ = W.window(sim.rowptr, sim.col, T / Tmax, K, 16 * dt, 4, 0.05)
+        Tn = T.copy()
+        zeros = np.zeros(s.n)
+        oracle.substeps(sim.rowptr, sim.col, Tn, zeros, np.zeros(s.n, np.uint8), zeros.copy(), 16, dt, Tmax, K,
+                        0.0, 0.0)
+        errs.append(float(np.max(np.abs(y * Tmax - Tn) / Tn)))
+        T = Tn
+    assert errs[0] > 0.05
+    assert errs[19] < 1e-3
+    assert all(errs[k + 1] < errs[k] for k in range(0, 19, 3))
