@@ -93,6 +93,11 @@ _SIGS = {
     "ehc_nn_predict": (_I, [_P, _P, _P, _P]),
     "ehc_nn_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "ehc_nn_destroy": (None, [_P]),
+    "ehc_cheb_create": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_P)]),
+    "ehc_cheb_coefficients": (_I, [_P, _P, _P]),
+    "ehc_cheb_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
+    "ehc_cheb_stats": (_I, [_P, _P, _P]),
+    "ehc_cheb_destroy": (None, [_P]),
     "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
                               ctypes.POINTER(_P)]),
     "ehc_batch_size": (_I, [_P, _P, _P]),
@@ -447,3 +452,49 @@ class EhcNN:
         _check(self._lib.ehc_nn_step(self._h, self.ctx._h, float(tau), float(t_fs), ctypes.byref(fb),
                                      ctypes.byref(rho)), "ehc_nn_step")
         return bool(fb.value), float(rho.value)
+
+
+class EhcCheb:
+    """Chebyshev window propagator bound to a context (ehc_cheb_*)."""
+
+    def __init__(self, ctx: "Ehc", n_window: int = 16, stages: int = 4, damping: float = 0.05):
+        L = load_library()
+        self._lib = L
+        self.ctx = ctx
+        self.n_window = int(n_window)
+        self.stages = int(stages)
+        h = ctypes.c_void_p()
+        _check(L.ehc_cheb_create(ctx._h, self.n_window, self.stages, float(damping), ctypes.byref(h)),
+               "ehc_cheb_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.ehc_cheb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coefficients(self):
+        nu = np.empty(self.stages + 1)
+        mut = np.empty(self.stages + 1)
+        _check(self._lib.ehc_cheb_coefficients(self._h, nu.ctypes.data_as(_P), mut.ctypes.data_as(_P)),
+               "ehc_cheb_coefficients")
+        return nu, mut
+
+    def step(self, tau: float, t_fs: float = 0.0):
+        fb = ctypes.c_int32()
+        rho = ctypes.c_double()
+        _check(self._lib.ehc_cheb_step(self._h, self.ctx._h, float(tau), float(t_fs), ctypes.byref(fb),
+                                       ctypes.byref(rho)), "ehc_cheb_step")
+        return bool(fb.value), float(rho.value)
+
+    def stats(self):
+        w = ctypes.c_int64()
+        f = ctypes.c_int64()
+        _check(self._lib.ehc_cheb_stats(self._h, ctypes.byref(w), ctypes.byref(f)), "ehc_cheb_stats")
+        return int(w.value), int(f.value)

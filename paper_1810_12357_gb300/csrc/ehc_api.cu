@@ -1108,6 +1108,207 @@ int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Chebyshev window propagator
+
+struct ehc_cheb {
+  int n_w = 16, s = 4;
+  double eps = 0.05;
+  int64_t n = 0;
+  std::vector<double> nu, mut;     // stage coefficients, index 1..s
+  float *y[3] = {nullptr, nullptr, nullptr};   // stage values (padded to ps floats)
+  float *F0 = nullptr, *F1 = nullptr, *part = nullptr, *rho = nullptr, *host = nullptr;
+  float *rr[2] = {nullptr, nullptr};   // row value ranges of the stage values
+  double *T1 = nullptr, *dTc = nullptr;
+  int64_t windows = 0, fallbacks = 0;
+};
+
+namespace {
+
+// Chebyshev polynomial T_j and its derivative at x (three-term recurrence)
+void cheb_eval(int j, double x, double *T, double *dT) {
+  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
+  if (j == 0) {
+    *T = 1.0;
+    *dT = 0.0;
+    return;
+  }
+  for (int k = 1; k < j; ++k) {
+    const double t2 = 2.0 * x * t1 - t0, d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
+    t0 = t1;
+    t1 = t2;
+    d0 = d1;
+    d1 = d2;
+  }
+  *T = t1;
+  *dT = d1;
+}
+
+// first-order damped Chebyshev coefficients: w0 = 1 + eps/s^2,
+// w1 = T_s(w0)/T_s'(w0), b_j = 1/T_j(w0); nu_j = -b_j/b_{j-2},
+// mut_j = 2 w1 b_j/b_{j-1} (mut_1 = w1/w0)
+void cheb_coefficients(int s, double eps, std::vector<double> &nu, std::vector<double> &mut) {
+  const double w0 = 1.0 + eps / ((double)s * s);
+  double Ts, dTs;
+  cheb_eval(s, w0, &Ts, &dTs);
+  const double w1 = Ts / dTs;
+  std::vector<double> b(s + 1);
+  for (int j = 0; j <= s; ++j) {
+    double T, dT;
+    cheb_eval(j, w0, &T, &dT);
+    b[j] = 1.0 / T;
+  }
+  nu.assign(s + 1, 0.0);
+  mut.assign(s + 1, 0.0);
+  mut[1] = w1 / w0;
+  for (int j = 2; j <= s; ++j) {
+    nu[j] = -b[j] / b[j - 2];
+    mut[j] = 2.0 * w1 * b[j] / b[j - 1];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, double damping, ehc_cheb **out) {
+  if (!hc || !out || n_window < 1 || stages < 2 || stages > 32 || !(damping >= 0.0) || damping > 10.0)
+    return EHC_E_INVAL;
+  *out = nullptr;
+  Ctx &c = hc->c;
+  if (c.p.flux_prec != 0 || c.p.laser_on) return EHC_E_INVAL;
+  ehc_cheb *w = new (std::nothrow) ehc_cheb();
+  if (!w) return EHC_E_NOMEM;
+  w->n_w = n_window;
+  w->s = stages;
+  w->eps = damping;
+  w->n = c.n;
+  cheb_coefficients(stages, damping, w->nu, w->mut);
+  const int64_t n = c.n > 0 ? c.n : 1;
+  const int64_t np4 = c.ps > 0 ? c.ps : 4;
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  for (int k = 0; k < 3; ++k) A(dalloc(&w->y[k], np4));
+  A(dalloc(&w->F0, n));
+  A(dalloc(&w->F1, n));
+  A(dalloc(&w->part, cheb_blocks(n)));
+  A(dalloc(&w->rho, 1));
+  A(dalloc(&w->T1, n));
+  A(dalloc(&w->dTc, n));
+  A(dalloc(&w->rr[0], 2 * (c.nrows > 0 ? c.nrows : 1)));
+  A(dalloc(&w->rr[1], 2 * (c.nrows > 0 ? c.nrows : 1)));
+  A(cudaMallocHost((void **)&w->host, sizeof(float) * 4));
+  if (ok)
+    for (int k = 0; k < 3; ++k) A(cudaMemsetAsync(w->y[k], 0, sizeof(float) * np4, c.stream));
+  if (ok) A(cudaStreamSynchronize(c.stream));
+  if (!ok) {
+    cudaGetLastError();
+    ehc_cheb_destroy(w);
+    return EHC_E_NOMEM;
+  }
+  *out = w;
+  return EHC_OK;
+}
+
+void ehc_cheb_destroy(ehc_cheb *w) {
+  if (!w) return;
+  for (int k = 0; k < 3; ++k)
+    if (w->y[k]) cudaFree(w->y[k]);
+  void *p[] = {w->F0, w->F1, w->part, w->rho, w->T1, w->dTc, w->rr[0], w->rr[1]};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  if (w->host) cudaFreeHost(w->host);
+  delete w;
+}
+
+int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_out, double *mut_out) {
+  if (!w || !nu_out || !mut_out) return EHC_E_INVAL;
+  for (int j = 0; j <= w->s; ++j) {
+    nu_out[j] = w->nu[j];
+    mut_out[j] = w->mut[j];
+  }
+  return EHC_OK;
+}
+
+int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_back, double *rho_out) {
+  if (!w || !hc || hc->c.n != w->n) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  if (!(c.stability <= 2.0)) return EHC_E_UNSTABLE;
+  if (c.n == 0) return EHC_OK;
+  if (!tile_path(c)) {
+    // the stages run in the row-tile kernel; without it advance the window plainly
+    w->windows += 1;
+    w->fallbacks += 1;
+    if (fell_back) *fell_back = 1;
+    if (rho_out) *rho_out = -1.0;
+    return ehc_substep(hc, w->n_w, t_fs);
+  }
+  int r = ensure_t(c);
+  if (r) return r;
+  const double *T0 = c.T[c.tcur];
+  const double tauw = (double)w->n_w * c.p.dt_sub_fs;
+  // Y_0 and the row ranges of the first stage (unknown: widest tier)
+  CK(cheb_mirror(c, T0, w->y[0]));
+  CK(cudaMemsetAsync(w->rr[0], 0xfe, sizeof(float) * c.nrows, c.stream));
+  CK(cudaMemsetAsync(w->rr[0] + c.nrows, 0x7f, sizeof(float) * c.nrows, c.stream));
+  int par = 0;
+  for (int j = 1; j <= w->s; ++j) {
+    StageArgs sa;
+    sa.yin = w->y[(j - 1) % 3];
+    sa.yprev = j >= 2 ? w->y[(j - 2) % 3] : nullptr;
+    sa.yout = w->y[j % 3];
+    sa.Fout = j == 1 ? w->F0 : nullptr;
+    sa.rr[0] = w->rr[0];
+    sa.rr[1] = w->rr[1];
+    sa.nu = (float)w->nu[j];
+    sa.mt = (float)(w->mut[j] * tauw * c.K);
+    CK(launch_cheb_stage(c, sa, par, c.stream));
+    par ^= 1;
+  }
+  float *ys = w->y[w->s % 3];
+  CK(cheb_to_T(c, ys, w->T1));
+  // electron-phonon coupling over the window (kept in dTc until accepted)
+  CK(nn_couple_window(c, T0, w->T1, ys, w->dTc, w->n_w));
+  // pair flux of the end state for the residual
+  StageArgs sf;
+  sf.yin = ys;
+  sf.yprev = nullptr;
+  sf.yout = w->y[(w->s + 1) % 3];
+  sf.Fout = w->F1;
+  sf.rr[0] = w->rr[0];
+  sf.rr[1] = w->rr[1];
+  sf.nu = 0.0f;
+  sf.mt = 0.0f;
+  CK(launch_cheb_stage(c, sf, par, c.stream));
+  CK(cheb_residual(c, T0, w->T1, w->F0, w->F1, tauw, w->part, w->rho));
+  CK(cudaMemcpyAsync(w->host, w->rho, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  const double rho = w->host[0];
+  w->windows += 1;
+  if (rho_out) *rho_out = rho;
+  if (rho <= tau) {
+    CK(nn_accept(c, w->dTc));
+    CK(cudaMemcpyAsync(c.T[c.tcur], w->T1, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+    c.ff_valid = false;
+    c.t_stale = false;
+    if (fell_back) *fell_back = 0;
+    return EHC_OK;
+  }
+  w->fallbacks += 1;
+  if (fell_back) *fell_back = 1;
+  return ehc_substep(hc, w->n_w, t_fs);
+}
+
+int ehc_cheb_stats(const ehc_cheb *w, int64_t *windows, int64_t *fallbacks) {
+  if (!w) return EHC_E_INVAL;
+  if (windows) *windows = w->windows;
+  if (fallbacks) *fallbacks = w->fallbacks;
+  return EHC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Learned window propagator
 
 struct ehc_nn {

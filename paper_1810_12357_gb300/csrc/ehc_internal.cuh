@@ -110,6 +110,18 @@ struct RepArgs {
   int32_t *err;
 };
 
+// Arguments of a Chebyshev-window stage launch of the row-tile kernel: pair
+// flux of the values yin, Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + mt F into
+// yout, and optionally F itself into Fout (values as delta = (T - Tref)/Tmax).
+struct StageArgs {
+  const float *yin;     // Y_{j-1}: the values the tiles are copied from (padded to ps)
+  const float *yprev;   // Y_{j-2} (null for the first stage)
+  float *yout;          // Y_j
+  float *Fout;          // the pair-flux sum F(Y_{j-1}) per atom, or null
+  float *rr[2];         // row value ranges of the stage values (read [parity], write [parity ^ 1])
+  float nu, mt;         // nu_j and mut_j tau K
+};
+
 // Deterministic block-partial reductions.
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 constexpr int kRedThreads = 256;
@@ -137,6 +149,13 @@ bool tile_path(const Ctx &c);
 bool tile_size(int32_t staged, int num_sms, int32_t *tb, int32_t grid[2]);
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
                                  int pairs, int parity, int k, cudaStream_t st);
+cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st);
+// kernels_window.cu (Chebyshev window propagator)
+cudaError_t cheb_mirror(Ctx &c, const double *T, float *y);
+cudaError_t cheb_to_T(Ctx &c, const float *y, double *T);
+cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
+                          float *part, float *out);
+int cheb_blocks(int64_t n);
 // kernels_nn.cu (learned window propagator)
 int nn_blocks(int64_t n);
 cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm,

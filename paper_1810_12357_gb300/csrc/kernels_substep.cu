@@ -173,7 +173,9 @@ struct TileDesc {
 };
 
 // computed by one warp: lane r < 9 handles neighbour row r
-__device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2 item, int parity, TileDesc *d) {
+// rr_in: row ranges to read instead of the system's own (null: the system's)
+__device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2 item, int parity, TileDesc *d,
+                                          const float *rr_in = nullptr) {
   const int lane = threadIdx.x & 31;
   // copy the system's arguments (whole 8-byte words) into the descriptor
   static_assert(sizeof(RepArgs) % 8 == 0, "RepArgs must be a whole number of 8-byte words");
@@ -191,7 +193,7 @@ __device__ __forceinline__ void make_desc(const RepArgs *__restrict__ reps, int2
   const int32_t ncx = d->ra.ncx;
   const int32_t *row_nbr = d->ra.row_nbr;
   const int32_t *start = d->ra.start;
-  const float *rr = d->ra.rrange[parity];
+  const float *rr = rr_in ? rr_in : d->ra.rrange[parity];
   const int32_t nrows = d->ra.nrows;
   int32_t R2 = -1, a = 0, len = 0;
   float mn = 3.0e38f, mx = -3.0e38f;
@@ -278,10 +280,10 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
-template <int TIER, bool LASER, int PP>
-__device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, int parity, int k,
-                                          const float *tile, int32_t s, float di, const uint32_t *pv, float ui,
-                                          float li, double Ai) {
+template <int TIER, bool LASER, int PP, bool STAGE>
+__device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, const StageArgs &sa, int parity,
+                                          int k, const float *tile, int32_t s, float di, const uint32_t *pv,
+                                          float ui, float li, double Ai) {
   const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
@@ -292,6 +294,14 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
       F = pair_acc<TIER>(F, di, tile[pv[m] & 0xffffu], th, ai, m2ai);
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
+  if (STAGE) {
+    // Chebyshev stage: Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + mut tau K F(Y_{j-1});
+    // ui carries Y_{j-2} of this atom
+    const float h = di + fmaf(sa.nu, ui - di, sa.mt * F);
+    sa.yout[s] = h;
+    if (sa.Fout) sa.Fout[s] = F;
+    return h;
+  }
   const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err};
   return update_atom<LASER>(s, di, li, ui, Ai, F, load_coef(cf), o, k);
 }
@@ -309,7 +319,7 @@ struct TilePipe {
 
 // producer side, after the compute warps released tile b of item it: the row's
 // value range for the tier choice of the next substep
-__device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity) {
+__device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity, float *rr_out = nullptr) {
   const int b = it % kTileBufs;
   if ((threadIdx.x & 31) == 0) {
     float a = sp.wmin[b][0], c = sp.wmax[b][0];
@@ -318,7 +328,7 @@ __device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity) {
       c = fmaxf(c, sp.wmax[b][w]);
     }
     const TileDesc &D = sp.desc[it % kDescRing];
-    float *rr = D.ra.rrange[parity ^ 1];
+    float *rr = rr_out ? rr_out : D.ra.rrange[parity ^ 1];
     rr[D.row] = a;
     rr[D.ra.nrows + D.row] = c;
   }
@@ -338,10 +348,13 @@ __device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity) {
 // (bounded) for its copies in flight before leaving.
 // PP = 9: exactly nine index words per atom (18-neighbour FCC shells) in every
 // system; PP = 16: any count up to 32 neighbours, ra.P words.
-template <bool LASER, int PP>
+// STAGE: one stage of the Chebyshev window propagator instead of a substep
+// (pair flux of the tile values sa.yin, stage update into sa.yout, optionally
+// the flux itself into sa.Fout); rows and tiers as for substeps.
+template <bool LASER, int PP, bool STAGE>
 __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
     substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
-                        int parity, int k) {
+                        int parity, int k, StageArgs sa) {
   extern __shared__ __align__(128) float tiles[];   // kTileBufs x tb words
   __shared__ TilePipe sp;
   if ((int)blockIdx.x >= nwork) return;
@@ -361,7 +374,9 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
     int32_t *err = nullptr;
     int issued = 0;
     bool ok = true;
-    make_desc(reps, work[blockIdx.x], parity, &sp.desc[0]);
+    const float *rr_in = STAGE ? sa.rr[parity] : nullptr;
+    float *rr_out = STAGE ? sa.rr[parity ^ 1] : nullptr;
+    make_desc(reps, work[blockIdx.x], parity, &sp.desc[0], rr_in);
     int made = 1;
     for (int it = 0; it < n_it && ok; ++it) {
       const int b = it % kTileBufs;
@@ -369,12 +384,12 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       if (use > 0) {
         ok = mbar_wait(&sp.empty[b], (use - 1) & 1);
         if (!ok) break;
-        close_item(sp, it - kTileBufs, parity);
+        close_item(sp, it - kTileBufs, parity, rr_out);
       }
       TileDesc *d = &sp.desc[it % kDescRing];
       err = d->ra.err;
       if (lane == 0) {
-        const float *hin = d->ra.dmir[parity];
+        const float *hin = STAGE ? sa.yin : d->ra.dmir[parity];
         float *dst = tiles + (int64_t)b * tb;
         // an empty row has nothing to update (and its tile is not covered by
         // the build's largest-tile figure): copy nothing.  A row whose tile
@@ -403,12 +418,13 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       // descriptors ahead: one after the first item's copies, then up to kDescAhead
       const int want = (it == 0) ? 2 : it + 1 + kDescAhead;
       for (; made < want && made < n_it; ++made)
-        make_desc(reps, work[blockIdx.x + (int64_t)made * gridDim.x], parity, &sp.desc[made % kDescRing]);
+        make_desc(reps, work[blockIdx.x + (int64_t)made * gridDim.x], parity, &sp.desc[made % kDescRing],
+                  rr_in);
     }
     // release the last items: their row ranges
     for (int it = (issued > kTileBufs ? issued - kTileBufs : 0); it < issued && ok; ++it) {
       ok = mbar_wait(&sp.empty[it % kTileBufs], (uint32_t)(it / kTileBufs) & 1);
-      if (ok) close_item(sp, it, parity);
+      if (ok) close_item(sp, it, parity, rr_out);
     }
     if (!ok) {
       if (lane == 0 && err) atomicOr(err, ERR_TIMEOUT);
@@ -438,15 +454,21 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
 #pragma unroll
       for (int m = 0; m < PP; ++m)
         if (PP != 16 || m < D.ra.P) pv[m] = __ldg(pidx + (m * ps + s));
-      const float ui = D.ra.uTl[s];
-      const float li = D.ra.lo[s];
-      const double Ai = D.ra.A[s];
       const float di = tile[sb + q];
+      float ui = 0.0f, li = 0.0f;
+      double Ai = 0.0;
+      if (STAGE) {
+        ui = sa.yprev ? sa.yprev[s] : di;
+      } else {
+        ui = D.ra.uTl[s];
+        li = D.ra.lo[s];
+        Ai = D.ra.A[s];
+      }
       float h;
-      if (tier == 3) h = row_atom<3, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
-      else if (tier == 2) h = row_atom<2, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
-      else if (tier == 1) h = row_atom<1, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
-      else h = row_atom<0, LASER, PP>(D.ra, &D.cf, parity, k, tile, s, di, pv, ui, li, Ai);
+      if (tier == 3) h = row_atom<3, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
+      else if (tier == 2) h = row_atom<2, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
+      else if (tier == 1) h = row_atom<1, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
+      else h = row_atom<0, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
       vmin = fminf(vmin, h);
       vmax = fmaxf(vmax, h);
     }
@@ -597,11 +619,16 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     const unsigned nt = kTileThreads + 32;
     const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
     if (P == 9) {
-      if (laser) substep_tile_kernel<true, 9><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
-      else substep_tile_kernel<false, 9><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
+      if (laser)
+        substep_tile_kernel<true, 9, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
+      else
+        substep_tile_kernel<false, 9, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
     } else {
-      if (laser) substep_tile_kernel<true, 16><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
-      else substep_tile_kernel<false, 16><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k);
+      if (laser)
+        substep_tile_kernel<true, 16, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
+      else
+        substep_tile_kernel<false, 16, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k,
+                                                                     StageArgs{});
     }
   } else {
     if (laser)
@@ -615,6 +642,20 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// one stage of the Chebyshev window over the context's rows (row-tile path)
+cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  const int32_t P = (c.n_max + 1) / 2;
+  const int32_t tb = c.tile_floats;
+  const int32_t tg = c.tile_grid[P == 9 ? 0 : 1];
+  const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
+  const unsigned nt = kTileThreads + 32;
+  const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
+  if (P == 9) substep_tile_kernel<false, 9, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
+  else substep_tile_kernel<false, 16, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
+  return cudaGetLastError();
+}
+
 // one substep of the row-tile kernel over an explicit work list (batched systems)
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
                                  int pairs, int parity, int k, cudaStream_t st) {
@@ -622,8 +663,10 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
   if (g == 0) return cudaSuccess;
   const unsigned nt = kTileThreads + 32;
   const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
-  if (pairs == 9) substep_tile_kernel<false, 9><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k);
-  else substep_tile_kernel<false, 16><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k);
+  if (pairs == 9)
+    substep_tile_kernel<false, 9, false><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k, StageArgs{});
+  else
+    substep_tile_kernel<false, 16, false><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k, StageArgs{});
   return cudaGetLastError();
 }
 
@@ -635,13 +678,17 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2]) {
   const int32_t tb = ((staged + staged / 8 + 64 + 255) / 256) * 256;
   const int64_t bytes = (int64_t)sizeof(float) * kTileBufs * tb;
   if (bytes > kTileMaxBytes) return false;
-  const void *inst[2][2] = {{(const void *)substep_tile_kernel<true, 9>, (const void *)substep_tile_kernel<false, 9>},
-                            {(const void *)substep_tile_kernel<true, 16>, (const void *)substep_tile_kernel<false, 16>}};
+  const void *inst[2][3] = {{(const void *)substep_tile_kernel<true, 9, false>,
+                             (const void *)substep_tile_kernel<false, 9, false>,
+                             (const void *)substep_tile_kernel<false, 9, true>},
+                            {(const void *)substep_tile_kernel<true, 16, false>,
+                             (const void *)substep_tile_kernel<false, 16, false>,
+                             (const void *)substep_tile_kernel<false, 16, true>}};
   int32_t g[2] = {0, 0};
   for (int w = 0; w < 2; ++w) {
     int bps = 1 << 30;
     bool ok = true;
-    for (int l = 0; l < 2 && ok; ++l) {
+    for (int l = 0; l < 3 && ok; ++l) {
       int b = 0;
       ok = cudaFuncSetAttribute(inst[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inst[w][l], kTileThreads + 32, (size_t)bytes) ==

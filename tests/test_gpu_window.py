@@ -1,0 +1,88 @@
+"""Chebyshev window propagator (ehc_cheb_*) on the GPU against the FP64
+reference oracle/window.py, plus its conservation, fallback and ledger."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import window as W
+from paper_1810_12357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(s, p):
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    g.build_neighbors(x, v)
+    return g, x, v
+
+
+def test_coefficients_match_the_reference():
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(6, 1)
+    g, _, _ = _ctx(s, dict(I.params_hotspot_fp64(), flux_prec=0))
+    for st, eps in ((4, 0.05), (6, 0.3), (2, 0.0)):
+        w = EhcCheb(g, 16, st, eps)
+        nu, mut = w.coefficients()
+        _, _, _, nu_o, mut_o = W.coefficients(st, eps)
+        assert np.allclose(nu[1:], nu_o[1:], rtol=1e-13, atol=1e-15)
+        assert np.allclose(mut[1:], mut_o[1:], rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("peak", [3000.0, 12000.0])
+def test_one_window_matches_the_fp64_reference(peak):
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(10, 1, peak=peak)
+    p = dict(I.params_hotspot_fp64(), flux_prec=0, G=0.0)
+    g, _, _ = _ctx(s, p)
+    K = g.energy()["K_per_fs"]
+    w = EhcCheb(g, 16, 4, 0.05)
+    fb, rho = w.step(1e30)
+    assert not fb
+    Tg = g.get_te().cpu().numpy()
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"])
+    y, _ = W.window(rowptr, col, s.Te / p["Tmax"], K, 16 * p["dt_sub"], 4, 0.05)
+    To = y * p["Tmax"]
+    assert np.max(np.abs(Tg - To) / To) < 1e-5
+    assert np.max(np.abs(To - s.Te)) > 1.0        # the window did move the temperatures
+    # every stage keeps the sum of temperatures
+    assert abs(Tg.sum() - s.Te.sum()) < 1e-6 * s.Te.sum()
+
+
+def test_fallback_is_the_plain_path():
+    # tau = 0: the window is redone with plain substeps, bit for bit
+    import torch
+    from paper_1810_12357_gb300 import Ehc, EhcCheb
+    s = I.track_system(8, 22, r0=6.0)
+    p = I.params_track()
+    a, x, v = _ctx(s, p)
+    b, _, _ = _ctx(s, p)
+    w = EhcCheb(a, 16, 4, 0.05)
+    for _ in range(3):
+        fb, rho = w.step(0.0)
+        assert fb and rho > 0.0
+        b.substep(16)
+    assert np.array_equal(a.get_te().cpu().numpy(), b.get_te().cpu().numpy())
+    assert w.stats() == (3, 3)
+
+
+def test_accepted_windows_keep_the_ledger_closed():
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(8, 3, peak=6000.0)
+    p = dict(I.params_hotspot_fp64(), flux_prec=0, frozen=0, couple_mode=1, G=3e18)
+    g, x, v = _ctx(s, p)
+    w = EhcCheb(g, 16, 4, 0.05)
+    for step in range(3):
+        if step:
+            g.build_neighbors(x, v)
+        for _ in range(4):
+            fb, _ = w.step(1e30)
+            assert not fb
+        g.couple(v, 64 * p["dt_sub"])
+    e = g.energy()
+    assert abs(e["drift"]) < 1e-8
+    assert e["E_lat"] != 0.0
