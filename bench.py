@@ -410,6 +410,92 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_window(args):
+    """Chebyshev window propagator on the 4,000,000-atom track: every MD step
+    (build, 100 substeps' worth of electron evolution, hand-over, drift) advances
+    the electrons by windows of n_w substeps, each with `stages` flux evaluations,
+    the a-posteriori residual test and the fallback to plain substeps; the same
+    run with plain substeps from the same state is the reference and the judge
+    of the error."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc, EhcCheb
+    s, p = workload(args.cells)
+    n = s.n
+    n_w, st, tau = args.window, args.stages, args.tau
+    n_win = N_SUB // n_w
+    rest = N_SUB - n_win * n_w
+    stream = torch.cuda.current_stream()
+
+    def run(use_window):
+        g = Ehc(p, s)
+        g.set_te(s.Te)
+        x = torch.as_tensor(s.x, device="cuda").contiguous()
+        v = torch.as_tensor(s.v, device="cuda").contiguous()
+        w = None
+        stats = {"fallbacks": 0, "windows": 0, "rho": []}
+        t_fs = 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        evo = []   # the electron evolution of each timed MD step (windows or substeps)
+        for step in range(args.warmup + args.steps):
+            if step == args.warmup:
+                torch.cuda.synchronize()
+                e0.record(stream)
+            g.build_neighbors(x, v)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            if use_window:
+                if w is None:
+                    w = EhcCheb(g, n_w, st, args.damping)
+                for k in range(n_win):
+                    fb, rho = w.step(tau, t_fs + k * n_w * DT_SUB)
+                    if step >= args.warmup:
+                        stats["fallbacks"] += int(fb)
+                        stats["windows"] += 1
+                        stats["rho"].append(rho)
+                if rest:
+                    g.substep(rest, t_fs + n_win * n_w * DT_SUB)
+            else:
+                g.substep(N_SUB, t_fs)
+            a1.record(stream)
+            if step >= args.warmup:
+                evo.append((a0, a1))
+            g.couple(v, DT_MD)
+            g.drift(x, v, DT_MD)
+            t_fs += DT_MD
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats["evo_ms"] = sum(a.elapsed_time(b) for a, b in evo)
+        T = g.get_te()
+        e = g.energy()
+        return ms, T, e, stats
+
+    ms_w, Tw, ew, st_w = run(True)
+    ms_p, Tp, ep, st_p = run(False)
+    err = float(((Tw - Tp).abs() / Tp).max())
+    # value: the electrons' evolution alone (what the propagator stands in for)
+    value = n * N_SUB * args.steps / (st_w["evo_ms"] * 1e-3)
+    plain = n * N_SUB * args.steps / (st_p["evo_ms"] * 1e-3)
+    whole = n * N_SUB * args.steps / (ms_w * 1e-3)
+    whole_plain = n * N_SUB * args.steps / (ms_p * 1e-3)
+    rho = st_w["rho"] or [0.0]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_w / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 stages / f64 state and ledger", "data": "synthetic",
+            "config": config_dict(args.cells, n, {"path": "chebyshev window", "window_substeps": n_w,
+                                                 "stages": st, "damping": args.damping, "residual_tau": tau}),
+            "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
+                       "whole_md_step": {"value": whole, "plain_value": whole_plain,
+                                         "speedup_vs_plain": whole / whole_plain},
+                       "fallbacks": st_w["fallbacks"], "windows": st_w["windows"],
+                       "rho_median": float(np.median(rho)), "rho_max": float(np.max(rho)),
+                       "energy_drift": ew["drift"], "plain_energy_drift": ep["drift"],
+                       "md_steps_total": args.warmup + args.steps}}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Learned window propagator on the 4,000,000-atom track: windows of 16
     substeps advanced by the network (with the a-posteriori residual check and
@@ -508,7 +594,10 @@ def main():
     ap.add_argument("--ref-substeps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="track", choices=["track", "batch", "learned"])
+    ap.add_argument("--workload", default="track", choices=["track", "batch", "learned", "window"])
+    ap.add_argument("--window", type=int, default=20)
+    ap.add_argument("--stages", type=int, default=4)
+    ap.add_argument("--damping", type=float, default=0.05)
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)
@@ -524,6 +613,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "window":
+        run_window(args)
     else:
         run_gpu(args)
 

@@ -125,6 +125,7 @@ int ensure_t(Ctx &c) {
   if (c.t_stale) {
     CK(launch_merge(c, c.parity, c.stream));
     c.t_stale = false;
+    c.t_version += 1;
   }
   return EHC_OK;
 }
@@ -144,6 +145,7 @@ int ensure_split(Ctx &c) {
 }
 
 int run_substeps(Ctx &c, int32_t n_sub) {
+  c.t_version += 1;
   const int p0 = (c.p.flux_prec == 1) ? c.tcur : c.parity;
   const int ab = (c.A == c.abuf[0]) ? 0 : 1;
   const int path = (c.p.flux_prec == 1) ? 2 : (tile_path(c) ? 1 : 0);
@@ -408,6 +410,7 @@ void ehc_destroy(ehc_ctx *h) {
 int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
   if (!h || (!Te_dev && h->c.n > 0)) return EHC_E_INVAL;
   Ctx &c = h->c;
+  c.t_version += 1;
   if (c.n > 0) {
     CK(cudaMemcpyAsync(c.T[c.tcur], Te_dev, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
     CK(cudaMemsetAsync(c.A, 0, sizeof(double) * c.n, c.stream));
@@ -446,6 +449,7 @@ namespace {
 // first half of a neighbour build: queue every kernel and the copies of the
 // per-step scalars to pinned host memory (no synchronisation)
 int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev) {
+  c.t_version += 1;
   if (!c.have_te) return EHC_E_STATE;
   if (c.n > 0 && (!x_dev || !v_dev)) return EHC_E_INVAL;
   int r0 = ensure_t(c);
@@ -472,6 +476,7 @@ int build_finish(Ctx &c, bool own_tiles) {
   c.n_max = w[1];
   c.staged_max = w[2];
   c.row_max = w[3];
+  c.builds += 1;
   // size the row-tile buffers (grown only when a build outgrows them)
   if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
     int32_t tb = 0, grid[2] = {0, 0};
@@ -583,6 +588,7 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
 int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
   if (!h) return EHC_E_INVAL;
   Ctx &c = h->c;
+  c.t_version += 1;
   if (!c.built) return EHC_E_STATE;
   if (c.n > 0 && !v_dev && !c.p.frozen) return EHC_E_INVAL;
   int r = ensure_t(c);
@@ -779,6 +785,7 @@ int ehc_save(ehc_ctx *h, const char *path) {
 int ehc_load(ehc_ctx *h, const char *path) {
   if (!h || !path) return EHC_E_INVAL;
   Ctx &c = h->c;
+  c.t_version += 1;
   FILE *f = std::fopen(path, "rb");
   if (!f) return EHC_E_INVAL;
   CkptHeader hd;
@@ -1120,6 +1127,13 @@ struct ehc_cheb {
   float *rr[2] = {nullptr, nullptr};   // row value ranges of the stage values
   double *T1 = nullptr, *dTc = nullptr;
   int64_t windows = 0, fallbacks = 0;
+  // the row ranges of the state the next window starts from are in rr[rr_par]
+  // if the previous window was accepted and no build came in between
+  int64_t rr_build = -1;
+  int rr_par = 0;
+  // y[y0_buf] holds the values of the context's state while t_version == y0_version
+  int64_t y0_version = -1;
+  int y0_buf = 0;
 };
 
 namespace {
@@ -1246,17 +1260,31 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   int r = ensure_t(c);
   if (r) return r;
   const double *T0 = c.T[c.tcur];
+  double *T1 = c.T[c.tcur ^ 1];   // free outside builds and FP64 substeps; becomes the state on accept
   const double tauw = (double)w->n_w * c.p.dt_sub_fs;
-  // Y_0 and the row ranges of the first stage (unknown: widest tier)
-  CK(cheb_mirror(c, T0, w->y[0]));
-  CK(cudaMemsetAsync(w->rr[0], 0xfe, sizeof(float) * c.nrows, c.stream));
-  CK(cudaMemsetAsync(w->rr[0] + c.nrows, 0x7f, sizeof(float) * c.nrows, c.stream));
+  // Y_0: the previous window's end values if nothing touched T since, else from T
+  int b0 = 0;
+  if (w->y0_version == c.t_version) {
+    b0 = w->y0_buf;
+  } else {
+    CK(cheb_mirror(c, T0, w->y[0]));
+  }
+  // row ranges of the first stage: those of the previous window's end state when
+  // it was accepted since the last build, else unknown (widest tier)
   int par = 0;
+  if (w->rr_build == c.builds && w->y0_version == c.t_version) {
+    par = w->rr_par;
+  } else {
+    CK(cudaMemsetAsync(w->rr[0], 0xfe, sizeof(float) * c.nrows, c.stream));
+    CK(cudaMemsetAsync(w->rr[0] + c.nrows, 0x7f, sizeof(float) * c.nrows, c.stream));
+  }
+  w->rr_build = -1;
+  w->y0_version = -1;
   for (int j = 1; j <= w->s; ++j) {
     StageArgs sa;
-    sa.yin = w->y[(j - 1) % 3];
-    sa.yprev = j >= 2 ? w->y[(j - 2) % 3] : nullptr;
-    sa.yout = w->y[j % 3];
+    sa.yin = w->y[(b0 + j - 1) % 3];
+    sa.yprev = j >= 2 ? w->y[(b0 + j - 2) % 3] : nullptr;
+    sa.yout = w->y[(b0 + j) % 3];
     sa.Fout = j == 1 ? w->F0 : nullptr;
     sa.rr[0] = w->rr[0];
     sa.rr[1] = w->rr[1];
@@ -1265,32 +1293,38 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
     CK(launch_cheb_stage(c, sa, par, c.stream));
     par ^= 1;
   }
-  float *ys = w->y[w->s % 3];
-  CK(cheb_to_T(c, ys, w->T1));
-  // electron-phonon coupling over the window (kept in dTc until accepted)
-  CK(nn_couple_window(c, T0, w->T1, ys, w->dTc, w->n_w));
+  const int bs = (b0 + w->s) % 3;
+  float *ys = w->y[bs];
+  // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
+  CK(cheb_finish(c, T0, ys, T1, w->dTc, w->n_w));
   // pair flux of the end state for the residual
   StageArgs sf;
   sf.yin = ys;
   sf.yprev = nullptr;
-  sf.yout = w->y[(w->s + 1) % 3];
+  sf.yout = w->y[(bs + 1) % 3];
   sf.Fout = w->F1;
   sf.rr[0] = w->rr[0];
   sf.rr[1] = w->rr[1];
   sf.nu = 0.0f;
   sf.mt = 0.0f;
   CK(launch_cheb_stage(c, sf, par, c.stream));
-  CK(cheb_residual(c, T0, w->T1, w->F0, w->F1, tauw, w->part, w->rho));
+  CK(cheb_residual(c, T0, T1, w->F0, w->F1, tauw, w->part, w->rho));
   CK(cudaMemcpyAsync(w->host, w->rho, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
   const double rho = w->host[0];
   w->windows += 1;
   if (rho_out) *rho_out = rho;
   if (rho <= tau) {
-    CK(nn_accept(c, w->dTc));
-    CK(cudaMemcpyAsync(c.T[c.tcur], w->T1, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+    CK(cheb_accept(c, w->dTc));
+    c.tcur ^= 1;
     c.ff_valid = false;
     c.t_stale = false;
+    c.t_version += 1;
+    // ys is the state's mirror; the flux pass recorded its row ranges
+    w->y0_version = c.t_version;
+    w->y0_buf = bs;
+    w->rr_build = c.builds;
+    w->rr_par = par ^ 1;
     if (fell_back) *fell_back = 0;
     return EHC_OK;
   }
@@ -1439,6 +1473,7 @@ int ehc_nn_predict(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, double *Tout_
 int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_back, double *rho_out) {
   if (!nn || !hc || hc->c.n != nn->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
+  c.t_version += 1;
   if (!c.built) return EHC_E_STATE;
   if (!(c.stability <= 2.0)) return EHC_E_UNSTABLE;
   int r = ensure_t(c);

@@ -152,7 +152,8 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
 cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st);
 // kernels_window.cu (Chebyshev window propagator)
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y);
-cudaError_t cheb_to_T(Ctx &c, const float *y, double *T);
+cudaError_t cheb_finish(Ctx &c, const double *T0, float *y, double *T1, double *dTc, int n_w);
+cudaError_t cheb_accept(Ctx &c, const double *dTc);
 cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
                           float *part, float *out);
 int cheb_blocks(int64_t n);
@@ -257,6 +258,8 @@ struct Ctx {
   bool t_stale = false;          // T[tcur] is behind the float-float state
   int parity = 0;                // mirror buffer holding the current snapshot
   int64_t md_step = 0;
+  int64_t builds = 0;            // neighbour builds so far
+  int64_t t_version = 0;         // bumped by everything that changes or reorders T
   int32_t n_max = 0;             // largest neighbour count this MD step
   int32_t dev_err = 0;
 

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "ehc_internal.cuh"
 
 namespace ehc {
@@ -23,36 +25,33 @@ __global__ void mirror_kernel(int64_t n, const double *__restrict__ T, double Tr
   if (s < n) y[s] = (float)((T[s] - Tref) * invTmax);
 }
 
-__global__ void to_T_kernel(int64_t n, const float *__restrict__ y, double Tref, double Tmax,
-                            double *__restrict__ T) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s < n) T[s] = Tref + Tmax * (double)y[s];
-}
-
 // rho_i = |T1 - T0 - tau (R(T0) + R(T1)) / 2| / max(1 K, 1e-3 T0) with
-// R = Tmax K F - chi (G/C_e)(T - T_l) (the right-hand side of Eq. HeatTransport);
-// block maxima into part
+// R = Tmax K F - chi (G/C_e)(T - T_l) (the right-hand side of Eq. HeatTransport).
+// Only T1 - T0 is formed in FP64; the rest is single precision, ample for a
+// threshold of order one.  Grid-stride loop, block maxima into part.
 __global__ void __launch_bounds__(kWinThreads) residual_kernel(int64_t n, const double *__restrict__ T0,
                                                               const double *__restrict__ T1,
                                                               const float *__restrict__ F0,
                                                               const float *__restrict__ F1,
                                                               const float *__restrict__ uTl,
-                                                              const StepCoef *__restrict__ cf, double tau,
+                                                              const StepCoef *__restrict__ cf, float htau,
                                                               float *__restrict__ part) {
   __shared__ float red[kWinThreads / 32];
+  const float TK = (float)(cf->dtTK / cf->dt), cG = (float)(cf->dtcG / cf->dt);
+  const float Tref = (float)cf->Tref;
   float rho = 0.0f;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) {
-    const double TK = cf->dtTK / cf->dt, cG = cf->dtcG / cf->dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float ui = uTl[i];
     const bool chi = ui == ui;
-    const double Tl = chi ? cf->Tref - (double)ui : 0.0;
     const double t0 = T0[i], t1 = T1[i];
-    const double R0 = TK * (double)F0[i] - (chi ? cG * (t0 - Tl) : 0.0);
-    const double R1 = TK * (double)F1[i] - (chi ? cG * (t1 - Tl) : 0.0);
-    const double res = fabs(t1 - t0 - 0.5 * tau * (R0 + R1));
-    rho = (float)(res / fmax(1.0, 1e-3 * t0));
-    if (!(rho == rho)) rho = 3.0e38f;
+    const float dT = (float)(t1 - t0);
+    const float t0f = (float)t0;
+    // T - T_l = (T - Tref) + (Tref - T_l)
+    const float c0 = chi ? cG * ((t0f - Tref) + ui) : 0.0f;
+    const float c1 = chi ? cG * (((float)t1 - Tref) + ui) : 0.0f;
+    const float R = fmaf(TK, F0[i] + F1[i], -(c0 + c1));
+    const float r = fabsf(fmaf(-htau, R, dT)) / fmaxf(1.0f, 1e-3f * t0f);
+    rho = (r == r) ? fmaxf(rho, r) : 3.0e38f;
   }
   for (int o = 16; o > 0; o >>= 1) rho = fmaxf(rho, __shfl_down_sync(0xffffffffu, rho, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rho;
@@ -82,7 +81,12 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-int cheb_blocks(int64_t n) { return (int)nblk(n > 0 ? n : 1, kWinThreads); }
+constexpr int kResBlocks = 304;   // 2 x 152 SMs, grid-stride
+
+int cheb_blocks(int64_t n) {
+  (void)n;
+  return kResBlocks;
+}
 
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y) {
   if (c.n > 0)
@@ -90,17 +94,52 @@ cudaError_t cheb_mirror(Ctx &c, const double *T, float *y) {
   return cudaGetLastError();
 }
 
-cudaError_t cheb_to_T(Ctx &c, const float *y, double *T) {
-  if (c.n > 0) to_T_kernel<<<nblk(c.n, kWinThreads), kWinThreads, 0, c.stream>>>(c.n, y, c.p.Tref_K, c.p.Tmax_K, T);
+// T1 = Tref + Tmax y minus the coupling of the window, f (T0 - T_l) with
+// f = 1 - (1 - dt G/C_e)^n_w; the decrement (single precision, the same value
+// in T1 and in the ledger) goes to dTc, handed to the lattice ledger only if the
+// window is accepted, and y becomes the values of T1
+__global__ void finish_kernel(int64_t n, const double *__restrict__ T0, float *__restrict__ y,
+                              const float *__restrict__ uTl, float f, float Tref, float invTmax, double Tref_d,
+                              double Tmax_d, double *__restrict__ T1, double *__restrict__ dTc) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const float ys = y[s];
+  const float ui = uTl[s];
+  float dT = 0.0f;
+  if (ui == ui) dT = f * (((float)T0[s] - Tref) + ui);   // f (T0 - T_l), T_l = Tref - ui
+  const double dTd = (double)dT;
+  T1[s] = fma(Tmax_d, (double)ys, Tref_d) - dTd;
+  dTc[s] = dTd;
+  if (dT != 0.0f) y[s] = fmaf(-dT, invTmax, ys);
+}
+
+cudaError_t cheb_finish(Ctx &c, const double *T0, float *y, double *T1, double *dTc, int n_w) {
+  if (c.n == 0) return cudaSuccess;
+  const double f = 1.0 - std::pow(1.0 - c.p.dt_sub_fs * c.cG, (double)n_w);
+  finish_kernel<<<nblk(c.n, kWinThreads), kWinThreads, 0, c.stream>>>(
+      c.n, T0, y, c.uTl, (float)f, (float)c.p.Tref_K, (float)(1.0 / c.p.Tmax_K), c.p.Tref_K, c.p.Tmax_K, T1, dTc);
+  return cudaGetLastError();
+}
+
+// accepted window: its coupling energy to the ledger A
+__global__ void accept_kernel(int64_t n, const double *__restrict__ dTc, double VC, double *__restrict__ A) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double d = dTc[s];
+  if (d != 0.0) A[s] += VC * d;
+}
+
+cudaError_t cheb_accept(Ctx &c, const double *dTc) {
+  if (c.n > 0) accept_kernel<<<nblk(c.n, kWinThreads), kWinThreads, 0, c.stream>>>(c.n, dTc, c.VC, c.A);
   return cudaGetLastError();
 }
 
 cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
                           float *part, float *out) {
   if (c.n == 0) return cudaSuccess;
-  const unsigned nb = nblk(c.n, kWinThreads);
-  residual_kernel<<<nb, kWinThreads, 0, c.stream>>>(c.n, T0, T1, F0, F1, c.uTl, c.coef, tau, part);
-  max_kernel<<<1, 256, 0, c.stream>>>((int)nb, part, out);
+  residual_kernel<<<kResBlocks, kWinThreads, 0, c.stream>>>(c.n, T0, T1, F0, F1, c.uTl, c.coef, (float)(0.5 * tau),
+                                                           part);
+  max_kernel<<<1, 256, 0, c.stream>>>(kResBlocks, part, out);
   return cudaGetLastError();
 }
 
