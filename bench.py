@@ -420,6 +420,9 @@ def run_window(args):
     import torch
     from paper_1810_12357_gb300 import Ehc, EhcCheb
     s, p = workload(args.cells)
+    if args.frozen_lattice:
+        # hand-over to the electrons' ledger only: both runs see the same lattice
+        p = dict(p, frozen=1)
     n = s.n
     n_w, st, tau = args.window, args.stages, args.tau
     n_win = N_SUB // n_w
@@ -485,7 +488,8 @@ def run_window(args):
             "warmup": args.warmup, "ms_per_step": ms_w / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 stages / f64 state and ledger", "data": "synthetic",
             "config": config_dict(args.cells, n, {"path": "chebyshev window", "window_substeps": n_w,
-                                                 "stages": st, "damping": args.damping, "residual_tau": tau}),
+                                                 "stages": st, "damping": args.damping, "residual_tau": tau,
+                                                 "lattice": "frozen" if args.frozen_lattice else "Langevin, free flight"}),
             "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
                        "whole_md_step": {"value": whole, "plain_value": whole_plain,
                                          "speedup_vs_plain": whole / whole_plain},
@@ -598,6 +602,7 @@ def main():
     ap.add_argument("--window", type=int, default=20)
     ap.add_argument("--stages", type=int, default=4)
     ap.add_argument("--damping", type=float, default=0.05)
+    ap.add_argument("--frozen-lattice", action="store_true")
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)

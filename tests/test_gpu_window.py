@@ -86,3 +86,34 @@ def test_accepted_windows_keep_the_ledger_closed():
     e = g.energy()
     assert abs(e["drift"]) < 1e-8
     assert e["E_lat"] != 0.0
+
+
+def test_window_run_matches_the_reference_run():
+    # 20 windows of 25 substeps (5 stages) on a 55,296-atom track profile,
+    # coupling off: the GPU windows follow the FP64 reference windows; both
+    # differ from the plain substeps by about a per cent while the initial
+    # front is sharp (see the one-window bounds of the reference)
+    import torch
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.track_system(24, 2, r0=20.0)
+    p = dict(I.params_track(), G=0.0)
+    g, _, _ = _ctx(s, p)
+    K = g.energy()["K_per_fs"]
+    w = EhcCheb(g, 25, 5, 0.05)
+    for _ in range(20):
+        fb, _ = w.step(1e30)
+        assert not fb
+    Tg = g.get_te().cpu().numpy()
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    th = s.Te / p["Tmax"]
+    for _ in range(20):
+        th, _ = W.window(sim.rowptr, sim.col, th, K, 25 * p["dt_sub"], 5, 0.05)
+    To = th * p["Tmax"]
+    sim.substeps(500)
+    err_ref = float(np.max(np.abs(Tg - To) / To))
+    err_plain = float(np.max(np.abs(Tg - sim.T) / sim.T))
+    print(f"window run: vs FP64 windows {err_ref:.2e}, vs plain substeps {err_plain:.2e}")
+    assert err_ref < 1e-5
+    assert err_plain < 3e-2

@@ -136,3 +136,63 @@ def test_window_against_plain_substeps_on_the_track():
     assert errs[0] > 0.05
     assert errs[19] < 1e-3
     assert all(errs[k + 1] < errs[k] for k in range(0, 19, 3))
+
+
+def P2_closed(s, eps, z):
+    # P_s(z) = a_s + b_s T_s(w0 + w1 z), w1 = T_s'(w0)/T_s''(w0), b_s = T_s''/T_s'^2,
+    # a_s = 1 - b_s T_s(w0); T_s', T_s'' from x = cosh(t): T_s = cosh(s t),
+    # T_s' = s sinh(s t)/sinh t, T_s'' = (s^2 cosh(s t) sinh t - s sinh(s t) cosh t) / sinh^3 t
+    w0 = 1.0 + eps / (s * s)
+    t = math.acosh(w0)
+    Ts = math.cosh(s * t)
+    d1 = s * math.sinh(s * t) / math.sinh(t)
+    d2 = (s * s * math.cosh(s * t) * math.sinh(t) - s * math.sinh(s * t) * math.cosh(t)) / math.sinh(t) ** 3
+    w1 = d1 / d2
+    b = d2 / (d1 * d1)
+    return (1.0 - b * Ts) + b * T_closed(s, w0 + w1 * z)
+
+
+@pytest.mark.parametrize("s", [4, 7, 10])
+def test_second_order_stability_polynomial(s):
+    eps = 2.0 / 13.0
+    h = 1e-4
+    assert P2_closed(s, eps, 0.0) == pytest.approx(1.0, abs=1e-13)
+    assert (P2_closed(s, eps, h) - P2_closed(s, eps, -h)) / (2 * h) == pytest.approx(1.0, rel=1e-7)
+    d2 = (P2_closed(s, eps, h) - 2 * P2_closed(s, eps, 0.0) + P2_closed(s, eps, -h)) / (h * h)
+    assert d2 == pytest.approx(1.0, rel=1e-4)
+    b = W.beta2(s, eps)
+    assert b == pytest.approx(0.653 * s * s, rel=0.08)
+    zs = np.linspace(-b, 0.0, 2001)
+    assert max(abs(P2_closed(s, eps, z)) for z in zs) <= 1.0 + 1e-12
+    # the recurrence's coefficients reproduce the same polynomial on a scalar mode
+    _, _, mu, nu, mut, gam, _, _ = W.coefficients2(s, eps)
+    for z in (-0.3 * b, -0.8 * b):
+        y0, F0 = 1.0, z
+        ym2, ym1 = y0, y0 + mut[1] * F0
+        for j in range(2, s + 1):
+            y = (1 - mu[j] - nu[j]) * y0 + mu[j] * ym1 + nu[j] * ym2 + mut[j] * z * ym1 + gam[j] * z * y0
+            ym2, ym1 = ym1, y
+        assert ym1 == pytest.approx(P2_closed(s, eps, z), rel=1e-10, abs=1e-12)
+
+
+def test_second_order_window_on_a_lattice_mode_and_invariants():
+    a, x, rowptr, col = _fcc(6)
+    shell = I.fcc_shell_vectors(a, 4.0)
+    th0, amp, K = 0.003, 1e-9, 1.0
+    c = 1.0 - 2.0 * th0 * (1.0 - th0)
+    s, eps = 7, 2.0 / 13.0
+    k = 2.0 * math.pi / (3 * a)
+    lam = K * c * float((1.0 - np.cos(k * shell[:, 0])).sum())
+    mode = np.sin(k * x[:, 0])
+    for tau in (0.05, 0.9 * W.beta2(s, eps) / lam):
+        y, _ = W.window2(rowptr, col, th0 + amp * mode, K, tau, s, eps)
+        a1 = float((y - th0) @ mode / (mode @ mode))
+        assert a1 == pytest.approx(amp * P2_closed(s, eps, -tau * lam), rel=2e-5, abs=1e-17)
+    hs = I.hot_spot_system(5, 3, peak=9000.0)
+    rp, cl = oracle.neighbors(hs.x, hs.box, hs.periodic, 4.0)
+    th = hs.Te / 2.0e4
+    y, _ = W.window2(rp, cl, th, 20.0, 0.02, s, eps)
+    assert abs(y.sum() - th.sum()) < 1e-13 * th.sum()
+    u = np.full(hs.n, 0.0617)
+    yu, _ = W.window2(rp, cl, u, 20.0, 0.02, s, eps)
+    assert np.all(yu == u)
