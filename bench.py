@@ -424,7 +424,10 @@ def run_window(args):
         # hand-over to the electrons' ledger only: both runs see the same lattice
         p = dict(p, frozen=1)
     n = s.n
-    n_w, st, tau = args.window, args.stages, args.tau
+    n_w, st = args.window, args.stages
+    # the trapezoid residual of a 100-substep window is of order 50-70 on this
+    # workload; --tau given explicitly overrides
+    tau = args.tau if args.tau_given else 100.0
     n_win = N_SUB // n_w
     rest = N_SUB - n_win * n_w
     stream = torch.cuda.current_stream()
@@ -450,7 +453,7 @@ def run_window(args):
             a0.record(stream)
             if use_window:
                 if w is None:
-                    w = EhcCheb(g, n_w, st, args.damping)
+                    w = EhcCheb(g, n_w, st, args.damping, order=args.order)
                 for k in range(n_win):
                     fb, rho = w.step(tau, t_fs + k * n_w * DT_SUB)
                     if step >= args.warmup:
@@ -488,7 +491,8 @@ def run_window(args):
             "warmup": args.warmup, "ms_per_step": ms_w / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 stages / f64 state and ledger", "data": "synthetic",
             "config": config_dict(args.cells, n, {"path": "chebyshev window", "window_substeps": n_w,
-                                                 "stages": st, "damping": args.damping, "residual_tau": tau,
+                                                 "stages": st, "order": args.order, "damping": args.damping,
+                                                 "residual_tau": tau,
                                                  "lattice": "frozen" if args.frozen_lattice else "Langevin, free flight"}),
             "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
                        "whole_md_step": {"value": whole, "plain_value": whole_plain,
@@ -599,10 +603,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="track", choices=["track", "batch", "learned", "window"])
-    ap.add_argument("--window", type=int, default=20)
-    ap.add_argument("--stages", type=int, default=4)
-    ap.add_argument("--damping", type=float, default=0.05)
+    ap.add_argument("--window", type=int, default=100)
+    ap.add_argument("--stages", type=int, default=16)
+    ap.add_argument("--damping", type=float, default=2.0 / 13.0)
     ap.add_argument("--frozen-lattice", action="store_true")
+    ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)
@@ -610,6 +615,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--replicas", type=int, default=256)
     args = ap.parse_args()
+    args.tau_given = any(a == "--tau" or a.startswith("--tau=") for a in sys.argv[1:])
     if args.warmup < 3 and args.impl == "ehc":
         args.warmup = 3
     if args.impl == "reference":

@@ -256,26 +256,37 @@ void ehc_nn_destroy(ehc_nn *nn);
 
 /* ---- Chebyshev window propagator ---------------------------------------------
  * A window of n_window explicit substeps of Eq. HeatTransport is advanced with
- * `stages` evaluations of the pair flux instead of n_window: the first-order
- * damped Chebyshev recurrence (Runge-Kutta-Chebyshev family; no counterpart in
- * the paper, which integrates with plain explicit substeps).  With
- * theta = T / Tmax, tau_w = n_window dt and F_i = sum_j f(theta_i, theta_j):
+ * `stages` evaluations of the pair flux instead of n_window: the damped
+ * Chebyshev recurrences (Runge-Kutta-Chebyshev family, first or second order;
+ * no counterpart in the paper, which integrates with plain explicit substeps).
+ * With theta = T / Tmax, tau_w = n_window dt, F_i = sum_j f(theta_i, theta_j),
+ * w0 = 1 + damping / s^2 and T_j the Chebyshev polynomials (all at w0):
  *   Y_0 = theta,  Y_1 = Y_0 + mut_1 tau_w K F(Y_0),
- *   Y_j = Y_{j-1} + nu_j (Y_{j-2} - Y_{j-1}) + mut_j tau_w K F(Y_{j-1}),  j = 2..s,
- *   w0 = 1 + damping / s^2, w1 = T_s(w0) / T_s'(w0), b_j = 1 / T_j(w0),
- *   mut_1 = w1 / w0, nu_j = -b_j / b_{j-2}, mut_j = 2 w1 b_j / b_{j-1}
- * (T_j Chebyshev polynomials).  A linear mode of rate lambda is multiplied by
- * T_s(w0 - w1 tau_w lambda) / T_s(w0): stable while tau_w lambda <= (1 + w0)/w1,
- * about (2 - 4 damping / 3) s^2; every stage keeps sum_i T_i.  The coupling of
- * the window is applied after the stages as in ehc_nn_step, and so are the
- * residual test and the fallback to plain substeps.  Stages run in FP32 on the
- * row-tile path (values (T - Tref)/Tmax); contexts without it always fall back.
- * Single-precision flux, no laser source; bound to the context's atom count. */
+ *   Y_j = Y_{j-1} + nu_j (Y_{j-2} - Y_{j-1}) + kap_j (Y_0 - Y_{j-1})
+ *         + mut_j tau_w K F(Y_{j-1}) + gam_j tau_w K F(Y_0),   j = 2..s.
+ * order 1: w1 = T_s / T_s', b_j = 1 / T_j, mut_1 = w1 / w0, nu_j = -b_j / b_{j-2},
+ *   mut_j = 2 w1 b_j / b_{j-1}, kap = gam = 0; a linear mode of rate lambda is
+ *   multiplied by T_s(w0 - w1 tau_w lambda) / T_s(w0), stable while tau_w lambda
+ *   <= (1 + w0) / w1, about (2 - 4 damping / 3) s^2.
+ * order 2: w1 = T_s' / T_s'', b_j = T_j'' / T_j'^2 (b_0 = b_1 = b_2),
+ *   a_j = 1 - b_j T_j, mut_1 = b_1 w1, mu_j = 2 b_j w0 / b_{j-1}, nu_j = -b_j / b_{j-2},
+ *   mut_j = 2 b_j w1 / b_{j-1}, kap_j = 1 - mu_j - nu_j, gam_j = -a_{j-1} mut_j;
+ *   the multiplier a_s + b_s T_s(w0 - w1 tau_w lambda) agrees with exp(-tau_w lambda)
+ *   to second order; stable to about 0.65 s^2 (damping 2/13).
+ * Every stage keeps sum_i T_i.  The coupling of the window is applied after
+ * the stages as in ehc_nn_step, and so are the residual test and the fallback
+ * to plain substeps.  Stages run in FP32 on the row-tile path (values
+ * (T - Tref)/Tmax); contexts without it always fall back.  Single-precision
+ * flux, no laser source; bound to the context's atom count. */
 typedef struct ehc_cheb ehc_cheb;
-/* n_window >= 1, 2 <= stages <= 32, 0 <= damping <= 10 (EHC_E_INVAL otherwise). */
-int ehc_cheb_create(ehc_ctx *c, int32_t n_window, int32_t stages, double damping, ehc_cheb **out);
-/* nu and mut for j = 0..stages into host arrays of stages + 1 doubles (index 0 unused). */
-int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_host, double *mut_host);
+/* n_window >= 1, 2 <= stages <= 32, order 1 or 2, 0 <= damping <= 10
+ * (EHC_E_INVAL otherwise). */
+int ehc_cheb_create(ehc_ctx *c, int32_t n_window, int32_t stages, int32_t order, double damping,
+                    ehc_cheb **out);
+/* nu, mut and (if not NULL) kap, gam for j = 0..stages into host arrays of
+ * stages + 1 doubles (index 0 unused). */
+int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_host, double *mut_host, double *kap_host,
+                          double *gam_host);
 /* Advance the context by one window (see ehc_nn_step for rho, tau and the
  * fallback).  Synchronises once. */
 int ehc_cheb_step(ehc_cheb *w, ehc_ctx *c, double tau, double t_fs, int32_t *fell_back, double *rho_out);

@@ -93,8 +93,9 @@ _SIGS = {
     "ehc_nn_predict": (_I, [_P, _P, _P, _P]),
     "ehc_nn_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "ehc_nn_destroy": (None, [_P]),
-    "ehc_cheb_create": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_P)]),
-    "ehc_cheb_coefficients": (_I, [_P, _P, _P]),
+    "ehc_cheb_create": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                             ctypes.POINTER(_P)]),
+    "ehc_cheb_coefficients": (_I, [_P, _P, _P, _P, _P]),
     "ehc_cheb_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "ehc_cheb_stats": (_I, [_P, _P, _P]),
     "ehc_cheb_destroy": (None, [_P]),
@@ -457,14 +458,15 @@ class EhcNN:
 class EhcCheb:
     """Chebyshev window propagator bound to a context (ehc_cheb_*)."""
 
-    def __init__(self, ctx: "Ehc", n_window: int = 16, stages: int = 4, damping: float = 0.05):
+    def __init__(self, ctx: "Ehc", n_window: int = 16, stages: int = 4, damping: float = 0.05, order: int = 1):
         L = load_library()
         self._lib = L
         self.ctx = ctx
         self.n_window = int(n_window)
         self.stages = int(stages)
+        self.order = int(order)
         h = ctypes.c_void_p()
-        _check(L.ehc_cheb_create(ctx._h, self.n_window, self.stages, float(damping), ctypes.byref(h)),
+        _check(L.ehc_cheb_create(ctx._h, self.n_window, self.stages, self.order, float(damping), ctypes.byref(h)),
                "ehc_cheb_create")
         self._h = h
 
@@ -480,11 +482,11 @@ class EhcCheb:
             pass
 
     def coefficients(self):
-        nu = np.empty(self.stages + 1)
-        mut = np.empty(self.stages + 1)
-        _check(self._lib.ehc_cheb_coefficients(self._h, nu.ctypes.data_as(_P), mut.ctypes.data_as(_P)),
+        """(nu, mut, kap, gam) for stages 0..s (index 0 unused)."""
+        a = [np.empty(self.stages + 1) for _ in range(4)]
+        _check(self._lib.ehc_cheb_coefficients(self._h, *[x.ctypes.data_as(_P) for x in a]),
                "ehc_cheb_coefficients")
-        return nu, mut
+        return tuple(a)
 
     def step(self, tau: float, t_fs: float = 0.0):
         fb = ctypes.c_int32()

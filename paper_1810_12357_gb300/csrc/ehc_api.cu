@@ -1118,11 +1118,11 @@ int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
 // Chebyshev window propagator
 
 struct ehc_cheb {
-  int n_w = 16, s = 4;
+  int n_w = 16, s = 4, order = 1;
   double eps = 0.05;
   int64_t n = 0;
-  std::vector<double> nu, mut;     // stage coefficients, index 1..s
-  float *y[3] = {nullptr, nullptr, nullptr};   // stage values (padded to ps floats)
+  std::vector<double> nu, mut, kap, gam;   // stage coefficients, index 1..s
+  float *y[4] = {nullptr, nullptr, nullptr, nullptr};   // stage values (padded to ps floats)
   float *F0 = nullptr, *F1 = nullptr, *part = nullptr, *rho = nullptr, *host = nullptr;
   float *rr[2] = {nullptr, nullptr};   // row value ranges of the stage values
   double *T1 = nullptr, *dTc = nullptr;
@@ -1138,45 +1138,65 @@ struct ehc_cheb {
 
 namespace {
 
-// Chebyshev polynomial T_j and its derivative at x (three-term recurrence)
-void cheb_eval(int j, double x, double *T, double *dT) {
-  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
+// Chebyshev polynomial T_j and its first two derivatives at x (three-term
+// recurrence T_j = 2x T_{j-1} - T_{j-2}, differentiated)
+void cheb_eval(int j, double x, double *T, double *dT, double *ddT) {
+  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0, e0 = 0.0, e1 = 0.0;
   if (j == 0) {
     *T = 1.0;
     *dT = 0.0;
+    *ddT = 0.0;
     return;
   }
   for (int k = 1; k < j; ++k) {
-    const double t2 = 2.0 * x * t1 - t0, d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
+    const double t2 = 2.0 * x * t1 - t0, d2 = 2.0 * t1 + 2.0 * x * d1 - d0, e2 = 4.0 * d1 + 2.0 * x * e1 - e0;
     t0 = t1;
     t1 = t2;
     d0 = d1;
     d1 = d2;
+    e0 = e1;
+    e1 = e2;
   }
   *T = t1;
   *dT = d1;
+  *ddT = e1;
 }
 
-// first-order damped Chebyshev coefficients: w0 = 1 + eps/s^2,
-// w1 = T_s(w0)/T_s'(w0), b_j = 1/T_j(w0); nu_j = -b_j/b_{j-2},
-// mut_j = 2 w1 b_j/b_{j-1} (mut_1 = w1/w0)
-void cheb_coefficients(int s, double eps, std::vector<double> &nu, std::vector<double> &mut) {
+// Damped Chebyshev stage coefficients, w0 = 1 + eps/s^2.
+// order 1: w1 = T_s/T_s', b_j = 1/T_j; mut_1 = w1/w0, nu_j = -b_j/b_{j-2},
+//          mut_j = 2 w1 b_j/b_{j-1}, kap = gam = 0.
+// order 2: w1 = T_s'/T_s'', b_j = T_j''/T_j'^2 (b_0 = b_1 = b_2),
+//          a_j = 1 - b_j T_j; mut_1 = b_1 w1, mu_j = 2 b_j w0/b_{j-1},
+//          nu_j = -b_j/b_{j-2}, mut_j = 2 b_j w1/b_{j-1}, kap_j = 1 - mu_j - nu_j,
+//          gam_j = -a_{j-1} mut_j.  (All at w0.)
+void cheb_coefficients(int s, int order, double eps, ehc_cheb *w) {
   const double w0 = 1.0 + eps / ((double)s * s);
-  double Ts, dTs;
-  cheb_eval(s, w0, &Ts, &dTs);
-  const double w1 = Ts / dTs;
-  std::vector<double> b(s + 1);
-  for (int j = 0; j <= s; ++j) {
-    double T, dT;
-    cheb_eval(j, w0, &T, &dT);
-    b[j] = 1.0 / T;
+  std::vector<double> T(s + 1), d1(s + 1), d2(s + 1), b(s + 1);
+  for (int j = 0; j <= s; ++j) cheb_eval(j, w0, &T[j], &d1[j], &d2[j]);
+  w->nu.assign(s + 1, 0.0);
+  w->mut.assign(s + 1, 0.0);
+  w->kap.assign(s + 1, 0.0);
+  w->gam.assign(s + 1, 0.0);
+  if (order == 1) {
+    const double w1 = T[s] / d1[s];
+    for (int j = 0; j <= s; ++j) b[j] = 1.0 / T[j];
+    w->mut[1] = w1 / w0;
+    for (int j = 2; j <= s; ++j) {
+      w->nu[j] = -b[j] / b[j - 2];
+      w->mut[j] = 2.0 * w1 * b[j] / b[j - 1];
+    }
+    return;
   }
-  nu.assign(s + 1, 0.0);
-  mut.assign(s + 1, 0.0);
-  mut[1] = w1 / w0;
+  const double w1 = d1[s] / d2[s];
+  for (int j = 2; j <= s; ++j) b[j] = d2[j] / (d1[j] * d1[j]);
+  b[0] = b[1] = b[2];
+  w->mut[1] = b[1] * w1;
   for (int j = 2; j <= s; ++j) {
-    nu[j] = -b[j] / b[j - 2];
-    mut[j] = 2.0 * w1 * b[j] / b[j - 1];
+    const double mu = 2.0 * b[j] * w0 / b[j - 1];
+    w->nu[j] = -b[j] / b[j - 2];
+    w->mut[j] = 2.0 * b[j] * w1 / b[j - 1];
+    w->kap[j] = 1.0 - mu - w->nu[j];
+    w->gam[j] = -(1.0 - b[j - 1] * T[j - 1]) * w->mut[j];
   }
 }
 
@@ -1184,8 +1204,10 @@ void cheb_coefficients(int s, double eps, std::vector<double> &nu, std::vector<d
 
 extern "C" {
 
-int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, double damping, ehc_cheb **out) {
-  if (!hc || !out || n_window < 1 || stages < 2 || stages > 32 || !(damping >= 0.0) || damping > 10.0)
+int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order, double damping,
+                    ehc_cheb **out) {
+  if (!hc || !out || n_window < 1 || stages < 2 || stages > 32 || (order != 1 && order != 2) ||
+      !(damping >= 0.0) || damping > 10.0)
     return EHC_E_INVAL;
   *out = nullptr;
   Ctx &c = hc->c;
@@ -1194,14 +1216,15 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, double dampin
   if (!w) return EHC_E_NOMEM;
   w->n_w = n_window;
   w->s = stages;
+  w->order = order;
   w->eps = damping;
   w->n = c.n;
-  cheb_coefficients(stages, damping, w->nu, w->mut);
+  cheb_coefficients(stages, order, damping, w);
   const int64_t n = c.n > 0 ? c.n : 1;
   const int64_t np4 = c.ps > 0 ? c.ps : 4;
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
-  for (int k = 0; k < 3; ++k) A(dalloc(&w->y[k], np4));
+  for (int k = 0; k < 4; ++k) A(dalloc(&w->y[k], np4));
   A(dalloc(&w->F0, n));
   A(dalloc(&w->F1, n));
   A(dalloc(&w->part, cheb_blocks(n)));
@@ -1212,7 +1235,7 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, double dampin
   A(dalloc(&w->rr[1], 2 * (c.nrows > 0 ? c.nrows : 1)));
   A(cudaMallocHost((void **)&w->host, sizeof(float) * 4));
   if (ok)
-    for (int k = 0; k < 3; ++k) A(cudaMemsetAsync(w->y[k], 0, sizeof(float) * np4, c.stream));
+    for (int k = 0; k < 4; ++k) A(cudaMemsetAsync(w->y[k], 0, sizeof(float) * np4, c.stream));
   if (ok) A(cudaStreamSynchronize(c.stream));
   if (!ok) {
     cudaGetLastError();
@@ -1225,7 +1248,7 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, double dampin
 
 void ehc_cheb_destroy(ehc_cheb *w) {
   if (!w) return;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (w->y[k]) cudaFree(w->y[k]);
   void *p[] = {w->F0, w->F1, w->part, w->rho, w->T1, w->dTc, w->rr[0], w->rr[1]};
   for (void *q : p)
@@ -1234,11 +1257,13 @@ void ehc_cheb_destroy(ehc_cheb *w) {
   delete w;
 }
 
-int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_out, double *mut_out) {
+int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_out, double *mut_out, double *kap_out, double *gam_out) {
   if (!w || !nu_out || !mut_out) return EHC_E_INVAL;
   for (int j = 0; j <= w->s; ++j) {
     nu_out[j] = w->nu[j];
     mut_out[j] = w->mut[j];
+    if (kap_out) kap_out[j] = w->kap[j];
+    if (gam_out) gam_out[j] = w->gam[j];
   }
   return EHC_OK;
 }
@@ -1262,13 +1287,16 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   const double *T0 = c.T[c.tcur];
   double *T1 = c.T[c.tcur ^ 1];   // free outside builds and FP64 substeps; becomes the state on accept
   const double tauw = (double)w->n_w * c.p.dt_sub_fs;
-  // Y_0: the previous window's end values if nothing touched T since, else from T
+  // Y_0 stays in y[b0] through the window (the second-order stages use it);
+  // the stages rotate through the other three buffers.  Y_0 is the previous
+  // window's end values if nothing touched T since, else made from T.
   int b0 = 0;
   if (w->y0_version == c.t_version) {
     b0 = w->y0_buf;
   } else {
     CK(cheb_mirror(c, T0, w->y[0]));
   }
+  float *rot[3] = {w->y[(b0 + 1) & 3], w->y[(b0 + 2) & 3], w->y[(b0 + 3) & 3]};
   // row ranges of the first stage: those of the previous window's end state when
   // it was accepted since the last build, else unknown (widest tier)
   int par = 0;
@@ -1280,29 +1308,41 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   }
   w->rr_build = -1;
   w->y0_version = -1;
+  const float *Y0 = w->y[b0];
   for (int j = 1; j <= w->s; ++j) {
     StageArgs sa;
-    sa.yin = w->y[(b0 + j - 1) % 3];
-    sa.yprev = j >= 2 ? w->y[(b0 + j - 2) % 3] : nullptr;
-    sa.yout = w->y[(b0 + j) % 3];
+    sa.yin = j == 1 ? Y0 : rot[(j - 2) % 3];
+    sa.yprev = j == 1 ? nullptr : (j == 2 ? Y0 : rot[(j - 3) % 3]);
+    sa.yout = rot[(j - 1) % 3];
     sa.Fout = j == 1 ? w->F0 : nullptr;
+    const bool second = w->order == 2 && j >= 2;
+    sa.y0 = second ? Y0 : nullptr;
+    sa.F0 = second ? w->F0 : nullptr;
     sa.rr[0] = w->rr[0];
     sa.rr[1] = w->rr[1];
     sa.nu = (float)w->nu[j];
     sa.mt = (float)(w->mut[j] * tauw * c.K);
+    sa.kap = (float)w->kap[j];
+    sa.gt = (float)(w->gam[j] * tauw * c.K);
     CK(launch_cheb_stage(c, sa, par, c.stream));
     par ^= 1;
   }
-  const int bs = (b0 + w->s) % 3;
-  float *ys = w->y[bs];
+  float *ys = rot[(w->s - 1) % 3];
+  int bs = 0;
+  for (int k = 0; k < 4; ++k)
+    if (w->y[k] == ys) bs = k;
   // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
   CK(cheb_finish(c, T0, ys, T1, w->dTc, w->n_w));
   // pair flux of the end state for the residual
   StageArgs sf;
   sf.yin = ys;
   sf.yprev = nullptr;
-  sf.yout = w->y[(bs + 1) % 3];
+  sf.y0 = nullptr;
+  sf.F0 = nullptr;
+  sf.yout = rot[w->s % 3];   // scratch (Y_{s-1} or an older stage)
   sf.Fout = w->F1;
+  sf.kap = 0.0f;
+  sf.gt = 0.0f;
   sf.rr[0] = w->rr[0];
   sf.rr[1] = w->rr[1];
   sf.nu = 0.0f;

@@ -111,15 +111,19 @@ struct RepArgs {
 };
 
 // Arguments of a Chebyshev-window stage launch of the row-tile kernel: pair
-// flux of the values yin, Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + mt F into
-// yout, and optionally F itself into Fout (values as delta = (T - Tref)/Tmax).
+// flux F of the values yin and the stage update
+//   Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + kap (Y_0 - Y_{j-1}) + mt F + gt F_0
+// into yout (values as delta = (T - Tref)/Tmax), optionally F itself into Fout.
+// The Y_0 and F_0 terms belong to the second-order recurrence (null otherwise).
 struct StageArgs {
   const float *yin;     // Y_{j-1}: the values the tiles are copied from (padded to ps)
   const float *yprev;   // Y_{j-2} (null for the first stage)
+  const float *y0;      // Y_0 (null: no kap term)
+  const float *F0;      // F(Y_0) (null: no gt term)
   float *yout;          // Y_j
   float *Fout;          // the pair-flux sum F(Y_{j-1}) per atom, or null
   float *rr[2];         // row value ranges of the stage values (read [parity], write [parity ^ 1])
-  float nu, mt;         // nu_j and mut_j tau K
+  float nu, mt, kap, gt;   // nu_j, mut_j tau K, 1 - mu_j - nu_j, gam_j tau K
 };
 
 // Deterministic block-partial reductions.

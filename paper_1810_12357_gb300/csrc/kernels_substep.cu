@@ -295,9 +295,12 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
   if (STAGE) {
-    // Chebyshev stage: Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + mut tau K F(Y_{j-1});
-    // ui carries Y_{j-2} of this atom
-    const float h = di + fmaf(sa.nu, ui - di, sa.mt * F);
+    // Chebyshev stage: Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + kap (Y_0 - Y_{j-1})
+    // + mut tau K F(Y_{j-1}) + gam tau K F(Y_0); ui carries Y_{j-2}, li Y_0 and
+    // Ai F(Y_0) of this atom
+    float inc = sa.mt * F;
+    if (sa.y0) inc = fmaf(sa.kap, li - di, fmaf(sa.gt, (float)Ai, inc));
+    const float h = di + fmaf(sa.nu, ui - di, inc);
     sa.yout[s] = h;
     if (sa.Fout) sa.Fout[s] = F;
     return h;
@@ -459,6 +462,10 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       double Ai = 0.0;
       if (STAGE) {
         ui = sa.yprev ? sa.yprev[s] : di;
+        if (sa.y0) {
+          li = sa.y0[s];
+          Ai = (double)sa.F0[s];
+        }
       } else {
         ui = D.ra.uTl[s];
         li = D.ra.lo[s];

@@ -27,25 +27,37 @@ def test_coefficients_match_the_reference():
     g, _, _ = _ctx(s, dict(I.params_hotspot_fp64(), flux_prec=0))
     for st, eps in ((4, 0.05), (6, 0.3), (2, 0.0)):
         w = EhcCheb(g, 16, st, eps)
-        nu, mut = w.coefficients()
+        nu, mut, kap, gam = w.coefficients()
         _, _, _, nu_o, mut_o = W.coefficients(st, eps)
         assert np.allclose(nu[1:], nu_o[1:], rtol=1e-13, atol=1e-15)
         assert np.allclose(mut[1:], mut_o[1:], rtol=1e-13, atol=1e-15)
+        assert np.all(kap == 0.0) and np.all(gam == 0.0)
+    for st in (4, 10):
+        eps = 2.0 / 13.0
+        w = EhcCheb(g, 16, st, eps, order=2)
+        nu, mut, kap, gam = w.coefficients()
+        _, _, mu_o, nu_o, mut_o, gam_o, _, _ = W.coefficients2(st, eps)
+        assert np.allclose(nu[2:], nu_o[2:], rtol=1e-12, atol=1e-14)
+        assert np.allclose(mut[1:], mut_o[1:], rtol=1e-12, atol=1e-14)
+        assert np.allclose(kap[2:], 1.0 - mu_o[2:] - nu_o[2:], rtol=1e-10, atol=1e-13)
+        assert np.allclose(gam[2:], gam_o[2:], rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("peak", [3000.0, 12000.0])
-def test_one_window_matches_the_fp64_reference(peak):
+@pytest.mark.parametrize("peak,order", [(3000.0, 1), (12000.0, 1), (12000.0, 2)])
+def test_one_window_matches_the_fp64_reference(peak, order):
     from paper_1810_12357_gb300 import EhcCheb
     s = I.hot_spot_system(10, 1, peak=peak)
     p = dict(I.params_hotspot_fp64(), flux_prec=0, G=0.0)
     g, _, _ = _ctx(s, p)
     K = g.energy()["K_per_fs"]
-    w = EhcCheb(g, 16, 4, 0.05)
+    st, eps = (4, 0.05) if order == 1 else (6, 2.0 / 13.0)
+    w = EhcCheb(g, 16, st, eps, order=order)
     fb, rho = w.step(1e30)
     assert not fb
     Tg = g.get_te().cpu().numpy()
     rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"])
-    y, _ = W.window(rowptr, col, s.Te / p["Tmax"], K, 16 * p["dt_sub"], 4, 0.05)
+    win = W.window if order == 1 else W.window2
+    y, _ = win(rowptr, col, s.Te / p["Tmax"], K, 16 * p["dt_sub"], st, eps)
     To = y * p["Tmax"]
     assert np.max(np.abs(Tg - To) / To) < 1e-5
     assert np.max(np.abs(To - s.Te)) > 1.0        # the window did move the temperatures
