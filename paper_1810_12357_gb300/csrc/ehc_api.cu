@@ -1123,6 +1123,7 @@ struct ehc_cheb {
   int64_t n = 0;
   std::vector<double> nu, mut, kap, gam;   // stage coefficients, index 1..s
   float *y[4] = {nullptr, nullptr, nullptr, nullptr};   // stage values (padded to ps floats)
+  float *z[4] = {nullptr, nullptr, nullptr, nullptr};   // the window's change Y_j - Y_0 (z[3]: scratch)
   float *F0 = nullptr, *F1 = nullptr, *part = nullptr, *rho = nullptr, *host = nullptr;
   float *rr[2] = {nullptr, nullptr};   // row value ranges of the stage values
   double *T1 = nullptr, *dTc = nullptr;
@@ -1225,6 +1226,7 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
   for (int k = 0; k < 4; ++k) A(dalloc(&w->y[k], np4));
+  for (int k = 0; k < 4; ++k) A(dalloc(&w->z[k], n));
   A(dalloc(&w->F0, n));
   A(dalloc(&w->F1, n));
   A(dalloc(&w->part, cheb_blocks(n)));
@@ -1248,8 +1250,10 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order
 
 void ehc_cheb_destroy(ehc_cheb *w) {
   if (!w) return;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 4; ++k) {
     if (w->y[k]) cudaFree(w->y[k]);
+    if (w->z[k]) cudaFree(w->z[k]);
+  }
   void *p[] = {w->F0, w->F1, w->part, w->rho, w->T1, w->dTc, w->rr[0], w->rr[1]};
   for (void *q : p)
     if (q) cudaFree(q);
@@ -1312,12 +1316,13 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   for (int j = 1; j <= w->s; ++j) {
     StageArgs sa;
     sa.yin = j == 1 ? Y0 : rot[(j - 2) % 3];
-    sa.yprev = j == 1 ? nullptr : (j == 2 ? Y0 : rot[(j - 3) % 3]);
+    sa.y0 = Y0;
+    sa.zin = j >= 2 ? w->z[(j - 2) % 3] : nullptr;
+    sa.zprev = j >= 3 ? w->z[(j - 3) % 3] : nullptr;
+    sa.zout = w->z[(j - 1) % 3];
     sa.yout = rot[(j - 1) % 3];
     sa.Fout = j == 1 ? w->F0 : nullptr;
-    const bool second = w->order == 2 && j >= 2;
-    sa.y0 = second ? Y0 : nullptr;
-    sa.F0 = second ? w->F0 : nullptr;
+    sa.F0 = (w->order == 2 && j >= 2) ? w->F0 : nullptr;
     sa.rr[0] = w->rr[0];
     sa.rr[1] = w->rr[1];
     sa.nu = (float)w->nu[j];
@@ -1328,18 +1333,21 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
     par ^= 1;
   }
   float *ys = rot[(w->s - 1) % 3];
+  const float *zs = w->z[(w->s - 1) % 3];
   int bs = 0;
   for (int k = 0; k < 4; ++k)
     if (w->y[k] == ys) bs = k;
   // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
-  CK(cheb_finish(c, T0, ys, T1, w->dTc, w->n_w));
+  CK(cheb_finish(c, T0, zs, ys, T1, w->dTc, w->n_w));
   // pair flux of the end state for the residual
   StageArgs sf;
   sf.yin = ys;
-  sf.yprev = nullptr;
-  sf.y0 = nullptr;
+  sf.y0 = ys;
+  sf.zin = nullptr;
+  sf.zprev = nullptr;
   sf.F0 = nullptr;
   sf.yout = rot[w->s % 3];   // scratch (Y_{s-1} or an older stage)
+  sf.zout = w->z[3];         // scratch
   sf.Fout = w->F1;
   sf.kap = 0.0f;
   sf.gt = 0.0f;

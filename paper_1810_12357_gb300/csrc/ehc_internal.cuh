@@ -110,17 +110,21 @@ struct RepArgs {
   int32_t *err;
 };
 
-// Arguments of a Chebyshev-window stage launch of the row-tile kernel: pair
-// flux F of the values yin and the stage update
-//   Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + kap (Y_0 - Y_{j-1}) + mt F + gt F_0
-// into yout (values as delta = (T - Tref)/Tmax), optionally F itself into Fout.
-// The Y_0 and F_0 terms belong to the second-order recurrence (null otherwise).
+// Arguments of a Chebyshev-window stage launch of the row-tile kernel.  The
+// window's change z_j = Y_j - Y_0 is carried separately (single precision
+// relative to the change):
+//   z_j = z_{j-1} + nu (z_{j-2} - z_{j-1}) - kap z_{j-1} + mt F(Y_{j-1}) + gt F_0,
+//   Y_j = Y_0 + z_j (the values the next stage's tiles are copied from),
+// values as delta = (T - Tref)/Tmax; optionally F itself into Fout.  The kap and
+// F_0 terms belong to the second-order recurrence (F0 null otherwise).
 struct StageArgs {
   const float *yin;     // Y_{j-1}: the values the tiles are copied from (padded to ps)
-  const float *yprev;   // Y_{j-2} (null for the first stage)
-  const float *y0;      // Y_0 (null: no kap term)
+  const float *y0;      // Y_0
+  const float *zin;     // z_{j-1} (null: zero, the first stage)
+  const float *zprev;   // z_{j-2} (null: zero)
   const float *F0;      // F(Y_0) (null: no gt term)
   float *yout;          // Y_j
+  float *zout;          // z_j
   float *Fout;          // the pair-flux sum F(Y_{j-1}) per atom, or null
   float *rr[2];         // row value ranges of the stage values (read [parity], write [parity ^ 1])
   float nu, mt, kap, gt;   // nu_j, mut_j tau K, 1 - mu_j - nu_j, gam_j tau K
@@ -156,7 +160,7 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
 cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st);
 // kernels_window.cu (Chebyshev window propagator)
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y);
-cudaError_t cheb_finish(Ctx &c, const double *T0, float *y, double *T1, double *dTc, int n_w);
+cudaError_t cheb_finish(Ctx &c, const double *T0, const float *z, float *y, double *T1, double *dTc, int n_w);
 cudaError_t cheb_accept(Ctx &c, const double *dTc);
 cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
                           float *part, float *out);

@@ -280,10 +280,15 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
+// per-atom inputs of a Chebyshev stage
+struct StageIn {
+  float zm1, zm2, y0, F0;
+};
+
 template <int TIER, bool LASER, int PP, bool STAGE>
 __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, const StageArgs &sa, int parity,
                                           int k, const float *tile, int32_t s, float di, const uint32_t *pv,
-                                          float ui, float li, double Ai) {
+                                          float ui, float li, double Ai, const StageIn &si) {
   const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
@@ -295,12 +300,12 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
       F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
     }
   if (STAGE) {
-    // Chebyshev stage: Y_j = Y_{j-1} + nu (Y_{j-2} - Y_{j-1}) + kap (Y_0 - Y_{j-1})
-    // + mut tau K F(Y_{j-1}) + gam tau K F(Y_0); ui carries Y_{j-2}, li Y_0 and
-    // Ai F(Y_0) of this atom
-    float inc = sa.mt * F;
-    if (sa.y0) inc = fmaf(sa.kap, li - di, fmaf(sa.gt, (float)Ai, inc));
-    const float h = di + fmaf(sa.nu, ui - di, inc);
+    // Chebyshev stage on the window's change: z_j = z_{j-1} + nu (z_{j-2} - z_{j-1})
+    // - kap z_{j-1} + mut tau K F(Y_{j-1}) + gam tau K F(Y_0), Y_j = Y_0 + z_j
+    const float inc = fmaf(sa.gt, si.F0, fmaf(-sa.kap, si.zm1, sa.mt * F));
+    const float z = si.zm1 + fmaf(sa.nu, si.zm2 - si.zm1, inc);
+    const float h = si.y0 + z;
+    sa.zout[s] = z;
     sa.yout[s] = h;
     if (sa.Fout) sa.Fout[s] = F;
     return h;
@@ -460,22 +465,26 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
       const float di = tile[sb + q];
       float ui = 0.0f, li = 0.0f;
       double Ai = 0.0;
+      StageIn si = {0.0f, 0.0f, 0.0f, 0.0f};
       if (STAGE) {
-        ui = sa.yprev ? sa.yprev[s] : di;
-        if (sa.y0) {
-          li = sa.y0[s];
-          Ai = (double)sa.F0[s];
-        }
+        si.y0 = sa.y0[s];
+        if (sa.zin) si.zm1 = sa.zin[s];
+        if (sa.zprev) si.zm2 = sa.zprev[s];
+        if (sa.F0) si.F0 = sa.F0[s];
       } else {
         ui = D.ra.uTl[s];
         li = D.ra.lo[s];
         Ai = D.ra.A[s];
       }
       float h;
-      if (tier == 3) h = row_atom<3, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
-      else if (tier == 2) h = row_atom<2, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
-      else if (tier == 1) h = row_atom<1, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
-      else h = row_atom<0, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai);
+      if (tier == 3) h = row_atom<3, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
+                                                              si);
+      else if (tier == 2) h = row_atom<2, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
+                                                                   si);
+      else if (tier == 1) h = row_atom<1, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
+                                                                   si);
+      else h = row_atom<0, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
+                                                    si);
       vmin = fminf(vmin, h);
       vmax = fmaxf(vmax, h);
     }
