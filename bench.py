@@ -108,10 +108,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(cells: int):
+def workload(cells: int, tile_threads: int = 0):
     from paper_1810_12357_gb300 import inputs as I
     s = I.track_system(cells, seed=2)
-    p = I.params_track()
+    p = dict(I.params_track(), tile_threads=tile_threads)
     return s, p
 
 
@@ -140,7 +140,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    s, p = workload(args.cells)
+    s, p = workload(args.cells, args.tile_threads)
     n = s.n
     sim = Ehc(p, s)
     sim.set_te(s.Te)
@@ -352,7 +352,7 @@ def run_batch(args):
     from paper_1810_12357_gb300 import inputs as I
     ws, rank, local = _dist()
     systems = I.batch_replicas(args.replicas, 4)
-    p = I.params_track()
+    p = dict(I.params_track(), tile_threads=args.tile_threads)
     x = torch.as_tensor(np.concatenate([s.x for s in systems]), device="cuda").contiguous()
     v = torch.as_tensor(np.concatenate([s.v for s in systems]), device="cuda").contiguous()
     Te = torch.as_tensor(np.concatenate([s.Te for s in systems]), device="cuda").contiguous()
@@ -608,6 +608,7 @@ def main():
     ap.add_argument("--damping", type=float, default=2.0 / 13.0)
     ap.add_argument("--frozen-lattice", action="store_true")
     ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)

@@ -69,7 +69,10 @@ extern "C" {
  *                   penetration length, pulse centre and standard deviation
  *   seed            Philox4x32-10 key of the Langevin random force
  *   max_neighbors   width of the neighbour table (<= 0: 32, at most 64)
- *   use_graph       1: replay substep loops from a captured CUDA graph */
+ *   use_graph       1: replay substep loops from a captured CUDA graph
+ *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
+ *                   timing tuner on the first substep call of 8 or more substeps (and after
+ *                   tiles grow), 256 or 128 = fixed; both give identical results */
 typedef struct ehc_params {
   double rc_A;
   double dt_sub_fs;
@@ -96,7 +99,8 @@ typedef struct ehc_params {
   int32_t laser_on;
   int32_t max_neighbors;
   int32_t use_graph;
-  int32_t reserved[7];
+  int32_t tile_threads;
+  int32_t reserved[6];
 } ehc_params;
 
 /* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked

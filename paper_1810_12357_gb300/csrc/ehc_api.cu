@@ -150,14 +150,14 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   const int ab = (c.A == c.abuf[0]) ? 0 : 1;
   const int path = (c.p.flux_prec == 1) ? 2 : (tile_path(c) ? 1 : 0);
   const int pairs = (c.n_max + 1) / 2;
-  const int tile = c.tile_floats;
+  const int tile = c.tile_floats, nt = c.tile_nt;
   bool use_graph = c.p.use_graph && n_sub >= 4;
   if (use_graph) {
     int hit = -1;
     for (int i = 0; i < c.n_graphs; ++i) {
       const auto &e = c.graphs[i];
       if (e.n_sub == n_sub && e.parity == p0 && e.tcur == c.tcur && e.abuf == ab && e.path == path &&
-          e.pairs == pairs && e.tile == tile)
+          e.pairs == pairs && e.tile == tile && e.nt == nt)
         hit = i;
     }
     if (hit < 0) {
@@ -178,7 +178,7 @@ int run_substeps(Ctx &c, int32_t n_sub) {
         c.graphs[lru] = c.graphs[7];
         c.n_graphs = 7;
       }
-      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, path, pairs, tile, exec, 0};
+      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, path, pairs, tile, nt, exec, 0};
       hit = c.n_graphs++;
     }
     c.graphs[hit].last_use = ++c.use_clock;
@@ -275,6 +275,11 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   Ctx &c = h->c;
   c.p = *p;
   c.n = n_atoms;
+  if (p->tile_threads != 0 && p->tile_threads != 128 && p->tile_threads != 256) {
+    delete h;
+    return EHC_E_INVAL;
+  }
+  c.tile_nt_fixed = p->tile_threads;
   c.W = W;
   c.stream = (cudaStream_t)stream;
   c.g.rcq = llrint(p->rc_A * 1048576.0);
@@ -479,9 +484,12 @@ int build_finish(Ctx &c, bool own_tiles) {
   c.builds += 1;
   // size the row-tile buffers (grown only when a build outgrows them)
   if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
-    int32_t tb = 0, grid[2] = {0, 0};
-    if (tile_size(c.staged_max, c.num_sms, &tb, grid)) {
+    int32_t tb = 0, grid[2] = {0, 0}, grid128[2] = {0, 0};
+    if (tile_size(c.staged_max, c.num_sms, &tb, grid, grid128)) {
       c.tile_floats = tb;
+      c.tile_nt = 0;
+      c.tile_grid128[0] = grid128[0];
+      c.tile_grid128[1] = grid128[1];
       c.tile_grid[0] = grid[0];
       c.tile_grid[1] = grid[1];
     }
@@ -546,6 +554,36 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
 }
 
 
+}  // extern "C"
+
+namespace {
+
+// Tuner of the row-tile kernel's width: two substeps with 256 and two with 128
+// threads owning atoms, timed with events on the stream; the narrower form is
+// kept only if clearly faster.  Both forms give identical results (the same
+// arithmetic per atom), so the four substeps are ordinary substeps.
+template <typename Launch>
+int tune_width(cudaStream_t st, int32_t *nt_out, Launch launch) {
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&ev[i]));
+  CK(cudaEventRecord(ev[0], st));
+  for (int k = 0; k < 2; ++k) CK(launch(k, 256));
+  CK(cudaEventRecord(ev[1], st));
+  for (int k = 2; k < 4; ++k) CK(launch(k, 128));
+  CK(cudaEventRecord(ev[2], st));
+  CK(cudaEventSynchronize(ev[2]));
+  float t256 = 0.f, t128 = 0.f;
+  CK(cudaEventElapsedTime(&t256, ev[0], ev[1]));
+  CK(cudaEventElapsedTime(&t128, ev[1], ev[2]));
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  *nt_out = (t128 < 0.97f * t256) ? 128 : 256;
+  return EHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
   if (!h || n_sub < 0) return EHC_E_INVAL;
   Ctx &c = h->c;
@@ -578,7 +616,23 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
     }
     int r = ensure_split(c);
     if (r) return r;
-    r = run_substeps(c, chunk);
+    int32_t rest = chunk;
+    const int pw = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
+    if (c.tile_nt_fixed) c.tile_nt = c.tile_nt_fixed;
+    if (!laser && c.tile_nt == 0 && chunk >= 8 && tile_path(c) && c.tile_grid128[pw] > 0) {
+      const int p0 = c.parity;
+      c.t_version += 1;
+      int32_t chosen = 256;
+      r = tune_width(c.stream, &chosen, [&](int k, int nt) {
+        c.tile_nt = nt;
+        return launch_substep(c, k, p0 ^ (k & 1), c.stream);
+      });
+      c.tile_nt = chosen;
+      if (r) return r;
+      c.t_stale = true;
+      rest -= 4;   // an even count: the mirror parity is unchanged
+    }
+    r = run_substeps(c, rest);
     if (r) return r;
     done += chunk;
   }
@@ -843,10 +897,11 @@ struct ehc_batch {
   RepArgs *reps_dev = nullptr;
   int2 *work = nullptr;
   int32_t nwork = 0, tile_floats = 0, num_sms = 0;
-  int32_t tile_grid[2] = {0, 0};
+  int32_t tile_grid[2] = {0, 0}, tile_grid128[2] = {0, 0};
+  int32_t tile_nt = 0;           // threads owning atoms chosen by the tuner (0: not tuned yet)
   int parity = 0;
   struct G {
-    int n_sub, parity, pairs, tile;
+    int n_sub, parity, pairs, tile, nt;
     cudaGraphExec_t exec;
   };
   std::vector<G> graphs;
@@ -1000,9 +1055,12 @@ int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v
     tab[r] = rep_args(c);
   }
   if (staged > b->tile_floats) {
-    int32_t tb = 0, grid[2] = {0, 0};
-    if (tile_size(staged, b->num_sms, &tb, grid)) {
+    int32_t tb = 0, grid[2] = {0, 0}, grid128[2] = {0, 0};
+    if (tile_size(staged, b->num_sms, &tb, grid, grid128)) {
       b->tile_floats = tb;
+      b->tile_nt = 0;
+      b->tile_grid128[0] = grid128[0];
+      b->tile_grid128[1] = grid128[1];
       b->tile_grid[0] = grid[0];
       b->tile_grid[1] = grid[1];
     }
@@ -1038,18 +1096,34 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
   CK(batch_join(*b));
   const int p0 = b->parity;
   const int pairs = batch_pairs(*b);
+  const int pw = pairs == 9 ? 0 : 1;
+  int32_t rest = n_sub;
+  if (b->p.tile_threads) b->tile_nt = b->p.tile_threads;
+  if (b->tile_nt == 0 && n_sub >= 8 && b->tile_grid128[pw] > 0) {
+    int32_t chosen = 256;
+    int r = tune_width(b->stream, &chosen, [&](int k, int nt) {
+      return launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats,
+                                  nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw], pairs, p0 ^ (k & 1), k, nt,
+                                  b->stream);
+    });
+    if (r) return r;
+    b->tile_nt = chosen;
+    rest -= 4;   // an even count: the mirror parity is unchanged
+  }
+  const int nt = b->tile_nt == 128 ? 128 : 256;
+  const int32_t tgrid = nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw];
   int hit = -1;
   for (size_t i = 0; i < b->graphs.size(); ++i) {
     const auto &g = b->graphs[i];
-    if (g.n_sub == n_sub && g.parity == p0 && g.pairs == pairs && g.tile == b->tile_floats) hit = (int)i;
+    if (g.n_sub == rest && g.parity == p0 && g.pairs == pairs && g.tile == b->tile_floats && g.nt == nt)
+      hit = (int)i;
   }
   if (hit < 0) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int k = 0; k < n_sub && le == cudaSuccess; ++k)
-      le = launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats, b->tile_grid[pairs == 9 ? 0 : 1],
-                                pairs, p0 ^ (k & 1), k,
+    for (int k = 0; k < rest && le == cudaSuccess; ++k)
+      le = launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats, tgrid, pairs, p0 ^ (k & 1), k, nt,
                                 b->cap_stream);
     cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
     if (le != cudaSuccess || ee != cudaSuccess) return EHC_E_CUDA;
@@ -1061,7 +1135,7 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
       cudaGraphExecDestroy(b->graphs.front().exec);
       b->graphs.erase(b->graphs.begin());
     }
-    b->graphs.push_back({n_sub, p0, pairs, b->tile_floats, exec});
+    b->graphs.push_back({rest, p0, pairs, b->tile_floats, nt, exec});
     hit = (int)b->graphs.size() - 1;
   }
   CK(cudaGraphLaunch(b->graphs[hit].exec, b->stream));

@@ -154,9 +154,9 @@ bool tile_path(const Ctx &c);
 // tile capacity tb with headroom for the largest staged tile, the shared-memory
 // opt-in and the resident grid of each index width (9 and 16 words); false:
 // the buffers do not fit
-bool tile_size(int32_t staged, int num_sms, int32_t *tb, int32_t grid[2]);
+bool tile_size(int32_t staged, int num_sms, int32_t *tb, int32_t grid[2], int32_t grid128[2]);
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
-                                 int pairs, int parity, int k, cudaStream_t st);
+                                 int pairs, int parity, int k, int nt, cudaStream_t st);
 cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st);
 // kernels_window.cu (Chebyshev window propagator)
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y);
@@ -248,6 +248,9 @@ struct Ctx {
   int32_t row_max = 0;
   int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)
   int32_t tile_grid[2] = {0, 0};  // resident CTAs of the row-tile kernel (9 / 16 index words)
+  int32_t tile_grid128[2] = {0, 0};  // the same for its 128-thread form
+  int32_t tile_nt = 0;           // threads owning atoms chosen by the tuner (0: not tuned yet, 256)
+  int32_t tile_nt_fixed = 0;     // ehc_params.tile_threads (0: tuned)
   int32_t num_sms = 0;
   RepArgs *reps = nullptr;       // device table of the row-tile kernel (this system only)
   int2 *work = nullptr;          // (system, row) work list of the row-tile kernel
@@ -280,7 +283,7 @@ struct Ctx {
 
   // captured substep loops, keyed by everything a launch bakes in
   struct GraphEntry {
-    int n_sub, parity, tcur, abuf, path, pairs, tile;
+    int n_sub, parity, tcur, abuf, path, pairs, tile, nt;
     cudaGraphExec_t exec;
     uint64_t last_use;
   };

@@ -318,20 +318,22 @@ constexpr int kTileBufs = 2;   // tiles in flight per CTA
 constexpr int kDescAhead = 2;  // descriptors are prepared this many items ahead of their copies
 constexpr int kDescRing = kTileBufs + kDescAhead + 1;
 
+template <int NT>
 struct TilePipe {
   uint64_t full[kTileBufs];    // tile b holds its item (one arrival + the copied bytes)
   uint64_t empty[kTileBufs];   // every compute warp is done with tile b
   TileDesc desc[kDescRing];    // item it uses slot it % kDescRing
-  float wmin[kTileBufs][kTileThreads / 32], wmax[kTileBufs][kTileThreads / 32];
+  float wmin[kTileBufs][NT / 32], wmax[kTileBufs][NT / 32];
 };
 
 // producer side, after the compute warps released tile b of item it: the row's
 // value range for the tier choice of the next substep
-__device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity, float *rr_out = nullptr) {
+template <int NT>
+__device__ __forceinline__ void close_item(TilePipe<NT> &sp, int it, int parity, float *rr_out = nullptr) {
   const int b = it % kTileBufs;
   if ((threadIdx.x & 31) == 0) {
     float a = sp.wmin[b][0], c = sp.wmax[b][0];
-    for (int w = 1; w < kTileThreads / 32; ++w) {
+    for (int w = 1; w < NT / 32; ++w) {
       a = fminf(a, sp.wmin[b][w]);
       c = fmaxf(c, sp.wmax[b][w]);
     }
@@ -359,15 +361,16 @@ __device__ __forceinline__ void close_item(TilePipe &sp, int it, int parity, flo
 // STAGE: one stage of the Chebyshev window propagator instead of a substep
 // (pair flux of the tile values sa.yin, stage update into sa.yout, optionally
 // the flux itself into sa.Fout); rows and tiers as for substeps.
-template <bool LASER, int PP, bool STAGE>
-__global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
+// NT: threads that own atoms (256, or 128 for short rows); one producer warp more.
+template <bool LASER, int PP, bool STAGE, int NT>
+__global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTileMinBlocks)
     substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
                         int parity, int k, StageArgs sa) {
   extern __shared__ __align__(128) float tiles[];   // kTileBufs x tb words
-  __shared__ TilePipe sp;
+  __shared__ TilePipe<NT> sp;
   if ((int)blockIdx.x >= nwork) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int aw = kTileThreads / 32;   // warps 0..aw-1 compute; warp aw produces
+  const int aw = NT / 32;   // warps 0..aw-1 compute; warp aw produces
   const int n_it = (nwork - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (threadIdx.x == 0) {
     for (int b = 0; b < kTileBufs; ++b) {
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, kTileMinBlocks)
     const int64_t ps = D.ra.ps;
     const uint32_t *pidx = D.ra.pidx;
     float vmin = 3.0e38f, vmax = -3.0e38f;
-    for (int q = threadIdx.x; q < row_len; q += kTileThreads) {
+    for (int q = threadIdx.x; q < row_len; q += NT) {
       const int32_t s = row_s + q;
       uint32_t pv[PP];
 #pragma unroll
@@ -630,21 +633,23 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   } else if (tile_path(c)) {
     const int32_t P = (c.n_max + 1) / 2;
     const int32_t tb = c.tile_floats;
-    const int32_t tg = c.tile_grid[P == 9 ? 0 : 1];
-    const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
-    const unsigned nt = kTileThreads + 32;
     const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
-    if (P == 9) {
-      if (laser)
-        substep_tile_kernel<true, 9, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
-      else
-        substep_tile_kernel<false, 9, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
+    const bool narrow = c.tile_nt == 128 && !laser && c.tile_grid128[P == 9 ? 0 : 1] > 0;
+    const int32_t tg = narrow ? c.tile_grid128[P == 9 ? 0 : 1] : c.tile_grid[P == 9 ? 0 : 1];
+    const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
+    const StageArgs none{};
+    if (narrow) {
+      if (P == 9) substep_tile_kernel<false, 9, false, 128><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      else substep_tile_kernel<false, 16, false, 128><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
     } else {
-      if (laser)
-        substep_tile_kernel<true, 16, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, StageArgs{});
-      else
-        substep_tile_kernel<false, 16, false><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k,
-                                                                     StageArgs{});
+      const unsigned nt = kTileThreads + 32;
+      if (P == 9) {
+        if (laser) substep_tile_kernel<true, 9, false, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+        else substep_tile_kernel<false, 9, false, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      } else {
+        if (laser) substep_tile_kernel<true, 16, false, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+        else substep_tile_kernel<false, 16, false, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      }
     }
   } else {
     if (laser)
@@ -667,22 +672,27 @@ cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStrea
   const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
   const unsigned nt = kTileThreads + 32;
   const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
-  if (P == 9) substep_tile_kernel<false, 9, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
-  else substep_tile_kernel<false, 16, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
+  if (P == 9) substep_tile_kernel<false, 9, true, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
+  else substep_tile_kernel<false, 16, true, 256><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, 0, sa);
   return cudaGetLastError();
 }
 
-// one substep of the row-tile kernel over an explicit work list (batched systems)
+// one substep of the row-tile kernel over an explicit work list (batched
+// systems), nt = 256 or 128 threads owning atoms
 cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t nwork, int32_t tb, int grid,
-                                 int pairs, int parity, int k, cudaStream_t st) {
+                                 int pairs, int parity, int k, int nt, cudaStream_t st) {
   const unsigned g = (unsigned)(nwork < grid ? nwork : grid);
   if (g == 0) return cudaSuccess;
-  const unsigned nt = kTileThreads + 32;
   const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
-  if (pairs == 9)
-    substep_tile_kernel<false, 9, false><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k, StageArgs{});
-  else
-    substep_tile_kernel<false, 16, false><<<g, nt, shm, st>>>(reps, work, nwork, tb, parity, k, StageArgs{});
+  const StageArgs none{};
+  if (nt == 128) {
+    if (pairs == 9) substep_tile_kernel<false, 9, false, 128><<<g, 160, shm, st>>>(reps, work, nwork, tb, parity, k, none);
+    else substep_tile_kernel<false, 16, false, 128><<<g, 160, shm, st>>>(reps, work, nwork, tb, parity, k, none);
+  } else {
+    const unsigned ntt = kTileThreads + 32;
+    if (pairs == 9) substep_tile_kernel<false, 9, false, 256><<<g, ntt, shm, st>>>(reps, work, nwork, tb, parity, k, none);
+    else substep_tile_kernel<false, 16, false, 256><<<g, ntt, shm, st>>>(reps, work, nwork, tb, parity, k, none);
+  }
   return cudaGetLastError();
 }
 
@@ -690,17 +700,20 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
 // resized only when a build outgrows them), the shared-memory opt-in of every
 // instance and the resident grid of each width (grid[0]: 9 index words,
 // grid[1]: 16).
-bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2]) {
+bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], int32_t grid128[2]) {
   const int32_t tb = ((staged + staged / 8 + 64 + 255) / 256) * 256;
   const int64_t bytes = (int64_t)sizeof(float) * kTileBufs * tb;
   if (bytes > kTileMaxBytes) return false;
-  const void *inst[2][3] = {{(const void *)substep_tile_kernel<true, 9, false>,
-                             (const void *)substep_tile_kernel<false, 9, false>,
-                             (const void *)substep_tile_kernel<false, 9, true>},
-                            {(const void *)substep_tile_kernel<true, 16, false>,
-                             (const void *)substep_tile_kernel<false, 16, false>,
-                             (const void *)substep_tile_kernel<false, 16, true>}};
-  int32_t g[2] = {0, 0};
+  // [width][instance]: 256-thread instances (laser, plain, stage) and 128-thread ones (plain)
+  const void *inst[2][3] = {{(const void *)substep_tile_kernel<true, 9, false, 256>,
+                             (const void *)substep_tile_kernel<false, 9, false, 256>,
+                             (const void *)substep_tile_kernel<false, 9, true, 256>},
+                            {(const void *)substep_tile_kernel<true, 16, false, 256>,
+                             (const void *)substep_tile_kernel<false, 16, false, 256>,
+                             (const void *)substep_tile_kernel<false, 16, true, 256>}};
+  const void *inst128[2] = {(const void *)substep_tile_kernel<false, 9, false, 128>,
+                            (const void *)substep_tile_kernel<false, 16, false, 128>};
+  int32_t g[2] = {0, 0}, g128[2] = {0, 0};
   for (int w = 0; w < 2; ++w) {
     int bps = 1 << 30;
     bool ok = true;
@@ -713,12 +726,18 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2]) {
       bps = b < bps ? b : bps;
     }
     if (ok) g[w] = bps * num_sms;
+    int b = 0;
+    if (cudaFuncSetAttribute(inst128[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inst128[w], 160, (size_t)bytes) == cudaSuccess && b > 0)
+      g128[w] = b * num_sms;
   }
   cudaGetLastError();
   if (g[0] == 0 && g[1] == 0) return false;
   *tb_out = tb;
   grid[0] = g[0];
   grid[1] = g[1];
+  grid128[0] = g128[0];
+  grid128[1] = g128[1];
   return true;
 }
 

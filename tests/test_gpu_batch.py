@@ -64,3 +64,21 @@ def test_batch_replica_matches_oracle():
         err = float(np.max(np.abs(Tb[lo:lo + s.n] - sim.T) / sim.T))
         assert err < 1e-4, (r, err)
         assert abs(b.energy(r)["drift"]) < 1e-8
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_tile_widths_and_tuner_give_identical_results(batched):
+    # the 128- and 256-thread forms of the row-tile kernel, and the tuner's
+    # choice between them, change only the schedule: results are bit-identical
+    systems = I.batch_replicas(4, 9, n_min=8000, n_max=40000)
+    res = []
+    for tt in (256, 128, 0):
+        p = dict(I.params_track(), tile_threads=tt)
+        if batched:
+            b, _, _ = _run_batch(systems, p, 2, 20)
+            res.append(b.get_te().cpu().numpy())
+        else:
+            g, _, _ = run_gpu(systems[0], p, 2, 20)
+            res.append(g.get_te().cpu().numpy())
+    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[0], res[2])
