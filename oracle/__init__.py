@@ -51,6 +51,10 @@ def lib():
         L.oracle_pair_flux.restype = dbl
         L.oracle_flux_sum.argtypes = [i64, P, P, P, P]
         L.oracle_flux_sum.restype = None
+        L.oracle_pair_dflux_a.argtypes = [dbl, dbl]
+        L.oracle_pair_dflux_a.restype = dbl
+        L.oracle_flux_vjp.argtypes = [i64, P, P, P, P, P]
+        L.oracle_flux_vjp.restype = None
         L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
                                       dbl, P, P, dbl, dbl, dbl, P]
         L.oracle_substeps.restype = ctypes.c_int
@@ -141,6 +145,22 @@ def flux_sum(rowptr, col, theta):
     lib().oracle_flux_sum(n, _p(np.ascontiguousarray(rowptr, dtype=np.int64)),
                           _p(np.ascontiguousarray(col, dtype=np.int32)), _p(th), _p(F))
     return F
+
+
+def pair_dflux_a(a: float, b: float) -> float:
+    """d f(a, b) / d a of the pair term (Eq. HeatTransport)."""
+    return lib().oracle_pair_dflux_a(float(a), float(b))
+
+
+def flux_vjp(rowptr, col, theta, lam):
+    """out_m = sum_i lam_i dF_i/dtheta_m: the transposed Jacobian of flux_sum."""
+    n = rowptr.shape[0] - 1
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    lm = np.ascontiguousarray(lam, dtype=np.float64)
+    out = np.empty(n)
+    lib().oracle_flux_vjp(n, _p(np.ascontiguousarray(rowptr, dtype=np.int64)),
+                          _p(np.ascontiguousarray(col, dtype=np.int32)), _p(th), _p(lm), _p(out))
+    return out
 
 
 def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=None,

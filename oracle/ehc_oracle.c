@@ -272,6 +272,33 @@ void oracle_flux_sum(int64_t n, const int64_t *rowptr, const int32_t *col, const
   }
 }
 
+/* Partial derivative of the pair term in its first argument, from the same
+ * two-exponential form: d/da [b (1 - a) e^{a-b} - a (1 - b) e^{b-a}]
+ *   = -b e^{a-b} + b (1 - a) e^{a-b} - (1 - b) e^{b-a} + a (1 - b) e^{b-a}
+ *   = -( a b e^{a-b} + (1 - a)(1 - b) e^{b-a} ).
+ * Pins: central differences of oracle_pair_flux. */
+double oracle_pair_dflux_a(double a, double b) {
+  return -(a * b * exp(a - b) + (1.0 - a) * (1.0 - b) * exp(b - a));
+}
+
+/* Transposed Jacobian of the flux sum applied to lam (the adjoint of one
+ * flux evaluation): out_m = sum_i lam_i dF_i/dtheta_m, with
+ * F_i = sum_{j in row i} f(theta_i, theta_j).  Written as the plain double sum
+ * over rows i and their entries, not in any symmetrised form, so it holds for
+ * any list.  Pins: <u, J v> by central differences of oracle_flux_sum. */
+void oracle_flux_vjp(int64_t n, const int64_t *rowptr, const int32_t *col, const double *theta,
+                     const double *lam, double *out) {
+  for (int64_t m = 0; m < n; ++m) out[m] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      /* dF_i/dtheta_i gains d_a f(theta_i, theta_j); dF_i/dtheta_j gains
+       * d_b f(theta_i, theta_j) = -d_a f(theta_j, theta_i) (f is odd) */
+      out[i] += lam[i] * oracle_pair_dflux_a(theta[i], theta[j]);
+      out[j] -= lam[i] * oracle_pair_dflux_a(theta[j], theta[i]);
+    }
+}
+
 /* Optional time-dependent source (Sec. 5, Eq. LaserIntesity), a Gaussian pulse
  * absorbed with exponential decay below the irradiated surface:
  *   S(depth, t) = (F / l_p) exp(-depth / l_p) exp(-(t - t0)^2 / (2 s^2)) / (s sqrt(2 pi))

@@ -22,7 +22,11 @@ the same stability interval.
 
 Pinned in tests/test_oracle_window.py against the closed forms
 T_s(x) = cos(s arccos x) / cosh(s arccosh x), a linear-regime lattice mode,
-conservation and the uniform fixed point.
+conservation and the uniform fixed point.  The general stage form with free
+coefficients (window_general, its adjoint gradient window_grad and
+stability_polynomial, used to train windows) is pinned by reproducing both
+recurrences and their closed-form stability polynomials, and by central
+differences of the loss and of the flux sum (flux_vjp).
 """
 from __future__ import annotations
 
@@ -30,7 +34,7 @@ import math
 
 import numpy as np
 
-from . import flux_sum
+from . import flux_sum, flux_vjp
 
 
 def cheb(j: int, x: float) -> float:
@@ -161,3 +165,99 @@ def window(rowptr, col, theta, K: float, tau: float, s: int, eps: float, coeffs=
         y = y_prev + nu[j] * (y_prev2 - y_prev) + mut[j] * tau * K * F
         y_prev2, y_prev = y_prev, y
     return y_prev, F0
+
+
+# ---- windows with arbitrary stage coefficients (trained windows) ----------------
+#
+# The general stage of both recurrences above, written on the window's change
+# z_j = Y_j - Y_0 (z_0 = 0), with a_j = mut_j tau K and g_j = gam_j tau K:
+#   z_1 = a_1 F(Y_0),
+#   z_j = z_{j-1} + nu_j (z_{j-2} - z_{j-1}) - kap_j z_{j-1} + a_j F(Y_{j-1}) + g_j F(Y_0),
+# which is Y_j = (1 - mu_j - nu_j) Y_0 + mu_j Y_{j-1} + nu_j Y_{j-2} + ... with
+# kap_j = 1 - mu_j - nu_j.  Training treats nu, mut, kap, gam (stages 1..s) as
+# free parameters.
+
+
+def window_general(rowptr, col, theta, K: float, tau: float, coeffs):
+    """Stages of one window with coefficients (nu, mut, kap, gam), each indexed
+    j = 0..s (index 0 unused).  Returns (z, F): z[j] = Y_j - Y_0 for j = 0..s and
+    F[j] = F(Y_{j-1}) for j = 1..s (F[1] = F(Y_0))."""
+    nu, mut, kap, gam = (np.asarray(c, dtype=np.float64) for c in coeffs)
+    s = len(nu) - 1
+    y0 = np.asarray(theta, dtype=np.float64)
+    z = [np.zeros_like(y0)]
+    F = [None, flux_sum(rowptr, col, y0)]
+    z.append(mut[1] * tau * K * F[1])
+    for j in range(2, s + 1):
+        F.append(flux_sum(rowptr, col, y0 + z[j - 1]))
+        z.append(z[j - 1] + nu[j] * (z[j - 2] - z[j - 1]) - kap[j] * z[j - 1]
+                 + tau * K * (mut[j] * F[j] + gam[j] * F[1]))
+    return z, F
+
+
+def window_loss(T0, T1, z_s, Tmax: float) -> float:
+    """Training loss of a window: the mean squared relative error of the end
+    temperatures, mean_i ((T0_i + Tmax z_s,i - T1_i) / T0_i)^2."""
+    r = (np.asarray(T0) + Tmax * z_s - np.asarray(T1)) / np.asarray(T0)
+    return float(np.mean(r * r))
+
+
+def window_grad(rowptr, col, T0, T1, Tmax: float, K: float, tau: float, coeffs):
+    """Loss (window_loss) of the window started from T0 against the target T1,
+    and its gradient with respect to (nu, mut, kap, gam), by the adjoint of the
+    stage recurrence: with lam_j = dL/dz_j, going down from j = s,
+      dL/dnu_j = <lam_j, z_{j-2} - z_{j-1}>,  dL/dkap_j = -<lam_j, z_{j-1}>,
+      dL/dmut_j = tau K <lam_j, F(Y_{j-1})>,  dL/dgam_j = tau K <lam_j, F(Y_0)>,
+      lam_{j-1} += (1 - nu_j - kap_j) lam_j + a_j J(Y_{j-1})^T lam_j,
+      lam_{j-2} += nu_j lam_j,
+    J the Jacobian of the flux sum (flux_vjp); Y_0 is data, not a parameter.
+    Returns (loss, [g_nu, g_mut, g_kap, g_gam]) with entries for j = 0..s
+    (0 for j = 0, and for nu_1, kap_1, gam_1, which stage 1 does not use)."""
+    nu, mut, kap, gam = (np.asarray(c, dtype=np.float64) for c in coeffs)
+    s = len(nu) - 1
+    T0 = np.asarray(T0, dtype=np.float64)
+    T1 = np.asarray(T1, dtype=np.float64)
+    y0 = T0 / Tmax
+    z, F = window_general(rowptr, col, y0, K, tau, coeffs)
+    n = T0.shape[0]
+    loss = window_loss(T0, T1, z[s], Tmax)
+    lam = [np.zeros(n) for _ in range(s + 1)]
+    # d/dz_s of mean(((T0 + Tmax z_s - T1) / T0)^2)
+    lam[s] = 2.0 * Tmax * (T0 + Tmax * z[s] - T1) / (T0 * T0) / n
+    g = [np.zeros(s + 1) for _ in range(4)]
+    for j in range(s, 1, -1):
+        lj = lam[j]
+        g[0][j] = lj @ (z[j - 2] - z[j - 1])
+        g[1][j] = tau * K * (lj @ F[j])
+        g[2][j] = -(lj @ z[j - 1])
+        g[3][j] = tau * K * (lj @ F[1])
+        lam[j - 1] += (1.0 - nu[j] - kap[j]) * lj + mut[j] * tau * K * flux_vjp(rowptr, col, y0 + z[j - 1], lj)
+        lam[j - 2] += nu[j] * lj
+    g[1][1] = tau * K * (lam[1] @ F[1])
+    return loss, g
+
+
+def stability_polynomial(coeffs, x):
+    """P(x) of the stages on the linear test mode tau K F(Y) = -x Y (Y_0 = 1):
+    the factor one window applies to a mode of rate lambda, x = tau lambda."""
+    nu, mut, kap, gam = (np.asarray(c, dtype=np.float64) for c in coeffs)
+    s = len(nu) - 1
+    x = np.asarray(x, dtype=np.float64)
+    zm2 = np.zeros_like(x)
+    zm1 = -mut[1] * x
+    for j in range(2, s + 1):
+        z = zm1 + nu[j] * (zm2 - zm1) - kap[j] * zm1 - mut[j] * x * (1.0 + zm1) - gam[j] * x
+        zm2, zm1 = zm1, z
+    return 1.0 + zm1
+
+
+def coefficient_sets(s: int, order: int, eps: float):
+    """(nu, mut, kap, gam) of the damped Chebyshev recurrence of the given order
+    in the general stage form (kap = gam = 0 for order 1)."""
+    if order == 1:
+        _, _, mu, nu, mut = coefficients(s, eps)
+        return [nu.copy(), mut.copy(), np.zeros(s + 1), np.zeros(s + 1)]
+    _, _, mu, nu, mut, gam, _, _ = coefficients2(s, eps)
+    kap = 1.0 - mu - nu
+    kap[0] = kap[1] = 0.0
+    return [nu.copy(), mut.copy(), kap, gam.copy()]

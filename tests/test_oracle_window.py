@@ -196,3 +196,83 @@ def test_second_order_window_on_a_lattice_mode_and_invariants():
     u = np.full(hs.n, 0.0617)
     yu, _ = W.window2(rp, cl, u, 20.0, 0.02, s, eps)
     assert np.all(yu == u)
+
+
+# ---- windows with free stage coefficients (the trained window) ----------------
+
+def _small_system(seed=3):
+    # 5^3 FCC cells (500 atoms) with a smooth profile and a random ripple,
+    # theta within (0.01, 0.5)
+    _, x, rowptr, col = _fcc(5)
+    rng = np.random.default_rng(seed)
+    box = 5 * 3.615
+    th = 0.05 + 0.3 * np.exp(-np.sum((x - 0.5 * box) ** 2, axis=1) / 30.0) + 0.02 * rng.random(x.shape[0])
+    return rowptr, col, th
+
+
+def test_pair_derivative_matches_differences():
+    for a, b in [(0.1, 0.3), (0.5, 0.02), (0.7, 0.7), (0.01, 0.9), (0.33, 0.31)]:
+        h = 1e-6
+        fd = (oracle.pair_flux(a + h, b) - oracle.pair_flux(a - h, b)) / (2 * h)
+        assert oracle.pair_dflux_a(a, b) == pytest.approx(fd, rel=1e-8, abs=1e-10)
+    # at a = b the slope is -(a^2 + (1 - a)^2), the linearisation of the pair term
+    assert oracle.pair_dflux_a(0.2, 0.2) == pytest.approx(-(0.04 + 0.64), rel=1e-15)
+
+
+def test_flux_vjp_is_the_transposed_jacobian():
+    rowptr, col, th = _small_system()
+    rng = np.random.default_rng(1)
+    u, v = rng.normal(size=th.size), rng.normal(size=th.size)
+    h = 1e-6
+    Jv = (oracle.flux_sum(rowptr, col, th + h * v) - oracle.flux_sum(rowptr, col, th - h * v)) / (2 * h)
+    assert np.dot(u, Jv) == pytest.approx(np.dot(oracle.flux_vjp(rowptr, col, th, u), v), rel=1e-7)
+    # sum_i F_i = 0 for every state, so J^T 1 = 0
+    assert np.max(np.abs(oracle.flux_vjp(rowptr, col, th, np.ones(th.size)))) < 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_general_stages_reproduce_both_recurrences(order):
+    rowptr, col, th = _small_system()
+    K, tau, s = 40.0, 0.05, 6
+    C = W.coefficient_sets(s, order, 0.05 if order == 1 else 2 / 13)
+    z, _ = W.window_general(rowptr, col, th, K, tau, C)
+    if order == 1:
+        y, _ = W.window(rowptr, col, th, K, tau, s, 0.05)
+    else:
+        y, _ = W.window2(rowptr, col, th, K, tau, s, 2 / 13)
+    # same arithmetic in another rounding order (-kap z against kap (Y_0 - Y))
+    assert np.max(np.abs(th + z[s] - y)) < 1e-10
+    # and the general stability polynomial is the closed form of each family
+    for x in (0.0, 0.7, 3.0, 11.0, 0.5 * (W.beta(s, 0.05) if order == 1 else W.beta2(s, 2 / 13))):
+        want = P_closed(s, 0.05, -x) if order == 1 else P2_closed(s, 2 / 13, -x)
+        assert W.stability_polynomial(C, x) == pytest.approx(want, rel=1e-11, abs=1e-13)
+
+
+def test_window_gradient_matches_differences():
+    rowptr, col, th = _small_system()
+    K, tau, s, Tmax = 40.0, 0.06, 5, 20000.0
+    T0 = th * Tmax
+    C = W.coefficient_sets(s, 2, 2 / 13)
+    # target: the same window with perturbed coefficients, so the loss is not at a minimum
+    Ct = [c * (1.0 + 0.05 * np.sin(np.arange(c.size) + k)) for k, c in enumerate(C)]
+    zt, _ = W.window_general(rowptr, col, th, K, tau, Ct)
+    T1 = T0 + Tmax * zt[s]
+    loss, g = W.window_grad(rowptr, col, T0, T1, Tmax, K, tau, C)
+    assert loss > 0
+    checked = 0
+    for k in range(4):
+        for j in range(1, s + 1):
+            if j == 1 and k != 1:
+                assert g[k][j] == 0.0   # stage 1 uses mut_1 only
+                continue
+            h = 1e-6 * max(abs(C[k][j]), 1e-3)
+            Cp = [c.copy() for c in C]
+            Cm = [c.copy() for c in C]
+            Cp[k][j] += h
+            Cm[k][j] -= h
+            lp = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cp)[0][s], Tmax)
+            lm = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cm)[0][s], Tmax)
+            fd = (lp - lm) / (2 * h)
+            assert g[k][j] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(loss) / h), (k, j)
+            checked += 1
+    assert checked == 4 * s - 3
