@@ -296,6 +296,46 @@ int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_host, double *mut_host, 
 int ehc_cheb_step(ehc_cheb *w, ehc_ctx *c, double tau, double t_fs, int32_t *fell_back, double *rho_out);
 /* windows advanced and windows redone by plain substeps since creation */
 int ehc_cheb_stats(const ehc_cheb *w, int64_t *windows, int64_t *fallbacks);
+
+/* ---- trained windows -----------------------------------------------------------
+ * The stage coefficients nu, mut, kap, gam (j = 1..s) are free parameters that
+ * can be set and trained on windows of the plain method, so that s stages
+ * reproduce n_window explicit substeps of Eq. HeatTransport better than the
+ * damped Chebyshev values they start from (a learned propagator: a message-
+ * passing network of s layers whose message is the paper's pair flux and whose
+ * layer weights are learned; no counterpart in the paper).  In the form of the
+ * stages on the window's change z_j = Y_j - Y_0 (a_j = mut_j tau_w K,
+ * g_j = gam_j tau_w K):
+ *   z_1 = a_1 F(Y_0),
+ *   z_j = z_{j-1} + nu_j (z_{j-2} - z_{j-1}) - kap_j z_{j-1} + a_j F(Y_{j-1}) + g_j F(Y_0).
+ * Any coefficients keep sum_i T_i (every stage adds pair fluxes only). */
+/* Replace the coefficients (host arrays of stages + 1 doubles, index 0 unused;
+ * nu_1, kap_1 and gam_1 are ignored: stage 1 uses mut_1 only).  They become the
+ * base of training: Adam works on relative changes d, c = base (1 + d), so a
+ * coefficient set to 0 stays 0.  Resets the optimiser.  EHC_E_INVAL for
+ * non-finite values or |c| > 1e6.  Synchronises. */
+int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *c, const double *nu_host, const double *mut_host,
+                              const double *kap_host, const double *gam_host);
+/* One training step on one window: Tin_dev -> Ttar_dev (caller order, device; the
+ * target is the state after n_window plain substeps with the coupling off) on
+ * the context's neighbour list and K.  Loss mean_i ((T^_i - T*_i) / Tin_i)^2 of the
+ * s stages' prediction T^ to *loss_host; dL/d(nu, mut, kap, gam) to grad_host
+ * (4 (stages + 1) floats: the four sets one after another, index j within each)
+ * if not NULL.  If lr > 0, one Adam step of rate lr on the relative changes, on
+ * the loss plus a penalty that keeps |P(x)| <= 1 for the window's linear
+ * stability polynomial P on 0 < x <= 1.1 n_window s_c (s_c the context's
+ * per-substep stability number, a bound of dt lambda_max), after which the
+ * stages use the new coefficients.  Forward and backward run on the GPU (one
+ * thread per atom on the neighbour list, single precision, FP64 reductions);
+ * the first call allocates (1 + 3 stages) floats per atom.  Synchronises. */
+int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, const double *Ttar_dev, float lr,
+                        float *loss_host, float *grad_host);
+/* The stages' flux-only prediction of one window from Tin_dev into Tout_dev
+ * (caller order, device), with the training kernels. */
+int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, double *Tout_dev);
+/* Largest X such that |P(x)| <= 1 on [0, X] for the current coefficients (the
+ * window is stable for modes with tau_w lambda <= X); host computation. */
+int ehc_cheb_stability(const ehc_cheb *w, double *beta);
 void ehc_cheb_destroy(ehc_cheb *w);
 
 /* ---- Batched replicas --------------------------------------------------------

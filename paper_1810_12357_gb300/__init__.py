@@ -98,6 +98,10 @@ _SIGS = {
     "ehc_cheb_coefficients": (_I, [_P, _P, _P, _P, _P]),
     "ehc_cheb_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "ehc_cheb_stats": (_I, [_P, _P, _P]),
+    "ehc_cheb_set_coefficients": (_I, [_P, _P, _P, _P, _P, _P]),
+    "ehc_cheb_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, _P, _P]),
+    "ehc_cheb_predict": (_I, [_P, _P, _P, _P]),
+    "ehc_cheb_stability": (_I, [_P, _P]),
     "ehc_cheb_destroy": (None, [_P]),
     "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
                               ctypes.POINTER(_P)]),
@@ -501,3 +505,40 @@ class EhcCheb:
         f = ctypes.c_int64()
         _check(self._lib.ehc_cheb_stats(self._h, ctypes.byref(w), ctypes.byref(f)), "ehc_cheb_stats")
         return int(w.value), int(f.value)
+
+    def set_coefficients(self, nu, mut, kap, gam):
+        """Replace the stage coefficients (arrays of stages + 1, index 0 unused);
+        they become the base that training changes relatively."""
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (nu, mut, kap, gam)]
+        if any(x.shape != (self.stages + 1,) for x in a):
+            raise ValueError("coefficient arrays need stages + 1 entries")
+        _check(self._lib.ehc_cheb_set_coefficients(self._h, self.ctx._h, *[x.ctypes.data_as(_P) for x in a]),
+               "ehc_cheb_set_coefficients")
+
+    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False, ctx=None):
+        """Loss of the window Tin -> Ttar and (lr > 0) one Adam step on the
+        coefficients; `ctx` (same atom count) supplies the neighbour list and K.
+        With want_grad, also dL/d(nu, mut, kap, gam) as a (4, stages + 1) array."""
+        loss = ctypes.c_float()
+        g = np.empty(4 * (self.stages + 1), dtype=np.float32) if want_grad else None
+        c = ctx if ctx is not None else self.ctx
+        _check(self._lib.ehc_cheb_train_step(self._h, c._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr),
+                                             ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
+               "ehc_cheb_train_step")
+        if want_grad:
+            return float(loss.value), g.reshape(4, self.stages + 1)
+        return float(loss.value)
+
+    def predict(self, Tin, ctx=None):
+        """Flux-only prediction of one window from Tin (caller order)."""
+        import torch
+        out = torch.empty_like(Tin)
+        c = ctx if ctx is not None else self.ctx
+        _check(self._lib.ehc_cheb_predict(self._h, c._h, _ptr(Tin), _ptr(out)), "ehc_cheb_predict")
+        return out
+
+    def stability(self) -> float:
+        """Largest X with |P(x)| <= 1 on [0, X] for the current coefficients."""
+        b = ctypes.c_double()
+        _check(self._lib.ehc_cheb_stability(self._h, ctypes.byref(b)), "ehc_cheb_stability")
+        return float(b.value)

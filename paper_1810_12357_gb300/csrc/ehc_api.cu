@@ -1209,6 +1209,15 @@ struct ehc_cheb {
   // y[y0_buf] holds the values of the context's state while t_version == y0_version
   int64_t y0_version = -1;
   int y0_buf = 0;
+  // training of the coefficients (allocated at the first train or predict call):
+  // Adam on the relative changes d of the coefficients from `base`, c = base (1 + d)
+  std::vector<double> base[4];          // nu, mut, kap, gam at the last set (or creation)
+  float *tbuf = nullptr;                // y0 | z[1..s] | F[1..s] | lam[1..s], n floats each
+  double *tT0 = nullptr, *tT1 = nullptr, *tlpart = nullptr, *tdpart = nullptr;
+  float *tp = nullptr, *tm = nullptr, *tv = nullptr, *tgc = nullptr, *tgd = nullptr;
+  float *tc0 = nullptr, *tpen = nullptr, *tloss = nullptr;
+  float *thost = nullptr;               // pinned: pen[np] | loss | gc[np] | d[np]
+  int adam_t = 0;
 };
 
 namespace {
@@ -1275,6 +1284,116 @@ void cheb_coefficients(int s, int order, double eps, ehc_cheb *w) {
   }
 }
 
+// ---- training helpers ----
+int cheb_np(const ehc_cheb *w) { return 4 * (w->s + 1); }
+
+const std::vector<double> &cheb_set(const ehc_cheb *w, int q) {
+  return q == 0 ? w->nu : (q == 1 ? w->mut : (q == 2 ? w->kap : w->gam));
+}
+
+std::vector<double> &cheb_set(ehc_cheb *w, int q) {
+  return q == 0 ? w->nu : (q == 1 ? w->mut : (q == 2 ? w->kap : w->gam));
+}
+
+// P(x) of the stages on the linear test mode tau K F(Y) = -x Y (Y_0 = 1)
+double cheb_poly(const ehc_cheb *w, double x) {
+  double z2 = 0.0, z1 = -w->mut[1] * x;
+  for (int j = 2; j <= w->s; ++j) {
+    const double z = z1 + w->nu[j] * (z2 - z1) - w->kap[j] * z1 - w->mut[j] * x * (1.0 + z1) - w->gam[j] * x;
+    z2 = z1;
+    z1 = z;
+  }
+  return 1.0 + z1;
+}
+
+// Penalty wpen sum_k max(|P(x_k)| - 1, 0)^2 over x_k = xmax k / npts, k = 1..npts,
+// and its gradient with respect to the relative changes d (c = base (1 + d)),
+// carried through the recurrence in forward mode.
+double cheb_penalty(const ehc_cheb *w, double xmax, int npts, double wpen, std::vector<double> &g) {
+  const int s = w->s, np = cheb_np(w), S1 = s + 1;
+  g.assign(np, 0.0);
+  std::vector<double> d1(np), d2(np), d(np);
+  double pen = 0.0;
+  for (int k = 1; k <= npts; ++k) {
+    const double x = xmax * k / npts;
+    std::fill(d1.begin(), d1.end(), 0.0);
+    std::fill(d2.begin(), d2.end(), 0.0);
+    double z2 = 0.0, z1 = -w->mut[1] * x;
+    d1[S1 + 1] = -x * w->base[1][1];
+    for (int j = 2; j <= s; ++j) {
+      const double nu = w->nu[j], kap = w->kap[j], mu = w->mut[j], ga = w->gam[j];
+      const double z = z1 + nu * (z2 - z1) - kap * z1 - mu * x * (1.0 + z1) - ga * x;
+      const double c1 = 1.0 - nu - kap - mu * x;
+      for (int b = 0; b < np; ++b) d[b] = c1 * d1[b] + nu * d2[b];
+      d[j] += (z2 - z1) * w->base[0][j];
+      d[S1 + j] += -x * (1.0 + z1) * w->base[1][j];
+      d[2 * S1 + j] += -z1 * w->base[2][j];
+      d[3 * S1 + j] += -x * w->base[3][j];
+      d2.swap(d1);
+      d1.swap(d);
+      z2 = z1;
+      z1 = z;
+    }
+    const double P = 1.0 + z1, e = std::fabs(P) - 1.0;
+    if (e > 0.0) {
+      pen += wpen * e * e;
+      const double f = wpen * 2.0 * e * (P > 0.0 ? 1.0 : -1.0);
+      for (int b = 0; b < np; ++b) g[b] += f * d1[b];
+    }
+  }
+  return pen;
+}
+
+int cheb_train_prepare(ehc_cheb *w, Ctx &c) {
+  if (w->tbuf) return EHC_OK;
+  const int s = w->s, np = cheb_np(w);
+  const int64_t n = c.n > 0 ? c.n : 1;
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dalloc(&w->tbuf, n * (1 + 3 * (int64_t)s)));
+  A(dalloc(&w->tT0, n));
+  A(dalloc(&w->tT1, n));
+  A(dalloc(&w->tlpart, (int64_t)wt_loss_partials(n)));
+  A(dalloc(&w->tdpart, (int64_t)wt_dot_partials(n, s)));
+  for (float **q : {&w->tp, &w->tm, &w->tv, &w->tgc, &w->tgd, &w->tc0, &w->tpen}) A(dalloc(q, np));
+  A(dalloc(&w->tloss, 1));
+  A(cudaMallocHost((void **)&w->thost, sizeof(float) * (3 * np + 1)));
+  if (ok) {
+    for (float *q : {w->tp, w->tm, w->tv}) A(cudaMemsetAsync(q, 0, sizeof(float) * np, c.stream));
+    for (int b = 0; b < np; ++b) w->thost[b] = (float)w->base[b / (s + 1)][b % (s + 1)];
+    A(cudaMemcpyAsync(w->tc0, w->thost, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
+    A(cudaStreamSynchronize(c.stream));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    return EHC_E_NOMEM;
+  }
+  w->adam_t = 0;
+  return EHC_OK;
+}
+
+WtTab cheb_train_tab(const ehc_cheb *w, int64_t n) {
+  WtTab t{};
+  for (int j = 1; j <= w->s; ++j) {
+    t.z[j] = w->tbuf + n * j;
+    t.F[j] = w->tbuf + n * (w->s + j);
+    t.lam[j] = w->tbuf + n * (2 * w->s + j);
+  }
+  return t;
+}
+
+WtCoef cheb_train_coef(const ehc_cheb *w, const Ctx &c) {
+  WtCoef k{};
+  const double tauK = (double)w->n_w * c.p.dt_sub_fs * c.K;
+  for (int j = 1; j <= w->s; ++j) {
+    k.nu[j] = (float)w->nu[j];
+    k.kap[j] = (float)w->kap[j];
+    k.a[j] = (float)(w->mut[j] * tauK);
+    k.g[j] = (float)(w->gam[j] * tauK);
+  }
+  return k;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1295,6 +1414,7 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order
   w->eps = damping;
   w->n = c.n;
   cheb_coefficients(stages, order, damping, w);
+  for (int q = 0; q < 4; ++q) w->base[q] = cheb_set(w, q);
   const int64_t n = c.n > 0 ? c.n : 1;
   const int64_t np4 = c.ps > 0 ? c.ps : 4;
   bool ok = true;
@@ -1328,10 +1448,13 @@ void ehc_cheb_destroy(ehc_cheb *w) {
     if (w->y[k]) cudaFree(w->y[k]);
     if (w->z[k]) cudaFree(w->z[k]);
   }
-  void *p[] = {w->F0, w->F1, w->part, w->rho, w->T1, w->dTc, w->rr[0], w->rr[1]};
+  void *p[] = {w->F0,  w->F1,     w->part,   w->rho, w->T1, w->dTc, w->rr[0], w->rr[1], w->tbuf,
+               w->tT0, w->tT1,    w->tlpart, w->tdpart, w->tp, w->tm,  w->tv,    w->tgc,   w->tgd,
+               w->tc0, w->tpen,   w->tloss};
   for (void *q : p)
     if (q) cudaFree(q);
   if (w->host) cudaFreeHost(w->host);
+  if (w->thost) cudaFreeHost(w->thost);
   delete w;
 }
 
@@ -1387,6 +1510,9 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   w->rr_build = -1;
   w->y0_version = -1;
   const float *Y0 = w->y[b0];
+  // the F(Y_0) term of the later stages (second order, or trained coefficients)
+  bool use_f0 = false;
+  for (int j = 2; j <= w->s; ++j) use_f0 = use_f0 || w->gam[j] != 0.0;
   for (int j = 1; j <= w->s; ++j) {
     StageArgs sa;
     sa.yin = j == 1 ? Y0 : rot[(j - 2) % 3];
@@ -1396,7 +1522,7 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
     sa.zout = w->z[(j - 1) % 3];
     sa.yout = rot[(j - 1) % 3];
     sa.Fout = j == 1 ? w->F0 : nullptr;
-    sa.F0 = (w->order == 2 && j >= 2) ? w->F0 : nullptr;
+    sa.F0 = (use_f0 && j >= 2) ? w->F0 : nullptr;
     sa.rr[0] = w->rr[0];
     sa.rr[1] = w->rr[1];
     sa.nu = (float)w->nu[j];
@@ -1459,6 +1585,109 @@ int ehc_cheb_stats(const ehc_cheb *w, int64_t *windows, int64_t *fallbacks) {
   if (!w) return EHC_E_INVAL;
   if (windows) *windows = w->windows;
   if (fallbacks) *fallbacks = w->fallbacks;
+  return EHC_OK;
+}
+
+int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *hc, const double *nu_host, const double *mut_host,
+                              const double *kap_host, const double *gam_host) {
+  if (!w || !hc || hc->c.n != w->n || !nu_host || !mut_host || !kap_host || !gam_host) return EHC_E_INVAL;
+  const double *src[4] = {nu_host, mut_host, kap_host, gam_host};
+  for (int q = 0; q < 4; ++q)
+    for (int j = 0; j <= w->s; ++j)
+      if (!std::isfinite(src[q][j]) || std::fabs(src[q][j]) > 1e6) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  for (int q = 0; q < 4; ++q) {
+    cheb_set(w, q).assign(src[q], src[q] + w->s + 1);
+    cheb_set(w, q)[0] = 0.0;
+    w->base[q] = cheb_set(w, q);
+  }
+  // stage 1 is Y_1 = Y_0 + mut_1 tau K F(Y_0): its nu, kap and gam are unused
+  for (int q : {0, 2, 3}) w->base[q][1] = cheb_set(w, q)[1] = 0.0;
+  if (w->tbuf) {
+    const int np = cheb_np(w);
+    for (float *q : {w->tp, w->tm, w->tv}) CK(cudaMemsetAsync(q, 0, sizeof(float) * np, c.stream));
+    for (int b = 0; b < np; ++b) w->thost[b] = (float)w->base[b / (w->s + 1)][b % (w->s + 1)];
+    CK(cudaMemcpyAsync(w->tc0, w->thost, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    w->adam_t = 0;
+  }
+  return EHC_OK;
+}
+
+int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
+                        float *loss_host, float *grad_host) {
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f))
+    return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  const int s = w->s, np = cheb_np(w);
+  if (c.n == 0) {
+    if (loss_host) *loss_host = 0.0f;
+    if (grad_host) std::memset(grad_host, 0, sizeof(float) * np);
+    return EHC_OK;
+  }
+  int r = cheb_train_prepare(w, c);
+  if (r) return r;
+  const WtTab t = cheb_train_tab(w, c.n);
+  const WtCoef k = cheb_train_coef(w, c);
+  const double tauK = (double)w->n_w * c.p.dt_sub_fs * c.K;
+  float *y0 = w->tbuf;
+  CK(nn_gather(c, Tin_dev, Ttar_dev, w->tT0, w->tT1, y0, false));
+  CK(wt_stages(c, s, k, y0, t));
+  // keep |P| <= 1 on the spectrum bound of the window (tau lambda_max <= n_w x
+  // the context's per-substep stability number), with 10 % margin
+  std::vector<double> pg;
+  cheb_penalty(w, 1.1 * (double)w->n_w * c.stability, 2048, 1e3, pg);
+  float *hp = w->thost, *hl = w->thost + np, *hg = w->thost + np + 1, *hd = w->thost + 2 * np + 1;
+  for (int b = 0; b < np; ++b) hp[b] = (float)pg[b];
+  CK(cudaMemcpyAsync(w->tpen, hp, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
+  CK(wt_backward(c, s, k, y0, t, w->tT0, w->tT1, w->tlpart, w->tdpart, tauK, w->tc0, w->tpen, w->tgc, w->tgd,
+                 w->tloss));
+  CK(cudaMemcpyAsync(hl, w->tloss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(hg, w->tgc, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
+  if (lr > 0.0f) {
+    w->adam_t += 1;
+    CK(wt_adam(c.stream, np, w->tp, w->tm, w->tv, w->tgd, lr, w->adam_t));
+    CK(cudaMemcpyAsync(hd, w->tp, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  if (loss_host) *loss_host = *hl;
+  if (grad_host) std::memcpy(grad_host, hg, sizeof(float) * np);
+  if (lr > 0.0f)
+    for (int b = 0; b < np; ++b) {
+      const int q = b / (s + 1), j = b % (s + 1);
+      cheb_set(w, q)[j] = w->base[q][j] * (1.0 + (double)hd[b]);
+    }
+  return EHC_OK;
+}
+
+int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, double *Tout_dev) {
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Tout_dev))) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  if (c.n == 0) return EHC_OK;
+  int r = cheb_train_prepare(w, c);
+  if (r) return r;
+  const WtTab t = cheb_train_tab(w, c.n);
+  CK(nn_gather(c, Tin_dev, nullptr, w->tT0, nullptr, w->tbuf, false));
+  CK(wt_stages(c, w->s, cheb_train_coef(w, c), w->tbuf, t));
+  CK(wt_end(c, w->tT0, t.z[w->s], w->tT1));
+  CK(launch_unpermute(c, w->tT1, Tout_dev, 0));
+  return EHC_OK;
+}
+
+int ehc_cheb_stability(const ehc_cheb *w, double *beta) {
+  if (!w || !beta) return EHC_E_INVAL;
+  // no polynomial of degree s with P(0) = 1, P'(0) = -1 stays within [-1, 1]
+  // beyond 2 s^2; scan a little past it
+  const double xlim = 2.05 * w->s * w->s, h = xlim / 40000.0;
+  double good = 0.0;
+  for (int k = 1; k <= 40000; ++k) {
+    const double x = k * h;
+    if (!(std::fabs(cheb_poly(w, x)) <= 1.0 + 1e-9)) break;
+    good = x;
+  }
+  *beta = good;
   return EHC_OK;
 }
 

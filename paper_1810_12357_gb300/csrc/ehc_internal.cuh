@@ -165,6 +165,27 @@ cudaError_t cheb_accept(Ctx &c, const double *dTc);
 cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
                           float *part, float *out);
 int cheb_blocks(int64_t n);
+// kernels_wtrain.cu (training of the window's stage coefficients)
+constexpr int kMaxStages = 32;
+// per-stage buffers of a window kept for the backward sweep: z[j] = Y_j - Y_0,
+// F[j] = F(Y_{j-1}) (F[1] = F(Y_0)), lam[j] = dL/dz_j, j = 1..s
+struct WtTab {
+  const float *z[kMaxStages + 1];
+  const float *F[kMaxStages + 1];
+  const float *lam[kMaxStages + 1];
+};
+// stage coefficients as the kernels take them: a_j = mut_j tau K, g_j = gam_j tau K
+struct WtCoef {
+  float nu[kMaxStages + 1], kap[kMaxStages + 1], a[kMaxStages + 1], g[kMaxStages + 1];
+};
+cudaError_t wt_stages(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t);
+cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t, const double *T0,
+                        const double *T1, double *lpart, double *dpart, double tauK, const float *c0,
+                        const float *pen, float *gc, float *gd, float *loss);
+size_t wt_dot_partials(int64_t n, int s);
+size_t wt_loss_partials(int64_t n);
+cudaError_t wt_adam(cudaStream_t st, int np, float *p, float *m, float *v, const float *g, float lr, int t);
+cudaError_t wt_end(Ctx &c, const double *T0, const float *zs, double *T1);
 // kernels_nn.cu (learned window propagator)
 int nn_blocks(int64_t n);
 cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm,

@@ -1,15 +1,17 @@
-"""Training and evaluation of the learned window propagator (ehc_nn_*).
+"""Training and evaluation of the learned window propagators: the message-
+passing network (ehc_nn_*) and the Chebyshev window with trained stage
+coefficients (ehc_cheb_train_step).
 
 Training windows come from the plain method itself: a context runs n_w
 explicit substeps of Eq. HeatTransport with the coupling switched off (G = 0),
 and each (state, state n_w substeps later) pair is one window.  The network is
-trained on the GPU by the library's own forward/backward kernels and Adam.
+Both are trained on the GPU by the library's own forward/backward kernels and Adam.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import Ehc, EhcNN
+from . import Ehc
 
 
 def generate_windows(system, params: dict, n_windows: int, n_w: int = 16, stride: int = 1):
@@ -33,24 +35,26 @@ def generate_windows(system, params: dict, n_windows: int, n_w: int = 16, stride
     return g, pairs
 
 
-def train(nn: EhcNN, pairs, steps: int, lr: float = 3e-3, log_every: int = 0):
-    """Adam steps cycling through the windows; returns the loss history."""
+def train(model, pairs, steps: int, lr: float = 3e-3, log_every: int = 0, ctx=None):
+    """Adam steps cycling through the windows of the network (EhcNN) or of the
+    trained Chebyshev window (EhcCheb); returns the loss history.  `ctx` is the
+    context the windows were generated on (default the model's own)."""
     hist = []
     for k in range(steps):
         t0, t1 = pairs[k % len(pairs)]
-        loss = nn.train_step(t0, t1, lr)
+        loss = model.train_step(t0, t1, lr, ctx=ctx)
         hist.append(loss)
         if log_every and k % log_every == 0:
             print(f"step {k} loss {loss:.4e}")
     return hist
 
 
-def window_error(nn: EhcNN, pairs):
+def window_error(model, pairs, ctx=None):
     """Max relative and RMS absolute error of flux-only predictions on windows."""
     import torch
     mx, ms = 0.0, 0.0
     for t0, t1 in pairs:
-        p = nn.predict(t0)
+        p = model.predict(t0) if ctx is None else model.predict(t0, ctx=ctx)
         d = (p - t1).abs()
         mx = max(mx, float((d / t1).max()))
         ms = max(ms, float(torch.sqrt((d * d).mean())))

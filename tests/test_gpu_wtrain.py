@@ -1,0 +1,119 @@
+"""Chebyshev windows with free and trained stage coefficients on the GPU
+(ehc_cheb_set_coefficients, ehc_cheb_train_step, ehc_cheb_predict,
+ehc_cheb_stability) against the FP64 reference of the general stage form in
+oracle/window.py (window_general, window_grad, stability_polynomial), and what
+training gains over the untrained coefficients."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import window as W
+from paper_1810_12357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(s, p):
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    g.build_neighbors(x, v)
+    return g
+
+
+def _perturbed(C, amp=0.05):
+    out = [c * (1.0 + amp * np.sin(1.7 * np.arange(c.size) + k)) for k, c in enumerate(C)]
+    for q in (0, 2, 3):
+        out[q][1] = 0.0
+    return out
+
+
+def test_free_coefficients_predict_and_step_match_the_reference():
+    import torch
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(10, 1, peak=12000.0)
+    p = dict(I.params_hotspot_fp64(), flux_prec=0, G=0.0)
+    g = _ctx(s, p)
+    K = g.energy()["K_per_fs"]
+    st = 6
+    w = EhcCheb(g, 16, st, 2.0 / 13.0, order=2)
+    C = _perturbed(W.coefficient_sets(st, 2, 2.0 / 13.0))
+    w.set_coefficients(*C)
+    got = w.coefficients()
+    for q in range(4):
+        assert np.array_equal(got[q][1:], C[q][1:])
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"])
+    z, _ = W.window_general(rowptr, col, s.Te / p["Tmax"], K, 16 * p["dt_sub"], C)
+    To = s.Te + p["Tmax"] * z[st]
+    assert np.max(np.abs(To - s.Te)) > 1.0
+    # training kernels (one thread per atom)
+    Tp = w.predict(torch.as_tensor(s.Te, device="cuda")).cpu().numpy()
+    assert np.max(np.abs(Tp - To) / To) < 1e-5
+    # the product stages (row-tile kernel), the same coefficients
+    fb, _ = w.step(1e30)
+    assert not fb
+    Tg = g.get_te().cpu().numpy()
+    assert np.max(np.abs(Tg - To) / To) < 1e-5
+    assert abs(Tg.sum() - s.Te.sum()) < 1e-6 * s.Te.sum()
+    # the stability interval of the coefficients, against the reference polynomial
+    beta = w.stability()
+    assert abs(W.stability_polynomial(C, beta)) <= 1.0 + 1e-9
+    xs = np.linspace(beta, 1.02 * beta + 1e-3, 50)[1:]
+    assert np.max(np.abs(W.stability_polynomial(C, xs))) > 1.0
+
+
+def test_window_gradient_matches_the_reference():
+    import torch
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(8, 2, peak=12000.0)
+    p = dict(I.params_hotspot_fp64(), flux_prec=0, G=0.0)
+    g = _ctx(s, p)
+    K = g.energy()["K_per_fs"]
+    st, n_w = 5, 16
+    w = EhcCheb(g, n_w, st, 2.0 / 13.0, order=2)
+    C = _perturbed(W.coefficient_sets(st, 2, 2.0 / 13.0))
+    w.set_coefficients(*C)
+    # target: n_w plain substeps of the reference with the coupling off
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    sim.substeps(n_w)
+    T1 = sim.T.copy()
+    loss_o, g_o = W.window_grad(sim.rowptr, sim.col, s.Te, T1, p["Tmax"], K, n_w * p["dt_sub"], C)
+    loss_g, g_g = w.train_step(torch.as_tensor(s.Te, device="cuda"), torch.as_tensor(T1, device="cuda"), 0.0,
+                               want_grad=True)
+    g_o = np.array(g_o)
+    print(f"loss {loss_g:.6e} vs {loss_o:.6e}; grad rel diff "
+          f"{np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o):.2e}")
+    assert loss_g == pytest.approx(loss_o, rel=1e-4)
+    assert np.linalg.norm(g_g - g_o) <= 1e-3 * np.linalg.norm(g_o)
+    big = np.abs(g_o) > 1e-2 * np.max(np.abs(g_o))
+    assert np.all(np.abs(g_g[big] - g_o[big]) <= 1e-2 * np.abs(g_o[big]))
+    # entries stage 1 does not use
+    assert g_g[0, 1] == 0.0 and g_g[2, 1] == 0.0 and g_g[3, 1] == 0.0
+    # lr = 0 leaves the coefficients alone
+    assert all(np.array_equal(a[1:], b[1:]) for a, b in zip(w.coefficients(), C))
+
+
+def test_training_beats_the_untrained_window():
+    # 100-substep windows with 12 stages on the 16,384-atom track profile,
+    # trained from the first-order damped Chebyshev coefficients on windows of
+    # the plain method, evaluated on a held-out track (other seed and radius)
+    from paper_1810_12357_gb300 import EhcCheb
+    from paper_1810_12357_gb300 import learned as Lm
+    p = I.params_track()
+    ctx, pairs = Lm.generate_windows(I.track_system(16, 2, r0=20.0), p, 8, n_w=100)
+    ctx_h, held = Lm.generate_windows(I.track_system(16, 7, r0=15.0), p, 6, n_w=100)
+    w = EhcCheb(ctx, 100, 12, 0.05, order=1)
+    stab = ctx.energy()["stability"]
+    assert w.stability() >= 100 * stab          # first order, 12 stages: stable on the whole bound
+    e0 = Lm.window_error(w, held[1:], ctx=ctx_h)[0]
+    hist = Lm.train(w, pairs[1:], 300, lr=3e-3)
+    e1 = Lm.window_error(w, held[1:], ctx=ctx_h)[0]
+    print(f"held-out max rel window error: untrained {e0:.3e}, trained {e1:.3e}; "
+          f"loss {hist[0]:.3e} -> {min(hist):.3e}; stability {w.stability():.1f} (bound {100 * stab:.1f})")
+    assert e1 < e0 / 3.0
+    assert w.stability() >= 100 * stab
