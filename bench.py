@@ -410,7 +410,7 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_window(args):
+def run_window(args, coeffs=None, learned_info=None):
     """Chebyshev window propagator on the 4,000,000-atom track: every MD step
     (build, 100 substeps' worth of electron evolution, hand-over, drift) advances
     the electrons by windows of n_w substeps, each with `stages` flux evaluations,
@@ -454,6 +454,11 @@ def run_window(args):
             if use_window:
                 if w is None:
                     w = EhcCheb(g, n_w, st, args.damping, order=args.order)
+                    if coeffs is not None:
+                        w.set_coefficients(*coeffs)
+                    stats["stability"] = w.stability()
+                    stats["stability_bound"] = n_w * g.energy()["stability"]
+                    stats["spectrum"] = w.spectrum(iters=300)
                 for k in range(n_win):
                     fb, rho = w.step(tau, t_fs + k * n_w * DT_SUB)
                     if step >= args.warmup:
@@ -487,24 +492,92 @@ def run_window(args):
     whole = n * N_SUB * args.steps / (ms_w * 1e-3)
     whole_plain = n * N_SUB * args.steps / (ms_p * 1e-3)
     rho = st_w["rho"] or [0.0]
+    path = {"path": "chebyshev window", "order": args.order, "damping": args.damping}
+    if coeffs is not None:
+        path = {"path": "learned window: stage coefficients trained on the plain method's windows"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_w / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 stages / f64 state and ledger", "data": "synthetic",
-            "config": config_dict(args.cells, n, {"path": "chebyshev window", "window_substeps": n_w,
-                                                 "stages": st, "order": args.order, "damping": args.damping,
-                                                 "residual_tau": tau,
-                                                 "lattice": "frozen" if args.frozen_lattice else "Langevin, free flight"}),
-            "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
+            "config": config_dict(args.cells, n, dict(path, window_substeps=n_w, stages=st, residual_tau=tau,
+                                                      lattice="frozen" if args.frozen_lattice
+                                                      else "Langevin, free flight")),
+            "learned" if coeffs is not None else "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
                        "whole_md_step": {"value": whole, "plain_value": whole_plain,
                                          "speedup_vs_plain": whole / whole_plain},
                        "fallbacks": st_w["fallbacks"], "windows": st_w["windows"],
                        "rho_median": float(np.median(rho)), "rho_max": float(np.max(rho)),
                        "energy_drift": ew["drift"], "plain_energy_drift": ep["drift"],
+                       "stability_interval": st_w.get("stability"),
+                       "spectrum_bound": st_w.get("stability_bound"),
+                       "spectrum_estimate": st_w.get("spectrum"),
                        "md_steps_total": args.warmup + args.steps}}
+    if learned_info:
+        line["learned"].update(learned_info)
     print(json.dumps(line), flush=True)
 
 
+def train_window(args):
+    """Stage coefficients of the learned window: Adam on windows of the plain
+    method from 256,000-atom track and hot-spot cells (40^3 cells, coupling
+    off), starting from the first-order damped Chebyshev values; returns the
+    coefficients and the training record (held-out window errors included)."""
+    from paper_1810_12357_gb300 import EhcCheb, learned
+    from paper_1810_12357_gb300 import inputs as I
+    n_w, st = args.window, args.stages
+    p = I.params_track()
+    t0 = time.perf_counter()
+    train_sys = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
+    train_sys += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
+                  for k in range(3)]
+    per = 9   # windows per run: the first (left out) and eight for training
+    ctxs, pairs = [], []
+    for s in train_sys:
+        g, pr = learned.generate_windows(s, p, per, n_w)
+        ctxs.append(g)
+        pairs.append(pr)
+    w = EhcCheb(ctxs[0], n_w, st, args.damping, order=args.order)
+    beta0 = w.stability()
+    # the stability range of training: the spectrum of the training states
+    spec = max(w.spectrum(pairs[c][0][0], iters=300, ctx=ctxs[c]) for c in range(len(ctxs)))
+    hist = []
+    for k in range(args.train_steps):
+        c = k % len(ctxs)
+        # the first window of every run (the sharp initial front) is left to the
+        # residual test and the plain substeps
+        prs = pairs[c][1:]
+        t_in, t_out = prs[(k // len(ctxs)) % len(prs)]
+        lr = 3e-3 if k < args.train_steps * 3 // 4 else 1e-3
+        hist.append(w.train_step(t_in, t_out, lr, ctx=ctxs[c], power=args.loss_power))
+    coeffs = [c.copy() for c in w.coefficients()]
+    t_train = time.perf_counter() - t0
+    del pairs
+    # held-out windows of another track (its first window excluded as in training):
+    # trained against untrained coefficients, window by window
+    held_g, held = learned.generate_windows(I.track_system(40, 199, peak=20000.0, r0=20.0), p, 8, n_w)
+    base = EhcCheb(held_g, n_w, st, args.damping, order=args.order)
+    per_t = [learned.window_error(w, [h], ctx=held_g)[0] for h in held[1:]]
+    per_u = [learned.window_error(base, [h])[0] for h in held[1:]]
+    info = {"train_s": t_train, "train_windows": (per - 1) * len(train_sys), "train_steps": args.train_steps,
+            "train_cells": "256,000-atom tracks and hot spots (40^3 cells), first window of each run left out",
+            "start": "damped Chebyshev order %d, damping %.4g" % (args.order, args.damping),
+            "loss": "mean relative error^%d" % args.loss_power,
+            "training_spectrum_tauK_lambda_max": spec, "stability_untrained": beta0,
+            "stability_trained": w.stability(),
+            "heldout_256k_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
+    return coeffs, info
+
+
 def run_learned(args):
+    """Learned propagator on the 4,000,000-atom track.  Default: the window with
+    trained stage coefficients (train_window, then run_window with them); with
+    --model nn the message-passing network below."""
+    if args.model == "window":
+        coeffs, info = train_window(args)
+        return run_window(args, coeffs, info)
+    return run_learned_nn(args)
+
+
+def run_learned_nn(args):
     """Learned window propagator on the 4,000,000-atom track: windows of 16
     substeps advanced by the network (with the a-posteriori residual check and
     fallback to plain substeps), against the plain path from the same state."""
@@ -604,8 +677,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="track", choices=["track", "batch", "learned", "window"])
     ap.add_argument("--window", type=int, default=100)
-    ap.add_argument("--stages", type=int, default=16)
-    ap.add_argument("--damping", type=float, default=2.0 / 13.0)
+    ap.add_argument("--stages", type=int, default=None)
+    ap.add_argument("--model", default="window", choices=["window", "nn"])
+    ap.add_argument("--damping", type=float, default=None)
     ap.add_argument("--frozen-lattice", action="store_true")
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--tile-threads", type=int, default=0)
@@ -614,9 +688,18 @@ def main():
     ap.add_argument("--windows", type=int, default=20)
     ap.add_argument("--train-windows", type=int, default=480)
     ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--loss-power", type=int, default=8)
     ap.add_argument("--replicas", type=int, default=256)
     args = ap.parse_args()
     args.tau_given = any(a == "--tau" or a.startswith("--tau=") for a in sys.argv[1:])
+    # window defaults: second order, damping 2/13, 16 stages; the learned window
+    # trains 15 stages from the second-order values (stable on 1.1 x the
+    # spectrum of the training states: 0.65 s^2 = 146 >= 139)
+    trained = args.workload == "learned" and args.model == "window"
+    if args.stages is None:
+        args.stages = 15 if trained else 16
+    if args.damping is None:
+        args.damping = 2.0 / 13.0
     if args.warmup < 3 and args.impl == "ehc":
         args.warmup = 3
     if args.impl == "reference":

@@ -318,23 +318,35 @@ int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *c, const double *nu_host, co
                               const double *kap_host, const double *gam_host);
 /* One training step on one window: Tin_dev -> Ttar_dev (caller order, device; the
  * target is the state after n_window plain substeps with the coupling off) on
- * the context's neighbour list and K.  Loss mean_i ((T^_i - T*_i) / Tin_i)^2 of the
+ * the context's neighbour list and K.  Loss mean_i ((T^_i - T*_i) / Tin_i)^p,
+ * p = loss_power (2, 4 or 8; the higher powers weigh the worst atoms), of the
  * s stages' prediction T^ to *loss_host; dL/d(nu, mut, kap, gam) to grad_host
  * (4 (stages + 1) floats: the four sets one after another, index j within each)
- * if not NULL.  If lr > 0, one Adam step of rate lr on the relative changes, on
- * the loss plus a penalty that keeps |P(x)| <= 1 for the window's linear
- * stability polynomial P on 0 < x <= 1.1 n_window s_c (s_c the context's
- * per-substep stability number, a bound of dt lambda_max), after which the
- * stages use the new coefficients.  Forward and backward run on the GPU (one
- * thread per atom on the neighbour list, single precision, FP64 reductions);
- * the first call allocates (1 + 3 stages) floats per atom.  Synchronises. */
+ * if not NULL.  If lr > 0, one Adam step of rate lr on the relative changes;
+ * mut and gam are then rescaled so that P'(0) = -1 for the window's linear
+ * stability polynomial P (slow modes decay at the plain rate), and the step is
+ * halved (up to 20 times, else not taken) until |P(x)| <= 1 + 1e-6 on a grid of
+ * 16384 points of 0 < x <= X_r, X_r = 1.1 x the largest ehc_cheb_spectrum
+ * estimate so far, or 1.1 n_window s_c without one (s_c the context's
+ * per-substep stability number, a bound of dt lambda_max).  Training must start
+ * from coefficients that meet this (EHC_E_UNSTABLE otherwise, nothing changed).
+ * Forward and backward run on the GPU (one thread per atom on the neighbour
+ * list, single precision, FP64 reductions); the first call allocates
+ * (1 + 3 stages) floats per atom.  Synchronises. */
 int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, const double *Ttar_dev, float lr,
-                        float *loss_host, float *grad_host);
+                        int32_t loss_power, float *loss_host, float *grad_host);
+/* Estimate x = tau_w K |lambda_max| of the linearised pair flux at the state
+ * Tin_dev (caller order, device) or, if NULL, at the context's T, by `iters`
+ * (1..100000) power iterations with the transposed Jacobian; to *x_out.  The
+ * largest estimate so far bounds the stability range of training.  The
+ * iteration approaches |lambda_max| from below. */
+int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, int32_t iters, double *x_out);
 /* The stages' flux-only prediction of one window from Tin_dev into Tout_dev
  * (caller order, device), with the training kernels. */
 int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, double *Tout_dev);
-/* Largest X such that |P(x)| <= 1 on [0, X] for the current coefficients (the
- * window is stable for modes with tau_w lambda <= X); host computation. */
+/* Largest X such that |P(x)| <= 1 + 1e-5 on [0, X] for the current coefficients
+ * (the window is stable for modes with tau_w lambda <= X), scanned on 200000
+ * points of [0, 2.05 stages^2]; host computation. */
 int ehc_cheb_stability(const ehc_cheb *w, double *beta);
 void ehc_cheb_destroy(ehc_cheb *w);
 

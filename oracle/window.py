@@ -195,15 +195,15 @@ def window_general(rowptr, col, theta, K: float, tau: float, coeffs):
     return z, F
 
 
-def window_loss(T0, T1, z_s, Tmax: float) -> float:
-    """Training loss of a window: the mean squared relative error of the end
-    temperatures, mean_i ((T0_i + Tmax z_s,i - T1_i) / T0_i)^2."""
+def window_loss(T0, T1, z_s, Tmax: float, power: int = 2) -> float:
+    """Training loss of a window: the mean of the relative error of the end
+    temperatures to the given even power, mean_i ((T0_i + Tmax z_s,i - T1_i) / T0_i)^p."""
     r = (np.asarray(T0) + Tmax * z_s - np.asarray(T1)) / np.asarray(T0)
-    return float(np.mean(r * r))
+    return float(np.mean(r ** power))
 
 
-def window_grad(rowptr, col, T0, T1, Tmax: float, K: float, tau: float, coeffs):
-    """Loss (window_loss) of the window started from T0 against the target T1,
+def window_grad(rowptr, col, T0, T1, Tmax: float, K: float, tau: float, coeffs, power: int = 2):
+    """Loss (window_loss, exponent `power`) of the window started from T0 against the target T1,
     and its gradient with respect to (nu, mut, kap, gam), by the adjoint of the
     stage recurrence: with lam_j = dL/dz_j, going down from j = s,
       dL/dnu_j = <lam_j, z_{j-2} - z_{j-1}>,  dL/dkap_j = -<lam_j, z_{j-1}>,
@@ -220,10 +220,11 @@ def window_grad(rowptr, col, T0, T1, Tmax: float, K: float, tau: float, coeffs):
     y0 = T0 / Tmax
     z, F = window_general(rowptr, col, y0, K, tau, coeffs)
     n = T0.shape[0]
-    loss = window_loss(T0, T1, z[s], Tmax)
+    loss = window_loss(T0, T1, z[s], Tmax, power)
     lam = [np.zeros(n) for _ in range(s + 1)]
-    # d/dz_s of mean(((T0 + Tmax z_s - T1) / T0)^2)
-    lam[s] = 2.0 * Tmax * (T0 + Tmax * z[s] - T1) / (T0 * T0) / n
+    # d/dz_s of mean(r^p), r = (T0 + Tmax z_s - T1) / T0
+    r = (T0 + Tmax * z[s] - T1) / T0
+    lam[s] = power * r ** (power - 1) * Tmax / T0 / n
     g = [np.zeros(s + 1) for _ in range(4)]
     for j in range(s, 1, -1):
         lj = lam[j]

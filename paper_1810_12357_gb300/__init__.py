@@ -99,9 +99,10 @@ _SIGS = {
     "ehc_cheb_step": (_I, [_P, _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "ehc_cheb_stats": (_I, [_P, _P, _P]),
     "ehc_cheb_set_coefficients": (_I, [_P, _P, _P, _P, _P, _P]),
-    "ehc_cheb_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, _P, _P]),
+    "ehc_cheb_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, ctypes.c_int32, _P, _P]),
     "ehc_cheb_predict": (_I, [_P, _P, _P, _P]),
     "ehc_cheb_stability": (_I, [_P, _P]),
+    "ehc_cheb_spectrum": (_I, [_P, _P, _P, ctypes.c_int32, _P]),
     "ehc_cheb_destroy": (None, [_P]),
     "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
                               ctypes.POINTER(_P)]),
@@ -515,14 +516,15 @@ class EhcCheb:
         _check(self._lib.ehc_cheb_set_coefficients(self._h, self.ctx._h, *[x.ctypes.data_as(_P) for x in a]),
                "ehc_cheb_set_coefficients")
 
-    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False, ctx=None):
-        """Loss of the window Tin -> Ttar and (lr > 0) one Adam step on the
-        coefficients; `ctx` (same atom count) supplies the neighbour list and K.
-        With want_grad, also dL/d(nu, mut, kap, gam) as a (4, stages + 1) array."""
+    def train_step(self, Tin, Ttar, lr: float, want_grad: bool = False, ctx=None, power: int = 2):
+        """Loss mean(rel. error^power) of the window Tin -> Ttar and (lr > 0) one
+        Adam step on the coefficients; `ctx` (same atom count) supplies the
+        neighbour list and K.  With want_grad, also dL/d(nu, mut, kap, gam) as a
+        (4, stages + 1) array."""
         loss = ctypes.c_float()
         g = np.empty(4 * (self.stages + 1), dtype=np.float32) if want_grad else None
         c = ctx if ctx is not None else self.ctx
-        _check(self._lib.ehc_cheb_train_step(self._h, c._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr),
+        _check(self._lib.ehc_cheb_train_step(self._h, c._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr), int(power),
                                              ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
                "ehc_cheb_train_step")
         if want_grad:
@@ -542,3 +544,13 @@ class EhcCheb:
         b = ctypes.c_double()
         _check(self._lib.ehc_cheb_stability(self._h, ctypes.byref(b)), "ehc_cheb_stability")
         return float(b.value)
+
+    def spectrum(self, Tin=None, iters: int = 200, ctx=None) -> float:
+        """tau_w K |lambda_max| of the linearised flux at Tin (or the context's
+        state), by power iteration; the largest estimate bounds training's
+        stability range."""
+        x = ctypes.c_double()
+        c = ctx if ctx is not None else self.ctx
+        _check(self._lib.ehc_cheb_spectrum(self._h, c._h, _ptr(Tin) if Tin is not None else None, int(iters),
+                                           ctypes.byref(x)), "ehc_cheb_spectrum")
+        return float(x.value)

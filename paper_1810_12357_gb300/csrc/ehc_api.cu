@@ -1215,9 +1215,11 @@ struct ehc_cheb {
   float *tbuf = nullptr;                // y0 | z[1..s] | F[1..s] | lam[1..s], n floats each
   double *tT0 = nullptr, *tT1 = nullptr, *tlpart = nullptr, *tdpart = nullptr;
   float *tp = nullptr, *tm = nullptr, *tv = nullptr, *tgc = nullptr, *tgd = nullptr;
-  float *tc0 = nullptr, *tpen = nullptr, *tloss = nullptr;
-  float *thost = nullptr;               // pinned: pen[np] | loss | gc[np] | d[np]
+  float *tc0 = nullptr, *tloss = nullptr;
+  float *thost = nullptr;               // pinned: c0[np] | loss | gc[np] | d[np]
   int adam_t = 0;
+  std::vector<double> dacc;             // the accepted relative changes
+  double x_spec = 0.0;                  // largest tau_w K |lambda_max| estimated so far (0: none)
 };
 
 namespace {
@@ -1306,42 +1308,43 @@ double cheb_poly(const ehc_cheb *w, double x) {
   return 1.0 + z1;
 }
 
-// Penalty wpen sum_k max(|P(x_k)| - 1, 0)^2 over x_k = xmax k / npts, k = 1..npts,
-// and its gradient with respect to the relative changes d (c = base (1 + d)),
-// carried through the recurrence in forward mode.
-double cheb_penalty(const ehc_cheb *w, double xmax, int npts, double wpen, std::vector<double> &g) {
-  const int s = w->s, np = cheb_np(w), S1 = s + 1;
-  g.assign(np, 0.0);
-  std::vector<double> d1(np), d2(np), d(np);
-  double pen = 0.0;
-  for (int k = 1; k <= npts; ++k) {
-    const double x = xmax * k / npts;
-    std::fill(d1.begin(), d1.end(), 0.0);
-    std::fill(d2.begin(), d2.end(), 0.0);
-    double z2 = 0.0, z1 = -w->mut[1] * x;
-    d1[S1 + 1] = -x * w->base[1][1];
-    for (int j = 2; j <= s; ++j) {
-      const double nu = w->nu[j], kap = w->kap[j], mu = w->mut[j], ga = w->gam[j];
-      const double z = z1 + nu * (z2 - z1) - kap * z1 - mu * x * (1.0 + z1) - ga * x;
-      const double c1 = 1.0 - nu - kap - mu * x;
-      for (int b = 0; b < np; ++b) d[b] = c1 * d1[b] + nu * d2[b];
-      d[j] += (z2 - z1) * w->base[0][j];
-      d[S1 + j] += -x * (1.0 + z1) * w->base[1][j];
-      d[2 * S1 + j] += -z1 * w->base[2][j];
-      d[3 * S1 + j] += -x * w->base[3][j];
-      d2.swap(d1);
-      d1.swap(d);
-      z2 = z1;
-      z1 = z;
-    }
-    const double P = 1.0 + z1, e = std::fabs(P) - 1.0;
-    if (e > 0.0) {
-      pen += wpen * e * e;
-      const double f = wpen * 2.0 * e * (P > 0.0 ? 1.0 : -1.0);
-      for (int b = 0; b < np; ++b) g[b] += f * d1[b];
-    }
+// coefficients base (1 + d), then mut and gam scaled so that P'(0) = -1
+// (c_j = -dz_j/dx at x = 0: c_1 = mut_1, c_j = (1 - nu_j - kap_j) c_{j-1} + nu_j c_{j-2}
+// + mut_j + gam_j, linear in (mut, gam)); d is rewritten to match
+void cheb_apply(ehc_cheb *w, std::vector<double> &d) {
+  const int s = w->s, S1 = s + 1;
+  for (int b = 0; b < cheb_np(w); ++b) cheb_set(w, b / S1)[b % S1] = w->base[b / S1][b % S1] * (1.0 + d[b]);
+  double c2 = 0.0, c1 = w->mut[1];
+  for (int j = 2; j <= s; ++j) {
+    const double cj = (1.0 - w->nu[j] - w->kap[j]) * c1 + w->nu[j] * c2 + w->mut[j] + w->gam[j];
+    c2 = c1;
+    c1 = cj;
   }
-  return pen;
+  if (std::isfinite(c1) && c1 > 0.0)
+    for (int j = 1; j <= s; ++j) {
+      w->mut[j] /= c1;
+      w->gam[j] /= c1;
+    }
+  for (int b = 0; b < cheb_np(w); ++b) {
+    const double bs = w->base[b / S1][b % S1];
+    d[b] = bs != 0.0 ? cheb_set(w, b / S1)[b % S1] / bs - 1.0 : 0.0;
+  }
+}
+
+// stability check of training: |P| <= 1 + kStabTol on a grid of kStabGrid points
+// (the sampling misses a peak between points by at most s^2 (2 dx / X)^2 / 2,
+// about 2e-6 for 16 stages on X = 140)
+constexpr int kStabGrid = 16384;
+constexpr double kStabTol = 1e-6;
+
+// max over x_k = xmax k / npts (k = 1..npts) of |P(x_k)| - 1
+double cheb_violation(const ehc_cheb *w, double xmax, int npts) {
+  double v = -1.0;
+  for (int k = 1; k <= npts; ++k) {
+    const double P = std::fabs(cheb_poly(w, xmax * k / npts)) - 1.0;
+    v = std::isfinite(P) ? std::max(v, P) : 1e300;
+  }
+  return v;
 }
 
 int cheb_train_prepare(ehc_cheb *w, Ctx &c) {
@@ -1355,7 +1358,7 @@ int cheb_train_prepare(ehc_cheb *w, Ctx &c) {
   A(dalloc(&w->tT1, n));
   A(dalloc(&w->tlpart, (int64_t)wt_loss_partials(n)));
   A(dalloc(&w->tdpart, (int64_t)wt_dot_partials(n, s)));
-  for (float **q : {&w->tp, &w->tm, &w->tv, &w->tgc, &w->tgd, &w->tc0, &w->tpen}) A(dalloc(q, np));
+  for (float **q : {&w->tp, &w->tm, &w->tv, &w->tgc, &w->tgd, &w->tc0}) A(dalloc(q, np));
   A(dalloc(&w->tloss, 1));
   A(cudaMallocHost((void **)&w->thost, sizeof(float) * (3 * np + 1)));
   if (ok) {
@@ -1369,6 +1372,7 @@ int cheb_train_prepare(ehc_cheb *w, Ctx &c) {
     return EHC_E_NOMEM;
   }
   w->adam_t = 0;
+  w->dacc.assign(np, 0.0);
   return EHC_OK;
 }
 
@@ -1450,7 +1454,7 @@ void ehc_cheb_destroy(ehc_cheb *w) {
   }
   void *p[] = {w->F0,  w->F1,     w->part,   w->rho, w->T1, w->dTc, w->rr[0], w->rr[1], w->tbuf,
                w->tT0, w->tT1,    w->tlpart, w->tdpart, w->tp, w->tm,  w->tv,    w->tgc,   w->tgd,
-               w->tc0, w->tpen,   w->tloss};
+               w->tc0, w->tloss};
   for (void *q : p)
     if (q) cudaFree(q);
   if (w->host) cudaFreeHost(w->host);
@@ -1610,13 +1614,15 @@ int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *hc, const double *nu_host, c
     CK(cudaMemcpyAsync(w->tc0, w->thost, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     w->adam_t = 0;
+    w->dacc.assign(np, 0.0);
   }
   return EHC_OK;
 }
 
 int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
-                        float *loss_host, float *grad_host) {
-  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f))
+                        int32_t loss_power, float *loss_host, float *grad_host) {
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f) ||
+      (loss_power != 2 && loss_power != 4 && loss_power != 8))
     return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1628,20 +1634,18 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const d
   }
   int r = cheb_train_prepare(w, c);
   if (r) return r;
+  // stability range: 1.1 x the estimate of tau_w K |lambda_max| if one was made
+  // (ehc_cheb_spectrum), else 1.1 x the bound n_w x the per-substep stability number
+  const double xr = 1.1 * (w->x_spec > 0.0 ? w->x_spec : (double)w->n_w * c.stability);
+  if (lr > 0.0f && cheb_violation(w, xr, kStabGrid) > kStabTol) return EHC_E_UNSTABLE;
   const WtTab t = cheb_train_tab(w, c.n);
   const WtCoef k = cheb_train_coef(w, c);
   const double tauK = (double)w->n_w * c.p.dt_sub_fs * c.K;
   float *y0 = w->tbuf;
   CK(nn_gather(c, Tin_dev, Ttar_dev, w->tT0, w->tT1, y0, false));
   CK(wt_stages(c, s, k, y0, t));
-  // keep |P| <= 1 on the spectrum bound of the window (tau lambda_max <= n_w x
-  // the context's per-substep stability number), with 10 % margin
-  std::vector<double> pg;
-  cheb_penalty(w, 1.1 * (double)w->n_w * c.stability, 2048, 1e3, pg);
-  float *hp = w->thost, *hl = w->thost + np, *hg = w->thost + np + 1, *hd = w->thost + 2 * np + 1;
-  for (int b = 0; b < np; ++b) hp[b] = (float)pg[b];
-  CK(cudaMemcpyAsync(w->tpen, hp, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
-  CK(wt_backward(c, s, k, y0, t, w->tT0, w->tT1, w->tlpart, w->tdpart, tauK, w->tc0, w->tpen, w->tgc, w->tgd,
+  float *hl = w->thost + np, *hg = w->thost + np + 1, *hd = w->thost + 2 * np + 1;
+  CK(wt_backward(c, s, k, y0, t, w->tT0, w->tT1, loss_power, w->tlpart, w->tdpart, tauK, w->tc0, w->tgc, w->tgd,
                  w->tloss));
   CK(cudaMemcpyAsync(hl, w->tloss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaMemcpyAsync(hg, w->tgc, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
@@ -1653,11 +1657,61 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const d
   CK(cudaStreamSynchronize(c.stream));
   if (loss_host) *loss_host = *hl;
   if (grad_host) std::memcpy(grad_host, hg, sizeof(float) * np);
-  if (lr > 0.0f)
-    for (int b = 0; b < np; ++b) {
-      const int q = b / (s + 1), j = b % (s + 1);
-      cheb_set(w, q)[j] = w->base[q][j] * (1.0 + (double)hd[b]);
+  if (lr > 0.0f) {
+    // the Adam step, projected to P'(0) = -1 (slow modes decay at the plain rate)
+    // and taken back by halves until |P| <= 1 on (0, xr] again
+    const std::vector<double> dold = w->dacc;
+    std::vector<double> dtry(np);
+    bool taken = false;
+    double t = 1.0;
+    for (int k = 0; k <= 20 && !taken; ++k, t *= 0.5) {
+      for (int b = 0; b < np; ++b) dtry[b] = dold[b] + t * ((double)hd[b] - dold[b]);
+      cheb_apply(w, dtry);
+      taken = cheb_violation(w, xr, kStabGrid) <= kStabTol;
     }
+    if (taken) {
+      w->dacc = dtry;
+    } else {
+      dtry = dold;
+      cheb_apply(w, dtry);
+    }
+    for (int b = 0; b < np; ++b) hd[b] = (float)w->dacc[b];
+    CK(cudaMemcpyAsync(w->tp, hd, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+  }
+  return EHC_OK;
+}
+
+int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t iters, double *x_out) {
+  if (!w || !hc || hc->c.n != w->n || iters < 1 || iters > 100000) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  if (c.n == 0) {
+    if (x_out) *x_out = 0.0;
+    return EHC_OK;
+  }
+  int r = cheb_train_prepare(w, c);
+  if (r) return r;
+  const WtTab t = cheb_train_tab(w, c.n);
+  float *y = w->tbuf;
+  if (Tin_dev) {
+    CK(nn_gather(c, Tin_dev, nullptr, w->tT0, nullptr, y, false));
+  } else {
+    r = ensure_t(c);
+    if (r) return r;
+    CK(cheb_mirror(c, c.T[c.tcur], y));
+  }
+  float *zero = const_cast<float *>(t.z[1]);
+  CK(cudaMemsetAsync(zero, 0, sizeof(float) * c.n, c.stream));
+  CK(wt_power(c, y, zero, const_cast<float *>(t.F[1]), const_cast<float *>(t.lam[1]), w->tdpart, w->tlpart,
+              iters));
+  double ss = 0.0;
+  CK(cudaMemcpyAsync(&ss, w->tlpart, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  const double x = (double)w->n_w * c.p.dt_sub_fs * c.K * std::sqrt(ss);
+  if (!std::isfinite(x)) return EHC_E_RANGE;
+  w->x_spec = std::max(w->x_spec, x);
+  if (x_out) *x_out = x;
   return EHC_OK;
 }
 
@@ -1680,11 +1734,12 @@ int ehc_cheb_stability(const ehc_cheb *w, double *beta) {
   if (!w || !beta) return EHC_E_INVAL;
   // no polynomial of degree s with P(0) = 1, P'(0) = -1 stays within [-1, 1]
   // beyond 2 s^2; scan a little past it
-  const double xlim = 2.05 * w->s * w->s, h = xlim / 40000.0;
+  constexpr int kScan = 200000;
+  const double xlim = 2.05 * w->s * w->s, h = xlim / kScan;
   double good = 0.0;
-  for (int k = 1; k <= 40000; ++k) {
+  for (int k = 1; k <= kScan; ++k) {
     const double x = k * h;
-    if (!(std::fabs(cheb_poly(w, x)) <= 1.0 + 1e-9)) break;
+    if (!(std::fabs(cheb_poly(w, x)) <= 1.0 + 1e-5)) break;
     good = x;
   }
   *beta = good;

@@ -180,12 +180,16 @@ struct WtCoef {
 };
 cudaError_t wt_stages(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t);
 cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t, const double *T0,
-                        const double *T1, double *lpart, double *dpart, double tauK, const float *c0,
-                        const float *pen, float *gc, float *gd, float *loss);
+                        const double *T1, int loss_power, double *lpart, double *dpart, double tauK,
+                        const float *c0, float *gc, float *gd, float *loss);
 size_t wt_dot_partials(int64_t n, int s);
 size_t wt_loss_partials(int64_t n);
 cudaError_t wt_adam(cudaStream_t st, int np, float *p, float *m, float *v, const float *g, float lr, int t);
 cudaError_t wt_end(Ctx &c, const double *T0, const float *zs, double *T1);
+// |lambda_max| of the pair-flux Jacobian at the values y by `iters` products with
+// J^T (v, u: n floats; part: wt_dot_partials; ss: one double, |J^T v|^2 at the end)
+cudaError_t wt_power(Ctx &c, const float *y, const float *zero, float *v, float *u, double *part, double *ss,
+                     int iters);
 // kernels_nn.cu (learned window propagator)
 int nn_blocks(int64_t n);
 cudaError_t nn_gather(Ctx &c, const double *Tin, const double *Ttar, double *Ts, double *Ttar_s, float *dm,

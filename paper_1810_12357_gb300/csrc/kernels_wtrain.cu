@@ -8,8 +8,9 @@
 //   z_j = z_{j-1} + nu_j (z_{j-2} - z_{j-1}) - kap_j z_{j-1} + a_j F(Y_{j-1}) + g_j F(Y_0),
 // F_i = sum_j f(theta_i, theta_j) the pair flux of Eq. HeatTransport, evaluated as
 // f(a, b) = D cosh D - P sinh D with D = b - a, P = a + b - 2ab.
-// Loss of a window against the plain method's end state T1:
-//   L = mean_i ((T0_i + Tmax z_s,i - T1_i) / T0_i)^2.
+// Loss of a window against the plain method's end state T1 (p = 2, 4 or 8; the
+// higher powers weigh the atoms with the largest errors):
+//   L = mean_i ((T0_i + Tmax z_s,i - T1_i) / T0_i)^p.
 // Adjoint lam_j = dL/dz_j, from j = s down:
 //   lam_{j-1} += (1 - nu_j - kap_j) lam_j + a_j J(Y_{j-1})^T lam_j,  lam_{j-2} += nu_j lam_j,
 //   dL/dnu_j = <lam_j, z_{j-2} - z_{j-1}>, dL/dkap_j = -<lam_j, z_{j-1}>,
@@ -92,21 +93,24 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return r;
 }
 
-// r_i = (T0 + Tmax z_s - T1) / T0: lam_s = dL/dz_s = 2 Tmax r / (n T0), block sums of r^2
+// r_i = (T0 + Tmax z_s - T1) / T0, loss mean r^p (p = 2, 4, 8):
+// lam_s = dL/dz_s = p r^(p-1) Tmax / (n T0), block sums of r^p
 __global__ void __launch_bounds__(kWtThreads) wt_loss_kernel(int32_t n, const float *__restrict__ zs,
                                                             const double *__restrict__ T0,
-                                                            const double *__restrict__ T1, double Tmax,
+                                                            const double *__restrict__ T1, double Tmax, int pw,
                                                             float *__restrict__ lam, double *__restrict__ part) {
   __shared__ double red[kWtThreads / 32];
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0;
+  double rp = 0.0;
   if (i < n) {
     const double t0 = T0[i];
     const double r = (fma(Tmax, (double)zs[i], t0) - T1[i]) / t0;
-    r2 = r * r;
-    lam[i] = (float)(2.0 * Tmax * r / ((double)n * t0));
+    double rq = r;   // r^(p-1)
+    for (int k = 2; k < pw; ++k) rq *= r;
+    rp = rq * r;
+    lam[i] = (float)(pw * rq * Tmax / ((double)n * t0));
   }
-  const double b = block_sum<kWtThreads>(r2, red);
+  const double b = block_sum<kWtThreads>(rp, red);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }
 
@@ -165,11 +169,11 @@ __global__ void __launch_bounds__(kWtThreads) wt_dots_kernel(int32_t n, WtTab t,
 
 // gradient entry (q, j) per block (q: nu, mut, kap, gam), the last block the loss:
 // gc = dL/dc (the tau K factor for mut and gam; stage 1 only has mut), and, for
-// Adam on the relative changes d (c = c0 (1 + d)), gd = gc c0 + pen
+// Adam on the relative changes d (c = c0 (1 + d)), gd = gc c0
 __global__ void wt_final_kernel(int s, int nbd, const double *__restrict__ part, int nbl,
                                 const double *__restrict__ lpart, double tauK, double inv_n,
-                                const float *__restrict__ c0, const float *__restrict__ pen,
-                                float *__restrict__ gc, float *__restrict__ gd, float *__restrict__ loss) {
+                                const float *__restrict__ c0, float *__restrict__ gc, float *__restrict__ gd,
+                                float *__restrict__ loss) {
   __shared__ double red[4];
   const int b = blockIdx.x;
   const int np = 4 * (s + 1);
@@ -191,7 +195,7 @@ __global__ void wt_final_kernel(int s, int nbd, const double *__restrict__ part,
   double g = (q == 1 || q == 3) ? v * tauK : v;
   if (j == 0 || (j == 1 && q != 1)) g = 0.0;
   gc[b] = (float)g;
-  gd[b] = c0[b] != 0.0f ? (float)(g * (double)c0[b]) + pen[b] : 0.0f;
+  gd[b] = c0[b] != 0.0f ? (float)(g * (double)c0[b]) : 0.0f;
 }
 
 __global__ void wt_adam_kernel(int np, float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
@@ -205,6 +209,46 @@ __global__ void wt_adam_kernel(int np, float *__restrict__ p, float *__restrict_
   m[k] = mk;
   v[k] = vk;
   p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+// power iteration on J^T: a start vector without a uniform part (hash of the atom
+// index), sums of squares, and the normalisation v = u / |u|
+__global__ void wt_seed_kernel(int32_t n, float *__restrict__ v) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t h = (uint32_t)i * 0x9E3779B9u + 0x7F4A7C15u;
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  v[i] = (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+__global__ void __launch_bounds__(kWtThreads) wt_sumsq_kernel(int32_t n, const float *__restrict__ u,
+                                                             double *__restrict__ part) {
+  __shared__ double red[kWtThreads / 32];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += (double)u[i] * u[i];
+  const double b = block_sum<kWtThreads>(a, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+__global__ void wt_total_kernel(int nb, const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double red[4];
+  double a = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) a += part[k];
+  const double b = block_sum<128>(a, red);
+  if (threadIdx.x == 0) *out = b;
+}
+
+__global__ void wt_normalise_kernel(int32_t n, const float *__restrict__ u, const double *__restrict__ ss,
+                                    float *__restrict__ v) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double q = *ss;
+  v[i] = q > 0.0 ? (float)(u[i] / sqrt(q)) : 0.0f;
 }
 
 __global__ void wt_end_kernel(int64_t n, const double *__restrict__ T0, const float *__restrict__ zs, double Tmax,
@@ -229,8 +273,8 @@ cudaError_t wt_stages(Ctx &c, int s, const WtCoef &k, const float *y0, const WtT
 }
 
 cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t, const double *T0,
-                        const double *T1, double *lpart, double *dpart, double tauK, const float *c0,
-                        const float *pen, float *gc, float *gd, float *loss) {
+                        const double *T1, int loss_power, double *lpart, double *dpart, double tauK,
+                        const float *c0, float *gc, float *gd, float *loss) {
   if (c.n == 0) return cudaSuccess;
   const int32_t n = (int32_t)c.n;
   const float th = (float)(c.p.Tref_K / c.p.Tmax_K);
@@ -239,8 +283,8 @@ cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const W
     if (e != cudaSuccess) return e;
   }
   const unsigned nbl = wblk(n);
-  wt_loss_kernel<<<nbl, kWtThreads, 0, c.stream>>>(n, t.z[s], T0, T1, c.p.Tmax_K, const_cast<float *>(t.lam[s]),
-                                                   lpart);
+  wt_loss_kernel<<<nbl, kWtThreads, 0, c.stream>>>(n, t.z[s], T0, T1, c.p.Tmax_K, loss_power,
+                                                   const_cast<float *>(t.lam[s]), lpart);
   for (int j = s; j >= 2; --j)
     wt_adjoint_kernel<<<wblk(n), kWtThreads, 0, c.stream>>>(
         n, c.nbr, c.cnt, th, y0, t.z[j - 1], t.lam[j], 1.0f - k.nu[j] - k.kap[j], k.a[j], k.nu[j],
@@ -248,7 +292,7 @@ cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const W
   const unsigned nbd = std::min<unsigned>(wblk(n), kWtDotBlocks);
   wt_dots_kernel<<<dim3(nbd, s), kWtThreads, 0, c.stream>>>(n, t, dpart);
   wt_final_kernel<<<4 * (s + 1) + 1, 128, 0, c.stream>>>(s, (int)nbd, dpart, (int)nbl, lpart, tauK, 1.0 / n, c0,
-                                                         pen, gc, gd, loss);
+                                                         gc, gd, loss);
   return cudaGetLastError();
 }
 
@@ -263,6 +307,28 @@ cudaError_t wt_adam(cudaStream_t st, int np, float *p, float *m, float *v, const
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
   wt_adam_kernel<<<(np + 127) / 128, 128, 0, st>>>(np, p, m, v, g, lr, b1, b2, 1e-12f, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t wt_power(Ctx &c, const float *y, const float *zero, float *v, float *u, double *part, double *ss,
+                     int iters) {
+  if (c.n == 0) return cudaSuccess;
+  const int32_t n = (int32_t)c.n;
+  const float th = (float)(c.p.Tref_K / c.p.Tmax_K);
+  const unsigned nbd = std::min<unsigned>(wblk(n), kWtDotBlocks);
+  wt_seed_kernel<<<wblk(n), kWtThreads, 0, c.stream>>>(n, u);
+  for (int it = 0; it <= iters; ++it) {
+    // v = u / |u|; then u = J(y)^T v (the adjoint kernel with lam_{j-1} = u zeroed,
+    // c1 = 0, a = 1), so that |u| -> |lambda_max| as the iteration converges
+    wt_sumsq_kernel<<<nbd, kWtThreads, 0, c.stream>>>(n, u, part);
+    wt_total_kernel<<<1, 128, 0, c.stream>>>((int)nbd, part, ss);
+    if (it == iters) break;
+    wt_normalise_kernel<<<wblk(n), kWtThreads, 0, c.stream>>>(n, u, ss, v);
+    cudaError_t e = cudaMemsetAsync(u, 0, sizeof(float) * n, c.stream);
+    if (e != cudaSuccess) return e;
+    wt_adjoint_kernel<<<wblk(n), kWtThreads, 0, c.stream>>>(n, c.nbr, c.cnt, th, y, zero, v, 0.0f, 1.0f, 0.0f, u,
+                                                           nullptr);
+  }
   return cudaGetLastError();
 }
 

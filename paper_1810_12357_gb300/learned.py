@@ -35,14 +35,15 @@ def generate_windows(system, params: dict, n_windows: int, n_w: int = 16, stride
     return g, pairs
 
 
-def train(model, pairs, steps: int, lr: float = 3e-3, log_every: int = 0, ctx=None):
+def train(model, pairs, steps: int, lr: float = 3e-3, log_every: int = 0, ctx=None, **kw):
     """Adam steps cycling through the windows of the network (EhcNN) or of the
     trained Chebyshev window (EhcCheb); returns the loss history.  `ctx` is the
-    context the windows were generated on (default the model's own)."""
+    context the windows were generated on (default the model's own); further
+    keywords go to the model's train_step."""
     hist = []
     for k in range(steps):
         t0, t1 = pairs[k % len(pairs)]
-        loss = model.train_step(t0, t1, lr, ctx=ctx)
+        loss = model.train_step(t0, t1, lr, ctx=ctx, **kw)
         hist.append(loss)
         if log_every and k % log_every == 0:
             print(f"step {k} loss {loss:.4e}")

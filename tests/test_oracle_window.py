@@ -248,7 +248,8 @@ def test_general_stages_reproduce_both_recurrences(order):
         assert W.stability_polynomial(C, x) == pytest.approx(want, rel=1e-11, abs=1e-13)
 
 
-def test_window_gradient_matches_differences():
+@pytest.mark.parametrize("power", [2, 4])
+def test_window_gradient_matches_differences(power):
     rowptr, col, th = _small_system()
     K, tau, s, Tmax = 40.0, 0.06, 5, 20000.0
     T0 = th * Tmax
@@ -257,7 +258,7 @@ def test_window_gradient_matches_differences():
     Ct = [c * (1.0 + 0.05 * np.sin(np.arange(c.size) + k)) for k, c in enumerate(C)]
     zt, _ = W.window_general(rowptr, col, th, K, tau, Ct)
     T1 = T0 + Tmax * zt[s]
-    loss, g = W.window_grad(rowptr, col, T0, T1, Tmax, K, tau, C)
+    loss, g = W.window_grad(rowptr, col, T0, T1, Tmax, K, tau, C, power)
     assert loss > 0
     checked = 0
     for k in range(4):
@@ -270,8 +271,8 @@ def test_window_gradient_matches_differences():
             Cm = [c.copy() for c in C]
             Cp[k][j] += h
             Cm[k][j] -= h
-            lp = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cp)[0][s], Tmax)
-            lm = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cm)[0][s], Tmax)
+            lp = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cp)[0][s], Tmax, power)
+            lm = W.window_loss(T0, T1, W.window_general(rowptr, col, th, K, tau, Cm)[0][s], Tmax, power)
             fd = (lp - lm) / (2 * h)
             assert g[k][j] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(loss) / h), (k, j)
             checked += 1
