@@ -165,8 +165,10 @@ int ehc_drift(ehc_ctx *c, double *x_dev, const double *v_dev, double dt_fs);
 
 /* One whole MD step with HOST buffers: copies x_host, v_host [N,3] to the
  * device, runs build, n_sub substeps from t_fs, couple and drift, and copies
- * x, v and the electronic temperatures back (Te_host_out [N]).  Host buffers
- * should be page-locked for full copy speed.  Synchronises. */
+ * x, v and the electronic temperatures back (Te_host_out [N]).  The velocity
+ * upload overlaps the binning and neighbour search, its download the drift (on
+ * a second stream of the context).  Host buffers should be page-locked for full
+ * copy speed.  Synchronises. */
 int ehc_md_step_host(ehc_ctx *c, double *x_host, double *v_host, int32_t n_sub,
                      double t_fs, double dt_md_fs, double *Te_host_out);
 

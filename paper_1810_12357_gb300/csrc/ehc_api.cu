@@ -67,6 +67,9 @@ void free_all(Ctx &c) {
   c.n_graphs = 0;
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   if (c.pulse_ev) cudaEventDestroy(c.pulse_ev);
+  if (c.io_stream) cudaStreamDestroy(c.io_stream);
+  for (cudaEvent_t e : c.io_ev)
+    if (e) cudaEventDestroy(e);
 }
 
 // read back scal[0..15] and the error word; synchronises the stream
@@ -368,6 +371,8 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, 0));
   A(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   A(cudaEventCreateWithFlags(&c.pulse_ev, cudaEventDisableTiming));
+  A(cudaStreamCreateWithFlags(&c.io_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t &e : c.io_ev) A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   if (!ok) {
     cudaGetLastError();
     free_all(c);
@@ -453,7 +458,9 @@ namespace {
 
 // first half of a neighbour build: queue every kernel and the copies of the
 // per-step scalars to pinned host memory (no synchronisation)
-int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev) {
+// v_ready (if not null): an event after which v_dev holds the velocities; the
+// stream waits for it only before the velocity gather, after the neighbour search
+int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t v_ready = nullptr) {
   c.t_version += 1;
   if (!c.have_te) return EHC_E_STATE;
   if (c.n > 0 && (!x_dev || !v_dev)) return EHC_E_INVAL;
@@ -462,9 +469,11 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev) {
   c.ff_valid = false;
   CK(launch_bin(c, x_dev));
   CK(launch_sort_cells(c));
-  CK(launch_gather(c, v_dev, c.te_orig_order));
+  CK(launch_gather(c, c.te_orig_order));
   c.te_orig_order = false;
   CK(launch_neighbors(c));
+  if (v_ready) CK(cudaStreamWaitEvent(c.stream, v_ready, 0));
+  CK(launch_gather_vel(c, v_dev));
   CK(launch_lattice_temperature(c));
   CK(launch_globals(c));
   CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));
@@ -756,25 +765,48 @@ int ehc_md_step_host(ehc_ctx *h, double *x_host, double *v_host, int32_t n_sub, 
   if (!h || (h->c.n > 0 && (!x_host || !v_host || !Te_host_out))) return EHC_E_INVAL;
   Ctx &c = h->c;
   const size_t b3 = sizeof(double) * 3 * (size_t)c.n;
-  if (c.n > 0) {
-    CK(cudaMemcpyAsync(c.x_dev, x_host, b3, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemcpyAsync(c.v_dev, v_host, b3, cudaMemcpyHostToDevice, c.stream));
+  if (!c.have_te) return EHC_E_STATE;
+  if (c.n == 0) {
+    int r = ehc_build_neighbors(h, c.x_dev, c.v_dev);
+    if (r == EHC_OK) r = ehc_substep(h, n_sub, t_fs);
+    if (r == EHC_OK) r = ehc_couple(h, c.v_dev, dt_md_fs);
+    if (r == EHC_OK) r = ehc_drift(h, c.x_dev, c.v_dev, dt_md_fs);
+    return r ? r : ehc_sync(h);
   }
-  int r = ehc_build_neighbors(h, c.x_dev, c.v_dev);
+  // the positions go first on the context stream; the velocities, needed only by
+  // the velocity gather after the neighbour search, come on io_stream meanwhile
+  CK(cudaEventRecord(c.io_ev[0], c.stream));
+  CK(cudaStreamWaitEvent(c.io_stream, c.io_ev[0], 0));
+  CK(cudaMemcpyAsync(c.x_dev, x_host, b3, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemcpyAsync(c.v_dev, v_host, b3, cudaMemcpyHostToDevice, c.io_stream));
+  CK(cudaEventRecord(c.io_ev[1], c.io_stream));
+  int r = build_enqueue(c, c.x_dev, c.v_dev, c.io_ev[1]);
+  if (r) {
+    cudaStreamSynchronize(c.io_stream);
+    cudaStreamSynchronize(c.stream);
+    return r;
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  r = build_finish(c, true);
   if (r) return r;
   r = ehc_substep(h, n_sub, t_fs);
   if (r) return r;
   r = ehc_couple(h, c.v_dev, dt_md_fs);
   if (r) return r;
+  // the velocities are final after the hand-over: download them on io_stream
+  // while the context stream runs the drift (which only reads them)
+  CK(cudaEventRecord(c.io_ev[2], c.stream));
+  CK(cudaStreamWaitEvent(c.io_stream, c.io_ev[2], 0));
+  CK(cudaMemcpyAsync(v_host, c.v_dev, b3, cudaMemcpyDeviceToHost, c.io_stream));
   r = ehc_drift(h, c.x_dev, c.v_dev, dt_md_fs);
-  if (r) return r;
-  r = ehc_get_te(h, c.T_out);
-  if (r) return r;
-  if (c.n > 0) {
-    CK(cudaMemcpyAsync(x_host, c.x_dev, b3, cudaMemcpyDeviceToHost, c.stream));
-    CK(cudaMemcpyAsync(v_host, c.v_dev, b3, cudaMemcpyDeviceToHost, c.stream));
-    CK(cudaMemcpyAsync(Te_host_out, c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+  if (r == EHC_OK) r = ehc_get_te(h, c.T_out);
+  if (r) {
+    cudaStreamSynchronize(c.io_stream);
+    return r;
   }
+  CK(cudaMemcpyAsync(x_host, c.x_dev, b3, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(Te_host_out, c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.io_stream));
   return ehc_sync(h);
 }
 

@@ -139,7 +139,8 @@ struct Ctx;
 // kernels_build.cu
 cudaError_t launch_bin(Ctx &c, const double *x);
 cudaError_t launch_sort_cells(Ctx &c);
-cudaError_t launch_gather(Ctx &c, const double *v, bool first);
+cudaError_t launch_gather(Ctx &c, bool first);
+cudaError_t launch_gather_vel(Ctx &c, const double *v);
 cudaError_t launch_neighbors(Ctx &c);
 cudaError_t launch_lattice_temperature(Ctx &c);
 cudaError_t launch_globals(Ctx &c);
@@ -223,6 +224,10 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t pulse_ev = nullptr;
+  // host-buffer MD step: the velocity upload and download run on io_stream,
+  // ordered against the context stream by io_ev
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev[3] = {nullptr, nullptr, nullptr};
 
   // device buffers
   int32_t *type_orig = nullptr;  // caller's type index per atom (original order), or null

@@ -169,7 +169,9 @@ __global__ void drift_kernel(int64_t n3, double *__restrict__ x, const double *_
                              double L0, double L1, double L2, int p0, int p1, int p2) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n3) return;
-  const int k = (int)(j % 3);
+  // the coordinate index without a 64-bit division (n3 < 2^32 for every
+  // context that fits a GPU: 3 x 2^31 atoms would need 48 GB per array)
+  const int k = n3 < (int64_t)0xffffffff ? (int)((uint32_t)j % 3u) : (int)(j % 3);
   const double L = k == 0 ? L0 : (k == 1 ? L1 : L2);
   const int per = k == 0 ? p0 : (k == 1 ? p1 : p2);
   // no contraction: x + v dt rounds the product and the sum separately
