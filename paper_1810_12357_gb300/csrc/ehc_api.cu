@@ -469,11 +469,15 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t 
   c.ff_valid = false;
   CK(launch_bin(c, x_dev));
   CK(launch_sort_cells(c));
-  CK(launch_gather(c, c.te_orig_order));
+  // with velocities still in flight the gather leaves them to a second pass after
+  // the neighbour search
+  CK(launch_gather(c, v_ready ? nullptr : v_dev, c.te_orig_order));
   c.te_orig_order = false;
   CK(launch_neighbors(c));
-  if (v_ready) CK(cudaStreamWaitEvent(c.stream, v_ready, 0));
-  CK(launch_gather_vel(c, v_dev));
+  if (v_ready) {
+    CK(cudaStreamWaitEvent(c.stream, v_ready, 0));
+    CK(launch_gather_vel(c, v_dev));
+  }
   CK(launch_lattice_temperature(c));
   CK(launch_globals(c));
   CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));

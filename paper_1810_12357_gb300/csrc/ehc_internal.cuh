@@ -139,7 +139,9 @@ struct Ctx;
 // kernels_build.cu
 cudaError_t launch_bin(Ctx &c, const double *x);
 cudaError_t launch_sort_cells(Ctx &c);
-cudaError_t launch_gather(Ctx &c, bool first);
+// v == nullptr: positions, temperatures and types only; launch_gather_vel then
+// gathers the velocities (before the lattice temperature)
+cudaError_t launch_gather(Ctx &c, const double *v, bool first);
 cudaError_t launch_gather_vel(Ctx &c, const double *v);
 cudaError_t launch_neighbors(Ctx &c);
 cudaError_t launch_lattice_temperature(Ctx &c);

@@ -146,14 +146,10 @@ __global__ void sort_cells_kernel(const int32_t *__restrict__ start, int64_t nce
 }
 
 // move per-atom data into the new sorted order
-// velocities in sorted order on the 2^-48 A/fs grid (exact momentum sums) with
-// |v|^2 in FP64, and the speed guard; separate from gather_kernel so that the
-// velocities are needed only after the neighbour search
-__global__ void gather_vel_kernel(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ v,
-                                  VelQ *__restrict__ v_s, int32_t *__restrict__ err) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int64_t o = perm[s];
+// velocity of sorted atom s from the caller-order array: on the 2^-48 A/fs grid
+// (exact momentum sums) with |v|^2 in FP64, and the speed guard
+__device__ __forceinline__ void gather_velocity(int64_t s, int64_t o, const double *__restrict__ v,
+                                                VelQ *__restrict__ v_s, int32_t *__restrict__ err) {
   const double vx = v[3 * o + 0], vy = v[3 * o + 1], vz = v[3 * o + 2];
   if (!(fabs(vx) < kVelMax && fabs(vy) < kVelMax && fabs(vz) < kVelMax)) atomicOr(err, ERR_SPEED);
   VelQ vq;
@@ -164,12 +160,21 @@ __global__ void gather_vel_kernel(int64_t n, const int32_t *__restrict__ perm, c
   v_s[s] = vq;
 }
 
+// the velocities alone, for a build whose velocities arrive after its neighbour search
+__global__ void gather_vel_kernel(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ v,
+                                  VelQ *__restrict__ v_s, int32_t *__restrict__ err) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  gather_velocity(s, perm[s], v, v_s, err);
+}
+
+// v == nullptr: the velocities are gathered later by gather_vel_kernel
 __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const int4 *__restrict__ q,
-                              const int32_t *__restrict__ type_orig,
+                              const double *__restrict__ v, const int32_t *__restrict__ type_orig,
                               const int32_t *__restrict__ inv_old, int src_is_orig,
                               const double *__restrict__ T_old, const double *__restrict__ A_old,
                               int32_t *__restrict__ inv_new, int4 *__restrict__ q_s,
-                              int8_t *__restrict__ type_s,
+                              VelQ *__restrict__ v_s, int8_t *__restrict__ type_s,
                               double *__restrict__ T_new, double *__restrict__ A_new,
                               float *__restrict__ dmir0, double Tref, double invTmax,
                               const double *__restrict__ depth, float *__restrict__ srcw,
@@ -179,6 +184,7 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
   int32_t o = perm[s];
   q_s[s] = q[o];
   inv_new[o] = (int32_t)s;
+  if (v) gather_velocity(s, o, v, v_s, err);
   int32_t ty = type_orig ? type_orig[o] : 0;
   type_s[s] = (int8_t)(ty < 0 ? 0 : (ty >= kMaxTypes ? kMaxTypes - 1 : ty));
   int64_t src = src_is_orig ? (int64_t)o : (int64_t)inv_old[o];
@@ -560,14 +566,14 @@ cudaError_t launch_gather_vel(Ctx &c, const double *v) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(Ctx &c, bool src_is_orig) {
+cudaError_t launch_gather(Ctx &c, const double *v, bool src_is_orig) {
   int nxt = c.cur_inv ^ 1;
   int tn = c.tcur ^ 1;
   bool laser = c.p.laser_on && c.have_depth;
   if (c.n > 0)
     gather_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
-        c.n, c.perm, c.q_orig, c.type_orig, c.inv_perm[c.cur_inv], src_is_orig ? 1 : 0, c.T[c.tcur], c.A,
-        c.inv_perm[nxt], c.q_s, c.type_s, c.T[tn], c.A_tmp, c.dmir[0], c.p.Tref_K, 1.0 / c.p.Tmax_K,
+        c.n, c.perm, c.q_orig, v, c.type_orig, c.inv_perm[c.cur_inv], src_is_orig ? 1 : 0, c.T[c.tcur], c.A,
+        c.inv_perm[nxt], c.q_s, c.v_s, c.type_s, c.T[tn], c.A_tmp, c.dmir[0], c.p.Tref_K, 1.0 / c.p.Tmax_K,
         laser ? c.depth_orig : nullptr, c.srcw, c.srcw_d, laser ? 1.0 / c.p.laser_lp_A : 0.0, c.err);
   c.cur_inv = nxt;
   c.tcur = tn;
