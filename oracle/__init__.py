@@ -56,7 +56,7 @@ def lib():
         L.oracle_flux_vjp.argtypes = [i64, P, P, P, P, P]
         L.oracle_flux_vjp.restype = None
         L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
-                                      dbl, P, P, dbl, dbl, dbl, P]
+                                      dbl, P, P, dbl, dbl, dbl, P, P, P]
         L.oracle_substeps.restype = ctypes.c_int
         L.oracle_philox4x32_10.argtypes = [P, P, P]
         L.oracle_philox4x32_10.restype = None
@@ -164,8 +164,10 @@ def flux_vjp(rowptr, col, theta, lam):
 
 
 def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=None,
-             source=None, Ce_SI=1.0, vatom_A3=1.0, t_start=0.0):
-    """In place on T and A; returns (status, E_src increment)."""
+             source=None, Ce_SI=1.0, vatom_A3=1.0, t_start=0.0, Tfix=None, eres=None):
+    """In place on T and A; returns (status, E_src increment).  Tfix: per-atom
+    border temperature (NaN: free atom); the kelvin sum the border absorbed is
+    added to eres[0] (a one-element float64 array) when given."""
     n = rowptr.shape[0] - 1
     esrc = np.zeros(1)
     src = None
@@ -173,11 +175,15 @@ def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=No
         src = np.ascontiguousarray([1.0, source["fluence_Jm2"], source["lp_A"], source["t0_fs"],
                                     source["sigma_fs"]], dtype=np.float64)
         depth = np.ascontiguousarray(depth, dtype=np.float64)
+    if Tfix is not None:
+        Tfix = np.ascontiguousarray(Tfix, dtype=np.float64)
     st = lib().oracle_substeps(n, _p(rowptr), _p(col), _p(T), _p(Tl), _p(chi), _p(A), int(n_sub),
                                float(dt), float(Tmax), float(K), float(cG), float(VG),
                                _p(depth) if depth is not None else None,
                                _p(src) if src is not None else None, float(Ce_SI),
-                               float(vatom_A3), float(t_start), _p(esrc))
+                               float(vatom_A3), float(t_start), _p(esrc),
+                               _p(Tfix) if Tfix is not None else None,
+                               _p(eres) if eres is not None else None)
     return st, float(esrc[0])
 
 
@@ -244,6 +250,13 @@ class OracleSim:
         self.E_src = 0.0
         self.n_stopped = 0
         self.VC = None
+        self.Tfix = None          # border temperatures (NaN: free atom), original order
+        self.E_res = 0.0          # energy absorbed by the border in closed MD steps [eV]
+        self.eres_T = np.zeros(1) # kelvin sum absorbed in the current MD step
+
+    def set_border(self, Tfix):
+        """Fixed-temperature border: atoms with a finite Tfix are held there."""
+        self.Tfix = None if Tfix is None else np.ascontiguousarray(Tfix, dtype=np.float64).copy()
 
     # electronic temperature ------------------------------------------------
     def set_te(self, Te):
@@ -265,6 +278,8 @@ class OracleSim:
             s = float(self.T.sum())
             self.E_base += self.VC * (s - self.ST_base)
             self.ST_base = s
+            self.E_res += self.VC * float(self.eres_T[0])
+            self.eres_T[0] = 0.0
         self.rowptr, self.col = neighbors(x, self.box, self.per, p["rc"])
         self.Tl, self.Kself = lattice_temperature(self.rowptr, self.col, v, self.mass,
                                                   p.get("dof_mode", 0))
@@ -295,7 +310,7 @@ class OracleSim:
         st, es = substeps(self.rowptr, self.col, self.T, self.Tl, self.chi, self.A, n_sub,
                           p["dt_sub"], p["Tmax"], self.K, self.cG, self.VG, depth=self.depth,
                           source=p.get("laser"), Ce_SI=self.Ce, vatom_A3=self.vatom,
-                          t_start=t_start)
+                          t_start=t_start, Tfix=self.Tfix, eres=self.eres_T)
         if st < 0:
             raise FloatingPointError(f"theta left [0,1] at substep {-st - 1}")
         self.E_src += es
@@ -313,6 +328,7 @@ class OracleSim:
     def energy(self) -> dict:
         s = float(self.T.sum())
         E_e = self.E_base + self.VC * (s - self.ST_base) if self.VC is not None else self.E_base
-        return {"E_e": E_e, "E_lat": self.E_lat, "E_src": self.E_src, "E_e0": self.E_e0,
+        E_res = self.E_res + (self.VC * float(self.eres_T[0]) if self.VC is not None else 0.0)
+        return {"E_e": E_e, "E_lat": self.E_lat, "E_src": self.E_src, "E_e0": self.E_e0, "E_res": E_res,
                 "sum_T": s, "max_T": float(self.T.max()),
-                "drift": (E_e + self.E_lat - self.E_src - self.E_e0) / max(abs(self.E_e0), abs(E_e))}
+                "drift": (E_e + self.E_lat - self.E_src + E_res - self.E_e0) / max(abs(self.E_e0), abs(E_e))}

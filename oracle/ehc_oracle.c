@@ -320,11 +320,18 @@ typedef struct {
  * chi_i = 0 switches the coupling off for atom i (Eq. Xi guard).
  * Returns the number of substeps done, or -(substep+1) if some theta left
  * [0, 1] or became NaN. */
+/* Optional fixed-temperature border (a Dirichlet condition on T_e, as the
+ * 300 K border shell of the paper's cascade runs, Sec. 5): where Tfix[i] is not
+ * NaN, atom i is an electron reservoir held at Tfix[i].  Every substep is first
+ * taken for all atoms as above (so a border atom exchanges pair fluxes and
+ * coupling energy with its T held at Tfix[i]); then each border atom is put back
+ * to Tfix[i] and the change it would have made, T_new - Tfix[i], is added to
+ * *Eres_T (kelvin; times V_atom C_e it is the energy the reservoir absorbed). */
 int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double *T,
                     const double *Tl, const uint8_t *chi, double *A, int n_sub, double dt,
                     double Tmax, double K, double cG, double VG, const double *depth,
                     const double *src, double Ce_SI, double vatom_A3, double t_start,
-                    double *E_src) {
+                    double *E_src, const double *Tfix, double *Eres_T) {
   double *theta = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   double *Tn = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   if (!theta || !Tn) { free(theta); free(Tn); return -1000000; }
@@ -366,6 +373,15 @@ int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double
       Tn[i] = T[i] + dt * dTdt;
     }
     esrc += esrc_step;
+    if (Tfix) {
+      double absorbed = 0.0;
+      for (int64_t i = 0; i < n; ++i)
+        if (Tfix[i] == Tfix[i]) {
+          absorbed += Tn[i] - Tfix[i];
+          Tn[i] = Tfix[i];
+        }
+      if (Eres_T) *Eres_T += absorbed;
+    }
     memcpy(T, Tn, sizeof(double) * (size_t)n);
   }
   if (E_src) *E_src += esrc;
