@@ -142,8 +142,17 @@ def run_gpu(args):
 
     s, p = workload(args.cells, args.tile_threads)
     n = s.n
+    tfix = None
+    if args.border > 0:
+        # fixed 300 K electron shell of the given thickness at the box faces
+        shell = np.any((s.x < args.border) | (s.x > s.box - args.border), axis=1)
+        s.Te[shell] = 300.0
+        tfix = np.where(shell, 300.0, np.nan)
+        args.border_atoms = int(shell.sum())
     sim = Ehc(p, s)
     sim.set_te(s.Te)
+    if tfix is not None:
+        sim.set_border(tfix)
     x = torch.as_tensor(s.x, device=dev).contiguous()
     v = torch.as_tensor(s.v, device=dev).contiguous()
     stream = torch.cuda.current_stream()
@@ -192,11 +201,11 @@ def run_gpu(args):
     # end to end through the host-buffer entry point: inputs copied in, results copied out
     e2e_ms = float("nan")
     if not args.no_e2e:
-        e2e_ms = _e2e(args, s, p, n, barrier, stream)
+        e2e_ms = _e2e(args, s, p, n, barrier, stream, tfix)
     _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks)
 
 
-def _e2e(args, s, p, n, barrier, stream):
+def _e2e(args, s, p, n, barrier, stream, tfix=None):
     import torch
     from paper_1810_12357_gb300 import Ehc
     xh = torch.as_tensor(s.x).clone().pin_memory()
@@ -204,6 +213,8 @@ def _e2e(args, s, p, n, barrier, stream):
     Teh = torch.empty(n, dtype=torch.float64).pin_memory()
     h = Ehc(p, s)
     h.set_te(s.Te)
+    if tfix is not None:
+        h.set_border(tfix)
     e2e_steps = max(1, min(args.steps, 10))
     for k in range(2):
         h.md_step_host(xh, vh, N_SUB, k * DT_MD, DT_MD, Teh)
@@ -252,8 +263,11 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 pair flux / f64 state", "data": "synthetic",
-        "config": config_dict(args.cells, n, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                                              "path": "plain"}),
+        "config": config_dict(args.cells, n, dict({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                                   "path": "plain"},
+                                                  **({"border": "fixed 300 K electron shell %g A thick, %d atoms"
+                                                      % (args.border, args.border_atoms)}
+                                                     if args.border > 0 else {}))),
         "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
@@ -683,6 +697,7 @@ def main():
     ap.add_argument("--frozen-lattice", action="store_true")
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--tile-threads", type=int, default=0)
+    ap.add_argument("--border", type=float, default=0.0)
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)

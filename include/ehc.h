@@ -107,7 +107,7 @@ typedef struct ehc_params {
  * incrementally: E_e0 = sum_i V_atom int_0^{T_i} C_e(T) dT at ehc_set_te, then
  * each MD step adds V_atom C_e sum_i dT_i with that step's C_e.  E_lat is the
  * kinetic energy the lattice received, E_src the energy of the source term.
- * drift = (E_e + E_lat - E_src - E_e0) / max(|E_e0|, |E_e|). */
+ * drift = (E_e + E_lat - E_src + E_res - E_e0) / max(|E_e0|, |E_e|). */
 typedef struct ehc_energy_t {
   double E_e, E_lat, E_src, E_e0, drift;
   double sum_T, max_T, mean_T;
@@ -117,6 +117,8 @@ typedef struct ehc_energy_t {
   int64_t md_step;
   int32_t max_count;                /* largest neighbour count */
   int32_t device_error;             /* bit set of device-side error flags */
+  double E_res;                     /* energy absorbed by the fixed-temperature border
+                                       (ehc_set_border), 0 without one */
 } ehc_energy_t;
 
 typedef struct ehc_ctx ehc_ctx;
@@ -158,6 +160,22 @@ int ehc_substep(ehc_ctx *c, int32_t n_sub, double t_fs);
  * substeps to its velocity (Eqs. RateExchange, WorkDone, Xi), in place on v_dev
  * [N,3].  dt_md_fs is the MD step (Langevin friction and noise amplitude). */
 int ehc_couple(ehc_ctx *c, double *v_dev, double dt_md_fs);
+
+/* Fixed-temperature electron border (a Dirichlet condition on T_e, as the 300 K
+ * border shell of the paper's cascade runs, Sec. 5; no other counterpart in the
+ * paper).  Tfix_dev [N] (caller order, device, copied): atom i with a finite
+ * Tfix_dev[i] is an electron reservoir held at that temperature (0..Tmax_K, else
+ * EHC_E_RANGE at the build); NaN marks a free atom; NULL removes the border.
+ * Takes effect at the next ehc_build_neighbors.  Every substep is taken for all
+ * atoms (a border atom exchanges pair fluxes and coupling energy at its fixed
+ * T), then border atoms are put back to their temperature; what they would have
+ * gained, times V_atom C_e, is the reservoir energy E_res of ehc_energy, which
+ * closes the ledger.  Set T_e of border atoms to Tfix in ehc_set_te: a
+ * difference is otherwise charged to the reservoir at the first substep.  The
+ * first call allocates 40 bytes per atom.  With a border, ehc_cheb_step and
+ * ehc_nn_step advance by plain substeps (counted as fallbacks) and ehc_save
+ * returns EHC_E_STATE. */
+int ehc_set_border(ehc_ctx *c, const double *Tfix_dev);
 
 /* Free flight x += v dt, wrapped into the box on periodic axes: the stand-in
  * for the host MD integrator when no interatomic forces are available. */

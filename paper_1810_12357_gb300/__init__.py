@@ -59,7 +59,7 @@ class ehc_energy_t(ctypes.Structure):
         ("max_T", ctypes.c_double), ("mean_T", ctypes.c_double), ("Te_mean_step", ctypes.c_double),
         ("Tlat_step", ctypes.c_double), ("Ce_SI", ctypes.c_double), ("K_per_fs", ctypes.c_double),
         ("stability", ctypes.c_double), ("n_stopped", ctypes.c_int64), ("md_step", ctypes.c_int64),
-        ("max_count", ctypes.c_int32), ("device_error", ctypes.c_int32),
+        ("max_count", ctypes.c_int32), ("device_error", ctypes.c_int32), ("E_res", ctypes.c_double),
     ]
 
 
@@ -71,6 +71,7 @@ _SIGS = {
                         ctypes.POINTER(_P)]),
     "ehc_set_te": (_I, [_P, _P]),
     "ehc_set_depth": (_I, [_P, _P]),
+    "ehc_set_border": (_I, [_P, _P]),
     "ehc_build_neighbors": (_I, [_P, _P, _P]),
     "ehc_substep": (_I, [_P, ctypes.c_int32, ctypes.c_double]),
     "ehc_couple": (_I, [_P, _P, ctypes.c_double]),
@@ -249,6 +250,15 @@ class Ehc:
     def set_depth(self, depth):
         t = self._dev(depth)
         _check(self._lib.ehc_set_depth(self._h, _ptr(t)), "ehc_set_depth")
+
+    def set_border(self, Tfix):
+        """Fixed-temperature border from the next build: atoms with a finite
+        Tfix (caller order) are held there, NaN marks free atoms; None removes it."""
+        if Tfix is None:
+            _check(self._lib.ehc_set_border(self._h, None), "ehc_set_border")
+            return
+        t = self._dev(Tfix)
+        _check(self._lib.ehc_set_border(self._h, _ptr(t)), "ehc_set_border")
 
     def build_neighbors(self, x, v):
         _check(self._lib.ehc_build_neighbors(self._h, _ptr(x), _ptr(v)), "ehc_build_neighbors")

@@ -56,7 +56,8 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work};
+                 c.work, c.tfix_orig, c.bnd_s, c.bnd_row, c.bnd_cnt, c.bnd_off, c.bnd_n, c.bnd_h, c.bnd_l, c.bnd_T,
+                 c.bnd_R, c.bnd_part};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -154,13 +155,14 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   const int path = (c.p.flux_prec == 1) ? 2 : (tile_path(c) ? 1 : 0);
   const int pairs = (c.n_max + 1) / 2;
   const int tile = c.tile_floats, nt = c.tile_nt;
+  const int border = c.has_border ? 1 : 0;
   bool use_graph = c.p.use_graph && n_sub >= 4;
   if (use_graph) {
     int hit = -1;
     for (int i = 0; i < c.n_graphs; ++i) {
       const auto &e = c.graphs[i];
       if (e.n_sub == n_sub && e.parity == p0 && e.tcur == c.tcur && e.abuf == ab && e.path == path &&
-          e.pairs == pairs && e.tile == tile && e.nt == nt)
+          e.pairs == pairs && e.tile == tile && e.nt == nt && e.border == border)
         hit = i;
     }
     if (hit < 0) {
@@ -181,7 +183,7 @@ int run_substeps(Ctx &c, int32_t n_sub) {
         c.graphs[lru] = c.graphs[7];
         c.n_graphs = 7;
       }
-      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, path, pairs, tile, nt, exec, 0};
+      c.graphs[c.n_graphs] = {n_sub, p0, c.tcur, ab, path, pairs, tile, nt, border, exec, 0};
       hit = c.n_graphs++;
     }
     c.graphs[hit].last_use = ++c.use_clock;
@@ -439,7 +441,47 @@ int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
   c.ST_base = c.scal_host[0];
   c.VC_prev = -1;
   c.E_src = 0;
+  c.E_res = 0;
   c.md_step = 0;
+  return EHC_OK;
+}
+
+int ehc_set_border(ehc_ctx *h, const double *Tfix_dev) {
+  if (!h) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!Tfix_dev || c.n == 0) {
+    c.border_next = false;
+    return EHC_OK;
+  }
+  if (!c.tfix_orig) {
+    const int64_t n = c.n;
+    bool ok = true;
+    auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+    A(dalloc(&c.tfix_orig, n));
+    A(dalloc(&c.bnd_s, n));
+    A(dalloc(&c.bnd_row, n));
+    A(dalloc(&c.bnd_h, n));
+    A(dalloc(&c.bnd_l, n));
+    A(dalloc(&c.bnd_T, n));
+    A(dalloc(&c.bnd_R, n));
+    A(dalloc(&c.bnd_cnt, (int64_t)border_blocks(n)));
+    A(dalloc(&c.bnd_off, (int64_t)border_blocks(n)));
+    A(dalloc(&c.bnd_part, (int64_t)border_red_blocks()));
+    A(dalloc(&c.bnd_n, 1));
+    if (ok) A(cudaMemsetAsync(c.bnd_n, 0, sizeof(int32_t), c.stream));
+    if (!ok) {
+      cudaGetLastError();
+      for (void **q : {(void **)&c.tfix_orig, (void **)&c.bnd_s, (void **)&c.bnd_row, (void **)&c.bnd_h, (void **)&c.bnd_l,
+                       (void **)&c.bnd_T, (void **)&c.bnd_R, (void **)&c.bnd_cnt, (void **)&c.bnd_off,
+                       (void **)&c.bnd_part, (void **)&c.bnd_n}) {
+        if (*q) cudaFree(*q);
+        *q = nullptr;
+      }
+      return EHC_E_NOMEM;
+    }
+  }
+  CK(cudaMemcpyAsync(c.tfix_orig, Tfix_dev, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+  c.border_next = true;
   return EHC_OK;
 }
 
@@ -473,6 +515,14 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t 
   // the neighbour search
   CK(launch_gather(c, v_ready ? nullptr : v_dev, c.te_orig_order));
   c.te_orig_order = false;
+  if (c.bnd_n) {
+    // the reservoirs of the previous MD step's list (kelvin) go to scal[10]; then
+    // the list of the new sort order, or none
+    CK(border_sum(c, c.scal + 10));
+    if (c.border_next) CK(border_build(c));
+    else CK(cudaMemsetAsync(c.bnd_n, 0, sizeof(int32_t), c.stream));
+  }
+  c.has_border = c.border_next;
   CK(launch_neighbors(c));
   if (v_ready) {
     CK(cudaStreamWaitEvent(c.stream, v_ready, 0));
@@ -513,6 +563,7 @@ int build_finish(Ctx &c, bool own_tiles) {
   if (c.VC_prev > 0) {
     c.E_base += c.VC_prev * (sumT - c.ST_base);
     c.ST_base = sumT;
+    if (c.bnd_n) c.E_res += c.VC_prev * c.scal_host[10];
   }
   const double N = (double)(c.n > 0 ? c.n : 1);
   // system means (Sec. 2): mean electronic temperature, classical T_lat = K / ((3/2) k_B N)
@@ -690,6 +741,7 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   int r0 = ensure_t(c);
   if (r0) return r0;
   CK(launch_ledger(c));
+  if (c.bnd_n) CK(border_sum(c, c.scal + 11));
   int r = readback(c);
   if (r) return r;
   const double sumT = c.scal_host[0];
@@ -698,8 +750,10 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   out->E_lat = c.scal_host[8];
   out->E_src = c.E_src;
   out->E_e0 = c.E_e0;
+  // the border's reservoirs: closed MD steps, and the current one with its C_e
+  out->E_res = c.E_res + (c.bnd_n && c.VC_prev > 0 ? c.VC_prev * c.scal_host[11] : 0.0);
   const double scale = std::max(std::fabs(c.E_e0), std::fabs(out->E_e));
-  out->drift = scale > 0 ? (out->E_e + out->E_lat - out->E_src - out->E_e0) / scale : 0.0;
+  out->drift = scale > 0 ? (out->E_e + out->E_lat - out->E_src + out->E_res - out->E_e0) / scale : 0.0;
   out->sum_T = sumT;
   out->max_T = c.scal_host[1];
   out->mean_T = c.n > 0 ? sumT / (double)c.n : 0.0;
@@ -835,7 +889,7 @@ struct CkptHeader {
 int ehc_save(ehc_ctx *h, const char *path) {
   if (!h || !path) return EHC_E_INVAL;
   Ctx &c = h->c;
-  if (!c.have_te) return EHC_E_STATE;
+  if (!c.have_te || c.has_border || c.border_next) return EHC_E_STATE;
   std::vector<double> T(c.n), A(c.n);
   int r = ehc_get_te(h, c.T_out);
   if (r) return r;
@@ -1515,8 +1569,9 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   if (!c.built) return EHC_E_STATE;
   if (!(c.stability <= 2.0)) return EHC_E_UNSTABLE;
   if (c.n == 0) return EHC_OK;
-  if (!tile_path(c)) {
-    // the stages run in the row-tile kernel; without it advance the window plainly
+  if (!tile_path(c) || c.has_border) {
+    // the stages run in the row-tile kernel and know no border; without it, or
+    // with a border, advance the window plainly
     w->windows += 1;
     w->fallbacks += 1;
     if (fell_back) *fell_back = 1;
@@ -1921,6 +1976,14 @@ int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_
   int r = ensure_t(c);
   if (r) return r;
   if (c.n == 0) return EHC_OK;
+  if (c.has_border) {
+    // the network knows no border: plain substeps
+    nn->windows += 1;
+    nn->fallbacks += 1;
+    if (fell_back) *fell_back = 1;
+    if (rho_out) *rho_out = -1.0;
+    return ehc_substep(hc, nn->n_w, t_fs);
+  }
   // the window's state in sorted order: T0 and its mirror
   CK(nn_gather(c, c.T[c.tcur], nullptr, nn->T0, nullptr, nn->dm0, true));
   CK(nn_forward(c, nn->H, nn->pb, nn->sigma, nn->n_w, nn->dm0, nn->h, nn->T0, nn->T1, nn->dm1));

@@ -209,6 +209,12 @@ cudaError_t nn_residual(Ctx &c, const float *d0, const float *d1, const double *
                         float *part, float *out);
 cudaError_t nn_couple_window(Ctx &c, const double *T0, double *T1, float *d1, double *dTc, int n_w);
 cudaError_t nn_accept(Ctx &c, const double *dTc);
+// kernels_border.cu (fixed-temperature border)
+int border_blocks(int64_t n);
+int border_red_blocks();
+cudaError_t border_build(Ctx &c);                 // the list of the current sort order
+cudaError_t border_sum(Ctx &c, double *out);       // sum of the list's reservoirs [K] into *out (device)
+cudaError_t border_fix(Ctx &c, int parity, bool tile, cudaStream_t st);   // after substep of parity
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);
@@ -314,8 +320,17 @@ struct Ctx {
   double E_e0 = 0, E_base = 0, ST_base = 0, VC_prev = -1, E_src = 0;
 
   // captured substep loops, keyed by everything a launch bakes in
+  // fixed-temperature border: tfix_orig (caller order, NaN = free) set by
+  // ehc_set_border takes effect at the next build (border_next); the build
+  // turns it into the sorted list bnd_* of bnd_n entries (device count)
+  double *tfix_orig = nullptr;
+  bool border_next = false, has_border = false;
+  int32_t *bnd_s = nullptr, *bnd_row = nullptr, *bnd_cnt = nullptr, *bnd_off = nullptr, *bnd_n = nullptr;
+  float *bnd_h = nullptr, *bnd_l = nullptr;
+  double *bnd_T = nullptr, *bnd_R = nullptr, *bnd_part = nullptr;
+  double E_res = 0.0;   // energy the border absorbed in closed MD steps [eV]
   struct GraphEntry {
-    int n_sub, parity, tcur, abuf, path, pairs, tile, nt;
+    int n_sub, parity, tcur, abuf, path, pairs, tile, nt, border;
     cudaGraphExec_t exec;
     uint64_t last_use;
   };

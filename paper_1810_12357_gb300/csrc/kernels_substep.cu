@@ -660,6 +660,12 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
                                                               c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef,
                                                               c.err);
   }
+  // border atoms back to their fixed temperature, the change into their reservoirs
+  if (c.has_border) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return border_fix(c, parity, c.p.flux_prec == 0 && tile_path(c), st);
+  }
   return cudaGetLastError();
 }
 

@@ -9,12 +9,14 @@ from paper_1810_12357_gb300 import inputs as I
 
 
 def run_oracle(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float | None = None,
-               drift: bool = True, t0: float = 0.0):
+               drift: bool = True, t0: float = 0.0, border=None):
     """The electrons and the lattice advance the same time per MD step unless
-    dt_md is given: dt_md = n_sub * dt_sub."""
+    dt_md is given: dt_md = n_sub * dt_sub.  border: per-atom fixed T_e (NaN: free)."""
     dt_md = n_sub * p["dt_sub"] if dt_md is None else dt_md
     sim = oracle.OracleSim(p, system.box, system.periodic, system.mass_amu, system.type, depth=system.depth)
     sim.set_te(system.Te)
+    if border is not None:
+        sim.set_border(border)
     x = system.x.copy()
     v = system.v.copy()
     t = t0
@@ -29,12 +31,14 @@ def run_oracle(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float | 
 
 
 def run_gpu(system: I.System, p: dict, n_md: int, n_sub: int, dt_md: float | None = None,
-            drift: bool = True, t0: float = 0.0):
+            drift: bool = True, t0: float = 0.0, border=None):
     dt_md = n_sub * p["dt_sub"] if dt_md is None else dt_md
     import torch
     from paper_1810_12357_gb300 import Ehc
     g = Ehc(p, system)
     g.set_te(system.Te)
+    if border is not None:
+        g.set_border(border)
     if system.depth is not None:
         g.set_depth(system.depth)
     x = torch.as_tensor(system.x, device="cuda").contiguous()
