@@ -56,7 +56,9 @@ def lib():
         L.oracle_flux_vjp.argtypes = [i64, P, P, P, P, P]
         L.oracle_flux_vjp.restype = None
         L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
-                                      dbl, P, P, dbl, dbl, dbl, P, P, P]
+                                      dbl, P, P, dbl, dbl, dbl, P, P, P, P]
+        L.oracle_pair_weights.argtypes = [i64, P, P, P, P, P, dbl, i32, P]
+        L.oracle_pair_weights.restype = None
         L.oracle_substeps.restype = ctypes.c_int
         L.oracle_philox4x32_10.argtypes = [P, P, P]
         L.oracle_philox4x32_10.restype = None
@@ -163,8 +165,19 @@ def flux_vjp(rowptr, col, theta, lam):
     return out
 
 
+def pair_weights(x, box, periodic, rowptr, col, S2_A2: float, n_shell: int):
+    """Distance weights S2 / (n_shell r_ij^2) of the list entries (oracle_pair_weights)."""
+    q, Lq = quantize(x, box, periodic)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    w = np.empty(col.shape[0])
+    lib().oracle_pair_weights(rowptr.shape[0] - 1, _p(np.ascontiguousarray(rowptr, dtype=np.int64)),
+                              _p(np.ascontiguousarray(col, dtype=np.int32)), _p(q), _p(Lq), _p(per),
+                              float(S2_A2), int(n_shell), _p(w))
+    return w
+
+
 def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=None,
-             source=None, Ce_SI=1.0, vatom_A3=1.0, t_start=0.0, Tfix=None, eres=None):
+             source=None, Ce_SI=1.0, vatom_A3=1.0, t_start=0.0, Tfix=None, eres=None, weights=None):
     """In place on T and A; returns (status, E_src increment).  Tfix: per-atom
     border temperature (NaN: free atom); the kelvin sum the border absorbed is
     added to eres[0] (a one-element float64 array) when given."""
@@ -177,13 +190,16 @@ def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=No
         depth = np.ascontiguousarray(depth, dtype=np.float64)
     if Tfix is not None:
         Tfix = np.ascontiguousarray(Tfix, dtype=np.float64)
+    if weights is not None:
+        weights = np.ascontiguousarray(weights, dtype=np.float64)
     st = lib().oracle_substeps(n, _p(rowptr), _p(col), _p(T), _p(Tl), _p(chi), _p(A), int(n_sub),
                                float(dt), float(Tmax), float(K), float(cG), float(VG),
                                _p(depth) if depth is not None else None,
                                _p(src) if src is not None else None, float(Ce_SI),
                                float(vatom_A3), float(t_start), _p(esrc),
                                _p(Tfix) if Tfix is not None else None,
-                               _p(eres) if eres is not None else None)
+                               _p(eres) if eres is not None else None,
+                               _p(weights) if weights is not None else None)
     return st, float(esrc[0])
 
 
@@ -281,6 +297,8 @@ class OracleSim:
             self.E_res += self.VC * float(self.eres_T[0])
             self.eres_T[0] = 0.0
         self.rowptr, self.col = neighbors(x, self.box, self.per, p["rc"])
+        ns = int(p.get("rate_shell_n", 0))
+        self.w = pair_weights(x, self.box, self.per, self.rowptr, self.col, p["zb2"], ns) if ns > 0 else None
         self.Tl, self.Kself = lattice_temperature(self.rowptr, self.col, v, self.mass,
                                                   p.get("dof_mode", 0))
         self.chi = np.ascontiguousarray((self.Kself >= p["eps_ke"]).astype(np.uint8))
@@ -310,7 +328,7 @@ class OracleSim:
         st, es = substeps(self.rowptr, self.col, self.T, self.Tl, self.chi, self.A, n_sub,
                           p["dt_sub"], p["Tmax"], self.K, self.cG, self.VG, depth=self.depth,
                           source=p.get("laser"), Ce_SI=self.Ce, vatom_A3=self.vatom,
-                          t_start=t_start, Tfix=self.Tfix, eres=self.eres_T)
+                          t_start=t_start, Tfix=self.Tfix, eres=self.eres_T, weights=self.w)
         if st < 0:
             raise FloatingPointError(f"theta left [0,1] at substep {-st - 1}")
         self.E_src += es

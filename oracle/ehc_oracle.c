@@ -320,6 +320,29 @@ typedef struct {
  * chi_i = 0 switches the coupling off for atom i (Eq. Xi guard).
  * Returns the number of substeps done, or -(substep+1) if some theta left
  * [0, 1] or became NaN. */
+/* Distance weights of the pair rates (an optional variant; the paper uses one
+ * rate K for every pair of the list): w_ij = S2 / (n_shell r_ij^2), the weight
+ * b^2 / r^2 renormalised so that an ideal shell of n_shell neighbours with
+ * second moment S2 = sum_j r_j^2 keeps sum_j w_j r_j^2 = S2.  r_ij^2 is the exact
+ * squared minimum-image distance on the quantised grid (units 2^-40 A^2), one
+ * weight per entry of the list.  Pins: the two FCC shells at r_c = 4 A get
+ * 4/3 and 2/3; symmetry; a sin mode decays at the weighted lattice sum. */
+void oracle_pair_weights(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *q,
+                         const int64_t *Lq, const int32_t *periodic, double S2_A2, int32_t n_shell,
+                         double *w) {
+  const double S2q = S2_A2 * 1099511627776.0; /* A^2 -> grid units 2^-40 A^2 */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t j = col[e];
+      int64_t d2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        const int64_t d = o_disp((int64_t)q[3 * j + k] - (int64_t)q[3 * i + k], Lq[k], periodic[k]);
+        d2 += d * d;
+      }
+      w[e] = S2q / ((double)n_shell * (double)d2);
+    }
+}
+
 /* Optional fixed-temperature border (a Dirichlet condition on T_e, as the
  * 300 K border shell of the paper's cascade runs, Sec. 5): where Tfix[i] is not
  * NaN, atom i is an electron reservoir held at Tfix[i].  Every substep is first
@@ -331,7 +354,7 @@ int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double
                     const double *Tl, const uint8_t *chi, double *A, int n_sub, double dt,
                     double Tmax, double K, double cG, double VG, const double *depth,
                     const double *src, double Ce_SI, double vatom_A3, double t_start,
-                    double *E_src, const double *Tfix, double *Eres_T) {
+                    double *E_src, const double *Tfix, double *Eres_T, const double *pw) {
   double *theta = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   double *Tn = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   if (!theta || !Tn) { free(theta); free(Tn); return -1000000; }
@@ -359,7 +382,8 @@ int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double
 #pragma omp parallel for schedule(static) reduction(+ : esrc_step)
     for (int64_t i = 0; i < n; ++i) {
       double F = 0.0;
-      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) F += oracle_pair_flux(theta[i], theta[col[p]]);
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        F += (pw ? pw[p] : 1.0) * oracle_pair_flux(theta[i], theta[col[p]]);
       double dTdt = Tmax * K * F;
       if (chi[i]) {
         dTdt -= cG * (T[i] - Tl[i]);
