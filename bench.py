@@ -141,6 +141,9 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
 
     s, p = workload(args.cells, args.tile_threads)
+    if args.rate_shell > 0:
+        # distance-weighted pair rates: the general single-precision kernel
+        p = dict(p, rate_shell_n=args.rate_shell)
     n = s.n
     tfix = None
     if args.border > 0:
@@ -256,9 +259,11 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
     ms_step = ms / args.steps
     value = job_value(ws, n, N_SUB, args.steps, ms)
     sub_launch_ms = statistics.mean(sub_ms) / N_SUB
-    achieved = B_ALG * n / (sub_launch_ms * 1e-3) / 1e9
+    # the weighted variant reads one 4-byte weight per pair on top
+    b_alg = B_ALG + (4 * N_NB if args.rate_shell > 0 else 0)
+    achieved = b_alg * n / (sub_launch_ms * 1e-3) / 1e9
     peak, kind = _peaks()
-    traffic = _traffic_from_profile(n)
+    traffic = _traffic_from_profile(n) if args.rate_shell == 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -267,14 +272,17 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                                                    "path": "plain"},
                                                   **({"border": "fixed 300 K electron shell %g A thick, %d atoms"
                                                       % (args.border, args.border_atoms)}
-                                                     if args.border > 0 else {}))),
+                                                     if args.border > 0 else {}),
+                                                  **({"pair_rates": "distance-weighted, S2/(%d r^2)" % args.rate_shell}
+                                                     if args.rate_shell > 0 else {}))),
         "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "substep_tile_kernel", "bytes_per_atom_substep": B_ALG,
+                     "kernel": "substep_tile_kernel" if args.rate_shell == 0 else "substep_f32_kernel (weighted)",
+                     "bytes_per_atom_substep": b_alg,
                      "peak_kind": kind, "substep_ms": sub_launch_ms},
         "clocks": clocks,
         "energy_drift": e["drift"],
@@ -698,6 +706,7 @@ def main():
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--border", type=float, default=0.0)
+    ap.add_argument("--rate-shell", type=int, default=0)
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)

@@ -70,6 +70,14 @@ extern "C" {
  *   seed            Philox4x32-10 key of the Langevin random force
  *   max_neighbors   width of the neighbour table (<= 0: 32, at most 64)
  *   use_graph       1: replay substep loops from a captured CUDA graph
+ *   rate_shell_n    0: every pair of the list exchanges at the rate K of Eq. Kij (paper);
+ *                   n > 0: pair (i, j) at the rate K w_ij, w_ij = S2 / (n r_ij^2) with
+ *                   S2 = zb2_A2 and r_ij the pair distance at the build: the weight
+ *                   b^2 / r^2 renormalised so that sum_j w_j r_j^2 over an ideal shell of
+ *                   n neighbours with second moment S2 stays S2 (the continuum
+ *                   conductivity is unchanged; no counterpart in the paper, where K_ij
+ *                   is one rate for all pairs).  Weighted contexts use the general
+ *                   single-precision or the FP64 substep kernel, not the row tiles
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after
  *                   tiles grow), 256 or 128 = fixed; both give identical results */
@@ -100,7 +108,8 @@ typedef struct ehc_params {
   int32_t max_neighbors;
   int32_t use_graph;
   int32_t tile_threads;
-  int32_t reserved[6];
+  int32_t rate_shell_n;
+  int32_t reserved[5];
 } ehc_params;
 
 /* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked
@@ -362,7 +371,9 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, const do
  * iteration approaches |lambda_max| from below. */
 int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, int32_t iters, double *x_out);
 /* The stages' flux-only prediction of one window from Tin_dev into Tout_dev
- * (caller order, device), with the training kernels. */
+ * (caller order, device), with the training kernels.  Training, prediction and
+ * the spectrum estimate take uniform pair rates only (EHC_E_INVAL with
+ * rate_shell_n > 0); windows of weighted contexts run as plain substeps. */
 int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, double *Tout_dev);
 /* Largest X such that |P(x)| <= 1 + 1e-5 on [0, X] for the current coefficients
  * (the window is stable for modes with tau_w lambda <= X), scanned on 200000

@@ -56,7 +56,7 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.tfix_orig, c.bnd_s, c.bnd_row, c.bnd_cnt, c.bnd_off, c.bnd_n, c.bnd_h, c.bnd_l, c.bnd_T,
+                 c.work, c.wgt, c.tfix_orig, c.bnd_s, c.bnd_row, c.bnd_cnt, c.bnd_off, c.bnd_n, c.bnd_h, c.bnd_l, c.bnd_T,
                  c.bnd_R, c.bnd_part};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -270,6 +270,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   if (p->flux_prec != 0 && p->flux_prec != 1) return EHC_E_INVAL;
   if (p->couple_mode != 0 && p->couple_mode != 1) return EHC_E_INVAL;
   if (p->laser_on && (!(p->laser_lp_A > 0) || !(p->laser_sigma_fs > 0))) return EHC_E_INVAL;
+  if (p->rate_shell_n < 0) return EHC_E_INVAL;
   int32_t W = p->max_neighbors <= 0 ? 32 : p->max_neighbors;
   if (W > kMaxWidth || W > 255) return EHC_E_INVAL;
   for (int t = 0; t < n_types; ++t)
@@ -334,6 +335,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.q_s, n));
   A(dalloc(&c.v_s, n));
   A(dalloc(&c.nbr, (size_t)W * n));
+  if (c.p.rate_shell_n > 0) A(dalloc(&c.wgt, (size_t)W * n));
   c.ps = (n + 3) / 4 * 4;
   A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * (size_t)(c.ps > 0 ? c.ps : 4)));
   A(dalloc(&c.dlo, n));
@@ -1042,7 +1044,8 @@ int ehc_batch_create(const ehc_params *p, int32_t n_rep, const int64_t *n_atoms_
                      const int32_t periodic[3], const double *mass_amu_host, void *stream, ehc_batch **out) {
   if (!p || n_rep <= 0 || !n_atoms_host || !boxes_host || !periodic || !mass_amu_host || !out) return EHC_E_INVAL;
   *out = nullptr;
-  if (p->laser_on || p->flux_prec != 0) return EHC_E_INVAL;   // batches use the single-precision path, no source
+  // batches use the row tiles: single precision, no source, uniform pair rates
+  if (p->laser_on || p->flux_prec != 0 || p->rate_shell_n != 0) return EHC_E_INVAL;
   ehc_batch *b = new (std::nothrow) ehc_batch();
   if (!b) return EHC_E_NOMEM;
   b->p = *p;
@@ -1713,7 +1716,7 @@ int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *hc, const double *nu_host, c
 int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
                         int32_t loss_power, float *loss_host, float *grad_host) {
   if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f) ||
-      (loss_power != 2 && loss_power != 4 && loss_power != 8))
+      (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0)
     return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1774,7 +1777,7 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const d
 }
 
 int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t iters, double *x_out) {
-  if (!w || !hc || hc->c.n != w->n || iters < 1 || iters > 100000) return EHC_E_INVAL;
+  if (!w || !hc || hc->c.n != w->n || iters < 1 || iters > 100000 || hc->c.p.rate_shell_n != 0) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
   if (c.n == 0) {
@@ -1807,7 +1810,8 @@ int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t i
 }
 
 int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, double *Tout_dev) {
-  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Tout_dev))) return EHC_E_INVAL;
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Tout_dev)) || hc->c.p.rate_shell_n != 0)
+    return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
   if (c.n == 0) return EHC_OK;
@@ -1861,7 +1865,7 @@ int ehc_nn_create(ehc_ctx *hc, int32_t hidden, int32_t n_window, double sigma, e
   if (!hc || !out || (hidden != 8 && hidden != 16) || n_window < 1 || !(sigma > 0)) return EHC_E_INVAL;
   *out = nullptr;
   Ctx &c = hc->c;
-  if (c.p.flux_prec != 0 || c.p.laser_on) return EHC_E_INVAL;
+  if (c.p.flux_prec != 0 || c.p.laser_on || c.p.rate_shell_n != 0) return EHC_E_INVAL;
   ehc_nn *nn = new (std::nothrow) ehc_nn();
   if (!nn) return EHC_E_NOMEM;
   nn->H = hidden;

@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
                                                        int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
                                                        int64_t ps, uint8_t *__restrict__ cnt,
                                                        int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
-                                                       int32_t *__restrict__ maxrow, int32_t *__restrict__ err) {
+                                                       int32_t *__restrict__ maxrow, int32_t *__restrict__ err,
+                                                       float *__restrict__ wgt, double wn) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 qi = q_s[s];
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+              if (wgt) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
             }
             ++m;
           }
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
+              if (wgt) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
             }
             ++m;
           }
@@ -589,9 +592,11 @@ cudaError_t launch_neighbors(Ctx &c) {
   bool fast = true;
   for (int k = 0; k < 3; ++k) fast = fast && (!c.g.per[k] || c.g.nc[k] >= 3);
   auto kern = fast ? neighbor_kernel<true> : neighbor_kernel<false>;
+  // pair weights S2 / (n_shell r^2) with r^2 = d2 2^-40 A^2 (d2 on the 2^-20 A grid)
+  const double wn = c.p.rate_shell_n > 0 ? c.p.zb2_A2 * 1099511627776.0 / (double)c.p.rate_shell_n : 0.0;
   kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
                                              reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt,
-                                             c.maxstaged, c.maxrow, c.err);
+                                             c.maxstaged, c.maxrow, c.err, c.wgt, wn);
   return cudaGetLastError();
 }
 

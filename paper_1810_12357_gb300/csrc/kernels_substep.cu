@@ -507,11 +507,12 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
 // general single-precision path: one thread per atom, int32 neighbour table,
 // neighbour values gathered from global memory (any row length)
 template <bool LASER>
+// wgt (if not null): pair weights w_ij [slot][atom] multiplying each pair term
 __global__ void __launch_bounds__(256) substep_f32_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const float *__restrict__ hin, float *__restrict__ hout, float *__restrict__ lo, double *__restrict__ A,
     const float *__restrict__ uTl, const float *__restrict__ srcw, const float *__restrict__ pulse_f, int k,
-    const StepCoef *__restrict__ cf, int32_t *__restrict__ err) {
+    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float th = cf->th_ref;
@@ -521,6 +522,12 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   float F = 0.0f;
   const int32_t *np = nbr + s;
   int j = 0;
+  if (wgt) {
+    const float *wp = wgt + s;
+    for (; j < c; ++j)
+      F = fmaf(__ldg(wp + (int64_t)j * n),
+               pair_acc<0>(0.0f, di, __ldg(hin + __ldg(np + (int64_t)j * n)), th, ai, m2ai), F);
+  }
   for (; j + 6 <= c; j += 6) {
     int32_t t[6];
     float dj[6];
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const double *__restrict__ Tin, double *__restrict__ Tout, double *__restrict__ A,
     const double *__restrict__ Tl, const double *__restrict__ srcw, const double *__restrict__ pulse,
-    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err) {
+    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double inv = cf->invTmax;
@@ -575,7 +582,8 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     const double a = lo ? ti : tj, b = lo ? tj : ti;
     const double E = exp(a - b);
     const double phi = b * (1.0 - a) * E - a * (1.0 - b) / E;
-    F += lo ? phi : -phi;
+    const double w = wgt ? (double)__ldg(wgt + (int64_t)j * n + s) : 1.0;
+    F += w * (lo ? phi : -phi);
   }
   double inc = cf->dtTK * F;
   const double tl = Tl[s];
@@ -599,7 +607,8 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // table holds at most 32 neighbours per atom
 bool tile_path(const Ctx &c) {
   const int w = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
-  return c.p.flux_prec == 0 && c.W <= 32 && c.nwork > 0 && c.staged_max <= c.tile_floats && c.tile_grid[w] > 0;
+  return c.p.flux_prec == 0 && c.p.rate_shell_n == 0 && c.W <= 32 && c.nwork > 0 &&
+         c.staged_max <= c.tile_floats && c.tile_grid[w] > 0;
 }
 
 cudaError_t launch_split(Ctx &c, cudaStream_t st) {
@@ -626,10 +635,10 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     double *Tout = c.T[parity ^ 1];
     if (laser)
       substep_f64_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                             c.pulse, k, c.coef, c.err);
+                                                             c.pulse, k, c.coef, c.err, c.wgt);
     else
       substep_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                              c.pulse, k, c.coef, c.err);
+                                                              c.pulse, k, c.coef, c.err, c.wgt);
   } else if (tile_path(c)) {
     const int32_t P = (c.n_max + 1) / 2;
     const int32_t tb = c.tile_floats;
@@ -654,11 +663,11 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   } else {
     if (laser)
       substep_f32_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity], c.dmir[parity ^ 1],
-                                                             c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef, c.err);
+                                                             c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
     else
       substep_f32_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity], c.dmir[parity ^ 1],
                                                               c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef,
-                                                              c.err);
+                                                              c.err, c.wgt);
   }
   // border atoms back to their fixed temperature, the change into their reservoirs
   if (c.has_border) {
