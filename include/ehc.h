@@ -179,9 +179,10 @@ int ehc_couple(ehc_ctx *c, double *v_dev, double dt_md_fs);
  * atoms (a border atom exchanges pair fluxes and coupling energy at its fixed
  * T), then border atoms are put back to their temperature; what they would have
  * gained, times V_atom C_e, is the reservoir energy E_res of ehc_energy, which
- * closes the ledger.  Set T_e of border atoms to Tfix in ehc_set_te: a
- * difference is otherwise charged to the reservoir at the first substep.  The
- * first call allocates 40 bytes per atom.  With a border, ehc_cheb_step and
+ * closes the ledger.  The build sets border atoms to their Tfix and charges a
+ * difference to the reservoir (set T_e of border atoms to Tfix in ehc_set_te to
+ * avoid one).  The
+ * first call allocates 17 bytes per atom.  With a border, ehc_cheb_step and
  * ehc_nn_step advance by plain substeps (counted as fallbacks) and ehc_save
  * returns EHC_E_STATE. */
 int ehc_set_border(ehc_ctx *c, const double *Tfix_dev);

@@ -56,8 +56,7 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.wgt, c.tfix_orig, c.bnd_s, c.bnd_row, c.bnd_cnt, c.bnd_off, c.bnd_n, c.bnd_h, c.bnd_l, c.bnd_T,
-                 c.bnd_R, c.bnd_part};
+                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -230,6 +229,8 @@ RepArgs rep_args(const Ctx &c) {
   ra.uTl = c.uTl;
   ra.srcw = c.srcw;
   ra.pulse_f = c.pulse_f;
+  ra.fix = c.has_border ? c.bmask : nullptr;
+  ra.res = c.bres;
   ra.rrange[0] = c.rrange[0];
   ra.rrange[1] = c.rrange[1];
   ra.cf = c.coef;
@@ -460,22 +461,13 @@ int ehc_set_border(ehc_ctx *h, const double *Tfix_dev) {
     bool ok = true;
     auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
     A(dalloc(&c.tfix_orig, n));
-    A(dalloc(&c.bnd_s, n));
-    A(dalloc(&c.bnd_row, n));
-    A(dalloc(&c.bnd_h, n));
-    A(dalloc(&c.bnd_l, n));
-    A(dalloc(&c.bnd_T, n));
-    A(dalloc(&c.bnd_R, n));
-    A(dalloc(&c.bnd_cnt, (int64_t)border_blocks(n)));
-    A(dalloc(&c.bnd_off, (int64_t)border_blocks(n)));
+    A(dalloc(&c.bmask, n));
+    A(dalloc(&c.bres, n));
     A(dalloc(&c.bnd_part, (int64_t)border_red_blocks()));
-    A(dalloc(&c.bnd_n, 1));
-    if (ok) A(cudaMemsetAsync(c.bnd_n, 0, sizeof(int32_t), c.stream));
+    if (ok) A(cudaMemsetAsync(c.bres, 0, sizeof(double) * n, c.stream));
     if (!ok) {
       cudaGetLastError();
-      for (void **q : {(void **)&c.tfix_orig, (void **)&c.bnd_s, (void **)&c.bnd_row, (void **)&c.bnd_h, (void **)&c.bnd_l,
-                       (void **)&c.bnd_T, (void **)&c.bnd_R, (void **)&c.bnd_cnt, (void **)&c.bnd_off,
-                       (void **)&c.bnd_part, (void **)&c.bnd_n}) {
+      for (void **q : {(void **)&c.tfix_orig, (void **)&c.bmask, (void **)&c.bres, (void **)&c.bnd_part}) {
         if (*q) cudaFree(*q);
         *q = nullptr;
       }
@@ -511,19 +503,14 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t 
   int r0 = ensure_t(c);
   if (r0) return r0;
   c.ff_valid = false;
+  // the reservoirs of the closing MD step into scal[10], cleared, before the re-sort
+  if (c.bres) CK(border_flush(c, c.scal + 10, true));
   CK(launch_bin(c, x_dev));
   CK(launch_sort_cells(c));
   // with velocities still in flight the gather leaves them to a second pass after
   // the neighbour search
   CK(launch_gather(c, v_ready ? nullptr : v_dev, c.te_orig_order));
   c.te_orig_order = false;
-  if (c.bnd_n) {
-    // the reservoirs of the previous MD step's list (kelvin) go to scal[10]; then
-    // the list of the new sort order, or none
-    CK(border_sum(c, c.scal + 10));
-    if (c.border_next) CK(border_build(c));
-    else CK(cudaMemsetAsync(c.bnd_n, 0, sizeof(int32_t), c.stream));
-  }
   c.has_border = c.border_next;
   CK(launch_neighbors(c));
   if (v_ready) {
@@ -532,6 +519,9 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t 
   }
   CK(launch_lattice_temperature(c));
   CK(launch_globals(c));
+  // border of the new sort order: after the means, so that the closing step's
+  // ledger sees the temperatures before border atoms are set to T_b
+  if (c.has_border) CK(border_apply(c));
   CK(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c.stream));
   return EHC_OK;
@@ -565,7 +555,7 @@ int build_finish(Ctx &c, bool own_tiles) {
   if (c.VC_prev > 0) {
     c.E_base += c.VC_prev * (sumT - c.ST_base);
     c.ST_base = sumT;
-    if (c.bnd_n) c.E_res += c.VC_prev * c.scal_host[10];
+    if (c.bres) c.E_res += c.VC_prev * c.scal_host[10] * (c.p.flux_prec == 1 ? 1.0 : c.p.Tmax_K);
   }
   const double N = (double)(c.n > 0 ? c.n : 1);
   // system means (Sec. 2): mean electronic temperature, classical T_lat = K / ((3/2) k_B N)
@@ -743,7 +733,7 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   int r0 = ensure_t(c);
   if (r0) return r0;
   CK(launch_ledger(c));
-  if (c.bnd_n) CK(border_sum(c, c.scal + 11));
+  if (c.bres) CK(border_flush(c, c.scal + 11, false));
   int r = readback(c);
   if (r) return r;
   const double sumT = c.scal_host[0];
@@ -753,7 +743,9 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   out->E_src = c.E_src;
   out->E_e0 = c.E_e0;
   // the border's reservoirs: closed MD steps, and the current one with its C_e
-  out->E_res = c.E_res + (c.bnd_n && c.VC_prev > 0 ? c.VC_prev * c.scal_host[11] : 0.0);
+  out->E_res = c.E_res + (c.bres && c.VC_prev > 0
+                               ? c.VC_prev * c.scal_host[11] * (c.p.flux_prec == 1 ? 1.0 : c.p.Tmax_K)
+                               : 0.0);
   const double scale = std::max(std::fabs(c.E_e0), std::fabs(out->E_e));
   out->drift = scale > 0 ? (out->E_e + out->E_lat - out->E_src + out->E_res - out->E_e0) / scale : 0.0;
   out->sum_T = sumT;

@@ -108,6 +108,8 @@ struct RepArgs {
   float *rrange[2];
   const StepCoef *cf;
   int32_t *err;
+  const uint8_t *fix;   // border mask (null: no border)
+  double *res;          // border reservoirs (delta units)
 };
 
 // Arguments of a Chebyshev-window stage launch of the row-tile kernel.  The
@@ -210,11 +212,9 @@ cudaError_t nn_residual(Ctx &c, const float *d0, const float *d1, const double *
 cudaError_t nn_couple_window(Ctx &c, const double *T0, double *T1, float *d1, double *dTc, int n_w);
 cudaError_t nn_accept(Ctx &c, const double *dTc);
 // kernels_border.cu (fixed-temperature border)
-int border_blocks(int64_t n);
 int border_red_blocks();
-cudaError_t border_build(Ctx &c);                 // the list of the current sort order
-cudaError_t border_sum(Ctx &c, double *out);       // sum of the list's reservoirs [K] into *out (device)
-cudaError_t border_fix(Ctx &c, int parity, bool tile, cudaStream_t st);   // after substep of parity
+cudaError_t border_flush(Ctx &c, double *out, bool clear);   // sum of the reservoirs into *out (device)
+cudaError_t border_apply(Ctx &c);                            // mask of the current sort order, T to T_b
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);
@@ -322,13 +322,13 @@ struct Ctx {
 
   // captured substep loops, keyed by everything a launch bakes in
   // fixed-temperature border: tfix_orig (caller order, NaN = free) set by
-  // ehc_set_border takes effect at the next build (border_next); the build
-  // turns it into the sorted list bnd_* of bnd_n entries (device count)
+  // ehc_set_border takes effect at the next build (border_next), which makes
+  // the sorted mask bmask; bres holds the reservoirs (delta units on the
+  // single-precision paths, kelvin on the FP64 path), bnd_part sum partials
   double *tfix_orig = nullptr;
   bool border_next = false, has_border = false;
-  int32_t *bnd_s = nullptr, *bnd_row = nullptr, *bnd_cnt = nullptr, *bnd_off = nullptr, *bnd_n = nullptr;
-  float *bnd_h = nullptr, *bnd_l = nullptr;
-  double *bnd_T = nullptr, *bnd_R = nullptr, *bnd_part = nullptr;
+  uint8_t *bmask = nullptr;
+  double *bres = nullptr, *bnd_part = nullptr;
   double E_res = 0.0;   // energy the border absorbed in closed MD steps [eV]
   struct GraphEntry {
     int n_sub, parity, tcur, abuf, path, pairs, tile, nt, border;

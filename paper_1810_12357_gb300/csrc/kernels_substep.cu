@@ -127,6 +127,8 @@ struct OutPtrs {
   double *A;
   const float *srcw, *pulse_f;
   int32_t *err;
+  const uint8_t *fix;   // border mask (null: none)
+  double *res;          // border reservoirs (delta units)
 };
 
 // state update of one atom (single-precision path); Ai is the atom's exchanged
@@ -149,6 +151,12 @@ __device__ __forceinline__ float update_atom(int64_t s, float di, float li, floa
     const float e = fmaf(c, w, -p);      // p + e == c * w exactly
     ff_add(h, l, p);
     ff_add(h, l, e);
+  }
+  if (o.fix && o.fix[s]) {
+    // border atom: its value stays, the change it would have made goes to its reservoir
+    o.res[s] += ((double)h - (double)di) + ((double)l - (double)li);
+    h = di;
+    l = li;
   }
   o.hout[s] = h;
   o.lo[s] = l;
@@ -310,7 +318,7 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
     if (sa.Fout) sa.Fout[s] = F;
     return h;
   }
-  const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err};
+  const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err, ra.fix, ra.res};
   return update_atom<LASER>(s, di, li, ui, Ai, F, load_coef(cf), o, k);
 }
 
@@ -512,7 +520,8 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const float *__restrict__ hin, float *__restrict__ hout, float *__restrict__ lo, double *__restrict__ A,
     const float *__restrict__ uTl, const float *__restrict__ srcw, const float *__restrict__ pulse_f, int k,
-    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
+    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt,
+    const uint8_t *__restrict__ fix, double *__restrict__ res) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float th = cf->th_ref;
@@ -539,7 +548,7 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
     for (int u = 0; u < 6; ++u) F = pair_acc<0>(F, di, dj[u], th, ai, m2ai);
   }
   for (; j < c; ++j) F = pair_acc<0>(F, di, __ldg(hin + __ldg(np + (int64_t)j * n)), th, ai, m2ai);
-  const OutPtrs o = {hout, lo, A, srcw, pulse_f, err};
+  const OutPtrs o = {hout, lo, A, srcw, pulse_f, err, fix, res};
   update_atom<LASER>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k);
 }
 
@@ -567,7 +576,8 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const double *__restrict__ Tin, double *__restrict__ Tout, double *__restrict__ A,
     const double *__restrict__ Tl, const double *__restrict__ srcw, const double *__restrict__ pulse,
-    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
+    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt,
+    const uint8_t *__restrict__ fix, double *__restrict__ res) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double inv = cf->invTmax;
@@ -593,7 +603,12 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     A[s] += cf->dtVG * d;
   }
   if (LASER) inc += cf->dt * pulse[k] * srcw[s];
-  const double To = Ti + inc;
+  double To = Ti + inc;
+  if (fix && fix[s]) {
+    // border atom: its temperature stays, the change goes to its reservoir (kelvin)
+    res[s] += To - Ti;
+    To = Ti;
+  }
   Tout[s] = To;
   const double th = To * inv;
   if (!(th >= 0.0 && th <= 1.0)) atomicOr(err, ERR_RANGE);
@@ -635,10 +650,10 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     double *Tout = c.T[parity ^ 1];
     if (laser)
       substep_f64_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                             c.pulse, k, c.coef, c.err, c.wgt);
+                                                             c.pulse, k, c.coef, c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
     else
       substep_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                              c.pulse, k, c.coef, c.err, c.wgt);
+                                                              c.pulse, k, c.coef, c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
   } else if (tile_path(c)) {
     const int32_t P = (c.n_max + 1) / 2;
     const int32_t tb = c.tile_floats;
@@ -663,17 +678,11 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   } else {
     if (laser)
       substep_f32_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity], c.dmir[parity ^ 1],
-                                                             c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
+                                                             c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
     else
       substep_f32_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity], c.dmir[parity ^ 1],
                                                               c.dlo, c.A, c.uTl, c.srcw, c.pulse_f, k, c.coef,
-                                                              c.err, c.wgt);
-  }
-  // border atoms back to their fixed temperature, the change into their reservoirs
-  if (c.has_border) {
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return border_fix(c, parity, c.p.flux_prec == 0 && tile_path(c), st);
+                                                              c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
   }
   return cudaGetLastError();
 }
