@@ -40,9 +40,13 @@ DT_MD = N_SUB * DT_SUB # fs, the lattice advances the same time as the electrons
 N_NB = 18              # neighbours per atom in FCC Cu at r_c = 4.0 A
 B_ALG = 4 * N_NB + 44  # algorithmic bytes per atom-substep of the substep kernel
 # kernels launched per MD step: bin + 3-phase scan + scatter + cell sort + gather
-# + neighbour list + lattice temperature + 2 reduction kernels = 11; N_SUB substeps;
-# hand-over + 2 reduction kernels = 3; drift = 1
-LAUNCHES_PER_STEP = 11 + N_SUB + 3 + 1
+# + neighbour list + lattice temperature + 2 reduction kernels = 11; the float-pair
+# split before the first substep and the merge at the next build = 2; N_SUB
+# substeps; hand-over + 2 reduction kernels = 3; drift = 1 (117, as an ncu launch
+# list of the track counts); a border adds its mask kernel and the two
+# reservoir-sum kernels per build
+LAUNCHES_PER_STEP = 11 + 2 + N_SUB + 3 + 1
+BORDER_LAUNCHES_PER_STEP = 3
 
 
 def _dist():
@@ -278,7 +282,7 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "substep_tile_kernel" if args.rate_shell == 0 else "substep_f32_kernel (weighted)",
@@ -437,8 +441,8 @@ def run_window(args, coeffs=None, learned_info=None):
     (build, 100 substeps' worth of electron evolution, hand-over, drift) advances
     the electrons by windows of n_w substeps, each with `stages` flux evaluations,
     the a-posteriori residual test and the fallback to plain substeps; the same
-    run with plain substeps from the same state is the reference and the judge
-    of the error."""
+    run with plain substeps from the same state is the reference that measures
+    the error."""
     import torch
     from paper_1810_12357_gb300 import Ehc, EhcCheb
     s, p = workload(args.cells)
