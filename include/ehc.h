@@ -44,6 +44,8 @@ extern "C" {
 #define EHC_E_TIMEOUT (-7)      /* a bounded device wait gave up */
 #define EHC_E_STATE (-8)        /* call order violated (e.g. substep before build) */
 #define EHC_E_BOUNDS (-9)       /* atom outside the extent of a non-periodic axis */
+#define EHC_E_INDEX (-10)       /* a gathered index outside its table (found only by
+                                   the bounds-checked build, libehc_checked.so) */
 
 /* Parameters of one system.  Paper references:
  *   Tmax_K          T^e_max of the normalisation theta = T/T_max, T_min = 0 (Sec. 2)

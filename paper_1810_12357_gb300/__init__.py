@@ -125,10 +125,13 @@ _lib = None
 
 
 def load_library(path: str | None = None):
-    """Load libehc.so (raises if it has not been built: no fallback exists)."""
+    """Load libehc.so (raises if it has not been built: no fallback exists).
+    With EHC_CHECKED=1 in the environment the bounds-checked build
+    libehc_checked.so is loaded instead (build.build(checked=True) makes it)."""
     global _lib
     if _lib is None:
-        p = path or LIB_PATH
+        p = path or (os.path.join(os.path.dirname(LIB_PATH), "libehc_checked.so")
+                     if os.environ.get("EHC_CHECKED") == "1" else LIB_PATH)
         if not os.path.exists(p):
             raise RuntimeError(f"libehc.so not built ({p}); run __graft_entry__.build()")
         L = ctypes.CDLL(p)

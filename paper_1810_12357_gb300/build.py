@@ -2,6 +2,9 @@
 
 Each translation unit in csrc/ is compiled by nvcc in parallel, then linked
 into paper_1810_12357_gb300/libehc.so.  The object files go to _build/.
+build(checked=True) makes libehc_checked.so instead: the same sources with
+-DEHC_CHECKED, where every gathered neighbour and tile index is bounds-checked
+(an index outside its table sets an error bit, EHC_E_INDEX, and is not used).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "ehc")
 LIB = os.path.join(HERE, "libehc.so")
+LIB_CHECKED = os.path.join(HERE, "libehc_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -33,23 +37,27 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale(extra: list[str]) -> bool:
-    if not os.path.exists(LIB):
+def _stale(extra: list[str], lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     return any(os.path.getmtime(d) > t for d in deps + extra)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          checked: bool = False) -> str:
     extra_flags = list(extra_flags or [])
-    if not force and not _stale([__file__]):
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    lib, obj_dir = (LIB_CHECKED, OBJ + "_checked") if checked else (LIB, OBJ)
+    if checked:
+        extra_flags.append("-DEHC_CHECKED")
+    if not force and not _stale([__file__], lib):
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     nv = nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         cmd = [nv, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -60,13 +68,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nv, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -12,7 +12,18 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ehc_internal.cuh"
+
+// an NVTX range over one library call (named in profiler timelines; next to free
+// when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 using namespace ehc;
 
@@ -41,6 +52,7 @@ cudaError_t dalloc(T **p, size_t count) {
 }
 
 int err_code(int32_t bits) {
+  if (bits & ERR_INDEX) return EHC_E_INDEX;
   if (bits & ERR_BOUNDS) return EHC_E_BOUNDS;
   if (bits & ERR_NBR_OVERFLOW) return EHC_E_NBR_OVERFLOW;
   if (bits & (ERR_RANGE | ERR_SPEED)) return EHC_E_RANGE;
@@ -254,6 +266,7 @@ const char *ehc_strerror(int code) {
     case EHC_E_TIMEOUT: return "bounded device wait timed out";
     case EHC_E_STATE: return "call out of order";
     case EHC_E_BOUNDS: return "atom outside a non-periodic box extent";
+    case EHC_E_INDEX: return "gathered index outside its table (bounds-checked build)";
     default: return "unknown error";
   }
 }
@@ -423,6 +436,7 @@ void ehc_destroy(ehc_ctx *h) {
 }
 
 int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
+  NvtxRange nvtx_range("ehc_set_te");
   if (!h || (!Te_dev && h->c.n > 0)) return EHC_E_INVAL;
   Ctx &c = h->c;
   c.t_version += 1;
@@ -601,6 +615,7 @@ int build_finish(Ctx &c, bool own_tiles) {
 extern "C" {
 
 int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
+  NvtxRange nvtx_range("ehc_build_neighbors");
   if (!h) return EHC_E_INVAL;
   Ctx &c = h->c;
   int r = build_enqueue(c, x_dev, v_dev);
@@ -641,6 +656,7 @@ int tune_width(cudaStream_t st, int32_t *nt_out, Launch launch) {
 extern "C" {
 
 int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
+  NvtxRange nvtx_range("ehc_substep");
   if (!h || n_sub < 0) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.built) return EHC_E_STATE;
@@ -696,6 +712,7 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
 }
 
 int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
+  NvtxRange nvtx_range("ehc_couple");
   if (!h) return EHC_E_INVAL;
   Ctx &c = h->c;
   c.t_version += 1;
@@ -710,6 +727,7 @@ int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
 }
 
 int ehc_drift(ehc_ctx *h, double *x_dev, const double *v_dev, double dt_fs) {
+  NvtxRange nvtx_range("ehc_drift");
   if (!h || (h->c.n > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
   CK(launch_drift(h->c, x_dev, v_dev, dt_fs));
   return EHC_OK;
@@ -727,6 +745,7 @@ int ehc_sync(ehc_ctx *h) {
 }
 
 int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
+  NvtxRange nvtx_range("ehc_energy");
   if (!h || !out) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.have_te) return EHC_E_STATE;
@@ -814,6 +833,7 @@ int ehc_export_neighbors(ehc_ctx *h, int64_t *rowptr, int32_t *col, int64_t cap)
 
 int ehc_md_step_host(ehc_ctx *h, double *x_host, double *v_host, int32_t n_sub, double t_fs, double dt_md_fs,
                      double *Te_host_out) {
+  NvtxRange nvtx_range("ehc_md_step_host");
   if (!h || (h->c.n > 0 && (!x_host || !v_host || !Te_host_out))) return EHC_E_INVAL;
   Ctx &c = h->c;
   const size_t b3 = sizeof(double) * 3 * (size_t)c.n;
@@ -881,6 +901,7 @@ struct CkptHeader {
 }  // namespace
 
 int ehc_save(ehc_ctx *h, const char *path) {
+  NvtxRange nvtx_range("ehc_save");
   if (!h || !path) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.have_te || c.has_border || c.border_next) return EHC_E_STATE;
@@ -921,6 +942,7 @@ int ehc_save(ehc_ctx *h, const char *path) {
 }
 
 int ehc_load(ehc_ctx *h, const char *path) {
+  NvtxRange nvtx_range("ehc_load");
   if (!h || !path) return EHC_E_INVAL;
   Ctx &c = h->c;
   c.t_version += 1;
@@ -1121,6 +1143,7 @@ int ehc_batch_set_te(ehc_batch *b, const double *Te_dev) {
 }
 
 int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v_dev) {
+  NvtxRange nvtx_range("ehc_batch_build_neighbors");
   if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
   CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
@@ -1157,6 +1180,7 @@ int ehc_batch_build_neighbors(ehc_batch *b, const double *x_dev, const double *v
 }
 
 int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
+  NvtxRange nvtx_range("ehc_batch_substep");
   if (!b || n_sub < 0) return EHC_E_INVAL;
   for (auto *h : b->rep) {
     if (!h->c.built) return EHC_E_STATE;
@@ -1233,6 +1257,7 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
 }
 
 int ehc_batch_couple(ehc_batch *b, double *v_dev, double dt_md_fs) {
+  NvtxRange nvtx_range("ehc_batch_couple");
   if (!b || (b->n_total > 0 && !v_dev)) return EHC_E_INVAL;
   CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
@@ -1244,6 +1269,7 @@ int ehc_batch_couple(ehc_batch *b, double *v_dev, double dt_md_fs) {
 }
 
 int ehc_batch_drift(ehc_batch *b, double *x_dev, const double *v_dev, double dt_fs) {
+  NvtxRange nvtx_range("ehc_batch_drift");
   if (!b || (b->n_total > 0 && (!x_dev || !v_dev))) return EHC_E_INVAL;
   CK(batch_fork(*b));
   for (size_t r = 0; r < b->rep.size(); ++r) {
@@ -1559,6 +1585,7 @@ int ehc_cheb_coefficients(const ehc_cheb *w, double *nu_out, double *mut_out, do
 }
 
 int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_back, double *rho_out) {
+  NvtxRange nvtx_range("ehc_cheb_step");
   if (!w || !hc || hc->c.n != w->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1707,6 +1734,7 @@ int ehc_cheb_set_coefficients(ehc_cheb *w, ehc_ctx *hc, const double *nu_host, c
 
 int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
                         int32_t loss_power, float *loss_host, float *grad_host) {
+  NvtxRange nvtx_range("ehc_cheb_train_step");
   if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f) ||
       (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0)
     return EHC_E_INVAL;
@@ -1934,6 +1962,7 @@ int ehc_nn_get_params(ehc_nn *nn, ehc_ctx *hc, float *params_host) {
 
 int ehc_nn_train_step(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, float lr,
                       float *loss_host, float *grad_host) {
+  NvtxRange nvtx_range("ehc_nn_train_step");
   if (!nn || !hc || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || hc->c.n != nn->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1964,6 +1993,7 @@ int ehc_nn_predict(ehc_nn *nn, ehc_ctx *hc, const double *Tin_dev, double *Tout_
 }
 
 int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_back, double *rho_out) {
+  NvtxRange nvtx_range("ehc_nn_step");
   if (!nn || !hc || hc->c.n != nn->n) return EHC_E_INVAL;
   Ctx &c = hc->c;
   c.t_version += 1;

@@ -34,7 +34,24 @@ enum DevErr : int32_t {
   ERR_TIMEOUT = 8,       // bounded wait gave up
   ERR_NEG_KE = 16,       // (informational) kinetic energy could not pay A_i
   ERR_SPEED = 32,        // a velocity component outside the fixed-point range (|v| >= 256 A/fs or NaN)
+  ERR_INDEX = 64,        // (EHC_CHECKED builds) a gathered index outside its table
 };
+
+// Builds with -DEHC_CHECKED bounds-check every gathered neighbour and tile index:
+// an index outside [0, bound) sets ERR_INDEX in the device error word and is
+// replaced by 0, so the access stays in bounds (no trap).  Otherwise a no-op.
+__device__ __forceinline__ uint32_t checked_index(uint32_t i, uint32_t bound, int32_t *err) {
+#ifdef EHC_CHECKED
+  if (i >= bound) {
+    atomicOr(err, ERR_INDEX);
+    return 0u;
+  }
+#else
+  (void)bound;
+  (void)err;
+#endif
+  return i;
+}
 
 // Sorted velocity of one atom: components on a fixed-point grid of 2^-48 A/fs
 // (|v| < 256 A/fs, so sums over an atom and up to 64 neighbours stay exact in
@@ -109,7 +126,7 @@ struct RepArgs {
   const StepCoef *cf;
   int32_t *err;
   const uint8_t *fix;   // border mask (null: no border)
-  double *res;          // border reservoirs (delta units)
+  double *res;          // border reservoirs (single-precision paths: a float pair per atom, delta units)
 };
 
 // Arguments of a Chebyshev-window stage launch of the row-tile kernel.  The
@@ -323,8 +340,9 @@ struct Ctx {
   // captured substep loops, keyed by everything a launch bakes in
   // fixed-temperature border: tfix_orig (caller order, NaN = free) set by
   // ehc_set_border takes effect at the next build (border_next), which makes
-  // the sorted mask bmask; bres holds the reservoirs (delta units on the
-  // single-precision paths, kelvin on the FP64 path), bnd_part sum partials
+  // the sorted mask bmask; bres holds the reservoirs, 8 bytes per atom: a float
+  // pair in delta units on the single-precision paths, a double in kelvin on the
+  // FP64 path; bnd_part sum partials
   double *tfix_orig = nullptr;
   bool border_next = false, has_border = false;
   uint8_t *bmask = nullptr;

@@ -217,7 +217,7 @@ __device__ __forceinline__ uint32_t wrap_shift(int32_t dcell, int64_t L) {
   return dcell > 1 ? (uint32_t)(-L) : (dcell < -1 ? (uint32_t)L : 0u);
 }
 
-template <bool FAST>
+template <bool FAST, bool WEIGHTS>
 __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
                                                        const int32_t *__restrict__ start,
                                                        const int32_t *__restrict__ row_nbr, int32_t W,
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (wgt) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
+              if (WEIGHTS) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
             }
             ++m;
           }
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (wgt) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
+              if (WEIGHTS) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
             }
             ++m;
           }
@@ -380,7 +380,8 @@ template <bool ONE_TYPE>
 __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
                                     const VelQ *__restrict__ v_s, const int8_t *__restrict__ type_s,
                                     MassTable mt, RecipTab rt, int dof_mode, double eps_ke, double Tref,
-                                    double *__restrict__ Tl_d, float *__restrict__ Tl_f, float *__restrict__ uTl) {
+                                    double *__restrict__ Tl_d, float *__restrict__ Tl_f, float *__restrict__ uTl,
+                                    int32_t *__restrict__ err) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int c = cnt[s];
@@ -390,7 +391,7 @@ __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, 
     long long qx = vi.x, qy = vi.y, qz = vi.z;
     double sw = vi.w;
     for (int k = 0; k < c; ++k) {
-      const VelQ vj = v_s[nbr[(int64_t)k * n + s]];
+      const VelQ vj = v_s[checked_index(nbr[(int64_t)k * n + s], (uint32_t)n, err)];
       qx += vj.x;
       qy += vj.y;
       qz += vj.z;
@@ -406,7 +407,7 @@ __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, 
     double pz = mi * ((double)vi.z * kVelUnit);
     double W = mi * vi.w;
     for (int k = 0; k < c; ++k) {
-      const int32_t t = nbr[(int64_t)k * n + s];
+      const int32_t t = checked_index(nbr[(int64_t)k * n + s], (uint32_t)n, err);
       const VelQ vj = v_s[t];
       const double mj = mt.m[type_s[t]];
       M += mj;
@@ -591,7 +592,9 @@ cudaError_t launch_neighbors(Ctx &c) {
   if (c.n == 0) return cudaGetLastError();
   bool fast = true;
   for (int k = 0; k < 3; ++k) fast = fast && (!c.g.per[k] || c.g.nc[k] >= 3);
-  auto kern = fast ? neighbor_kernel<true> : neighbor_kernel<false>;
+  // the weighted forms store each pair's rate weight beside its index
+  auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
+                    : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);
   // pair weights S2 / (n_shell r^2) with r^2 = d2 2^-40 A^2 (d2 on the 2^-20 A grid)
   const double wn = c.p.rate_shell_n > 0 ? c.p.zb2_A2 * 1099511627776.0 / (double)c.p.rate_shell_n : 0.0;
   kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
@@ -610,11 +613,11 @@ cudaError_t launch_lattice_temperature(Ctx &c) {
   if (c.mt.n_types == 1)
     lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,
                                                                     c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
-                                                                    c.Tl_d, c.Tl_f, c.uTl);
+                                                                    c.Tl_d, c.Tl_f, c.uTl, c.err);
   else
     lattice_temp_kernel<false><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,
                                                                      c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,
-                                                                     c.Tl_d, c.Tl_f, c.uTl);
+                                                                     c.Tl_d, c.Tl_f, c.uTl, c.err);
   return cudaGetLastError();
 }
 

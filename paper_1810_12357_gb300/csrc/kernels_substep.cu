@@ -128,14 +128,16 @@ struct OutPtrs {
   const float *srcw, *pulse_f;
   int32_t *err;
   const uint8_t *fix;   // border mask (null: none)
-  double *res;          // border reservoirs (delta units)
+  float2 *res;          // border reservoirs: float pairs in delta units
 };
 
 // state update of one atom (single-precision path); Ai is the atom's exchanged
 // energy before this substep; returns the new hi
-template <bool LASER>
+// BORDER: a border atom (fixed, the mask value its caller loaded with the other
+// per-atom inputs) keeps its value, its change goes to o.res
+template <bool LASER, bool BORDER>
 __device__ __forceinline__ float update_atom(int64_t s, float di, float li, float ui, double Ai, float F,
-                                             const CoefF &cf, const OutPtrs &o, int k) {
+                                             const CoefF &cf, const OutPtrs &o, int k, bool fixed = false) {
   float inc = cf.dtK * F;
   const bool chi = (ui == ui);
   float d = 0.0f;
@@ -145,16 +147,25 @@ __device__ __forceinline__ float update_atom(int64_t s, float di, float li, floa
   }
   float h = di, l = li;
   ff_add(h, l, inc);
+  float p = 0.0f, e = 0.0f;
   if (LASER) {
     const float c = o.pulse_f[k], w = o.srcw[s];
-    const float p = c * w;
-    const float e = fmaf(c, w, -p);      // p + e == c * w exactly
+    p = c * w;
+    e = fmaf(c, w, -p);                  // p + e == c * w exactly
     ff_add(h, l, p);
     ff_add(h, l, e);
   }
-  if (o.fix && o.fix[s]) {
-    // border atom: its value stays, the change it would have made goes to its reservoir
-    o.res[s] += ((double)h - (double)di) + ((double)l - (double)li);
+  if (BORDER && fixed) {
+    // border atom: its value stays; the change it would have made, the increments
+    // just added to the float pair, goes to its float-pair reservoir (single-
+    // precision arithmetic only, as exact as the state)
+    float2 r = o.res[s];
+    ff_add(r.x, r.y, inc);
+    if (LASER) {
+      ff_add(r.x, r.y, p);
+      ff_add(r.x, r.y, e);
+    }
+    o.res[s] = r;
     h = di;
     l = li;
   }
@@ -293,10 +304,11 @@ struct StageIn {
   float zm1, zm2, y0, F0;
 };
 
-template <int TIER, bool LASER, int PP, bool STAGE>
+template <int TIER, bool LASER, int PP, bool STAGE, bool BORDER>
 __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, const StageArgs &sa, int parity,
-                                          int k, const float *tile, int32_t s, float di, const uint32_t *pv,
-                                          float ui, float li, double Ai, const StageIn &si) {
+                                          int k, const float *tile, uint32_t tlen, int32_t s, float di,
+                                          const uint32_t *pv, float ui, float li, double Ai, const StageIn &si,
+                                          bool fixed) {
   const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
@@ -304,8 +316,8 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
 #pragma unroll
   for (int m = 0; m < PP; ++m)
     if (PP != 16 || m < ra.P) {
-      F = pair_acc<TIER>(F, di, tile[pv[m] & 0xffffu], th, ai, m2ai);
-      F = pair_acc<TIER>(F, di, tile[pv[m] >> 16], th, ai, m2ai);
+      F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai);
+      F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai);
     }
   if (STAGE) {
     // Chebyshev stage on the window's change: z_j = z_{j-1} + nu (z_{j-2} - z_{j-1})
@@ -318,8 +330,9 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
     if (sa.Fout) sa.Fout[s] = F;
     return h;
   }
-  const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err, ra.fix, ra.res};
-  return update_atom<LASER>(s, di, li, ui, Ai, F, load_coef(cf), o, k);
+  const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err, ra.fix,
+                     reinterpret_cast<float2 *>(ra.res)};
+  return update_atom<LASER, BORDER>(s, di, li, ui, Ai, F, load_coef(cf), o, k, fixed);
 }
 
 constexpr int kTileBufs = 2;   // tiles in flight per CTA
@@ -370,7 +383,7 @@ __device__ __forceinline__ void close_item(TilePipe<NT> &sp, int it, int parity,
 // (pair flux of the tile values sa.yin, stage update into sa.yout, optionally
 // the flux itself into sa.Fout); rows and tiers as for substeps.
 // NT: threads that own atoms (256, or 128 for short rows); one producer warp more.
-template <bool LASER, int PP, bool STAGE, int NT>
+template <bool LASER, int PP, bool STAGE, int NT, bool BORDER = false>
 __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTileMinBlocks)
     substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
                         int parity, int k, StageArgs sa) {
@@ -476,6 +489,7 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
       const float di = tile[sb + q];
       float ui = 0.0f, li = 0.0f;
       double Ai = 0.0;
+      bool fixed = false;
       StageIn si = {0.0f, 0.0f, 0.0f, 0.0f};
       if (STAGE) {
         si.y0 = sa.y0[s];
@@ -486,16 +500,17 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
         ui = D.ra.uTl[s];
         li = D.ra.lo[s];
         Ai = D.ra.A[s];
+        if (BORDER) fixed = D.ra.fix[s] != 0;
       }
       float h;
-      if (tier == 3) h = row_atom<3, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
-                                                              si);
-      else if (tier == 2) h = row_atom<2, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
-                                                                   si);
-      else if (tier == 1) h = row_atom<1, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
-                                                                   si);
-      else h = row_atom<0, LASER, PP, STAGE>(D.ra, &D.cf, sa, parity, k, tile, s, di, pv, ui, li, Ai,
-                                                    si);
+      if (tier == 3) h = row_atom<3, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
+                                                              si, fixed);
+      else if (tier == 2) h = row_atom<2, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
+                                                                   si, fixed);
+      else if (tier == 1) h = row_atom<1, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
+                                                                   si, fixed);
+      else h = row_atom<0, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
+                                                    si, fixed);
       vmin = fminf(vmin, h);
       vmax = fmaxf(vmax, h);
     }
@@ -527,6 +542,7 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   const float th = cf->th_ref;
   const int c = cnt[s];
   const float di = hin[s];
+  const bool fixed = fix && fix[s];
   const float ai = th + di, m2ai = -2.0f * ai;
   float F = 0.0f;
   const int32_t *np = nbr + s;
@@ -535,21 +551,23 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
     const float *wp = wgt + s;
     for (; j < c; ++j)
       F = fmaf(__ldg(wp + (int64_t)j * n),
-               pair_acc<0>(0.0f, di, __ldg(hin + __ldg(np + (int64_t)j * n)), th, ai, m2ai), F);
+               pair_acc<0>(0.0f, di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai),
+               F);
   }
   for (; j + 6 <= c; j += 6) {
     int32_t t[6];
     float dj[6];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) t[u] = __ldg(np + (int64_t)(j + u) * n);
+    for (int u = 0; u < 6; ++u) t[u] = checked_index(__ldg(np + (int64_t)(j + u) * n), n, err);
 #pragma unroll
     for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
 #pragma unroll
     for (int u = 0; u < 6; ++u) F = pair_acc<0>(F, di, dj[u], th, ai, m2ai);
   }
-  for (; j < c; ++j) F = pair_acc<0>(F, di, __ldg(hin + __ldg(np + (int64_t)j * n)), th, ai, m2ai);
-  const OutPtrs o = {hout, lo, A, srcw, pulse_f, err, fix, res};
-  update_atom<LASER>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k);
+  for (; j < c; ++j)
+    F = pair_acc<0>(F, di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai);
+  const OutPtrs o = {hout, lo, A, srcw, pulse_f, err, fix, reinterpret_cast<float2 *>(res)};
+  update_atom<LASER, true>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k, fixed);
 }
 
 // T (FP64) -> hi + lo of delta = (T - Tref) / Tmax
@@ -586,7 +604,7 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
   const double ti = Ti * inv;
   double F = 0.0;
   for (int j = 0; j < c; ++j) {
-    const int32_t t = __ldg(nbr + (int64_t)j * n + s);
+    const int32_t t = checked_index(__ldg(nbr + (int64_t)j * n + s), n, err);
     const double tj = __ldg(Tin + t) * inv;
     const bool lo = (ti < tj) || (ti == tj && s < t);
     const double a = lo ? ti : tj, b = lo ? tj : ti;
@@ -662,7 +680,20 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     const int32_t tg = narrow ? c.tile_grid128[P == 9 ? 0 : 1] : c.tile_grid[P == 9 ? 0 : 1];
     const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
     const StageArgs none{};
-    if (narrow) {
+    if (c.has_border && narrow) {
+      if (P == 9) substep_tile_kernel<false, 9, false, 128, true><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      else substep_tile_kernel<false, 16, false, 128, true><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+    } else if (c.has_border) {
+      // the forms that keep border atoms
+      const unsigned nt = kTileThreads + 32;
+      if (P == 9) {
+        if (laser) substep_tile_kernel<true, 9, false, 256, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+        else substep_tile_kernel<false, 9, false, 256, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      } else {
+        if (laser) substep_tile_kernel<true, 16, false, 256, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+        else substep_tile_kernel<false, 16, false, 256, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      }
+    } else if (narrow) {
       if (P == 9) substep_tile_kernel<false, 9, false, 128><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
       else substep_tile_kernel<false, 16, false, 128><<<grid, 160, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
     } else {
@@ -737,6 +768,14 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
                              (const void *)substep_tile_kernel<false, 16, true, 256>}};
   const void *inst128[2] = {(const void *)substep_tile_kernel<false, 9, false, 128>,
                             (const void *)substep_tile_kernel<false, 16, false, 128>};
+  // the border forms run on the same grid (their extra CTAs, if any, wait for a
+  // free slot: no CTA waits on another)
+  const void *inst_border[2][3] = {{(const void *)substep_tile_kernel<true, 9, false, 256, true>,
+                                    (const void *)substep_tile_kernel<false, 9, false, 256, true>,
+                                    (const void *)substep_tile_kernel<false, 9, false, 128, true>},
+                                   {(const void *)substep_tile_kernel<true, 16, false, 256, true>,
+                                    (const void *)substep_tile_kernel<false, 16, false, 256, true>,
+                                    (const void *)substep_tile_kernel<false, 16, false, 128, true>}};
   int32_t g[2] = {0, 0}, g128[2] = {0, 0};
   for (int w = 0; w < 2; ++w) {
     int bps = 1 << 30;
@@ -749,6 +788,9 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
            b > 0;
       bps = b < bps ? b : bps;
     }
+    for (int l = 0; l < 3 && ok; ++l)
+      ok = cudaFuncSetAttribute(inst_border[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+           cudaSuccess;
     if (ok) g[w] = bps * num_sms;
     int b = 0;
     if (cudaFuncSetAttribute(inst128[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
