@@ -282,7 +282,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
-        "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)) * args.steps,
+        # every rank's kernels in the timed region (one replica per rank)
+        "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)) * args.steps * ws,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "substep_tile_kernel" if args.rate_shell == 0 else "substep_f32_kernel (weighted)",
@@ -291,7 +292,7 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "clocks": clocks,
         "energy_drift": e["drift"],
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:   # the oracle's timing: one process, N = 1 only
         line["cpu_baseline"] = cpu_baseline(args.cells)
     print(json.dumps(line), flush=True)
     if ws > 1:
