@@ -78,7 +78,8 @@ extern "C" {
  *                   b^2 / r^2 renormalised so that sum_j w_j r_j^2 over an ideal shell of
  *                   n neighbours with second moment S2 stays S2 (the continuum
  *                   conductivity is unchanged; no counterpart in the paper, where K_ij
- *                   is one rate for all pairs).  Weighted contexts use the general
+ *                   is one rate for all pairs; the weights are computed and kept in
+ *                   single precision).  Weighted contexts use the general
  *                   single-precision or the FP64 substep kernel, not the row tiles
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after

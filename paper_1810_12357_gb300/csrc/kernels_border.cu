@@ -39,15 +39,22 @@ __global__ void __launch_bounds__(256) border_sum_partial(int64_t n, double *__r
   __shared__ double sh[8];
   double a = 0.0;
   float2 *R2 = reinterpret_cast<float2 *>(R);
+  // float pairs: each thread sums its pairs as a float pair (single-precision
+  // operations) and converts once
+  float ah = 0.0f, al = 0.0f;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     if (pairs) {
       const float2 r = R2[s];
-      a += (double)r.x + (double)r.y;
+      const float t = ah + r.x, bb = t - ah;
+      const float e = (ah - (t - bb)) + (r.x - bb) + (al + r.y);
+      ah = t + e;
+      al = e - (ah - t);
     } else {
       a += R[s];
     }
     if (clear) R[s] = 0.0;   // both forms: eight zero bytes
   }
+  if (pairs) a = (double)ah + (double)al;
   const double r = bsum(a, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }

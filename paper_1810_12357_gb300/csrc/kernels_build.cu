@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
                                                        int64_t ps, uint8_t *__restrict__ cnt,
                                                        int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
                                                        int32_t *__restrict__ maxrow, int32_t *__restrict__ err,
-                                                       float *__restrict__ wgt, double wn) {
+                                                       float *__restrict__ wgt, float wn) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 qi = q_s[s];
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (WEIGHTS) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
+              if (WEIGHTS) wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
             }
             ++m;
           }
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (WEIGHTS) wgt[(int64_t)m * n + s] = (float)(wn / (double)(d2 > 0 ? d2 : 1));
+              if (WEIGHTS) wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
             }
             ++m;
           }
@@ -595,11 +595,12 @@ cudaError_t launch_neighbors(Ctx &c) {
   // the weighted forms store each pair's rate weight beside its index
   auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
                     : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);
-  // pair weights S2 / (n_shell r^2) with r^2 = d2 2^-40 A^2 (d2 on the 2^-20 A grid)
+  // pair weights S2 / (n_shell r^2) with r^2 = d2 2^-40 A^2 (d2 on the 2^-20 A grid),
+  // in single precision (as stored): d2 rounded to float, one correctly rounded division
   const double wn = c.p.rate_shell_n > 0 ? c.p.zb2_A2 * 1099511627776.0 / (double)c.p.rate_shell_n : 0.0;
   kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
                                              reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt,
-                                             c.maxstaged, c.maxrow, c.err, c.wgt, wn);
+                                             c.maxstaged, c.maxrow, c.err, c.wgt, (float)wn);
   return cudaGetLastError();
 }
 

@@ -548,7 +548,21 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   const int32_t *np = nbr + s;
   int j = 0;
   if (wgt) {
+    // six pairs at a time: their index, weight and value loads are in flight together
     const float *wp = wgt + s;
+    for (; j + 6 <= c; j += 6) {
+      int32_t t[6];
+      float dj[6], wj[6];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        t[u] = checked_index(__ldg(np + (int64_t)(j + u) * n), n, err);
+        wj[u] = __ldg(wp + (int64_t)(j + u) * n);
+      }
+#pragma unroll
+      for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
+#pragma unroll
+      for (int u = 0; u < 6; ++u) F = fmaf(wj[u], pair_acc<0>(0.0f, di, dj[u], th, ai, m2ai), F);
+    }
     for (; j < c; ++j)
       F = fmaf(__ldg(wp + (int64_t)j * n),
                pair_acc<0>(0.0f, di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai),
