@@ -26,7 +26,8 @@ conservation and the uniform fixed point.  The general stage form with free
 coefficients (window_general, its adjoint gradient window_grad and
 stability_polynomial, used to train windows) is pinned by reproducing both
 recurrences and their closed-form stability polynomials, and by central
-differences of the loss and of the flux sum (flux_vjp).
+differences of the loss and of the flux sum (flux_vjp); the adjoint through a
+chain of windows (rollout_grad) by central differences of rollout_loss.
 """
 from __future__ import annotations
 
@@ -262,3 +263,75 @@ def coefficient_sets(s: int, order: int, eps: float):
     kap = 1.0 - mu - nu
     kap[0] = kap[1] = 0.0
     return [nu.copy(), mut.copy(), kap, gam.copy()]
+
+
+# ---- rollouts: chains of windows (training against a trajectory) -------------
+#
+# K windows in a row, each started from the previous one's end: theta_0 =
+# T_in / Tmax, theta_w = theta_{w-1} + z_s(theta_{w-1}).  Loss against the plain
+# method's trajectory T*_1..T*_K:
+#   L = sum_w mean_i ((Tmax theta_w,i - T*_w,i) / T*_w,i)^p.
+# Its adjoint runs the windows backwards: with Lam_w = dL/dtheta_w, window w's
+# stage adjoint starts from lam_s = Lam_w and, besides the coefficient
+# gradients, gives dL/dtheta_{w-1} through the window:
+#   Lam_w + sum_{j>=1} a_j J(Y_{j-1})^T lam_j + J(Y_0)^T sum_{j>=2} g_j lam_j,
+# (Y_{j-1} = Y_0 + z_{j-1} depends on Y_0 directly), to which the loss term of
+# window w-1 is added.
+
+
+def rollout_loss(rowptr, col, T_in, T_targets, Tmax: float, K: float, tau: float, coeffs, power: int = 2):
+    """Loss of len(T_targets) chained windows started from T_in."""
+    th = np.asarray(T_in, dtype=np.float64) / Tmax
+    s = len(coeffs[0]) - 1
+    L = 0.0
+    for Tt in T_targets:
+        z, _ = window_general(rowptr, col, th, K, tau, coeffs)
+        th = th + z[s]
+        r = (Tmax * th - Tt) / Tt
+        L += float(np.mean(r ** power))
+    return L
+
+
+def rollout_grad(rowptr, col, T_in, T_targets, Tmax: float, K: float, tau: float, coeffs, power: int = 2):
+    """rollout_loss and its gradient with respect to (nu, mut, kap, gam), by the
+    adjoint through the chain of windows (see above)."""
+    nu, mut, kap, gam = (np.asarray(c, dtype=np.float64) for c in coeffs)
+    s = len(nu) - 1
+    n = np.asarray(T_in).shape[0]
+    ths = [np.asarray(T_in, dtype=np.float64) / Tmax]
+    stages = []
+    L = 0.0
+    for Tt in T_targets:
+        z, F = window_general(rowptr, col, ths[-1], K, tau, coeffs)
+        stages.append((z, F))
+        ths.append(ths[-1] + z[s])
+        r = (Tmax * ths[-1] - Tt) / Tt
+        L += float(np.mean(r ** power))
+    g = [np.zeros(s + 1) for _ in range(4)]
+    aK, gK = tau * K * mut, tau * K * gam
+    Lam = np.zeros(n)
+    for w in range(len(T_targets) - 1, -1, -1):
+        Tt = np.asarray(T_targets[w], dtype=np.float64)
+        r = (Tmax * ths[w + 1] - Tt) / Tt
+        Lam = Lam + power * r ** (power - 1) * Tmax / Tt / n
+        y0 = ths[w]
+        z, F = stages[w]
+        lam = [np.zeros(n) for _ in range(s + 1)]
+        lam[s] = Lam.copy()
+        mu = np.zeros(n)       # sum_j a_j J(Y_{j-1})^T lam_j for j >= 2
+        gsum = np.zeros(n)     # sum_{j>=2} g_j lam_j
+        for j in range(s, 1, -1):
+            lj = lam[j]
+            g[0][j] += lj @ (z[j - 2] - z[j - 1])
+            g[1][j] += tau * K * (lj @ F[j])
+            g[2][j] += -(lj @ z[j - 1])
+            g[3][j] += tau * K * (lj @ F[1])
+            v = aK[j] * flux_vjp(rowptr, col, y0 + z[j - 1], lj)
+            lam[j - 1] += (1.0 - nu[j] - kap[j]) * lj + v
+            lam[j - 2] += nu[j] * lj
+            mu += v
+            gsum += gK[j] * lj
+        g[1][1] += tau * K * (lam[1] @ F[1])
+        mu += flux_vjp(rowptr, col, y0, aK[1] * lam[1] + gsum)
+        Lam = Lam + mu
+    return L, g

@@ -277,3 +277,37 @@ def test_window_gradient_matches_differences(power):
             assert g[k][j] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(loss) / h), (k, j)
             checked += 1
     assert checked == 4 * s - 3
+
+
+@pytest.mark.parametrize("power", [2, 4])
+def test_rollout_gradient_matches_differences(power):
+    # three chained windows against a trajectory the window itself would not
+    # reproduce (other coefficients): the adjoint through the chain against
+    # central differences of the rollout loss, for every coefficient
+    rowptr, col, th = _small_system(5)
+    # tau K lambda_max about 11.5, inside the 5-stage second-order interval (16):
+    # the chained windows stay bounded
+    K, tau, s, Tmax = 40.0, 0.02, 5, 20000.0
+    C = W.coefficient_sets(s, 2, 2 / 13)
+    Ct = [c * (1.0 + 0.05 * np.cos(np.arange(c.size) + 2 * k)) for k, c in enumerate(C)]
+    T_in = th * Tmax
+    targets, y = [], th.copy()
+    for _ in range(3):
+        z, _ = W.window_general(rowptr, col, y, K, tau, Ct)
+        y = y + z[s]
+        targets.append(Tmax * y)
+    loss, g = W.rollout_grad(rowptr, col, T_in, targets, Tmax, K, tau, C, power)
+    assert loss == pytest.approx(W.rollout_loss(rowptr, col, T_in, targets, Tmax, K, tau, C, power), rel=1e-14)
+    for k in range(4):
+        for j in range(1, s + 1):
+            if j == 1 and k != 1:
+                assert g[k][j] == 0.0
+                continue
+            h = 1e-6 * max(abs(C[k][j]), 1e-3)
+            Cp = [c.copy() for c in C]
+            Cm = [c.copy() for c in C]
+            Cp[k][j] += h
+            Cm[k][j] -= h
+            fd = (W.rollout_loss(rowptr, col, T_in, targets, Tmax, K, tau, Cp, power)
+                  - W.rollout_loss(rowptr, col, T_in, targets, Tmax, K, tau, Cm, power)) / (2 * h)
+            assert g[k][j] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(loss) / h), (k, j)
