@@ -544,53 +544,42 @@ def run_window(args, coeffs=None, learned_info=None):
 
 
 def train_window(args):
-    """Stage coefficients of the learned window: Adam on windows of the plain
-    method from 256,000-atom track and hot-spot cells (40^3 cells, coupling
-    off), starting from the first-order damped Chebyshev values; returns the
-    coefficients and the training record (held-out window errors included)."""
+    """Stage coefficients of the learned window: Adam on rollouts of 6 chained
+    windows against the plain method's trajectories (coupling off) of 256,000-atom
+    track and hot-spot cells (40^3 cells), from the second-order damped Chebyshev
+    values, each rollout started after the first window (the sharp initial front
+    is left to the residual test); returns the coefficients and the training
+    record with held-out rollout errors."""
     from paper_1810_12357_gb300 import EhcCheb, learned
     from paper_1810_12357_gb300 import inputs as I
-    n_w, st = args.window, args.stages
+    n_w, st, nwin = args.window, args.stages, 6
     p = I.params_track()
     t0 = time.perf_counter()
     train_sys = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
     train_sys += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
                   for k in range(3)]
-    per = 9   # windows per run: the first (left out) and eight for training
-    ctxs, pairs = [], []
-    for s in train_sys:
-        g, pr = learned.generate_windows(s, p, per, n_w)
-        ctxs.append(g)
-        pairs.append(pr)
-    w = EhcCheb(ctxs[0], n_w, st, args.damping, order=args.order)
+    data = [learned.generate_trajectory(s, p, nwin, n_w) for s in train_sys]
+    w = EhcCheb(data[0][0], n_w, st, args.damping, order=args.order)
     beta0 = w.stability()
     # the stability range of training: the spectrum of the training states
-    spec = max(w.spectrum(pairs[c][0][0], iters=300, ctx=ctxs[c]) for c in range(len(ctxs)))
-    hist = []
-    for k in range(args.train_steps):
-        c = k % len(ctxs)
-        # the first window of every run (the sharp initial front) is left to the
-        # residual test and the plain substeps
-        prs = pairs[c][1:]
-        t_in, t_out = prs[(k // len(ctxs)) % len(prs)]
-        lr = 3e-3 if k < args.train_steps * 3 // 4 else 1e-3
-        hist.append(w.train_step(t_in, t_out, lr, ctx=ctxs[c], power=args.loss_power))
+    spec = max(w.spectrum(t_in, iters=300, ctx=c) for c, t_in, _ in data)
+    hist = learned.train_rollout(w, data, args.train_steps, lr=5e-3, lr_final=2e-3, power=args.loss_power)
     coeffs = [c.copy() for c in w.coefficients()]
     t_train = time.perf_counter() - t0
-    del pairs
-    # held-out windows of another track (its first window excluded as in training):
-    # trained against untrained coefficients, window by window
-    held_g, held = learned.generate_windows(I.track_system(40, 199, peak=20000.0, r0=20.0), p, 8, n_w)
-    base = EhcCheb(held_g, n_w, st, args.damping, order=args.order)
-    per_t = [learned.window_error(w, [h], ctx=held_g)[0] for h in held[1:]]
-    per_u = [learned.window_error(base, [h])[0] for h in held[1:]]
-    info = {"train_s": t_train, "train_windows": (per - 1) * len(train_sys), "train_steps": args.train_steps,
-            "train_cells": "256,000-atom tracks and hot spots (40^3 cells), first window of each run left out",
+    del data
+    # held-out rollouts of another track: trained against untrained coefficients
+    hc, h0, ht = learned.generate_trajectory(I.track_system(40, 199, peak=20000.0, r0=20.0), p, nwin, n_w)
+    base = EhcCheb(hc, n_w, st, args.damping, order=args.order)
+    per_u = learned.rollout_error(base, h0, ht, ctx=hc)
+    per_t = learned.rollout_error(w, h0, ht, ctx=hc)
+    info = {"train_s": t_train, "train_rollouts": len(train_sys), "rollout_windows": nwin,
+            "train_steps": args.train_steps,
+            "train_cells": "256,000-atom tracks and hot spots (40^3 cells), rollouts from the end of the first window",
             "start": "damped Chebyshev order %d, damping %.4g" % (args.order, args.damping),
-            "loss": "mean relative error^%d" % args.loss_power,
+            "loss": "sum over the rollout's windows of mean relative error^%d" % args.loss_power,
             "training_spectrum_tauK_lambda_max": spec, "stability_untrained": beta0,
-            "stability_trained": w.stability(),
-            "heldout_256k_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
+            "stability_trained": w.stability(), "loss_first": hist[0], "loss_last": hist[-1],
+            "heldout_256k_rollout_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
     return coeffs, info
 
 
@@ -716,8 +705,8 @@ def main():
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)
     ap.add_argument("--train-windows", type=int, default=480)
-    ap.add_argument("--train-steps", type=int, default=1500)
-    ap.add_argument("--loss-power", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=None)
+    ap.add_argument("--loss-power", type=int, default=2)
     ap.add_argument("--replicas", type=int, default=256)
     args = ap.parse_args()
     args.tau_given = any(a == "--tau" or a.startswith("--tau=") for a in sys.argv[1:])
@@ -726,6 +715,9 @@ def main():
     # window trains the same 15 stages from those values
     if args.stages is None:
         args.stages = 15
+    if args.train_steps is None:
+        # rollout training of the window; the network's Adam steps
+        args.train_steps = 400 if args.model == "window" else 1500
     if args.damping is None:
         args.damping = 2.0 / 13.0
     if args.warmup < 3 and args.impl == "ehc":

@@ -374,6 +374,18 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, const do
  * largest estimate so far bounds the stability range of training.  The
  * iteration approaches |lambda_max| from below. */
 int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, int32_t iters, double *x_out);
+/* One training step on a rollout: n_win (1..64) windows chained from Tin_dev,
+ * each started from the previous one's end, against the plain method's states
+ * after each window, Ttar_dev [n_win][N] (caller order, device, coupling off).
+ * Loss sum_w mean_i ((T^_w,i - T*_w,i) / T*_w,i)^p, p = loss_power (2, 4, 8); its
+ * gradient by the adjoint through the chain (GPU kernels: the stage sweep of
+ * each window in reverse, the window-start adjoint passed back); gradient and
+ * Adam step as in ehc_cheb_train_step (same stability constraint, same
+ * EHC_E_UNSTABLE).  The first call with a given n_win allocates
+ * (n_win + 1 + 2 n_win stages + 5) floats and n_win doubles per atom.
+ * Synchronises. */
+int ehc_cheb_train_rollout(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, const double *Ttar_dev, int32_t n_win,
+                           float lr, int32_t loss_power, float *loss_host, float *grad_host);
 /* The stages' flux-only prediction of one window from Tin_dev into Tout_dev
  * (caller order, device), with the training kernels.  Training, prediction and
  * the spectrum estimate take uniform pair rates only (EHC_E_INVAL with

@@ -103,6 +103,7 @@ _SIGS = {
     "ehc_cheb_set_coefficients": (_I, [_P, _P, _P, _P, _P, _P]),
     "ehc_cheb_train_step": (_I, [_P, _P, _P, _P, ctypes.c_float, ctypes.c_int32, _P, _P]),
     "ehc_cheb_predict": (_I, [_P, _P, _P, _P]),
+    "ehc_cheb_train_rollout": (_I, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _P, _P]),
     "ehc_cheb_stability": (_I, [_P, _P]),
     "ehc_cheb_spectrum": (_I, [_P, _P, _P, ctypes.c_int32, _P]),
     "ehc_cheb_destroy": (None, [_P]),
@@ -542,6 +543,24 @@ class EhcCheb:
         _check(self._lib.ehc_cheb_train_step(self._h, c._h, _ptr(Tin), _ptr(Ttar), ctypes.c_float(lr), int(power),
                                              ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
                "ehc_cheb_train_step")
+        if want_grad:
+            return float(loss.value), g.reshape(4, self.stages + 1)
+        return float(loss.value)
+
+    def train_rollout(self, Tin, Ttargets, lr: float, want_grad: bool = False, ctx=None, power: int = 8):
+        """Loss of len(Ttargets) windows chained from Tin against the plain
+        trajectory Ttargets (a (K, N) tensor, or a list of K tensors, caller
+        order) and (lr > 0) one Adam step on the coefficients."""
+        import torch
+        tt = torch.stack(list(Ttargets)).contiguous() if not isinstance(Ttargets, torch.Tensor) else Ttargets
+        tt = tt.to(torch.float64).contiguous()
+        loss = ctypes.c_float()
+        g = np.empty(4 * (self.stages + 1), dtype=np.float32) if want_grad else None
+        c = ctx if ctx is not None else self.ctx
+        _check(self._lib.ehc_cheb_train_rollout(self._h, c._h, _ptr(Tin), _ptr(tt), int(tt.shape[0]),
+                                                ctypes.c_float(lr), int(power), ctypes.byref(loss),
+                                                g.ctypes.data_as(_P) if g is not None else None),
+               "ehc_cheb_train_rollout")
         if want_grad:
             return float(loss.value), g.reshape(4, self.stages + 1)
         return float(loss.value)

@@ -1330,6 +1330,10 @@ struct ehc_cheb {
   float *thost = nullptr;               // pinned: c0[np] | loss | gc[np] | d[np]
   int adam_t = 0;
   std::vector<double> dacc;             // the accepted relative changes
+  // rollout training (ehc_cheb_train_rollout), for up to ro_cap windows
+  float *ro_buf = nullptr;              // window starts | per window z[1..s], F[1..s] | 5 work vectors
+  double *ro_T = nullptr, *ro_lpart = nullptr;
+  int ro_cap = 0;
   double x_spec = 0.0;                  // largest tau_w K |lambda_max| estimated so far (0: none)
 };
 
@@ -1497,6 +1501,12 @@ WtTab cheb_train_tab(const ehc_cheb *w, int64_t n) {
   return t;
 }
 
+// after a backward pass (loss in w->tloss, gradients in w->tgc / w->tgd): the
+// loss and gradient to the host and, if lr > 0, the Adam step, projected to
+// P'(0) = -1 (slow modes decay at the plain rate) and taken back by halves until
+// |P| <= 1 on (0, xr] again
+int cheb_step_tail(ehc_cheb *w, Ctx &c, float lr, double xr, float *loss_host, float *grad_host);
+
 WtCoef cheb_train_coef(const ehc_cheb *w, const Ctx &c) {
   WtCoef k{};
   const double tauK = (double)w->n_w * c.p.dt_sub_fs * c.K;
@@ -1507,6 +1517,42 @@ WtCoef cheb_train_coef(const ehc_cheb *w, const Ctx &c) {
     k.g[j] = (float)(w->gam[j] * tauK);
   }
   return k;
+}
+
+int cheb_step_tail(ehc_cheb *w, Ctx &c, float lr, double xr, float *loss_host, float *grad_host) {
+  const int np = cheb_np(w);
+  float *hl = w->thost + np, *hg = w->thost + np + 1, *hd = w->thost + 2 * np + 1;
+  CK(cudaMemcpyAsync(hl, w->tloss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(hg, w->tgc, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
+  if (lr > 0.0f) {
+    w->adam_t += 1;
+    CK(wt_adam(c.stream, np, w->tp, w->tm, w->tv, w->tgd, lr, w->adam_t));
+    CK(cudaMemcpyAsync(hd, w->tp, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  if (loss_host) *loss_host = *hl;
+  if (grad_host) std::memcpy(grad_host, hg, sizeof(float) * np);
+  if (lr > 0.0f) {
+    const std::vector<double> dold = w->dacc;
+    std::vector<double> dtry(np);
+    bool taken = false;
+    double t = 1.0;
+    for (int k = 0; k <= 20 && !taken; ++k, t *= 0.5) {
+      for (int b = 0; b < np; ++b) dtry[b] = dold[b] + t * ((double)hd[b] - dold[b]);
+      cheb_apply(w, dtry);
+      taken = cheb_violation(w, xr, kStabGrid) <= kStabTol;
+    }
+    if (taken) {
+      w->dacc = dtry;
+    } else {
+      dtry = dold;
+      cheb_apply(w, dtry);
+    }
+    for (int b = 0; b < np; ++b) hd[b] = (float)w->dacc[b];
+    CK(cudaMemcpyAsync(w->tp, hd, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+  }
+  return EHC_OK;
 }
 
 }  // namespace
@@ -1570,6 +1616,8 @@ void ehc_cheb_destroy(ehc_cheb *w) {
     if (q) cudaFree(q);
   if (w->host) cudaFreeHost(w->host);
   if (w->thost) cudaFreeHost(w->thost);
+  for (void *q : {(void *)w->ro_buf, (void *)w->ro_T, (void *)w->ro_lpart})
+    if (q) cudaFree(q);
   delete w;
 }
 
@@ -1758,42 +1806,84 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const d
   float *y0 = w->tbuf;
   CK(nn_gather(c, Tin_dev, Ttar_dev, w->tT0, w->tT1, y0, false));
   CK(wt_stages(c, s, k, y0, t));
-  float *hl = w->thost + np, *hg = w->thost + np + 1, *hd = w->thost + 2 * np + 1;
   CK(wt_backward(c, s, k, y0, t, w->tT0, w->tT1, loss_power, w->tlpart, w->tdpart, tauK, w->tc0, w->tgc, w->tgd,
                  w->tloss));
-  CK(cudaMemcpyAsync(hl, w->tloss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
-  CK(cudaMemcpyAsync(hg, w->tgc, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
-  if (lr > 0.0f) {
-    w->adam_t += 1;
-    CK(wt_adam(c.stream, np, w->tp, w->tm, w->tv, w->tgd, lr, w->adam_t));
-    CK(cudaMemcpyAsync(hd, w->tp, sizeof(float) * np, cudaMemcpyDeviceToHost, c.stream));
+  return cheb_step_tail(w, c, lr, xr, loss_host, grad_host);
+}
+
+int ehc_cheb_train_rollout(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const double *Ttar_dev, int32_t n_win,
+                           float lr, int32_t loss_power, float *loss_host, float *grad_host) {
+  NvtxRange nvtx_range("ehc_cheb_train_rollout");
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || n_win < 1 || n_win > 64 ||
+      !(lr >= 0.0f) || (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0)
+    return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  const int s = w->s, np = cheb_np(w);
+  if (c.n == 0) {
+    if (loss_host) *loss_host = 0.0f;
+    if (grad_host) std::memset(grad_host, 0, sizeof(float) * np);
+    return EHC_OK;
   }
-  CK(cudaStreamSynchronize(c.stream));
-  if (loss_host) *loss_host = *hl;
-  if (grad_host) std::memcpy(grad_host, hg, sizeof(float) * np);
-  if (lr > 0.0f) {
-    // the Adam step, projected to P'(0) = -1 (slow modes decay at the plain rate)
-    // and taken back by halves until |P| <= 1 on (0, xr] again
-    const std::vector<double> dold = w->dacc;
-    std::vector<double> dtry(np);
-    bool taken = false;
-    double t = 1.0;
-    for (int k = 0; k <= 20 && !taken; ++k, t *= 0.5) {
-      for (int b = 0; b < np; ++b) dtry[b] = dold[b] + t * ((double)hd[b] - dold[b]);
-      cheb_apply(w, dtry);
-      taken = cheb_violation(w, xr, kStabGrid) <= kStabTol;
+  int r = cheb_train_prepare(w, c);
+  if (r) return r;
+  const double xr = 1.1 * (w->x_spec > 0.0 ? w->x_spec : (double)w->n_w * c.stability);
+  if (lr > 0.0f && cheb_violation(w, xr, kStabGrid) > kStabTol) return EHC_E_UNSTABLE;
+  const int64_t n = c.n;
+  if (n_win > w->ro_cap) {
+    for (void *q : {(void *)w->ro_buf, (void *)w->ro_T, (void *)w->ro_lpart})
+      if (q) cudaFree(q);
+    w->ro_buf = nullptr;
+    w->ro_T = w->ro_lpart = nullptr;
+    w->ro_cap = 0;
+    bool ok = true;
+    auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+    A(dalloc(&w->ro_buf, n * ((int64_t)n_win + 1 + (int64_t)n_win * 2 * s + 5)));
+    A(dalloc(&w->ro_T, n * (int64_t)n_win));
+    A(dalloc(&w->ro_lpart, (int64_t)wt_loss_partials(n) * n_win));
+    if (ok) A(cudaMemsetAsync(w->ro_buf, 0, sizeof(float) * n * ((int64_t)n_win + 1 + (int64_t)n_win * 2 * s + 5),
+                              c.stream));
+    if (!ok) {
+      cudaGetLastError();
+      return EHC_E_NOMEM;
     }
-    if (taken) {
-      w->dacc = dtry;
-    } else {
-      dtry = dold;
-      cheb_apply(w, dtry);
-    }
-    for (int b = 0; b < np; ++b) hd[b] = (float)w->dacc[b];
-    CK(cudaMemcpyAsync(w->tp, hd, sizeof(float) * np, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaStreamSynchronize(c.stream));
+    w->ro_cap = n_win;
   }
-  return EHC_OK;
+  // layout within ro_buf (capacity ro_cap windows)
+  const int cap = w->ro_cap;
+  float *starts = w->ro_buf;
+  float *zf = starts + n * (cap + 1);
+  float *Lam = zf + n * (int64_t)cap * 2 * s;
+  float *mu = Lam + n, *gs = mu + n, *tmp = gs + n, *zero = tmp + n;
+  const WtTab t1 = cheb_train_tab(w, n);
+  float *lam[kMaxStages + 1] = {};
+  for (int j = 1; j <= s; ++j) lam[j] = const_cast<float *>(t1.lam[j]);
+  std::vector<WtTab> tabs(n_win);
+  std::vector<const float *> ys(n_win + 1);
+  std::vector<const double *> Tt(n_win);
+  for (int v = 0; v <= n_win; ++v) ys[v] = starts + n * v;
+  for (int v = 0; v < n_win; ++v) {
+    tabs[v] = WtTab{};
+    for (int j = 1; j <= s; ++j) {
+      tabs[v].z[j] = zf + n * ((int64_t)v * 2 * s + j - 1);
+      tabs[v].F[j] = zf + n * ((int64_t)v * 2 * s + s + j - 1);
+      tabs[v].lam[j] = lam[j];
+    }
+    Tt[v] = w->ro_T + n * v;
+  }
+  const WtCoef k = cheb_train_coef(w, c);
+  const double tauK = (double)w->n_w * c.p.dt_sub_fs * c.K;
+  // the start state and the targets in sorted order; then the windows, each from
+  // the previous one's end
+  CK(nn_gather(c, Tin_dev, nullptr, w->tT0, nullptr, starts, false));
+  for (int v = 0; v < n_win; ++v) CK(nn_gather(c, Ttar_dev + n * v, nullptr, w->ro_T + n * v, nullptr, tmp, false));
+  for (int v = 0; v < n_win; ++v) {
+    CK(wt_stages(c, s, k, ys[v], tabs[v]));
+    CK(wt_next_start(c, ys[v], tabs[v].z[s], const_cast<float *>(ys[v + 1])));
+  }
+  CK(wt_rollout(c, s, k, n_win, ys.data(), tabs.data(), Tt.data(), lam, Lam, mu, gs, tmp, zero, loss_power,
+                w->ro_lpart, w->tdpart, tauK, w->tc0, w->tgc, w->tgd, w->tloss));
+  return cheb_step_tail(w, c, lr, xr, loss_host, grad_host);
 }
 
 int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t iters, double *x_out) {

@@ -204,6 +204,15 @@ cudaError_t wt_stages(Ctx &c, int s, const WtCoef &k, const float *y0, const WtT
 cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const WtTab &t, const double *T0,
                         const double *T1, int loss_power, double *lpart, double *dpart, double tauK,
                         const float *c0, float *gc, float *gd, float *loss);
+// rollout of nwin chained windows: y0[0..nwin] the window starts (y0[w + 1] = y0[w]
+// + z_s of window w), t[w] their stage buffers, Tt[w] the targets (sorted, FP64),
+// lam[1..s] shared adjoint buffers; Lam, mu, gs, tmp: n floats of work space; zero:
+// n zero floats; lpart: nwin x wt_loss_partials
+cudaError_t wt_rollout(Ctx &c, int s, const WtCoef &k, int nwin, const float *const *y0, const WtTab *t,
+                       const double *const *Tt, float *const *lam, float *Lam, float *mu, float *gs, float *tmp,
+                       const float *zero, int loss_power, double *lpart, double *dpart, double tauK,
+                       const float *c0, float *gc, float *gd, float *loss);
+cudaError_t wt_next_start(Ctx &c, const float *y0, const float *zs, float *y1);
 size_t wt_dot_partials(int64_t n, int s);
 size_t wt_loss_partials(int64_t n);
 cudaError_t wt_adam(cudaStream_t st, int np, float *p, float *m, float *v, const float *g, float lr, int t);

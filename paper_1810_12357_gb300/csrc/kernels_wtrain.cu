@@ -115,11 +115,14 @@ __global__ void __launch_bounds__(kWtThreads) wt_loss_kernel(int32_t n, const fl
 }
 
 // stage j of the backward sweep: lam1 = lam_{j-1} += c1 lam_j + a (J(Y_{j-1})^T lam_j),
-// lam2 = lam_{j-2} += nu lam_j (lam2 == nullptr when j - 2 = 0)
+// lam2 = lam_{j-2} += nu lam_j (lam2 == nullptr when j - 2 = 0); for rollouts
+// also mu += a J(Y_{j-1})^T lam_j and gs += g lam_j (the window-start adjoint's
+// parts; null when not wanted)
 __global__ void __launch_bounds__(kWtThreads) wt_adjoint_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt, float th,
     const float *__restrict__ y0, const float *__restrict__ zm1, const float *__restrict__ lam, float c1, float a,
-    float nu, float *__restrict__ lam1, float *__restrict__ lam2) {
+    float nu, float *__restrict__ lam1, float *__restrict__ lam2, float g = 0.0f, float *__restrict__ mu = nullptr,
+    float *__restrict__ gs = nullptr) {
   const int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   const float am = th + (y0[m] + zm1[m]);
@@ -133,11 +136,14 @@ __global__ void __launch_bounds__(kWtThreads) wt_adjoint_kernel(
   }
   lam1[m] += fmaf(a, acc, c1 * lm);
   if (lam2) lam2[m] += nu * lm;
+  if (mu) mu[m] += a * acc;
+  if (gs) gs[m] += g * lm;
 }
 
 // per stage j = blockIdx.y + 1 the four inner products of the gradient, block
 // sums into part[(4 j + q) * gridDim.x + blockIdx.x]
-__global__ void __launch_bounds__(kWtThreads) wt_dots_kernel(int32_t n, WtTab t, double *__restrict__ part) {
+__global__ void __launch_bounds__(kWtThreads) wt_dots_kernel(int32_t n, WtTab t, double *__restrict__ part,
+                                                            int accumulate = 0) {
   __shared__ double red[kWtThreads / 32];
   const int j = blockIdx.y + 1;
   const float *lam = t.lam[j];
@@ -160,10 +166,17 @@ __global__ void __launch_bounds__(kWtThreads) wt_dots_kernel(int32_t n, WtTab t,
   const double v3 = block_sum<kWtThreads>(s3, red);
   if (threadIdx.x == 0) {
     const size_t base = (size_t)4 * j * gridDim.x + blockIdx.x;
-    part[base] = v0;
-    part[base + gridDim.x] = v1;
-    part[base + 2 * gridDim.x] = v2;
-    part[base + 3 * gridDim.x] = v3;
+    if (accumulate) {
+      part[base] += v0;
+      part[base + gridDim.x] += v1;
+      part[base + 2 * gridDim.x] += v2;
+      part[base + 3 * gridDim.x] += v3;
+    } else {
+      part[base] = v0;
+      part[base + gridDim.x] = v1;
+      part[base + 2 * gridDim.x] = v2;
+      part[base + 3 * gridDim.x] = v3;
+    }
   }
 }
 
@@ -251,6 +264,39 @@ __global__ void wt_normalise_kernel(int32_t n, const float *__restrict__ u, cons
   v[i] = q > 0.0 ? (float)(u[i] / sqrt(q)) : 0.0f;
 }
 
+// window w of a rollout: r = (Tref + Tmax y - T*) / T* at the window's end y,
+// block sums of r^p into part, and Lam += p r^(p-1) Tmax / (n T*)
+__global__ void __launch_bounds__(kWtThreads) wt_rollout_loss_kernel(int32_t n, const float *__restrict__ y,
+                                                                    const double *__restrict__ Tt, double Tref,
+                                                                    double Tmax, int pw, float *__restrict__ Lam,
+                                                                    double *__restrict__ part) {
+  __shared__ double red[kWtThreads / 32];
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double rp = 0.0;
+  if (i < n) {
+    const double t = Tt[i];
+    const double r = (fma(Tmax, (double)y[i], Tref) - t) / t;
+    double rq = r;
+    for (int k = 2; k < pw; ++k) rq *= r;
+    rp = rq * r;
+    Lam[i] += (float)(pw * rq * Tmax / ((double)n * t));
+  }
+  const double b = block_sum<kWtThreads>(rp, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+// out = a + b (the next window's start), out = c x + y (the VJP input), x += y
+__global__ void wt_add_kernel(int32_t n, const float *__restrict__ a, const float *__restrict__ b,
+                              float *__restrict__ out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + b[i];
+}
+__global__ void wt_axpy_kernel(int32_t n, float c, const float *__restrict__ x, const float *__restrict__ y,
+                               float *__restrict__ out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fmaf(c, x[i], y[i]);
+}
+
 __global__ void wt_end_kernel(int64_t n, const double *__restrict__ T0, const float *__restrict__ zs, double Tmax,
                               double *__restrict__ T1) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -293,6 +339,51 @@ cudaError_t wt_backward(Ctx &c, int s, const WtCoef &k, const float *y0, const W
   wt_dots_kernel<<<dim3(nbd, s), kWtThreads, 0, c.stream>>>(n, t, dpart);
   wt_final_kernel<<<4 * (s + 1) + 1, 128, 0, c.stream>>>(s, (int)nbd, dpart, (int)nbl, lpart, tauK, 1.0 / n, c0,
                                                          gc, gd, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t wt_rollout(Ctx &c, int s, const WtCoef &k, int nwin, const float *const *y0, const WtTab *t,
+                       const double *const *Tt, float *const *lam, float *Lam, float *mu, float *gs, float *tmp,
+                       const float *zero, int loss_power, double *lpart, double *dpart, double tauK,
+                       const float *c0, float *gc, float *gd, float *loss) {
+  if (c.n == 0) return cudaSuccess;
+  const int32_t n = (int32_t)c.n;
+  const float th = (float)(c.p.Tref_K / c.p.Tmax_K);
+  const unsigned nb = wblk(n), nbl = wblk(n);
+  const unsigned nbd = std::min<unsigned>(wblk(n), kWtDotBlocks);
+  cudaError_t e = cudaMemsetAsync(Lam, 0, sizeof(float) * n, c.stream);
+  for (int w = nwin - 1; w >= 0 && e == cudaSuccess; --w) {
+    // the loss of window w at its end y0[w + 1] seeds Lam
+    wt_rollout_loss_kernel<<<nbl, kWtThreads, 0, c.stream>>>(n, y0[w + 1], Tt[w], c.p.Tref_K, c.p.Tmax_K,
+                                                             loss_power, Lam, lpart + (size_t)w * nbl);
+    WtTab tw = t[w];
+    for (int j = 1; j <= s; ++j) tw.lam[j] = lam[j];
+    e = cudaMemcpyAsync(lam[s], Lam, sizeof(float) * n, cudaMemcpyDeviceToDevice, c.stream);
+    for (int j = 1; j < s && e == cudaSuccess; ++j) e = cudaMemsetAsync(lam[j], 0, sizeof(float) * n, c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mu, 0, sizeof(float) * n, c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gs, 0, sizeof(float) * n, c.stream);
+    if (e != cudaSuccess) break;
+    for (int j = s; j >= 2; --j)
+      wt_adjoint_kernel<<<nb, kWtThreads, 0, c.stream>>>(n, c.nbr, c.cnt, th, y0[w], tw.z[j - 1], lam[j],
+                                                          1.0f - k.nu[j] - k.kap[j], k.a[j], k.nu[j], lam[j - 1],
+                                                          j >= 3 ? lam[j - 2] : nullptr, k.g[j], mu, gs);
+    wt_dots_kernel<<<dim3(nbd, s), kWtThreads, 0, c.stream>>>(n, tw, dpart, w < nwin - 1 ? 1 : 0);
+    // mu += J(Y_0)^T (a_1 lam_1 + gs): the adjoint kernel at Y_0 (zero change)
+    wt_axpy_kernel<<<nb, kWtThreads, 0, c.stream>>>(n, k.a[1], lam[1], gs, tmp);
+    wt_adjoint_kernel<<<nb, kWtThreads, 0, c.stream>>>(n, c.nbr, c.cnt, th, y0[w], zero, tmp, 0.0f, 1.0f, 0.0f, mu,
+                                                        nullptr);
+    // the window-start adjoint: Lam (the end's) + mu
+    wt_add_kernel<<<nb, kWtThreads, 0, c.stream>>>(n, Lam, mu, Lam);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  wt_final_kernel<<<4 * (s + 1) + 1, 128, 0, c.stream>>>(s, (int)nbd, dpart, (int)(nbl * nwin), lpart, tauK,
+                                                         1.0 / n, c0, gc, gd, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t wt_next_start(Ctx &c, const float *y0, const float *zs, float *y1) {
+  if (c.n > 0) wt_add_kernel<<<wblk(c.n), kWtThreads, 0, c.stream>>>((int32_t)c.n, y0, zs, y1);
   return cudaGetLastError();
 }
 

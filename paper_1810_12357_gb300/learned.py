@@ -74,3 +74,47 @@ def init_params(H: int, seed: int = 0) -> np.ndarray:
     p[7 * H:8 * H] = rng.normal(0, 0.01, size=H)         # u
     p[8 * H] = 1.0                                        # c0
     return p
+
+
+def generate_trajectory(system, params: dict, n_windows: int, n_w: int = 100, skip: int = 1):
+    """A plain flux-only trajectory for rollout training: the state after `skip`
+    windows of n_w plain substeps (the sharp initial front is left to the
+    residual test) and the states after each of the next n_windows windows, as
+    (context, T0, targets [n_windows, N]) on the device, caller order."""
+    import torch
+    p = dict(params, G=0.0, frozen=1)
+    g = Ehc(p, system)
+    g.set_te(system.Te)
+    x = torch.as_tensor(system.x, device="cuda")
+    v = torch.as_tensor(system.v, device="cuda")
+    g.build_neighbors(x, v)
+    for _ in range(skip):
+        g.substep(n_w)
+    t0 = g.get_te()
+    targets = []
+    for _ in range(n_windows):
+        g.substep(n_w)
+        targets.append(g.get_te())
+    return g, t0, torch.stack(targets).contiguous()
+
+
+def rollout_error(model, t0, targets, ctx=None):
+    """Max relative error after each window when the model's windows are chained
+    from t0 (flux only), against the plain trajectory."""
+    out = []
+    t = t0
+    for k in range(targets.shape[0]):
+        t = model.predict(t) if ctx is None else model.predict(t, ctx=ctx)
+        out.append(float(((t - targets[k]).abs() / targets[k]).max()))
+    return out
+
+
+def train_rollout(model, data, steps: int, lr: float = 3e-3, power: int = 8, lr_final: float | None = None):
+    """Adam steps on the rollout loss, cycling through data = [(ctx, t0, targets)];
+    the rate drops to lr_final for the last quarter.  Returns the loss history."""
+    hist = []
+    for k in range(steps):
+        ctx, t0, tt = data[k % len(data)]
+        rate = lr if (lr_final is None or k < steps * 3 // 4) else lr_final
+        hist.append(model.train_rollout(t0, tt, rate, ctx=ctx, power=power))
+    return hist

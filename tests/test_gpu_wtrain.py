@@ -143,3 +143,64 @@ def test_training_beats_the_untrained_window():
     assert e1 < e0 / 1.5
     # every accepted step keeps |P| <= 1 on 1.1 x the estimated spectrum
     assert w.stability() >= 1.1 * xs * (1.0 - 1e-3)
+
+
+@pytest.mark.parametrize("power", [2, 8])
+def test_rollout_gradient_matches_the_reference(power):
+    # three chained windows (16 substeps, 8 second-order stages, perturbed
+    # coefficients) against a trajectory of other coefficients: loss and gradient
+    # of the GPU adjoint through the chain against the FP64 oracle's
+    import torch
+    from paper_1810_12357_gb300 import EhcCheb
+    s = I.hot_spot_system(8, 4, peak=8000.0)
+    p = dict(I.params_hotspot_fp64(), flux_prec=0, G=0.0)
+    g = _ctx(s, p)
+    K = g.energy()["K_per_fs"]
+    st, n_w = 8, 16
+    w = EhcCheb(g, n_w, st, 2.0 / 13.0, order=2)
+    C = _perturbed(W.coefficient_sets(st, 2, 2.0 / 13.0), 0.03)
+    Ct = _perturbed(W.coefficient_sets(st, 2, 2.0 / 13.0), -0.03)
+    w.set_coefficients(*C)
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"])
+    tau = n_w * p["dt_sub"]
+    targets, y = [], s.Te / p["Tmax"]
+    for _ in range(3):
+        z, _ = W.window_general(rowptr, col, y, K, tau, Ct)
+        y = y + z[st]
+        targets.append(p["Tmax"] * y)
+    loss_o, g_o = W.rollout_grad(rowptr, col, s.Te, targets, p["Tmax"], K, tau, C, power)
+    loss_g, g_g = w.train_rollout(torch.as_tensor(s.Te, device="cuda"),
+                                  torch.as_tensor(np.array(targets), device="cuda"), 0.0, want_grad=True, power=power)
+    g_o = np.array(g_o)
+    rel = np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o)
+    print(f"rollout p={power}: loss {loss_g:.6e} vs {loss_o:.6e}; grad rel diff {rel:.2e}")
+    assert loss_g == pytest.approx(loss_o, rel=2e-3)
+    assert rel < 5e-3
+
+
+def test_rollout_training_beats_the_untrained_window():
+    # 100-substep windows, 15 second-order stages trained on 6-window rollouts of
+    # one 16,384-atom track, evaluated on rollouts of two other tracks: the max error
+    # of every held-out rollout falls to about half (single-window training, by
+    # contrast, does not improve on these coefficients)
+    import torch
+    from paper_1810_12357_gb300 import EhcCheb
+    from paper_1810_12357_gb300 import learned as Lm
+    p = I.params_track()
+    train = [Lm.generate_trajectory(I.track_system(16, 2, r0=20.0), p, 6)]
+    held = [Lm.generate_trajectory(I.track_system(16, 7, r0=15.0), p, 6),
+            Lm.generate_trajectory(I.track_system(16, 9, peak=12000.0, r0=25.0), p, 6)]
+    ctx = train[0][0]
+    w = EhcCheb(ctx, 100, 15, 2.0 / 13.0, order=2)
+    xs = max(w.spectrum(t0, iters=300, ctx=c) for c, t0, _ in train)
+    base = [Lm.rollout_error(w, t0, tt, ctx=c) for c, t0, tt in held]
+    hist = Lm.train_rollout(w, train, 400, lr=5e-3, lr_final=2e-3, power=2)
+    after = [Lm.rollout_error(w, t0, tt, ctx=c) for c, t0, tt in held]
+    for b, a in zip(base, after):
+        print("held-out rollout untrained", " ".join(f"{x:.2e}" for x in b))
+        print("held-out rollout trained  ", " ".join(f"{x:.2e}" for x in a))
+    print(f"loss {hist[0]:.3e} -> {hist[-1]:.3e}, stability {w.stability():.1f} (1.1 x spectrum {1.1 * xs:.1f})")
+    assert hist[-1] < hist[0]
+    for b, a in zip(base, after):
+        assert max(a) < 0.75 * max(b)
+    assert w.stability() >= 1.1 * xs * (1.0 - 1e-3)
