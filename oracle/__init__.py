@@ -57,6 +57,14 @@ def lib():
         L.oracle_flux_vjp.restype = None
         L.oracle_substeps.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl, dbl,
                                       dbl, P, P, dbl, dbl, dbl, P, P, P, P]
+        L.oracle_substeps_local.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, dbl, dbl, dbl,
+                                            ctypes.c_int, dbl, ctypes.c_int, dbl, dbl, dbl, dbl, dbl,
+                                            P, P, dbl, P, P, P, P]
+        L.oracle_substeps_local.restype = ctypes.c_int
+        L.oracle_ce_energy.argtypes = [dbl, dbl, dbl]
+        L.oracle_ce_energy.restype = dbl
+        L.oracle_ce_energy_inv.argtypes = [dbl, dbl, dbl]
+        L.oracle_ce_energy_inv.restype = dbl
         L.oracle_pair_weights.argtypes = [i64, P, P, P, P, P, dbl, i32, P]
         L.oracle_pair_weights.restype = None
         L.oracle_substeps.restype = ctypes.c_int
@@ -203,6 +211,42 @@ def substeps(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, K, cG, VG, *, depth=No
     return st, float(esrc[0])
 
 
+def substeps_local(rowptr, col, T, Tl, chi, A, n_sub, dt, Tmax, *, kappa0, kappa_mode, Tlat, dim_d,
+                   S2_A2, gamma, cap_SI, G, vatom_A3, depth=None, source=None, t_start=0.0, Tfix=None,
+                   weights=None):
+    """LOCAL per-atom C_e / kappa_e form (oracle_substeps_local), in place on T and
+    A; returns (status, E_src increment [eV], border energy increment [eV])."""
+    n = rowptr.shape[0] - 1
+    esrc = np.zeros(1)
+    eres = np.zeros(1)
+    src = None
+    if source is not None:
+        src = np.ascontiguousarray([1.0, source["fluence_Jm2"], source["lp_A"], source["t0_fs"],
+                                    source["sigma_fs"]], dtype=np.float64)
+        depth = np.ascontiguousarray(depth, dtype=np.float64)
+    if Tfix is not None:
+        Tfix = np.ascontiguousarray(Tfix, dtype=np.float64)
+    if weights is not None:
+        weights = np.ascontiguousarray(weights, dtype=np.float64)
+    st = lib().oracle_substeps_local(n, _p(rowptr), _p(col), _p(T), _p(Tl), _p(chi), _p(A), int(n_sub),
+                                     float(dt), float(Tmax), float(kappa0), int(kappa_mode), float(Tlat),
+                                     int(dim_d), float(S2_A2), float(gamma), float(cap_SI), float(G),
+                                     float(vatom_A3), _p(depth) if depth is not None else None,
+                                     _p(src) if src is not None else None, float(t_start), _p(esrc),
+                                     _p(Tfix) if Tfix is not None else None, _p(eres),
+                                     _p(weights) if weights is not None else None)
+    return st, float(esrc[0]), float(eres[0])
+
+
+def ce_energy(T: float, gamma: float, cap: float) -> float:
+    """U(T) = int_0^T min(gamma T', cap) dT' [J m^-3] (the C routine)."""
+    return lib().oracle_ce_energy(float(T), float(gamma), float(cap))
+
+
+def ce_energy_inv(U: float, gamma: float, cap: float) -> float:
+    return lib().oracle_ce_energy_inv(float(U), float(gamma), float(cap))
+
+
 def philox4x32_10(ctr, key):
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
@@ -238,6 +282,28 @@ def ce_integral(T: np.ndarray, gamma: float, cap: float) -> np.ndarray:
     return np.where(T <= Tc, 0.5 * gamma * T * T, 0.5 * cap * Tc + cap * (T - Tc))
 
 
+def local_stability_rate(p: dict, nmax: int, Tlat: float, Tmin: float, Tmax_atoms: float, cap: float) -> float:
+    """Rate bound [1/fs] of the LOCAL form's explicit step, 2 n_max K + G / C_min:
+    in the energy variables U_i the linearised pair terms form a symmetric matrix
+    whose rows sum to at most K = 2 d kappa_ij / (Z b^2 C_e) per pair (the step in
+    T has the same spectrum: its Jacobian is similar to that one).  kappa_mode 1:
+    K = 2 d kappa0 / (gamma Z b^2 T_lat), times T_hi / T_c where the hottest atom
+    is above the cap; kappa_mode 0: K = 2 d kappa0 / (Z b^2 C_e(T_min))."""
+    g = p["gamma_Ce"]
+    def ce(T):
+        c = g * T
+        return min(c, cap) if cap > 0 else c
+    geo = 2.0 * p["dim_d"] / (p["zb2"] * 1e-20)
+    if p["kappa_mode"] == 1:
+        K = geo * p["kappa0"] / (g * Tlat) if Tlat > 0 else float("inf")
+        if cap > 0 and g * Tmax_atoms > cap:
+            K *= Tmax_atoms / (cap / g)
+    else:
+        K = geo * p["kappa0"] / ce(Tmin) if Tmin > 0 else float("inf")
+    cmin = ce(Tmin)
+    return (2.0 * nmax * K + (p["G"] / cmin if cmin > 0 else float("inf"))) * 1e-15
+
+
 class OracleSim:
     """MD-step driver around the oracle primitives, with the same call sequence
     as the library: set_te -> per MD step [build(x, v) -> substeps(n) ->
@@ -246,7 +312,9 @@ class OracleSim:
     p: dict with keys rc, dt_sub, Tmax, gamma_Ce, Ce_cap_kB, kappa0,
     kappa_mode, G, eps_ke, dim_d, zb2, couple_mode, frozen, seed, dof_mode,
     vatom (<= 0: box volume / N), and optionally 'laser' (dict with
-    fluence_Jm2, lp_A, t0_fs, sigma_fs) with `depth` per atom.
+    fluence_Jm2, lp_A, t0_fs, sigma_fs) with `depth` per atom, and ce_mode
+    (0: C_e and kappa_e at the system means, Sec. 2; 1: the LOCAL per-atom form,
+    substeps_local, whose ledger is E_e = sum_i V_atom U(T_i)).
     """
 
     def __init__(self, p: dict, box, periodic, mass_amu, types, depth=None):
@@ -269,6 +337,7 @@ class OracleSim:
         self.Tfix = None          # border temperatures (NaN: free atom), original order
         self.E_res = 0.0          # energy absorbed by the border in closed MD steps [eV]
         self.eres_T = np.zeros(1) # kelvin sum absorbed in the current MD step
+        self.E_res_local = 0.0    # border energy of the LOCAL form [eV]
 
     def set_border(self, Tfix):
         """Fixed-temperature border: atoms with a finite Tfix are held there."""
@@ -307,6 +376,8 @@ class OracleSim:
         self.Te_mean = float(self.T.mean())
         ke = 0.5 * self.mass * (v * v).sum(axis=1) * MVV_EV
         self.Tlat = float(ke.sum() / (1.5 * KB_EV * self.n))
+        self.Tmin = float(self.T.min()) if self.n else 0.0
+        self.Tmax_atoms = float(self.T.max()) if self.n else 0.0
         Ce = p["gamma_Ce"] * self.Te_mean
         cap = self.cap_SI()
         if cap > 0:
@@ -320,11 +391,27 @@ class OracleSim:
         self.gamma_L = p["G"] * self.vatom * 1e-30 / (3.0 * KB_J) * 1e-15
         nmax = int(np.diff(self.rowptr).max()) if self.n else 0
         self.stability = p["dt_sub"] * (2.0 * nmax * self.K + self.cG)
+        if p.get("ce_mode", 0) == 1:
+            self.stability = p["dt_sub"] * local_stability_rate(p, nmax, self.Tlat, self.Tmin,
+                                                                 self.Tmax_atoms, cap)
 
     def substeps(self, n_sub: int, t_start: float = 0.0):
         if self.stability > 2.0:
             raise ValueError("unstable substep")
         p = self.p
+        if p.get("ce_mode", 0) == 1:
+            st, es, er = substeps_local(self.rowptr, self.col, self.T, self.Tl, self.chi, self.A, n_sub,
+                                        p["dt_sub"], p["Tmax"], kappa0=p["kappa0"],
+                                        kappa_mode=p["kappa_mode"], Tlat=self.Tlat, dim_d=p["dim_d"],
+                                        S2_A2=p["zb2"], gamma=p["gamma_Ce"], cap_SI=self.cap_SI(),
+                                        G=p["G"], vatom_A3=self.vatom, depth=self.depth,
+                                        source=p.get("laser"), t_start=t_start, Tfix=self.Tfix,
+                                        weights=self.w)
+            if st < 0:
+                raise FloatingPointError(f"theta left [0,1] at substep {-st - 1}")
+            self.E_src += es
+            self.E_res_local += er
+            return
         st, es = substeps(self.rowptr, self.col, self.T, self.Tl, self.chi, self.A, n_sub,
                           p["dt_sub"], p["Tmax"], self.K, self.cG, self.VG, depth=self.depth,
                           source=p.get("laser"), Ce_SI=self.Ce, vatom_A3=self.vatom,
@@ -335,9 +422,19 @@ class OracleSim:
 
     def couple(self, v, dt_md: float):
         p = self.p
+        local = p.get("ce_mode", 0) == 1
+        if local:
+            Tb, Ab = self.T.copy(), self.A.copy()
         dKE, stopped = couple(v, self.mass, self.A, self.T, self.chi, mode=p["couple_mode"],
                               frozen=p["frozen"], seed=p["seed"], md_step=self.md_step,
                               dt_md=dt_md, gamma_fs=self.gamma_L, VC=self.VC)
+        if local:
+            # a stopped atom's unpaid energy returns to its own electrons: U_i += (A_i - dKE_i) / V
+            idx = np.nonzero(self.T != Tb)[0]
+            cap = self.cap_SI()
+            for i in idx:
+                U = ce_energy(Tb[i], p["gamma_Ce"], cap) + (Ab[i] - dKE[i]) * EV_J / (self.vatom * 1e-30)
+                self.T[i] = ce_energy_inv(U, p["gamma_Ce"], cap)
         self.E_lat += float(dKE.sum())
         self.n_stopped += stopped
         self.md_step += 1
@@ -347,6 +444,10 @@ class OracleSim:
         s = float(self.T.sum())
         E_e = self.E_base + self.VC * (s - self.ST_base) if self.VC is not None else self.E_base
         E_res = self.E_res + (self.VC * float(self.eres_T[0]) if self.VC is not None else 0.0)
+        if self.p.get("ce_mode", 0) == 1:
+            E_e = float((ce_integral(self.T, self.p["gamma_Ce"], self.cap_SI())
+                         * self.vatom * 1e-30 / EV_J).sum())
+            E_res = self.E_res_local
         return {"E_e": E_e, "E_lat": self.E_lat, "E_src": self.E_src, "E_e0": self.E_e0, "E_res": E_res,
                 "sum_T": s, "max_T": float(self.T.max()),
                 "drift": (E_e + self.E_lat - self.E_src + E_res - self.E_e0) / max(abs(self.E_e0), abs(E_e))}

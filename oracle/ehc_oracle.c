@@ -414,6 +414,116 @@ int oracle_substeps(int64_t n, const int64_t *rowptr, const int32_t *col, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* LOCAL per-atom form of Eq. HeatTransport (Sec. 2: "C_e = lambda T_e",
+ * "kappa_e = kappa0 T_e / T_lat", evaluated per atom instead of at the system
+ * means).  Every atom carries its own heat capacity C_e,i = min(gamma T_i, cap)
+ * and conductivity kappa_i = kappa0 T_i / T_lat (kappa_mode 1; kappa0 in mode 0,
+ * T_lat the system's classical lattice temperature of the MD step).  The pair
+ * rate of Eq. Kij, K_ij C_e = 2 d kappa / (Z b^2), becomes a pair energy rate
+ * with the pair-averaged kappa_ij = (kappa_i + kappa_j) / 2, so that what atom i
+ * gains from j is exactly what j loses to i:
+ *   q_ij = (2 d / S2) kappa_ij T_max f(theta_i, theta_j) w_ij           [W m^-3]
+ *   e_i  = dt [ sum_j q_ij - chi_i G (T_i - T_l,i) + S_i(t) ]           [J m^-3]
+ * The explicit step advances the electron energy density of each atom,
+ * U(T) = int_0^T C_e dT' (gamma T^2 / 2 below T_c = cap / gamma, linear above),
+ * U_i' = U(T_i) + e_i, and returns T_i' = U^{-1}(U_i') in closed form.  To first
+ * order this is C_e,i dT_i = e_i; advancing U keeps sum_i U_i exact (the energy
+ * form).  Jacobi: every atom reads the previous substep.  A_i, the energy handed
+ * to the lattice, and the laser source are those of oracle_substeps.  Border
+ * atoms (Tfix finite) keep Tfix and the energy they would have gained,
+ * V_atom dt e_i, goes to *Eres_eV.
+ * Pins: conservation of sum_i U_i; relaxation of an isolated periodic lattice
+ * to U^{-1}(mean U); small-mode decay at the lattice sum with K = 2 d kappa0 /
+ * (gamma S2 T_lat); the coupling-only closed form of gamma T dT/dt = -G (T -
+ * T_l); above the cap with constant kappa, equal to oracle_substeps. */
+static double o_ue(double T, double gamma, double cap) {
+  if (cap > 0.0 && gamma * T > cap) {
+    const double Tc = cap / gamma;
+    return 0.5 * cap * Tc + cap * (T - Tc);
+  }
+  return 0.5 * gamma * T * T;
+}
+
+static double o_ue_inv(double U, double gamma, double cap) {
+  if (cap > 0.0) {
+    const double Tc = cap / gamma;
+    const double Uc = 0.5 * cap * Tc;
+    if (U > Uc) return Tc + (U - Uc) / cap;
+  }
+  return sqrt(2.0 * U / gamma);   /* NaN for U < 0: caught by the range test */
+}
+
+double oracle_ce_energy(double T, double gamma, double cap) { return o_ue(T, gamma, cap); }
+double oracle_ce_energy_inv(double U, double gamma, double cap) { return o_ue_inv(U, gamma, cap); }
+
+int oracle_substeps_local(int64_t n, const int64_t *rowptr, const int32_t *col, double *T,
+                          const double *Tl, const uint8_t *chi, double *A, int n_sub, double dt,
+                          double Tmax, double kappa0, int kappa_mode, double Tlat, int dim_d,
+                          double S2_A2, double gamma, double cap, double G, double vatom_A3,
+                          const double *depth, const double *src, double t_start, double *E_src,
+                          const double *Tfix, double *Eres_eV, const double *pw) {
+  double *theta = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *Tn = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  if (!theta || !Tn) { free(theta); free(Tn); return -1000000; }
+  oracle_source S = {0, 0, 0, 0, 0};
+  if (src) { S.on = (src[0] != 0.0); S.fluence_Jm2 = src[1]; S.lp_A = src[2]; S.t0_fs = src[3]; S.sigma_fs = src[4]; }
+  const double dts = dt * 1.0e-15;                   /* s */
+  const double geo = 2.0 * (double)dim_d / (S2_A2 * 1.0e-20);   /* 2 d / (Z b^2)  [m^-2] */
+  const double V = vatom_A3 * 1.0e-30;               /* m^3 */
+  double esrc = 0.0, eres = 0.0;
+  int status = n_sub;
+  for (int s = 0; s < n_sub; ++s) {
+    double t = t_start + dt * (double)s;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      theta[i] = T[i] / Tmax;
+      if (!(theta[i] >= 0.0 && theta[i] <= 1.0)) bad = 1;
+    }
+    if (bad) { status = -(s + 1); break; }
+    double pulse = 0.0;
+    if (S.on) {
+      double sig_s = S.sigma_fs * 1.0e-15;
+      double dtp = (t - S.t0_fs) / S.sigma_fs;
+      pulse = S.fluence_Jm2 / (S.lp_A * 1.0e-10) * exp(-0.5 * dtp * dtp) / (sig_s * sqrt(2.0 * M_PI));
+    }
+    double esrc_step = 0.0, eres_step = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : esrc_step, eres_step)
+    for (int64_t i = 0; i < n; ++i) {
+      const double ki = kappa_mode == 1 ? kappa0 * T[i] / Tlat : kappa0;
+      double P = 0.0;                                  /* W m^-3 */
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        const int32_t j = col[p];
+        const double kj = kappa_mode == 1 ? kappa0 * T[j] / Tlat : kappa0;
+        const double kij = 0.5 * (ki + kj);
+        P += (pw ? pw[p] : 1.0) * geo * kij * Tmax * oracle_pair_flux(theta[i], theta[j]);
+      }
+      if (chi[i]) {
+        P -= G * (T[i] - Tl[i]);
+        A[i] += dts * G * V * (T[i] - Tl[i]) / O_EV;
+      }
+      if (S.on) {
+        double Sw = pulse * exp(-depth[i] / S.lp_A);
+        P += Sw;
+        esrc_step += Sw * V * dts / O_EV;
+      }
+      if (Tfix && Tfix[i] == Tfix[i]) {
+        eres_step += P * dts * V / O_EV;
+        Tn[i] = Tfix[i];
+      } else {
+        Tn[i] = o_ue_inv(o_ue(T[i], gamma, cap) + P * dts, gamma, cap);
+      }
+    }
+    esrc += esrc_step;
+    eres += eres_step;
+    memcpy(T, Tn, sizeof(double) * (size_t)n);
+  }
+  if (E_src) *E_src += esrc;
+  if (Eres_eV) *Eres_eV += eres;
+  free(theta); free(Tn);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator, from its published definition
  * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
  * SC'11): ten rounds of two 32x32->64 multiplications with the round keys
