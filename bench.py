@@ -148,6 +148,9 @@ def run_gpu(args):
     if args.rate_shell > 0:
         # distance-weighted pair rates: the general single-precision kernel
         p = dict(p, rate_shell_n=args.rate_shell)
+    if args.ce_local:
+        # LOCAL per-atom C_e / kappa_e: the general single-precision kernel on the energy state
+        p = dict(p, ce_mode=1)
     n = s.n
     tfix = None
     if args.border > 0:
@@ -263,11 +266,17 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
     ms_step = ms / args.steps
     value = job_value(ws, n, N_SUB, args.steps, ms)
     sub_launch_ms = statistics.mean(sub_ms) / N_SUB
-    # the weighted variant reads one 4-byte weight per pair on top
-    b_alg = B_ALG + (4 * N_NB if args.rate_shell > 0 else 0)
+    # the weighted variant reads one 4-byte weight per pair on top; the LOCAL form
+    # reads and writes the 4-byte high word of its energy state besides the mirror
+    b_alg = B_ALG + (4 * N_NB if args.rate_shell > 0 else 0) + (8 if args.ce_local else 0)
     achieved = b_alg * n / (sub_launch_ms * 1e-3) / 1e9
     peak, kind = _peaks()
-    traffic = _traffic_from_profile(n) if args.rate_shell == 0 else None
+    traffic = _traffic_from_profile(n) if args.rate_shell == 0 and not args.ce_local else None
+    kname = "substep_tile_kernel"
+    if args.ce_local:
+        kname = "substep_local_f32_kernel" + (" (weighted)" if args.rate_shell > 0 else "")
+    elif args.rate_shell > 0:
+        kname = "substep_f32_kernel (weighted)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -278,7 +287,11 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                                                       % (args.border, args.border_atoms)}
                                                      if args.border > 0 else {}),
                                                   **({"pair_rates": "distance-weighted, S2/(%d r^2)" % args.rate_shell}
-                                                     if args.rate_shell > 0 else {}))),
+                                                     if args.rate_shell > 0 else {}),
+                                                  **({"electron_heat_capacity": "LOCAL per-atom C_e = gamma T_i "
+                                                      "(cap 3 k_B), kappa_i = kappa0 T_i / T_lat, pair energy "
+                                                      "rates with (kappa_i + kappa_j) / 2, energy state"}
+                                                     if args.ce_local else {}))),
         "e2e": ({"value": job_value(ws, n, N_SUB, 1, e2e_ms), "unit": UNIT,
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
@@ -286,14 +299,14 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)) * args.steps * ws,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "substep_tile_kernel" if args.rate_shell == 0 else "substep_f32_kernel (weighted)",
+                     "kernel": kname,
                      "bytes_per_atom_substep": b_alg,
                      "peak_kind": kind, "substep_ms": sub_launch_ms},
         "clocks": clocks,
         "energy_drift": e["drift"],
     }
     if not args.no_cpu_baseline and ws == 1:   # the oracle's timing: one process, N = 1 only
-        line["cpu_baseline"] = cpu_baseline(args.cells)
+        line["cpu_baseline"] = cpu_baseline(args.cells, ce_local=args.ce_local)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -314,11 +327,13 @@ def _traffic_from_profile(n):
 
 # ------------------------------------------------------------ CPU oracle arm
 
-def cpu_baseline(cells: int, n_sub: int = N_SUB):
+def cpu_baseline(cells: int, n_sub: int = N_SUB, ce_local: bool = False):
     """One MD step of the same workload through the CPU oracle (neighbour build,
     lattice temperature, n_sub substeps, Langevin hand-over), all host cores."""
     import oracle
     s, p = workload(cells)
+    if ce_local:
+        p = dict(p, ce_mode=1)
     sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
     sim.set_te(s.Te)
     v = s.v.copy()
@@ -701,6 +716,8 @@ def main():
     ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--border", type=float, default=0.0)
     ap.add_argument("--rate-shell", type=int, default=0)
+    ap.add_argument("--ce-local", action="store_true",
+                    help="LOCAL per-atom C_e / kappa_e energy form (ehc_params.ce_mode = 1)")
     ap.add_argument("--hidden", type=int, default=8)
     ap.add_argument("--tau", type=float, default=0.05)
     ap.add_argument("--windows", type=int, default=20)

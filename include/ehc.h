@@ -53,6 +53,7 @@ extern "C" {
  *                   Ce_cap_kB * k_B per atomic volume
  *   kappa0, kappa_mode  kappa_e = kappa0 (mode 0) or kappa0 <T_e>/<T_lat> (mode 1, Sec. 2);
  *                   C_e and kappa_e use the system means at the start of each MD step
+ *                   (per atom with ce_mode 1)
  *   dim_d, zb2_A2   d and Z b^2 of Eq. Kij: K = 2 kappa_e d / (C_e Z b^2) [1/fs]
  *   G               electron-phonon coupling of Eq. HeatTransport [W m^-3 K^-1]
  *   eps_ke_eV       atoms with own kinetic energy below this do not exchange (Eq. Xi guard)
@@ -81,6 +82,18 @@ extern "C" {
  *                   is one rate for all pairs; the weights are computed and kept in
  *                   single precision).  Weighted contexts use the general
  *                   single-precision or the FP64 substep kernel, not the row tiles
+ *   ce_mode         0: C_e and kappa_e at the system means of the MD step (Sec. 2, as in the
+ *                   paper); 1: LOCAL per-atom form: C_e,i = min(gamma T_i, cap), kappa_i =
+ *                   kappa0 T_i / T_lat (kappa_mode 1) or kappa0, pair energy rates
+ *                   (2 d / Z b^2) kappa_ij T_max f_ij with kappa_ij = (kappa_i + kappa_j) / 2;
+ *                   each substep advances the atom's electron energy density U = int C_e dT
+ *                   and inverts it in closed form, so sum_i U_i is conserved and the ledger's
+ *                   E_e is sum_i V_atom U(T_i).  Runs on the general single-precision and the
+ *                   FP64 substep kernels; no border (ehc_set_border: EHC_E_STATE), batch,
+ *                   network or window training (EHC_E_INVAL); ehc_cheb_step and ehc_nn_step
+ *                   advance such a context with plain substeps.  The stability number is
+ *                   dt (2 n_max K + G / C_min) with K = 2 d kappa0 / (gamma Z b^2 T_lat)
+ *                   (times T_hi / T_c above the cap) or 2 d kappa0 / (Z b^2 C_e(T_min))
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after
  *                   tiles grow), 256 or 128 = fixed; both give identical results */
@@ -112,7 +125,8 @@ typedef struct ehc_params {
   int32_t use_graph;
   int32_t tile_threads;
   int32_t rate_shell_n;
-  int32_t reserved[5];
+  int32_t ce_mode;
+  int32_t reserved[4];
 } ehc_params;
 
 /* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked

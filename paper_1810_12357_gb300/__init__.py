@@ -49,7 +49,8 @@ class ehc_params(ctypes.Structure):
         ("couple_mode", ctypes.c_int32), ("frozen", ctypes.c_int32), ("dof_mode", ctypes.c_int32),
         ("flux_prec", ctypes.c_int32), ("laser_on", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("tile_threads", ctypes.c_int32), ("rate_shell_n", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("ce_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -179,6 +180,7 @@ def make_params(p: dict) -> ehc_params:
     q.flux_prec = int(p.get("flux_prec", 0))
     q.max_neighbors = int(p.get("max_neighbors", 0))
     q.rate_shell_n = int(p.get("rate_shell_n", 0))
+    q.ce_mode = int(p.get("ce_mode", 0))
     q.use_graph = int(p.get("use_graph", 1))
     q.tile_threads = int(p.get("tile_threads", 0))
     return q

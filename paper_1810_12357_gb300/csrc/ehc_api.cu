@@ -68,7 +68,7 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part};
+                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -285,6 +285,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   if (p->couple_mode != 0 && p->couple_mode != 1) return EHC_E_INVAL;
   if (p->laser_on && (!(p->laser_lp_A > 0) || !(p->laser_sigma_fs > 0))) return EHC_E_INVAL;
   if (p->rate_shell_n < 0) return EHC_E_INVAL;
+  if (p->ce_mode != 0 && p->ce_mode != 1) return EHC_E_INVAL;
   int32_t W = p->max_neighbors <= 0 ? 32 : p->max_neighbors;
   if (W > kMaxWidth || W > 255) return EHC_E_INVAL;
   for (int t = 0; t < n_types; ++t)
@@ -330,6 +331,8 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   c.mt.n_types = n_types;
   for (int t = 0; t < kMaxTypes; ++t) c.mt.m[t] = t < n_types ? mass_amu_host[t] : mass_amu_host[0];
   c.vatom = p->vatom_A3 > 0 ? p->vatom_A3 : (n_atoms > 0 ? box_A[0] * box_A[1] * box_A[2] / (double)n_atoms : 1.0);
+  c.cap_si = cap_SI(c);
+  c.local = p->ce_mode == 1;
   c.max_sub = 65536;
 
   const int64_t n = n_atoms;
@@ -353,6 +356,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   c.ps = (n + 3) / 4 * 4;
   A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * (size_t)(c.ps > 0 ? c.ps : 4)));
   A(dalloc(&c.dlo, n));
+  if (c.local) A(dalloc(&c.uhi, n));
   A(dalloc(&c.uTl, n));
   A(dalloc(&c.pulse_f, c.max_sub));
   c.nrows = (int64_t)c.g.nc[1] * c.g.nc[2];
@@ -371,7 +375,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.srcw_d, n));
   A(dalloc(&c.pulse, c.max_sub));
   A(dalloc(&c.dKE, n));
-  A(dalloc(&c.partials, kRedBlocks * 4));
+  A(dalloc(&c.partials, kRedBlocks * 6));
   A(dalloc(&c.scal, 16));
   A(dalloc(&c.err, 4));
   A(dalloc(&c.coef, 1));
@@ -466,6 +470,7 @@ int ehc_set_te(ehc_ctx *h, const double *Te_dev) {
 int ehc_set_border(ehc_ctx *h, const double *Tfix_dev) {
   if (!h) return EHC_E_INVAL;
   Ctx &c = h->c;
+  if (c.local && Tfix_dev) return EHC_E_STATE;   // the border is a form of the global C_e only
   if (!Tfix_dev || c.n == 0) {
     c.border_next = false;
     return EHC_OK;
@@ -565,8 +570,10 @@ int build_finish(Ctx &c, bool own_tiles) {
   }
   const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
   c.wsum = c.scal_host[3];
-  // ledger: close the previous MD step with its own C_e
-  if (c.VC_prev > 0) {
+  c.Tmin = -c.scal_host[4];
+  // ledger: close the previous MD step with its own C_e (the LOCAL form's E_e is
+  // evaluated directly from the temperatures)
+  if (c.VC_prev > 0 && !c.local) {
     c.E_base += c.VC_prev * (sumT - c.ST_base);
     c.ST_base = sumT;
     if (c.bres) c.E_res += c.VC_prev * c.scal_host[10] * (c.p.flux_prec == 1 ? 1.0 : c.p.Tmax_K);
@@ -591,6 +598,30 @@ int build_finish(Ctx &c, bool own_tiles) {
   c.gammaL = c.p.G * c.vatom * 1e-30 / (3.0 * kKB_J) * 1e-15;
   c.stability = c.p.dt_sub_fs * (2.0 * c.n_max * c.K + c.cG);
   c.VC_prev = c.VC;
+  if (c.local) {
+    // LOCAL form: pair energy rates (2 d / Z b^2) kappa_ij Tmax f_ij, kappa_ij the
+    // mean of kappa0 T / T_lat (or kappa0) of the two atoms, in units of gamma Tmax^2
+    const double gam = c.p.gamma_Ce, Tm = c.p.Tmax_K;
+    const double geo = 2.0 * c.p.dim_d / (c.p.zb2_A2 * 1e-20);
+    const double dts = c.p.dt_sub_fs * 1e-15;
+    double Ku;   // [1/s]
+    if (c.p.kappa_mode == 1) Ku = c.Tlat > 0 ? geo * c.p.kappa0 / (gam * c.Tlat) : HUGE_VAL;
+    else Ku = geo * c.p.kappa0 / (gam * Tm);
+    c.K = Ku * 1e-15;
+    // stability: dt (2 n_max K_hi + G / C_min) with the rate of the energy
+    // variables: kappa_mode 1, Ku (times T_hi / T_c above the cap); mode 0,
+    // 2 d kappa0 / (Z b^2 C_e(T_min))
+    const double cap = c.cap_si;
+    auto ce = [&](double T) { return (cap > 0 && gam * T > cap) ? cap : gam * T; };
+    const double Tc = cap > 0 ? cap / gam : HUGE_VAL;
+    const double Thi = c.scal_host[1];
+    double Khi;
+    if (c.p.kappa_mode == 1) Khi = Ku * (Thi > Tc ? Thi / Tc : 1.0);
+    else Khi = c.Tmin > 0 ? geo * c.p.kappa0 / ce(c.Tmin) : HUGE_VAL;
+    const double cmin = ce(c.Tmin);
+    c.cG = (cmin > 0 ? c.p.G / cmin : HUGE_VAL) * 1e-15;
+    c.stability = c.p.dt_sub_fs * (2.0 * c.n_max * Khi * 1e-15 + c.cG);
+  }
   StepCoef &cf = *c.coef_host;
   cf.dt = c.p.dt_sub_fs;
   cf.dtTK = c.p.dt_sub_fs * c.p.Tmax_K * c.K;
@@ -604,6 +635,25 @@ int build_finish(Ctx &c, bool own_tiles) {
   cf.dtcGn_f = (float)(c.p.dt_sub_fs * c.cG / c.p.Tmax_K);
   cf.Tmax_f = (float)c.p.Tmax_K;
   cf.pad[0] = cf.pad[1] = cf.pad[2] = 0.f;
+  {
+    const double gam = c.p.gamma_Ce, Tm = c.p.Tmax_K;
+    const double th = c.p.Tref_K / Tm;
+    const double thc = c.cap_si > 0 ? c.cap_si / gam / Tm : 0.0;
+    auto u = [&](double t) { return (thc > 0 && t > thc) ? thc * t - 0.5 * thc * thc : 0.5 * t * t; };
+    cf.dtKu = c.local ? c.p.dt_sub_fs * c.K : 0.0;
+    cf.dtgu = c.p.dt_sub_fs * 1e-15 * c.p.G / (gam * Tm * Tm);
+    cf.thc = thc;
+    cf.u_ref = u(th);
+    cf.dtKu_f = (float)cf.dtKu;
+    cf.dtgu_f = (float)cf.dtgu;
+    cf.thc_f = (float)thc;
+    cf.inv_thc_f = thc > 0 ? (float)(1.0 / thc) : 0.f;
+    cf.wc_f = thc > 0 ? (float)(0.5 * thc * thc - cf.u_ref) : 0.f;
+    cf.thsq_f = (float)(th * th);
+    cf.kmode = c.p.kappa_mode == 1 ? 1 : 0;
+    cf.pad2 = 0.f;
+    cf.dtVGu = (double)cf.dtgu_f * c.vatom * 1e-30 * gam * Tm * Tm / kEV_J;
+  }
   CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
   if (own_tiles) CK(upload_reps(c));   // a batch keeps its own table of every replica
   c.built = true;
@@ -674,6 +724,18 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
       for (int k = 0; k < chunk; ++k) {
         const double t = t_fs + c.p.dt_sub_fs * (double)(done + k);
         const double u = (t - c.p.laser_t0_fs) / sig;
+        if (c.local) {
+          // LOCAL form: the source's energy density in units of gamma Tmax^2 per fs
+          const double gT2 = c.p.gamma_Ce * c.p.Tmax_K * c.p.Tmax_K;
+          const double rate = S0 * std::exp(-0.5 * u * u) / gT2 * 1e-15;
+          c.pulse_host[k] = rate;
+          const float cf = (float)(c.p.dt_sub_fs * rate);
+          c.pulse_f_host[k] = cf;
+          const double eV_per_u = c.vatom * 1e-30 * gT2 / kEV_J;
+          if (c.p.flux_prec == 1) c.E_src += eV_per_u * c.p.dt_sub_fs * rate * c.wsum;
+          else c.E_src += eV_per_u * (double)cf * c.wsum;
+          continue;
+        }
         const double rate = S0 * std::exp(-0.5 * u * u) / c.Ce * 1e-15;  // K / fs at depth 0
         c.pulse_host[k] = rate;
         // the single-precision path adds the exact product of these two floats per atom
@@ -758,6 +820,7 @@ int ehc_energy(ehc_ctx *h, ehc_energy_t *out) {
   const double sumT = c.scal_host[0];
   std::memset(out, 0, sizeof(*out));
   out->E_e = c.E_base + (c.VC_prev > 0 ? c.VC_prev * (sumT - c.ST_base) : 0.0);
+  if (c.local) out->E_e = c.scal_host[5] * c.vatom * 1e-30 / kEV_J;   // sum_i V_atom U(T_i)
   out->E_lat = c.scal_host[8];
   out->E_src = c.E_src;
   out->E_e0 = c.E_e0;
@@ -1059,7 +1122,7 @@ int ehc_batch_create(const ehc_params *p, int32_t n_rep, const int64_t *n_atoms_
   if (!p || n_rep <= 0 || !n_atoms_host || !boxes_host || !periodic || !mass_amu_host || !out) return EHC_E_INVAL;
   *out = nullptr;
   // batches use the row tiles: single precision, no source, uniform pair rates
-  if (p->laser_on || p->flux_prec != 0 || p->rate_shell_n != 0) return EHC_E_INVAL;
+  if (p->laser_on || p->flux_prec != 0 || p->rate_shell_n != 0 || p->ce_mode != 0) return EHC_E_INVAL;
   ehc_batch *b = new (std::nothrow) ehc_batch();
   if (!b) return EHC_E_NOMEM;
   b->p = *p;
@@ -1784,7 +1847,7 @@ int ehc_cheb_train_step(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, const d
                         int32_t loss_power, float *loss_host, float *grad_host) {
   NvtxRange nvtx_range("ehc_cheb_train_step");
   if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || !(lr >= 0.0f) ||
-      (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0)
+      (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0 || hc->c.local)
     return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1815,7 +1878,7 @@ int ehc_cheb_train_rollout(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, cons
                            float lr, int32_t loss_power, float *loss_host, float *grad_host) {
   NvtxRange nvtx_range("ehc_cheb_train_rollout");
   if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Ttar_dev)) || n_win < 1 || n_win > 64 ||
-      !(lr >= 0.0f) || (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0)
+      !(lr >= 0.0f) || (loss_power != 2 && loss_power != 4 && loss_power != 8) || hc->c.p.rate_shell_n != 0 || hc->c.local)
     return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1887,7 +1950,7 @@ int ehc_cheb_train_rollout(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, cons
 }
 
 int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t iters, double *x_out) {
-  if (!w || !hc || hc->c.n != w->n || iters < 1 || iters > 100000 || hc->c.p.rate_shell_n != 0) return EHC_E_INVAL;
+  if (!w || !hc || hc->c.n != w->n || iters < 1 || iters > 100000 || hc->c.p.rate_shell_n != 0 || hc->c.local) return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
   if (c.n == 0) {
@@ -1920,7 +1983,7 @@ int ehc_cheb_spectrum(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, int32_t i
 }
 
 int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *hc, const double *Tin_dev, double *Tout_dev) {
-  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Tout_dev)) || hc->c.p.rate_shell_n != 0)
+  if (!w || !hc || hc->c.n != w->n || (hc->c.n > 0 && (!Tin_dev || !Tout_dev)) || hc->c.p.rate_shell_n != 0 || hc->c.local)
     return EHC_E_INVAL;
   Ctx &c = hc->c;
   if (!c.built) return EHC_E_STATE;
@@ -1975,7 +2038,7 @@ int ehc_nn_create(ehc_ctx *hc, int32_t hidden, int32_t n_window, double sigma, e
   if (!hc || !out || (hidden != 8 && hidden != 16) || n_window < 1 || !(sigma > 0)) return EHC_E_INVAL;
   *out = nullptr;
   Ctx &c = hc->c;
-  if (c.p.flux_prec != 0 || c.p.laser_on || c.p.rate_shell_n != 0) return EHC_E_INVAL;
+  if (c.p.flux_prec != 0 || c.p.laser_on || c.p.rate_shell_n != 0 || c.local) return EHC_E_INVAL;
   ehc_nn *nn = new (std::nothrow) ehc_nn();
   if (!nn) return EHC_E_NOMEM;
   nn->H = hidden;
@@ -2092,8 +2155,8 @@ int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_
   int r = ensure_t(c);
   if (r) return r;
   if (c.n == 0) return EHC_OK;
-  if (c.has_border) {
-    // the network knows no border: plain substeps
+  if (c.has_border || c.local) {
+    // the network knows neither a border nor the LOCAL form: plain substeps
     nn->windows += 1;
     nn->fallbacks += 1;
     if (fell_back) *fell_back = 1;

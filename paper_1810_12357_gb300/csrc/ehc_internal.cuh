@@ -99,7 +99,30 @@ struct StepCoef {
   float dtcGn_f;   // dt * G / (C_e Tmax)
   float Tmax_f;
   float pad[3];
+  // LOCAL per-atom C_e / kappa_e form (ce_mode 1).  State: the electron energy
+  // density in units of gamma Tmax^2, u(theta) = theta^2 / 2 below theta_c =
+  // T_c / Tmax and theta_c theta - theta_c^2 / 2 above (no cap: theta_c = 0).
+  double dtKu;     // dt * 2 d kappa0 / (Z b^2 gamma T_lat) (kappa_mode 1) or / (... gamma Tmax) (mode 0) [1]
+  double dtgu;     // dt * G / (gamma Tmax^2) [1/K]
+  double thc;      // theta_c (0: no cap)
+  double u_ref;    // u(Tref / Tmax): the single-precision state is w = u - u_ref
+  float dtKu_f, dtgu_f, thc_f, inv_thc_f;
+  float wc_f;      // w at the cap, u(theta_c) - u_ref
+  float thsq_f;    // (Tref / Tmax)^2
+  int32_t kmode;   // 1: kappa_ij / kappa_scale = (theta_i + theta_j) / 2; 0: 1
+  float pad2;
+  double dtVGu;    // (double)dtgu_f * V_atom gamma Tmax^2 [eV/K]: the lattice's share, single-precision path
 };
+
+// u(theta) and its inverse of the LOCAL form (FP64): energy density per gamma Tmax^2
+__device__ __forceinline__ double ue_of(double th, double thc) {
+  if (thc > 0.0 && th > thc) return thc * th - 0.5 * thc * thc;
+  return 0.5 * th * th;
+}
+__device__ __forceinline__ double ue_inv(double u, double thc) {
+  if (thc > 0.0 && u > 0.5 * thc * thc) return (u + 0.5 * thc * thc) / thc;
+  return sqrt(2.0 * u);   // NaN for u < 0: caught by the range checks
+}
 
 // Row tiles: a row is the run of cells with the same (cy, cz); its atoms are a
 // contiguous range of the sorted order.  Every neighbour of an atom lies in the
@@ -286,6 +309,10 @@ struct Ctx {
   int tcur = 0;
   float *dmir[2] = {nullptr, nullptr};  // hi part of delta = (T - Tref)/Tmax, double-buffered
   float *dlo = nullptr;          // lo part of delta (float-float state of the FP32 path)
+  // LOCAL form (ce_mode 1), single-precision path: the state is the float pair
+  // (uhi, dlo) of w = u - u_ref; dmir holds delta = theta - Tref/Tmax rebuilt from it
+  bool local = false;
+  float *uhi = nullptr;
   float *uTl = nullptr;          // Tref - T_l,i (NaN: atom below the guard)
   double *abuf[2] = {nullptr, nullptr};
   double *A = nullptr;           // one of abuf
@@ -301,7 +328,7 @@ struct Ctx {
   float *pulse_f_host = nullptr;
   int32_t max_sub = 0;
   double *dKE = nullptr;
-  double *partials = nullptr;    // [kRedBlocks * 4]
+  double *partials = nullptr;    // [kRedBlocks * 6]
   double *scal = nullptr;        // device scalars [16]
   double *scal_host = nullptr;   // pinned mirror [16]
   int32_t *err = nullptr;        // device error word
@@ -345,6 +372,8 @@ struct Ctx {
 
   // ledger (host, FP64)
   double E_e0 = 0, E_base = 0, ST_base = 0, VC_prev = -1, E_src = 0;
+  double Tmin = 0;       // smallest T_e at the build (LOCAL form's stability number)
+  double cap_si = 0;     // cap of C_e per unit volume [J m^-3 K^-1] (0: none)
 
   // captured substep loops, keyed by everything a launch bakes in
   // fixed-temperature border: tfix_orig (caller order, NaN = free) set by

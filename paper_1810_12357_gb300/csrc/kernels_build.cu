@@ -458,18 +458,31 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
   return r;
 }
 
-// partial sums per block: [0] sum T, [1] max T, [2] sum KE (eV), [3] sum srcw
+// electronic energy per unit volume: int_0^T min(gamma T', cap) dT' [J m^-3]
+__device__ __forceinline__ double ce_integral(double t, double gamma, double cap) {
+  if (cap > 0.0 && gamma * t > cap) {
+    const double Tc = cap / gamma;
+    return 0.5 * cap * Tc + cap * (t - Tc);
+  }
+  return 0.5 * gamma * t * t;
+}
+
+// partial sums per block (stride kGlob): [0] sum T, [1] max T, [2] sum KE (eV),
+// [3] sum srcw, [4] max(-T), [5] sum of the energy integral if gamma > 0
+constexpr int kGlob = 6;
 __global__ void globals_partial(int64_t n, const double *__restrict__ T, const VelQ *__restrict__ v_s,
                                 const int8_t *__restrict__ type_s, MassTable mt,
-                                const float *__restrict__ srcw, const double *__restrict__ srcw_d,
-                                double *__restrict__ part) {
+                                const float *__restrict__ srcw, const double *__restrict__ srcw_d, double gamma,
+                                double cap, double *__restrict__ part) {
   __shared__ double sh[32];
-  double sT = 0, mT = -1e300, sK = 0, sW = 0;
+  double sT = 0, mT = -1e300, sK = 0, sW = 0, mN = -1e300, sE = 0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     double t = T[s];
     sT += t;
     mT = fmax(mT, t);
+    mN = fmax(mN, -t);
+    if (gamma > 0.0) sE += ce_integral(t, gamma, cap);
     if (v_s) sK += 0.5 * mt.m[type_s[s]] * v_s[s].w * kMVV;
     if (srcw_d) sW += srcw_d[s];
     else if (srcw) sW += (double)srcw[s];
@@ -478,61 +491,73 @@ __global__ void globals_partial(int64_t n, const double *__restrict__ T, const V
   double r1 = block_max(mT, sh);
   double r2 = block_sum(sK, sh);
   double r3 = block_sum(sW, sh);
+  double r4 = block_max(mN, sh);
+  double r5 = block_sum(sE, sh);
   if (threadIdx.x == 0) {
-    part[blockIdx.x * 4 + 0] = r0;
-    part[blockIdx.x * 4 + 1] = r1;
-    part[blockIdx.x * 4 + 2] = r2;
-    part[blockIdx.x * 4 + 3] = r3;
+    double *o = part + (int64_t)blockIdx.x * kGlob;
+    o[0] = r0;
+    o[1] = r1;
+    o[2] = r2;
+    o[3] = r3;
+    o[4] = r4;
+    o[5] = r5;
   }
 }
 
 __global__ void globals_final(int nb, const double *__restrict__ part, double *__restrict__ out) {
   __shared__ double sh[32];
-  double sT = 0, mT = -1e300, sK = 0, sW = 0;
+  double sT = 0, mT = -1e300, sK = 0, sW = 0, mN = -1e300, sE = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    sT += part[b * 4 + 0];
-    mT = fmax(mT, part[b * 4 + 1]);
-    sK += part[b * 4 + 2];
-    sW += part[b * 4 + 3];
+    const double *q = part + (int64_t)b * kGlob;
+    sT += q[0];
+    mT = fmax(mT, q[1]);
+    sK += q[2];
+    sW += q[3];
+    mN = fmax(mN, q[4]);
+    sE += q[5];
   }
   double r0 = block_sum(sT, sh);
   double r1 = block_max(mT, sh);
   double r2 = block_sum(sK, sh);
   double r3 = block_sum(sW, sh);
+  double r4 = block_max(mN, sh);
+  double r5 = block_sum(sE, sh);
   if (threadIdx.x == 0) {
     out[0] = r0;
     out[1] = r1;
     out[2] = r2;
     out[3] = r3;
+    out[4] = r4;
+    out[5] = r5;
   }
 }
 
-// initial electronic energy per unit volume: int_0^T min(gamma T', cap) dT'
-// partials: [0] sum T, [1] max T, [2] sum of the integral [J m^-3], [3] unused
+// initial electronic energy: partials [0] sum T, [1] max T, [2] sum of the
+// energy integral [J m^-3], [3] 0, [4] max(-T), [5] the integral again
 __global__ void seed_partial(int64_t n, const double *__restrict__ T, double gamma, double cap,
                              double *__restrict__ part) {
   __shared__ double sh[32];
-  double sT = 0, mT = -1e300, sE = 0;
+  double sT = 0, mT = -1e300, sE = 0, mN = -1e300;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const double t = T[s];
     sT += t;
     mT = fmax(mT, t);
-    if (cap > 0.0 && gamma * t > cap) {
-      const double Tc = cap / gamma;
-      sE += 0.5 * cap * Tc + cap * (t - Tc);
-    } else {
-      sE += 0.5 * gamma * t * t;
-    }
+    mN = fmax(mN, -t);
+    sE += ce_integral(t, gamma, cap);
   }
   double r0 = block_sum(sT, sh);
   double r1 = block_max(mT, sh);
   double r2 = block_sum(sE, sh);
+  double r4 = block_max(mN, sh);
   if (threadIdx.x == 0) {
-    part[blockIdx.x * 4 + 0] = r0;
-    part[blockIdx.x * 4 + 1] = r1;
-    part[blockIdx.x * 4 + 2] = r2;
-    part[blockIdx.x * 4 + 3] = 0.0;
+    double *o = part + (int64_t)blockIdx.x * kGlob;
+    o[0] = r0;
+    o[1] = r1;
+    o[2] = r2;
+    o[3] = 0.0;
+    o[4] = r4;
+    o[5] = r2;
   }
 }
 
@@ -626,14 +651,15 @@ cudaError_t launch_globals(Ctx &c) {
   const bool laser = c.p.laser_on && c.have_depth;
   globals_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(
       c.n, c.T[c.tcur], c.v_s, c.type_s, c.mt, (laser && c.p.flux_prec == 0) ? c.srcw : nullptr,
-      (laser && c.p.flux_prec == 1) ? c.srcw_d : nullptr, c.partials);
+      (laser && c.p.flux_prec == 1) ? c.srcw_d : nullptr, c.local ? c.p.gamma_Ce : 0.0, c.cap_si, c.partials);
   globals_final<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ledger(Ctx &c) {
   globals_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.T[c.tcur], nullptr, nullptr, c.mt, nullptr,
-                                                            nullptr, c.partials);
+                                                            nullptr, c.local ? c.p.gamma_Ce : 0.0, c.cap_si,
+                                                            c.partials);
   globals_final<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal);
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ namespace {
 
 constexpr double kMVV = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;  // amu (A/fs)^2 -> eV
 constexpr double kKB = 8.617333262e-5;
+constexpr double kEVJ = 1.602176634e-19;   // J per eV
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // multiplications (high and low halves) with Weyl-sequence key increments.
@@ -79,7 +80,7 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
                               double *__restrict__ A,
                               double *__restrict__ T, double *__restrict__ v, double *__restrict__ dKE,
                               int mode, int frozen, uint64_t seed, uint64_t md_step, double e1, double inv_VC,
-                              unsigned long long *__restrict__ n_stopped) {
+                              unsigned long long *__restrict__ n_stopped, double thc, double inv_Tmax) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double Ai = A[s];
@@ -123,7 +124,12 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   // the new kinetic energy is the target up to the rounding of the scaling
   const double d = target - K0;
   dKE[s] = d;
-  if (target == 0.0) T[s] += (Ai - d) * inv_VC;
+  if (target == 0.0) {
+    // the unpaid part returns to the atom's electrons: T += dE / (V_atom C_e), or in
+    // the LOCAL form (inv_Tmax > 0) u += dE / (V_atom gamma Tmax^2) with inv_VC that factor
+    if (inv_Tmax > 0.0) T[s] = ue_inv(ue_of(T[s] * inv_Tmax, thc) + (Ai - d) * inv_VC, thc) / inv_Tmax;
+    else T[s] += (Ai - d) * inv_VC;
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -213,7 +219,10 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
   if (c.n > 0)
     couple_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
         c.n, c.perm, c.type_s, c.mt, kv, kv0, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode, c.p.frozen, c.p.seed,
-        (uint64_t)c.md_step, e1, 1.0 / c.VC, reinterpret_cast<unsigned long long *>(c.scal + 9));
+        (uint64_t)c.md_step, e1,
+        c.local ? kEVJ / (c.vatom * 1e-30 * c.p.gamma_Ce * c.p.Tmax_K * c.p.Tmax_K) : 1.0 / c.VC,
+        reinterpret_cast<unsigned long long *>(c.scal + 9), c.local ? c.coef_host->thc : 0.0,
+        c.local ? 1.0 / c.p.Tmax_K : 0.0);
   sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
   sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
   return cudaGetLastError();

@@ -79,6 +79,15 @@ __device__ __forceinline__ float pair_acc(float F, float di, float dj, float th,
   return fmaf(D, fmaf(-P, S, C), F);
 }
 
+// (F, Fc) += t: TwoSum of F and t, the rounding error accumulated in Fc
+__device__ __forceinline__ void two_sum_acc(float &F, float &Fc, float t) {
+  const float s = __fadd_rn(F, t);
+  const float bb = __fsub_rn(s, F);
+  const float e = __fadd_rn(__fsub_rn(F, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+  Fc = __fadd_rn(Fc, e);
+  F = s;
+}
+
 // exact float -> double by bit assembly on the integer pipes (zero and
 // subnormal inputs give a signed zero); keeps the FP64 pipe for the ledger
 __device__ __forceinline__ double f2d(float f) {
@@ -150,7 +159,7 @@ __device__ __forceinline__ float update_atom(int64_t s, float di, float li, floa
   float p = 0.0f, e = 0.0f;
   if (LASER) {
     const float c = o.pulse_f[k], w = o.srcw[s];
-    p = c * w;
+    p = __fmul_rn(c, w);                 // not fused into the sums below
     e = fmaf(c, w, -p);                  // p + e == c * w exactly
     ff_add(h, l, p);
     ff_add(h, l, e);
@@ -584,6 +593,162 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   update_atom<LASER, true>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k, fixed);
 }
 
+// LOCAL per-atom C_e / kappa_e form, single precision (one thread per atom).
+// The state is each atom's electron energy density in units of gamma Tmax^2,
+// held as the float pair (uhi, lo) of w = u - u_ref; hin / hout hold the mirror
+// delta = theta - theta_ref the neighbours read, rebuilt from w after the update:
+//   below the cap  theta = sqrt(theta_ref^2 + 2 w), delta = 2 w / (theta + theta_ref)
+//   above it       theta = theta_c + (w - w_c) / theta_c
+// Pair term kappa_ij f_ij with kappa_ij / kappa_scale = (theta_i + theta_j) / 2
+// (kappa_mode 1) or 1: the mean is formed from fl(theta_i + theta_j), which both
+// atoms compute alike, and multiplies the already rounded fl(Delta B), so the
+// two atoms' terms t_ij are exact negatives.  They are summed with TwoSum (the
+// sum and its rounding errors), and dt Ku times that sum enters the float-pair
+// state as an exact two-float product, as does the coupling: sum_i w_i changes
+// only by the second-order rounding of the compensation (single-precision
+// rounding of the accumulation and of the product would leave a bias of
+// about 1e-11 of the energy per substep on a hot track core).
+//   w_i += dt Ku sum_j kappa_ij f_ij w_ij - chi_i dt G/(gamma Tmax^2) (T_i - T_l,i) + source
+template <bool LASER>
+__global__ void __launch_bounds__(256) substep_local_f32_kernel(
+    int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
+    const float *__restrict__ hin, float *__restrict__ hout, float *__restrict__ uhi, float *__restrict__ lo,
+    double *__restrict__ A, const float *__restrict__ uTl, const float *__restrict__ srcw,
+    const float *__restrict__ pulse_f, int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err,
+    const float *__restrict__ wgt) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const float th = cf->th_ref;
+  const bool km = cf->kmode != 0;
+  const int c = cnt[s];
+  const float di = hin[s];
+  const float ai = th + di, m2ai = -2.0f * ai;
+  float F = 0.0f, Fc = 0.0f;
+  const int32_t *np = nbr + s;
+  const float *wp = wgt ? wgt + s : nullptr;
+  int j = 0;
+  for (; j + 6 <= c; j += 6) {
+    int32_t t[6];
+    float dj[6], wj[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      t[u] = checked_index(__ldg(np + (int64_t)(j + u) * n), n, err);
+      wj[u] = wp ? __ldg(wp + (int64_t)(j + u) * n) : 1.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const float fij = pair_acc<0>(0.0f, di, dj[u], th, ai, m2ai);
+      const float kij = km ? 0.5f * (ai + (th + dj[u])) : 1.0f;
+      two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj[u]), fij));
+    }
+  }
+  for (; j < c; ++j) {
+    const float dj = __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err));
+    const float wj = wp ? __ldg(wp + (int64_t)j * n) : 1.0f;
+    const float fij = pair_acc<0>(0.0f, di, dj, th, ai, m2ai);
+    const float kij = km ? 0.5f * (ai + (th + dj)) : 1.0f;
+    two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj), fij));
+  }
+  const float Ku = cf->dtKu_f;
+  const float p0 = __fmul_rn(Ku, F);
+  const float e0 = fmaf(Ku, F, -p0) + Ku * Fc;   // the product's error and the compensation
+  const float ui = uTl[s];
+  const bool chi = (ui == ui);
+  float dT = 0.0f;
+  float h = uhi[s], l = lo[s];
+  ff_add(h, l, p0);
+  ff_add(h, l, e0);
+  if (chi) {
+    dT = fmaf(cf->Tmax_f, di, ui);        // T_i - T_l,i
+    const float g = -cf->dtgu_f;
+    const float q0 = __fmul_rn(g, dT);
+    ff_add(h, l, q0);
+    ff_add(h, l, fmaf(g, dT, -q0));       // exactly dt G (T_i - T_l,i) / (gamma Tmax^2) in two parts
+  }
+  if (LASER) {
+    const float cc = pulse_f[k], w = srcw[s];
+    const float p = __fmul_rn(cc, w);
+    ff_add(h, l, p);
+    ff_add(h, l, fmaf(cc, w, -p));        // the exact product, in two parts
+  }
+  uhi[s] = h;
+  lo[s] = l;
+  // the lattice gets what the electrons lost: the same single-precision coefficient
+  if (chi) A[s] = fma(cf->dtVGu, f2d(dT), A[s]);
+  float dn;
+  if (cf->thc_f > 0.0f && h > cf->wc_f) {
+    dn = fmaf(h - cf->wc_f, cf->inv_thc_f, cf->thc_f - th);
+  } else {
+    const float q = fmaf(2.0f, h, cf->thsq_f);
+    dn = (2.0f * h) / (sqrtf(q) + th);    // NaN if the energy went negative
+  }
+  hout[s] = dn;
+  const float tn = th + dn;
+  if (!(tn >= 0.0f && tn <= 1.0f)) atomicOr(err, ERR_RANGE);
+}
+
+// LOCAL form, double precision: u(theta_i) + du -> theta by the closed-form inverse
+template <bool LASER>
+__global__ void __launch_bounds__(256) substep_local_f64_kernel(
+    int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
+    const double *__restrict__ Tin, double *__restrict__ Tout, double *__restrict__ A,
+    const double *__restrict__ Tl, const double *__restrict__ srcw, const double *__restrict__ pulse, int k,
+    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double inv = cf->invTmax;
+  const bool km = cf->kmode != 0;
+  const int c = cnt[s];
+  const double Ti = Tin[s];
+  const double ti = Ti * inv;
+  double F = 0.0;
+  for (int j = 0; j < c; ++j) {
+    const int32_t t = checked_index(__ldg(nbr + (int64_t)j * n + s), n, err);
+    const double tj = __ldg(Tin + t) * inv;
+    const bool lo = (ti < tj) || (ti == tj && s < t);
+    const double a = lo ? ti : tj, b = lo ? tj : ti;
+    const double E = exp(a - b);
+    const double phi = b * (1.0 - a) * E - a * (1.0 - b) / E;
+    const double kij = km ? 0.5 * (a + b) : 1.0;
+    const double w = wgt ? (double)__ldg(wgt + (int64_t)j * n + s) : 1.0;
+    F += w * kij * (lo ? phi : -phi);
+  }
+  double du = cf->dtKu * F;
+  const double tl = Tl[s];
+  if (tl >= 0.0) {
+    const double d = Ti - tl;
+    du -= cf->dtgu * d;
+    A[s] += cf->dtVG * d;
+  }
+  if (LASER) du += cf->dt * pulse[k] * srcw[s];
+  const double th = ue_inv(ue_of(ti, cf->thc) + du, cf->thc);
+  Tout[s] = th / inv;
+  if (!(th >= 0.0 && th <= 1.0)) atomicOr(err, ERR_RANGE);
+}
+
+// LOCAL form: T (FP64) -> the state w = u(theta) - u_ref as a float pair and the mirror
+__global__ void split_local_kernel(int64_t n, const double *__restrict__ T, double Tref, double invTmax,
+                                   double thc, double u_ref, float *__restrict__ mir, float *__restrict__ uhi,
+                                   float *__restrict__ lo) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double w = ue_of(T[s] * invTmax, thc) - u_ref;
+  const float h = (float)w;
+  uhi[s] = h;
+  lo[s] = (float)(w - (double)h);
+  mir[s] = (float)((T[s] - Tref) * invTmax);
+}
+
+// LOCAL form: state -> T (FP64)
+__global__ void merge_local_kernel(int64_t n, const float *__restrict__ uhi, const float *__restrict__ lo,
+                                   double thc, double u_ref, double Tmax, double *__restrict__ T) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  T[s] = Tmax * ue_inv(u_ref + ((double)uhi[s] + (double)lo[s]), thc);
+}
+
 // T (FP64) -> hi + lo of delta = (T - Tref) / Tmax
 __global__ void split_kernel(int64_t n, const double *__restrict__ T, double Tref, double invTmax,
                              float *__restrict__ hi, float *__restrict__ lo) {
@@ -654,11 +819,17 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // table holds at most 32 neighbours per atom
 bool tile_path(const Ctx &c) {
   const int w = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
-  return c.p.flux_prec == 0 && c.p.rate_shell_n == 0 && c.W <= 32 && c.nwork > 0 &&
+  return c.p.flux_prec == 0 && c.p.rate_shell_n == 0 && !c.local && c.W <= 32 && c.nwork > 0 &&
          c.staged_max <= c.tile_floats && c.tile_grid[w] > 0;
 }
 
 cudaError_t launch_split(Ctx &c, cudaStream_t st) {
+  if (c.n > 0 && c.local) {
+    const StepCoef &cf = *c.coef_host;
+    split_local_kernel<<<nblk(c.n, 256), 256, 0, st>>>(c.n, c.T[c.tcur], c.p.Tref_K, 1.0 / c.p.Tmax_K, cf.thc,
+                                                       cf.u_ref, c.dmir[c.parity], c.uhi, c.dlo);
+    return cudaGetLastError();
+  }
   if (c.n > 0)
     split_kernel<<<nblk(c.n, 256), 256, 0, st>>>(c.n, c.T[c.tcur], c.p.Tref_K, 1.0 / c.p.Tmax_K, c.dmir[c.parity],
                                                  c.dlo);
@@ -666,6 +837,12 @@ cudaError_t launch_split(Ctx &c, cudaStream_t st) {
 }
 
 cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t st) {
+  if (c.n > 0 && c.local) {
+    const StepCoef &cf = *c.coef_host;
+    merge_local_kernel<<<nblk(c.n, 256), 256, 0, st>>>(c.n, c.uhi, c.dlo, cf.thc, cf.u_ref, c.p.Tmax_K,
+                                                       c.T[c.tcur]);
+    return cudaGetLastError();
+  }
   if (c.n > 0)
     merge_kernel<<<nblk(c.n, 256), 256, 0, st>>>(c.n, c.dmir[parity], c.dlo, c.p.Tref_K, c.p.Tmax_K, c.T[c.tcur]);
   return cudaGetLastError();
@@ -677,6 +854,27 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
   const int32_t n = (int32_t)c.n;
   const bool laser = c.p.laser_on && c.have_depth;
+  if (c.local) {
+    if (c.p.flux_prec == 1) {
+      const double *Tin = c.T[parity];
+      double *Tout = c.T[parity ^ 1];
+      if (laser)
+        substep_local_f64_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d,
+                                                                     c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt);
+      else
+        substep_local_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d,
+                                                                      c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt);
+    } else if (laser) {
+      substep_local_f32_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity],
+                                                                   c.dmir[parity ^ 1], c.uhi, c.dlo, c.A, c.uTl,
+                                                                   c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
+    } else {
+      substep_local_f32_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity],
+                                                                    c.dmir[parity ^ 1], c.uhi, c.dlo, c.A, c.uTl,
+                                                                    c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
+    }
+    return cudaGetLastError();
+  }
   if (c.p.flux_prec == 1) {
     const double *Tin = c.T[parity];
     double *Tout = c.T[parity ^ 1];
