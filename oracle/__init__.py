@@ -65,6 +65,12 @@ def lib():
         L.oracle_ce_energy.restype = dbl
         L.oracle_ce_energy_inv.argtypes = [dbl, dbl, dbl]
         L.oracle_ce_energy_inv.restype = dbl
+        L.oracle_forces.argtypes = [i64, P, P, P, P, P, dbl, dbl, dbl, dbl, P, P]
+        L.oracle_forces.restype = None
+        L.oracle_morse.argtypes = [dbl, dbl, dbl, dbl, P, P]
+        L.oracle_morse.restype = None
+        L.oracle_kick.argtypes = [i64, P, P, P, dbl]
+        L.oracle_kick.restype = None
         L.oracle_pair_weights.argtypes = [i64, P, P, P, P, P, dbl, i32, P]
         L.oracle_pair_weights.restype = None
         L.oracle_substeps.restype = ctypes.c_int
@@ -73,7 +79,7 @@ def lib():
         L.oracle_gauss3.argtypes = [u64, u64, u64, P]
         L.oracle_gauss3.restype = None
         L.oracle_couple.argtypes = [i64, P, P, P, P, P, ctypes.c_int, ctypes.c_int, u64, u64,
-                                    dbl, dbl, dbl, P]
+                                    dbl, dbl, dbl, P, dbl, dbl]
         L.oracle_couple.restype = i64
         L.oracle_num_threads.restype = ctypes.c_int
         L.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -261,13 +267,38 @@ def gauss3(atom_id: int, step: int, seed: int):
     return g
 
 
-def couple(v, mass_of_atom, A, T, chi, *, mode, frozen, seed, md_step, dt_md, gamma_fs, VC):
+def couple(v, mass_of_atom, A, T, chi, *, mode, frozen, seed, md_step, dt_md, gamma_fs, VC,
+           stop_beta=0.0, stop_ecut=0.0):
     n = T.shape[0]
     dKE = np.empty(n)
     stopped = lib().oracle_couple(n, _p(v), _p(mass_of_atom), _p(A), _p(T), _p(chi), int(mode),
                                   int(frozen), int(seed), int(md_step), float(dt_md),
-                                  float(gamma_fs), float(VC), _p(dKE))
+                                  float(gamma_fs), float(VC), _p(dKE), float(stop_beta), float(stop_ecut))
     return dKE, int(stopped)
+
+
+def morse(r: float, D: float, alpha: float, r0: float):
+    """(phi, phi') of the unshifted Morse pair potential [eV, eV/A]."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_morse(float(r), float(D), float(alpha), float(r0), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def forces(x, box, periodic, rowptr, col, *, D, alpha, r0, rc):
+    """Shifted-force Morse forces [N, 3] (eV/A) and per-atom energies [N] (eV)."""
+    q, Lq = quantize(x, box, periodic)
+    n = x.shape[0]
+    F = np.zeros((n, 3))
+    E = np.zeros(n)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    lib().oracle_forces(n, _p(rowptr), _p(col), _p(q), _p(Lq), _p(per), float(D), float(alpha), float(r0),
+                        float(rc), _p(F), _p(E))
+    return F, E
+
+
+def kick(v, F, mass_of_atom, dt: float):
+    """v += dt F / m in place (velocity-Verlet half kick with dt = half the step)."""
+    lib().oracle_kick(v.shape[0], _p(v), _p(F), _p(mass_of_atom), float(dt))
 
 
 # --------------------------------------------------------------------------
@@ -366,6 +397,7 @@ class OracleSim:
             self.E_res += self.VC * float(self.eres_T[0])
             self.eres_T[0] = 0.0
         self.rowptr, self.col = neighbors(x, self.box, self.per, p["rc"])
+        self.x_build = np.ascontiguousarray(x, dtype=np.float64).copy()
         ns = int(p.get("rate_shell_n", 0))
         self.w = pair_weights(x, self.box, self.per, self.rowptr, self.col, p["zb2"], ns) if ns > 0 else None
         self.Tl, self.Kself = lattice_temperature(self.rowptr, self.col, v, self.mass,
@@ -420,6 +452,14 @@ class OracleSim:
             raise FloatingPointError(f"theta left [0,1] at substep {-st - 1}")
         self.E_src += es
 
+    def forces(self):
+        """Shifted-force Morse forces and potential energy at the positions of the
+        last build (p: pot_D, pot_alpha, pot_r0; cutoff rc)."""
+        p = self.p
+        F, E = forces(self.x_build, self.box, self.per, self.rowptr, self.col, D=p["pot_D"],
+                      alpha=p["pot_alpha"], r0=p["pot_r0"], rc=p["rc"])
+        return F, float(E.sum())
+
     def couple(self, v, dt_md: float):
         p = self.p
         local = p.get("ce_mode", 0) == 1
@@ -427,7 +467,8 @@ class OracleSim:
             Tb, Ab = self.T.copy(), self.A.copy()
         dKE, stopped = couple(v, self.mass, self.A, self.T, self.chi, mode=p["couple_mode"],
                               frozen=p["frozen"], seed=p["seed"], md_step=self.md_step,
-                              dt_md=dt_md, gamma_fs=self.gamma_L, VC=self.VC)
+                              dt_md=dt_md, gamma_fs=self.gamma_L, VC=self.VC,
+                              stop_beta=p.get("stop_beta", 0.0), stop_ecut=p.get("stop_ecut", 10.0))
         if local:
             # a stopped atom's unpaid energy returns to its own electrons: U_i += (A_i - dKE_i) / V
             idx = np.nonzero(self.T != Tb)[0]

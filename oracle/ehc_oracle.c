@@ -343,6 +343,60 @@ void oracle_pair_weights(int64_t n, const int64_t *rowptr, const int32_t *col, c
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Interatomic forces for the lattice side of Eq. Motion (F_i; the paper uses an
+ * EAM potential, not available here): a Morse pair potential
+ *   phi(r) = D [exp(-2 alpha (r - r0)) - 2 exp(-alpha (r - r0))]
+ * in shifted-force form on the neighbour list (r <= r_c):
+ *   phi_sf(r) = phi(r) - phi(r_c) - (r - r_c) phi'(r_c),
+ * so that energy and force both vanish at the cutoff.  Displacements are the
+ * exact integer minimum-image differences of the quantised positions.
+ *   F_i = sum_j phi_sf'(r_ij) (x_j - x_i) / r_ij   [eV/A],
+ *   E_i = (1/2) sum_j phi_sf(r_ij)                 [eV].
+ * Pins: F = -grad E by central differences; sum_i F_i = 0; a perfect FCC lattice
+ * has F = 0 and E_i = (12 phi_sf(a/sqrt2) + 6 phi_sf(a)) / 2; energy of a
+ * velocity-Verlet run conserved to O(dt^2). */
+void oracle_morse(double r, double D, double alpha, double r0, double *phi, double *dphi) {
+  const double e1 = exp(-alpha * (r - r0));
+  *phi = D * (e1 * e1 - 2.0 * e1);
+  *dphi = -2.0 * alpha * D * (e1 * e1 - e1);
+}
+
+void oracle_forces(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *q,
+                   const int64_t *Lq, const int32_t *periodic, double D, double alpha, double r0,
+                   double rc, double *F, double *E) {
+  double pc, dpc;
+  oracle_morse(rc, D, alpha, r0, &pc, &dpc);
+  const double g = 1.0 / 1048576.0;   /* grid unit [A] */
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double f[3] = {0.0, 0.0, 0.0}, e = 0.0;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int64_t j = col[p];
+      double d[3];
+      for (int k = 0; k < 3; ++k)
+        d[k] = g * (double)o_disp((int64_t)q[3 * j + k] - (int64_t)q[3 * i + k], Lq[k], periodic[k]);
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double ph, dph;
+      oracle_morse(r, D, alpha, r0, &ph, &dph);
+      const double phs = ph - pc - (r - rc) * dpc;
+      const double dphs = dph - dpc;
+      for (int k = 0; k < 3; ++k) f[k] += dphs * d[k] / r;
+      e += 0.5 * phs;
+    }
+    for (int k = 0; k < 3; ++k) F[3 * i + k] = f[k];
+    E[i] = e;
+  }
+}
+
+/* Velocity-Verlet half kick: v_i += (dt / (m_i)) F_i, with F in eV/A, m in amu,
+ * v in A/fs (1 eV/(A amu) = 1/o_mvv_ev() A/fs^2). */
+void oracle_kick(int64_t n, double *v, const double *F, const double *mass_of_atom, double dt) {
+  const double mvv = o_mvv_ev();
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) v[3 * i + k] += dt * F[3 * i + k] / (mass_of_atom[i] * mvv);
+}
+
 /* Optional fixed-temperature border (a Dirichlet condition on T_e, as the
  * 300 K border shell of the paper's cascade runs, Sec. 5): where Tfix[i] is not
  * NaN, atom i is an electron reservoir held at Tfix[i].  Every substep is first
@@ -581,9 +635,17 @@ void oracle_gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
  * bookkeeping sink) and reports dKE_i = A_i.  A is reset to zero.
  * dKE (out) holds each atom's kinetic-energy change.  Returns the number of
  * atoms that had to be stopped. */
+/* Electronic stopping (the cascade runs of Sec. 5: a friction force on atoms
+ * with kinetic energy above a cut, 10 eV there, with SRIM's stopping power): here
+ * m dv/dt = -beta m v above E_cut (a stopping power proportional to the speed),
+ * integrated over the MD step: the atom's kinetic energy K loses
+ * K (1 - exp(-2 beta dt_md)), and its own electrons gain that energy, through the
+ * same exact hand-over as A_i (the target kinetic energy is K + A_i minus the
+ * stopping loss; whatever the lattice does not take goes back to T_i). */
 int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *A, double *T,
                       const uint8_t *chi, int mode, int frozen, uint64_t seed, uint64_t md_step,
-                      double dt_md, double gamma_fs, double VC, double *dKE) {
+                      double dt_md, double gamma_fs, double VC, double *dKE, double stop_beta,
+                      double stop_ecut) {
   const double mvv = o_mvv_ev();
   int64_t stopped = 0;
 #pragma omp parallel for schedule(static) reduction(+ : stopped)
@@ -595,6 +657,8 @@ int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *
     double *vi = v + 3 * i;
     double K0 = 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) * mvv;
     double target = K0 + A[i];
+    const int slowed = stop_beta > 0.0 && K0 > stop_ecut;
+    if (slowed) target -= K0 * (1.0 - exp(-2.0 * stop_beta * dt_md));
     if (target < 0.0) { target = 0.0; stopped += 1; }
     double w[3] = {vi[0], vi[1], vi[2]};
     if (mode == 1) {
@@ -609,7 +673,7 @@ int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *
     double s = (Kw > 0.0) ? sqrt(target / Kw) : 0.0;
     for (int k = 0; k < 3; ++k) vi[k] = w[k] * s;
     dKE[i] = target - K0;   /* the kinetic energy after scaling is the target */
-    if (target == 0.0) T[i] += (A[i] - dKE[i]) / VC;
+    if (target == 0.0 || slowed) T[i] += (A[i] - dKE[i]) / VC;
     A[i] = 0.0;
   }
   return stopped;
