@@ -47,6 +47,7 @@ B_ALG = 4 * N_NB + 44  # algorithmic bytes per atom-substep of the substep kerne
 # reservoir-sum kernels per build
 LAUNCHES_PER_STEP = 11 + 2 + N_SUB + 3 + 1
 BORDER_LAUNCHES_PER_STEP = 3
+VERLET_EXTRA_LAUNCHES = 3   # velocity-Verlet: force kernel, its energy sum and two kicks in place of the drift
 
 
 def _dist():
@@ -151,6 +152,12 @@ def run_gpu(args):
     if args.ce_local:
         # LOCAL per-atom C_e / kappa_e: the general single-precision kernel on the energy state
         p = dict(p, ce_mode=1)
+    verlet = args.md == "verlet"
+    if verlet:
+        # interacting lattice: shifted-force Morse pair potential for Cu (Girifalco and
+        # Weizer) on the r_c neighbour list, velocity-Verlet with the MD step dt_md
+        p = dict(p, pot_D=0.3429, pot_alpha=1.3588, pot_r0=2.866)
+        args.no_e2e = True
     n = s.n
     tfix = None
     if args.border > 0:
@@ -174,10 +181,30 @@ def run_gpu(args):
 
     t_fs = 0.0
     sub_ev = []
+    force_ev = []
+    F = None
+    if verlet:
+        sim.build_neighbors(x, v)
+        F, _ = sim.forces()
 
     def step(record: bool):
         nonlocal t_fs
-        sim.build_neighbors(x, v)
+        if verlet:
+            # kick, drift, build at the new positions, forces, kick; then the electrons
+            sim.kick(v, F, 0.5 * DT_MD)
+            sim.drift(x, v, DT_MD)
+            sim.build_neighbors(x, v)
+            if record:
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+            sim.forces(F, energy=False)
+            if record:
+                f1.record(stream)
+                force_ev.append((f0, f1))
+            sim.kick(v, F, 0.5 * DT_MD)
+        else:
+            sim.build_neighbors(x, v)
         if record:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -187,7 +214,8 @@ def run_gpu(args):
             e1.record(stream)
             sub_ev.append((e0, e1))
         sim.couple(v, DT_MD)
-        sim.drift(x, v, DT_MD)
+        if not verlet:
+            sim.drift(x, v, DT_MD)
         t_fs += DT_MD
 
     for _ in range(args.warmup):
@@ -207,6 +235,8 @@ def run_gpu(args):
     ms = t0.elapsed_time(t1)
     sub_ms = [a.elapsed_time(b) for a, b in sub_ev]
     e = sim.energy()
+    if verlet:
+        args.force_ms = statistics.mean(a.elapsed_time(b) for a, b in force_ev)
 
     # end to end through the host-buffer entry point: inputs copied in, results copied out
     e2e_ms = float("nan")
@@ -288,6 +318,10 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                                                      if args.border > 0 else {}),
                                                   **({"pair_rates": "distance-weighted, S2/(%d r^2)" % args.rate_shell}
                                                      if args.rate_shell > 0 else {}),
+                                                  **({"lattice": "velocity-Verlet, shifted-force Morse pair "
+                                                      "potential (Cu, D 0.3429 eV, alpha 1.3588/A, r0 2.866 A) on the "
+                                                      "r_c list, in place of free flight"}
+                                                     if args.md == "verlet" else {}),
                                                   **({"electron_heat_capacity": "LOCAL per-atom C_e = gamma T_i "
                                                       "(cap 3 k_B), kappa_i = kappa0 T_i / T_lat, pair energy "
                                                       "rates with (kappa_i + kappa_j) / 2, energy state"}
@@ -296,7 +330,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                  "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 2 * 3 * n * 8 + n * 8}
                 if e2e_ms == e2e_ms else None),
         # every rank's kernels in the timed region (one replica per rank)
-        "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)) * args.steps * ws,
+        "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)
+                         + (VERLET_EXTRA_LAUNCHES if args.md == "verlet" else 0)) * args.steps * ws,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kname,
@@ -305,6 +340,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "clocks": clocks,
         "energy_drift": e["drift"],
     }
+    if args.md == "verlet":
+        line["force_kernel_ms"] = args.force_ms
     if not args.no_cpu_baseline and ws == 1:   # the oracle's timing: one process, N = 1 only
         line["cpu_baseline"] = cpu_baseline(args.cells, ce_local=args.ce_local)
     print(json.dumps(line), flush=True)
@@ -716,6 +753,8 @@ def main():
     ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--border", type=float, default=0.0)
     ap.add_argument("--rate-shell", type=int, default=0)
+    ap.add_argument("--md", default="free", choices=["free", "verlet"],
+                    help="lattice step: free flight, or velocity-Verlet with Morse forces")
     ap.add_argument("--ce-local", action="store_true",
                     help="LOCAL per-atom C_e / kappa_e energy form (ehc_params.ce_mode = 1)")
     ap.add_argument("--hidden", type=int, default=8)

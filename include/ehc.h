@@ -94,6 +94,16 @@ extern "C" {
  *                   advance such a context with plain substeps.  The stability number is
  *                   dt (2 n_max K + G / C_min) with K = 2 d kappa0 / (gamma Z b^2 T_lat)
  *                   (times T_hi / T_c above the cap) or 2 d kappa0 / (Z b^2 C_e(T_min))
+ *   pot_*           lattice forces of ehc_forces (the paper's MD runs use an EAM potential;
+ *                   this library carries a pair potential for the velocity-Verlet lattice
+ *                   side): Morse phi(r) = D [e^{-2 alpha (r - r0)} - 2 e^{-alpha (r - r0)}] in
+ *                   shifted-force form on the neighbour list (energy and force vanish at
+ *                   rc_A); pot_D_eV = 0 gives zero forces
+ *   stop_*          electronic stopping (Sec. 5 cascades: a friction force on atoms above a
+ *                   kinetic-energy cut, 10 eV there): in ehc_couple an atom with kinetic
+ *                   energy K > stop_ecut_eV loses K (1 - e^{-2 beta dt_md}) (m dv/dt = -beta m v
+ *                   over the MD step) to its own electrons, through the same exact hand-over
+ *                   as A_i; stop_beta_per_fs = 0 switches it off
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after
  *                   tiles grow), 256 or 128 = fixed; both give identical results */
@@ -127,6 +137,11 @@ typedef struct ehc_params {
   int32_t rate_shell_n;
   int32_t ce_mode;
   int32_t reserved[4];
+  double pot_D_eV;          /* Morse pair potential of ehc_forces (0: no forces) */
+  double pot_alpha_perA;
+  double pot_r0_A;
+  double stop_beta_per_fs;  /* electronic stopping rate in ehc_couple (0: none) */
+  double stop_ecut_eV;      /* kinetic energy above which an atom is stopped */
 } ehc_params;
 
 /* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked
@@ -204,9 +219,28 @@ int ehc_couple(ehc_ctx *c, double *v_dev, double dt_md_fs);
  * returns EHC_E_STATE. */
 int ehc_set_border(ehc_ctx *c, const double *Tfix_dev);
 
-/* Free flight x += v dt, wrapped into the box on periodic axes: the stand-in
- * for the host MD integrator when no interatomic forces are available. */
+/* Free flight x += v dt, wrapped into the box on periodic axes: the position
+ * update of the velocity-Verlet step (and the whole lattice step when no
+ * interatomic forces are used). */
 int ehc_drift(ehc_ctx *c, double *x_dev, const double *v_dev, double dt_fs);
+
+/* Interatomic forces F_i of Eq. Motion from the shifted-force Morse potential
+ * (ehc_params.pot_*) at the positions of the last ehc_build_neighbors, over its
+ * neighbour list (pairs with r <= rc_A): F_dev [N,3] eV/A, caller order, written
+ * (device, caller-owned).  Pair terms in single precision on the exact integer
+ * displacements of the quantised positions, sums per atom in single precision,
+ * the potential energy summed in FP64 into *epot_host [eV] when epot_host is not
+ * NULL (then the call synchronises).  EHC_E_STATE before the first build. */
+int ehc_forces(ehc_ctx *c, double *F_dev, double *epot_host);
+
+/* Velocity-Verlet kick v_i += dt F_i / m_i (caller order, per-type masses, F in
+ * eV/A, v in A/fs): called with dt = half the MD step before the drift and after
+ * the forces of the new positions. */
+int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
+
+/* Largest speed max_i |v_i| [A/fs] of v_dev [N,3] into *vmax_host, for a variable
+ * MD step (the cascade runs of Sec. 5 cap the displacement per step).  Synchronises. */
+int ehc_max_speed(ehc_ctx *c, const double *v_dev, double *vmax_host);
 
 /* One whole MD step with HOST buffers: copies x_host, v_host [N,3] to the
  * device, runs build, n_sub substeps from t_fs, couple and drift, and copies

@@ -51,6 +51,8 @@ class ehc_params(ctypes.Structure):
         ("use_graph", ctypes.c_int32), ("tile_threads", ctypes.c_int32), ("rate_shell_n", ctypes.c_int32),
         ("ce_mode", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 4),
+        ("pot_D_eV", ctypes.c_double), ("pot_alpha_perA", ctypes.c_double), ("pot_r0_A", ctypes.c_double),
+        ("stop_beta_per_fs", ctypes.c_double), ("stop_ecut_eV", ctypes.c_double),
     ]
 
 
@@ -78,6 +80,9 @@ _SIGS = {
     "ehc_substep": (_I, [_P, ctypes.c_int32, ctypes.c_double]),
     "ehc_couple": (_I, [_P, _P, ctypes.c_double]),
     "ehc_drift": (_I, [_P, _P, _P, ctypes.c_double]),
+    "ehc_forces": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ehc_kick": (_I, [_P, _P, _P, ctypes.c_double]),
+    "ehc_max_speed": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
     "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
     "ehc_sync": (_I, [_P]),
@@ -181,6 +186,11 @@ def make_params(p: dict) -> ehc_params:
     q.max_neighbors = int(p.get("max_neighbors", 0))
     q.rate_shell_n = int(p.get("rate_shell_n", 0))
     q.ce_mode = int(p.get("ce_mode", 0))
+    q.pot_D_eV = float(p.get("pot_D", 0.0))
+    q.pot_alpha_perA = float(p.get("pot_alpha", 0.0))
+    q.pot_r0_A = float(p.get("pot_r0", 0.0))
+    q.stop_beta_per_fs = float(p.get("stop_beta", 0.0))
+    q.stop_ecut_eV = float(p.get("stop_ecut", 10.0))
     q.use_graph = int(p.get("use_graph", 1))
     q.tile_threads = int(p.get("tile_threads", 0))
     return q
@@ -279,6 +289,25 @@ class Ehc:
 
     def drift(self, x, v, dt_fs: float):
         _check(self._lib.ehc_drift(self._h, _ptr(x), _ptr(v), float(dt_fs)), "ehc_drift")
+
+    def forces(self, F=None, energy: bool = True):
+        """Morse forces of the last build's positions (caller order, [N, 3] eV/A) and
+        the potential energy [eV] (None, without a synchronisation, if not `energy`)."""
+        import torch
+        if F is None:
+            F = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        e = ctypes.c_double()
+        _check(self._lib.ehc_forces(self._h, _ptr(F), ctypes.byref(e) if energy else None), "ehc_forces")
+        return F, (e.value if energy else None)
+
+    def kick(self, v, F, dt_fs: float):
+        """v += dt F / m in place."""
+        _check(self._lib.ehc_kick(self._h, _ptr(v), _ptr(F), float(dt_fs)), "ehc_kick")
+
+    def max_speed(self, v) -> float:
+        r = ctypes.c_double()
+        _check(self._lib.ehc_max_speed(self._h, _ptr(v), ctypes.byref(r)), "ehc_max_speed")
+        return r.value
 
     def md_step_host(self, x_host, v_host, n_sub: int, t_fs: float, dt_md_fs: float, Te_host_out):
         """Whole MD step on host buffers (torch CPU tensors, ideally pinned)."""

@@ -68,7 +68,7 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi};
+                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -286,6 +286,9 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   if (p->laser_on && (!(p->laser_lp_A > 0) || !(p->laser_sigma_fs > 0))) return EHC_E_INVAL;
   if (p->rate_shell_n < 0) return EHC_E_INVAL;
   if (p->ce_mode != 0 && p->ce_mode != 1) return EHC_E_INVAL;
+  if (!(p->pot_D_eV >= 0) || (p->pot_D_eV > 0 && (!(p->pot_alpha_perA > 0) || !(p->pot_r0_A > 0))) ||
+      !(p->stop_beta_per_fs >= 0) || !(p->stop_ecut_eV >= 0))
+    return EHC_E_INVAL;
   int32_t W = p->max_neighbors <= 0 ? 32 : p->max_neighbors;
   if (W > kMaxWidth || W > 255) return EHC_E_INVAL;
   for (int t = 0; t < n_types; ++t)
@@ -376,6 +379,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.pulse, c.max_sub));
   A(dalloc(&c.dKE, n));
   A(dalloc(&c.partials, kRedBlocks * 6));
+  A(dalloc(&c.md_part, md_force_blocks(n)));
   A(dalloc(&c.scal, 16));
   A(dalloc(&c.err, 4));
   A(dalloc(&c.coef, 1));
@@ -785,6 +789,36 @@ int ehc_couple(ehc_ctx *h, double *v_dev, double dt_md_fs) {
   CK(launch_couple(c, v_dev, dt_md_fs));
   c.ff_valid = false;
   c.md_step += 1;
+  return EHC_OK;
+}
+
+int ehc_forces(ehc_ctx *h, double *F_dev, double *epot_host) {
+  NvtxRange nvtx_range("ehc_forces");
+  if (!h || (h->c.n > 0 && !F_dev)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  CK(launch_forces(c, F_dev, c.md_part, c.scal + 6));
+  if (epot_host) {
+    CK(cudaMemcpyAsync(c.scal_host + 6, c.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    *epot_host = c.scal_host[6];
+  }
+  return EHC_OK;
+}
+
+int ehc_kick(ehc_ctx *h, double *v_dev, const double *F_dev, double dt_fs) {
+  if (!h || (h->c.n > 0 && (!v_dev || !F_dev)) || !(dt_fs == dt_fs)) return EHC_E_INVAL;
+  CK(launch_kick(h->c, v_dev, F_dev, dt_fs));
+  return EHC_OK;
+}
+
+int ehc_max_speed(ehc_ctx *h, const double *v_dev, double *vmax_host) {
+  if (!h || !vmax_host || (h->c.n > 0 && !v_dev)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  CK(launch_vmax(c, v_dev, c.partials, kRedBlocks, c.scal + 7));
+  CK(cudaMemcpyAsync(c.scal_host + 7, c.scal + 7, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  *vmax_host = c.scal_host[7];
   return EHC_OK;
 }
 

@@ -267,6 +267,13 @@ cudaError_t border_apply(Ctx &c);                            // mask of the curr
 // kernels_couple.cu
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md);
 cudaError_t launch_drift(Ctx &c, double *x, const double *v, double dt);
+// lattice side (kernels_md.cu): shifted-force Morse forces of the last build's
+// positions into F (caller order, [N,3]) and their energy into *out; v += dt F / m;
+// the largest |v| into *out
+int md_force_blocks(int64_t n);
+cudaError_t launch_forces(Ctx &c, double *F, double *part, double *out);
+cudaError_t launch_kick(Ctx &c, double *v, const double *F, double dt);
+cudaError_t launch_vmax(Ctx &c, const double *v, double *part, int nb, double *out);
 cudaError_t launch_philox_normals(const int64_t *ids, int64_t n, uint64_t step, uint64_t seed,
                                   double *out, cudaStream_t s);
 
@@ -374,6 +381,7 @@ struct Ctx {
   double E_e0 = 0, E_base = 0, ST_base = 0, VC_prev = -1, E_src = 0;
   double Tmin = 0;       // smallest T_e at the build (LOCAL form's stability number)
   double cap_si = 0;     // cap of C_e per unit volume [J m^-3 K^-1] (0: none)
+  double *md_part = nullptr;  // block sums of the force kernel's energy
 
   // captured substep loops, keyed by everything a launch bakes in
   // fixed-temperature border: tfix_orig (caller order, NaN = free) set by

@@ -80,7 +80,8 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
                               double *__restrict__ A,
                               double *__restrict__ T, double *__restrict__ v, double *__restrict__ dKE,
                               int mode, int frozen, uint64_t seed, uint64_t md_step, double e1, double inv_VC,
-                              unsigned long long *__restrict__ n_stopped, double thc, double inv_Tmax) {
+                              unsigned long long *__restrict__ n_stopped, double thc, double inv_Tmax,
+                              double stop_f, double stop_ecut) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double Ai = A[s];
@@ -100,6 +101,9 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
   const double K0 = 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2) * kMVV;
   double target = K0 + Ai;
+  // electronic stopping above the cut: the friction's loss over the MD step
+  const bool slowed = stop_f > 0.0 && K0 > stop_ecut;
+  if (slowed) target -= K0 * stop_f;
   if (target < 0.0) {
     target = 0.0;
     atomicAdd(n_stopped, 1ull);
@@ -124,8 +128,8 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   // the new kinetic energy is the target up to the rounding of the scaling
   const double d = target - K0;
   dKE[s] = d;
-  if (target == 0.0) {
-    // the unpaid part returns to the atom's electrons: T += dE / (V_atom C_e), or in
+  if (target == 0.0 || slowed) {
+    // the unpaid part (and the stopping loss) goes to the atom's electrons: T += dE / (V_atom C_e), or in
     // the LOCAL form (inv_Tmax > 0) u += dE / (V_atom gamma Tmax^2) with inv_VC that factor
     if (inv_Tmax > 0.0) T[s] = ue_inv(ue_of(T[s] * inv_Tmax, thc) + (Ai - d) * inv_VC, thc) / inv_Tmax;
     else T[s] += (Ai - d) * inv_VC;
@@ -222,7 +226,8 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
         (uint64_t)c.md_step, e1,
         c.local ? kEVJ / (c.vatom * 1e-30 * c.p.gamma_Ce * c.p.Tmax_K * c.p.Tmax_K) : 1.0 / c.VC,
         reinterpret_cast<unsigned long long *>(c.scal + 9), c.local ? c.coef_host->thc : 0.0,
-        c.local ? 1.0 / c.p.Tmax_K : 0.0);
+        c.local ? 1.0 / c.p.Tmax_K : 0.0,
+        c.p.stop_beta_per_fs > 0 ? -std::expm1(-2.0 * c.p.stop_beta_per_fs * dt_md) : 0.0, c.p.stop_ecut_eV);
   sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
   sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
   return cudaGetLastError();

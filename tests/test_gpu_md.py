@@ -1,0 +1,152 @@
+"""Lattice side on the GPU against the oracle: shifted-force Morse forces and
+energy (ehc_forces vs oracle_forces), a coupled velocity-Verlet run (kick, drift,
+build, forces, kick, substeps, hand-over) step for step, the total energy
+KE + PE + E_e of that run, the largest speed, and electronic stopping in the
+hand-over (global and LOCAL forms)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_12357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MORSE = dict(pot_D=0.3429, pot_alpha=1.3588, pot_r0=2.866)     # Cu, Girifalco and Weizer
+MVV = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19
+
+
+def _params(**kw):
+    # K = 2 d kappa0 / (C_e S2) = 5.3 / fs at kappa0 = 40: 100 substeps of 5e-3 fs per
+    # 0.5 fs MD step stay below the stability limit (dt 2 n_max K = 0.95)
+    p = dict(I.params_hotspot_fp64(), kappa0=40.0, dt_sub=5e-3, G=3e18, frozen=0, couple_mode=0, **MORSE)
+    p.update(kw)
+    return p
+
+
+def _oracle_verlet(s, p, n_md, n_sub, dt_md):
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    x, v = s.x.copy(), s.v.copy()
+    mass = sim.mass
+    sim.build(x, v)
+    F, _ = sim.forces()
+    tot = []
+    for step in range(n_md):
+        oracle.kick(v, F, mass, 0.5 * dt_md)
+        x = I.wrap(x + v * dt_md, s.box, s.periodic)
+        sim.build(x, v)
+        F, pe = sim.forces()
+        oracle.kick(v, F, mass, 0.5 * dt_md)
+        sim.substeps(n_sub, step * dt_md)
+        sim.couple(v, dt_md)
+        ke = 0.5 * float((mass[:, None] * v * v).sum()) * MVV
+        tot.append(ke + pe + sim.energy()["E_e"])
+    return sim, x, v, np.array(tot)
+
+
+def _gpu_verlet(s, p, n_md, n_sub, dt_md):
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda").contiguous()
+    v = torch.as_tensor(s.v, device="cuda").contiguous()
+    m = torch.as_tensor(s.mass_amu[s.type], device="cuda")
+    g.build_neighbors(x, v)
+    F, _ = g.forces()
+    tot = []
+    for step in range(n_md):
+        g.kick(v, F, 0.5 * dt_md)
+        g.drift(x, v, dt_md)
+        g.build_neighbors(x, v)
+        F, pe = g.forces(F)
+        g.kick(v, F, 0.5 * dt_md)
+        g.substep(n_sub, step * dt_md)
+        g.couple(v, dt_md)
+        ke = 0.5 * float((m[:, None] * v * v).sum()) * MVV
+        tot.append(ke + pe + g.energy()["E_e"])
+    torch.cuda.synchronize()
+    return g, x.cpu().numpy(), v.cpu().numpy(), np.array(tot)
+
+
+def test_forces_match_the_oracle():
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.hot_spot_system(10, 8, disp_sigma=0.1)
+    p = _params()
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
+    F, pe = g.forces()
+    Fg = F.cpu().numpy()
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"])
+    Fo, Eo = oracle.forces(s.x, s.box, s.periodic, rowptr, col, D=p["pot_D"], alpha=p["pot_alpha"],
+                           r0=p["pot_r0"], rc=p["rc"])
+    # single-precision pair terms and sums: about 18 x 2^-24 of the largest pair force
+    err = float(np.max(np.abs(Fg - Fo)))
+    assert err < 2e-5, err
+    assert np.abs(Fo).max() > 0.1
+    assert pe == pytest.approx(float(Eo.sum()), rel=1e-6)
+    print(f"Morse forces: max |F_gpu - F_oracle| {err:.1e} eV/A of max {np.abs(Fo).max():.2f}, "
+          f"E_pot {pe:.6f} vs {Eo.sum():.6f} eV")
+
+
+def test_verlet_run_matches_the_oracle_and_keeps_the_total_energy():
+    s = I.hot_spot_system(10, 8, peak=6000.0, disp_sigma=0.05)
+    p = _params()
+    n_md, n_sub, dt_md = 12, 100, 0.5
+    sim, xo, vo, to = _oracle_verlet(s, p, n_md, n_sub, dt_md)
+    g, xg, vg, tg = _gpu_verlet(s, p, n_md, n_sub, dt_md)
+    d = I.min_image(xg - xo, s.box, s.periodic)
+    assert np.max(np.abs(d)) < 1e-6
+    assert np.max(np.abs(vg - vo)) < 1e-5 * np.abs(vo).max()
+    T = g.get_te().cpu().numpy()
+    assert float(np.max(np.abs(T - sim.T) / sim.T)) < 1e-4
+    # the electrons heated the lattice, and KE + PE + E_e stayed put up to the
+    # Verlet error, on both sides alike
+    assert sim.energy()["E_lat"] > 0.0
+    ke0 = 0.5 * float((s.mass_amu[s.type][:, None] * s.v * s.v).sum()) * MVV
+    assert np.max(np.abs(to - to[0])) < 2e-3 * ke0
+    assert np.max(np.abs(tg - to)) < 1e-6 * abs(to[0])
+    assert abs(g.energy()["drift"]) < 1e-9
+    print(f"Verlet: total energy spread {np.ptp(to):.2e} eV (oracle) {np.ptp(tg):.2e} eV (GPU), "
+          f"KE0 {ke0:.1f} eV, E_lat {sim.energy()['E_lat']:.3e} eV")
+
+
+def test_max_speed():
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.hot_spot_system(6, 2)
+    s.v[17] = [0.7, -0.3, 0.2]
+    g = Ehc(_params(), s)
+    vmax = g.max_speed(torch.as_tensor(s.v, device="cuda"))
+    assert vmax == pytest.approx(float(np.sqrt((s.v * s.v).sum(1)).max()), rel=1e-15)
+
+
+@pytest.mark.parametrize("ce_mode,couple_mode", [(0, 0), (0, 1), (1, 0)])
+def test_stopping_matches_the_oracle(ce_mode, couple_mode):
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _drive import run_gpu, run_oracle
+    s = I.hot_spot_system(8, 3, peak=3000.0)
+    fast = np.array([5, 100, 900])
+    # 28-37 eV atoms: above the 10 eV cut; each hands its electrons (2.5e-6 eV/K
+    # per atom) about 1e-3 eV per MD step
+    s.v[fast] = [[0.08, 0.05, -0.03], [-0.06, 0.07, 0.01], [0.02, 0.03, 0.1]]
+    p = dict(I.params_hotspot_fp64(), frozen=0, couple_mode=couple_mode, ce_mode=ce_mode, G=3e18,
+             stop_beta=1e-3, stop_ecut=10.0)
+    sim, xo, vo = run_oracle(s, p, 2, 20)
+    g, xg, vg = run_gpu(s, p, 2, 20)
+    vg = vg.cpu().numpy()
+    # the Langevin force's Box-Muller transform runs in single precision on the GPU
+    assert np.max(np.abs(vg - vo)) < (1e-12 if couple_mode == 0 else 1e-6) * np.abs(vo).max()
+    T = g.get_te().cpu().numpy()
+    assert float(np.max(np.abs(T - sim.T) / sim.T)) < 1e-11
+    # the stopped atoms' electrons took the energy
+    sim0, _, _ = run_oracle(s, dict(p, stop_beta=0.0), 2, 20)
+    assert np.all(sim.T[fast] > sim0.T[fast] + 1.0)
+    eg, eo = g.energy(), sim.energy()
+    assert eg["E_lat"] == pytest.approx(eo["E_lat"], rel=1e-10 if couple_mode == 0 else 1e-8)
+    assert abs(eg["drift"]) < 1e-12 and abs(eo["drift"]) < 1e-12
