@@ -27,12 +27,16 @@ constexpr double kMVVmd = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;  // amu 
 
 struct MorseF {
   float D, alpha, r0, rc, pc, dpc;   // pc, dpc: phi(r_c), phi'(r_c)
+  int32_t L[3], half[3];             // box on the grid and floor(L / 2) (0: axis not periodic)
 };
 
-__device__ __forceinline__ int64_t min_image(int64_t d, int64_t L, int per) {
-  if (per) {
-    if (2 * d > L) d -= L;
-    else if (2 * d < -L) d += L;
+// minimum image on the grid: both coordinates lie in [0, L) with L < 2^31, so the
+// difference fits in int32; 2 d > L  <=>  d > floor(L / 2) for integers (a
+// displacement of exactly half the box keeps its sign, as in the neighbour search)
+__device__ __forceinline__ int32_t min_image(int32_t d, int32_t L, int32_t half) {
+  if (half > 0) {
+    if (d > half) d -= L;
+    else if (d < -half) d += L;
   }
   return d;
 }
@@ -52,7 +56,7 @@ __device__ __forceinline__ double blk_sum(double v, double *sh) {
 // partial sums of the energy in part[blockIdx.x]
 __global__ void __launch_bounds__(kMdThreads) morse_force_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt, const int4 *__restrict__ q_s,
-    Grid g, MorseF m, const int32_t *__restrict__ perm, double *__restrict__ F, double *__restrict__ part,
+    MorseF m, const int32_t *__restrict__ perm, double *__restrict__ F, double *__restrict__ part,
     int32_t *__restrict__ err) {
   __shared__ double sh[kMdThreads / 32];
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,9 +69,9 @@ __global__ void __launch_bounds__(kMdThreads) morse_force_kernel(
     for (int j = 0; j < c; ++j) {
       const int32_t t = checked_index(__ldg(nbr + (int64_t)j * n + s), n, err);
       const int4 qj = q_s[t];
-      const float dx = (float)min_image((int64_t)qj.x - qi.x, g.Lq[0], g.per[0]) * unit;
-      const float dy = (float)min_image((int64_t)qj.y - qi.y, g.Lq[1], g.per[1]) * unit;
-      const float dz = (float)min_image((int64_t)qj.z - qi.z, g.Lq[2], g.per[2]) * unit;
+      const float dx = (float)min_image(qj.x - qi.x, m.L[0], m.half[0]) * unit;
+      const float dy = (float)min_image(qj.y - qi.y, m.L[1], m.half[1]) * unit;
+      const float dz = (float)min_image(qj.z - qi.z, m.L[2], m.half[2]) * unit;
       const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       const float e1 = expf(-m.alpha * (r - m.r0));
       const float phi = m.D * fmaf(e1, e1, -2.0f * e1);
@@ -149,9 +153,13 @@ cudaError_t launch_forces(Ctx &c, double *F, double *part, double *out) {
       pc = c.p.pot_D_eV * (e1 * e1 - 2.0 * e1);
       dpc = -2.0 * c.p.pot_alpha_perA * c.p.pot_D_eV * (e1 * e1 - e1);
     }
-    const MorseF m{(float)c.p.pot_D_eV, (float)c.p.pot_alpha_perA, (float)c.p.pot_r0_A, (float)c.p.rc_A,
-                   (float)pc, (float)dpc};
-    morse_force_kernel<<<nb, kMdThreads, 0, c.stream>>>((int32_t)c.n, c.nbr, c.cnt, c.q_s, c.g, m, c.perm, F, part,
+    MorseF m{(float)c.p.pot_D_eV, (float)c.p.pot_alpha_perA, (float)c.p.pot_r0_A, (float)c.p.rc_A,
+             (float)pc, (float)dpc, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < 3; ++k) {
+      m.L[k] = (int32_t)c.g.Lq[k];
+      m.half[k] = c.g.per[k] ? (int32_t)(c.g.Lq[k] / 2) : 0;
+    }
+    morse_force_kernel<<<nb, kMdThreads, 0, c.stream>>>((int32_t)c.n, c.nbr, c.cnt, c.q_s, m, c.perm, F, part,
                                                         c.err);
   }
   md_sum_final<<<1, kMdThreads, 0, c.stream>>>(c.n > 0 ? nb : 0, part, out);
