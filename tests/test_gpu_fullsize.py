@@ -127,3 +127,69 @@ def test_256k_track_10k_substeps():
     assert abs(e["drift"]) < 1e-9
     assert e["n_stopped"] == sim.n_stopped
     print(f"track40 (256k atoms) FP32, 10k substeps: max rel T_e err {err:.3e}, drift {e['drift']:.3e}")
+
+
+def test_fullsize_local_form_sampled_substeps_and_ledger():
+    """The LOCAL per-atom C_e / kappa_e form (ce_mode 1) in the launch configuration
+    of `bench.py --ce-local` (4,000,000 atoms): sampled atoms after 10 substeps
+    against oracle_substeps_local on their 10-hop neighbourhood (system T_lat of
+    the build), then the ledger of a whole MD step."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.track_system(100, 2)
+    p = dict(I.params_track(), ce_mode=1)
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    g.build_neighbors(x, v)
+    g.substep(N_SUB_SAMPLE, 0.0)
+    Tg = g.get_te().cpu().numpy()
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    rng = np.random.default_rng(11)
+    rho = np.hypot(s.x[:, 0] - 0.5 * s.box[0], s.x[:, 1] - 0.5 * s.box[1])
+    picks = np.concatenate([rng.choice(np.flatnonzero(rho < 8.0), 4, replace=False),
+                            rng.choice(np.flatnonzero((rho > 15.0) & (rho < 40.0)), 4, replace=False),
+                            rng.choice(np.flatnonzero(rho > 80.0), 4, replace=False)])
+    worst = 0.0
+    for a in picks:
+        ball, loc, rp, col = _ball(sim.rowptr, sim.col, a, N_SUB_SAMPLE)
+        T = s.Te[ball].copy()
+        Aacc = np.zeros(ball.size)
+        st, _, _ = oracle.substeps_local(rp, col, T, sim.Tl[ball].copy(), sim.chi[ball].copy(), Aacc,
+                                         N_SUB_SAMPLE, p["dt_sub"], p["Tmax"], kappa0=p["kappa0"],
+                                         kappa_mode=p["kappa_mode"], Tlat=sim.Tlat, dim_d=p["dim_d"],
+                                         S2_A2=p["zb2"], gamma=p["gamma_Ce"], cap_SI=sim.cap_SI(), G=p["G"],
+                                         vatom_A3=sim.vatom)
+        assert st == N_SUB_SAMPLE
+        worst = max(worst, abs(Tg[a] - T[loc[a]]) / T[loc[a]])
+    assert worst < 1e-4, worst
+    g.substep(100 - N_SUB_SAMPLE, N_SUB_SAMPLE * p["dt_sub"])
+    g.couple(v, 100 * p["dt_sub"])
+    e = g.energy()
+    assert abs(e["drift"]) < 1e-9
+    print(f"full-size LOCAL form: sampled T_e max rel err {worst:.3e}, MD-step drift {e['drift']:.1e}")
+
+
+def test_fullsize_forces():
+    """Morse forces of all 4,000,000 atoms of the track (positions displaced by
+    0.05 A so that the forces do not vanish by symmetry) against oracle_forces."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.track_system(100, 2, disp_sigma=0.05)
+    p = dict(I.params_track(), pot_D=0.3429, pot_alpha=1.3588, pot_r0=2.866)
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
+    F, pe = g.forces()
+    Fg = F.cpu().numpy()
+    rowptr, col = oracle.neighbors(s.x, s.box, s.periodic, p["rc"], cap_per_atom=24)
+    Fo, Eo = oracle.forces(s.x, s.box, s.periodic, rowptr, col, D=p["pot_D"], alpha=p["pot_alpha"],
+                           r0=p["pot_r0"], rc=p["rc"])
+    err = float(np.max(np.abs(Fg - Fo)))
+    assert err < 2e-5, err
+    assert pe == pytest.approx(float(Eo.sum()), rel=1e-6)
+    print(f"full-size forces: max |dF| {err:.1e} eV/A of max {np.abs(Fo).max():.2f}, E_pot rel "
+          f"{abs(pe - Eo.sum()) / abs(Eo.sum()):.1e}")

@@ -115,3 +115,4 @@ def test_local_form_refusals_and_plain_fallbacks():
         EhcNN(a)
     with pytest.raises(EhcError):
         EhcBatch(p, [s, s])
+
