@@ -304,7 +304,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
     traffic = _traffic_from_profile(n) if args.rate_shell == 0 and not args.ce_local else None
     kname = "substep_tile_kernel"
     if args.ce_local:
-        kname = "substep_local_f32_kernel" + (" (weighted)" if args.rate_shell > 0 else "")
+        # the row tiles take the LOCAL form unless weights send it to the general kernel
+        kname = "substep_local_f32_kernel (weighted)" if args.rate_shell > 0 else "substep_tile_kernel (LOCAL form)"
     elif args.rate_shell > 0:
         kname = "substep_f32_kernel (weighted)"
     line = {

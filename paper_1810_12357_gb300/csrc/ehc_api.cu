@@ -68,7 +68,7 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part};
+                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -163,7 +163,7 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   c.t_version += 1;
   const int p0 = (c.p.flux_prec == 1) ? c.tcur : c.parity;
   const int ab = (c.A == c.abuf[0]) ? 0 : 1;
-  const int path = (c.p.flux_prec == 1) ? 2 : (tile_path(c) ? 1 : 0);
+  const int path = (c.p.flux_prec == 1) ? 2 : ((tile_path(c) || local_tile(c)) ? 1 : 0);
   const int pairs = (c.n_max + 1) / 2;
   const int tile = c.tile_floats, nt = c.tile_nt;
   const int border = c.has_border ? 1 : 0;
@@ -243,6 +243,8 @@ RepArgs rep_args(const Ctx &c) {
   ra.pulse_f = c.pulse_f;
   ra.fix = c.has_border ? c.bmask : nullptr;
   ra.res = c.bres;
+  ra.uhi = c.uhi;
+  ra.ldmax = c.ldmax;
   ra.rrange[0] = c.rrange[0];
   ra.rrange[1] = c.rrange[1];
   ra.cf = c.coef;
@@ -360,6 +362,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * (size_t)(c.ps > 0 ? c.ps : 4)));
   A(dalloc(&c.dlo, n));
   if (c.local) A(dalloc(&c.uhi, n));
+  if (c.local) A(dalloc(&c.ldmax, 3));
   A(dalloc(&c.uTl, n));
   A(dalloc(&c.pulse_f, c.max_sub));
   c.nrows = (int64_t)c.g.nc[1] * c.g.nc[2];

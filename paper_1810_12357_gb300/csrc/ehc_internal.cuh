@@ -150,6 +150,8 @@ struct RepArgs {
   int32_t *err;
   const uint8_t *fix;   // border mask (null: no border)
   double *res;          // border reservoirs (single-precision paths: a float pair per atom, delta units)
+  float *uhi;           // LOCAL form: high word of the energy state (lo holds its low word)
+  uint32_t *ldmax;      // LOCAL form: ring of the largest |Delta| per substep (float bits)
 };
 
 // Arguments of a Chebyshev-window stage launch of the row-tile kernel.  The
@@ -196,6 +198,8 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t s);
 cudaError_t launch_split(Ctx &c, cudaStream_t s);
 cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
 bool tile_path(const Ctx &c);
+// the LOCAL form's substeps run on the row tiles (single precision, no laser source)
+bool local_tile(const Ctx &c);
 // tile capacity tb with headroom for the largest staged tile, the shared-memory
 // opt-in and the resident grid of each index width (9 and 16 words); false:
 // the buffers do not fit
@@ -320,6 +324,7 @@ struct Ctx {
   // (uhi, dlo) of w = u - u_ref; dmir holds delta = theta - Tref/Tmax rebuilt from it
   bool local = false;
   float *uhi = nullptr;
+  uint32_t *ldmax = nullptr;   // [3] ring of the largest |Delta| per substep (float bits)
   float *uTl = nullptr;          // Tref - T_l,i (NaN: atom below the guard)
   double *abuf[2] = {nullptr, nullptr};
   double *A = nullptr;           // one of abuf

@@ -209,6 +209,44 @@ __device__ __forceinline__ float update_atom(int64_t s, float di, float li, floa
   return h;
 }
 
+// LOCAL form, state update of one atom (single-precision paths): (h, l) is the
+// float pair of w = u - u_ref, F + Fc the compensated pair sum; the new mirror
+// value delta = theta - theta_ref goes to hout[s] and is returned
+__device__ __forceinline__ float update_atom_local(int64_t s, float di, float h, float l, float ui, double Ai,
+                                                   float F, float Fc, const StepCoef *__restrict__ cf,
+                                                   float *__restrict__ hout, float *__restrict__ uhi,
+                                                   float *__restrict__ lo, double *__restrict__ A,
+                                                   int32_t *__restrict__ err) {
+  const float th = cf->th_ref;
+  const float Ku = cf->dtKu_f;
+  const float p0 = __fmul_rn(Ku, F);
+  ff_add(h, l, p0);
+  ff_add(h, l, fmaf(Ku, F, -p0) + Ku * Fc);     // the product's error and the compensation
+  const bool chi = (ui == ui);
+  float dT = 0.0f;
+  if (chi) {
+    dT = fmaf(cf->Tmax_f, di, ui);               // T_i - T_l,i
+    const float g = -cf->dtgu_f;
+    const float q0 = __fmul_rn(g, dT);
+    ff_add(h, l, q0);
+    ff_add(h, l, fmaf(g, dT, -q0));
+  }
+  uhi[s] = h;
+  lo[s] = l;
+  if (chi) A[s] = fma(cf->dtVGu, f2d(dT), Ai);
+  float dn;
+  if (cf->thc_f > 0.0f && h > cf->wc_f) {
+    dn = fmaf(h - cf->wc_f, cf->inv_thc_f, cf->thc_f - th);
+  } else {
+    const float q = fmaf(2.0f, h, cf->thsq_f);
+    dn = (2.0f * h) / (sqrtf(q) + th);
+  }
+  hout[s] = dn;
+  const float tn = th + dn;
+  if (!(tn >= 0.0f && tn <= 1.0f)) atomicOr(err, ERR_RANGE);
+  return dn;
+}
+
 // Tile descriptor of the row tile around row R of one system.  Neighbour row r
 // is placed at tile offset off[r]: after the previous row rounded up to 4
 // words, congruent to its first global index modulo 4, so that each row moves
@@ -336,14 +374,36 @@ struct StageIn {
   float zm1, zm2, y0, F0;
 };
 
-template <int TIER, bool LASER, int PP, bool STAGE, bool BORDER>
+// LOCAL: the LOCAL C_e / kappa_e form (wh: the high word of the atom's energy
+// state, li its low word): the series order TIER is the one of the whole
+// substep (a per-tile order could differ between the two tiles a pair spans, and
+// the pair terms must be exact negatives), kappa_ij weights, TwoSum sums; the
+// largest |Delta| seen is raised in *mdp
+template <int TIER, bool LASER, int PP, bool STAGE, bool BORDER, bool LOCAL = false>
 __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf, const StageArgs &sa, int parity,
                                           int k, const float *tile, uint32_t tlen, int32_t s, float di,
                                           const uint32_t *pv, float ui, float li, double Ai, const StageIn &si,
-                                          bool fixed) {
+                                          bool fixed, float wh = 0.0f, float *mdp = nullptr) {
   const float th = cf->th_ref;
   const float ai = th + di;
   const float m2ai = -2.0f * ai;
+  if (LOCAL) {
+    const bool km = cf->kmode != 0;
+    float F = 0.0f, Fc = 0.0f;
+#pragma unroll
+    for (int m = 0; m < PP; ++m)
+      if (PP != 16 || m < ra.P) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const float dj = tile[checked_index(half ? (pv[m] >> 16) : (pv[m] & 0xffffu), tlen, ra.err)];
+          const float fij = pair_acc<TIER>(0.0f, di, dj, th, ai, m2ai);
+          const float kij = km ? 0.5f * (ai + (th + dj)) : 1.0f;
+          two_sum_acc(F, Fc, __fmul_rn(kij, fij));
+          *mdp = fmaxf(*mdp, fabsf(dj - di));
+        }
+      }
+    return update_atom_local(s, di, wh, li, ui, Ai, F, Fc, cf, ra.dmir[parity ^ 1], ra.uhi, ra.lo, ra.A, ra.err);
+  }
   float F = 0.0f;
 #pragma unroll
   for (int m = 0; m < PP; ++m)
@@ -415,7 +475,7 @@ __device__ __forceinline__ void close_item(TilePipe<NT> &sp, int it, int parity,
 // (pair flux of the tile values sa.yin, stage update into sa.yout, optionally
 // the flux itself into sa.Fout); rows and tiers as for substeps.
 // NT: threads that own atoms (256, or 128 for short rows); one producer warp more.
-template <bool LASER, int PP, bool STAGE, int NT, bool BORDER = false>
+template <bool LASER, int PP, bool STAGE, int NT, bool BORDER = false, bool LOCAL = false>
 __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTileMinBlocks)
     substep_tile_kernel(const RepArgs *__restrict__ reps, const int2 *__restrict__ work, int32_t nwork, int32_t tb,
                         int parity, int k, StageArgs sa) {
@@ -499,6 +559,16 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
     return;
   }
   // compute warps
+  // LOCAL form: one series order for the substep, from the previous substep's
+  // largest |Delta| (margin 1.25; the first substep of a call: the full series)
+  int ltier = 0;
+  float lmd = 0.0f;
+  if (LOCAL) {
+    uint32_t *ring = reps[0].ldmax;
+    const float prev = 1.25f * __uint_as_float(ring[k % 3]);
+    ltier = prev < 1.2e-4f ? 3 : (prev < 0.02f ? 2 : (prev < 0.12f ? 1 : 0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) ring[(k + 2) % 3] = 0u;
+  }
   for (int it = 0; it < n_it; ++it) {
     const int b = it % kTileBufs;
     if (!mbar_wait(&sp.full[b], (uint32_t)(it / kTileBufs) & 1)) {
@@ -519,7 +589,7 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
       for (int m = 0; m < PP; ++m)
         if (PP != 16 || m < D.ra.P) pv[m] = __ldg(pidx + (m * ps + s));
       const float di = tile[sb + q];
-      float ui = 0.0f, li = 0.0f;
+      float ui = 0.0f, li = 0.0f, wh = 0.0f;
       double Ai = 0.0;
       bool fixed = false;
       StageIn si = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -533,9 +603,17 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
         li = D.ra.lo[s];
         Ai = D.ra.A[s];
         if (BORDER) fixed = D.ra.fix[s] != 0;
+        if (LOCAL) wh = D.ra.uhi[s];
       }
       float h;
-      if (tier == 3) h = row_atom<3, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
+      if (LOCAL) {
+        const uint32_t tl = (uint32_t)D.staged;
+        if (ltier == 3) h = row_atom<3, false, PP, false, false, true>(D.ra, &D.cf, sa, parity, k, tile, tl, s, di, pv, ui, li, Ai, si, false, wh, &lmd);
+        else if (ltier == 2) h = row_atom<2, false, PP, false, false, true>(D.ra, &D.cf, sa, parity, k, tile, tl, s, di, pv, ui, li, Ai, si, false, wh, &lmd);
+        else if (ltier == 1) h = row_atom<1, false, PP, false, false, true>(D.ra, &D.cf, sa, parity, k, tile, tl, s, di, pv, ui, li, Ai, si, false, wh, &lmd);
+        else h = row_atom<0, false, PP, false, false, true>(D.ra, &D.cf, sa, parity, k, tile, tl, s, di, pv, ui, li, Ai, si, false, wh, &lmd);
+      }
+      else if (tier == 3) h = row_atom<3, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
                                                               si, fixed);
       else if (tier == 2) h = row_atom<2, LASER, PP, STAGE, BORDER>(D.ra, &D.cf, sa, parity, k, tile, (uint32_t)D.staged, s, di, pv, ui, li, Ai,
                                                                    si, fixed);
@@ -556,6 +634,14 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
       mbar_arrive(&sp.empty[b]);
     }
     __syncwarp();
+  }
+  if (LOCAL) {
+    for (int o = 16; o > 0; o >>= 1) lmd = fmaxf(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
+    if (lane == 0) {
+      uint32_t *nx = reps[0].ldmax + (k + 1) % 3;
+      const uint32_t mb = __float_as_uint(lmd);
+      if (mb > *((volatile uint32_t *)nx)) atomicMax(nx, mb);
+    }
   }
 }
 
@@ -616,10 +702,55 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   update_atom<LASER, true>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k, fixed);
 }
 
+// Pair sum of the LOCAL form for one atom with the series order TIER (one order
+// for every atom of the substep, so the two terms of a pair stay exact negatives);
+// also the largest |Delta| seen
+template <int TIER>
+__device__ __forceinline__ void local_pair_sum(int32_t n, int32_t s, int c, const int32_t *__restrict__ nbr,
+                                               const float *__restrict__ hin, const float *__restrict__ wgt,
+                                               float di, float th, float ai, float m2ai, bool km,
+                                               int32_t *__restrict__ err, float &F, float &Fc, float &md) {
+  const int32_t *np = nbr + s;
+  const float *wp = wgt ? wgt + s : nullptr;
+  int j = 0;
+  for (; j + 6 <= c; j += 6) {
+    int32_t t[6];
+    float dj[6], wj[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      t[u] = checked_index(__ldg(np + (int64_t)(j + u) * n), n, err);
+      wj[u] = wp ? __ldg(wp + (int64_t)(j + u) * n) : 1.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const float fij = pair_acc<TIER>(0.0f, di, dj[u], th, ai, m2ai);
+      const float kij = km ? 0.5f * (ai + (th + dj[u])) : 1.0f;
+      two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj[u]), fij));
+      md = fmaxf(md, fabsf(dj[u] - di));
+    }
+  }
+  for (; j < c; ++j) {
+    const float dj = __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err));
+    const float wj = wp ? __ldg(wp + (int64_t)j * n) : 1.0f;
+    const float fij = pair_acc<TIER>(0.0f, di, dj, th, ai, m2ai);
+    const float kij = km ? 0.5f * (ai + (th + dj)) : 1.0f;
+    two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj), fij));
+    md = fmaxf(md, fabsf(dj - di));
+  }
+}
+
 // LOCAL per-atom C_e / kappa_e form, single precision (one thread per atom).
-// The pair term takes the full series for every pair: choosing the order per
-// pair (pair_term) was measured slower here (133 against 128 us per substep on
-// the 4M track), the kernel being bound by instruction issue, not the series.
+// Series order: one for all atoms of a substep (the two terms of every pair stay
+// exact negatives), chosen from the largest |Delta| of the previous substep of
+// the call, with a margin of 1.25, against the row tiles' thresholds (truncation
+// below 3e-8 of B); the first substep of a call takes the full series.
+// dmax[3]: the largest |Delta| as float bits, in a ring: substep k reads
+// dmax[k % 3], raises dmax[(k + 1) % 3] and clears dmax[(k + 2) % 3], which no
+// other substep touches meanwhile.  Choosing the order per pair instead
+// (pair_term) measured slower here (133 against 128 us per substep on the 4M
+// track): the branches cost more than the series they save.
 // The state is each atom's electron energy density in units of gamma Tmax^2,
 // held as the float pair (uhi, lo) of w = u - u_ref; hin / hout hold the mirror
 // delta = theta - theta_ref the neighbours read, rebuilt from w after the update:
@@ -641,41 +772,26 @@ __global__ void __launch_bounds__(256) substep_local_f32_kernel(
     const float *__restrict__ hin, float *__restrict__ hout, float *__restrict__ uhi, float *__restrict__ lo,
     double *__restrict__ A, const float *__restrict__ uTl, const float *__restrict__ srcw,
     const float *__restrict__ pulse_f, int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err,
-    const float *__restrict__ wgt) {
+    const float *__restrict__ wgt, uint32_t *__restrict__ dmax) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) dmax[(k + 2) % 3] = 0u;
   if (s >= n) return;
   const float th = cf->th_ref;
   const bool km = cf->kmode != 0;
   const int c = cnt[s];
   const float di = hin[s];
   const float ai = th + di, m2ai = -2.0f * ai;
-  float F = 0.0f, Fc = 0.0f;
-  const int32_t *np = nbr + s;
-  const float *wp = wgt ? wgt + s : nullptr;
-  int j = 0;
-  for (; j + 6 <= c; j += 6) {
-    int32_t t[6];
-    float dj[6], wj[6];
-#pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      t[u] = checked_index(__ldg(np + (int64_t)(j + u) * n), n, err);
-      wj[u] = wp ? __ldg(wp + (int64_t)(j + u) * n) : 1.0f;
-    }
-#pragma unroll
-    for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
-#pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      const float fij = pair_acc<0>(0.0f, di, dj[u], th, ai, m2ai);
-      const float kij = km ? 0.5f * (ai + (th + dj[u])) : 1.0f;
-      two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj[u]), fij));
-    }
-  }
-  for (; j < c; ++j) {
-    const float dj = __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err));
-    const float wj = wp ? __ldg(wp + (int64_t)j * n) : 1.0f;
-    const float fij = pair_acc<0>(0.0f, di, dj, th, ai, m2ai);
-    const float kij = km ? 0.5f * (ai + (th + dj)) : 1.0f;
-    two_sum_acc(F, Fc, __fmul_rn(__fmul_rn(kij, wj), fij));
+  float F = 0.0f, Fc = 0.0f, md = 0.0f;
+  const float prev = 1.25f * __uint_as_float(dmax[k % 3]);   // the same value in every thread
+  if (prev < 1.2e-4f) local_pair_sum<3>(n, s, c, nbr, hin, wgt, di, th, ai, m2ai, km, err, F, Fc, md);
+  else if (prev < 0.02f) local_pair_sum<2>(n, s, c, nbr, hin, wgt, di, th, ai, m2ai, km, err, F, Fc, md);
+  else if (prev < 0.12f) local_pair_sum<1>(n, s, c, nbr, hin, wgt, di, th, ai, m2ai, km, err, F, Fc, md);
+  else local_pair_sum<0>(n, s, c, nbr, hin, wgt, di, th, ai, m2ai, km, err, F, Fc, md);
+  {
+    // raise the next substep's bound (a read first: most atoms need no atomic)
+    uint32_t *nx = dmax + (k + 1) % 3;
+    const uint32_t mb = __float_as_uint(md);
+    if (mb > *((volatile uint32_t *)nx)) atomicMax(nx, mb);
   }
   const float Ku = cf->dtKu_f;
   const float p0 = __fmul_rn(Ku, F);
@@ -843,11 +959,15 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // the row-tile kernel applies when two buffers fit in shared memory and the
 // table holds at most 32 neighbours per atom
-bool tile_path(const Ctx &c) {
+static bool tile_fits(const Ctx &c) {
   const int w = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
-  return c.p.flux_prec == 0 && c.p.rate_shell_n == 0 && !c.local && c.W <= 32 && c.nwork > 0 &&
+  return c.p.flux_prec == 0 && c.p.rate_shell_n == 0 && c.W <= 32 && c.nwork > 0 &&
          c.staged_max <= c.tile_floats && c.tile_grid[w] > 0;
 }
+
+bool tile_path(const Ctx &c) { return !c.local && tile_fits(c); }
+
+bool local_tile(const Ctx &c) { return c.local && !(c.p.laser_on && c.have_depth) && tile_fits(c); }
 
 cudaError_t launch_split(Ctx &c, cudaStream_t st) {
   if (c.n > 0 && c.local) {
@@ -874,6 +994,14 @@ cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// the first substep of a call takes the full series (state changed between
+// calls: hand-over, stopping, a new build): the ring's first word at a large
+// float (bytes 0x7f), the others cleared
+static void local_tier_reset(Ctx &c, cudaStream_t st) {
+  cudaMemsetAsync(c.ldmax, 0x7f, sizeof(uint32_t), st);
+  cudaMemsetAsync(c.ldmax + 1, 0, 2 * sizeof(uint32_t), st);
+}
+
 // substep k of the current call; parity selects the mirror (FP32) or the T
 // buffer (FP64) that holds the previous snapshot.
 cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
@@ -881,6 +1009,19 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
   const int32_t n = (int32_t)c.n;
   const bool laser = c.p.laser_on && c.have_depth;
   if (c.local) {
+    if (local_tile(c)) {
+      if (k == 0) local_tier_reset(c, st);
+      const int32_t P = (c.n_max + 1) / 2;
+      const int32_t tb = c.tile_floats;
+      const size_t shm = sizeof(float) * kTileBufs * (size_t)tb;
+      const int32_t tg = c.tile_grid[P == 9 ? 0 : 1];
+      const unsigned grid = (unsigned)(c.nwork < tg ? c.nwork : tg);
+      const unsigned nt = kTileThreads + 32;
+      const StageArgs none{};
+      if (P == 9) substep_tile_kernel<false, 9, false, 256, false, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      else substep_tile_kernel<false, 16, false, 256, false, true><<<grid, nt, shm, st>>>(c.reps, c.work, c.nwork, tb, parity, k, none);
+      return cudaGetLastError();
+    }
     if (c.p.flux_prec == 1) {
       const double *Tin = c.T[parity];
       double *Tout = c.T[parity ^ 1];
@@ -891,13 +1032,17 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
         substep_local_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d,
                                                                       c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt);
     } else if (laser) {
+      if (k == 0) local_tier_reset(c, st);
       substep_local_f32_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity],
                                                                    c.dmir[parity ^ 1], c.uhi, c.dlo, c.A, c.uTl,
-                                                                   c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
+                                                                   c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt,
+                                                                   c.ldmax);
     } else {
+      if (k == 0) local_tier_reset(c, st);
       substep_local_f32_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity],
                                                                     c.dmir[parity ^ 1], c.uhi, c.dlo, c.A, c.uTl,
-                                                                    c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt);
+                                                                    c.srcw, c.pulse_f, k, c.coef, c.err, c.wgt,
+                                                                    c.ldmax);
     }
     return cudaGetLastError();
   }
@@ -1014,6 +1159,8 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
                                    {(const void *)substep_tile_kernel<true, 16, false, 256, true>,
                                     (const void *)substep_tile_kernel<false, 16, false, 256, true>,
                                     (const void *)substep_tile_kernel<false, 16, false, 128, true>}};
+  const void *inst_local[2] = {(const void *)substep_tile_kernel<false, 9, false, 256, false, true>,
+                               (const void *)substep_tile_kernel<false, 16, false, 256, false, true>};
   int32_t g[2] = {0, 0}, g128[2] = {0, 0};
   for (int w = 0; w < 2; ++w) {
     int bps = 1 << 30;
@@ -1028,6 +1175,10 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
     }
     for (int l = 0; l < 3 && ok; ++l)
       ok = cudaFuncSetAttribute(inst_border[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+           cudaSuccess;
+    // the LOCAL form's instances run on the same grid
+    if (ok)
+      ok = cudaFuncSetAttribute(inst_local[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
            cudaSuccess;
     if (ok) g[w] = bps * num_sms;
     int b = 0;

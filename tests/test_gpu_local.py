@@ -116,3 +116,18 @@ def test_local_form_refusals_and_plain_fallbacks():
     with pytest.raises(EhcError):
         EhcBatch(p, [s, s])
 
+
+def test_local_row_tiles_equal_the_general_kernel():
+    """The LOCAL form on the row tiles (16-bit tile indices, the default for FCC
+    lists) and on the general kernel (forced by a table wider than 32 slots): the
+    same pair terms in the same order with the same series order per substep,
+    TwoSum sums, the same update."""
+    s = I.track_system(16, 5, peak=20000.0, r0=8.0)
+    p = dict(I.params_track(), ce_mode=1)
+    a, _, _ = run_gpu(s, p, 3, 40)
+    b, _, _ = run_gpu(s, dict(p, max_neighbors=40), 3, 40)
+    Ta, Tb = a.get_te().cpu().numpy(), b.get_te().cpu().numpy()
+    d = relerr(Ta, Tb)
+    assert d < 1e-7, d
+    assert abs(a.energy()["drift"]) < 1e-12
+    print(f"LOCAL row tiles vs general kernel: {d:.1e}")
