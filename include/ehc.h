@@ -238,6 +238,15 @@ int ehc_forces(ehc_ctx *c, double *F_dev, double *epot_host);
  * the forces of the new positions. */
 int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
 
+/* Failure-detection probe of the bounded device waits (no counterpart in the
+ * paper): one block waits, with the mbarrier poll loop of the row-tile kernels
+ * and a budget of `polls` polls, on a phase that completes (complete != 0) or
+ * that nothing completes (complete = 0).  Returns EHC_E_TIMEOUT when the wait
+ * ran out, EHC_OK otherwise; the result travels in a word of its own, so the
+ * context's error state is untouched and the context stays usable.
+ * Synchronises.  EHC_E_INVAL for polls = 0. */
+int ehc_probe_wait(ehc_ctx *c, uint32_t polls, int32_t complete);
+
 /* Largest speed max_i |v_i| [A/fs] of v_dev [N,3] into *vmax_host, for a variable
  * MD step (the cascade runs of Sec. 5 cap the displacement per step).  Synchronises. */
 int ehc_max_speed(ehc_ctx *c, const double *v_dev, double *vmax_host);

@@ -83,6 +83,7 @@ _SIGS = {
     "ehc_forces": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "ehc_kick": (_I, [_P, _P, _P, ctypes.c_double]),
     "ehc_max_speed": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ehc_probe_wait": (_I, [_P, ctypes.c_uint32, ctypes.c_int32]),
     "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
     "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
     "ehc_sync": (_I, [_P]),
@@ -303,6 +304,10 @@ class Ehc:
     def kick(self, v, F, dt_fs: float):
         """v += dt F / m in place."""
         _check(self._lib.ehc_kick(self._h, _ptr(v), _ptr(F), float(dt_fs)), "ehc_kick")
+
+    def probe_wait(self, polls: int, complete: bool) -> int:
+        """Return code of the bounded-wait probe (EHC_E_TIMEOUT when it ran out)."""
+        return int(self._lib.ehc_probe_wait(self._h, int(polls), 1 if complete else 0))
 
     def max_speed(self, v) -> float:
         r = ctypes.c_double()

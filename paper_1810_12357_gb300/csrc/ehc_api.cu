@@ -815,6 +815,20 @@ int ehc_kick(ehc_ctx *h, double *v_dev, const double *F_dev, double dt_fs) {
   return EHC_OK;
 }
 
+int ehc_probe_wait(ehc_ctx *h, uint32_t polls, int32_t complete) {
+  if (!h || polls == 0) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  // its own word (scal[7] as int32): the context's sticky error word stays untouched
+  int32_t *flag = reinterpret_cast<int32_t *>(c.scal + 7);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), c.stream));
+  CK(launch_wait_probe(polls, complete ? 1 : 0, flag, c.stream));
+  int32_t got = 0;
+  CK(cudaMemcpyAsync(&c.scal_host[7], flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  std::memcpy(&got, &c.scal_host[7], sizeof(got));
+  return (got & ERR_TIMEOUT) ? EHC_E_TIMEOUT : EHC_OK;
+}
+
 int ehc_max_speed(ehc_ctx *h, const double *v_dev, double *vmax_host) {
   if (!h || !vmax_host || (h->c.n > 0 && !v_dev)) return EHC_E_INVAL;
   Ctx &c = h->c;

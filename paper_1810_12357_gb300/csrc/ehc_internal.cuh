@@ -198,6 +198,8 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t s);
 cudaError_t launch_split(Ctx &c, cudaStream_t s);
 cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
 bool tile_path(const Ctx &c);
+// the bounded-wait probe (kernels_substep.cu): ERR_TIMEOUT into *flag if the wait runs out
+cudaError_t launch_wait_probe(uint32_t polls, int complete, int32_t *flag, cudaStream_t st);
 // the LOCAL form's substeps run on the row tiles (single precision, no laser source)
 bool local_tile(const Ctx &c);
 // tile capacity tb with headroom for the largest staged tile, the shared-memory

@@ -369,6 +369,23 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
+// Failure-detection probe: the bounded wait of the tile kernels on an mbarrier
+// phase that completes (count 1, one arrival) or never completes (count 2, one
+// arrival: a flag nothing sets).  After `polls` unsuccessful polls the block
+// records ERR_TIMEOUT in *flag and returns; no asynchronous copy is involved.
+__global__ void wait_probe_kernel(uint32_t polls, int complete, int32_t *__restrict__ flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, complete ? 1u : 2u);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive(&bar);
+  bool ok = false;
+  for (uint32_t i = 0; i < polls && !ok; ++i) ok = mbar_test(&bar, 0);
+  if (!ok) atomicOr(flag, ERR_TIMEOUT);
+}
+
 // per-atom inputs of a Chebyshev stage
 struct StageIn {
   float zm1, zm2, y0, F0;
@@ -956,6 +973,11 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_wait_probe(uint32_t polls, int complete, int32_t *flag, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(polls, complete, flag);
+  return cudaGetLastError();
+}
 
 // the row-tile kernel applies when two buffers fit in shared memory and the
 // table holds at most 32 neighbours per atom
