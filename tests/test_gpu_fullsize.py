@@ -193,3 +193,46 @@ def test_fullsize_forces():
     assert pe == pytest.approx(float(Eo.sum()), rel=1e-6)
     print(f"full-size forces: max |dF| {err:.1e} eV/A of max {np.abs(Fo).max():.2f}, E_pot rel "
           f"{abs(pe - Eo.sum()) / abs(Eo.sum()):.1e}")
+
+
+def test_fullsize_laser_slab():
+    """The laser slab at its full size (60 x 60 x 200 cells, 2 % vacancies: 2,822,400
+    atoms, free z surfaces): the neighbour list bit for bit, and after 10 substeps
+    at the pulse peak, sampled atoms below the surface and deep in the slab against
+    the oracle with the source term on their 10-hop neighbourhood."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.laser_slab_system(60, 200, 3)
+    p = I.params_laser()
+    assert s.x.shape[0] == 2822400
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    g.set_depth(s.depth)
+    g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
+    rg, cg = g.export_neighbors(cap_per_atom=24)
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type, depth=s.depth)
+    sim.set_te(s.Te)
+    sim.build(s.x, s.v)
+    assert np.array_equal(rg, sim.rowptr)
+    assert np.array_equal(cg, sim.col)
+    t0 = 45.0
+    g.substep(N_SUB_SAMPLE, t0)
+    Tg = g.get_te().cpu().numpy()
+    rng = np.random.default_rng(5)
+    picks = np.concatenate([rng.choice(np.flatnonzero(s.depth < 3.0), 4, replace=False),
+                            rng.choice(np.flatnonzero((s.depth > 100.0) & (s.depth < 200.0)), 4, replace=False),
+                            rng.choice(np.flatnonzero(s.depth > 600.0), 4, replace=False)])
+    worst = 0.0
+    for a in picks:
+        ball, loc, rp, col = _ball(sim.rowptr, sim.col, a, N_SUB_SAMPLE)
+        T = s.Te[ball].copy()
+        Aacc = np.zeros(ball.size)
+        st, _ = oracle.substeps(rp, col, T, sim.Tl[ball].copy(), sim.chi[ball].copy(), Aacc, N_SUB_SAMPLE,
+                                p["dt_sub"], p["Tmax"], sim.K, sim.cG, sim.VG, depth=s.depth[ball].copy(),
+                                source=p["laser"], Ce_SI=sim.Ce, vatom_A3=sim.vatom, t_start=t0)
+        assert st == N_SUB_SAMPLE
+        worst = max(worst, abs(Tg[a] - T[loc[a]]) / T[loc[a]])
+    assert worst < 1e-4, worst
+    # the source heated the surface layer within the 10 substeps
+    assert Tg[s.depth < 3.0].mean() > s.Te[s.depth < 3.0].mean() + 1e-3
+    print(f"full-size laser slab: list bit-exact, sampled T_e max rel err {worst:.3e}")
