@@ -82,3 +82,24 @@ def test_tile_widths_and_tuner_give_identical_results(batched):
             res.append(g.get_te().cpu().numpy())
     assert np.array_equal(res[0], res[1])
     assert np.array_equal(res[0], res[2])
+
+
+def test_fullsize_batch_sampled_replicas():
+    """The batched workload at its full size (256 replicas, seed 4: about 33 M
+    atoms) in one batch: one MD step of 20 substeps; three replicas (the smallest,
+    a middle one and the largest) against the oracle run of the whole replica."""
+    systems = I.batch_replicas(256, 4)
+    p = I.params_track()
+    sizes = np.array([s.n for s in systems])
+    assert sizes.sum() > 30_000_000
+    b, _, _ = _run_batch(systems, p, 1, 20)
+    Tb = b.get_te().cpu().numpy()
+    order = np.argsort(sizes)
+    for r in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        s = systems[r]
+        sim, _, _ = run_oracle(s, p, 1, 20)
+        lo = b.offsets[r]
+        err = float(np.max(np.abs(Tb[lo:lo + s.n] - sim.T) / sim.T))
+        assert err < 1e-4, (r, s.n, err)
+        assert abs(b.energy(r)["drift"]) < 1e-9
+        print(f"full-size batch: replica {r} ({s.n:,} atoms) T_e err {err:.2e}")
