@@ -238,6 +238,26 @@ int ehc_forces(ehc_ctx *c, double *F_dev, double *epot_host);
  * the forces of the new positions. */
 int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
 
+/* Ghost exchange of a domain-decomposed run (one context per domain: its owned
+ * atoms plus the ghost atoms their neighbour rows reach; the paper's MPI fix
+ * exchanged the ghosts' electronic temperatures before every substep, Sec. 2.1).
+ * ehc_get_te_at writes the current T_e of the caller-order atoms idx_dev[0..m)
+ * (int32, device) to out_dev[0..m) (FP64, device); ehc_set_te_at overwrites
+ * them with vals_dev[0..m) between substep calls, the single-precision state
+ * included (the next substep then evaluates the full series everywhere).
+ * Indices outside [0, n) are skipped and reported as EHC_E_INDEX by the next
+ * synchronising call.  EHC_E_STATE before ehc_set_te.  Asynchronous. */
+int ehc_get_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, double *out_dev);
+int ehc_set_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, const double *vals_dev);
+
+/* System means of the MD step (Sec. 2: mean electronic and classical lattice
+ * temperature) in place of the ones the last ehc_build_neighbors computed from
+ * this context's atoms: for a domain of a decomposed system, whose means are the
+ * all-reduced sums over the owned atoms of every domain divided by the total
+ * count.  Recomputes C_e, kappa_e, K and the stability number for the step's
+ * substeps and hand-over.  EHC_E_STATE before the first build. */
+int ehc_set_step_means(ehc_ctx *c, double Te_mean, double Tlat);
+
 /* Failure-detection probe of the bounded device waits (no counterpart in the
  * paper): one block waits, with the mbarrier poll loop of the row-tile kernels
  * and a budget of `polls` polls, on a phase that completes (complete != 0) or

@@ -84,6 +84,9 @@ _SIGS = {
     "ehc_kick": (_I, [_P, _P, _P, ctypes.c_double]),
     "ehc_max_speed": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "ehc_probe_wait": (_I, [_P, ctypes.c_uint32, ctypes.c_int32]),
+    "ehc_get_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "ehc_set_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "ehc_set_step_means": (_I, [_P, ctypes.c_double, ctypes.c_double]),
     "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
     "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
     "ehc_sync": (_I, [_P]),
@@ -304,6 +307,20 @@ class Ehc:
     def kick(self, v, F, dt_fs: float):
         """v += dt F / m in place."""
         _check(self._lib.ehc_kick(self._h, _ptr(v), _ptr(F), float(dt_fs)), "ehc_kick")
+
+    def get_te_at(self, idx, out=None):
+        """T_e of the caller-order atoms idx (int32 device tensor) into a new or given tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(idx.numel(), dtype=torch.float64, device="cuda")
+        _check(self._lib.ehc_get_te_at(self._h, _ptr(idx), int(idx.numel()), _ptr(out)), "ehc_get_te_at")
+        return out
+
+    def set_te_at(self, idx, vals):
+        _check(self._lib.ehc_set_te_at(self._h, _ptr(idx), int(idx.numel()), _ptr(vals)), "ehc_set_te_at")
+
+    def set_step_means(self, Te_mean: float, Tlat: float):
+        _check(self._lib.ehc_set_step_means(self._h, float(Te_mean), float(Tlat)), "ehc_set_step_means")
 
     def probe_wait(self, polls: int, complete: bool) -> int:
         """Return code of the bounded-wait probe (EHC_E_TIMEOUT when it ran out)."""

@@ -553,42 +553,12 @@ int build_enqueue(Ctx &c, const double *x_dev, const double *v_dev, cudaEvent_t 
   return EHC_OK;
 }
 
-// second half, after the stream has been synchronised: per-step scalars (Sec. 2
-// means, C_e, kappa_e, Eq. Kij), ledger, stability, coefficient upload
-int build_finish(Ctx &c, bool own_tiles) {
-  int32_t w[4];
-  std::memcpy(w, c.scal_host + 16, sizeof(w));
-  c.dev_err = w[0];
-  c.n_max = w[1];
-  c.staged_max = w[2];
-  c.row_max = w[3];
-  c.builds += 1;
-  // size the row-tile buffers (grown only when a build outgrows them)
-  if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
-    int32_t tb = 0, grid[2] = {0, 0}, grid128[2] = {0, 0};
-    if (tile_size(c.staged_max, c.num_sms, &tb, grid, grid128)) {
-      c.tile_floats = tb;
-      c.tile_nt = 0;
-      c.tile_grid128[0] = grid128[0];
-      c.tile_grid128[1] = grid128[1];
-      c.tile_grid[0] = grid[0];
-      c.tile_grid[1] = grid[1];
-    }
-  }
-  const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
-  c.wsum = c.scal_host[3];
-  c.Tmin = -c.scal_host[4];
-  // ledger: close the previous MD step with its own C_e (the LOCAL form's E_e is
-  // evaluated directly from the temperatures)
-  if (c.VC_prev > 0 && !c.local) {
-    c.E_base += c.VC_prev * (sumT - c.ST_base);
-    c.ST_base = sumT;
-    if (c.bres) c.E_res += c.VC_prev * c.scal_host[10] * (c.p.flux_prec == 1 ? 1.0 : c.p.Tmax_K);
-  }
-  const double N = (double)(c.n > 0 ? c.n : 1);
-  // system means (Sec. 2): mean electronic temperature, classical T_lat = K / ((3/2) k_B N)
-  c.Te_mean = sumT / N;
-  c.Tlat = sumKE / (1.5 * kKB_EV * N);
+// per-step scalars from the system means of the step (Sec. 2: mean electronic
+// temperature, classical lattice temperature): C_e, kappa_e, K of Eq. Kij, the
+// stability number and the coefficient upload
+int step_coefficients(Ctx &c, double Te_mean, double Tlat) {
+  c.Te_mean = Te_mean;
+  c.Tlat = Tlat;
   double Ce = c.p.gamma_Ce * c.Te_mean;
   const double cap = cap_SI(c);
   if (cap > 0 && Ce > cap) Ce = cap;
@@ -662,6 +632,45 @@ int build_finish(Ctx &c, bool own_tiles) {
     cf.dtVGu = (double)cf.dtgu_f * c.vatom * 1e-30 * gam * Tm * Tm / kEV_J;
   }
   CK(cudaMemcpyAsync(c.coef, c.coef_host, sizeof(StepCoef), cudaMemcpyHostToDevice, c.stream));
+  return EHC_OK;
+}
+
+// second half, after the stream has been synchronised: per-step scalars (Sec. 2
+// means, C_e, kappa_e, Eq. Kij), ledger, stability, coefficient upload
+int build_finish(Ctx &c, bool own_tiles) {
+  int32_t w[4];
+  std::memcpy(w, c.scal_host + 16, sizeof(w));
+  c.dev_err = w[0];
+  c.n_max = w[1];
+  c.staged_max = w[2];
+  c.row_max = w[3];
+  c.builds += 1;
+  // size the row-tile buffers (grown only when a build outgrows them)
+  if (own_tiles && c.p.flux_prec == 0 && c.staged_max > c.tile_floats) {
+    int32_t tb = 0, grid[2] = {0, 0}, grid128[2] = {0, 0};
+    if (tile_size(c.staged_max, c.num_sms, &tb, grid, grid128)) {
+      c.tile_floats = tb;
+      c.tile_nt = 0;
+      c.tile_grid128[0] = grid128[0];
+      c.tile_grid128[1] = grid128[1];
+      c.tile_grid[0] = grid[0];
+      c.tile_grid[1] = grid[1];
+    }
+  }
+  const double sumT = c.scal_host[0], sumKE = c.scal_host[2];
+  c.wsum = c.scal_host[3];
+  c.Tmin = -c.scal_host[4];
+  // ledger: close the previous MD step with its own C_e (the LOCAL form's E_e is
+  // evaluated directly from the temperatures)
+  if (c.VC_prev > 0 && !c.local) {
+    c.E_base += c.VC_prev * (sumT - c.ST_base);
+    c.ST_base = sumT;
+    if (c.bres) c.E_res += c.VC_prev * c.scal_host[10] * (c.p.flux_prec == 1 ? 1.0 : c.p.Tmax_K);
+  }
+  // system means (Sec. 2): mean electronic temperature, classical T_lat = K / ((3/2) k_B N)
+  const double N = (double)(c.n > 0 ? c.n : 1);
+  const int rc = step_coefficients(c, sumT / N, sumKE / (1.5 * kKB_EV * N));
+  if (rc) return rc;
   if (own_tiles) CK(upload_reps(c));   // a batch keeps its own table of every replica
   c.built = true;
   return err_code(c.dev_err);
@@ -813,6 +822,39 @@ int ehc_kick(ehc_ctx *h, double *v_dev, const double *F_dev, double dt_fs) {
   if (!h || (h->c.n > 0 && (!v_dev || !F_dev)) || !(dt_fs == dt_fs)) return EHC_E_INVAL;
   CK(launch_kick(h->c, v_dev, F_dev, dt_fs));
   return EHC_OK;
+}
+
+int ehc_get_te_at(ehc_ctx *h, const int32_t *idx_dev, int64_t m, double *out_dev) {
+  if (!h || m < 0 || (m > 0 && (!idx_dev || !out_dev))) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  int r = ensure_t(c);
+  if (r) return r;
+  CK(launch_get_at(c, idx_dev, m, out_dev));
+  return EHC_OK;
+}
+
+int ehc_set_te_at(ehc_ctx *h, const int32_t *idx_dev, int64_t m, const double *vals_dev) {
+  if (!h || m < 0 || (m > 0 && (!idx_dev || !vals_dev))) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.have_te) return EHC_E_STATE;
+  if (m == 0) return EHC_OK;
+  c.t_version += 1;
+  CK(launch_set_at(c, idx_dev, m, vals_dev));
+  // the row tiles' value ranges no longer cover the new values: the next substep
+  // takes the full series everywhere
+  if (c.p.flux_prec == 0 && c.ff_valid && c.nrows > 0) {
+    CK(cudaMemsetAsync(c.rrange[c.parity], 0xfe, sizeof(float) * c.nrows, c.stream));
+    CK(cudaMemsetAsync(c.rrange[c.parity] + c.nrows, 0x7f, sizeof(float) * c.nrows, c.stream));
+  }
+  return EHC_OK;
+}
+
+int ehc_set_step_means(ehc_ctx *h, double Te_mean, double Tlat) {
+  if (!h || !(Te_mean >= 0) || !(Tlat >= 0)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  return step_coefficients(c, Te_mean, Tlat);
 }
 
 int ehc_probe_wait(ehc_ctx *h, uint32_t polls, int32_t complete) {

@@ -200,6 +200,9 @@ cudaError_t launch_merge(Ctx &c, int parity, cudaStream_t s);
 bool tile_path(const Ctx &c);
 // the bounded-wait probe (kernels_substep.cu): ERR_TIMEOUT into *flag if the wait runs out
 cudaError_t launch_wait_probe(uint32_t polls, int complete, int32_t *flag, cudaStream_t st);
+// ghost exchange (kernels_halo.cu): T of caller-order atoms idx[0..m) into out; overwrite them
+cudaError_t launch_get_at(Ctx &c, const int32_t *idx, int64_t m, double *out);
+cudaError_t launch_set_at(Ctx &c, const int32_t *idx, int64_t m, const double *vals);
 // the LOCAL form's substeps run on the row tiles (single precision, no laser source)
 bool local_tile(const Ctx &c);
 // tile capacity tb with headroom for the largest staged tile, the shared-memory

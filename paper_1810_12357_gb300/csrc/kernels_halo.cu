@@ -1,0 +1,85 @@
+// kernels_halo.cu -- device side of the domain-decomposed design: reading and
+// overwriting the electronic temperatures of a list of atoms (caller order)
+// between substep calls, for the ghost exchange of the paper's MPI fix
+// (ghost-atom temperatures before every substep, Sec. 2.1).
+//
+// An overwrite keeps the single-precision substep state consistent with T: the
+// float pair of delta = (T - Tref)/Tmax (the global form) or of the energy state
+// w = u(theta) - u_ref with the mirror (the LOCAL form).  Indices outside
+// [0, n) set ERR_INDEX and are skipped (always checked: the list comes from the
+// caller).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ehc_internal.cuh"
+
+namespace ehc {
+
+namespace {
+
+__global__ void get_at_kernel(int64_t m, int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ inv,
+                              const double *__restrict__ T, double *__restrict__ out, int32_t *__restrict__ err) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int32_t i = idx[k];
+  if (i < 0 || i >= n) {
+    atomicOr(err, ERR_INDEX);
+    out[k] = 0.0;
+    return;
+  }
+  out[k] = T[inv ? inv[i] : i];
+}
+
+// mode 0: T only (FP64 path, or a state not yet split); 1: also the float pair of
+// delta (hi in mir, lo in lo); 2: the LOCAL form's energy pair (uhi, lo) and mirror
+__global__ void set_at_kernel(int64_t m, int32_t n, const int32_t *__restrict__ idx, const int32_t *__restrict__ inv,
+                              const double *__restrict__ vals, double *__restrict__ T, float *__restrict__ mir,
+                              float *__restrict__ uhi, float *__restrict__ lo, int mode, double Tref,
+                              double invTmax, double thc, double u_ref, int32_t *__restrict__ err) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int32_t i = idx[k];
+  if (i < 0 || i >= n) {
+    atomicOr(err, ERR_INDEX);
+    return;
+  }
+  const int32_t s = inv ? inv[i] : i;
+  const double v = vals[k];
+  T[s] = v;
+  const double x = (v - Tref) * invTmax;
+  if (mode == 1) {
+    const float h = (float)x;
+    mir[s] = h;
+    lo[s] = (float)(x - (double)h);
+  } else if (mode == 2) {
+    const double w = ue_of(v * invTmax, thc) - u_ref;
+    const float h = (float)w;
+    uhi[s] = h;
+    lo[s] = (float)(w - (double)h);
+    mir[s] = (float)x;
+  }
+}
+
+inline unsigned hblk(int64_t m) { return (unsigned)((m + 255) / 256); }
+
+}  // namespace
+
+cudaError_t launch_get_at(Ctx &c, const int32_t *idx, int64_t m, double *out) {
+  if (m > 0)
+    get_at_kernel<<<hblk(m), 256, 0, c.stream>>>(m, (int32_t)c.n, idx, c.te_orig_order ? nullptr : c.inv_perm[c.cur_inv],
+                                                  c.T[c.tcur], out, c.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_at(Ctx &c, const int32_t *idx, int64_t m, const double *vals) {
+  if (m <= 0) return cudaSuccess;
+  int mode = 0;
+  if (c.p.flux_prec == 0 && c.ff_valid && !c.te_orig_order) mode = c.local ? 2 : 1;
+  const StepCoef &cf = *c.coef_host;
+  set_at_kernel<<<hblk(m), 256, 0, c.stream>>>(m, (int32_t)c.n, idx, c.te_orig_order ? nullptr : c.inv_perm[c.cur_inv],
+                                               vals, c.T[c.tcur], c.dmir[c.parity], c.uhi, c.dlo, mode, c.p.Tref_K,
+                                               1.0 / c.p.Tmax_K, cf.thc, cf.u_ref, c.err);
+  return cudaGetLastError();
+}
+
+}  // namespace ehc

@@ -39,6 +39,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "ehc_internal.cuh"
 
 namespace ehc {
@@ -1164,6 +1167,17 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
   const int32_t tb = ((staged + staged / 8 + 64 + 255) / 256) * 256;
   const int64_t bytes = (int64_t)sizeof(float) * kTileBufs * tb;
   if (bytes > kTileMaxBytes) return false;
+  // the shared-memory limit is an attribute of the kernel function, shared by
+  // every context of the process: it only ever grows, so that a context sized
+  // earlier for larger tiles keeps launching after a smaller one was sized
+  static std::mutex attr_mu;
+  static int64_t attr_bytes = 0;
+  int64_t limit;
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    attr_bytes = std::max(attr_bytes, bytes);
+    limit = attr_bytes;
+  }
   // [width][instance]: 256-thread instances (laser, plain, stage) and 128-thread ones (plain)
   const void *inst[2][3] = {{(const void *)substep_tile_kernel<true, 9, false, 256>,
                              (const void *)substep_tile_kernel<false, 9, false, 256>,
@@ -1189,22 +1203,22 @@ bool tile_size(int32_t staged, int num_sms, int32_t *tb_out, int32_t grid[2], in
     bool ok = true;
     for (int l = 0; l < 3 && ok; ++l) {
       int b = 0;
-      ok = cudaFuncSetAttribute(inst[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+      ok = cudaFuncSetAttribute(inst[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) == cudaSuccess &&
            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inst[w][l], kTileThreads + 32, (size_t)bytes) ==
                cudaSuccess &&
            b > 0;
       bps = b < bps ? b : bps;
     }
     for (int l = 0; l < 3 && ok; ++l)
-      ok = cudaFuncSetAttribute(inst_border[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      ok = cudaFuncSetAttribute(inst_border[w][l], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) ==
            cudaSuccess;
     // the LOCAL form's instances run on the same grid
     if (ok)
-      ok = cudaFuncSetAttribute(inst_local[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      ok = cudaFuncSetAttribute(inst_local[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) ==
            cudaSuccess;
     if (ok) g[w] = bps * num_sms;
     int b = 0;
-    if (cudaFuncSetAttribute(inst128[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+    if (cudaFuncSetAttribute(inst128[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inst128[w], 160, (size_t)bytes) == cudaSuccess && b > 0)
       g128[w] = b * num_sms;
   }
