@@ -250,6 +250,14 @@ int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
 int ehc_get_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, double *out_dev);
 int ehc_set_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, const double *vals_dev);
 
+/* Sums over the caller-order atoms idx_dev[0..m) of this context for the
+ * all-reduce of a domain-decomposed run: sums_host[0] = sum T_e [K] (current),
+ * sums_host[1] = sum (1/2) m |v|^2 [eV] with the velocities of the last build
+ * (the sums the build's system means are made of).  Deterministic (fixed grid).
+ * Synchronises; EHC_E_INDEX if an index is outside [0, n), EHC_E_STATE before
+ * the first build. */
+int ehc_sums_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, double *sums_host);
+
 /* System means of the MD step (Sec. 2: mean electronic and classical lattice
  * temperature) in place of the ones the last ehc_build_neighbors computed from
  * this context's atoms: for a domain of a decomposed system, whose means are the

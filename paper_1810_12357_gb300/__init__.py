@@ -87,6 +87,7 @@ _SIGS = {
     "ehc_get_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
     "ehc_set_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
     "ehc_set_step_means": (_I, [_P, ctypes.c_double, ctypes.c_double]),
+    "ehc_sums_at": (_I, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
     "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
     "ehc_sync": (_I, [_P]),
@@ -318,6 +319,12 @@ class Ehc:
 
     def set_te_at(self, idx, vals):
         _check(self._lib.ehc_set_te_at(self._h, _ptr(idx), int(idx.numel()), _ptr(vals)), "ehc_set_te_at")
+
+    def sums_at(self, idx):
+        """(sum T_e, sum of the kinetic energy [eV]) over the caller-order atoms idx."""
+        out = (ctypes.c_double * 2)()
+        _check(self._lib.ehc_sums_at(self._h, _ptr(idx), int(idx.numel()), out), "ehc_sums_at")
+        return out[0], out[1]
 
     def set_step_means(self, Te_mean: float, Tlat: float):
         _check(self._lib.ehc_set_step_means(self._h, float(Te_mean), float(Tlat)), "ehc_set_step_means")

@@ -850,6 +850,29 @@ int ehc_set_te_at(ehc_ctx *h, const int32_t *idx_dev, int64_t m, const double *v
   return EHC_OK;
 }
 
+int ehc_sums_at(ehc_ctx *h, const int32_t *idx_dev, int64_t m, double *sums_host) {
+  if (!h || !sums_host || m < 0 || (m > 0 && !idx_dev)) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  if (!c.built) return EHC_E_STATE;
+  int r = ensure_t(c);
+  if (r) return r;
+  if (m == 0 || c.n == 0) {
+    sums_host[0] = sums_host[1] = 0.0;
+    return EHC_OK;
+  }
+  // block sums in the global reductions' buffer (kRedBlocks x 6 >= 2 x 152 doubles),
+  // the result in scal[6..7]
+  CK(launch_sums_at(c, idx_dev, m, c.partials, c.scal + 6));
+  CK(cudaMemcpyAsync(c.scal_host + 6, c.scal + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.scal_host + 16, c.err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  sums_host[0] = c.scal_host[6];
+  sums_host[1] = c.scal_host[7];
+  int32_t w[4];
+  std::memcpy(w, c.scal_host + 16, sizeof(w));
+  return (w[0] & ERR_INDEX) ? EHC_E_INDEX : EHC_OK;
+}
+
 int ehc_set_step_means(ehc_ctx *h, double Te_mean, double Tlat) {
   if (!h || !(Te_mean >= 0) || !(Tlat >= 0)) return EHC_E_INVAL;
   Ctx &c = h->c;

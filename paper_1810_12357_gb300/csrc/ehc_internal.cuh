@@ -203,6 +203,9 @@ cudaError_t launch_wait_probe(uint32_t polls, int complete, int32_t *flag, cudaS
 // ghost exchange (kernels_halo.cu): T of caller-order atoms idx[0..m) into out; overwrite them
 cudaError_t launch_get_at(Ctx &c, const int32_t *idx, int64_t m, double *out);
 cudaError_t launch_set_at(Ctx &c, const int32_t *idx, int64_t m, const double *vals);
+// sum T and sum of the kinetic energy [eV] over the listed atoms into out[0..1]
+// (part: 2 x 152 doubles of block sums)
+cudaError_t launch_sums_at(Ctx &c, const int32_t *idx, int64_t m, double *part, double *out);
 // the LOCAL form's substeps run on the row tiles (single precision, no laser source)
 bool local_tile(const Ctx &c);
 // tile capacity tb with headroom for the largest staged tile, the shared-memory

@@ -60,6 +60,62 @@ __global__ void set_at_kernel(int64_t m, int32_t n, const int32_t *__restrict__ 
   }
 }
 
+constexpr int kSumBlocks = 152;   // one block per SM: a fixed grid, deterministic sums
+constexpr double kMVVh = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;   // amu (A/fs)^2 -> eV
+
+__device__ __forceinline__ double hsum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+// block partial sums over the listed atoms: [2b] sum T, [2b + 1] sum of the
+// kinetic energy (1/2) m |v|^2 [eV] with the velocities of the last build
+__global__ void __launch_bounds__(256) sums_at_partial(int64_t m, int32_t n, const int32_t *__restrict__ idx,
+                                                       const int32_t *__restrict__ inv, const double *__restrict__ T,
+                                                       const VelQ *__restrict__ v_s, const int8_t *__restrict__ type_s,
+                                                       MassTable mt, double *__restrict__ part,
+                                                       int32_t *__restrict__ err) {
+  __shared__ double sh[8];
+  double a = 0.0, b = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = idx[k];
+    if (i < 0 || i >= n) {
+      atomicOr(err, ERR_INDEX);
+      continue;
+    }
+    const int32_t s = inv[i];
+    a += T[s];
+    b += 0.5 * mt.m[type_s[s]] * v_s[s].w * kMVVh;
+  }
+  const double ra = hsum(a, sh);
+  const double rb = hsum(b, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ra;
+    part[2 * blockIdx.x + 1] = rb;
+  }
+}
+
+__global__ void __launch_bounds__(256) sums_at_final(const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double sh[8];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < kSumBlocks; k += blockDim.x) {
+    a += part[2 * k];
+    b += part[2 * k + 1];
+  }
+  const double ra = hsum(a, sh);
+  const double rb = hsum(b, sh);
+  if (threadIdx.x == 0) {
+    out[0] = ra;
+    out[1] = rb;
+  }
+}
+
 inline unsigned hblk(int64_t m) { return (unsigned)((m + 255) / 256); }
 
 }  // namespace
@@ -79,6 +135,13 @@ cudaError_t launch_set_at(Ctx &c, const int32_t *idx, int64_t m, const double *v
   set_at_kernel<<<hblk(m), 256, 0, c.stream>>>(m, (int32_t)c.n, idx, c.te_orig_order ? nullptr : c.inv_perm[c.cur_inv],
                                                vals, c.T[c.tcur], c.dmir[c.parity], c.uhi, c.dlo, mode, c.p.Tref_K,
                                                1.0 / c.p.Tmax_K, cf.thc, cf.u_ref, c.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sums_at(Ctx &c, const int32_t *idx, int64_t m, double *part, double *out) {
+  sums_at_partial<<<kSumBlocks, 256, 0, c.stream>>>(m, (int32_t)c.n, idx, c.inv_perm[c.cur_inv], c.T[c.tcur], c.v_s,
+                                                    c.type_s, c.mt, part, c.err);
+  sums_at_final<<<1, 256, 0, c.stream>>>(part, out);
   return cudaGetLastError();
 }
 

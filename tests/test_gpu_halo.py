@@ -37,7 +37,10 @@ def _domains(s, p, n_dom):
     return plans, ctxs
 
 
-def _run(s, p, n_dom):
+KB_EV = 8.617333262e-5
+
+
+def _run(s, p, n_dom, means="undivided"):
     import torch
     from paper_1810_12357_gb300 import Ehc
     ref = Ehc(p, s)
@@ -45,9 +48,23 @@ def _run(s, p, n_dom):
     ref.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
     e = ref.energy()
     plans, ctxs = _domains(s, p, n_dom)
+    if means == "undivided":
+        Te_mean, Tlat = e["Te_mean_step"], e["Tlat_step"]
+    else:
+        # the all-reduce of a multi-GPU run: every domain's sums over its owned atoms
+        sT = sK = 0.0
+        for pl, g in zip(plans, ctxs):
+            own = torch.as_tensor(np.flatnonzero(pl.owned_mask).astype(np.int32), device="cuda")
+            a, b = g.sums_at(own)
+            sT += a
+            sK += b
+        Te_mean, Tlat = sT / s.n, sK / (1.5 * KB_EV * s.n)
+        assert Te_mean == pytest.approx(e["Te_mean_step"], rel=1e-13)
+        assert Tlat == pytest.approx(e["Tlat_step"], rel=1e-13)
     for g in ctxs:
-        g.set_step_means(e["Te_mean_step"], e["Tlat_step"])
-        assert g.energy()["K_per_fs"] == e["K_per_fs"]
+        g.set_step_means(Te_mean, Tlat)
+        if means == "undivided":
+            assert g.energy()["K_per_fs"] == e["K_per_fs"]
     sends = {(pl.rank, q): torch.as_tensor(idx.astype(np.int32), device="cuda")
              for pl in plans for q, idx in pl.send.items()}
     recvs = {(q, pl.rank): torch.as_tensor(idx.astype(np.int32), device="cuda")
@@ -84,3 +101,14 @@ def test_single_precision_domains_agree_with_the_undivided_context():
     # each overwrite: truncation below 3e-8 of the pair term
     assert err < 1e-6, err
     print(f"single-precision domains vs undivided: {err:.1e}")
+
+
+def test_domain_means_from_owned_sums():
+    """The step means from each domain's sums over its owned atoms (ehc_sums_at),
+    added over the domains as an all-reduce would: the FP64 domains agree with the
+    undivided context to the rounding of the sums' order."""
+    s = I.track_system(10, 3, peak=20000.0, r0=6.0)
+    p = dict(I.params_track(), flux_prec=1)
+    T, T_ref = _run(s, p, 2, means="sums")
+    err = float(np.max(np.abs(T - T_ref) / T_ref))
+    assert err < 1e-12, err
