@@ -233,9 +233,11 @@ int ehc_drift(ehc_ctx *c, double *x_dev, const double *v_dev, double dt_fs);
  * NULL (then the call synchronises).  EHC_E_STATE before the first build. */
 int ehc_forces(ehc_ctx *c, double *F_dev, double *epot_host);
 
-/* Velocity-Verlet kick v_i += dt F_i / m_i (caller order, per-type masses, F in
- * eV/A, v in A/fs): called with dt = half the MD step before the drift and after
- * the forces of the new positions. */
+/* Velocity-Verlet kick of Eq. Motion's interatomic part, v_i += dt F_i / m_i
+ * (caller order, per-type masses, F in eV/A, v in A/fs; v_dev [N,3] updated in
+ * place, F_dev [N,3] read; both device, caller-owned): called with dt = half the
+ * MD step before the drift and after the forces of the new positions (the
+ * damping/friction part of Eq. Motion is ehc_couple's).  Asynchronous. */
 int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
 
 /* Ghost exchange of a domain-decomposed run (one context per domain: its owned
