@@ -105,3 +105,29 @@ def test_long_wave_rate_is_that_of_uniform_rates():
     _, _, lam_u, *_ = _decay(40, 40, 1, False)
     assert lam_w == pytest.approx(c * K * k * k * S2 / 6.0, rel=2e-3)
     assert lam_w == pytest.approx(lam_u, rel=2e-3)
+
+
+def test_paper_literal_normalisation_doubles_the_rate():
+    """Z b^2 of Eq. Kij read literally for FCC (Z = 12 nearest neighbours, b = a/sqrt2:
+    Z b^2 = 6 a^2) against the default second moment of the 18-neighbour shell
+    (S2 = 12 a^2): K doubles, so a sin mode decays at twice the lattice-sum rate."""
+    a = I.CU_A
+    x = I.fcc_lattice(10, 3, 3, a)
+    box = np.array([10 * a, 3 * a, 3 * a])
+    per = np.array([1, 1, 1], dtype=np.int32)
+    rowptr, col = oracle.neighbors(x, box, per, 4.0)
+    k = 2 * math.pi / (10 * a)
+    basis = np.sin(k * x[:, 0])
+    T0, amp, dt, n = 300.0, 1e-4, 1e-4, 50
+    zeros = np.zeros(x.shape[0])
+    rates = []
+    for zb2 in (I.fcc_shell_s2(a, 4.0), 6.0 * a * a):
+        K = 2.0 * 3 * 400.0 / (96.6 * 300.0 * zb2 * 1e-20) * 1e-15
+        T = T0 + amp * basis
+        oracle.substeps(rowptr, col, T, zeros, np.zeros(x.shape[0], np.uint8), zeros.copy(), n, dt, 1e5, K,
+                        0.0, 0.0)
+        a1 = float((T - T0) @ basis / (basis @ basis))
+        # explicit Euler: the mode's factor per substep is 1 - dt lambda exactly
+        rates.append((1.0 - (a1 / amp) ** (1.0 / n)) / dt)
+    assert I.fcc_shell_s2(a, 4.0) == pytest.approx(12 * a * a, rel=1e-12)
+    assert rates[1] == pytest.approx(2.0 * rates[0], rel=1e-5)
