@@ -88,8 +88,10 @@ extern "C" {
  *                   (2 d / Z b^2) kappa_ij T_max f_ij with kappa_ij = (kappa_i + kappa_j) / 2;
  *                   each substep advances the atom's electron energy density U = int C_e dT
  *                   and inverts it in closed form, so sum_i U_i is conserved and the ledger's
- *                   E_e is sum_i V_atom U(T_i).  Runs on the general single-precision and the
- *                   FP64 substep kernels; no border (ehc_set_border: EHC_E_STATE), batch,
+ *                   E_e is sum_i V_atom U(T_i).  Runs on the row tiles (one series order for
+ *                   each substep, from the previous substep's largest |Delta|), the general
+ *                   single-precision kernel (laser source, pair weights, wide tables) and the
+ *                   FP64 kernel; no border (ehc_set_border: EHC_E_STATE), batch,
  *                   network or window training (EHC_E_INVAL); ehc_cheb_step and ehc_nn_step
  *                   advance such a context with plain substeps.  The stability number is
  *                   dt (2 n_max K + G / C_min) with K = 2 d kappa0 / (gamma Z b^2 T_lat)
