@@ -150,3 +150,54 @@ def test_stopping_matches_the_oracle(ce_mode, couple_mode):
     eg, eo = g.energy(), sim.energy()
     assert eg["E_lat"] == pytest.approx(eo["E_lat"], rel=1e-10 if couple_mode == 0 else 1e-8)
     assert abs(eg["drift"]) < 1e-12 and abs(eo["drift"]) < 1e-12
+
+
+def test_cascade_with_a_variable_step_keeps_the_total_energy():
+    """A small cascade (Sec. 5 in miniature): a 1 keV knock-on atom aimed at a nearest
+    neighbour in a 4,000-atom lattice, velocity-Verlet with the step
+    dt = min(0.1 fs, 0.02 A / max |v|)
+    (ehc_max_speed), the electron substeps of 1e-3 fs sized to each step,
+    electronic stopping above 10 eV and the damping hand-over: the step varies,
+    the knock-on atom's energy spreads, and KE + PE + E_e stays put."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.hot_spot_system(10, 6, peak=300.0, disp_sigma=0.02)
+    pka = 1234
+    m = s.mass_amu[s.type[pka]]
+    s.v[pka] = np.array([0.7071, 0.7071, 0.02]) * math.sqrt(2 * 1000.0 / (m * MVV))
+    p = dict(I.params_track(), **MORSE, couple_mode=0, stop_beta=1e-5, stop_ecut=10.0)
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    x = torch.as_tensor(s.x, device="cuda").contiguous()
+    v = torch.as_tensor(s.v, device="cuda").contiguous()
+    mm = torch.as_tensor(s.mass_amu[s.type], device="cuda")
+    g.build_neighbors(x, v)
+    F, pe = g.forces()
+    e0 = g.energy()
+    tot0 = 0.5 * float((mm[:, None] * v * v).sum()) * MVV + pe + e0["E_e"]
+    ke_pka0 = 0.5 * m * float((v[pka] ** 2).sum()) * MVV
+    dts, tots = [], []
+    t = 0.0
+    for step in range(150):
+        vmax = g.max_speed(v)
+        n_sub = max(1, int(round(min(0.1, 0.02 / vmax) / p["dt_sub"])))
+        dt = n_sub * p["dt_sub"]
+        g.kick(v, F, 0.5 * dt)
+        g.drift(x, v, dt)
+        g.build_neighbors(x, v)
+        F, pe = g.forces(F)
+        g.kick(v, F, 0.5 * dt)
+        g.substep(n_sub, t)
+        g.couple(v, dt)
+        t += dt
+        dts.append(dt)
+        tots.append(0.5 * float((mm[:, None] * v * v).sum()) * MVV + pe + g.energy()["E_e"])
+    ke_pka = 0.5 * m * float((v[pka] ** 2).sum()) * MVV
+    # the oracle run of the same cascade: dt 0.036-0.069 fs, knock-on atom 1000 -> 260 eV,
+    # total energy within 0.10 eV
+    assert min(dts) < 0.7 * max(dts)            # the step grew as the knock-on atom slowed
+    assert ke_pka < 0.5 * ke_pka0
+    assert np.max(np.abs(np.array(tots) - tot0)) < 2e-3 * ke_pka0
+    assert abs(g.energy()["drift"]) < 1e-9
+    print(f"cascade: dt {min(dts):.3f}-{max(dts):.3f} fs over {t:.2f} fs, knock-on KE {ke_pka0:.0f} -> "
+          f"{ke_pka:.1f} eV, total energy spread {np.ptp(tots):.2e} eV")
