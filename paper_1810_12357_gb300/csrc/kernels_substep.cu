@@ -167,21 +167,33 @@ struct OutPtrs {
 };
 
 // state update of one atom (single-precision path); Ai is the atom's exchanged
-// energy before this substep; returns the new hi
+// energy before this substep, F + Fc its compensated pair sum (the pair terms,
+// exact negatives of each other, summed with TwoSum); returns the new hi.
+// Every increment reaches the float-pair state exactly to first order: dt K F
+// and the coupling term as two-float products (the rounded product, then its
+// exact error), so the state's sum over atoms changes by the coupling and the
+// source only, to the state's 48 bits (the rounding of each atom's own sum and
+// product would otherwise add a bias to the energy of about 1e-10 per 40
+// substeps on a hot system).
 // BORDER: a border atom (fixed, the mask value its caller loaded with the other
 // per-atom inputs) keeps its value, its change goes to o.res
 template <bool LASER, bool BORDER>
-__device__ __forceinline__ float update_atom(int64_t s, float di, float li, float ui, double Ai, float F,
+__device__ __forceinline__ float update_atom(int64_t s, float di, float li, float ui, double Ai, float F, float Fc,
                                              const CoefF &cf, const OutPtrs &o, int k, bool fixed = false) {
-  float inc = cf.dtK * F;
+  const float p0 = __fmul_rn(cf.dtK, F);
+  float er = fmaf(cf.dtK, F, -p0);      // p0 + er == dtK * F exactly
+  er = fmaf(cf.dtK, Fc, er);
   const bool chi = (ui == ui);
-  float d = 0.0f;
+  float d = 0.0f, q0 = 0.0f;
   if (chi) {
     d = fmaf(cf.Tmax, di, ui);           // T_i - T_l,i
-    inc = fmaf(-cf.dtcGn, d, inc);
+    q0 = __fmul_rn(-cf.dtcGn, d);
+    er += fmaf(-cf.dtcGn, d, -q0);       // q0 + its error == -dtcGn * d exactly
   }
   float h = di, l = li;
-  ff_add(h, l, inc);
+  ff_add(h, l, p0);
+  if (chi) ff_add(h, l, q0);
+  ff_add(h, l, er);
   float p = 0.0f, e = 0.0f;
   if (LASER) {
     const float c = o.pulse_f[k], w = o.srcw[s];
@@ -195,7 +207,9 @@ __device__ __forceinline__ float update_atom(int64_t s, float di, float li, floa
     // just added to the float pair, goes to its float-pair reservoir (single-
     // precision arithmetic only, as exact as the state)
     float2 r = o.res[s];
-    ff_add(r.x, r.y, inc);
+    ff_add(r.x, r.y, p0);
+    if (chi) ff_add(r.x, r.y, q0);
+    ff_add(r.x, r.y, er);
     if (LASER) {
       ff_add(r.x, r.y, p);
       ff_add(r.x, r.y, e);
@@ -424,13 +438,23 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
       }
     return update_atom_local(s, di, wh, li, ui, Ai, F, Fc, cf, ra.dmir[parity ^ 1], ra.uhi, ra.lo, ra.A, ra.err);
   }
-  float F = 0.0f;
+  float F = 0.0f, Fc = 0.0f;
+  if (STAGE) {
 #pragma unroll
-  for (int m = 0; m < PP; ++m)
-    if (PP != 16 || m < ra.P) {
-      F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai);
-      F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai);
-    }
+    for (int m = 0; m < PP; ++m)
+      if (PP != 16 || m < ra.P) {
+        F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai);
+        F = pair_acc<TIER>(F, di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai);
+      }
+  } else {
+    // the pair terms (exact negatives of their partners' terms), compensated sum
+#pragma unroll
+    for (int m = 0; m < PP; ++m)
+      if (PP != 16 || m < ra.P) {
+        two_sum_acc(F, Fc, pair_acc<TIER>(0.0f, di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai));
+        two_sum_acc(F, Fc, pair_acc<TIER>(0.0f, di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai));
+      }
+  }
   if (STAGE) {
     // Chebyshev stage on the window's change: z_j = z_{j-1} + nu (z_{j-2} - z_{j-1})
     // - kap z_{j-1} + mut tau K F(Y_{j-1}) + gam tau K F(Y_0), Y_j = Y_0 + z_j
@@ -444,7 +468,7 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
   }
   const OutPtrs o = {ra.dmir[parity ^ 1], ra.lo, ra.A, ra.srcw, ra.pulse_f, ra.err, ra.fix,
                      reinterpret_cast<float2 *>(ra.res)};
-  return update_atom<LASER, BORDER>(s, di, li, ui, Ai, F, load_coef(cf), o, k, fixed);
+  return update_atom<LASER, BORDER>(s, di, li, ui, Ai, F, Fc, load_coef(cf), o, k, fixed);
 }
 
 constexpr int kTileBufs = 2;   // tiles in flight per CTA
@@ -682,7 +706,9 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
   const float di = hin[s];
   const bool fixed = fix && fix[s];
   const float ai = th + di, m2ai = -2.0f * ai;
-  float F = 0.0f;
+  // pair terms (exact negatives of their partners' terms, the weights symmetric)
+  // summed with TwoSum
+  float F = 0.0f, Fc = 0.0f;
   const int32_t *np = nbr + s;
   int j = 0;
   if (wgt) {
@@ -699,12 +725,12 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
 #pragma unroll
       for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
 #pragma unroll
-      for (int u = 0; u < 6; ++u) F = fmaf(wj[u], pair_term(di, dj[u], th, ai, m2ai), F);
+      for (int u = 0; u < 6; ++u) two_sum_acc(F, Fc, __fmul_rn(wj[u], pair_term(di, dj[u], th, ai, m2ai)));
     }
     for (; j < c; ++j)
-      F = fmaf(__ldg(wp + (int64_t)j * n),
-               pair_term(di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai),
-               F);
+      two_sum_acc(F, Fc, __fmul_rn(__ldg(wp + (int64_t)j * n),
+                                   pair_term(di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)),
+                                             th, ai, m2ai)));
   }
   for (; j + 6 <= c; j += 6) {
     int32_t t[6];
@@ -714,12 +740,12 @@ __global__ void __launch_bounds__(256) substep_f32_kernel(
 #pragma unroll
     for (int u = 0; u < 6; ++u) dj[u] = __ldg(hin + t[u]);
 #pragma unroll
-    for (int u = 0; u < 6; ++u) F += pair_term(di, dj[u], th, ai, m2ai);
+    for (int u = 0; u < 6; ++u) two_sum_acc(F, Fc, pair_term(di, dj[u], th, ai, m2ai));
   }
   for (; j < c; ++j)
-    F += pair_term(di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai);
+    two_sum_acc(F, Fc, pair_term(di, __ldg(hin + checked_index(__ldg(np + (int64_t)j * n), n, err)), th, ai, m2ai));
   const OutPtrs o = {hout, lo, A, srcw, pulse_f, err, fix, reinterpret_cast<float2 *>(res)};
-  update_atom<LASER, true>(s, di, lo[s], uTl[s], A[s], F, load_coef(cf), o, k, fixed);
+  update_atom<LASER, true>(s, di, lo[s], uTl[s], A[s], F, Fc, load_coef(cf), o, k, fixed);
 }
 
 // Pair sum of the LOCAL form for one atom with the series order TIER (one order
