@@ -152,20 +152,62 @@ def test_stopping_matches_the_oracle(ce_mode, couple_mode):
     assert abs(eg["drift"]) < 1e-12 and abs(eo["drift"]) < 1e-12
 
 
-def test_cascade_with_a_variable_step_keeps_the_total_energy():
-    """A small cascade (Sec. 5 in miniature): a 1 keV knock-on atom aimed at a nearest
-    neighbour in a 4,000-atom lattice, velocity-Verlet with the step
-    dt = min(0.1 fs, 0.02 A / max |v|)
-    (ehc_max_speed), the electron substeps of 1e-3 fs sized to each step,
-    electronic stopping above 10 eV and the damping hand-over: the step varies,
-    the knock-on atom's energy spreads, and KE + PE + E_e stays put."""
-    import torch
-    from paper_1810_12357_gb300 import Ehc
+def _cascade_system():
     s = I.hot_spot_system(10, 6, peak=300.0, disp_sigma=0.02)
     pka = 1234
     m = s.mass_amu[s.type[pka]]
     s.v[pka] = np.array([0.7071, 0.7071, 0.02]) * math.sqrt(2 * 1000.0 / (m * MVV))
     p = dict(I.params_track(), **MORSE, couple_mode=0, stop_beta=1e-5, stop_ecut=10.0)
+    return s, p, pka
+
+
+def _cascade_n_sub(vmax, dt_sub):
+    # the step dt = min(0.1 fs, 0.02 A / max |v|) in whole electron substeps
+    return max(1, int(round(min(0.1, 0.02 / vmax) / dt_sub)))
+
+
+def _oracle_cascade(s, p, n_md):
+    """The cascade on the oracle: velocity-Verlet with the oracle's forces and
+    kicks, the largest speed from the FP64 velocities, substeps and hand-over."""
+    sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+    sim.set_te(s.Te)
+    x, v = s.x.copy(), s.v.copy()
+    mass = sim.mass
+    sim.build(x, v)
+    F, pe = sim.forces()
+    tot0 = 0.5 * float((mass[:, None] * v * v).sum()) * MVV + pe + sim.energy()["E_e"]
+    subs, tots = [], []
+    t = 0.0
+    for step in range(n_md):
+        n_sub = _cascade_n_sub(float(np.sqrt((v * v).sum(axis=1)).max()), p["dt_sub"])
+        dt = n_sub * p["dt_sub"]
+        oracle.kick(v, F, mass, 0.5 * dt)
+        x = I.wrap(x + v * dt, s.box, s.periodic)
+        sim.build(x, v)
+        F, pe = sim.forces()
+        oracle.kick(v, F, mass, 0.5 * dt)
+        sim.substeps(n_sub, t)
+        sim.couple(v, dt)
+        t += dt
+        subs.append(n_sub)
+        tots.append(0.5 * float((mass[:, None] * v * v).sum()) * MVV + pe + sim.energy()["E_e"])
+    return sim, v, np.array(subs), tot0, np.array(tots)
+
+
+def test_cascade_with_a_variable_step_matches_the_oracle():
+    """A small cascade (Sec. 5 in miniature): a 1 keV knock-on atom aimed at a nearest
+    neighbour in a 4,000-atom lattice, velocity-Verlet with the step
+    dt = min(0.1 fs, 0.02 A / max |v|)
+    (ehc_max_speed), the electron substeps of 1e-3 fs sized to each step,
+    electronic stopping above 10 eV and the damping hand-over.  The oracle runs the
+    same cascade: the GPU takes the same step sequence, its knock-on atom ends with
+    the oracle's kinetic energy, and KE + PE + E_e stays within 0.3 eV on both."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s, p, pka = _cascade_system()
+    m = s.mass_amu[s.type[pka]]
+    n_md = 150
+    sim, vo, subs_o, tot0_o, tots_o = _oracle_cascade(s, p, n_md)
     g = Ehc(p, s)
     g.set_te(s.Te)
     x = torch.as_tensor(s.x, device="cuda").contiguous()
@@ -176,11 +218,10 @@ def test_cascade_with_a_variable_step_keeps_the_total_energy():
     e0 = g.energy()
     tot0 = 0.5 * float((mm[:, None] * v * v).sum()) * MVV + pe + e0["E_e"]
     ke_pka0 = 0.5 * m * float((v[pka] ** 2).sum()) * MVV
-    dts, tots = [], []
+    subs, tots = [], []
     t = 0.0
-    for step in range(150):
-        vmax = g.max_speed(v)
-        n_sub = max(1, int(round(min(0.1, 0.02 / vmax) / p["dt_sub"])))
+    for step in range(n_md):
+        n_sub = _cascade_n_sub(g.max_speed(v), p["dt_sub"])
         dt = n_sub * p["dt_sub"]
         g.kick(v, F, 0.5 * dt)
         g.drift(x, v, dt)
@@ -190,14 +231,22 @@ def test_cascade_with_a_variable_step_keeps_the_total_energy():
         g.substep(n_sub, t)
         g.couple(v, dt)
         t += dt
-        dts.append(dt)
+        subs.append(n_sub)
         tots.append(0.5 * float((mm[:, None] * v * v).sum()) * MVV + pe + g.energy()["E_e"])
+    subs, tots = np.array(subs), np.array(tots)
     ke_pka = 0.5 * m * float((v[pka] ** 2).sum()) * MVV
-    # the oracle run of the same cascade: dt 0.036-0.069 fs, knock-on atom 1000 -> 260 eV,
-    # total energy within 0.10 eV
-    assert min(dts) < 0.7 * max(dts)            # the step grew as the knock-on atom slowed
+    ke_pka_o = 0.5 * m * float((vo[pka] ** 2).sum()) * MVV
+    # the same variable step, MD step for MD step
+    assert np.array_equal(subs, subs_o)
+    assert subs.min() < 0.7 * subs.max()        # the step grew as the knock-on atom slowed
+    # the knock-on atom gave up most of its energy, the same amount on both sides
     assert ke_pka < 0.5 * ke_pka0
-    assert np.max(np.abs(np.array(tots) - tot0)) < 2e-3 * ke_pka0
+    assert ke_pka == pytest.approx(ke_pka_o, rel=1e-3)
+    assert float(np.max(np.abs(v.cpu().numpy() - vo))) < 1e-3 * float(np.abs(vo).max())
+    # total energy KE + PE + E_e kept on both sides
+    assert np.max(np.abs(tots - tot0)) < 0.3
+    assert np.max(np.abs(tots_o - tot0_o)) < 0.3
     assert abs(g.energy()["drift"]) < 1e-9
-    print(f"cascade: dt {min(dts):.3f}-{max(dts):.3f} fs over {t:.2f} fs, knock-on KE {ke_pka0:.0f} -> "
-          f"{ke_pka:.1f} eV, total energy spread {np.ptp(tots):.2e} eV")
+    print(f"cascade: dt {p['dt_sub'] * subs.min():.3f}-{p['dt_sub'] * subs.max():.3f} fs over {t:.2f} fs, "
+          f"knock-on KE {ke_pka0:.0f} -> {ke_pka:.2f} eV (oracle {ke_pka_o:.2f}), total energy spread "
+          f"{np.ptp(tots):.2e} eV (oracle {np.ptp(tots_o):.2e})")
