@@ -4,8 +4,9 @@ coefficients (ehc_cheb_train_step).
 
 Training windows come from the plain method itself: a context runs n_w
 explicit substeps of Eq. HeatTransport with the coupling switched off (G = 0),
-and each (state, state n_w substeps later) pair is one window.  The network is
-Both are trained on the GPU by the library's own forward/backward kernels and Adam.
+and each (state, state n_w substeps later) pair is one window; rollouts chain
+several windows of one trajectory.  Both propagators are trained on the GPU by
+the library's own forward/backward kernels and Adam.
 """
 from __future__ import annotations
 
@@ -118,3 +119,45 @@ def train_rollout(model, data, steps: int, lr: float = 3e-3, power: int = 8, lr_
         rate = lr if (lr_final is None or k < steps * 3 // 4) else lr_final
         hist.append(model.train_rollout(t0, tt, rate, ctx=ctx, power=power))
     return hist
+
+
+def train_track_window(n_w: int = 100, stages: int = 15, damping: float = 2.0 / 13.0, order: int = 2,
+                       train_steps: int = 400, power: int = 2, nwin: int = 6):
+    """Stage coefficients of the learned window for the swift-ion track: Adam on
+    rollouts of `nwin` chained windows against the plain method's trajectories
+    (coupling off) of 256,000-atom track and hot-spot cells (40^3 cells), from the
+    damped Chebyshev values of the given order, each rollout started after the
+    first window (the sharp initial front is left to the residual test).  Returns
+    the coefficients (nu, mut, kap, gam) and a record of the training with
+    held-out rollout errors of a seventh cell."""
+    import time
+    from . import EhcCheb
+    from . import inputs as I
+    p = I.params_track()
+    t0 = time.perf_counter()
+    train_sys = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
+    train_sys += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
+                  for k in range(3)]
+    data = [generate_trajectory(s, p, nwin, n_w) for s in train_sys]
+    w = EhcCheb(data[0][0], n_w, stages, damping, order=order)
+    beta0 = w.stability()
+    # the stability range of training: the spectrum of the training states
+    spec = max(w.spectrum(t_in, iters=300, ctx=c) for c, t_in, _ in data)
+    hist = train_rollout(w, data, train_steps, lr=5e-3, lr_final=2e-3, power=power)
+    coeffs = [c.copy() for c in w.coefficients()]
+    t_train = time.perf_counter() - t0
+    del data
+    # held-out rollouts of another track: trained against untrained coefficients
+    hc, h0, ht = generate_trajectory(I.track_system(40, 199, peak=20000.0, r0=20.0), p, nwin, n_w)
+    base = EhcCheb(hc, n_w, stages, damping, order=order)
+    per_u = rollout_error(base, h0, ht, ctx=hc)
+    per_t = rollout_error(w, h0, ht, ctx=hc)
+    info = {"train_s": t_train, "train_rollouts": len(train_sys), "rollout_windows": nwin,
+            "train_steps": train_steps,
+            "train_cells": "256,000-atom tracks and hot spots (40^3 cells), rollouts from the end of the first window",
+            "start": "damped Chebyshev order %d, damping %.4g" % (order, damping),
+            "loss": "sum over the rollout's windows of mean relative error^%d" % power,
+            "training_spectrum_tauK_lambda_max": spec, "stability_untrained": beta0,
+            "stability_trained": w.stability(), "loss_first": hist[0], "loss_last": hist[-1],
+            "heldout_256k_rollout_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
+    return coeffs, info
