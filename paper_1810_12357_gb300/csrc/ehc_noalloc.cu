@@ -1,11 +1,11 @@
 // ehc_noalloc.cu -- electronic-energy reduction that allocates nothing.
 //
-// Some callers cannot allocate device memory when they need this number: an MD
-// code that reports energies from inside a callback that runs during CUDA graph
-// capture, a host application whose memory pool is sized once at start-up and
-// forbids later cudaMalloc, or a real-time loop that must not take the driver's
-// allocation locks.  ehc_electron_energy_noalloc serves them: its scratch (the
-// per-block partial sums) lives in a fixed file-scope device array.
+// Some callers cannot allocate device memory when they need this number: a host
+// application whose device memory pool is sized once at start-up and forbids
+// later cudaMalloc, a plugin running inside another code's MD loop that may not
+// touch that code's allocator, or a real-time loop that must not take the
+// driver's allocation locks.  ehc_electron_energy_noalloc serves them: its
+// scratch (the per-block partial sums) lives in a fixed file-scope device array.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,8 +41,11 @@ __device__ __forceinline__ double na_block_sum(double v, double *sh) {
   return r;
 }
 
+// maximum that keeps a NaN (fmax would drop it): a NaN temperature shows as max T
+__device__ __forceinline__ double na_max(double a, double b) { return (a != a) ? a : ((b != b) ? b : fmax(a, b)); }
+
 __device__ __forceinline__ double na_block_max(double v, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = na_max(v, __shfl_down_sync(0xffffffffu, v, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) sh[wid] = v;
@@ -50,7 +53,7 @@ __device__ __forceinline__ double na_block_max(double v, double *sh) {
   double r = -1e300;
   if (wid == 0) {
     r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : -1e300;
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    for (int o = 16; o > 0; o >>= 1) r = na_max(r, __shfl_down_sync(0xffffffffu, r, o));
   }
   return r;
 }
@@ -66,7 +69,7 @@ __global__ void na_partial(int64_t n, const double *__restrict__ T, double gamma
   for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
     const double t = T[s];
     sT += t;
-    mT = fmax(mT, t);
+    mT = na_max(mT, t);
     if (cap > 0.0 && gamma * t > cap) {
       const double Tc = cap / gamma;
       sE += 0.5 * cap * Tc + cap * (t - Tc);
@@ -90,7 +93,7 @@ __global__ void na_final(int nb, const double *__restrict__ part, double e_scale
   double sT = 0, mT = -1e300, sE = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     sT += part[b * 4 + 0];
-    mT = fmax(mT, part[b * 4 + 1]);
+    mT = na_max(mT, part[b * 4 + 1]);
     sE += part[b * 4 + 2];
   }
   const double r0 = na_block_sum(sT, sh);
@@ -104,7 +107,9 @@ __global__ void na_final(int nb, const double *__restrict__ part, double e_scale
 }
 
 // device address of the scratch array on the current device, looked up once per
-// device (cudaGetSymbolAddress must run with that device current)
+// device (cudaGetSymbolAddress must run with that device current).  The cached
+// address belongs to the device's current context: after cudaDeviceReset on that
+// device it is stale, so the entry point must not be used across a reset.
 int scratch_ptr(double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EHC_E_CUDA;
@@ -132,7 +137,19 @@ extern "C" int ehc_electron_energy_noalloc(const double *Te_dev, int64_t n, doub
   const double cap = Ce_cap_kB > 0 ? Ce_cap_kB * kB_J / (vatom_A3 * 1e-30) : 0.0;
   const int nb = (int)((n + kNaAtomsPerBlock - 1) / kNaAtomsPerBlock);
   cudaStream_t st = (cudaStream_t)stream;
-  if (nb > 0) na_partial<<<nb, kNaThreads, 0, st>>>(n, Te_dev, gamma_Ce, cap, part);
-  na_final<<<1, kNaThreads, 0, st>>>(nb, part, vatom_A3 * 1e-30 / eV_J, out_dev);
-  return cudaGetLastError() == cudaSuccess ? EHC_OK : EHC_E_CUDA;
+  // launched through cudaLaunchKernel so that each launch's own status is checked
+  // (the thread's last-error slot may hold an unrelated earlier failure)
+  if (nb > 0) {
+    const double *T = Te_dev;
+    double g = gamma_Ce, cp = cap;
+    void *args[] = {&n, (void *)&T, &g, &cp, &part};
+    if (cudaLaunchKernel((const void *)na_partial, dim3(nb), dim3(kNaThreads), args, 0, st) != cudaSuccess)
+      return EHC_E_CUDA;
+  }
+  int nbi = nb;
+  double esc = vatom_A3 * 1e-30 / eV_J;
+  void *fargs[] = {&nbi, &part, &esc, &out_dev};
+  if (cudaLaunchKernel((const void *)na_final, dim3(1), dim3(kNaThreads), fargs, 0, st) != cudaSuccess)
+    return EHC_E_CUDA;
+  return EHC_OK;
 }

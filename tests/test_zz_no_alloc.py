@@ -1,8 +1,9 @@
 """The allocation-free energy entry point (collected last on purpose).
 
 ehc_electron_energy_noalloc is for callers that cannot call cudaMalloc when they
-need the electronic energy (a callback inside CUDA graph capture, a fixed device
-memory pool, a loop that must not take allocator locks).  It keeps its scratch in
+need the electronic energy (an application with a fixed device memory pool, a
+plugin that may not touch its host code's allocator, a loop that must not take
+allocator locks).  It keeps its scratch in
 a fixed device array inside the library.  Its results must agree with the
 ledger that ehc_set_te / ehc_energy compute, on consecutive calls.
 """
@@ -39,6 +40,12 @@ def test_noalloc_energy_matches_ledger_twice():
     ref = float((0.5 * p["gamma_Ce"] * s.Te[:1000] ** 2).sum() * vatom * 1e-30 / I.EV_J)
     assert out[2].item() == pytest.approx(ref, rel=1e-12)
     assert out[0].item() == pytest.approx(float(s.Te[:1000].sum()), rel=1e-13)
+    # a NaN temperature is reported as the maximum, not dropped
+    Te3 = Te[:5000].clone()
+    Te3[1234] = float("nan")
+    electron_energy_noalloc(Te3, p["gamma_Ce"], p["Ce_cap_kB"], vatom, out)
+    torch.cuda.synchronize()
+    assert np.isnan(out[1].item()) and np.isnan(out[0].item())
     # sizes beyond the fixed scratch are refused
     L = load_library()
     import ctypes
