@@ -405,11 +405,20 @@ class OracleSim:
         self.chi = np.ascontiguousarray((self.Kself >= p["eps_ke"]).astype(np.uint8))
         # global means: mean electronic temperature and the classical lattice
         # temperature K / ((3/2) k_B N) (Sec. 2)
-        self.Te_mean = float(self.T.mean())
+        Te_mean = float(self.T.mean())
         ke = 0.5 * self.mass * (v * v).sum(axis=1) * MVV_EV
-        self.Tlat = float(ke.sum() / (1.5 * KB_EV * self.n))
+        Tlat = float(ke.sum() / (1.5 * KB_EV * self.n))
         self.Tmin = float(self.T.min()) if self.n else 0.0
         self.Tmax_atoms = float(self.T.max()) if self.n else 0.0
+        self.set_step_means(Te_mean, Tlat)
+
+    def set_step_means(self, Te_mean: float, Tlat: float):
+        """C_e, kappa_e, K and the coupling constants of the MD step from the
+        system means (Sec. 2: evaluated at the mean electronic and lattice
+        temperatures); a domain of a decomposed system passes the means of the
+        whole system."""
+        p = self.p
+        self.Te_mean, self.Tlat = float(Te_mean), float(Tlat)
         Ce = p["gamma_Ce"] * self.Te_mean
         cap = self.cap_SI()
         if cap > 0:

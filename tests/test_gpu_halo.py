@@ -112,3 +112,41 @@ def test_domain_means_from_owned_sums():
     T, T_ref = _run(s, p, 2, means="sums")
     err = float(np.max(np.abs(T - T_ref) / T_ref))
     assert err < 1e-12, err
+
+
+@pytest.mark.parametrize("flux_prec", [1, 0])
+def test_domains_rebuilt_every_md_step_on_one_gpu(flux_prec):
+    """halo.run_domains on one GPU: 2 and 3 slab domains of a system, each MD step
+    rebuilt from its owned atoms and the ghosts within r_c of its slab (no global
+    neighbour list), atoms migrating between domains, the means all-reduced from
+    the owned atoms' sums, the ghost temperatures packed and unpacked on the device
+    before every substep; against the undivided context.  FP64 flux: T_e within
+    1e-11, positions and velocities 1e-12 (the all-reduced means differ from the
+    undivided sums in the last bits); single-precision flux: T_e within 1e-7 (an
+    overwritten ghost makes the next substep take the full series, where the
+    undivided run takes each tile's own order)."""
+    import torch
+    import test_halo as TH
+    from paper_1810_12357_gb300 import halo
+    from _drive import run_gpu
+    s, p = TH._md_system()
+    p = dict(p, flux_prec=flux_prec)
+    tol = 1e-11 if flux_prec == 1 else 1e-7
+    g, xg, vg = run_gpu(s, p, TH.N_MD, TH.N_SUB_MD)
+    Tr, xr, vr = g.get_te().cpu().numpy(), xg.cpu().numpy(), vg.cpu().numpy()
+    for nd in (2, 3):
+        domains = [halo.SlabDomain.from_system(r, nd, s, p["rc"] + 1e-5, device="cuda") for r in range(nd)]
+        ids0 = [set(d.ids.tolist()) for d in domains]
+        halo.run_domains(domains, halo.LocalComm(nd), p, TH.N_MD, TH.N_SUB_MD)
+        assert sum(len(set(d.ids.tolist()) - i0) for d, i0 in zip(domains, ids0)) > 0
+        T, x, v = np.full(s.n, np.nan), np.full((s.n, 3), np.nan), np.full((s.n, 3), np.nan)
+        for d in domains:
+            ids = d.ids.cpu().numpy()
+            assert np.all(np.isnan(T[ids]))
+            T[ids], x[ids], v[ids] = d.T.cpu().numpy(), d.x.cpu().numpy(), d.v.cpu().numpy()
+        err = float(np.max(np.abs(T - Tr) / Tr))
+        print(f"{nd} domains rebuilt every MD step (flux_prec {flux_prec}): T_e max rel err {err:.2e}, "
+              f"x {np.max(np.abs(x - xr)):.1e} A, v {np.max(np.abs(v - vr)):.1e} A/fs")
+        assert err < tol
+        assert float(np.max(np.abs(x - xr))) < 1e3 * tol
+        assert float(np.max(np.abs(v - vr))) < tol * float(np.abs(vr).max())
