@@ -108,7 +108,16 @@ extern "C" {
  *                   as A_i; stop_beta_per_fs = 0 switches it off
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after
- *                   tiles grow), 256 or 128 = fixed; both give identical results */
+ *                   tiles grow), 256 or 128 = fixed; both give identical results
+ *   skin_A          skin of the neighbour search (0 <= skin_A <= rc_A; 0: none): cells are
+ *                   at least rc_A + skin_A wide, and a build takes the list from candidates
+ *                   (the atoms within rc_A + skin_A at the last candidate build) by the
+ *                   same exact integer test on the current positions, rebuilding the
+ *                   candidates only when some atom moved more than skin_A / 2 since; the
+ *                   list is the one the full search gives, in the same order.  A negative
+ *                   value sizes the cells the same way and searches them in full every
+ *                   build.  Used on grids with at least 3 cells per periodic axis, uniform
+ *                   pair rates and max_neighbors <= 32; other contexts search in full */
 typedef struct ehc_params {
   double rc_A;
   double dt_sub_fs;
@@ -144,6 +153,7 @@ typedef struct ehc_params {
   double pot_r0_A;
   double stop_beta_per_fs;  /* electronic stopping rate in ehc_couple (0: none) */
   double stop_ecut_eV;      /* kinetic energy above which an atom is stopped */
+  double skin_A;            /* neighbour-search skin (0: none; see below) */
 } ehc_params;
 
 /* Energy ledger and diagnostics (Sec. 3.2 energy balance).  E_e is tracked
@@ -250,7 +260,13 @@ int ehc_kick(ehc_ctx *c, double *v_dev, const double *F_dev, double dt_fs);
  * them with vals_dev[0..m) between substep calls, the single-precision state
  * included (the next substep then evaluates the full series everywhere).
  * Indices outside [0, n) are skipped and reported as EHC_E_INDEX by the next
- * synchronising call.  EHC_E_STATE before ehc_set_te.  Asynchronous. */
+ * synchronising call.  EHC_E_STATE before ehc_set_te.  Asynchronous.
+ * The context's own ledger (ehc_energy) is left alone by ehc_set_te_at: in a
+ * domain context it counts the ghosts' electronic energy, which the exchange
+ * overwrites, so a domain's drift is not a conservation check.  The conserved
+ * ledger of a decomposed run is the all-reduced one: E_e changes with
+ * V_atom C_e sum T over the owned atoms (ehc_sums_at), the exchanged energies
+ * with the owned atoms' hand-over. */
 int ehc_get_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, double *out_dev);
 int ehc_set_te_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, const double *vals_dev);
 
@@ -324,9 +340,9 @@ int ehc_load(ehc_ctx *c, const char *path);
 
 /* Electronic energy of a set of temperatures without allocating anything: the
  * paper has no counterpart; this serves callers that cannot call cudaMalloc at
- * the time they need the number (a callback that runs during CUDA graph capture,
- * an application whose device memory pool is fixed at start-up, a loop that must
- * not take the allocator's locks).  Te_dev [n] (device, any order); writes to
+ * the time they need the number (an application whose device memory pool is
+ * fixed at start-up, a plugin that may not touch its host code's allocator, a
+ * loop that must not take the allocator's locks).  Te_dev [n] (device, any order); writes to
  * out_dev (device, 3 doubles): sum of T [K], max T [K] and
  * sum_i V_atom int_0^{T_i} C_e dT [eV] with C_e = min(gamma_Ce T, Ce_cap_kB k_B / V_atom)
  * (Ce_cap_kB <= 0: no cap) -- the E_e0 that ehc_set_te computes.  Asynchronous on
@@ -334,9 +350,11 @@ int ehc_load(ehc_ctx *c, const char *path);
  * GPU that loads it until the process exits; n may not exceed 16,777,216
  * (EHC_E_INVAL beyond).  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls share the array and every call
- * overwrites the part it uses, so calls that overlap on the GPU (different
- * streams, or host threads) race; serialise them. */
+ * call before any stream capture; that address is cached per device, so do not
+ * use the entry point across a cudaDeviceReset.  All calls share the array and
+ * every call overwrites the part it uses, so calls that overlap on the GPU
+ * (different streams, or host threads) race; serialise them.  A NaN among the
+ * temperatures makes max T NaN. */
 int ehc_electron_energy_noalloc(const double *Te_dev, int64_t n, double gamma_Ce, double Ce_cap_kB,
                                 double vatom_A3, double *out_dev, void *stream);
 
@@ -485,6 +503,48 @@ int ehc_cheb_predict(ehc_cheb *w, ehc_ctx *c, const double *Tin_dev, double *Tou
  * points of [0, 2.05 stages^2]; host computation. */
 int ehc_cheb_stability(const ehc_cheb *w, double *beta);
 void ehc_cheb_destroy(ehc_cheb *w);
+
+/* ---- Learned corrector of the window propagator ---------------------------------
+ * A two-layer message-passing network over the context's neighbour list (node
+ * width 64) adds a learned pair flux to a window's result Y, so that the window
+ * follows n_w plain substeps of Eq. HeatTransport more closely (the paper has no
+ * network; it stands in for substeps of Eq. HeatTransport, Sec. 2.1).  With
+ * delta = (Y - Tref)/Tmax, D_ij = (delta_j - delta_i)/sigma, q_ij = D^2/(1 + D^2),
+ * rho_ij = r_ij / r_c, node features f_i = [Y_i/1e4, T_l,i/1e3 (0 below the
+ * kinetic-energy guard), z_i/18] (z_i the neighbour count) and <.> the mean over
+ * the atom's row:
+ *   in_i = [f_i, <f_j>, <q>, <q^2>, <rho>, <q rho>, 1, 0 x 5]                  (16)
+ *   h1 = relu(W1 in + b1), h2 = relu(W2 h1 + b2), u = W3 h2                 (64, 64, 16)
+ *   g_ij = w4 . relu(u_i + u_j + P [q_ij, rho_ij] + b4)                    (symmetric)
+ *   Y^_i = Y_i + kappa sum_j (Y_j - Y_i) g_ij,  kappa = n_w dt_sub K in a window.
+ * Every pair term is odd under i <-> j, so sum_i Y_i is kept.  The node MLP runs
+ * on the tensor cores with BF16 weights and activations and FP32 accumulation;
+ * the edge MLP in FP32 from BF16 weights.  Parameters (6336 floats): [W1 (64 x 16)
+ * | b1 (64) | W2 (64 x 64) | b2 (64) | W3 (16 x 64) | P (16 x 2) | b4 (16) | w4 (16)],
+ * row-major (out x in); FP32 master weights and Adam for training.  Zero weights
+ * (as created) make the identity.  The corrector is bound to the atom count of
+ * the context it was created with; single-precision flux and uniform pair rates
+ * only (EHC_E_INVAL otherwise). */
+typedef struct ehc_gnn ehc_gnn;
+int ehc_gnn_create(ehc_ctx *c, double sigma, ehc_gnn **out);
+/* set (resets Adam) or read the FP32 parameters [6336] (host); synchronise */
+int ehc_gnn_set_params(ehc_gnn *g, ehc_ctx *c, const float *params_host);
+int ehc_gnn_get_params(ehc_gnn *g, ehc_ctx *c, float *params_host);
+/* Y^ of Y_dev into Yhat_dev (caller order, device) on the context's current
+ * neighbour list and lattice temperatures; the correction Y^ - Y into dY_dev if
+ * not NULL.  Asynchronous; EHC_E_STATE before the first build. */
+int ehc_gnn_apply(ehc_gnn *g, ehc_ctx *c, double kappa, const double *Y_dev, double *Yhat_dev, double *dY_dev);
+/* One training step on a window: Y_dev the propagator's result, Tstar_dev the
+ * plain substeps' (caller order, device).  Loss mean(((Y^ - T*)/T*)^2) to
+ * *loss_host, its gradient [6336] to grad_host if not NULL, an Adam step of rate
+ * lr if lr > 0.  Synchronises. */
+int ehc_gnn_train_step(ehc_gnn *g, ehc_ctx *c, double kappa, const double *Y_dev, const double *Tstar_dev,
+                       float lr, float *loss_host, float *grad_host);
+/* Apply g (or no corrector: NULL) to the result of every window ehc_cheb_step
+ * takes with w, before its residual test; g stays owned by the caller and must
+ * outlive its use by w. */
+int ehc_cheb_set_corrector(ehc_cheb *w, ehc_gnn *g);
+void ehc_gnn_destroy(ehc_gnn *g);
 
 /* ---- Batched replicas --------------------------------------------------------
  * Independent systems (e.g. repeated cascades of different sizes, Sec. 4) that

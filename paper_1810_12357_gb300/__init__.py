@@ -52,7 +52,7 @@ class ehc_params(ctypes.Structure):
         ("ce_mode", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 4),
         ("pot_D_eV", ctypes.c_double), ("pot_alpha_perA", ctypes.c_double), ("pot_r0_A", ctypes.c_double),
-        ("stop_beta_per_fs", ctypes.c_double), ("stop_ecut_eV", ctypes.c_double),
+        ("stop_beta_per_fs", ctypes.c_double), ("stop_ecut_eV", ctypes.c_double), ("skin_A", ctypes.c_double),
     ]
 
 
@@ -118,6 +118,13 @@ _SIGS = {
     "ehc_cheb_stability": (_I, [_P, _P]),
     "ehc_cheb_spectrum": (_I, [_P, _P, _P, ctypes.c_int32, _P]),
     "ehc_cheb_destroy": (None, [_P]),
+    "ehc_cheb_set_corrector": (_I, [_P, _P]),
+    "ehc_gnn_create": (_I, [_P, ctypes.c_double, ctypes.POINTER(_P)]),
+    "ehc_gnn_set_params": (_I, [_P, _P, _P]),
+    "ehc_gnn_get_params": (_I, [_P, _P, _P]),
+    "ehc_gnn_apply": (_I, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    "ehc_gnn_train_step": (_I, [_P, _P, ctypes.c_double, _P, _P, ctypes.c_float, _P, _P]),
+    "ehc_gnn_destroy": (None, [_P]),
     "ehc_batch_create": (_I, [ctypes.POINTER(ehc_params), ctypes.c_int32, _P, _P, _P, _P, _P,
                               ctypes.POINTER(_P)]),
     "ehc_batch_size": (_I, [_P, _P, _P]),
@@ -198,6 +205,7 @@ def make_params(p: dict) -> ehc_params:
     q.stop_ecut_eV = float(p.get("stop_ecut", 10.0))
     q.use_graph = int(p.get("use_graph", 1))
     q.tile_threads = int(p.get("tile_threads", 0))
+    q.skin_A = float(p.get("skin", 0.0))
     return q
 
 
@@ -474,6 +482,71 @@ class EhcBatch:
         return {f: getattr(e, f) for f, _ in ehc_energy_t._fields_}
 
 
+GNN_PARAMS = 6336   # parameters of the corrector network (include/ehc.h)
+
+
+class EhcGnn:
+    """Learned corrector of the window propagator (ehc_gnn_*): a message-passing
+    network of node width 64 whose pair-flux output is added to a window's result.
+    Bound to the atom count of the context it is created on; `ctx` arguments
+    (default that context) supply the neighbour list and lattice temperatures."""
+
+    def __init__(self, ctx: "Ehc", sigma: float = 1e-3, params=None):
+        L = load_library()
+        self._lib = L
+        self.ctx = ctx
+        self.sigma = float(sigma)
+        h = ctypes.c_void_p()
+        _check(L.ehc_gnn_create(ctx._h, self.sigma, ctypes.byref(h)), "ehc_gnn_create")
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.ehc_gnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        if a.shape != (GNN_PARAMS,):
+            raise ValueError(f"the corrector takes {GNN_PARAMS} parameters")
+        _check(self._lib.ehc_gnn_set_params(self._h, self.ctx._h, a.ctypes.data_as(_P)), "ehc_gnn_set_params")
+
+    def get_params(self):
+        a = np.empty(GNN_PARAMS, dtype=np.float32)
+        _check(self._lib.ehc_gnn_get_params(self._h, self.ctx._h, a.ctypes.data_as(_P)), "ehc_gnn_get_params")
+        return a
+
+    def apply(self, Y, kappa: float, ctx=None, want_dY: bool = False):
+        """Corrected result Y^ of Y (caller order, device FP64); with want_dY also
+        the correction Y^ - Y."""
+        import torch
+        c = ctx or self.ctx
+        out = torch.empty_like(Y)
+        dY = torch.empty_like(Y) if want_dY else None
+        _check(self._lib.ehc_gnn_apply(self._h, c._h, float(kappa), _ptr(Y), _ptr(out),
+                                       _ptr(dY) if dY is not None else None), "ehc_gnn_apply")
+        return (out, dY) if want_dY else out
+
+    def train_step(self, Y, Tstar, kappa: float, lr: float, want_grad: bool = False, ctx=None):
+        """Loss of the window Y -> T* and (lr > 0) one Adam step; with want_grad
+        also the gradient [6336]."""
+        c = ctx or self.ctx
+        loss = ctypes.c_float()
+        g = np.empty(GNN_PARAMS, dtype=np.float32) if want_grad else None
+        _check(self._lib.ehc_gnn_train_step(self._h, c._h, float(kappa), _ptr(Y), _ptr(Tstar), float(lr),
+                                            ctypes.byref(loss), g.ctypes.data_as(_P) if g is not None else None),
+               "ehc_gnn_train_step")
+        return (float(loss.value), g) if want_grad else float(loss.value)
+
+
 class EhcNN:
     """Learned window propagator bound to a context (ehc_nn_*)."""
 
@@ -582,6 +655,17 @@ class EhcCheb:
         f = ctypes.c_int64()
         _check(self._lib.ehc_cheb_stats(self._h, ctypes.byref(w), ctypes.byref(f)), "ehc_cheb_stats")
         return int(w.value), int(f.value)
+
+    def set_corrector(self, gnn):
+        """Apply the corrector network (EhcGnn, or None) to every window's result."""
+        _check(self._lib.ehc_cheb_set_corrector(self._h, gnn._h if gnn is not None else None),
+               "ehc_cheb_set_corrector")
+        self._corrector = gnn   # keep it alive while the window uses it
+
+    def kappa(self, ctx=None) -> float:
+        """n_w dt_sub K of the context's current MD step (the corrector's scale)."""
+        c = ctx or self.ctx
+        return self.n_window * c.params["dt_sub"] * c.energy(check=False)["K_per_fs"]
 
     def set_coefficients(self, nu, mut, kap, gam):
         """Replace the stage coefficients (arrays of stages + 1, index 0 unused);

@@ -68,7 +68,8 @@ void free_all(Ctx &c) {
                  c.dmir[0], c.dmir[1], c.abuf[0], c.abuf[1], c.Tl_f, c.Tl_d, c.depth_orig, c.srcw,
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
-                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax};
+                 c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax,
+                 c.cand, c.ccnt, c.q_ref};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -309,6 +310,11 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   c.W = W;
   c.stream = (cudaStream_t)stream;
   c.g.rcq = llrint(p->rc_A * 1048576.0);
+  // cells at least r_c + |skin| wide (a negative skin: the same cells, full search every build)
+  const double skin = p->skin_A;
+  if (!(skin == skin) || std::fabs(skin) > p->rc_A) { delete h; return EHC_E_INVAL; }
+  const int64_t cellq = llrint((p->rc_A + std::fabs(skin)) * 1048576.0);
+  c.skin_q = skin > 0 ? cellq - c.g.rcq : 0;
   int64_t ncell = 1;
   for (int k = 0; k < 3; ++k) {
     c.box[k] = box_A[k];
@@ -317,7 +323,9 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
     if (c.g.Lq[k] <= 0 || c.g.Lq[k] >= INT32_MAX) { delete h; return EHC_E_INVAL; }
     c.g.per[k] = periodic[k] ? 1 : 0;
     if (c.g.per[k] && c.g.Lq[k] <= 2 * c.g.rcq) { delete h; return EHC_E_INVAL; }
-    int64_t nc = c.g.Lq[k] / c.g.rcq;
+    // the candidate radius must keep a unique minimum image too
+    if (c.g.per[k] && c.g.Lq[k] <= 2 * cellq) c.skin_q = 0;
+    int64_t nc = c.g.Lq[k] / cellq;
     if (nc < 1) nc = 1;
     if (nc > 1024) nc = 1024;
     c.g.nc[k] = (int32_t)nc;
@@ -383,8 +391,17 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.dKE, n));
   A(dalloc(&c.partials, kRedBlocks * 6));
   A(dalloc(&c.md_part, md_force_blocks(n)));
+  // device scalars, one slot per use (host mirror: scal_host[0..15], error words at [16..17]):
+  //   0-5 system sums of the build and the ledger (sum T, max T / sum U, sum KE, ...),
+  //   6-7 ehc_sums_at, 8 E_lat, 9 stopped-atom count (u64 bits), 10-11 border reservoirs,
+  //   12 ehc_probe_wait flag (int32), 13 ehc_max_speed result, 14 ehc_forces potential energy
   A(dalloc(&c.scal, 16));
-  A(dalloc(&c.err, 4));
+  A(dalloc(&c.err, 8));
+  if (c.skin_q > 0) {
+    A(dalloc(&c.cand, (int64_t)kCandWidth * (n > 0 ? n : 1)));
+    A(dalloc(&c.ccnt, n > 0 ? n : 1));
+    A(dalloc(&c.q_ref, n > 0 ? n : 1));
+  }
   A(dalloc(&c.coef, 1));
   A(dalloc(&c.x_dev, 3 * n));
   A(dalloc(&c.v_dev, 3 * n));
@@ -419,7 +436,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   if (n_types > 1 && n > 0)
     e = cudaMemcpyAsync(c.type_orig, type_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.scal, 0, sizeof(double) * 16, c.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 4, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.err, 0, sizeof(int32_t) * 8, c.stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c.row_nbr, rt.data(), sizeof(int32_t) * rt.size(), cudaMemcpyHostToDevice, c.stream);
   std::vector<int2> wl((size_t)c.nrows);
@@ -809,11 +826,11 @@ int ehc_forces(ehc_ctx *h, double *F_dev, double *epot_host) {
   if (!h || (h->c.n > 0 && !F_dev)) return EHC_E_INVAL;
   Ctx &c = h->c;
   if (!c.built) return EHC_E_STATE;
-  CK(launch_forces(c, F_dev, c.md_part, c.scal + 6));
+  CK(launch_forces(c, F_dev, c.md_part, c.scal + 14));
   if (epot_host) {
-    CK(cudaMemcpyAsync(c.scal_host + 6, c.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(c.scal_host + 14, c.scal + 14, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    *epot_host = c.scal_host[6];
+    *epot_host = c.scal_host[14];
   }
   return EHC_OK;
 }
@@ -883,24 +900,24 @@ int ehc_set_step_means(ehc_ctx *h, double Te_mean, double Tlat) {
 int ehc_probe_wait(ehc_ctx *h, uint32_t polls, int32_t complete) {
   if (!h || polls == 0) return EHC_E_INVAL;
   Ctx &c = h->c;
-  // its own word (scal[7] as int32): the context's sticky error word stays untouched
-  int32_t *flag = reinterpret_cast<int32_t *>(c.scal + 7);
+  // its own word (scal[12] as int32): the context's sticky error word stays untouched
+  int32_t *flag = reinterpret_cast<int32_t *>(c.scal + 12);
   CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), c.stream));
   CK(launch_wait_probe(polls, complete ? 1 : 0, flag, c.stream));
   int32_t got = 0;
-  CK(cudaMemcpyAsync(&c.scal_host[7], flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(&c.scal_host[12], flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
-  std::memcpy(&got, &c.scal_host[7], sizeof(got));
+  std::memcpy(&got, &c.scal_host[12], sizeof(got));
   return (got & ERR_TIMEOUT) ? EHC_E_TIMEOUT : EHC_OK;
 }
 
 int ehc_max_speed(ehc_ctx *h, const double *v_dev, double *vmax_host) {
   if (!h || !vmax_host || (h->c.n > 0 && !v_dev)) return EHC_E_INVAL;
   Ctx &c = h->c;
-  CK(launch_vmax(c, v_dev, c.partials, kRedBlocks, c.scal + 7));
-  CK(cudaMemcpyAsync(c.scal_host + 7, c.scal + 7, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CK(launch_vmax(c, v_dev, c.partials, kRedBlocks, c.scal + 13));
+  CK(cudaMemcpyAsync(c.scal_host + 13, c.scal + 13, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
-  *vmax_host = c.scal_host[7];
+  *vmax_host = c.scal_host[13];
   return EHC_OK;
 }
 
@@ -1481,7 +1498,13 @@ int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out) {
 // ---------------------------------------------------------------------------
 // Chebyshev window propagator
 
+struct ehc_gnn;
+namespace ehc {
+int gnn_correct_window(ehc_gnn *g, Ctx &c, double kappa, float *ys, double *T1);
+}
+
 struct ehc_cheb {
+  ehc_gnn *corr = nullptr;   // learned corrector applied to every window's result (or none)
   int n_w = 16, s = 4, order = 1;
   double eps = 0.05;
   int64_t n = 0;
@@ -1883,6 +1906,11 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
     if (w->y[k] == ys) bs = k;
   // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
   CK(cheb_finish(c, T0, zs, ys, T1, w->dTc, w->n_w));
+  // the learned corrector's pair flux on the window's result (T1 and its mirror)
+  if (w->corr) {
+    const int rc = gnn_correct_window(w->corr, c, tauw * c.K, ys, T1);
+    if (rc) return rc;
+  }
   // pair flux of the end state for the residual
   StageArgs sf;
   sf.yin = ys;
@@ -2301,6 +2329,157 @@ int ehc_nn_step(ehc_nn *nn, ehc_ctx *hc, double tau, double t_fs, int32_t *fell_
   nn->fallbacks += 1;
   if (fell_back) *fell_back = 1;
   return ehc_substep(hc, nn->n_w, t_fs);
+}
+
+
+}  // extern "C"
+
+// ---- learned corrector of the window propagator (kernels_gnn.cu) ----
+
+struct ehc_gnn {
+  int64_t n = 0;
+  double sigma = 1e-3;
+  int t = 0;                      // Adam steps taken
+  float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  __nv_bfloat16 *pb = nullptr, *in = nullptr, *u = nullptr;
+  float *y0 = nullptr, *ybuf = nullptr, *G = nullptr, *du = nullptr, *mpart = nullptr, *epart = nullptr;
+  double *T = nullptr, *Tt = nullptr, *lpart = nullptr, *loss = nullptr;
+  float *host = nullptr;          // pinned: gradient [kGnnParams] | loss
+  double *host_loss = nullptr;
+};
+
+namespace ehc {
+int gnn_correct_window(ehc_gnn *g, Ctx &c, double kappa, float *ys, double *T1) {
+  if (g->n != c.n) return EHC_E_INVAL;
+  CK(gnn_forward(c, g->pb, g->sigma, kappa, ys, g->in, g->u, T1, g->ybuf, nullptr));
+  CK(cudaMemcpyAsync(ys, g->ybuf, sizeof(float) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+  return EHC_OK;
+}
+}  // namespace ehc
+
+extern "C" {
+
+int ehc_gnn_create(ehc_ctx *hc, double sigma, ehc_gnn **out) {
+  if (!hc || !out || !(sigma > 0)) return EHC_E_INVAL;
+  *out = nullptr;
+  Ctx &c = hc->c;
+  if (c.p.flux_prec != 0 || c.p.rate_shell_n != 0 || c.local) return EHC_E_INVAL;
+  if (c.n > 2147483647LL) return EHC_E_INVAL;
+  ehc_gnn *g = new (std::nothrow) ehc_gnn();
+  if (!g) return EHC_E_NOMEM;
+  g->n = c.n;
+  g->sigma = sigma;
+  const int64_t n = c.n > 0 ? c.n : 1;
+  bool ok = gnn_setup(gnn_bwd_smem()) == cudaSuccess;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dalloc(&g->p, kGnnParams));
+  A(dalloc(&g->m, kGnnParams));
+  A(dalloc(&g->v, kGnnParams));
+  A(dalloc(&g->grad, kGnnParams));
+  A(dalloc(&g->pb, kGnnParams));
+  A(dalloc(&g->in, n * 16));
+  A(dalloc(&g->u, n * 16));
+  A(dalloc(&g->y0, n));
+  A(dalloc(&g->ybuf, n));
+  A(dalloc(&g->G, n));
+  A(dalloc(&g->du, n * 16));
+  A(dalloc(&g->mpart, (int64_t)gnn_mlp_blocks(c) * kGnnParams));
+  A(dalloc(&g->epart, (int64_t)gnn_edge_blocks(n) * 64));
+  A(dalloc(&g->T, n));
+  A(dalloc(&g->Tt, n));
+  A(dalloc(&g->lpart, gnn_loss_blocks(n)));
+  A(dalloc(&g->loss, 1));
+  A(cudaMallocHost((void **)&g->host, sizeof(float) * kGnnParams));
+  A(cudaMallocHost((void **)&g->host_loss, sizeof(double)));
+  if (ok) {
+    // all parameters zero: the identity corrector until parameters are set
+    A(cudaMemsetAsync(g->p, 0, sizeof(float) * kGnnParams, c.stream));
+    A(cudaMemsetAsync(g->m, 0, sizeof(float) * kGnnParams, c.stream));
+    A(cudaMemsetAsync(g->v, 0, sizeof(float) * kGnnParams, c.stream));
+    A(gnn_params_to_bf16(c.stream, g->p, g->pb));
+    A(cudaStreamSynchronize(c.stream));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    ehc_gnn_destroy(g);
+    return EHC_E_NOMEM;
+  }
+  *out = g;
+  return EHC_OK;
+}
+
+void ehc_gnn_destroy(ehc_gnn *g) {
+  if (!g) return;
+  void *d[] = {g->p, g->m, g->v, g->grad, g->pb, g->in, g->u, g->y0, g->ybuf, g->G, g->du, g->mpart, g->epart,
+               g->T, g->Tt, g->lpart, g->loss};
+  for (void *q : d)
+    if (q) cudaFree(q);
+  if (g->host) cudaFreeHost(g->host);
+  if (g->host_loss) cudaFreeHost(g->host_loss);
+  delete g;
+}
+
+int ehc_gnn_set_params(ehc_gnn *g, ehc_ctx *hc, const float *params_host) {
+  if (!g || !hc || !params_host) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  std::memcpy(g->host, params_host, sizeof(float) * kGnnParams);
+  CK(cudaMemcpyAsync(g->p, g->host, sizeof(float) * kGnnParams, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemsetAsync(g->m, 0, sizeof(float) * kGnnParams, c.stream));
+  CK(cudaMemsetAsync(g->v, 0, sizeof(float) * kGnnParams, c.stream));
+  CK(gnn_params_to_bf16(c.stream, g->p, g->pb));
+  CK(cudaStreamSynchronize(c.stream));
+  g->t = 0;
+  return EHC_OK;
+}
+
+int ehc_gnn_get_params(ehc_gnn *g, ehc_ctx *hc, float *params_host) {
+  if (!g || !hc || !params_host) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  CK(cudaMemcpyAsync(g->host, g->p, sizeof(float) * kGnnParams, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  std::memcpy(params_host, g->host, sizeof(float) * kGnnParams);
+  return EHC_OK;
+}
+
+int ehc_gnn_apply(ehc_gnn *g, ehc_ctx *hc, double kappa, const double *Y_dev, double *Yhat_dev, double *dY_dev) {
+  if (!g || !hc || hc->c.n != g->n || (g->n > 0 && (!Y_dev || !Yhat_dev)) || !(kappa == kappa)) return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  if (c.n == 0) return EHC_OK;
+  CK(nn_gather(c, Y_dev, nullptr, g->T, nullptr, g->y0, false));
+  CK(gnn_forward(c, g->pb, g->sigma, kappa, g->y0, g->in, g->u, g->T, g->ybuf, dY_dev ? g->Tt : nullptr));
+  CK(launch_unpermute(c, g->T, Yhat_dev, 0));
+  if (dY_dev) CK(launch_unpermute(c, g->Tt, dY_dev, 0));
+  return EHC_OK;
+}
+
+int ehc_gnn_train_step(ehc_gnn *g, ehc_ctx *hc, double kappa, const double *Y_dev, const double *Tstar_dev,
+                       float lr, float *loss_host, float *grad_host) {
+  NvtxRange nvtx_range("ehc_gnn_train_step");
+  if (!g || !hc || hc->c.n != g->n || g->n == 0 || !Y_dev || !Tstar_dev || !(kappa == kappa) || !(lr >= 0))
+    return EHC_E_INVAL;
+  Ctx &c = hc->c;
+  if (!c.built) return EHC_E_STATE;
+  CK(nn_gather(c, Y_dev, Tstar_dev, g->T, g->Tt, g->y0, false));
+  CK(gnn_forward(c, g->pb, g->sigma, kappa, g->y0, g->in, g->u, g->T, g->ybuf, nullptr));
+  CK(gnn_backward(c, g->pb, g->sigma, kappa, g->y0, g->in, g->u, g->T, g->Tt, g->G, g->du, g->lpart, g->loss,
+                  g->mpart, g->epart, g->grad));
+  if (grad_host) CK(cudaMemcpyAsync(g->host, g->grad, sizeof(float) * kGnnParams, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(g->host_loss, g->loss, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (lr > 0) {
+    g->t += 1;
+    CK(gnn_adam(c.stream, g->p, g->m, g->v, g->grad, lr, g->t, g->pb));
+  }
+  CK(cudaStreamSynchronize(c.stream));
+  if (grad_host) std::memcpy(grad_host, g->host, sizeof(float) * kGnnParams);
+  if (loss_host) *loss_host = (float)g->host_loss[0];
+  return EHC_OK;
+}
+
+int ehc_cheb_set_corrector(ehc_cheb *w, ehc_gnn *g) {
+  if (!w || (g && g->n != w->n)) return EHC_E_INVAL;
+  w->corr = g;
+  return EHC_OK;
 }
 
 }  // extern "C"

@@ -272,6 +272,28 @@ cudaError_t nn_residual(Ctx &c, const float *d0, const float *d1, const double *
                         float *part, float *out);
 cudaError_t nn_couple_window(Ctx &c, const double *T0, double *T1, float *d1, double *dTc, int n_w);
 cudaError_t nn_accept(Ctx &c, const double *dTc);
+// kernels_gnn.cu (learned corrector of the window propagator: node width 64,
+// tensor-core node MLP, 6336 parameters)
+constexpr int kGnnParams = 6336;
+constexpr int kCandWidth = 48;   // candidate slots per atom of the skin path
+int gnn_mlp_blocks(Ctx &c);
+int gnn_edge_blocks(int64_t n);
+int gnn_loss_blocks(int64_t n);
+size_t gnn_bwd_smem();
+cudaError_t gnn_setup(size_t smem);
+// corrected window result: y the window result's mirror (sorted), T (sorted FP64)
+// corrected in place, y_out its new mirror (must not alias y), dY (optional) the
+// correction; in, u: n x 16 BF16 work arrays
+cudaError_t gnn_forward(Ctx &c, const __nv_bfloat16 *wb, double sigma, double kappa, const float *y,
+                        __nv_bfloat16 *in, __nv_bfloat16 *u, double *T, float *y_out, double *dY);
+// gradient of the window loss mean(((Y^ - T*)/T*)^2) after gnn_forward: Yh the
+// corrected result, Ts the target (sorted FP64); the loss into *loss (device)
+cudaError_t gnn_backward(Ctx &c, const __nv_bfloat16 *wb, double sigma, double kappa, const float *y,
+                         const __nv_bfloat16 *in, const __nv_bfloat16 *u, const double *Yh, const double *Ts,
+                         float *G, float *du, double *lpart, double *loss, float *mpart, float *epart, float *grad);
+cudaError_t gnn_adam(cudaStream_t st, float *p, float *m, float *v, const float *g, float lr, int t,
+                     __nv_bfloat16 *pb);
+cudaError_t gnn_params_to_bf16(cudaStream_t st, const float *p, __nv_bfloat16 *pb);
 // kernels_border.cu (fixed-temperature border)
 int border_red_blocks();
 cudaError_t border_flush(Ctx &c, double *out, bool clear);   // sum of the reservoirs into *out (device)
@@ -354,7 +376,15 @@ struct Ctx {
   int32_t *err = nullptr;        // device error word
   int32_t *maxcnt = nullptr;     // device max count (err + 1)
   int32_t *maxstaged = nullptr;  // largest staged row-tile size (err + 2)
-  int32_t *maxrow = nullptr;     // longest row (err + 3)
+  int32_t *maxrow = nullptr;     // longest row (err + 3); err + 4: the candidate list's rebuild flag
+  // neighbour candidates with a skin (ehc_params.skin_A > 0): atoms within r_c + skin
+  // at the last candidate build, original ids [kCandWidth][N] by original id, their
+  // counts, and the quantised positions of that build
+  int64_t skin_q = 0;            // skin on the 2^-20 A grid (0: full search every build)
+  bool cand_valid = false;
+  int32_t *cand = nullptr;
+  uint8_t *ccnt = nullptr;
+  int4 *q_ref = nullptr;
   int32_t staged_max = 0;
   int32_t row_max = 0;
   int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)

@@ -371,6 +371,192 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
   }
 }
 
+// ---- neighbour lists from a candidate list with a skin (cells >= r_c + skin) ----
+// The candidates of an atom are the atoms within r_v = r_c + skin of it when the
+// candidate list was built (original ids, slot-major [Wc][N] by original id).
+// While no atom has moved more than skin / 2 on the grid since then, every pair
+// within r_c is among them, and the list of the MD step is the candidates that
+// pass the exact integer test with the current positions: the same set, and
+// written in the same order, as the full cell search (row, cell run, sorted
+// index).  The check below sets *flag when an atom moved further (or the list
+// is new); the candidate kernel then rebuilds the list first.
+
+__device__ __forceinline__ int32_t wrap_d(int32_t d, int32_t L, int32_t h, int per) {
+  return per ? (d > h ? d - L : (d < -h ? d + L : d)) : d;
+}
+
+// *flag |= 1 if some atom moved more than skin / 2 since the candidate build
+__global__ void skin_check_kernel(int32_t n, Grid g, const int4 *__restrict__ q, const int4 *__restrict__ q_ref,
+                                  int64_t half2, int32_t *__restrict__ flag) {
+  const int32_t o = blockIdx.x * blockDim.x + threadIdx.x;
+  bool far = false;
+  if (o < n) {
+    const int4 a = q[o], b = q_ref[o];
+    const int32_t L0 = (int32_t)g.Lq[0], L1 = (int32_t)g.Lq[1], L2 = (int32_t)g.Lq[2];
+    const int64_t dx = wrap_d(a.x - b.x, L0, L0 >> 1, g.per[0]);
+    const int64_t dy = wrap_d(a.y - b.y, L1, L1 >> 1, g.per[1]);
+    const int64_t dz = wrap_d(a.z - b.z, L2, L2 >> 1, g.per[2]);
+    far = dx * dx + dy * dy + dz * dz > half2;
+  }
+  if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// Candidate list (only when *flag is set): the full cell search with r_v, one
+// thread per sorted atom, candidates as original ids by original id; the
+// positions of the build go to q_ref.  FAST grids only (>= 3 cells per periodic
+// axis, cells at least r_v wide).
+__global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv2, const int4 *__restrict__ q_s,
+                                                   const int32_t *__restrict__ perm, const int32_t *__restrict__ start,
+                                                   const int32_t *__restrict__ row_nbr, int32_t Wc,
+                                                   int32_t *__restrict__ cand, uint8_t *__restrict__ ccnt,
+                                                   const int4 *__restrict__ q_orig, int4 *__restrict__ q_ref,
+                                                   const int32_t *__restrict__ flag, int32_t *__restrict__ err) {
+  if (*flag == 0) return;
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int4 qi = q_s[s];
+  const int32_t o = perm[s];
+  q_ref[o] = q_orig[o];
+  const int32_t ncx = g.nc[0], ny = g.nc[1];
+  const int32_t cx = qi.w % ncx, R = qi.w / ncx;
+  int32_t m = 0;
+  for (int r = 0; r < kRowNbr; ++r) {
+    const int32_t R2 = row_nbr[(int64_t)R * kRowNbr + r];
+    if (R2 < 0) break;
+    const uint32_t oy = wrap_shift(R2 % ny - R % ny, g.Lq[1]) - (uint32_t)qi.y;
+    const uint32_t oz = wrap_shift(R2 / ny - R / ny, g.Lq[2]) - (uint32_t)qi.z;
+    const int32_t *rowst = start + (int64_t)R2 * ncx;
+    for (int d = -1; d <= 1; ++d) {
+      int32_t c = cx + d;
+      if (g.per[0]) c = c < 0 ? c + ncx : (c >= ncx ? c - ncx : c);
+      else if (c < 0 || c >= ncx) continue;
+      const uint32_t ox = wrap_shift(c - cx, g.Lq[0]) - (uint32_t)qi.x;
+      for (int32_t t = rowst[c]; t < rowst[c + 1]; ++t) {
+        const int4 qj = q_s[t];
+        const int32_t dx = (int32_t)((uint32_t)qj.x + ox);
+        const int32_t dy = (int32_t)((uint32_t)qj.y + oy);
+        const int32_t dz = (int32_t)((uint32_t)qj.z + oz);
+        const uint64_t d2 = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                            (uint64_t)((int64_t)dz * dz);
+        if (d2 <= (uint64_t)rv2 && t != s) {
+          if (m < Wc) cand[(int64_t)m * n + o] = perm[t];
+          ++m;
+        }
+      }
+    }
+  }
+  if (m > Wc) atomicOr(err, ERR_NBR_OVERFLOW);
+  ccnt[o] = (uint8_t)(m < Wc ? m : Wc);
+}
+
+// The list of the MD step from the candidates: the same outputs as
+// neighbor_kernel<true, false> (nbr, pidx, cnt, maxima), in its visit order (row,
+// cell run, sorted index), from the candidates that pass the exact test.
+constexpr int kMaxHits = 32;
+__global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
+                                                     const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
+                                                     const int32_t *__restrict__ start,
+                                                     const int32_t *__restrict__ row_nbr, int32_t W,
+                                                     const int32_t *__restrict__ cand, const uint8_t *__restrict__ ccnt,
+                                                     int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
+                                                     int64_t ps, uint8_t *__restrict__ cnt,
+                                                     int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
+                                                     int32_t *__restrict__ maxrow, int32_t *__restrict__ err) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int4 qi = q_s[s];
+  const int32_t o = perm[s];
+  const int32_t ncx = g.nc[0];
+  const int32_t cx = qi.w % ncx, R = qi.w / ncx;
+  // the tile placement of the neighbour rows (as neighbor_kernel)
+  int32_t rowid[kRowNbr], pre[kRowNbr], rs[kRowNbr];
+  int nr = 0;
+  int32_t tend = 0, self_local = 0, own_len = 0;
+  for (int r = 0; r < kRowNbr; ++r) {
+    const int32_t R2 = row_nbr[(int64_t)R * kRowNbr + r];
+    if (R2 < 0) break;
+    const int32_t a = start[(int64_t)R2 * ncx], b = start[(int64_t)R2 * ncx + ncx];
+    const int32_t pr = ((tend + 3) & ~3) + (a & 3);
+    rowid[r] = R2;
+    pre[r] = pr;
+    rs[r] = a;
+    if (R2 == R) {
+      self_local = pr + (s - a);
+      own_len = b - a;
+    }
+    tend = pr + (b - a);
+    nr = r + 1;
+  }
+  // the cells of a neighbour row in visit order: cx-1, cx, cx+1 (deduplicated,
+  // wrapped); a run restarts where the visit order wraps to a lower cell
+  int32_t xo[3];
+  int nx = 0;
+  for (int d = -1; d <= 1; ++d) {
+    int32_t c = cx + d;
+    if (g.per[0]) c = c < 0 ? c + ncx : (c >= ncx ? c - ncx : c);
+    else if (c < 0 || c >= ncx) continue;
+    bool dup = false;
+    for (int q = 0; q < nx; ++q) dup |= xo[q] == c;
+    if (!dup) xo[nx++] = c;
+  }
+  const int32_t L0 = (int32_t)g.Lq[0], L1 = (int32_t)g.Lq[1], L2 = (int32_t)g.Lq[2];
+  const int64_t rc2 = g.rcq * g.rcq;
+  uint64_t key[kMaxHits];
+  int m = 0;
+  const int c = ccnt[o];
+  for (int k = 0; k < c; ++k) {
+    const int32_t t = inv[cand[(int64_t)k * n + o]];
+    const int4 qj = q_s[t];
+    const int64_t dx = wrap_d(qj.x - qi.x, L0, L0 >> 1, g.per[0]);
+    const int64_t dy = wrap_d(qj.y - qi.y, L1, L1 >> 1, g.per[1]);
+    const int64_t dz = wrap_d(qj.z - qi.z, L2, L2 >> 1, g.per[2]);
+    if (dx * dx + dy * dy + dz * dz > rc2 || t == s) continue;
+    // visit rank of t: its row's place, then its cell's run
+    const int32_t R2t = qj.w / ncx, cxt = qj.w % ncx;
+    int r = 0;
+    while (r < nr && rowid[r] != R2t) ++r;
+    int run = 0;
+    for (int q = 0, rn = 0; q < nx; ++q) {
+      if (q > 0 && xo[q] != xo[q - 1] + 1) ++rn;
+      if (xo[q] == cxt) run = rn;
+    }
+    if (r >= nr) {   // not in a neighbour row: cannot happen with a valid candidate list
+      atomicOr(err, ERR_INDEX);
+      continue;
+    }
+    const uint64_t kk = ((uint64_t)(2 * r + run) << 32) | (uint32_t)t;
+    // insertion into the sorted hits
+    if (m < kMaxHits) {
+      int p = m;
+      while (p > 0 && key[p - 1] > kk) {
+        key[p] = key[p - 1];
+        --p;
+      }
+      key[p] = kk;
+    }
+    ++m;
+  }
+  if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
+  const int mm = m < W ? (m < kMaxHits ? m : kMaxHits) : W;
+  for (int k = 0; k < mm; ++k) {
+    const int32_t t = (int32_t)(uint32_t)key[k];
+    const int r = (int)(key[k] >> 33);
+    nbr[(int64_t)k * n + s] = t;
+    pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)(pre[r] + (t - rs[r]));
+  }
+  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
+  cnt[s] = (uint8_t)mm;
+  const unsigned act = __activemask();
+  const int32_t wm = __reduce_max_sync(act, m);
+  const int32_t ws = __reduce_max_sync(act, (tend + 3) & ~3);
+  const int32_t wr = __reduce_max_sync(act, own_len);
+  if ((threadIdx.x & 31) == (__ffs(act) - 1)) {
+    atomicMax(maxcnt, wm);
+    atomicMax(maxstaged, ws);
+    atomicMax(maxrow, wr);
+  }
+}
+
 // Sec. 2: T_i^lat = sum_S (1/2) m |v - v_com|^2 / ((3/2) k_B N_j) over S = {i} + neighbours.
 // With M = sum m, P = sum m v, W = sum m |v|^2:  sum (1/2) m |v - v_com|^2 = (W - |P|^2 / M) / 2.
 // One atom type: M = m N_j, P = m sum v with sum v exact on the 2^-48 grid
@@ -617,6 +803,28 @@ cudaError_t launch_neighbors(Ctx &c) {
   if (c.n == 0) return cudaGetLastError();
   bool fast = true;
   for (int k = 0; k < 3; ++k) fast = fast && (!c.g.per[k] || c.g.nc[k] >= 3);
+  if (c.skin_q > 0 && fast && !c.wgt && c.W <= 32) {
+    // candidates with the skin: rebuilt when an atom moved more than skin / 2 (or
+    // at the first build), then the exact test of this step's positions
+    int32_t *flag = c.err + 4;
+    if (!c.cand_valid) {
+      cudaMemsetAsync(flag, 0xff, sizeof(int32_t), c.stream);
+    } else {
+      cudaMemsetAsync(flag, 0, sizeof(int32_t), c.stream);
+      const int64_t half = c.skin_q / 2;
+      skin_check_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>((int32_t)c.n, c.g, c.q_orig, c.q_ref, half * half,
+                                                              flag);
+    }
+    const int64_t rvq = c.g.rcq + c.skin_q;
+    cand_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, rvq * rvq, c.q_s, c.perm, c.cell_start,
+                                                      c.row_nbr, kCandWidth, c.cand, c.ccnt, c.q_orig, c.q_ref, flag,
+                                                      c.err);
+    filter_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>(
+        (int32_t)c.n, c.g, c.q_s, c.perm, c.inv_perm[c.cur_inv], c.cell_start, c.row_nbr, c.W, c.cand, c.ccnt,
+        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt, c.maxstaged, c.maxrow, c.err);
+    c.cand_valid = true;
+    return cudaGetLastError();
+  }
   // the weighted forms store each pair's rate weight beside its index
   auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
                     : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);

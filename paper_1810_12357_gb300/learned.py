@@ -161,3 +161,89 @@ def train_track_window(n_w: int = 100, stages: int = 15, damping: float = 2.0 / 
             "stability_trained": w.stability(), "loss_first": hist[0], "loss_last": hist[-1],
             "heldout_256k_rollout_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
     return coeffs, info
+
+
+def corrector_init(seed: int = 0):
+    """Initial corrector parameters (6336, FP32): He-scaled node layers, w4 = 0,
+    so that the untrained corrector is the identity."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    H, U, F = 64, 16, 16
+    W1 = np.zeros((H, F))
+    W1[:, :11] = rng.normal(0, np.sqrt(2.0 / 11), size=(H, 11))
+    W2 = rng.normal(0, np.sqrt(2.0 / H), size=(H, H))
+    W3 = rng.normal(0, np.sqrt(1.0 / H), size=(U, H))
+    P = rng.normal(0, 0.5, size=(U, 2))
+    parts = [W1.ravel(), np.full(H, 0.05), W2.ravel(), np.full(H, 0.05), W3.ravel(), P.ravel(), np.zeros(U),
+             np.zeros(U)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def corrector_windows(system, params: dict, coeffs, n_windows: int, n_w: int = 100, stages: int = 15,
+                      order: int = 2, skip: int = 1):
+    """Training pairs of the corrector from one cell: the states a run of the
+    window propagator visits (the initial state, or the plain state after `skip`
+    windows, then the window's own chained results) and, from each, the window's
+    result Y and the n_w plain substeps' result T* (coupling off), as
+    (context, [(Y, T*)], kappa)."""
+    import torch
+    from . import EhcCheb
+    p = dict(params, G=0.0, frozen=1)
+    g = Ehc(p, system)
+    g.set_te(system.Te)
+    x = torch.as_tensor(system.x, device="cuda")
+    v = torch.as_tensor(system.v, device="cuda")
+    g.build_neighbors(x, v)
+    if skip:
+        g.substep(skip * n_w)
+    w = EhcCheb(g, n_w, stages, 2.0 / 13.0, order=order)
+    w.set_coefficients(*coeffs)
+    s = g.get_te()
+    pairs = []
+    for _ in range(n_windows):
+        y = w.predict(s)
+        g.set_te(s)
+        g.build_neighbors(x, v)     # set_te starts a new MD step (frozen atoms: the same list)
+        g.substep(n_w)
+        pairs.append((y, g.get_te()))
+        s = y
+    return g, pairs, w.kappa()
+
+
+def train_track_corrector(coeffs, n_w: int = 100, stages: int = 15, order: int = 2, steps: int = 1500,
+                          lr: float = 1e-3, n_windows: int = 12, seed: int = 0):
+    """The corrector network of the learned window on the swift-ion track: Adam on
+    (window result, plain substeps) pairs of six 256,000-atom track and hot-spot
+    cells (40^3 cells), taken on the states a run of the window with the given
+    stage coefficients visits from the initial profile on (n_windows windows).
+    Returns the parameters and a record with the held-out error of a seventh
+    cell's windows with and without the corrector."""
+    import time
+    import numpy as np
+    from . import EhcGnn
+    from . import inputs as I
+    p = I.params_track()
+    t0 = time.perf_counter()
+    cells = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
+    cells += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
+              for k in range(3)]
+    data = [corrector_windows(c, p, coeffs, n_windows, n_w, stages, order, skip=0) for c in cells]
+    net = EhcGnn(data[0][0], params=corrector_init(seed))
+    hist = []
+    for k in range(steps):
+        ctx, pairs, kappa = data[k % len(data)]
+        y, ts = pairs[(k // len(data)) % len(pairs)]
+        hist.append(net.train_step(y, ts, kappa, lr if k < 3 * steps // 4 else 0.3 * lr, ctx=ctx))
+    params = net.get_params()
+    t_train = time.perf_counter() - t0
+    del data
+    # held-out: the windows of a seventh track, without and with the corrector
+    hc, hp, hk = corrector_windows(I.track_system(40, 199, peak=20000.0, r0=20.0), p, coeffs, n_windows, n_w,
+                                   stages, order, skip=0)
+    hnet = EhcGnn(hc, params=params)
+    err_u = [float(((y - t).abs() / t).max()) for y, t in hp]
+    err_t = [float(((hnet.apply(y, hk) - t).abs() / t).max()) for y, t in hp]
+    info = {"train_s": t_train, "train_cells": len(cells), "windows_per_cell": n_windows, "train_steps": steps,
+            "loss_first": hist[0], "loss_last": hist[-1],
+            "heldout_256k_window_max_rel_err": {"window": err_u, "window_and_corrector": err_t}}
+    return params, info

@@ -366,3 +366,28 @@ def test_speed_outside_fixed_point_range_refused():
     with pytest.raises(EhcError) as e:
         g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("T_lat", [300.0, 3000.0])
+def test_skin_candidates_give_the_full_search_list(T_lat):
+    """Neighbour lists taken from skin candidates (ehc_params.skin_A > 0: rebuilt only
+    when an atom moved more than skin / 2) are the lists of the full cell search on
+    the same cells (negative skin), in the same order: a track with free flight over
+    12 MD steps (at 3,000 K the candidates are rebuilt along the way) gives bitwise
+    the same temperatures and velocities, and its list equals the oracle's."""
+    torch = _torch()
+    s = I.track_system(12, 13, r0=8.0, disp_sigma=0.1, T_lat=T_lat)
+    res = []
+    for skin in (0.3, -0.3):
+        p = dict(I.params_track(), skin=skin, dt_sub=5e-4)
+        # MD steps of 0.5 fs: atoms move 0.2-0.6 A, past the skin's 0.15 A
+        g, x, v = run_gpu(s, p, 12, 100, dt_md=0.5)
+        res.append((g.get_te().cpu().numpy(), v.cpu().numpy(), x.cpu().numpy(), g))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    g = res[0][3]
+    ro, co = oracle.neighbors(res[0][2], s.box, s.periodic, 4.0, cap_per_atom=32)
+    # one more build on the final positions, against the oracle's list there
+    g.build_neighbors(torch.as_tensor(res[0][2], device="cuda"), torch.as_tensor(res[0][1], device="cuda"))
+    rg, cg = g.export_neighbors(cap_per_atom=32)
+    assert np.array_equal(rg, ro) and np.array_equal(cg, co)
