@@ -35,10 +35,17 @@ if ROOT not in sys.path:
 METRIC = "atom·substeps/s, 4M-atom track: plain vs learned propagator @≤1% T_e err"
 UNIT = "atom·substeps/s"
 N_SUB = 100            # substeps per MD step
+N_MD_RUN = 100         # MD steps of the track workload (10,000 substeps)
 DT_SUB = 1.0e-3        # fs, electronic substep (stable: dt (2 n_max K + G/C_e) = 1.9 at n_max = 18)
 DT_MD = N_SUB * DT_SUB # fs, the lattice advances the same time as the electrons
 N_NB = 18              # neighbours per atom in FCC Cu at r_c = 4.0 A
 B_ALG = 4 * N_NB + 44  # algorithmic bytes per atom-substep of the substep kernel
+# what the path computes in: FP32 pair terms summed with TwoSum, the substep state
+# an unevaluated float pair (about 48 bits) inside a substep call, T in FP64
+# between calls, the exchanged energy, reductions and ledger in FP64
+DTYPE = "f32 pair flux (TwoSum); float-pair (~48-bit) substep state; f64 T between calls, exchange and ledger"
+TIMED_S = 3.0          # the K-step timed block is repeated until about this many seconds are timed
+MAX_REPEATS = 30
 # kernels launched per MD step: bin + 3-phase scan + scatter + cell sort + gather
 # + neighbour list + lattice temperature + 2 reduction kernels = 11; the float-pair
 # split before the first substep and the merge at the next build = 2; N_SUB
@@ -113,10 +120,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(cells: int, tile_threads: int = 0):
+def workload(cells: int, tile_threads: int = 0, skin=None):
     from paper_1810_12357_gb300 import inputs as I
     s = I.track_system(cells, seed=2)
     p = dict(I.params_track(), tile_threads=tile_threads)
+    if skin is not None:
+        p["skin"] = skin
     return s, p
 
 
@@ -125,7 +134,8 @@ def config_dict(cells: int, n: int, extra=None, n_sub: int = N_SUB):
                      f"velocities, T_e radial Gaussian 20,000 K peak r0=2 nm on 300 K, C_e=gamma*T_e capped "
                      f"at 3 k_B/atom, K_e=K0*T_e/T_l, G=1e17, r_c=4.0 A, Langevin hand-over, free flight",
          "n_atoms": n, "substeps_per_step": n_sub, "dt_sub_fs": DT_SUB, "dt_md_fs": DT_MD,
-         "pair_flux": "fp32", "state_and_ledger": "fp64",
+         "pair_flux": "fp32, compensated sums", "substep_state": "float pair (~48 bits)",
+         "T_between_calls_exchange_and_ledger": "fp64",
          "l2": "inputs larger than L2 (~0.9 GB working set), no flush"}
     if extra:
         d.update(extra)
@@ -145,7 +155,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    s, p = workload(args.cells, args.tile_threads)
+    s, p = workload(args.cells, args.tile_threads, args.skin)
     if args.rate_shell > 0:
         # distance-weighted pair rates: the general single-precision kernel
         p = dict(p, rate_shell_n=args.rate_shell)
@@ -218,21 +228,58 @@ def run_gpu(args):
             sim.drift(x, v, DT_MD)
         t_fs += DT_MD
 
+    x0, v0 = x.clone(), v.clone()
+    md_done = 0
+
+    def restart():
+        # back to the workload's initial state (untimed): the track is a run of
+        # N_MD_RUN MD steps; later steps of free flight disorder the lattice
+        nonlocal t_fs, md_done, F
+        x.copy_(x0)
+        v.copy_(v0)
+        sim.set_te(s.Te)
+        t_fs = 0.0
+        md_done = 0
+        if verlet:
+            sim.build_neighbors(x, v)
+            F, _ = sim.forces()
+        for _ in range(args.warmup):
+            step(False)
+        md_done += args.warmup
+
     for _ in range(args.warmup):
         step(False)
+    md_done += args.warmup
     barrier()
     clk = ClockSampler(dev.index)
     clk.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    t0.record(stream)
-    for _ in range(args.steps):
-        step(True)
-    t1.record(stream)
-    barrier()
+    # the K-step block, timed between barriers with CUDA events on the context's
+    # stream; repeated (each block exactly K steps) until about TIMED_S seconds are
+    # timed, the reported step time the median block
+    blocks = []
+    while True:
+        if blocks and md_done + args.steps > max(N_MD_RUN, args.warmup + args.steps):
+            restart()
+        md_done += args.steps
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        t1.record(stream)
+        barrier()
+        blocks.append(t0.elapsed_time(t1))
+        if ws > 1:
+            blocks[-1] = max_over_ranks([blocks[-1]], dist, dev)[0]
+        if args.repeats > 0:
+            if len(blocks) >= args.repeats:
+                break
+        elif sum(blocks) * 1e-3 >= TIMED_S or len(blocks) >= MAX_REPEATS:
+            break
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
+    ms = statistics.median(blocks)
+    args.blocks_ms = blocks
     sub_ms = [a.elapsed_time(b) for a, b in sub_ev]
     e = sim.energy()
     if verlet:
@@ -258,17 +305,29 @@ def _e2e(args, s, p, n, barrier, stream, tfix=None):
     e2e_steps = max(1, min(args.steps, 10))
     for k in range(2):
         h.md_step_host(xh, vh, N_SUB, k * DT_MD, DT_MD, Teh)
-    barrier()
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for k in range(e2e_steps):
-        h.md_step_host(xh, vh, N_SUB, (k + 2) * DT_MD, DT_MD, Teh)
-    a1.record(stream)
-    barrier()
-    e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    # blocks of e2e_steps host-buffer MD steps until about a second and a half is
+    # timed; the median block's step time
+    per_step, k = [], 2
+    x_init, v_init = torch.as_tensor(s.x), torch.as_tensor(s.v)
+    while len(per_step) < MAX_REPEATS and sum(per_step) * e2e_steps * 1e-3 < 0.5 * TIMED_S:
+        if k + e2e_steps > N_MD_RUN:
+            # back to the initial state (untimed) after the workload's 100 MD steps
+            xh.copy_(x_init)
+            vh.copy_(v_init)
+            h.set_te(s.Te)
+            k = 0
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(e2e_steps):
+            h.md_step_host(xh, vh, N_SUB, k * DT_MD, DT_MD, Teh)
+            k += 1
+        a1.record(stream)
+        barrier()
+        per_step.append(a0.elapsed_time(a1) / e2e_steps)
     h.close()
-    return e2e_ms
+    return statistics.median(per_step)
 
 
 def max_over_ranks(vals, dist, device):
@@ -311,7 +370,7 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 pair flux / f64 state", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": config_dict(args.cells, n, dict({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                                    "path": "plain"},
                                                   **({"border": "fixed 300 K electron shell %g A thick, %d atoms"
@@ -339,12 +398,27 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                      "bytes_per_atom_substep": b_alg,
                      "peak_kind": kind, "substep_ms": sub_launch_ms},
         "clocks": clocks,
+        "timing": {"blocks": len(args.blocks_ms), "block_ms": args.blocks_ms,
+                   "timed_s": sum(args.blocks_ms) * 1e-3,
+                   "value_range": [job_value(ws, n, N_SUB, args.steps, max(args.blocks_ms)),
+                                   job_value(ws, n, N_SUB, args.steps, min(args.blocks_ms))],
+                   "note": "value and ms_per_step from the median of the K-step blocks"},
         "energy_drift": e["drift"],
     }
     if args.md == "verlet":
         line["force_kernel_ms"] = args.force_ms
     if not args.no_cpu_baseline and ws == 1:   # the oracle's timing: one process, N = 1 only
         line["cpu_baseline"] = cpu_baseline(args.cells, ce_local=args.ce_local)
+    plain_default = not (args.ce_local or args.rate_shell > 0 or args.border > 0 or args.md == "verlet")
+    if ws == 1 and plain_default and not args.no_learned:
+        # the metric's other half: the learned window on the same workload, trained
+        # here, against plain substeps from the same state over the same MD steps
+        coeffs, info = train_window(args)
+        corr = None
+        if not args.no_corrector:
+            from paper_1810_12357_gb300 import learned
+            corr = learned.train_track_corrector(coeffs, args.window, args.stages, args.order)
+        line["learned"] = window_line(args, coeffs, info, corr)["learned"]
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -482,7 +556,7 @@ def run_batch(args):
     sub_launch_ms = sub_ms / (args.steps * N_SUB)
     line = {"metric": METRIC, "value": n * N_SUB * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair flux / f64 state", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": f"batched replicas: {b.n_rep} FCC Cu cascade cells, log-uniform 8k-500k atoms "
                                    f"({n:,} atoms), random Gaussian hot spots, one substep launch per substep "
                                    f"over all replicas", "n_atoms": n, "replicas": b.n_rep,
@@ -495,7 +569,11 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_window(args, coeffs=None, learned_info=None):
+def run_window(args, coeffs=None, learned_info=None, corrector=None):
+    print(json.dumps(window_line(args, coeffs, learned_info, corrector)), flush=True)
+
+
+def window_line(args, coeffs=None, learned_info=None, corrector=None):
     """Chebyshev window propagator on the 4,000,000-atom track: every MD step
     (build, 100 substeps' worth of electron evolution, hand-over, drift) advances
     the electrons by windows of n_w substeps, each with `stages` flux evaluations,
@@ -517,9 +595,10 @@ def run_window(args, coeffs=None, learned_info=None):
     rest = N_SUB - n_win * n_w
     stream = torch.cuda.current_stream()
 
-    def run(use_window):
+    def run(use_window, corr=None):
         g = Ehc(p, s)
         g.set_te(s.Te)
+        net = None
         x = torch.as_tensor(s.x, device="cuda").contiguous()
         v = torch.as_tensor(s.v, device="cuda").contiguous()
         w = None
@@ -541,6 +620,10 @@ def run_window(args, coeffs=None, learned_info=None):
                     w = EhcCheb(g, n_w, st, args.damping, order=args.order)
                     if coeffs is not None:
                         w.set_coefficients(*coeffs)
+                    if corr is not None:
+                        from paper_1810_12357_gb300 import EhcGnn
+                        net = EhcGnn(g, params=corr)
+                        w.set_corrector(net)
                     stats["stability"] = w.stability()
                     stats["stability_bound"] = n_w * g.energy()["stability"]
                     stats["spectrum"] = w.spectrum(iters=300)
@@ -571,83 +654,78 @@ def run_window(args, coeffs=None, learned_info=None):
     ms_w, Tw, ew, st_w = run(True)
     ms_p, Tp, ep, st_p = run(False)
     err = float(((Tw - Tp).abs() / Tp).max())
-    # value: the electrons' evolution alone (what the propagator stands in for)
-    value = n * N_SUB * args.steps / (st_w["evo_ms"] * 1e-3)
-    plain = n * N_SUB * args.steps / (st_p["evo_ms"] * 1e-3)
+    corr_rec = None
+    if corrector is not None:
+        # the same window with the trained corrector network on every window's result
+        ms_c, Tc, ec, st_c = run(True, corrector[0])
+        corr_rec = {"whole_md_step": {"value": n * N_SUB * args.steps / (ms_c * 1e-3),
+                                      "speedup_vs_plain": ms_p / ms_c, "ms_per_step": ms_c / args.steps},
+                    "electrons_only": {"value": n * N_SUB * args.steps / (st_c["evo_ms"] * 1e-3),
+                                       "speedup_vs_plain": st_p["evo_ms"] / st_c["evo_ms"]},
+                    "max_rel_T_err_vs_plain": float(((Tc - Tp).abs() / Tp).max()),
+                    "window_without_corrector_max_rel_T_err_vs_plain": err,
+                    "fallbacks": st_c["fallbacks"], "windows": st_c["windows"], "energy_drift": ec["drift"],
+                    "network": "2 message-passing layers, node width 64 (tensor-core MLP 16-64-64-16, BF16 "
+                               "weights and activations, FP32 accumulate), edge MLP width 16, antisymmetric "
+                               "pair-flux output"}
+        corr_rec.update(corrector[1])
+    # the electrons' evolution alone (what the propagator stands in for) and the
+    # whole MD step (build, electrons, hand-over, drift), each against plain substeps
+    evo = n * N_SUB * args.steps / (st_w["evo_ms"] * 1e-3)
+    evo_plain = n * N_SUB * args.steps / (st_p["evo_ms"] * 1e-3)
     whole = n * N_SUB * args.steps / (ms_w * 1e-3)
     whole_plain = n * N_SUB * args.steps / (ms_p * 1e-3)
     rho = st_w["rho"] or [0.0]
     path = {"path": "chebyshev window", "order": args.order, "damping": args.damping}
     if coeffs is not None:
         path = {"path": "learned window: stage coefficients trained on the plain method's windows"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    key = "learned" if coeffs is not None else "window"
+    line = {"metric": METRIC, "value": whole, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_w / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 stages / f64 state and ledger", "data": "synthetic",
             "config": config_dict(args.cells, n, dict(path, window_substeps=n_w, stages=st, residual_tau=tau,
                                                       lattice="frozen" if args.frozen_lattice
                                                       else "Langevin, free flight")),
-            "learned" if coeffs is not None else "window": {"plain_value": plain, "speedup_vs_plain": value / plain, "max_rel_T_err_vs_plain": err,
-                       "whole_md_step": {"value": whole, "plain_value": whole_plain,
-                                         "speedup_vs_plain": whole / whole_plain},
-                       "fallbacks": st_w["fallbacks"], "windows": st_w["windows"],
-                       "rho_median": float(np.median(rho)), "rho_max": float(np.max(rho)),
-                       "energy_drift": ew["drift"], "plain_energy_drift": ep["drift"],
-                       "stability_interval": st_w.get("stability"),
-                       "spectrum_bound": st_w.get("stability_bound"),
-                       "spectrum_estimate": st_w.get("spectrum"),
-                       "md_steps_total": args.warmup + args.steps}}
+            key: {"whole_md_step": {"value": whole, "plain_value": whole_plain,
+                                    "speedup_vs_plain": whole / whole_plain,
+                                    "ms_per_step": ms_w / args.steps, "plain_ms_per_step": ms_p / args.steps},
+                  "electrons_only": {"value": evo, "plain_value": evo_plain, "speedup_vs_plain": evo / evo_plain},
+                  "max_rel_T_err_vs_plain": err,
+                  "fallbacks": st_w["fallbacks"], "windows": st_w["windows"],
+                  "rho_median": float(np.median(rho)), "rho_max": float(np.max(rho)),
+                  "energy_drift": ew["drift"], "plain_energy_drift": ep["drift"],
+                  "stability_interval": st_w.get("stability"),
+                  "spectrum_bound": st_w.get("stability_bound"),
+                  "spectrum_estimate": st_w.get("spectrum"),
+                  "md_steps_total": args.warmup + args.steps,
+                  "window_substeps": n_w, "stages": st, "residual_tau": tau}}
     if learned_info:
-        line["learned"].update(learned_info)
-    print(json.dumps(line), flush=True)
+        line[key].update(learned_info)
+    if corr_rec is not None:
+        line[key]["corrector"] = corr_rec
+    return line
 
 
 def train_window(args):
-    """Stage coefficients of the learned window: Adam on rollouts of 6 chained
-    windows against the plain method's trajectories (coupling off) of 256,000-atom
-    track and hot-spot cells (40^3 cells), from the second-order damped Chebyshev
-    values, each rollout started after the first window (the sharp initial front
-    is left to the residual test); returns the coefficients and the training
-    record with held-out rollout errors."""
-    from paper_1810_12357_gb300 import EhcCheb, learned
-    from paper_1810_12357_gb300 import inputs as I
-    n_w, st, nwin = args.window, args.stages, 6
-    p = I.params_track()
-    t0 = time.perf_counter()
-    train_sys = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
-    train_sys += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
-                  for k in range(3)]
-    data = [learned.generate_trajectory(s, p, nwin, n_w) for s in train_sys]
-    w = EhcCheb(data[0][0], n_w, st, args.damping, order=args.order)
-    beta0 = w.stability()
-    # the stability range of training: the spectrum of the training states
-    spec = max(w.spectrum(t_in, iters=300, ctx=c) for c, t_in, _ in data)
-    hist = learned.train_rollout(w, data, args.train_steps, lr=5e-3, lr_final=2e-3, power=args.loss_power)
-    coeffs = [c.copy() for c in w.coefficients()]
-    t_train = time.perf_counter() - t0
-    del data
-    # held-out rollouts of another track: trained against untrained coefficients
-    hc, h0, ht = learned.generate_trajectory(I.track_system(40, 199, peak=20000.0, r0=20.0), p, nwin, n_w)
-    base = EhcCheb(hc, n_w, st, args.damping, order=args.order)
-    per_u = learned.rollout_error(base, h0, ht, ctx=hc)
-    per_t = learned.rollout_error(w, h0, ht, ctx=hc)
-    info = {"train_s": t_train, "train_rollouts": len(train_sys), "rollout_windows": nwin,
-            "train_steps": args.train_steps,
-            "train_cells": "256,000-atom tracks and hot spots (40^3 cells), rollouts from the end of the first window",
-            "start": "damped Chebyshev order %d, damping %.4g" % (args.order, args.damping),
-            "loss": "sum over the rollout's windows of mean relative error^%d" % args.loss_power,
-            "training_spectrum_tauK_lambda_max": spec, "stability_untrained": beta0,
-            "stability_trained": w.stability(), "loss_first": hist[0], "loss_last": hist[-1],
-            "heldout_256k_rollout_max_rel_err_per_window": {"trained": per_t, "untrained": per_u}}
-    return coeffs, info
+    """Stage coefficients of the learned window (learned.train_track_window) with
+    the bench's window settings; returns the coefficients and the training record."""
+    from paper_1810_12357_gb300 import learned
+    return learned.train_track_window(args.window, args.stages, args.damping, args.order,
+                                      args.train_steps, args.loss_power)
 
 
 def run_learned(args):
     """Learned propagator on the 4,000,000-atom track.  Default: the window with
-    trained stage coefficients (train_window, then run_window with them); with
+    trained stage coefficients (train_window) and the corrector network trained on
+    its windows (learned.train_track_corrector), then run_window with both; with
     --model nn the message-passing network below."""
     if args.model == "window":
         coeffs, info = train_window(args)
-        return run_window(args, coeffs, info)
+        corr = None
+        if not args.no_corrector:
+            from paper_1810_12357_gb300 import learned
+            corr = learned.train_track_corrector(coeffs, args.window, args.stages, args.order)
+        return run_window(args, coeffs, info, corr)
     return run_learned_nn(args)
 
 
@@ -770,6 +848,14 @@ def main():
     ap.add_argument("--train-steps", type=int, default=None)
     ap.add_argument("--loss-power", type=int, default=2)
     ap.add_argument("--replicas", type=int, default=256)
+    ap.add_argument("--repeats", type=int, default=0,
+                    help="timed K-step blocks (0: as many as fill about %g s)" % TIMED_S)
+    ap.add_argument("--no-learned", action="store_true",
+                    help="leave the learned window out of the default line")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="neighbour-search skin [A] (default: the workload's)")
+    ap.add_argument("--no-corrector", action="store_true",
+                    help="learned window without the corrector network")
     args = ap.parse_args()
     args.tau_given = any(a == "--tau" or a.startswith("--tau=") for a in sys.argv[1:])
     # window defaults: second order, damping 2/13, 15 stages (stable to 0.65 s^2 =
