@@ -109,6 +109,11 @@ extern "C" {
  *   tile_threads    threads owning atoms in the row-tile substep kernel: 0 = chosen by a
  *                   timing tuner on the first substep call of 8 or more substeps (and after
  *                   tiles grow), 256 or 128 = fixed; both give identical results
+ *   tile_grid_quarters  with tile_threads fixed: the row-tile kernel's persistent grid in
+ *                   quarters of its resident CTAs (2, 3 or 4; 0 = 4); with tile_threads = 0
+ *                   the tuner times both widths with 4, 3 and 2 quarters (12 substeps of a
+ *                   call of 16 or more) and keeps the fastest, another choice than (256, 4)
+ *                   only if 3 % faster; every choice gives identical results
  *   skin_A          skin of the neighbour search (0 <= skin_A <= rc_A; 0: none): cells are
  *                   at least rc_A + skin_A wide, and a build takes the list from candidates
  *                   (the atoms within rc_A + skin_A at the last candidate build) by the
@@ -147,7 +152,8 @@ typedef struct ehc_params {
   int32_t tile_threads;
   int32_t rate_shell_n;
   int32_t ce_mode;
-  int32_t reserved[4];
+  int32_t tile_grid_quarters;
+  int32_t reserved[3];
   double pot_D_eV;          /* Morse pair potential of ehc_forces (0: no forces) */
   double pot_alpha_perA;
   double pot_r0_A;
@@ -544,6 +550,13 @@ int ehc_gnn_train_step(ehc_gnn *g, ehc_ctx *c, double kappa, const double *Y_dev
  * takes with w, before its residual test; g stays owned by the caller and must
  * outlive its use by w. */
 int ehc_cheb_set_corrector(ehc_cheb *w, ehc_gnn *g);
+
+/* The row-tile kernel's width (threads owning atoms: 256 or 128) and persistent
+ * grid (quarters of its resident CTAs) this context runs with: the tuner's choice
+ * after the first substep call of 16 or more substeps, or the fixed values of
+ * ehc_params; (0, 0) before either.  A caller can keep the choice for later
+ * contexts of the same shape (the Python binding caches it per GPU and shape). */
+int ehc_tuning(ehc_ctx *c, int32_t *tile_threads, int32_t *grid_quarters);
 void ehc_gnn_destroy(ehc_gnn *g);
 
 /* ---- Batched replicas --------------------------------------------------------
@@ -574,6 +587,9 @@ int ehc_batch_drift(ehc_batch *b, double *x_dev, const double *v_dev, double dt_
 int ehc_batch_get_te(ehc_batch *b, double *Te_dev_out);
 /* ledger of replica r */
 int ehc_batch_energy(ehc_batch *b, int32_t r, ehc_energy_t *out);
+/* the batch's row-tile width and grid share, as ehc_tuning (ehc_params of the
+ * batch: tile_threads, tile_grid_quarters) */
+int ehc_batch_tuning(ehc_batch *b, int32_t *tile_threads, int32_t *grid_quarters);
 void ehc_batch_destroy(ehc_batch *b);
 
 #ifdef __cplusplus

@@ -49,8 +49,8 @@ class ehc_params(ctypes.Structure):
         ("couple_mode", ctypes.c_int32), ("frozen", ctypes.c_int32), ("dof_mode", ctypes.c_int32),
         ("flux_prec", ctypes.c_int32), ("laser_on", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("tile_threads", ctypes.c_int32), ("rate_shell_n", ctypes.c_int32),
-        ("ce_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("ce_mode", ctypes.c_int32), ("tile_grid_quarters", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
         ("pot_D_eV", ctypes.c_double), ("pot_alpha_perA", ctypes.c_double), ("pot_r0_A", ctypes.c_double),
         ("stop_beta_per_fs", ctypes.c_double), ("stop_ecut_eV", ctypes.c_double), ("skin_A", ctypes.c_double),
     ]
@@ -119,6 +119,8 @@ _SIGS = {
     "ehc_cheb_spectrum": (_I, [_P, _P, _P, ctypes.c_int32, _P]),
     "ehc_cheb_destroy": (None, [_P]),
     "ehc_cheb_set_corrector": (_I, [_P, _P]),
+    "ehc_tuning": (_I, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "ehc_batch_tuning": (_I, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "ehc_gnn_create": (_I, [_P, ctypes.c_double, ctypes.POINTER(_P)]),
     "ehc_gnn_set_params": (_I, [_P, _P, _P]),
     "ehc_gnn_get_params": (_I, [_P, _P, _P]),
@@ -206,6 +208,7 @@ def make_params(p: dict) -> ehc_params:
     q.use_graph = int(p.get("use_graph", 1))
     q.tile_threads = int(p.get("tile_threads", 0))
     q.skin_A = float(p.get("skin", 0.0))
+    q.tile_grid_quarters = int(p.get("tile_grid_quarters", 0))
     return q
 
 
@@ -228,7 +231,7 @@ class Ehc:
     to the device first."""
 
     def __init__(self, params: dict, system=None, *, n=None, box=None, periodic=None, mass_amu=None,
-                 types=None, device="cuda"):
+                 types=None, device="cuda", tune_cache: bool = False):
         import torch
         L = load_library()
         if not torch.cuda.is_available():
@@ -238,7 +241,19 @@ class Ehc:
             n, box, periodic, mass_amu, types = (system.n, system.box, system.periodic, system.mass_amu,
                                                  system.type)
         self.n = int(n)
-        self.params = dict(params)
+        params = dict(params)
+        # tune_cache: the row-tile choice stored for this GPU and shape (tuning.py),
+        # else the tuner's choice is stored after the first long substep call
+        self._tune_key = None
+        if tune_cache and not params.get("tile_threads"):
+            from . import tuning
+            key = tuning.shape_class(self.n, box, params["rc"], params.get("skin", 0.0))
+            got = tuning.lookup(key)
+            if got:
+                params["tile_threads"], params["tile_grid_quarters"] = got
+            else:
+                self._tune_key = key
+        self.params = params
         self._p = make_params(params)
         box_a = np.ascontiguousarray(box, dtype=np.float64)
         per_a = np.ascontiguousarray(periodic, dtype=np.int32)
@@ -296,6 +311,19 @@ class Ehc:
 
     def substep(self, n_sub: int, t_fs: float = 0.0):
         _check(self._lib.ehc_substep(self._h, int(n_sub), float(t_fs)), "ehc_substep")
+        if self._tune_key is not None:
+            nt, q = self.tuning()
+            if nt:
+                from . import tuning
+                tuning.store(self._tune_key, nt, q)
+                self._tune_key = None
+
+    def tuning(self):
+        """(tile_threads, grid_quarters) the row-tile kernel runs with ((0, 0) before
+        the first long substep call when tuned)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.ehc_tuning(self._h, ctypes.byref(a), ctypes.byref(b)), "ehc_tuning")
+        return a.value, b.value
 
     def couple(self, v, dt_md_fs: float):
         _check(self._lib.ehc_couple(self._h, _ptr(v), float(dt_md_fs)), "ehc_couple")
@@ -420,13 +448,24 @@ class EhcBatch:
     list of inputs.System sharing one parameter set; per-atom arrays are the
     replicas' arrays concatenated in order (see `offsets`)."""
 
-    def __init__(self, params: dict, systems):
+    def __init__(self, params: dict, systems, tune_cache: bool = False):
         import torch
         L = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libehc needs a CUDA device; there is no CPU path")
         self._lib = L
-        self.params = dict(params)
+        params = dict(params)
+        self._tune_key = None
+        if tune_cache and not params.get("tile_threads"):
+            from . import tuning
+            key = tuning.shape_class(sum(int(x.n) for x in systems), systems[0].box, params["rc"],
+                                     params.get("skin", 0.0), replicas=len(systems))
+            got = tuning.lookup(key)
+            if got:
+                params["tile_threads"], params["tile_grid_quarters"] = got
+            else:
+                self._tune_key = key
+        self.params = params
         self._p = make_params(params)
         n = np.ascontiguousarray([s.n for s in systems], dtype=np.int64)
         boxes = np.ascontiguousarray(np.concatenate([s.box for s in systems]), dtype=np.float64)
@@ -463,6 +502,17 @@ class EhcBatch:
 
     def substep(self, n_sub: int, t_fs: float = 0.0):
         _check(self._lib.ehc_batch_substep(self._h, int(n_sub), float(t_fs)), "ehc_batch_substep")
+        if self._tune_key is not None:
+            nt, q = self.tuning()
+            if nt:
+                from . import tuning
+                tuning.store(self._tune_key, nt, q)
+                self._tune_key = None
+
+    def tuning(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.ehc_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b)), "ehc_batch_tuning")
+        return a.value, b.value
 
     def couple(self, v, dt_md_fs: float):
         _check(self._lib.ehc_batch_couple(self._h, _ptr(v), float(dt_md_fs)), "ehc_batch_couple")

@@ -166,7 +166,7 @@ int run_substeps(Ctx &c, int32_t n_sub) {
   const int ab = (c.A == c.abuf[0]) ? 0 : 1;
   const int path = (c.p.flux_prec == 1) ? 2 : ((tile_path(c) || local_tile(c)) ? 1 : 0);
   const int pairs = (c.n_max + 1) / 2;
-  const int tile = c.tile_floats, nt = c.tile_nt;
+  const int tile = c.tile_floats, nt = c.tile_nt * 8 + c.tile_q;   // width and grid share, both baked in
   const int border = c.has_border ? 1 : 0;
   bool use_graph = c.p.use_graph && n_sub >= 4;
   if (use_graph) {
@@ -307,6 +307,11 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
     return EHC_E_INVAL;
   }
   c.tile_nt_fixed = p->tile_threads;
+  if (p->tile_grid_quarters < 0 || p->tile_grid_quarters > 4 || (p->tile_grid_quarters && !p->tile_threads)) {
+    delete h;
+    return EHC_E_INVAL;
+  }
+  c.tile_q_fixed = p->tile_grid_quarters;
   c.W = W;
   c.stream = (cudaStream_t)stream;
   c.g.rcq = llrint(p->rc_A * 1048576.0);
@@ -712,25 +717,39 @@ int ehc_build_neighbors(ehc_ctx *h, const double *x_dev, const double *v_dev) {
 
 namespace {
 
-// Tuner of the row-tile kernel's width: two substeps with 256 and two with 128
-// threads owning atoms, timed with events on the stream; the narrower form is
-// kept only if clearly faster.  Both forms give identical results (the same
-// arithmetic per atom), so the four substeps are ordinary substeps.
+// Tuner of the row-tile kernel: the widths (256, 128 threads owning atoms) and
+// the persistent grid's share of the resident CTAs (4, 3, 2 quarters), timed with
+// events on the stream over two substeps each, twelve in all (an even count per
+// candidate, so the mirror parity is unchanged).  Another choice must beat the
+// first (256, full grid) by 3 %.  Every choice gives the same results: each
+// atom's arithmetic does not depend on the schedule.
+constexpr int kTuneCands = 6;
 template <typename Launch>
-int tune_width(cudaStream_t st, int32_t *nt_out, Launch launch) {
-  cudaEvent_t ev[3];
-  for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&ev[i]));
+int tune_tiles(cudaStream_t st, int32_t *nt_out, int32_t *q_out, Launch launch) {
+  const int32_t nts[kTuneCands] = {256, 256, 256, 128, 128, 128};
+  const int32_t qs[kTuneCands] = {4, 3, 2, 4, 3, 2};
+  cudaEvent_t ev[kTuneCands + 1];
+  for (int i = 0; i <= kTuneCands; ++i) CK(cudaEventCreate(&ev[i]));
   CK(cudaEventRecord(ev[0], st));
-  for (int k = 0; k < 2; ++k) CK(launch(k, 256));
-  CK(cudaEventRecord(ev[1], st));
-  for (int k = 2; k < 4; ++k) CK(launch(k, 128));
-  CK(cudaEventRecord(ev[2], st));
-  CK(cudaEventSynchronize(ev[2]));
-  float t256 = 0.f, t128 = 0.f;
-  CK(cudaEventElapsedTime(&t256, ev[0], ev[1]));
-  CK(cudaEventElapsedTime(&t128, ev[1], ev[2]));
-  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
-  *nt_out = (t128 < 0.97f * t256) ? 128 : 256;
+  for (int i = 0; i < kTuneCands; ++i) {
+    for (int k = 0; k < 2; ++k) CK(launch(2 * i + k, nts[i], qs[i]));
+    CK(cudaEventRecord(ev[i + 1], st));
+  }
+  CK(cudaEventSynchronize(ev[kTuneCands]));
+  float best = 0.f;
+  int bi = 0;
+  for (int i = 0; i < kTuneCands; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+    if (i == 0) best = t;
+    else if (t < 0.97f * best) {
+      best = t;
+      bi = i;
+    }
+  }
+  for (int i = 0; i <= kTuneCands; ++i) cudaEventDestroy(ev[i]);
+  *nt_out = nts[bi];
+  *q_out = qs[bi];
   return EHC_OK;
 }
 
@@ -785,19 +804,24 @@ int ehc_substep(ehc_ctx *h, int32_t n_sub, double t_fs) {
     if (r) return r;
     int32_t rest = chunk;
     const int pw = ((c.n_max + 1) / 2 == 9) ? 0 : 1;
-    if (c.tile_nt_fixed) c.tile_nt = c.tile_nt_fixed;
-    if (!laser && c.tile_nt == 0 && chunk >= 8 && tile_path(c) && c.tile_grid128[pw] > 0) {
+    if (c.tile_nt_fixed) {
+      c.tile_nt = c.tile_nt_fixed;
+      c.tile_q = c.tile_q_fixed ? c.tile_q_fixed : 4;
+    }
+    if (!laser && c.tile_nt == 0 && chunk >= 2 * kTuneCands + 4 && tile_path(c) && c.tile_grid128[pw] > 0) {
       const int p0 = c.parity;
       c.t_version += 1;
-      int32_t chosen = 256;
-      r = tune_width(c.stream, &chosen, [&](int k, int nt) {
+      int32_t chosen = 256, q = 4;
+      r = tune_tiles(c.stream, &chosen, &q, [&](int k, int nt, int qq) {
         c.tile_nt = nt;
+        c.tile_q = qq;
         return launch_substep(c, k, p0 ^ (k & 1), c.stream);
       });
       c.tile_nt = chosen;
+      c.tile_q = q;
       if (r) return r;
       c.t_stale = true;
-      rest -= 4;   // an even count: the mirror parity is unchanged
+      rest -= 2 * kTuneCands;   // an even count: the mirror parity is unchanged
     }
     r = run_substeps(c, rest);
     if (r) return r;
@@ -1201,6 +1225,7 @@ struct ehc_batch {
   int32_t nwork = 0, tile_floats = 0, num_sms = 0;
   int32_t tile_grid[2] = {0, 0}, tile_grid128[2] = {0, 0};
   int32_t tile_nt = 0;           // threads owning atoms chosen by the tuner (0: not tuned yet)
+  int32_t tile_q = 4;            // persistent grid in quarters of the resident CTAs
   int parity = 0;
   struct G {
     int n_sub, parity, pairs, tile, nt;
@@ -1403,24 +1428,30 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
   const int pairs = batch_pairs(*b);
   const int pw = pairs == 9 ? 0 : 1;
   int32_t rest = n_sub;
-  if (b->p.tile_threads) b->tile_nt = b->p.tile_threads;
-  if (b->tile_nt == 0 && n_sub >= 8 && b->tile_grid128[pw] > 0) {
-    int32_t chosen = 256;
-    int r = tune_width(b->stream, &chosen, [&](int k, int nt) {
+  if (b->p.tile_threads) {
+    b->tile_nt = b->p.tile_threads;
+    b->tile_q = b->p.tile_grid_quarters ? b->p.tile_grid_quarters : 4;
+  }
+  auto share = [](int32_t g, int32_t q) { return g * q / 4 > 0 ? g * q / 4 : 1; };
+  if (b->tile_nt == 0 && n_sub >= 2 * kTuneCands + 4 && b->tile_grid128[pw] > 0) {
+    int32_t chosen = 256, q = 4;
+    int r = tune_tiles(b->stream, &chosen, &q, [&](int k, int nt, int qq) {
       return launch_tile_worklist(b->reps_dev, b->work, b->nwork, b->tile_floats,
-                                  nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw], pairs, p0 ^ (k & 1), k, nt,
-                                  b->stream);
+                                  share(nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw], qq), pairs,
+                                  p0 ^ (k & 1), k, nt, b->stream);
     });
     if (r) return r;
     b->tile_nt = chosen;
-    rest -= 4;   // an even count: the mirror parity is unchanged
+    b->tile_q = q;
+    rest -= 2 * kTuneCands;   // an even count: the mirror parity is unchanged
   }
   const int nt = b->tile_nt == 128 ? 128 : 256;
-  const int32_t tgrid = nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw];
+  const int32_t tgrid = share(nt == 128 ? b->tile_grid128[pw] : b->tile_grid[pw], b->tile_q);
+  const int ntkey = nt * 8 + b->tile_q;
   int hit = -1;
   for (size_t i = 0; i < b->graphs.size(); ++i) {
     const auto &g = b->graphs[i];
-    if (g.n_sub == rest && g.parity == p0 && g.pairs == pairs && g.tile == b->tile_floats && g.nt == nt)
+    if (g.n_sub == rest && g.parity == p0 && g.pairs == pairs && g.tile == b->tile_floats && g.nt == ntkey)
       hit = (int)i;
   }
   if (hit < 0) {
@@ -1440,7 +1471,7 @@ int ehc_batch_substep(ehc_batch *b, int32_t n_sub, double t_fs) {
       cudaGraphExecDestroy(b->graphs.front().exec);
       b->graphs.erase(b->graphs.begin());
     }
-    b->graphs.push_back({rest, p0, pairs, b->tile_floats, nt, exec});
+    b->graphs.push_back({rest, p0, pairs, b->tile_floats, ntkey, exec});
     hit = (int)b->graphs.size() - 1;
   }
   CK(cudaGraphLaunch(b->graphs[hit].exec, b->stream));
@@ -2473,6 +2504,20 @@ int ehc_gnn_train_step(ehc_gnn *g, ehc_ctx *hc, double kappa, const double *Y_de
   CK(cudaStreamSynchronize(c.stream));
   if (grad_host) std::memcpy(grad_host, g->host, sizeof(float) * kGnnParams);
   if (loss_host) *loss_host = (float)g->host_loss[0];
+  return EHC_OK;
+}
+
+int ehc_batch_tuning(ehc_batch *b, int32_t *tile_threads, int32_t *grid_quarters) {
+  if (!b || !tile_threads || !grid_quarters) return EHC_E_INVAL;
+  *tile_threads = b->tile_nt;
+  *grid_quarters = b->tile_nt ? b->tile_q : 0;
+  return EHC_OK;
+}
+
+int ehc_tuning(ehc_ctx *h, int32_t *tile_threads, int32_t *grid_quarters) {
+  if (!h || !tile_threads || !grid_quarters) return EHC_E_INVAL;
+  *tile_threads = h->c.tile_nt;
+  *grid_quarters = h->c.tile_nt ? h->c.tile_q : 0;
   return EHC_OK;
 }
 

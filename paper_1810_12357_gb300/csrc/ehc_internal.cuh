@@ -391,6 +391,8 @@ struct Ctx {
   int32_t tile_grid[2] = {0, 0};  // resident CTAs of the row-tile kernel (9 / 16 index words)
   int32_t tile_grid128[2] = {0, 0};  // the same for its 128-thread form
   int32_t tile_nt = 0;           // threads owning atoms chosen by the tuner (0: not tuned yet, 256)
+  int32_t tile_q = 4;            // persistent grid of the row-tile kernel in quarters of the resident CTAs
+  int32_t tile_q_fixed = 0;      // ehc_params.tile_grid_quarters (0: tuned with the width, or 4)
   int32_t tile_nt_fixed = 0;     // ehc_params.tile_threads (0: tuned)
   int32_t num_sms = 0;
   RepArgs *reps = nullptr;       // device table of the row-tile kernel (this system only)

@@ -68,20 +68,61 @@ def test_batch_replica_matches_oracle():
 
 @pytest.mark.parametrize("batched", [False, True])
 def test_tile_widths_and_tuner_give_identical_results(batched):
-    # the 128- and 256-thread forms of the row-tile kernel, and the tuner's
-    # choice between them, change only the schedule: results are bit-identical
+    # the 128- and 256-thread forms of the row-tile kernel, its persistent grid's
+    # share of the resident CTAs, and the tuner's choice among them change only the
+    # schedule: results are bit-identical
     systems = I.batch_replicas(4, 9, n_min=8000, n_max=40000)
     res = []
-    for tt in (256, 128, 0):
-        p = dict(I.params_track(), tile_threads=tt)
+    for tt, q in ((256, 0), (128, 0), (256, 2), (128, 3), (0, 0)):
+        p = dict(I.params_track(), tile_threads=tt, tile_grid_quarters=q)
         if batched:
             b, _, _ = _run_batch(systems, p, 2, 20)
             res.append(b.get_te().cpu().numpy())
+            if tt == 0:
+                assert b.tuning()[0] in (128, 256) and b.tuning()[1] in (2, 3, 4)
         else:
             g, _, _ = run_gpu(systems[0], p, 2, 20)
             res.append(g.get_te().cpu().numpy())
-    assert np.array_equal(res[0], res[1])
-    assert np.array_equal(res[0], res[2])
+            if tt == 0:
+                assert g.tuning()[0] in (128, 256) and g.tuning()[1] in (2, 3, 4)
+    for r in res[1:]:
+        assert np.array_equal(res[0], r)
+
+
+def test_tuning_cache_keeps_the_choice(tmp_path, monkeypatch):
+    # the tuner's choice is stored per GPU and shape and reused by the next context
+    import json
+    import torch
+    from paper_1810_12357_gb300 import Ehc, EhcBatch
+    monkeypatch.setenv("EHC_TUNE_CACHE", str(tmp_path / "tuning.json"))
+    s = I.track_system(16, 3, r0=10.0)
+    p = I.params_track()
+    x = torch.as_tensor(s.x, device="cuda")
+    v = torch.as_tensor(s.v, device="cuda")
+    g = Ehc(p, s, tune_cache=True)
+    g.set_te(s.Te)
+    g.build_neighbors(x, v)
+    g.substep(20)
+    choice = g.tuning()
+    d = json.load(open(tmp_path / "tuning.json"))
+    assert list(d.values())[0] and choice[0] in (128, 256)
+    # a new context of the same shape starts with it (no tuning: a short call already shows it)
+    h = Ehc(p, s, tune_cache=True)
+    h.set_te(s.Te)
+    h.build_neighbors(x, v)
+    h.substep(2)
+    assert h.tuning() == choice
+    # the batch form
+    systems = I.batch_replicas(3, 8, n_min=8000, n_max=30000)
+    b, _, _ = _run_batch(systems, p, 1, 20)
+    bb = EhcBatch(p, systems, tune_cache=True)
+    bb.set_te(torch.as_tensor(np.concatenate([q.Te for q in systems]), device="cuda"))
+    bb.build_neighbors(torch.as_tensor(np.concatenate([q.x for q in systems]), device="cuda").contiguous(),
+                       torch.as_tensor(np.concatenate([q.v for q in systems]), device="cuda").contiguous())
+    bb.substep(20)
+    cb = bb.tuning()
+    b2 = EhcBatch(p, systems, tune_cache=True)
+    assert b2.params.get("tile_threads") == cb[0] and b2.params.get("tile_grid_quarters") == cb[1]
 
 
 def test_fullsize_batch_sampled_replicas():
