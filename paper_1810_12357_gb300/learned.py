@@ -210,24 +210,25 @@ def corrector_windows(system, params: dict, coeffs, n_windows: int, n_w: int = 1
     return g, pairs, w.kappa()
 
 
-def train_track_corrector(coeffs, n_w: int = 100, stages: int = 15, order: int = 2, steps: int = 1500,
-                          lr: float = 1e-3, n_windows: int = 12, seed: int = 0):
+def train_track_corrector(coeffs, n_w: int = 100, stages: int = 15, order: int = 2, steps: int = 800,
+                          lr: float = 3e-4, n_windows: int = 24, seed: int = 0, cells: int = 60, skip: int = 1):
     """The corrector network of the learned window on the swift-ion track: Adam on
-    (window result, plain substeps) pairs of six 256,000-atom track and hot-spot
-    cells (40^3 cells), taken on the states a run of the window with the given
-    stage coefficients visits from the initial profile on (n_windows windows).
-    Returns the parameters and a record with the held-out error of a seventh
-    cell's windows with and without the corrector."""
+    (window result, plain substeps) pairs of six track and hot-spot cells
+    (`cells`^3 FCC cells, 864,000 atoms at 60), taken on the states a run of the
+    window with the given stage coefficients visits after the first `skip`
+    windows (n_windows windows).  Returns the parameters and a record with the
+    held-out error of a seventh cell's windows with and without the corrector."""
     import time
     import numpy as np
     from . import EhcGnn
     from . import inputs as I
     p = I.params_track()
     t0 = time.perf_counter()
-    cells = [I.track_system(40, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
-    cells += [I.hot_spot_system(40, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
+    nc = cells
+    cells = [I.track_system(nc, 100 + k, peak=8000.0 + 6000.0 * k, r0=12.0 + 4.0 * k) for k in range(3)]
+    cells += [I.hot_spot_system(nc, 150 + k, peak=6000.0 + 6000.0 * k, sigma=8.0 + 3.0 * k, disp_sigma=0.0)
               for k in range(3)]
-    data = [corrector_windows(c, p, coeffs, n_windows, n_w, stages, order, skip=0) for c in cells]
+    data = [corrector_windows(c, p, coeffs, n_windows, n_w, stages, order, skip=skip) for c in cells]
     net = EhcGnn(data[0][0], params=corrector_init(seed))
     hist = []
     for k in range(steps):
@@ -238,12 +239,13 @@ def train_track_corrector(coeffs, n_w: int = 100, stages: int = 15, order: int =
     t_train = time.perf_counter() - t0
     del data
     # held-out: the windows of a seventh track, without and with the corrector
-    hc, hp, hk = corrector_windows(I.track_system(40, 199, peak=20000.0, r0=20.0), p, coeffs, n_windows, n_w,
-                                   stages, order, skip=0)
+    hc, hp, hk = corrector_windows(I.track_system(nc, 199, peak=20000.0, r0=20.0), p, coeffs, n_windows, n_w,
+                                   stages, order, skip=skip)
     hnet = EhcGnn(hc, params=params)
     err_u = [float(((y - t).abs() / t).max()) for y, t in hp]
     err_t = [float(((hnet.apply(y, hk) - t).abs() / t).max()) for y, t in hp]
-    info = {"train_s": t_train, "train_cells": len(cells), "windows_per_cell": n_windows, "train_steps": steps,
+    info = {"train_s": t_train, "train_cells": f"{len(cells)} cells of {nc}^3 FCC cells", "windows_per_cell": n_windows,
+            "train_steps": steps,
             "loss_first": hist[0], "loss_last": hist[-1],
             "heldout_256k_window_max_rel_err": {"window": err_u, "window_and_corrector": err_t}}
     return params, info
