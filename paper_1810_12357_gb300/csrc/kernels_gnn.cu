@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) gnn_feat_kernel(int32_t n, const int32_t 
 // weights of the node MLP in shared memory: W1 [64][16], W2 [64][64], W3 [16][64]
 // (row-major out x in, so that a B fragment's k pair is one 32-bit word), and for
 // the backward the transposes W2T [64][64], W3T [64][16]
-struct MlpSmem {
+struct __align__(16) MlpSmem {
   __nv_bfloat16 W1[kH * kF], W2[kH * kH], W3[kU * kH];
   float b1[kH], b2[kH];
 };
@@ -139,6 +139,18 @@ struct MlpSmemT {
 };
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// B fragments of two n-tiles (nt, nt + 1) and one k-chunk of a weight matrix held
+// row-major [N][K] in shared memory, by one ldmatrix.x4: lane l addresses row
+// (nt + l / 16) * 8 + l % 8 at column kc * 16 + ((l / 8) % 2) * 8; the four 8 x 8
+// matrices come back as b0, b1 of tile nt and b0, b1 of tile nt + 1
+__device__ __forceinline__ void ldsm_b2(const __nv_bfloat16 *W, int K, int nt, int kc, int lane, uint32_t b[4]) {
+  const __nv_bfloat16 *p = W + ((nt + (lane >> 4)) * 8 + (lane & 7)) * K + kc * 16 + ((lane >> 3) & 1) * 8;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+               : "r"(a));
+}
 
 // A fragment of a 16 x 16 slab of a row-major [n][16] BF16 array (rows past n are 0)
 __device__ __forceinline__ void load_a16(const __nv_bfloat16 *__restrict__ x, int64_t row0, int32_t n, int g, int t,
@@ -168,32 +180,38 @@ __device__ __forceinline__ void relu_to_a(const float c[8][4], const float *bias
 // c2 = h1 W2^T, h2 = relu(c2 + b2), c3 = h2 W3^T
 __device__ __forceinline__ void mlp_slab(const MlpSmem &w, const uint32_t ain[4], int g, int t, float c1[8][4],
                                          uint32_t h1[4][4], float c2[8][4], uint32_t h2[4][4], float c3[2][4]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t b[4];
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
+  for (int nt = 0; nt < 8; nt += 2) {
     c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.f;
-    const __nv_bfloat16 *wr = w.W1 + (nt * 8 + g) * kF + 2 * t;
-    mma16816(c1[nt], ain, ld32(wr), ld32(wr + 8));
+    c1[nt + 1][0] = c1[nt + 1][1] = c1[nt + 1][2] = c1[nt + 1][3] = 0.f;
+    ldsm_b2(w.W1, kF, nt, 0, lane, b);
+    mma16816(c1[nt], ain, b[0], b[1]);
+    mma16816(c1[nt + 1], ain, b[2], b[3]);
   }
   relu_to_a(c1, w.b1, t, h1);
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
+  for (int nt = 0; nt < 8; nt += 2) {
     c2[nt][0] = c2[nt][1] = c2[nt][2] = c2[nt][3] = 0.f;
+    c2[nt + 1][0] = c2[nt + 1][1] = c2[nt + 1][2] = c2[nt + 1][3] = 0.f;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
-      const __nv_bfloat16 *wr = w.W2 + (nt * 8 + g) * kH + 16 * kc + 2 * t;
-      mma16816(c2[nt], h1[kc], ld32(wr), ld32(wr + 8));
+      ldsm_b2(w.W2, kH, nt, kc, lane, b);
+      mma16816(c2[nt], h1[kc], b[0], b[1]);
+      mma16816(c2[nt + 1], h1[kc], b[2], b[3]);
     }
   }
   relu_to_a(c2, w.b2, t, h2);
+  c3[0][0] = c3[0][1] = c3[0][2] = c3[0][3] = 0.f;
+  c3[1][0] = c3[1][1] = c3[1][2] = c3[1][3] = 0.f;
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    c3[nt][0] = c3[nt][1] = c3[nt][2] = c3[nt][3] = 0.f;
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      const __nv_bfloat16 *wr = w.W3 + (nt * 8 + g) * kH + 16 * kc + 2 * t;
-      mma16816(c3[nt], h2[kc], ld32(wr), ld32(wr + 8));
-    }
+  for (int kc = 0; kc < 4; ++kc) {
+    ldsm_b2(w.W3, kH, 0, kc, lane, b);
+    mma16816(c3[0], h2[kc], b[0], b[1]);
+    mma16816(c3[1], h2[kc], b[2], b[3]);
   }
+  (void)g;
 }
 
 __device__ __forceinline__ void load_mlp_weights(const __nv_bfloat16 *__restrict__ wb, MlpSmem &w) {
@@ -207,7 +225,7 @@ __device__ __forceinline__ void load_mlp_weights(const __nv_bfloat16 *__restrict
 }
 
 // node MLP: u [n][16] BF16 from the layer-1 inputs; grid-stride over 16-node slabs
-__global__ void __launch_bounds__(kMlpThreads) gnn_mlp_kernel(int32_t n, const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(kMlpThreads, 8) gnn_mlp_kernel(int32_t n, const __nv_bfloat16 *__restrict__ in,
                                                               const __nv_bfloat16 *__restrict__ wb,
                                                               __nv_bfloat16 *__restrict__ u) {
   __shared__ MlpSmem w;
@@ -625,7 +643,9 @@ GeoArgs geo_of(const Ctx &c) {
 
 }  // namespace
 
-int gnn_mlp_blocks(Ctx &c) { return 4 * (c.num_sms > 0 ? c.num_sms : 152); }
+// resident blocks: 8 per SM for the forward (64 registers, 128 threads), whose
+// MMA chains need the warps to hide their latency
+int gnn_mlp_blocks(Ctx &c) { return 8 * (c.num_sms > 0 ? c.num_sms : 152); }
 int gnn_edge_blocks(int64_t n) { return (int)nblk(n > 0 ? n : 1, kEdgeThreads); }
 int gnn_loss_blocks(int64_t n) { return (int)nblk(n > 0 ? n : 1, 256); }
 size_t gnn_bwd_smem() { return sizeof(BwdStage); }
