@@ -730,6 +730,33 @@ def train_window(args):
                                       args.train_steps, args.loss_power)
 
 
+def run_corrector(args):
+    """Three corrected windows (100 substeps, 15 stages, the corrector with its
+    initial weights and w4 = 0.01) on the track of --cells cells: the corrector's
+    kernels in a form a profiler can capture; prints the mean window time."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc, EhcCheb, EhcGnn, learned
+    s, p = workload(args.cells)
+    g = Ehc(p, s)
+    g.set_te(s.Te)
+    g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
+    w = EhcCheb(g, args.window, args.stages, args.damping, order=args.order)
+    prm = learned.corrector_init(0)
+    prm[-16:] = 0.01
+    net = EhcGnn(g, params=prm)
+    w.set_corrector(net)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(3):
+        w.step(100.0, k * DT_MD)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": f"corrected windows on the {s.n:,}-atom track", "windows": 3,
+                      "ms_per_window": e0.elapsed_time(e1) / 3}), flush=True)
+
+
 def run_learned(args):
     """Learned propagator on the 4,000,000-atom track.  Default: the window with
     trained stage coefficients (train_window) and the corrector network trained on
@@ -843,7 +870,7 @@ def main():
     ap.add_argument("--ref-substeps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="track", choices=["track", "batch", "learned", "window"])
+    ap.add_argument("--workload", default="track", choices=["track", "batch", "learned", "window", "corrector"])
     ap.add_argument("--window", type=int, default=100)
     ap.add_argument("--stages", type=int, default=None)
     ap.add_argument("--model", default="window", choices=["window", "nn"])
@@ -895,6 +922,8 @@ def main():
         run_learned(args)
     elif args.workload == "window":
         run_window(args)
+    elif args.workload == "corrector":
+        run_corrector(args)
     else:
         run_gpu(args)
 
