@@ -53,6 +53,106 @@ __device__ __forceinline__ uint32_t checked_index(uint32_t i, uint32_t bound, in
   return i;
 }
 
+// ---- exact FP64 conversions on the integer pipes ----
+// The FP64 pipe of this GPU retires about two lanes per SM clock, so the
+// once-per-MD-step kernels keep it for the arithmetic the ledger needs and do
+// scalings by powers of two, roundings to integers, fixed-point sums and range
+// tests on the bit patterns.
+
+// round-half-even(x * 2^s) as int64, bit for bit what cvt.rni.s64.f64 gives for
+// x * 2^s (an exact scaling): NaN -> 0, out of range -> saturated.
+__device__ __forceinline__ long long rint_scaled(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long frac = b & 0xfffffffffffffull;
+  const bool neg = (b >> 63) != 0;
+  if (e == 0x7ff && frac != 0) return 0;                        // NaN
+  if (e == 0) return 0;                                          // zero, subnormal (|x 2^s| < 1/2 for s < 1000)
+  const unsigned long long m = frac | (1ull << 52);
+  const int sh = e - 1075 + s;                                   // x 2^s = m 2^sh
+  if (sh > 10) return neg ? (long long)0x8000000000000000ull : 0x7fffffffffffffffll;   // |x 2^s| >= 2^63
+  unsigned long long r;
+  if (sh >= 0) {
+    r = m << sh;
+  } else if (sh < -54) {
+    r = 0;                                                       // |x 2^s| < 1/2
+  } else {
+    const int k = -sh;                                           // 1..54
+    const unsigned long long q = m >> k;
+    const unsigned long long rem = m & ((1ull << k) - 1ull);
+    const unsigned long long half = 1ull << (k - 1);
+    r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  }
+  return neg ? -(long long)r : (long long)r;
+}
+
+// |x| < 2^k (false for NaN and infinities)
+__device__ __forceinline__ bool abs_below_pow2(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (int)((b >> 52) & 0x7ffu) < 1023 + k;
+}
+
+// (hi, lo) += floor(x * 2^96), a double 0 <= x < 2^31 on the 2^-96 fixed-point
+// grid (exact: the bits below 2^-96 are dropped), as a 128-bit integer in two
+// words; the usual exponents (2^-43 <= x < 2^11) take the branch-free path
+__device__ __forceinline__ void fix96_add(unsigned long long &hi, unsigned long long &lo, double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = e - 1075 + 96;                                  // x 2^96 = m 2^sh
+  const bool pos = !(b >> 63);
+  unsigned long long l = 0, h = 0;
+  if (pos && sh >= 0 && sh < 64) {
+    l = m << sh;
+    h = (m >> 1) >> (63 - sh);                                   // m >> (64 - sh), 0 for sh = 0
+  } else if (pos && e != 0) {
+    if (sh >= 64) h = m << (sh - 64 < 10 ? sh - 64 : 10);        // outside the stated range: clamped
+    else if (sh > -53) l = m >> (-sh);
+  }
+  const unsigned long long nl = lo + l;
+  hi += h + (nl < l ? 1ull : 0ull);
+  lo = nl;
+}
+
+// the double nearest to a signed 128-bit integer (ties to even)
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long hi0 = (unsigned long long)(u >> 64);
+  const int lz = hi0 ? __clzll((long long)hi0) : 64 + __clzll((long long)(unsigned long long)u);
+  u <<= lz;                                                      // top bit at 127
+  const unsigned long long top = (unsigned long long)(u >> 64);
+  const unsigned long long low = (unsigned long long)u;
+  unsigned long long m = top >> 11;                              // 53 bits
+  const unsigned long long rb = (top >> 10) & 1ull;              // first dropped bit
+  const bool sticky = ((top & 0x3ffull) | low) != 0;
+  if (rb && (sticky || (m & 1ull))) ++m;
+  int ex = 127 - lz;                                             // value = 1.f * 2^ex
+  if (m >> 53) {
+    m >>= 1;
+    ++ex;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                  (m & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+// exact float -> double by bit assembly on the integer pipes (zero and
+// subnormal inputs give a signed zero); keeps the FP64 pipe for the ledger
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sg = u & 0x80000000u;
+  const uint32_t ex = (u >> 23) & 0xffu;
+  const uint32_t man = u & 0x7fffffu;
+  uint32_t hi = sg, lo = 0u;
+  if (ex != 0u) {
+    hi = sg | ((ex + 896u) << 20) | (man >> 3);
+    lo = man << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Sorted velocity of one atom: components on a fixed-point grid of 2^-48 A/fs
 // (|v| < 256 A/fs, so sums over an atom and up to 64 neighbours stay exact in
 // int64) and |v|^2 in FP64.
@@ -65,10 +165,13 @@ struct __align__(32) VelQ {
 };
 
 // exact reciprocals of 1..kMaxWidth+1 and of (3/2) k_B times the same counts,
-// for the lattice temperature (one rounding instead of a division per atom)
+// for the lattice temperature (one rounding instead of a division per atom);
+// coefT[k]: the one-type factor from the 2^-96 fixed-point sums of an atom with
+// k neighbours to its temperature
 struct RecipTab {
   double inv_n[kMaxWidth + 2];
   double inv_dof[kMaxWidth + 2];
+  double coefT[kMaxWidth + 2];
 };
 
 struct MassTable {

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "ehc_internal.cuh"
 
 namespace ehc {
@@ -18,24 +20,41 @@ namespace {
 constexpr double kKB = 8.617333262e-5;          // eV/K (CODATA 2018)
 constexpr double kMVV = 1.66053906660e-27 * 1.0e10 / 1.602176634e-19;  // amu (A/fs)^2 -> eV
 
+// floor(v nc / L) for 0 <= v < L < 2^31 and nc < 2^20 without a 64-bit
+// division: a single-precision estimate (relative error below 2^-21, so within
+// one of the quotient) corrected by exact 64-bit products
+__device__ __forceinline__ int32_t cell_of(int64_t v, int32_t nc, int64_t L, float ncL) {
+  const int64_t num = v * (int64_t)nc;
+  int64_t c = (int64_t)__float2int_rz(__int2float_rz((int32_t)v) * ncL);
+  if (c * L > num) --c;
+  else if ((c + 1) * L <= num) ++c;
+  return (int32_t)c;
+}
+
 __global__ void bin_kernel(const double *__restrict__ x, int64_t n, Grid g, int4 *__restrict__ q,
                            int32_t *__restrict__ count, int32_t *__restrict__ err) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (o >= n) return;
-  int32_t qc[3];
-  int64_t cc[3];
+  int32_t qc[3], cc[3];
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
-    long long v = __double2ll_rn(x[3 * o + k] * 1048576.0);
+    // round-half-even(x 2^20), the oracle's llrint, on the integer pipes
+    long long v = rint_scaled(x[3 * o + k], 20);
     const long long L = g.Lq[k];
     if (g.per[k]) {
-      v %= L;
+      // one period either side without a division; further out, the floored modulo
       if (v < 0) v += L;
+      else if (v >= L) v -= L;
+      if (v < 0 || v >= L) {
+        v %= L;
+        if (v < 0) v += L;
+      }
     } else if (v < 0 || v >= L) {
       atomicOr(err, ERR_BOUNDS);
       v = v < 0 ? 0 : L - 1;
     }
     qc[k] = (int32_t)v;
-    int64_t c = (v * (int64_t)g.nc[k]) / L;
+    const int32_t c = cell_of(v, g.nc[k], L, (float)g.nc[k] / (float)L);
     cc[k] = c >= g.nc[k] ? g.nc[k] - 1 : c;
   }
   int32_t cell = (int32_t)(cc[0] + g.nc[0] * (cc[1] + (int64_t)g.nc[1] * cc[2]));
@@ -151,11 +170,12 @@ __global__ void sort_cells_kernel(const int32_t *__restrict__ start, int64_t nce
 __device__ __forceinline__ void gather_velocity(int64_t s, int64_t o, const double *__restrict__ v,
                                                 VelQ *__restrict__ v_s, int32_t *__restrict__ err) {
   const double vx = v[3 * o + 0], vy = v[3 * o + 1], vz = v[3 * o + 2];
-  if (!(fabs(vx) < kVelMax && fabs(vy) < kVelMax && fabs(vz) < kVelMax)) atomicOr(err, ERR_SPEED);
+  // |v| < 256 = 2^8 per component, tested on the exponent bits
+  if (!(abs_below_pow2(vx, 8) && abs_below_pow2(vy, 8) && abs_below_pow2(vz, 8))) atomicOr(err, ERR_SPEED);
   VelQ vq;
-  vq.x = __double2ll_rn(vx * kVelScale);
-  vq.y = __double2ll_rn(vy * kVelScale);
-  vq.z = __double2ll_rn(vz * kVelScale);
+  vq.x = rint_scaled(vx, 48);   // round-half-even(v 2^48)
+  vq.y = rint_scaled(vy, 48);
+  vq.z = rint_scaled(vz, 48);
   vq.w = vx * vx + vy * vy + vz * vz;
   v_s[s] = vq;
 }
@@ -217,17 +237,15 @@ __device__ __forceinline__ uint32_t wrap_shift(int32_t dcell, int64_t L) {
   return dcell > 1 ? (uint32_t)(-L) : (dcell < -1 ? (uint32_t)L : 0u);
 }
 
+// The search of one atom s (the visit order and outputs described above);
+// returns its neighbour count (before truncation to W), the 4-word aligned end
+// of its row tile and the length of its own row.
 template <bool FAST, bool WEIGHTS>
-__global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
-                                                       const int32_t *__restrict__ start,
-                                                       const int32_t *__restrict__ row_nbr, int32_t W,
-                                                       int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
-                                                       int64_t ps, uint8_t *__restrict__ cnt,
-                                                       int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
-                                                       int32_t *__restrict__ maxrow, int32_t *__restrict__ err,
-                                                       float *__restrict__ wgt, float wn) {
-  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+__device__ __forceinline__ int3 search_atom(int32_t s, int32_t n, const Grid &g, const int4 *__restrict__ q_s,
+                                            const int32_t *__restrict__ start, const int32_t *__restrict__ row_nbr,
+                                            int32_t W, int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
+                                            int64_t ps, uint8_t *__restrict__ cnt, int32_t *__restrict__ err,
+                                            float *__restrict__ wgt, float wn) {
   const int4 qi = q_s[s];
   const int32_t ncx = g.nc[0];
   const int32_t cx = qi.w % ncx;
@@ -359,11 +377,26 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
   const int32_t mm = m < W ? m : W;
   for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
   cnt[s] = (uint8_t)mm;
+  return make_int3(m, (tend + 3) & ~3, own_len);
+}
+
+template <bool FAST, bool WEIGHTS>
+__global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
+                                                       const int32_t *__restrict__ start,
+                                                       const int32_t *__restrict__ row_nbr, int32_t W,
+                                                       int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
+                                                       int64_t ps, uint8_t *__restrict__ cnt,
+                                                       int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
+                                                       int32_t *__restrict__ maxrow, int32_t *__restrict__ err,
+                                                       float *__restrict__ wgt, float wn) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int3 r = search_atom<FAST, WEIGHTS>(s, n, g, q_s, start, row_nbr, W, nbr, pidx16, ps, cnt, err, wgt, wn);
   // one atomic per warp for each of the three maxima
   const unsigned act = __activemask();
-  const int32_t wm = __reduce_max_sync(act, m);
-  const int32_t ws = __reduce_max_sync(act, (tend + 3) & ~3);
-  const int32_t wr = __reduce_max_sync(act, own_len);
+  const int32_t wm = __reduce_max_sync(act, r.x);
+  const int32_t ws = __reduce_max_sync(act, r.y);
+  const int32_t wr = __reduce_max_sync(act, r.z);
   if ((threadIdx.x & 31) == (__ffs(act) - 1)) {
     atomicMax(maxcnt, wm);
     atomicMax(maxstaged, ws);
@@ -572,19 +605,53 @@ __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, 
   if (s >= n) return;
   const int c = cnt[s];
   const VelQ vi = v_s[s];
-  double ke;
+  double T;
   if (ONE_TYPE) {
+    // n sum_S |v|^2 - |sum_S v|^2 = n sum_S |v - v_com|^2 exactly on the 2^-96 grid:
+    // int64 momentum sums of the fixed-point velocities and a 128-bit fixed-point
+    // sum of the FP64 |v|^2 (no cancellation, no FP64 pipe in the loop)
     long long qx = vi.x, qy = vi.y, qz = vi.z;
-    double sw = vi.w;
-    for (int k = 0; k < c; ++k) {
+    unsigned long long Wh = 0, Wl = 0;
+    fix96_add(Wh, Wl, vi.w);
+    // neighbours four at a time, software-pipelined: the next four indices are
+    // loaded while this four's velocities are summed (two gathers in flight)
+    int k = 0;
+    int32_t tn[4];
+    if (c >= 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tn[u] = (int32_t)checked_index(nbr[(int64_t)u * n + s], (uint32_t)n, err);
+    }
+    for (; k + 4 <= c; k += 4) {
+      VelQ vj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vj[u] = v_s[tn[u]];
+      if (k + 8 <= c) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          tn[u] = (int32_t)checked_index(nbr[(int64_t)(k + 4 + u) * n + s], (uint32_t)n, err);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        qx += vj[u].x;
+        qy += vj[u].y;
+        qz += vj[u].z;
+        fix96_add(Wh, Wl, vj[u].w);
+      }
+    }
+    for (; k < c; ++k) {
       const VelQ vj = v_s[checked_index(nbr[(int64_t)k * n + s], (uint32_t)n, err)];
       qx += vj.x;
       qy += vj.y;
       qz += vj.z;
-      sw += vj.w;
+      fix96_add(Wh, Wl, vj.w);
     }
-    const double sx = (double)qx * kVelUnit, sy = (double)qy * kVelUnit, sz = (double)qz * kVelUnit;
-    ke = 0.5 * mt.m[0] * (sw - (sx * sx + sy * sy + sz * sz) * rt.inv_n[c + 1]) * kMVV;
+    const unsigned __int128 W = ((unsigned __int128)Wh << 64) | Wl;
+    const __int128 S2 = (__int128)qx * qx + (__int128)qy * qy + (__int128)qz * qz;
+    // D >= 0 up to the roundings of |v|^2 and of the grid (a set moving as one): not below 0
+    __int128 D = (__int128)(c + 1) * (__int128)W - S2;
+    if (D < 0) D = 0;
+    // T = D 2^-96 (m / 2) kMVV / (c + 1) / ((3/2) k_B dof): one coefficient per count
+    T = i128_to_double(D) * rt.coefT[c];
   } else {
     const double mi = mt.m[type_s[s]];
     double M = mi;
@@ -602,10 +669,10 @@ __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, 
       pz += mj * ((double)vj.z * kVelUnit);
       W += mj * vj.w;
     }
-    ke = 0.5 * (W - (px * px + py * py + pz * pz) / M) * kMVV;
+    const double ke = fmax(0.5 * (W - (px * px + py * py + pz * pz) / M) * kMVV, 0.0);
+    const int dof = (dof_mode == 1) ? c : c + 1;
+    T = dof > 0 ? ke * rt.inv_dof[dof] : 0.0;
   }
-  const int dof = (dof_mode == 1) ? c : c + 1;
-  double T = dof > 0 ? ke * rt.inv_dof[dof] : 0.0;
   const double Ks = 0.5 * mt.m[ONE_TYPE ? 0 : type_s[s]] * vi.w * kMVV;
   const bool chi = Ks >= eps_ke;
   if (!chi) T = -1.0;
@@ -825,12 +892,11 @@ cudaError_t launch_neighbors(Ctx &c) {
     c.cand_valid = true;
     return cudaGetLastError();
   }
-  // the weighted forms store each pair's rate weight beside its index
-  auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
-                    : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);
   // pair weights S2 / (n_shell r^2) with r^2 = d2 2^-40 A^2 (d2 on the 2^-20 A grid),
   // in single precision (as stored): d2 rounded to float, one correctly rounded division
   const double wn = c.p.rate_shell_n > 0 ? c.p.zb2_A2 * 1099511627776.0 / (double)c.p.rate_shell_n : 0.0;
+  auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
+                    : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);
   kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
                                              reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt,
                                              c.maxstaged, c.maxrow, c.err, c.wgt, (float)wn);
@@ -843,6 +909,10 @@ cudaError_t launch_lattice_temperature(Ctx &c) {
   for (int k = 0; k < kMaxWidth + 2; ++k) {
     rt.inv_n[k] = k > 0 ? 1.0 / (double)k : 0.0;
     rt.inv_dof[k] = k > 0 ? 1.0 / (1.5 * kKB * (double)k) : 0.0;
+    // one atom type: T = D 2^-96 (m / 2) kMVV / (k + 1) / ((3/2) k_B dof) for k neighbours
+    const int dof = (c.p.dof_mode == 1) ? k : k + 1;
+    rt.coefT[k] = dof > 0 ? std::ldexp(0.5 * c.mt.m[0] * kMVV, -96) / (double)(k + 1) / (1.5 * kKB * (double)dof)
+                          : 0.0;
   }
   if (c.mt.n_types == 1)
     lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,

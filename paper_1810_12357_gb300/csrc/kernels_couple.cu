@@ -59,69 +59,118 @@ __device__ __forceinline__ void gauss3(uint64_t id, uint64_t step, uint64_t seed
   g[2] = r2 * cospif(2.0f * u3);
 }
 
-// s = sqrt(target / Kw) without an FP64 division or square root: Newton's
-// method for f(y) = Kw y^2 - target, started from the single-precision root and
-// stepped twice in FP64 with a single-precision 1 / f'(y0) (each step squares
-// the relative error, 1e-7 -> 1e-14 -> rounding).  Outside the normal
-// single-precision range the plain FP64 expression is used.
-__device__ __forceinline__ double scale_root(double target, double Kw) {
-  if (!(target > 1.0e-30 && target < 1.0e30 && Kw > 1.0e-30 && Kw < 1.0e30)) return sqrt(target / Kw);
-  const float kf = (float)Kw;
-  const float yf = sqrtf((float)target / kf);
-  const double c = (double)(0.5f / (kf * yf));   // ~ 1 / (2 Kw y)
-  double y = (double)yf;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) y = fma(fma(-Kw * y, y, target), c, y);
-  return y;
+// ---- float-float arithmetic (unevaluated sums h + l of two floats, about 47
+// significant bits) for the hand-over: the FP64 pipe retires about two lanes
+// per SM clock, the single-precision pipe 128, and the hand-over needs about
+// 1e-14 relative accuracy of the kinetic energies (Dekker, Numer. Math. 18,
+// 1971; Knuth's TwoSum) ----
+struct FF {
+  float h, l;
+};
+
+// h = x truncated to 24 significant bits (bit assembly), l = the remaining 29
+// bits rounded to a float (one integer-to-float conversion times a power of
+// two): x - (h + l) <= 2^-48 |x| for |x| >= 2^-74 (below, l = 0: an error under
+// 2^-98; below 2^-100, h = 0 too).  The caller keeps |x| < 2^100.
+__device__ __forceinline__ FF d2ff(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hw = (uint32_t)(b >> 32);
+  const uint32_t sg = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  FF r;
+  r.h = __uint_as_float(sg);
+  r.l = r.h;
+  if (e < -100) return r;
+  r.h = __uint_as_float(sg | ((uint32_t)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | ((uint32_t)(b >> 29) & 7u));
+  const uint32_t t = (uint32_t)b & 0x1fffffffu;        // x - h = t 2^(e - 52)
+  if (e >= -74) r.l = __fmul_rn(__uint2float_rn(t), __uint_as_float(sg | ((uint32_t)(e - 52 + 127) << 23)));
+  return r;
 }
 
-__global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ type_s,
-                              MassTable mt, double kv, double kv0, const double *__restrict__ Tl,
-                              double *__restrict__ A,
-                              double *__restrict__ T, double *__restrict__ v, double *__restrict__ dKE,
-                              int mode, int frozen, uint64_t seed, uint64_t md_step, double e1, double inv_VC,
-                              unsigned long long *__restrict__ n_stopped, double thc, double inv_Tmax,
-                              double stop_f, double stop_ecut) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const double Ai = A[s];
-  A[s] = 0.0;
-  if (!(Tl[s] >= 0.0)) {
-    dKE[s] = 0.0;
-    return;
-  }
-  if (frozen) {
-    dKE[s] = Ai;
-    return;
-  }
-  const int64_t o = perm[s];
-  const int ty = type_s[s];
-  const double m = mt.m[ty];
-  double *vi = v + 3 * o;
+// h + l rounded to the nearest double (both exact in FP64: one addition)
+__device__ __forceinline__ double ff2d(FF a) { return __dadd_rn(f2d(a.h), f2d(a.l)); }
+
+__device__ __forceinline__ FF ff_fast(float s, float e) {   // |s| >= |e|
+  FF r;
+  r.h = __fadd_rn(s, e);
+  r.l = __fsub_rn(e, __fsub_rn(r.h, s));
+  return r;
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return ff_fast(s, e);
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return ff_fast(p, e);
+}
+__device__ __forceinline__ FF ff_prod(float a, float b) {   // exact
+  const float p = __fmul_rn(a, b);
+  return FF{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_sqr3(FF x, FF y, FF z) {   // x^2 + y^2 + z^2
+  return ff_add(ff_add(ff_mul(x, x), ff_mul(y, y)), ff_mul(z, z));
+}
+
+// sqrt(t / K) for t, K in [1e-30, 1e30]: a single-precision root y0 and one
+// Newton step on K y^2 = t with the residual t - K y0^2 in float-float
+// (relative error ~1e-13)
+__device__ __forceinline__ FF ff_scale_root(FF t, FF K) {
+  // y0 to a few units of 2^-24 (approximate quotient and reciprocal square root):
+  // the Newton step squares that to below 1e-13
+  const float y0 = rsqrtf(__fdividef(K.h, t.h));
+  const FF r = ff_add(t, ff_neg(ff_mul(K, ff_prod(y0, y0))));
+  return ff_fast(y0, __fdividef(r.h, __fmul_rn(2.0f * K.h, y0)));
+}
+
+// per atom type: (m / 2) kMVV as a float pair, and the Langevin variance
+// factor k_B (1 - e^{-2 g dt}) / (m kMVV) in single precision
+struct CoupleTab {
+  FF hk[kMaxTypes];
+  float cv[kMaxTypes];
+  float ecut_f;   // the stopping cut in single precision (to find the atoms near it)
+};
+
+// The hand-over of one atom in FP64, step for step as the oracle: for atoms that
+// electronic stopping may slow, that may have to be stopped (K + A near or below
+// zero), or whose kinetic energies leave the float-float range.  Out of line:
+// such atoms are rare and only their warps pay for it.
+struct CoupleF64 {
+  double cv_num;   // k_B (1 - e^{-2 g dt}): the Langevin variance is cv_num T / (m kMVV)
+  double e1;       // e^{-g dt}
+  double stop_f;   // 1 - e^{-2 beta dt_md} (0: no stopping)
+  double stop_ecut;
+};
+
+__device__ __noinline__ void couple_atom_fp64(int64_t s, double m, double *vi, double Ai, float g0, float g1, float g2,
+                                              int mode, const CoupleF64 &cp, double *T, double *dKE,
+                                              unsigned long long *n_stopped, double inv_VC, double thc,
+                                              double inv_Tmax) {
   const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
   const double K0 = 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2) * kMVV;
   double target = K0 + Ai;
-  // electronic stopping above the cut: the friction's loss over the MD step
-  const bool slowed = stop_f > 0.0 && K0 > stop_ecut;
-  if (slowed) target -= K0 * stop_f;
+  const bool slowed = cp.stop_f > 0.0 && K0 > cp.stop_ecut;
+  if (slowed) target -= K0 * cp.stop_f;
   if (target < 0.0) {
     target = 0.0;
     atomicAdd(n_stopped, 1ull);
   }
   double w0 = v0, w1 = v1, w2 = v2;
   if (mode == 1) {
-    float g[3];
-    gauss3((uint64_t)o, md_step, seed, g);
     // noise amplitude in single precision (it multiplies a single-precision normal)
-    // variance factor k_B (1 - e^{-2 g dt}) / (m kMVV) = kv / (m kMVV), for type 0 from the host
-    const double cv = (ty == 0) ? kv0 : kv / (m * kMVV);
-    const float sig = sqrtf((float)(cv * T[s]));
-    w0 = v0 * e1 + (double)(sig * g[0]);
-    w1 = v1 * e1 + (double)(sig * g[1]);
-    w2 = v2 * e1 + (double)(sig * g[2]);
+    const float sig = sqrtf((float)(cp.cv_num / (m * kMVV) * T[s]));
+    w0 = v0 * cp.e1 + (double)(sig * g0);
+    w1 = v1 * cp.e1 + (double)(sig * g1);
+    w2 = v2 * cp.e1 + (double)(sig * g2);
   }
   const double Kw = 0.5 * m * (w0 * w0 + w1 * w1 + w2 * w2) * kMVV;
-  const double sc = (Kw > 0.0 && target > 0.0) ? scale_root(target, Kw) : 0.0;
+  const double sc = (Kw > 0.0 && target > 0.0) ? sqrt(target / Kw) : 0.0;
   vi[0] = w0 * sc;
   vi[1] = w1 * sc;
   vi[2] = w2 * sc;
@@ -134,6 +183,72 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
     if (inv_Tmax > 0.0) T[s] = ue_inv(ue_of(T[s] * inv_Tmax, thc) + (Ai - d) * inv_VC, thc) / inv_Tmax;
     else T[s] += (Ai - d) * inv_VC;
   }
+}
+
+__device__ __forceinline__ bool ff_in_range(FF a) { return a.h > 1.0e-30f && a.h < 1.0e30f; }
+
+// Every other atom in float-float: its kinetic energy K0 and the target K0 + A_i,
+// the trial velocity w (Langevin: friction and noise), K_w and the scale
+// sqrt(target / K_w) to about 1e-14, the velocity rounded once to FP64; the
+// lattice's change is A_i exactly.
+__global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ type_s,
+                              MassTable mt, CoupleTab ct, FF e1, CoupleF64 cp, const double *__restrict__ Tl,
+                              double *__restrict__ A, double *__restrict__ T, double *__restrict__ v,
+                              double *__restrict__ dKE, int mode, int frozen, uint64_t seed, uint64_t md_step,
+                              double inv_VC, unsigned long long *__restrict__ n_stopped, double thc,
+                              double inv_Tmax) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  // every load that does not depend on another is issued first: two waits on
+  // memory per atom (these, then the velocity at the permuted index)
+  const double Ai = A[s];
+  const long long tlb = __double_as_longlong(Tl[s]);
+  const int64_t o = perm[s];
+  const int ty = type_s[s];
+  const double Ts = mode == 1 ? T[s] : 0.0;
+  A[s] = 0.0;
+  // chi: T_l >= 0 (-0 included, NaN excluded), on the bit pattern
+  if (!((tlb >= 0 && tlb <= 0x7ff0000000000000ll) || tlb == (long long)0x8000000000000000ull)) {
+    dKE[s] = 0.0;
+    return;
+  }
+  if (frozen) {
+    dKE[s] = Ai;
+    return;
+  }
+  double *vi = v + 3 * o;
+  const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
+  float g[3] = {0.0f, 0.0f, 0.0f};
+  if (mode == 1) gauss3((uint64_t)o, md_step, seed, g);
+  const FF hk = ct.hk[ty];
+  const FF x0 = d2ff(v0), x1 = d2ff(v1), x2 = d2ff(v2);
+  const FF K0 = ff_mul(hk, ff_sqr3(x0, x1, x2));
+  const FF Af = d2ff(Ai);
+  const FF target = ff_add(K0, Af);
+  // stopping may apply (K0 near or above the cut), or K0 + A_i may be near or below zero
+  bool exact = (cp.stop_f > 0.0 && K0.h > 0.999f * ct.ecut_f) ||
+               !(target.h > 1.0e-10f * (K0.h + fabsf(Af.h))) || !ff_in_range(K0);
+  FF w0 = x0, w1 = x1, w2 = x2, Kw = K0;
+  if (!exact && mode == 1) {
+    // noise amplitude in single precision (it multiplies a single-precision normal)
+    const float sig = sqrtf(__fmul_rn(ct.cv[ty], d2ff(Ts).h));
+    w0 = ff_add(ff_mul(x0, e1), ff_prod(sig, g[0]));
+    w1 = ff_add(ff_mul(x1, e1), ff_prod(sig, g[1]));
+    w2 = ff_add(ff_mul(x2, e1), ff_prod(sig, g[2]));
+    Kw = ff_mul(hk, ff_sqr3(w0, w1, w2));
+  }
+  // (and the ratio target / K_w within 1e+-15 for the single-precision seed of the root)
+  exact = exact || !(ff_in_range(Kw) && ff_in_range(target) && target.h < 1.0e15f * Kw.h &&
+                     Kw.h < 1.0e15f * target.h);
+  if (exact) {
+    couple_atom_fp64(s, mt.m[ty], vi, Ai, g[0], g[1], g[2], mode, cp, T, dKE, n_stopped, inv_VC, thc, inv_Tmax);
+    return;
+  }
+  const FF sc = ff_scale_root(target, Kw);
+  vi[0] = ff2d(ff_mul(w0, sc));
+  vi[1] = ff2d(ff_mul(w1, sc));
+  vi[2] = ff2d(ff_mul(w2, sc));
+  dKE[s] = Ai;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -174,6 +289,19 @@ __device__ __forceinline__ bool ge_bits(double y, double L) {   // y >= L for y 
   return __double_as_longlong(y) >= __double_as_longlong(L);
 }
 
+// a coordinate outside [0, L) (or -0) back into the box: one period at most
+// per step, else the floored modulo.  Out of line: few atoms cross a face in a
+// step, and its FP64 additions then cost only the warps that have one.
+__device__ __noinline__ double wrap_coordinate(double y, double L) {
+  if (neg_bits(y) && y != 0.0) y += L;
+  else if (ge_bits(y, L)) y -= L;
+  if ((neg_bits(y) && y != 0.0) || (!neg_bits(y) && __double_as_longlong(y) > __double_as_longlong(L))) {
+    y = fmod(y, L);
+    if (y < 0.0) y += L;
+  }
+  return y;
+}
+
 // one thread per coordinate (coalesced over the flat [N][3] arrays)
 __global__ void drift_kernel(int64_t n3, double *__restrict__ x, const double *__restrict__ v, double dt,
                              double L0, double L1, double L2, int p0, int p1, int p2) {
@@ -187,13 +315,10 @@ __global__ void drift_kernel(int64_t n3, double *__restrict__ x, const double *_
   // no contraction: x + v dt rounds the product and the sum separately
   double y = __dadd_rn(x[j], __dmul_rn(v[j], dt));
   if (per) {
-    // one period at most per step; the same result as a floored modulo
-    if (neg_bits(y) && y != 0.0) y += L;
-    else if (ge_bits(y, L)) y -= L;
-    if ((neg_bits(y) && y != 0.0) || (!neg_bits(y) && __double_as_longlong(y) > __double_as_longlong(L))) {
-      y = fmod(y, L);
-      if (y < 0.0) y += L;
-    }
+    // inside [0, L) or -0, decided on the bit patterns: nothing to do
+    const long long b = __double_as_longlong(y);
+    const bool inside = (b >= 0 && b < __double_as_longlong(L)) || b == (long long)0x8000000000000000ull;
+    if (!inside) y = wrap_coordinate(y, L);
   }
   x[j] = y;
 }
@@ -214,20 +339,38 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 // scal[8] accumulates E_lat; scal[9] holds the stopped-atom counter (as u64 bits)
+static FF host_ff(double x) {   // nearest float and the nearest float to the rest
+  FF r;
+  r.h = (float)x;
+  r.l = (float)(x - (double)r.h);
+  return r;
+}
+
 cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
   const double gdt = c.gammaL * dt_md;
   const double e1 = std::exp(-gdt);
   const double one_m_e2 = 1.0 - std::exp(-2.0 * gdt);
   const double kv = kKB * one_m_e2;
-  const double kv0 = kv / (c.mt.m[0] * kMVV);
+  CoupleTab ct;
+  for (int t = 0; t < kMaxTypes; ++t) {
+    const double m = t < c.mt.n_types ? c.mt.m[t] : c.mt.m[0];
+    ct.hk[t] = host_ff(0.5 * m * kMVV);
+    // variance factor k_B (1 - e^{-2 g dt}) / (m kMVV)
+    ct.cv[t] = (float)(kv / (m * kMVV));
+  }
+  ct.ecut_f = (float)c.p.stop_ecut_eV;
+  CoupleF64 cp;
+  cp.cv_num = kv;
+  cp.e1 = e1;
+  cp.stop_f = c.p.stop_beta_per_fs > 0 ? -std::expm1(-2.0 * c.p.stop_beta_per_fs * dt_md) : 0.0;
+  cp.stop_ecut = c.p.stop_ecut_eV;
   if (c.n > 0)
     couple_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(
-        c.n, c.perm, c.type_s, c.mt, kv, kv0, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode, c.p.frozen, c.p.seed,
-        (uint64_t)c.md_step, e1,
+        c.n, c.perm, c.type_s, c.mt, ct, host_ff(e1), cp, c.Tl_d, c.A, c.T[c.tcur], v, c.dKE, c.p.couple_mode,
+        c.p.frozen, c.p.seed, (uint64_t)c.md_step,
         c.local ? kEVJ / (c.vatom * 1e-30 * c.p.gamma_Ce * c.p.Tmax_K * c.p.Tmax_K) : 1.0 / c.VC,
         reinterpret_cast<unsigned long long *>(c.scal + 9), c.local ? c.coef_host->thc : 0.0,
-        c.local ? 1.0 / c.p.Tmax_K : 0.0,
-        c.p.stop_beta_per_fs > 0 ? -std::expm1(-2.0 * c.p.stop_beta_per_fs * dt_md) : 0.0, c.p.stop_ecut_eV);
+        c.local ? 1.0 / c.p.Tmax_K : 0.0);
   sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
   sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
   return cudaGetLastError();

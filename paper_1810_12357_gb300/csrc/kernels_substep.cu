@@ -114,21 +114,6 @@ __device__ __forceinline__ void two_sum_acc(float &F, float &Fc, float t) {
   F = s;
 }
 
-// exact float -> double by bit assembly on the integer pipes (zero and
-// subnormal inputs give a signed zero); keeps the FP64 pipe for the ledger
-__device__ __forceinline__ double f2d(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t sg = u & 0x80000000u;
-  const uint32_t ex = (u >> 23) & 0xffu;
-  const uint32_t man = u & 0x7fffffu;
-  uint32_t hi = sg, lo = 0u;
-  if (ex != 0u) {
-    hi = sg | ((ex + 896u) << 20) | (man >> 3);
-    lo = man << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // (h, l) += x in float-float: TwoSum of h and x, then a fast renormalisation
 __device__ __forceinline__ void ff_add(float &h, float &l, float x) {
   const float s = h + x;
