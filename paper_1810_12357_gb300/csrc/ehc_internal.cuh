@@ -153,6 +153,24 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// x as an unevaluated float pair h + l on the integer pipes: h = x truncated to
+// 24 significant bits (bit assembly), l = the remaining 29 bits rounded to a
+// float (one integer-to-float conversion times a power of two), so that
+// |x - (h + l)| <= 2^-48 |x| for 2^-74 <= |x| < 2^127 (below, l = 0: an error
+// under 2^-98; below 2^-100, h = 0 too)
+__device__ __forceinline__ void split_pair(double x, float &h, float &l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hw = (uint32_t)(b >> 32);
+  const uint32_t sg = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  h = __uint_as_float(sg);
+  l = h;
+  if (e < -100) return;
+  h = __uint_as_float(sg | ((uint32_t)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | ((uint32_t)(b >> 29) & 7u));
+  const uint32_t t = (uint32_t)b & 0x1fffffffu;     // x - h = t 2^(e - 52)
+  if (e >= -74) l = __fmul_rn(__uint2float_rn(t), __uint_as_float(sg | ((uint32_t)(e - 52 + 127) << 23)));
+}
+
 // Sorted velocity of one atom: components on a fixed-point grid of 2^-48 A/fs
 // (|v| < 256 A/fs, so sums over an atom and up to 64 neighbours stay exact in
 // int64) and |v|^2 in FP64.

@@ -68,22 +68,10 @@ struct FF {
   float h, l;
 };
 
-// h = x truncated to 24 significant bits (bit assembly), l = the remaining 29
-// bits rounded to a float (one integer-to-float conversion times a power of
-// two): x - (h + l) <= 2^-48 |x| for |x| >= 2^-74 (below, l = 0: an error under
-// 2^-98; below 2^-100, h = 0 too).  The caller keeps |x| < 2^100.
+// x as a float pair (split_pair)
 __device__ __forceinline__ FF d2ff(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t hw = (uint32_t)(b >> 32);
-  const uint32_t sg = hw & 0x80000000u;
-  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
   FF r;
-  r.h = __uint_as_float(sg);
-  r.l = r.h;
-  if (e < -100) return r;
-  r.h = __uint_as_float(sg | ((uint32_t)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | ((uint32_t)(b >> 29) & 7u));
-  const uint32_t t = (uint32_t)b & 0x1fffffffu;        // x - h = t 2^(e - 52)
-  if (e >= -74) r.l = __fmul_rn(__uint2float_rn(t), __uint_as_float(sg | ((uint32_t)(e - 52 + 127) << 23)));
+  split_pair(x, r.h, r.l);
   return r;
 }
 

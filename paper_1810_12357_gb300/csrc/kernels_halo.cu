@@ -48,9 +48,10 @@ __global__ void set_at_kernel(int64_t m, int32_t n, const int32_t *__restrict__ 
   T[s] = v;
   const double x = (v - Tref) * invTmax;
   if (mode == 1) {
-    const float h = (float)x;
+    float h, l;
+    split_pair(x, h, l);   // as the split of a substep call
     mir[s] = h;
-    lo[s] = (float)(x - (double)h);
+    lo[s] = l;
   } else if (mode == 2) {
     const double w = ue_of(v * invTmax, thc) - u_ref;
     const float h = (float)w;

@@ -82,6 +82,21 @@ __device__ __forceinline__ float pair_acc(float F, float di, float dj, float th,
   return fmaf(D, fmaf(-P, S, C), F);
 }
 
+// the pair term alone, for the compensated sums: as pair_acc(0, ...), except
+// that B = 1 - P is applied as one fused operation, Delta - Delta P with a single
+// rounding (still exactly the negative of the partner's term: Delta changes
+// sign, P does not, and round-to-nearest is odd)
+template <int TIER>
+__device__ __forceinline__ float pair_flux(float di, float dj, float th, float ai, float m2ai) {
+  if (TIER == 3) {
+    const float D = dj - di;
+    const float b = th + dj;
+    const float P = fmaf(m2ai, b, ai + b);
+    return fmaf(-D, P, D);
+  }
+  return pair_acc<TIER>(0.0f, di, dj, th, ai, m2ai);
+}
+
 // fl(f(theta_i, theta_j)) = fl(Delta B) with the series order chosen from this
 // pair's own Delta^2 (the same thresholds and truncation bounds as the row tiles'
 // per-tile tiers): both atoms of a pair compute Delta^2 and P bit for bit alike,
@@ -93,7 +108,7 @@ __device__ __forceinline__ float pair_term(float di, float dj, float th, float a
   const float P = fmaf(m2ai, b, ai + b);
   float B;
   if (x < 1.44e-8f) {                                             // |Delta| < 1.2e-4
-    B = 1.0f - P;
+    return fmaf(-D, P, D);                                        // Delta (1 - P), one rounding
   } else if (x < 4.0e-4f) {                                       // |Delta| < 0.02
     B = fmaf(-P, fmaf(x, 1.6666667e-01f, 1.0f), fmaf(x, 0.5f, 1.0f));
   } else if (x < 1.44e-2f) {                                      // |Delta| < 0.12
@@ -436,8 +451,8 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
 #pragma unroll
     for (int m = 0; m < PP; ++m)
       if (PP != 16 || m < ra.P) {
-        two_sum_acc(F, Fc, pair_acc<TIER>(0.0f, di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai));
-        two_sum_acc(F, Fc, pair_acc<TIER>(0.0f, di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai));
+        two_sum_acc(F, Fc, pair_flux<TIER>(di, tile[checked_index(pv[m] & 0xffffu, tlen, ra.err)], th, ai, m2ai));
+        two_sum_acc(F, Fc, pair_flux<TIER>(di, tile[checked_index(pv[m] >> 16, tlen, ra.err)], th, ai, m2ai));
       }
   }
   if (STAGE) {
@@ -922,15 +937,15 @@ __global__ void merge_local_kernel(int64_t n, const float *__restrict__ uhi, con
   T[s] = Tmax * ue_inv(u_ref + ((double)uhi[s] + (double)lo[s]), thc);
 }
 
-// T (FP64) -> hi + lo of delta = (T - Tref) / Tmax
+// T (FP64) -> hi + lo of delta = (T - Tref) / Tmax (split_pair: the conversions on the integer pipes)
 __global__ void split_kernel(int64_t n, const double *__restrict__ T, double Tref, double invTmax,
                              float *__restrict__ hi, float *__restrict__ lo) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const double x = (T[s] - Tref) * invTmax;
-  const float h = (float)x;
+  float h, l;
+  split_pair((T[s] - Tref) * invTmax, h, l);
   hi[s] = h;
-  lo[s] = (float)(x - (double)h);
+  lo[s] = l;
 }
 
 // hi + lo -> T (FP64)
@@ -938,7 +953,7 @@ __global__ void merge_kernel(int64_t n, const float *__restrict__ hi, const floa
                              double Tmax, double *__restrict__ T) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  T[s] = Tref + Tmax * ((double)hi[s] + (double)lo[s]);
+  T[s] = Tref + Tmax * (f2d(hi[s]) + f2d(lo[s]));   // the pair's sum is exact in FP64
 }
 
 template <bool LASER>
