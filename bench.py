@@ -120,13 +120,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# neighbour-search skin of the track runs [A]: the list is still recomputed every MD
+# step by the exact test on the current positions (the same list as the full cell
+# search), from candidates within r_c + skin that are rebuilt when an atom has
+# moved more than skin / 2
+SKIN_A = 0.3
+
+
 def workload(cells: int, tile_threads: int = 0, skin=None):
     from paper_1810_12357_gb300 import inputs as I
     s = I.track_system(cells, seed=2)
-    p = dict(I.params_track(), tile_threads=tile_threads)
-    if skin is not None:
-        p["skin"] = skin
+    p = dict(I.params_track(), tile_threads=tile_threads, skin=SKIN_A if skin is None else skin)
     return s, p
+
+
+def neighbour_text(skin: float) -> str:
+    if skin > 0:
+        return (f"recomputed every MD step (exact integer test), from candidates within r_c + {skin:g} A "
+                f"rebuilt when an atom moved more than {skin / 2:g} A")
+    return "recomputed every MD step by the full cell search"
 
 
 def config_dict(cells: int, n: int, extra=None, n_sub: int = N_SUB):
@@ -136,7 +148,8 @@ def config_dict(cells: int, n: int, extra=None, n_sub: int = N_SUB):
          "n_atoms": n, "substeps_per_step": n_sub, "dt_sub_fs": DT_SUB, "dt_md_fs": DT_MD,
          "pair_flux": "fp32, compensated sums", "substep_state": "float pair (~48 bits)",
          "T_between_calls_exchange_and_ledger": "fp64",
-         "l2": "inputs larger than L2 (~0.9 GB working set), no flush"}
+         "l2": "inputs larger than L2 (~0.9 GB working set), no flush",
+         "neighbour_list": neighbour_text(SKIN_A)}
     if extra:
         d.update(extra)
     return d
@@ -373,6 +386,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": config_dict(args.cells, n, dict({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                                   "neighbour_list": neighbour_text(
+                                                       SKIN_A if args.skin is None else args.skin),
                                                    "path": "plain"},
                                                   **({"border": "fixed 300 K electron shell %g A thick, %d atoms"
                                                       % (args.border, args.border_atoms)}
@@ -896,7 +911,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="leave the learned window out of the default line")
     ap.add_argument("--skin", type=float, default=None,
-                    help="neighbour-search skin [A] (default: the workload's)")
+                    help="neighbour-search skin [A] (default: %g; 0 searches every cell every MD step)" % SKIN_A)
     ap.add_argument("--no-batch", action="store_true", help="leave the batched replicas out of the default line")
     ap.add_argument("--no-corrector", action="store_true",
                     help="learned window without the corrector network")

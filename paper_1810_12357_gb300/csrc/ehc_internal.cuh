@@ -499,7 +499,7 @@ struct Ctx {
   int32_t *maxstaged = nullptr;  // largest staged row-tile size (err + 2)
   int32_t *maxrow = nullptr;     // longest row (err + 3); err + 4: the candidate list's rebuild flag
   // neighbour candidates with a skin (ehc_params.skin_A > 0): atoms within r_c + skin
-  // at the last candidate build, original ids [kCandWidth][N] by original id, their
+  // at the last candidate build, original ids in visit order [N][kCandWidth] by original id, their
   // counts, and the quantised positions of that build
   int64_t skin_q = 0;            // skin on the 2^-20 A grid (0: full search every build)
   bool cand_valid = false;

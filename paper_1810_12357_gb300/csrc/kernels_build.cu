@@ -406,7 +406,9 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
 
 // ---- neighbour lists from a candidate list with a skin (cells >= r_c + skin) ----
 // The candidates of an atom are the atoms within r_v = r_c + skin of it when the
-// candidate list was built (original ids, slot-major [Wc][N] by original id).
+// candidate list was built: original ids in the visit order of that build, atom-
+// major [N][Wc] by original id (one atom's list is contiguous, so a build reads
+// about as many DRAM sectors as it uses).
 // While no atom has moved more than skin / 2 on the grid since then, every pair
 // within r_c is among them, and the list of the MD step is the candidates that
 // pass the exact integer test with the current positions: the same set, and
@@ -435,8 +437,8 @@ __global__ void skin_check_kernel(int32_t n, Grid g, const int4 *__restrict__ q,
 }
 
 // Candidate list (only when *flag is set): the full cell search with r_v, one
-// thread per sorted atom, candidates as original ids by original id; the
-// positions of the build go to q_ref.  FAST grids only (>= 3 cells per periodic
+// thread per sorted atom, candidates as original ids in visit order, atom-major
+// by original id; the positions of the build go to q_ref.  FAST grids only (>= 3 cells per periodic
 // axis, cells at least r_v wide).
 __global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv2, const int4 *__restrict__ q_s,
                                                    const int32_t *__restrict__ perm, const int32_t *__restrict__ start,
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv
         const uint64_t d2 = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
                             (uint64_t)((int64_t)dz * dz);
         if (d2 <= (uint64_t)rv2 && t != s) {
-          if (m < Wc) cand[(int64_t)m * n + o] = perm[t];
+          if (m < Wc) cand[(int64_t)o * Wc + m] = perm[t];
           ++m;
         }
       }
@@ -484,13 +486,90 @@ __global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv
 
 // The list of the MD step from the candidates: the same outputs as
 // neighbor_kernel<true, false> (nbr, pidx, cnt, maxima), in its visit order (row,
-// cell run, sorted index), from the candidates that pass the exact test.
-constexpr int kMaxHits = 32;
-__global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, const int4 *__restrict__ q_s,
+// cell run, sorted index).  The candidates are kept in the visit order of the
+// last build that sorted them, and the hits come out in that order unless a
+// candidate changed cell since; each hit's visit key (row place, cell run,
+// sorted index) is checked against the previous one as it is written.  An atom
+// whose keys do not rise sorts its candidate list by the current keys (an
+// insertion sort in local memory, rare: an atom that crosses a cell face
+// unsorts the lists of its ~20 candidates once), writes it back for the next
+// builds and writes its hits again in that order.  Every list is exactly the
+// full search's.
+constexpr int kFilterBatch = 4;   // candidates whose three dependent loads are in flight together
+
+// floor(x / d) for 0 <= x < 2^31 and d >= 1, with mg = floor(2^32 / d) (d > 1; any
+// value for d = 1): the high product is the quotient or one less
+__device__ __forceinline__ int32_t udiv_mg(int32_t x, int32_t d, uint32_t mg) {
+  if (d == 1) return x;
+  int32_t q = (int32_t)__umulhi((uint32_t)x, mg);
+  if (x - q * d >= d) ++q;
+  return q;
+}
+
+// a cell-index difference on a periodic axis of n cells as the offset in {-1, 0, 1}
+// of adjacent cells (anything else: outside)
+__device__ __forceinline__ int32_t wrap_off(int32_t d, int32_t n, int per) {
+  if (per) d = d > 1 ? d - n : (d < -1 ? d + n : d);
+  return d;
+}
+
+template <typename T>
+__device__ __forceinline__ T sel3(const T *v, int32_t d) {   // v[d + 1] for d in {-1, 0, 1}
+  return d < 0 ? v[0] : (d > 0 ? v[2] : v[1]);
+}
+
+// The atom's view of its 27 cells: per axis offset (-1, 0, 1) the image shift
+// minus its own coordinate, the x offset's cell run, and per row place the tile
+// base (row placement as neighbor_kernel)
+struct FilterView {
+  int32_t cx, cy, cz, dy_lo, dz_lo, nyc;
+  uint32_t sx[3], sy[3], sz[3];
+  int32_t run[3];
+  int32_t base[kRowNbr];
+};
+
+// the visit class 2 r + run of a candidate in cell cw (false: outside the 27 cells),
+// its shifts and tile base
+__device__ __forceinline__ bool classify(const FilterView &fv, const Grid &g, uint32_t mgx, uint32_t mgy,
+                                         int32_t cw, int &cls, uint32_t &ox, uint32_t &oy, uint32_t &oz,
+                                         int32_t &bs) {
+  const int32_t ncx = g.nc[0], ny = g.nc[1];
+  const int32_t R2 = udiv_mg(cw, ncx, mgx);
+  const int32_t cz = udiv_mg(R2, ny, mgy);
+  const int32_t dx = wrap_off(cw - R2 * ncx - fv.cx, ncx, g.per[0]);
+  const int32_t dy = wrap_off(R2 - cz * ny - fv.cy, ny, g.per[1]);
+  const int32_t dz = wrap_off(cz - fv.cz, g.nc[2], g.per[2]);
+  if ((uint32_t)(dx + 1) > 2u || (uint32_t)(dy + 1) > 2u || (uint32_t)(dz + 1) > 2u) return false;
+  const int r = (dz - fv.dz_lo) * fv.nyc + (dy - fv.dy_lo);
+  ox = sel3(fv.sx, dx);
+  oy = sel3(fv.sy, dy);
+  oz = sel3(fv.sz, dz);
+  int32_t b = 0;
+#pragma unroll
+  for (int q = 0; q < kRowNbr; ++q) b = (q == r) ? fv.base[q] : b;
+  bs = b;
+  cls = 2 * r + sel3(fv.run, dx);
+  return true;
+}
+
+// The list of the MD step from the candidates: the same outputs as
+// neighbor_kernel<true, false> (nbr, pidx, cnt, maxima), in its visit order (row,
+// cell run, sorted index).  The candidates are kept in the visit order of the
+// last build that sorted them, and the hits come out in that order unless a
+// candidate changed cell since; each hit's visit key (row place, cell run,
+// sorted index) is checked against the previous one as it is written.  An atom
+// whose keys do not rise sorts its candidate list by the current keys (an
+// insertion sort in local memory, rare: an atom that crosses a cell face
+// unsorts the lists of its ~20 candidates once), writes it back for the next
+// builds and writes its hits again in that order.  Every list is exactly the
+// full search's.  A candidate's cell offsets come from its cell index by two
+// multiply-high divisions (mgx, mgy: floor(2^32 / cells) of the x and y axes).
+__global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t mgx, uint32_t mgy,
+                                                     const int4 *__restrict__ q_s,
                                                      const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
                                                      const int32_t *__restrict__ start,
-                                                     const int32_t *__restrict__ row_nbr, int32_t W,
-                                                     const int32_t *__restrict__ cand, const uint8_t *__restrict__ ccnt,
+                                                     const int32_t *__restrict__ row_nbr, int32_t W, int32_t Wc,
+                                                     int32_t *__restrict__ cand, uint8_t *__restrict__ ccnt,
                                                      int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
                                                      int64_t ps, uint8_t *__restrict__ cnt,
                                                      int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
@@ -499,84 +578,145 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, const in
   if (s >= n) return;
   const int4 qi = q_s[s];
   const int32_t o = perm[s];
-  const int32_t ncx = g.nc[0];
-  const int32_t cx = qi.w % ncx, R = qi.w / ncx;
-  // the tile placement of the neighbour rows (as neighbor_kernel)
-  int32_t rowid[kRowNbr], pre[kRowNbr], rs[kRowNbr];
-  int nr = 0;
+  const int c = ccnt[o];
+  int32_t *cl = cand + (int64_t)o * Wc;
+  const int32_t ncx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  FilterView fv;
+  const int32_t R = udiv_mg(qi.w, ncx, mgx);
+  fv.cx = qi.w - R * ncx;
+  fv.cz = udiv_mg(R, ny, mgy);
+  fv.cy = R - fv.cz * ny;
+  fv.dy_lo = (g.per[1] || fv.cy > 0) ? -1 : 0;
+  fv.dz_lo = (g.per[2] || fv.cz > 0) ? -1 : 0;
+  fv.nyc = ((g.per[1] || fv.cy < ny - 1) ? 1 : 0) - fv.dy_lo + 1;
+  // per offset: the wrapped neighbour cell's image shift (wrap_shift of the raw
+  // cell difference, as the full search), minus the atom's own coordinate
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    int32_t xw = fv.cx + d, yw = fv.cy + d, zw = fv.cz + d;
+    if (g.per[0]) xw = xw < 0 ? xw + ncx : (xw >= ncx ? xw - ncx : xw);
+    if (g.per[1]) yw = yw < 0 ? yw + ny : (yw >= ny ? yw - ny : yw);
+    if (g.per[2]) zw = zw < 0 ? zw + nz : (zw >= nz ? zw - nz : zw);
+    fv.sx[d + 1] = wrap_shift(xw - fv.cx, g.Lq[0]) - (uint32_t)qi.x;
+    fv.sy[d + 1] = wrap_shift(yw - fv.cy, g.Lq[1]) - (uint32_t)qi.y;
+    fv.sz[d + 1] = wrap_shift(zw - fv.cz, g.Lq[2]) - (uint32_t)qi.z;
+  }
+  // x runs in visit order (cx-1, cx, cx+1; a run restarts where the cells wrap)
+  fv.run[0] = 0;
+  fv.run[1] = (g.per[0] && fv.cx == 0) ? 1 : 0;
+  fv.run[2] = fv.run[1] + ((g.per[0] && fv.cx == ncx - 1) ? 1 : 0);
+  if (!g.per[0] && fv.cx == 0) {   // no cell at -1: the runs start at the own cell
+    fv.run[1] = 0;
+    fv.run[2] = 0;
+  }
   int32_t tend = 0, self_local = 0, own_len = 0;
+  bool rows_done = false;
+#pragma unroll
   for (int r = 0; r < kRowNbr; ++r) {
-    const int32_t R2 = row_nbr[(int64_t)R * kRowNbr + r];
-    if (R2 < 0) break;
+    fv.base[r] = 0;
+    const int32_t R2 = rows_done ? -1 : row_nbr[(int64_t)R * kRowNbr + r];
+    if (R2 < 0) {
+      rows_done = true;
+      continue;
+    }
     const int32_t a = start[(int64_t)R2 * ncx], b = start[(int64_t)R2 * ncx + ncx];
     const int32_t pr = ((tend + 3) & ~3) + (a & 3);
-    rowid[r] = R2;
-    pre[r] = pr;
-    rs[r] = a;
+    fv.base[r] = pr - a;
     if (R2 == R) {
       self_local = pr + (s - a);
       own_len = b - a;
     }
     tend = pr + (b - a);
-    nr = r + 1;
   }
-  // the cells of a neighbour row in visit order: cx-1, cx, cx+1 (deduplicated,
-  // wrapped); a run restarts where the visit order wraps to a lower cell
-  int32_t xo[3];
-  int nx = 0;
-  for (int d = -1; d <= 1; ++d) {
-    int32_t c = cx + d;
-    if (g.per[0]) c = c < 0 ? c + ncx : (c >= ncx ? c - ncx : c);
-    else if (c < 0 || c >= ncx) continue;
-    bool dup = false;
-    for (int q = 0; q < nx; ++q) dup |= xo[q] == c;
-    if (!dup) xo[nx++] = c;
-  }
-  const int32_t L0 = (int32_t)g.Lq[0], L1 = (int32_t)g.Lq[1], L2 = (int32_t)g.Lq[2];
-  const int64_t rc2 = g.rcq * g.rcq;
-  uint64_t key[kMaxHits];
+  const uint64_t rc2u = (uint64_t)(g.rcq * g.rcq);
   int m = 0;
-  const int c = ccnt[o];
-  for (int k = 0; k < c; ++k) {
-    const int32_t t = inv[cand[(int64_t)k * n + o]];
-    const int4 qj = q_s[t];
-    const int64_t dx = wrap_d(qj.x - qi.x, L0, L0 >> 1, g.per[0]);
-    const int64_t dy = wrap_d(qj.y - qi.y, L1, L1 >> 1, g.per[1]);
-    const int64_t dz = wrap_d(qj.z - qi.z, L2, L2 >> 1, g.per[2]);
-    if (dx * dx + dy * dy + dz * dz > rc2 || t == s) continue;
-    // visit rank of t: its row's place, then its cell's run
-    const int32_t R2t = qj.w / ncx, cxt = qj.w % ncx;
-    int r = 0;
-    while (r < nr && rowid[r] != R2t) ++r;
-    int run = 0;
-    for (int q = 0, rn = 0; q < nx; ++q) {
-      if (q > 0 && xo[q] != xo[q - 1] + 1) ++rn;
-      if (xo[q] == cxt) run = rn;
+  uint64_t last = 0;
+  bool ordered = true;
+  for (int k0 = 0; k0 < c; k0 += kFilterBatch) {
+    int32_t t[kFilterBatch];
+    int4 qj[kFilterBatch];
+#pragma unroll
+    for (int u = 0; u < kFilterBatch; ++u) t[u] = k0 + u < c ? cl[k0 + u] : -1;
+#pragma unroll
+    for (int u = 0; u < kFilterBatch; ++u) t[u] = t[u] >= 0 ? inv[t[u]] : -1;
+#pragma unroll
+    for (int u = 0; u < kFilterBatch; ++u) qj[u] = q_s[t[u] >= 0 ? t[u] : s];
+#pragma unroll
+    for (int u = 0; u < kFilterBatch; ++u) {
+      if (t[u] < 0 || t[u] == s) continue;
+      int cls;
+      uint32_t ox, oy, oz;
+      int32_t bs;
+      if (!classify(fv, g, mgx, mgy, qj[u].w, cls, ox, oy, oz, bs)) {
+        ordered = false;   // a candidate left the 27 cells: dropped at the re-sort
+        continue;
+      }
+      const int32_t dx = (int32_t)((uint32_t)qj[u].x + ox);
+      const int32_t dy = (int32_t)((uint32_t)qj[u].y + oy);
+      const int32_t dz = (int32_t)((uint32_t)qj[u].z + oz);
+      const uint64_t d2 =
+          (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) + (uint64_t)((int64_t)dz * dz);
+      if (d2 > rc2u) continue;
+      const uint64_t key = ((uint64_t)cls << 32) | (uint32_t)t[u];
+      if (m > 0 && key <= last) ordered = false;
+      last = key;
+      if (m < W) {
+        nbr[(int64_t)m * n + s] = t[u];
+        pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(bs + t[u]);
+      }
+      ++m;
     }
-    if (r >= nr) {   // not in a neighbour row: cannot happen with a valid candidate list
-      atomicOr(err, ERR_INDEX);
-      continue;
-    }
-    const uint64_t kk = ((uint64_t)(2 * r + run) << 32) | (uint32_t)t;
-    // insertion into the sorted hits
-    if (m < kMaxHits) {
-      int p = m;
+  }
+  if (!ordered) {
+    // sort the candidates by their current visit keys (those outside the 27 cells
+    // dropped), write the list back, and the hits again in that order
+    uint64_t key[kCandWidth];
+    int32_t id[kCandWidth];
+    int nc = 0;
+    for (int k = 0; k < c; ++k) {
+      const int32_t idk = cl[k];
+      const int32_t tk = inv[idk];
+      int cls;
+      uint32_t ox, oy, oz;
+      int32_t bs;
+      if (tk == s || !classify(fv, g, mgx, mgy, q_s[tk].w, cls, ox, oy, oz, bs)) continue;
+      const uint64_t kk = ((uint64_t)cls << 32) | (uint32_t)tk;
+      int p = nc;
       while (p > 0 && key[p - 1] > kk) {
         key[p] = key[p - 1];
+        id[p] = id[p - 1];
         --p;
       }
       key[p] = kk;
+      id[p] = idk;
+      ++nc;
     }
-    ++m;
+    m = 0;
+    for (int k = 0; k < nc; ++k) {
+      cl[k] = id[k];
+      const int32_t tk = (int32_t)(uint32_t)key[k];
+      const int4 qk = q_s[tk];
+      int cls;
+      uint32_t ox = 0u, oy = 0u, oz = 0u;
+      int32_t bs = 0;
+      classify(fv, g, mgx, mgy, qk.w, cls, ox, oy, oz, bs);
+      const int32_t dx = (int32_t)((uint32_t)qk.x + ox);
+      const int32_t dy = (int32_t)((uint32_t)qk.y + oy);
+      const int32_t dz = (int32_t)((uint32_t)qk.z + oz);
+      const uint64_t d2 =
+          (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) + (uint64_t)((int64_t)dz * dz);
+      if (d2 > rc2u) continue;
+      if (m < W) {
+        nbr[(int64_t)m * n + s] = tk;
+        pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(bs + tk);
+      }
+      ++m;
+    }
+    // candidates that left the 27 cells are gone from the list written back
+    if (nc != c) ccnt[o] = (uint8_t)nc;
   }
   if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
-  const int mm = m < W ? (m < kMaxHits ? m : kMaxHits) : W;
-  for (int k = 0; k < mm; ++k) {
-    const int32_t t = (int32_t)(uint32_t)key[k];
-    const int r = (int)(key[k] >> 33);
-    nbr[(int64_t)k * n + s] = t;
-    pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)(pre[r] + (t - rs[r]));
-  }
+  const int32_t mm = m < W ? m : W;
   for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
   cnt[s] = (uint8_t)mm;
   const unsigned act = __activemask();
@@ -886,8 +1026,11 @@ cudaError_t launch_neighbors(Ctx &c) {
     cand_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, rvq * rvq, c.q_s, c.perm, c.cell_start,
                                                       c.row_nbr, kCandWidth, c.cand, c.ccnt, c.q_orig, c.q_ref, flag,
                                                       c.err);
+    const uint32_t mgx = c.g.nc[0] > 1 ? (uint32_t)(4294967296ull / (uint64_t)c.g.nc[0]) : 0u;
+    const uint32_t mgy = c.g.nc[1] > 1 ? (uint32_t)(4294967296ull / (uint64_t)c.g.nc[1]) : 0u;
     filter_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>(
-        (int32_t)c.n, c.g, c.q_s, c.perm, c.inv_perm[c.cur_inv], c.cell_start, c.row_nbr, c.W, c.cand, c.ccnt,
+        (int32_t)c.n, c.g, mgx, mgy, c.q_s, c.perm, c.inv_perm[c.cur_inv], c.cell_start, c.row_nbr, c.W, kCandWidth, c.cand,
+        c.ccnt,
         c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt, c.maxstaged, c.maxrow, c.err);
     c.cand_valid = true;
     return cudaGetLastError();
