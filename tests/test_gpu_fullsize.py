@@ -236,3 +236,29 @@ def test_fullsize_laser_slab():
     # the source heated the surface layer within the 10 substeps
     assert Tg[s.depth < 3.0].mean() > s.Te[s.depth < 3.0].mean() + 1e-3
     print(f"full-size laser slab: list bit-exact, sampled T_e max rel err {worst:.3e}")
+
+
+def test_fullsize_skin_lists_equal_the_oracle():
+    """The bench's track configuration: lists from 0.3 A skin candidates on the
+    4,000,000-atom track.  Four MD steps of 0.5 fs free flight (some thousand
+    atoms cross a cell face in each, so atoms re-sort their candidate lists), then
+    one more build: the list equals the oracle's on the final positions, and the
+    temperatures equal those of the full search (negative skin: the same cells,
+    searched in full every build) bit for bit."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    import torch
+    from _drive import run_gpu
+    s = I.track_system(100, 2)
+    res = []
+    for skin in (0.3, -0.3):
+        p = dict(I.params_track(), skin=skin, dt_sub=5e-4)
+        g, x, v = run_gpu(s, p, 4, 10, dt_md=0.5)
+        res.append((g, x, v, g.get_te().cpu().numpy()))
+    assert np.array_equal(res[0][3], res[1][3])
+    g, x, v, _ = res[0]
+    g.build_neighbors(x, v)
+    rg, cg = g.export_neighbors(cap_per_atom=24)
+    ro, co = oracle.neighbors(x.cpu().numpy(), s.box, s.periodic, 4.0, cap_per_atom=24)
+    assert np.array_equal(rg, ro) and np.array_equal(cg, co)
