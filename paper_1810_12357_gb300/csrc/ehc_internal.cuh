@@ -153,6 +153,22 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// the float nearest to x (ties to even), bit for bit the conversion's result, on
+// the integer pipes for |x| in the normal single-precision range (2^-126 up to
+// the largest float) and below 2^-150 (a signed zero); subnormal results,
+// infinities and NaN take the conversion instruction
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  if (e < -150) return __uint_as_float((uint32_t)(b >> 32) & 0x80000000u);
+  if (e < -126 || e > 127) return (float)x;
+  const uint32_t hi = (uint32_t)((b >> 29) & 0x7fffffu);       // the 23 kept fraction bits
+  const uint32_t rem = (uint32_t)b & 0x1fffffffu;              // the 29 dropped ones
+  uint32_t r = ((uint32_t)(e + 127) << 23) | hi;
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (hi & 1u))) ? 1u : 0u;   // may carry into the exponent
+  return __uint_as_float(((uint32_t)(b >> 32) & 0x80000000u) | r);
+}
+
 // x as an unevaluated float pair h + l on the integer pipes: h = x truncated to
 // 24 significant bits (bit assembly), l = the remaining 29 bits rounded to a
 // float (one integer-to-float conversion times a power of two), so that

@@ -211,7 +211,7 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
   double T = T_old[src];
   T_new[s] = T;
   A_new[s] = A_old[src];
-  dmir0[s] = (float)((T - Tref) * invTmax);
+  dmir0[s] = d2f_rn((T - Tref) * invTmax);
   if (depth) {   // source weights only with a laser source (nothing reads them otherwise)
     const double w = exp(-depth[o] * inv_lp);
     srcw[s] = (float)w;
@@ -235,6 +235,21 @@ __global__ void gather_kernel(int64_t n, const int32_t *__restrict__ perm, const
 // minimum image separately, as in the oracle.
 __device__ __forceinline__ uint32_t wrap_shift(int32_t dcell, int64_t L) {
   return dcell > 1 ? (uint32_t)(-L) : (dcell < -1 ? (uint32_t)L : 0u);
+}
+
+// the unused slots mm..W-1 of atom s (rounded up to whole words) hold its own
+// tile index, whose pair term is exactly zero: whole 32-bit words after an odd
+// slot, coalesced over consecutive atoms
+__device__ __forceinline__ void pad_pidx(uint16_t *__restrict__ pidx16, int64_t ps, int32_t s, int32_t mm,
+                                         int32_t W, uint16_t self) {
+  int32_t k = mm;
+  if (k & 1) {
+    pidx16[((int64_t)(k >> 1) * ps + s) * 2 + 1] = self;
+    ++k;
+  }
+  uint32_t *pw = reinterpret_cast<uint32_t *>(pidx16);
+  const uint32_t two = (uint32_t)self | ((uint32_t)self << 16);
+  for (int32_t w = k >> 1; w < (W + 1) >> 1; ++w) pw[(int64_t)w * ps + s] = two;
 }
 
 // The search of one atom s (the visit order and outputs described above);
@@ -375,7 +390,7 @@ __device__ __forceinline__ int3 search_atom(int32_t s, int32_t n, const Grid &g,
   }
   if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
   const int32_t mm = m < W ? m : W;
-  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
+  pad_pidx(pidx16, ps, s, mm, W, (uint16_t)self_local);
   cnt[s] = (uint8_t)mm;
   return make_int3(m, (tend + 3) & ~3, own_len);
 }
@@ -402,6 +417,30 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
     atomicMax(maxstaged, ws);
     atomicMax(maxrow, wr);
   }
+}
+
+// The one-type lattice temperature of atom s from its sums over S = {s} + its c
+// neighbours (Sec. 2): int64 momentum sums q of the 2^-48 grid velocities and the
+// 128-bit fixed-point sum (Wh, Wl) of |v|^2 on the 2^-96 grid;
+// n sum |v|^2 - |sum v|^2 = n sum |v - v_com|^2 exactly, rounded once.
+__device__ __forceinline__ void lattice_finish(int64_t s, const VelQ &vi, long long qx, long long qy, long long qz,
+                                               unsigned long long Wh, unsigned long long Wl, int c,
+                                               double m0, const RecipTab &rt, double eps_ke, double Tref,
+                                               double *__restrict__ Tl_d, float *__restrict__ Tl_f,
+                                               float *__restrict__ uTl) {
+  const unsigned __int128 W = ((unsigned __int128)Wh << 64) | Wl;
+  const __int128 S2 = (__int128)qx * qx + (__int128)qy * qy + (__int128)qz * qz;
+  // D >= 0 up to the roundings of |v|^2 and of the grid (a set moving as one): not below 0
+  __int128 D = (__int128)(c + 1) * (__int128)W - S2;
+  if (D < 0) D = 0;
+  // T = D 2^-96 (m / 2) kMVV / (c + 1) / ((3/2) k_B dof): one coefficient per count
+  double T = i128_to_double(D) * rt.coefT[c];
+  const double Ks = 0.5 * m0 * vi.w * kMVV;
+  const bool chi = Ks >= eps_ke;
+  if (!chi) T = -1.0;
+  Tl_d[s] = T;
+  Tl_f[s] = d2f_rn(T);
+  uTl[s] = chi ? d2f_rn(Tref - T) : __int_as_float(0x7fc00000);
 }
 
 // ---- neighbour lists from a candidate list with a skin (cells >= r_c + skin) ----
@@ -495,7 +534,8 @@ __global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv
 // unsorts the lists of its ~20 candidates once), writes it back for the next
 // builds and writes its hits again in that order.  Every list is exactly the
 // full search's.
-constexpr int kFilterBatch = 4;   // candidates whose three dependent loads are in flight together
+constexpr int kFilterBatch = 4;     // candidates whose three dependent loads are in flight together
+constexpr int kFilterThreads = 128;
 
 // floor(x / d) for 0 <= x < 2^31 and d >= 1, with mg = floor(2^32 / d) (d > 1; any
 // value for d = 1): the high product is the quotient or one less
@@ -525,7 +565,7 @@ struct FilterView {
   int32_t cx, cy, cz, dy_lo, dz_lo, nyc;
   uint32_t sx[3], sy[3], sz[3];
   int32_t run[3];
-  int32_t base[kRowNbr];
+  const int32_t *base;   // the rows' tile bases in shared memory, row place r at base[r * kFilterThreads]
 };
 
 // the visit class 2 r + run of a candidate in cell cw (false: outside the 27 cells),
@@ -544,10 +584,7 @@ __device__ __forceinline__ bool classify(const FilterView &fv, const Grid &g, ui
   ox = sel3(fv.sx, dx);
   oy = sel3(fv.sy, dy);
   oz = sel3(fv.sz, dz);
-  int32_t b = 0;
-#pragma unroll
-  for (int q = 0; q < kRowNbr; ++q) b = (q == r) ? fv.base[q] : b;
-  bs = b;
+  bs = fv.base[r * kFilterThreads];
   cls = 2 * r + sel3(fv.run, dx);
   return true;
 }
@@ -564,7 +601,7 @@ __device__ __forceinline__ bool classify(const FilterView &fv, const Grid &g, ui
 // builds and writes its hits again in that order.  Every list is exactly the
 // full search's.  A candidate's cell offsets come from its cell index by two
 // multiply-high divisions (mgx, mgy: floor(2^32 / cells) of the x and y axes).
-__global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t mgx, uint32_t mgy,
+__global__ void __launch_bounds__(kFilterThreads) filter_kernel(int32_t n, Grid g, uint32_t mgx, uint32_t mgy,
                                                      const int4 *__restrict__ q_s,
                                                      const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
                                                      const int32_t *__restrict__ start,
@@ -574,6 +611,7 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t
                                                      int64_t ps, uint8_t *__restrict__ cnt,
                                                      int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
                                                      int32_t *__restrict__ maxrow, int32_t *__restrict__ err) {
+  __shared__ int32_t sbase[kRowNbr * kFilterThreads];   // each thread's column: its rows' tile bases
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 qi = q_s[s];
@@ -582,6 +620,8 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t
   int32_t *cl = cand + (int64_t)o * Wc;
   const int32_t ncx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
   FilterView fv;
+  int32_t *mybase = sbase + threadIdx.x;
+  fv.base = mybase;
   const int32_t R = udiv_mg(qi.w, ncx, mgx);
   fv.cx = qi.w - R * ncx;
   fv.cz = udiv_mg(R, ny, mgy);
@@ -613,7 +653,7 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t
   bool rows_done = false;
 #pragma unroll
   for (int r = 0; r < kRowNbr; ++r) {
-    fv.base[r] = 0;
+    mybase[r * kFilterThreads] = 0;
     const int32_t R2 = rows_done ? -1 : row_nbr[(int64_t)R * kRowNbr + r];
     if (R2 < 0) {
       rows_done = true;
@@ -621,7 +661,7 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t
     }
     const int32_t a = start[(int64_t)R2 * ncx], b = start[(int64_t)R2 * ncx + ncx];
     const int32_t pr = ((tend + 3) & ~3) + (a & 3);
-    fv.base[r] = pr - a;
+    mybase[r * kFilterThreads] = pr - a;
     if (R2 == R) {
       self_local = pr + (s - a);
       own_len = b - a;
@@ -717,7 +757,7 @@ __global__ void __launch_bounds__(128) filter_kernel(int32_t n, Grid g, uint32_t
   }
   if (m > W) atomicOr(err, ERR_NBR_OVERFLOW);
   const int32_t mm = m < W ? m : W;
-  for (int32_t k = mm; k < W; ++k) pidx16[((int64_t)(k >> 1) * ps + s) * 2 + (k & 1)] = (uint16_t)self_local;
+  pad_pidx(pidx16, ps, s, mm, W, (uint16_t)self_local);
   cnt[s] = (uint8_t)mm;
   const unsigned act = __activemask();
   const int32_t wm = __reduce_max_sync(act, m);
@@ -785,13 +825,8 @@ __global__ void lattice_temp_kernel(int64_t n, const int32_t *__restrict__ nbr, 
       qz += vj.z;
       fix96_add(Wh, Wl, vj.w);
     }
-    const unsigned __int128 W = ((unsigned __int128)Wh << 64) | Wl;
-    const __int128 S2 = (__int128)qx * qx + (__int128)qy * qy + (__int128)qz * qz;
-    // D >= 0 up to the roundings of |v|^2 and of the grid (a set moving as one): not below 0
-    __int128 D = (__int128)(c + 1) * (__int128)W - S2;
-    if (D < 0) D = 0;
-    // T = D 2^-96 (m / 2) kMVV / (c + 1) / ((3/2) k_B dof): one coefficient per count
-    T = i128_to_double(D) * rt.coefT[c];
+    lattice_finish(s, vi, qx, qy, qz, Wh, Wl, c, mt.m[0], rt, eps_ke, Tref, Tl_d, Tl_f, uTl);
+    return;
   } else {
     const double mi = mt.m[type_s[s]];
     double M = mi;
@@ -869,17 +904,37 @@ __global__ void globals_partial(int64_t n, const double *__restrict__ T, const V
                                 double cap, double *__restrict__ part) {
   __shared__ double sh[32];
   double sT = 0, mT = -1e300, sK = 0, sW = 0, mN = -1e300, sE = 0;
+  // the largest and smallest T on the integer pipes: bit patterns mapped to keys
+  // that order like the values (NaN skipped, as fmax does); one atom type: the sum
+  // of |v|^2, times m kMVV / 2 once per thread
+  const bool one = mt.n_types == 1;
+  long long kmax = (long long)0x8000000000000000ull, kmin = 0x7fffffffffffffffll;
+  bool any = false;
+  double sw = 0.0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     double t = T[s];
     sT += t;
-    mT = fmax(mT, t);
-    mN = fmax(mN, -t);
+    const long long b = __double_as_longlong(t);
+    if ((b & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) {
+      const long long k = b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+      kmax = k > kmax ? k : kmax;
+      kmin = k < kmin ? k : kmin;
+      any = true;
+    }
     if (gamma > 0.0) sE += ce_integral(t, gamma, cap);
-    if (v_s) sK += 0.5 * mt.m[type_s[s]] * v_s[s].w * kMVV;
+    if (v_s) {
+      if (one) sw += v_s[s].w;
+      else sK += 0.5 * mt.m[type_s[s]] * v_s[s].w * kMVV;
+    }
     if (srcw_d) sW += srcw_d[s];
     else if (srcw) sW += (double)srcw[s];
   }
+  if (any) {
+    mT = __longlong_as_double(kmax >= 0 ? kmax : (kmax ^ 0x7fffffffffffffffll));
+    mN = -__longlong_as_double(kmin >= 0 ? kmin : (kmin ^ 0x7fffffffffffffffll));
+  }
+  if (v_s && one) sK = 0.5 * mt.m[0] * sw * kMVV;
   double r0 = block_sum(sT, sh);
   double r1 = block_max(mT, sh);
   double r2 = block_sum(sK, sh);
@@ -965,6 +1020,20 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+// reciprocal tables of the lattice temperature
+static RecipTab recip_table(const Ctx &c) {
+  RecipTab rt;
+  for (int k = 0; k < kMaxWidth + 2; ++k) {
+    rt.inv_n[k] = k > 0 ? 1.0 / (double)k : 0.0;
+    rt.inv_dof[k] = k > 0 ? 1.0 / (1.5 * kKB * (double)k) : 0.0;
+    // one atom type: T = D 2^-96 (m / 2) kMVV / (k + 1) / ((3/2) k_B dof) for k neighbours
+    const int dof = (c.p.dof_mode == 1) ? k : k + 1;
+    rt.coefT[k] = dof > 0 ? std::ldexp(0.5 * c.mt.m[0] * kMVV, -96) / (double)(k + 1) / (1.5 * kKB * (double)dof)
+                          : 0.0;
+  }
+  return rt;
+}
+
 cudaError_t launch_bin(Ctx &c, const double *x) {
   cudaMemsetAsync(c.cell_count, 0, sizeof(int32_t) * (c.g.ncell + 1), c.stream);
   if (c.n > 0) bin_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(x, c.n, c.g, c.q_orig, c.cell_count, c.err);
@@ -1028,10 +1097,10 @@ cudaError_t launch_neighbors(Ctx &c) {
                                                       c.err);
     const uint32_t mgx = c.g.nc[0] > 1 ? (uint32_t)(4294967296ull / (uint64_t)c.g.nc[0]) : 0u;
     const uint32_t mgy = c.g.nc[1] > 1 ? (uint32_t)(4294967296ull / (uint64_t)c.g.nc[1]) : 0u;
-    filter_kernel<<<nblk(c.n, 128), 128, 0, c.stream>>>(
-        (int32_t)c.n, c.g, mgx, mgy, c.q_s, c.perm, c.inv_perm[c.cur_inv], c.cell_start, c.row_nbr, c.W, kCandWidth, c.cand,
-        c.ccnt,
-        c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt, c.maxstaged, c.maxrow, c.err);
+    filter_kernel<<<nblk(c.n, kFilterThreads), kFilterThreads, 0, c.stream>>>(
+        (int32_t)c.n, c.g, mgx, mgy, c.q_s, c.perm, c.inv_perm[c.cur_inv], c.cell_start, c.row_nbr, c.W, kCandWidth,
+        c.cand, c.ccnt, c.nbr, reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt, c.maxstaged, c.maxrow,
+        c.err);
     c.cand_valid = true;
     return cudaGetLastError();
   }
@@ -1048,15 +1117,7 @@ cudaError_t launch_neighbors(Ctx &c) {
 
 cudaError_t launch_lattice_temperature(Ctx &c) {
   if (c.n == 0) return cudaGetLastError();
-  RecipTab rt;
-  for (int k = 0; k < kMaxWidth + 2; ++k) {
-    rt.inv_n[k] = k > 0 ? 1.0 / (double)k : 0.0;
-    rt.inv_dof[k] = k > 0 ? 1.0 / (1.5 * kKB * (double)k) : 0.0;
-    // one atom type: T = D 2^-96 (m / 2) kMVV / (k + 1) / ((3/2) k_B dof) for k neighbours
-    const int dof = (c.p.dof_mode == 1) ? k : k + 1;
-    rt.coefT[k] = dof > 0 ? std::ldexp(0.5 * c.mt.m[0] * kMVV, -96) / (double)(k + 1) / (1.5 * kKB * (double)dof)
-                          : 0.0;
-  }
+  const RecipTab rt = recip_table(c);
   if (c.mt.n_types == 1)
     lattice_temp_kernel<true><<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.nbr, c.cnt, c.v_s, c.type_s, c.mt, rt,
                                                                     c.p.dof_mode, c.p.eps_ke_eV, c.p.Tref_K,

@@ -22,7 +22,7 @@ constexpr int kWinThreads = 256;
 __global__ void mirror_kernel(int64_t n, const double *__restrict__ T, double Tref, double invTmax,
                               float *__restrict__ y) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s < n) y[s] = (float)((T[s] - Tref) * invTmax);
+  if (s < n) y[s] = d2f_rn((T[s] - Tref) * invTmax);   // the conversion on the integer pipes
 }
 
 // rho_i = |T1 - T0 - tau (R(T0) + R(T1)) / 2| / max(1 K, 1e-3 T0) with
@@ -107,9 +107,9 @@ __global__ void finish_kernel(int64_t n, const double *__restrict__ T0, const fl
   const double t0 = T0[s];
   const float ui = uTl[s];
   float dT = 0.0f;
-  if (ui == ui) dT = f * (((float)t0 - Tref) + ui);   // f (T0 - T_l), T_l = Tref - ui
-  const double dTd = (double)dT;
-  T1[s] = fma(Tmax_d, (double)z[s], t0) - dTd;
+  if (ui == ui) dT = f * ((d2f_rn(t0) - Tref) + ui);   // f (T0 - T_l), T_l = Tref - ui
+  const double dTd = f2d(dT);                            // conversions on the integer pipes
+  T1[s] = fma(Tmax_d, f2d(z[s]), t0) - dTd;
   dTc[s] = dTd;
   if (dT != 0.0f) y[s] = fmaf(-dT, invTmax, y[s]);
 }
@@ -127,7 +127,7 @@ __global__ void accept_kernel(int64_t n, const double *__restrict__ dTc, double 
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double d = dTc[s];
-  if (d != 0.0) A[s] += VC * d;
+  if ((__double_as_longlong(d) << 1) != 0) A[s] += VC * d;   // d != 0, on the bit pattern
 }
 
 cudaError_t cheb_accept(Ctx &c, const double *dTc) {
