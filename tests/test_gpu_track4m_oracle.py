@@ -2,7 +2,8 @@
 
 100 MD steps of 100 substeps (10,000 substeps of 1e-3 fs), Langevin hand-over,
 free flight, neighbour rebuild every MD step, in the launch configuration
-bench.py times (row-tile kernel, graph replay).  The oracle's run of the same
+bench.py times (row-tile kernel, graph replay, lists from 0.3 A skin candidates:
+the full search's lists).  The oracle's run of the same
 sequence is cached by tests/_track4m_reference.py (about 8 minutes on 16 host
 cores the first time).
 
@@ -38,6 +39,7 @@ def test_track_4m_10k_substeps_plain(ref):
     import torch
     from paper_1810_12357_gb300 import Ehc
     s, p = R.workload()
+    p = dict(p, skin=0.3)   # the bench's list path (the oracle searches in full)
     dt_md = R.N_SUB * p["dt_sub"]
     g = Ehc(p, s)
     g.set_te(s.Te)
@@ -68,6 +70,7 @@ def test_track_4m_learned_window_against_oracle(ref):
     from paper_1810_12357_gb300 import Ehc, EhcCheb, learned
     coeffs, info = learned.train_track_window()
     s, p = R.workload()
+    p = dict(p, skin=0.3)   # the bench's list path (the oracle searches in full)
     dt_md = R.N_SUB * p["dt_sub"]
     n_w = 100
     g = Ehc(p, s)
