@@ -69,7 +69,7 @@ void free_all(Ctx &c) {
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
                  c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax,
-                 c.cand, c.ccnt, c.q_ref};
+                 c.cand, c.ccnt, c.q_ref, c.perm_raw};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -365,6 +365,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.cell_fill, ncell));
   A(dalloc(&c.scan_tmp, ntiles + 1));
   A(dalloc(&c.perm, n));
+  A(dalloc(&c.perm_raw, n));
   A(dalloc(&c.inv_perm[0], n));
   A(dalloc(&c.inv_perm[1], n));
   A(dalloc(&c.q_s, n));

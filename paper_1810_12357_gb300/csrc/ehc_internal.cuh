@@ -473,6 +473,7 @@ struct Ctx {
   int32_t *cell_fill = nullptr;  // [ncell]
   int32_t *scan_tmp = nullptr;   // block sums of the scan
   int32_t *perm = nullptr;
+  int32_t *perm_raw = nullptr;   // [N] the cells' atoms in scatter order, before the sort by id
   int32_t *inv_perm[2] = {nullptr, nullptr};
   int cur_inv = 0;
   int4 *q_s = nullptr;           // sorted positions + cell id

@@ -148,20 +148,19 @@ __global__ void scatter_kernel(const int4 *__restrict__ q, int64_t n, const int3
 }
 
 // order each cell's atoms by original id (the scatter order is not deterministic)
-__global__ void sort_cells_kernel(const int32_t *__restrict__ start, int64_t ncell,
-                                  int32_t *__restrict__ perm) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  int32_t b = start[c], e = start[c + 1];
-  for (int32_t i = b + 1; i < e; ++i) {
-    int32_t key = perm[i];
-    int32_t j = i - 1;
-    while (j >= b && perm[j] > key) {
-      perm[j + 1] = perm[j];
-      --j;
-    }
-    perm[j + 1] = key;
-  }
+// the atoms of each cell by original id: each atom's place in its cell is the
+// number of the cell's atoms with a smaller id (a rank sort, one thread per atom,
+// from the scatter's unordered runs into perm)
+__global__ void rank_cells_kernel(int64_t n, const int4 *__restrict__ q, const int32_t *__restrict__ start,
+                                  const int32_t *__restrict__ raw, int32_t *__restrict__ perm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t key = raw[i];
+  const int32_t cell = q[key].w;
+  const int32_t b = start[cell], e = start[cell + 1];
+  int32_t r = 0;
+  for (int32_t j = b; j < e; ++j) r += raw[j] < key ? 1 : 0;
+  perm[b + r] = key;
 }
 
 // move per-atom data into the new sorted order
@@ -1047,8 +1046,10 @@ cudaError_t launch_bin(Ctx &c, const double *x) {
 
 cudaError_t launch_sort_cells(Ctx &c) {
   cudaMemsetAsync(c.cell_fill, 0, sizeof(int32_t) * c.g.ncell, c.stream);
-  if (c.n > 0) scatter_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.q_orig, c.n, c.cell_start, c.cell_fill, c.perm);
-  sort_cells_kernel<<<nblk(c.g.ncell, 256), 256, 0, c.stream>>>(c.cell_start, c.g.ncell, c.perm);
+  if (c.n > 0) {
+    scatter_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.q_orig, c.n, c.cell_start, c.cell_fill, c.perm_raw);
+    rank_cells_kernel<<<nblk(c.n, 256), 256, 0, c.stream>>>(c.n, c.q_orig, c.cell_start, c.perm_raw, c.perm);
+  }
   return cudaGetLastError();
 }
 
