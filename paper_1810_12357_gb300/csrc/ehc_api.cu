@@ -1091,14 +1091,20 @@ int ehc_md_step_host(ehc_ctx *h, double *x_host, double *v_host, int32_t n_sub, 
   CK(cudaEventRecord(c.io_ev[2], c.stream));
   CK(cudaStreamWaitEvent(c.io_stream, c.io_ev[2], 0));
   CK(cudaMemcpyAsync(v_host, c.v_dev, b3, cudaMemcpyDeviceToHost, c.io_stream));
-  r = ehc_drift(h, c.x_dev, c.v_dev, dt_md_fs);
-  if (r == EHC_OK) r = ehc_get_te(h, c.T_out);
+  // T_e in caller order first, downloaded on io_stream while the context stream
+  // runs the drift and downloads the positions
+  r = ehc_get_te(h, c.T_out);
+  if (r == EHC_OK) {
+    CK(cudaEventRecord(c.io_ev[3], c.stream));
+    CK(cudaStreamWaitEvent(c.io_stream, c.io_ev[3], 0));
+    CK(cudaMemcpyAsync(Te_host_out, c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.io_stream));
+    r = ehc_drift(h, c.x_dev, c.v_dev, dt_md_fs);
+  }
   if (r) {
     cudaStreamSynchronize(c.io_stream);
     return r;
   }
   CK(cudaMemcpyAsync(x_host, c.x_dev, b3, cudaMemcpyDeviceToHost, c.stream));
-  CK(cudaMemcpyAsync(Te_host_out, c.T_out, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.io_stream));
   return ehc_sync(h);
 }

@@ -462,7 +462,7 @@ struct Ctx {
   // host-buffer MD step: the velocity upload and download run on io_stream,
   // ordered against the context stream by io_ev
   cudaStream_t io_stream = nullptr;
-  cudaEvent_t io_ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   // device buffers
   int32_t *type_orig = nullptr;  // caller's type index per atom (original order), or null
