@@ -69,7 +69,7 @@ void free_all(Ctx &c) {
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
                  c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax,
-                 c.cand, c.ccnt, c.q_ref, c.perm_raw};
+                 c.cand, c.ccnt, c.q_ref, c.perm_raw, c.wgt_d};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -372,6 +372,7 @@ int ehc_create(const ehc_params *p, int64_t n_atoms, const double box_A[3], cons
   A(dalloc(&c.v_s, n));
   A(dalloc(&c.nbr, (size_t)W * n));
   if (c.p.rate_shell_n > 0) A(dalloc(&c.wgt, (size_t)W * n));
+  if (c.p.rate_shell_n > 0 && c.p.flux_prec == 1) A(dalloc(&c.wgt_d, (size_t)W * n));
   c.ps = (n + 3) / 4 * 4;
   A(dalloc(&c.pidx, (size_t)((W + 1) / 2) * (size_t)(c.ps > 0 ? c.ps : 4)));
   A(dalloc(&c.dlo, n));

@@ -538,6 +538,7 @@ struct Ctx {
   int32_t nwork = 0;
   float *rrange[2] = {nullptr, nullptr};  // [min of every row | max of every row] of each mirror
   float *wgt = nullptr;          // [W][N] pair weights (ehc_params.rate_shell_n > 0), else null
+  double *wgt_d = nullptr;       // [W][N] the same weights in FP64 for the FP64 flux path (flux_prec 1), else null
   StepCoef *coef = nullptr;      // device
   StepCoef *coef_host = nullptr; // pinned
   double *x_dev = nullptr, *v_dev = nullptr, *T_out = nullptr;  // staging of the host-buffer step

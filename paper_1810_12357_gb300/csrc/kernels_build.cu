@@ -259,7 +259,8 @@ __device__ __forceinline__ int3 search_atom(int32_t s, int32_t n, const Grid &g,
                                             const int32_t *__restrict__ start, const int32_t *__restrict__ row_nbr,
                                             int32_t W, int32_t *__restrict__ nbr, uint16_t *__restrict__ pidx16,
                                             int64_t ps, uint8_t *__restrict__ cnt, int32_t *__restrict__ err,
-                                            float *__restrict__ wgt, float wn) {
+                                            float *__restrict__ wgt, float wn, double *__restrict__ wgt_d,
+                                            double2 wq) {
   const int4 qi = q_s[s];
   const int32_t ncx = g.nc[0];
   const int32_t cx = qi.w % ncx;
@@ -351,7 +352,10 @@ __device__ __forceinline__ int3 search_atom(int32_t s, int32_t n, const Grid &g,
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (WEIGHTS) wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
+              if (WEIGHTS) {
+                wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
+                if (wgt_d) wgt_d[(int64_t)m * n + s] = wq.x / (wq.y * (double)(d2 > 0 ? (uint64_t)d2 : 1ull));
+              }
             }
             ++m;
           }
@@ -378,7 +382,10 @@ __device__ __forceinline__ int3 search_atom(int32_t s, int32_t n, const Grid &g,
             if (m < W) {
               nbr[(int64_t)m * n + s] = t;
               pidx16[((int64_t)(m >> 1) * ps + s) * 2 + (m & 1)] = (uint16_t)(prefix + (t - rs));
-              if (WEIGHTS) wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
+              if (WEIGHTS) {
+                wgt[(int64_t)m * n + s] = __fdiv_rn(wn, __ull2float_rn(d2 > 0 ? (uint64_t)d2 : 1ull));
+                if (wgt_d) wgt_d[(int64_t)m * n + s] = wq.x / (wq.y * (double)(d2 > 0 ? (uint64_t)d2 : 1ull));
+              }
             }
             ++m;
           }
@@ -402,10 +409,12 @@ __global__ void __launch_bounds__(128) neighbor_kernel(int32_t n, Grid g, const 
                                                        int64_t ps, uint8_t *__restrict__ cnt,
                                                        int32_t *__restrict__ maxcnt, int32_t *__restrict__ maxstaged,
                                                        int32_t *__restrict__ maxrow, int32_t *__restrict__ err,
-                                                       float *__restrict__ wgt, float wn) {
+                                                       float *__restrict__ wgt, float wn,
+                                                       double *__restrict__ wgt_d, double2 wq) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const int3 r = search_atom<FAST, WEIGHTS>(s, n, g, q_s, start, row_nbr, W, nbr, pidx16, ps, cnt, err, wgt, wn);
+  const int3 r = search_atom<FAST, WEIGHTS>(s, n, g, q_s, start, row_nbr, W, nbr, pidx16, ps, cnt, err, wgt, wn,
+                                            wgt_d, wq);
   // one atomic per warp for each of the three maxima
   const unsigned act = __activemask();
   const int32_t wm = __reduce_max_sync(act, r.x);
@@ -1110,9 +1119,11 @@ cudaError_t launch_neighbors(Ctx &c) {
   const double wn = c.p.rate_shell_n > 0 ? c.p.zb2_A2 * 1099511627776.0 / (double)c.p.rate_shell_n : 0.0;
   auto kern = c.wgt ? (fast ? neighbor_kernel<true, true> : neighbor_kernel<false, true>)
                     : (fast ? neighbor_kernel<true, false> : neighbor_kernel<false, false>);
+  // the FP64 path's weights in FP64, as the oracle forms them: S2 2^40 / (n_shell d2)
+  const double2 wq = make_double2(c.p.zb2_A2 * 1099511627776.0, (double)c.p.rate_shell_n);
   kern<<<nblk(c.n, 128), 128, 0, c.stream>>>((int32_t)c.n, c.g, c.q_s, c.cell_start, c.row_nbr, c.W, c.nbr,
                                              reinterpret_cast<uint16_t *>(c.pidx), c.ps, c.cnt, c.maxcnt,
-                                             c.maxstaged, c.maxrow, c.err, c.wgt, (float)wn);
+                                             c.maxstaged, c.maxrow, c.err, c.wgt, (float)wn, c.wgt_d, wq);
   return cudaGetLastError();
 }
 

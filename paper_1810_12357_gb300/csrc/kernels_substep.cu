@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(256) substep_local_f64_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const double *__restrict__ Tin, double *__restrict__ Tout, double *__restrict__ A,
     const double *__restrict__ Tl, const double *__restrict__ srcw, const double *__restrict__ pulse, int k,
-    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt) {
+    const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const double *__restrict__ wgt) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double inv = cf->invTmax;
@@ -900,7 +900,7 @@ __global__ void __launch_bounds__(256) substep_local_f64_kernel(
     const double E = exp(a - b);
     const double phi = b * (1.0 - a) * E - a * (1.0 - b) / E;
     const double kij = km ? 0.5 * (a + b) : 1.0;
-    const double w = wgt ? (double)__ldg(wgt + (int64_t)j * n + s) : 1.0;
+    const double w = wgt ? __ldg(wgt + (int64_t)j * n + s) : 1.0;
     F += w * kij * (lo ? phi : -phi);
   }
   double du = cf->dtKu * F;
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     int32_t n, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ cnt,
     const double *__restrict__ Tin, double *__restrict__ Tout, double *__restrict__ A,
     const double *__restrict__ Tl, const double *__restrict__ srcw, const double *__restrict__ pulse,
-    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const float *__restrict__ wgt,
+    int k, const StepCoef *__restrict__ cf, int32_t *__restrict__ err, const double *__restrict__ wgt,
     const uint8_t *__restrict__ fix, double *__restrict__ res) {
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(256) substep_f64_kernel(
     const double a = lo ? ti : tj, b = lo ? tj : ti;
     const double E = exp(a - b);
     const double phi = b * (1.0 - a) * E - a * (1.0 - b) / E;
-    const double w = wgt ? (double)__ldg(wgt + (int64_t)j * n + s) : 1.0;
+    const double w = wgt ? __ldg(wgt + (int64_t)j * n + s) : 1.0;
     F += w * (lo ? phi : -phi);
   }
   double inc = cf->dtTK * F;
@@ -1078,10 +1078,10 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
       double *Tout = c.T[parity ^ 1];
       if (laser)
         substep_local_f64_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d,
-                                                                     c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt);
+                                                                     c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt_d);
       else
         substep_local_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d,
-                                                                      c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt);
+                                                                      c.srcw_d, c.pulse, k, c.coef, c.err, c.wgt_d);
     } else if (laser) {
       if (k == 0) local_tier_reset(c, st);
       substep_local_f32_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, c.dmir[parity],
@@ -1102,10 +1102,10 @@ cudaError_t launch_substep(Ctx &c, int k, int parity, cudaStream_t st) {
     double *Tout = c.T[parity ^ 1];
     if (laser)
       substep_f64_kernel<true><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                             c.pulse, k, c.coef, c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
+                                                             c.pulse, k, c.coef, c.err, c.wgt_d, c.has_border ? c.bmask : nullptr, c.bres);
     else
       substep_f64_kernel<false><<<nblk(n, 256), 256, 0, st>>>(n, c.nbr, c.cnt, Tin, Tout, c.A, c.Tl_d, c.srcw_d,
-                                                              c.pulse, k, c.coef, c.err, c.wgt, c.has_border ? c.bmask : nullptr, c.bres);
+                                                              c.pulse, k, c.coef, c.err, c.wgt_d, c.has_border ? c.bmask : nullptr, c.bres);
   } else if (tile_path(c)) {
     const int32_t P = (c.n_max + 1) / 2;
     const int32_t tb = c.tile_floats;

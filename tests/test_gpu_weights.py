@@ -23,10 +23,11 @@ def test_weighted_rates_match_the_oracle(flux_prec):
     g, _, _ = run_gpu(s, p, 3, 60)
     Tg = g.get_te().cpu().numpy()
     err = float(np.max(np.abs(Tg - sim.T) / sim.T))
-    # the library computes the weights in single precision (r^2 rounded to float and
-    # one rounded division: relative error <= 2^-23), which bounds the FP64 path's
-    # difference by ~1.2e-7 of the relative change of T
-    assert err < (1e-4 if flux_prec == 0 else 1.2e-7), err
+    # the single-precision path reads single-precision weights (r^2 rounded to float,
+    # one rounded division); the FP64 path forms them as the oracle does,
+    # S2 2^40 / (n_shell d2) in FP64, so it is held to the FP64 bar (the Langevin
+    # normals are single precision on both paths, as in test_couple_parity)
+    assert err < (1e-4 if flux_prec == 0 else 1e-11), err
     e = g.energy()
     assert abs(e["drift"]) < 1e-9
     # the weights change the result against uniform rates
