@@ -539,7 +539,7 @@ def batch_line(args, steps=None, warmup=None):
     from paper_1810_12357_gb300 import inputs as I
     ws, rank, local = _dist()
     systems = I.batch_replicas(args.replicas, 4)
-    p = dict(I.params_track(), tile_threads=args.tile_threads)
+    p = dict(I.params_track(), tile_threads=args.tile_threads, skin=SKIN_A if args.skin is None else args.skin)
     x = torch.as_tensor(np.concatenate([s.x for s in systems]), device="cuda").contiguous()
     v = torch.as_tensor(np.concatenate([s.v for s in systems]), device="cuda").contiguous()
     Te = torch.as_tensor(np.concatenate([s.Te for s in systems]), device="cuda").contiguous()
@@ -590,7 +590,8 @@ def batch_line(args, steps=None, warmup=None):
             "config": {"workload": f"batched replicas: {b.n_rep} FCC Cu cascade cells, log-uniform 8k-500k atoms "
                                    f"({n:,} atoms), random Gaussian hot spots, one substep launch per substep "
                                    f"over all replicas", "n_atoms": n, "replicas": b.n_rep,
-                       "substeps_per_step": N_SUB, "dt_sub_fs": DT_SUB},
+                       "substeps_per_step": N_SUB, "dt_sub_fs": DT_SUB,
+                       "neighbour_list": neighbour_text(p["skin"])},
             "substep_only": {"value": n / (sub_launch_ms * 1e-3), "unit": UNIT, "substep_ms": sub_launch_ms},
             "roofline": {"bound": "hbm", "achieved": B_ALG * n / (sub_launch_ms * 1e-3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": B_ALG * n / (sub_launch_ms * 1e-3) / 1e9 / peak,
