@@ -46,13 +46,15 @@ B_ALG = 4 * N_NB + 44  # algorithmic bytes per atom-substep of the substep kerne
 DTYPE = "f32 pair flux (TwoSum); float-pair (~48-bit) substep state; f64 T between calls, exchange and ledger"
 TIMED_S = 3.0          # the K-step timed block is repeated until about this many seconds are timed
 MAX_REPEATS = 30
-# kernels launched per MD step: bin + 3-phase scan + scatter + cell sort + gather
-# + neighbour list + lattice temperature + 2 reduction kernels = 11; the float-pair
-# split before the first substep and the merge at the next build = 2; N_SUB
-# substeps; hand-over + 2 reduction kernels = 3; drift = 1 (117, as an ncu launch
-# list of the track counts); a border adds its mask kernel and the two
-# reservoir-sum kernels per build
+# kernels launched per MD step: bin + 3-phase scan + scatter + rank sort of the
+# cells + gather + neighbour list + lattice temperature + 2 reduction kernels = 11;
+# the float-pair split before the first substep and the merge at the next build =
+# 2; N_SUB substeps; hand-over + 2 reduction kernels = 3; drift = 1 (117, as an ncu
+# launch list of the track counts); lists from skin candidates add the skin check
+# and the candidate kernel (which returns at once unless a rebuild is due) = 2; a
+# border adds its mask kernel and the two reservoir-sum kernels per build
 LAUNCHES_PER_STEP = 11 + 2 + N_SUB + 3 + 1
+SKIN_LAUNCHES_PER_STEP = 2
 BORDER_LAUNCHES_PER_STEP = 3
 VERLET_EXTRA_LAUNCHES = 3   # velocity-Verlet: force kernel, its energy sum and two kicks in place of the drift
 
@@ -407,6 +409,8 @@ def _finish(args, ws, rank, dev, dist, ms, e2e_ms, sub_ms, e, n, clocks):
                 if e2e_ms == e2e_ms else None),
         # every rank's kernels in the timed region (one replica per rank)
         "gpu_launches": (LAUNCHES_PER_STEP + (BORDER_LAUNCHES_PER_STEP if args.border > 0 else 0)
+                         + (SKIN_LAUNCHES_PER_STEP if (SKIN_A if args.skin is None else args.skin) > 0
+                            and args.rate_shell == 0 else 0)
                          + (VERLET_EXTRA_LAUNCHES if args.md == "verlet" else 0)) * args.steps * ws,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
