@@ -618,7 +618,7 @@ def window_line(args, coeffs=None, learned_info=None, corrector=None):
     the error."""
     import torch
     from paper_1810_12357_gb300 import Ehc, EhcCheb
-    s, p = workload(args.cells)
+    s, p = workload(args.cells, skin=args.skin)
     if args.frozen_lattice:
         # hand-over to the electrons' ledger only: both runs see the same lattice
         p = dict(p, frozen=1)
@@ -756,7 +756,7 @@ def run_corrector(args):
     kernels in a form a profiler can capture; prints the mean window time."""
     import torch
     from paper_1810_12357_gb300 import Ehc, EhcCheb, EhcGnn, learned
-    s, p = workload(args.cells)
+    s, p = workload(args.cells, skin=args.skin)
     g = Ehc(p, s)
     g.set_te(s.Te)
     g.build_neighbors(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.v, device="cuda"))
