@@ -521,7 +521,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args.cells, s.n, {"path": "CPU oracle"}, n_sub),
+            "data": "synthetic", "config": config_dict(args.cells, s.n, {"path": "CPU oracle", "neighbour_list": "recomputed every MD step by the oracle's cell search (the lists the GPU path builds)"}, n_sub),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
