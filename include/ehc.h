@@ -40,7 +40,8 @@ extern "C" {
 #define EHC_E_UNSTABLE (-4)     /* substep violates dt (2 n_max K + G/C_e) <= 2 */
 #define EHC_E_RANGE (-5)        /* theta = T/T_max left [0,1] or became NaN, or a velocity
                                    component reached 256 A/fs (or NaN) at a build */
-#define EHC_E_NBR_OVERFLOW (-6) /* an atom has more neighbours than max_neighbors */
+#define EHC_E_NBR_OVERFLOW (-6) /* an atom has more neighbours than max_neighbors (or, with
+                                   skin_A > 0, more than 48 candidates within rc_A + skin_A) */
 #define EHC_E_TIMEOUT (-7)      /* a bounded device wait gave up */
 #define EHC_E_STATE (-8)        /* call order violated (e.g. substep before build) */
 #define EHC_E_BOUNDS (-9)       /* atom outside the extent of a non-periodic axis */
@@ -122,7 +123,9 @@ extern "C" {
  *                   list is the one the full search gives, in the same order.  A negative
  *                   value sizes the cells the same way and searches them in full every
  *                   build.  Used on grids with at least 3 cells per periodic axis, uniform
- *                   pair rates and max_neighbors <= 32; other contexts search in full */
+ *                   pair rates and max_neighbors <= 32; other contexts search in full.  At
+ *                   most 48 candidates per atom (more: EHC_E_NBR_OVERFLOW at the build; an
+ *                   FCC lattice at 300 K has about 19 within rc_A + 0.3 A for rc_A = 4 A) */
 typedef struct ehc_params {
   double rc_A;
   double dt_sub_fs;
