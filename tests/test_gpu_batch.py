@@ -37,10 +37,12 @@ def _run_batch(systems, p, n_md, n_sub):
     return b, x, v
 
 
-@pytest.mark.parametrize("couple_mode", [0, 1])
-def test_batch_equals_single_contexts(couple_mode):
+@pytest.mark.parametrize("couple_mode,skin", [(0, 0.0), (1, 0.0), (1, 0.3)])
+def test_batch_equals_single_contexts(couple_mode, skin):
+    # skin 0.3: the bench's batch configuration (each replica's list from its own
+    # skin candidates)
     systems = I.batch_replicas(5, 41, n_min=1500, n_max=12000)
-    p = dict(I.params_track(), couple_mode=couple_mode, Tmax=1e5)
+    p = dict(I.params_track(), couple_mode=couple_mode, Tmax=1e5, skin=skin)
     b, xb, vb = _run_batch(systems, p, 3, 40)
     Tb = b.get_te().cpu().numpy()
     vb = vb.cpu().numpy()
@@ -53,9 +55,10 @@ def test_batch_equals_single_contexts(couple_mode):
         assert eb["E_e"] == eg["E_e"] and eb["E_lat"] == eg["E_lat"]
 
 
-def test_batch_replica_matches_oracle():
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_batch_replica_matches_oracle(skin):
     systems = I.batch_replicas(4, 42, n_min=2000, n_max=8000)
-    p = I.params_track()
+    p = dict(I.params_track(), skin=skin)
     b, _, _ = _run_batch(systems, p, 2, 50)
     Tb = b.get_te().cpu().numpy()
     for r, s in enumerate(systems):
