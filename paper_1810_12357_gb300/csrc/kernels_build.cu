@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(128) cand_kernel(int32_t n, Grid g, int64_t rv
 // unsorts the lists of its ~20 candidates once), writes it back for the next
 // builds and writes its hits again in that order.  Every list is exactly the
 // full search's.
-constexpr int kFilterBatch = 4;     // candidates whose three dependent loads are in flight together
+constexpr int kFilterBatch = 2;     // candidates whose three dependent loads are in flight together
 constexpr int kFilterThreads = 128;
 
 // floor(x / d) for 0 <= x < 2^31 and d >= 1, with mg = floor(2^32 / d) (d > 1; any
