@@ -1549,7 +1549,7 @@ struct ehc_cheb {
   int64_t n = 0;
   std::vector<double> nu, mut, kap, gam;   // stage coefficients, index 1..s
   float *y[4] = {nullptr, nullptr, nullptr, nullptr};   // stage values (padded to ps floats)
-  float *z[4] = {nullptr, nullptr, nullptr, nullptr};   // the window's change Y_j - Y_0 (z[3]: scratch)
+  float *z[3] = {nullptr, nullptr, nullptr};   // the window's change Y_j - Y_0 of the last three stages
   float *F0 = nullptr, *F1 = nullptr, *part = nullptr, *rho = nullptr, *host = nullptr;
   float *rr[2] = {nullptr, nullptr};   // row value ranges of the stage values
   double *T1 = nullptr, *dTc = nullptr;
@@ -1822,7 +1822,7 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
   for (int k = 0; k < 4; ++k) A(dalloc(&w->y[k], np4));
-  for (int k = 0; k < 4; ++k) A(dalloc(&w->z[k], n));
+  for (int k = 0; k < 3; ++k) A(dalloc(&w->z[k], n));
   A(dalloc(&w->F0, n));
   A(dalloc(&w->F1, n));
   A(dalloc(&w->part, cheb_blocks(n)));
@@ -1846,10 +1846,10 @@ int ehc_cheb_create(ehc_ctx *hc, int32_t n_window, int32_t stages, int32_t order
 
 void ehc_cheb_destroy(ehc_cheb *w) {
   if (!w) return;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 4; ++k)
     if (w->y[k]) cudaFree(w->y[k]);
+  for (int k = 0; k < 3; ++k)
     if (w->z[k]) cudaFree(w->z[k]);
-  }
   void *p[] = {w->F0,  w->F1,     w->part,   w->rho, w->T1, w->dTc, w->rr[0], w->rr[1], w->tbuf,
                w->tT0, w->tT1,    w->tlpart, w->tdpart, w->tp, w->tm,  w->tv,    w->tgc,   w->tgd,
                w->tc0, w->tloss};
@@ -1957,8 +1957,8 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   sf.zin = nullptr;
   sf.zprev = nullptr;
   sf.F0 = nullptr;
-  sf.yout = rot[w->s % 3];   // scratch (Y_{s-1} or an older stage)
-  sf.zout = w->z[3];         // scratch
+  sf.yout = nullptr;   // only the flux (and the row ranges of ys) is kept
+  sf.zout = nullptr;
   sf.Fout = w->F1;
   sf.kap = 0.0f;
   sf.gt = 0.0f;

@@ -304,7 +304,7 @@ struct StageArgs {
   const float *zin;     // z_{j-1} (null: zero, the first stage)
   const float *zprev;   // z_{j-2} (null: zero)
   const float *F0;      // F(Y_0) (null: no gt term)
-  float *yout;          // Y_j
+  float *yout;          // Y_j (null with zout: a flux pass, Fout only)
   float *zout;          // z_j
   float *Fout;          // the pair-flux sum F(Y_{j-1}) per atom, or null
   float *rr[2];         // row value ranges of the stage values (read [parity], write [parity ^ 1])

@@ -461,8 +461,10 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
     const float inc = fmaf(sa.gt, si.F0, fmaf(-sa.kap, si.zm1, sa.mt * F));
     const float z = si.zm1 + fmaf(sa.nu, si.zm2 - si.zm1, inc);
     const float h = si.y0 + z;
-    sa.zout[s] = z;
-    sa.yout[s] = h;
+    if (sa.zout) {   // null: a flux pass, whose stage values are not kept
+      sa.zout[s] = z;
+      sa.yout[s] = h;
+    }
     if (sa.Fout) sa.Fout[s] = F;
     return h;
   }
@@ -613,6 +615,11 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
     ltier = prev < 1.2e-4f ? 3 : (prev < 0.02f ? 2 : (prev < 0.12f ? 1 : 0));
     if (blockIdx.x == 0 && threadIdx.x == 0) ring[(k + 2) % 3] = 0u;
   }
+  // The atoms of a row go to the compute warps in rounds of NT; the warps that
+  // take a row's last, partial round rotate from row to row (rot: the first of
+  // them), so that no warp carries every row's extra round and holds the others,
+  // which run at most one item ahead, back.
+  int rot = 0;
   for (int it = 0; it < n_it; ++it) {
     const int b = it % kTileBufs;
     if (!mbar_wait(&sp.full[b], (uint32_t)(it / kTileBufs) & 1)) {
@@ -626,7 +633,8 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
     const int64_t ps = D.ra.ps;
     const uint32_t *pidx = D.ra.pidx;
     float vmin = 3.0e38f, vmax = -3.0e38f;
-    for (int q = threadIdx.x; q < row_len; q += NT) {
+    const int vw = (warp + aw - rot) % aw;   // this warp's place in the row's rounds
+    for (int q = vw * 32 + lane; q < row_len; q += NT) {
       const int32_t s = row_s + q;
       uint32_t pv[PP];
 #pragma unroll
@@ -678,6 +686,7 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? kTileMinBlocks : 2 * kTil
       mbar_arrive(&sp.empty[b]);
     }
     __syncwarp();
+    rot = (rot + ((row_len % NT) + 31) / 32) % aw;
   }
   if (LOCAL) {
     for (int o = 16; o > 0; o >>= 1) lmd = fmaxf(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));

@@ -81,7 +81,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-constexpr int kResBlocks = 304;   // 2 x 152 SMs, grid-stride
+constexpr int kResBlocks = 1216;  // 8 x 152 SMs, grid-stride
 
 int cheb_blocks(int64_t n) {
   (void)n;
