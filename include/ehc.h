@@ -295,6 +295,20 @@ int ehc_sums_at(ehc_ctx *c, const int32_t *idx_dev, int64_t m, double *sums_host
  * substeps and hand-over.  EHC_E_STATE before the first build. */
 int ehc_set_step_means(ehc_ctx *c, double Te_mean, double Tlat);
 
+/* Key of the Langevin hand-over's random stream (the random-force coupling the
+ * paper cites beside Eqs. Motion and Xi; Philox4x32-10 counter = (atom id, MD
+ * step), key = seed).  By default atom i of the caller order draws with id i and
+ * the MD step counts this context's ehc_couple calls from 0.  A domain of a
+ * decomposed system renumbers its atoms and is a new context every MD step, so
+ * it sets ids_dev[0..n) (int64, device, caller order; copied, the caller keeps
+ * ownership) to the atoms' global ids and md_step to the system's MD step: its
+ * atoms then draw the numbers the undivided run draws.  ids_dev null returns to
+ * the caller index (md_step is set either way).  The ids are not checked for
+ * uniqueness (equal ids draw equal numbers) and are not part of a checkpoint.
+ * The first call with ids allocates n int64 on the device (EHC_E_NOMEM);
+ * EHC_E_INVAL for md_step < 0.  Asynchronous on the context stream. */
+int ehc_set_rng_ids(ehc_ctx *c, const int64_t *ids_dev, int64_t md_step);
+
 /* Failure-detection probe of the bounded device waits (no counterpart in the
  * paper): one block waits, with the mbarrier poll loop of the row-tile kernels
  * and a budget of `polls` polls, on a phase that completes (complete != 0) or

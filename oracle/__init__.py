@@ -79,7 +79,7 @@ def lib():
         L.oracle_gauss3.argtypes = [u64, u64, u64, P]
         L.oracle_gauss3.restype = None
         L.oracle_couple.argtypes = [i64, P, P, P, P, P, ctypes.c_int, ctypes.c_int, u64, u64,
-                                    dbl, dbl, dbl, P, dbl, dbl]
+                                    dbl, dbl, dbl, P, dbl, dbl, P]
         L.oracle_couple.restype = i64
         L.oracle_num_threads.restype = ctypes.c_int
         L.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -268,12 +268,19 @@ def gauss3(atom_id: int, step: int, seed: int):
 
 
 def couple(v, mass_of_atom, A, T, chi, *, mode, frozen, seed, md_step, dt_md, gamma_fs, VC,
-           stop_beta=0.0, stop_ecut=0.0):
+           stop_beta=0.0, stop_ecut=0.0, rng_id=None):
+    """Hand-over of one MD step (oracle_couple); rng_id: int64 ids keying the
+    atoms' Langevin numbers (None: the atom index)."""
     n = T.shape[0]
     dKE = np.empty(n)
+    rid = None
+    if rng_id is not None:
+        rid = np.ascontiguousarray(rng_id, dtype=np.int64)
+        assert rid.shape == (n,)
     stopped = lib().oracle_couple(n, _p(v), _p(mass_of_atom), _p(A), _p(T), _p(chi), int(mode),
                                   int(frozen), int(seed), int(md_step), float(dt_md),
-                                  float(gamma_fs), float(VC), _p(dKE), float(stop_beta), float(stop_ecut))
+                                  float(gamma_fs), float(VC), _p(dKE), float(stop_beta), float(stop_ecut),
+                                  _p(rid) if rid is not None else None)
     return dKE, int(stopped)
 
 
@@ -359,6 +366,7 @@ class OracleSim:
         self.vatom = float(v) if v and v > 0 else float(np.prod(self.box)) / self.n
         self.depth = depth
         self.md_step = 0
+        self.rng_ids = None   # ids keying the Langevin numbers (None: the atom index)
         self.T = None
         self.A = np.zeros(self.n)
         self.E_lat = 0.0
@@ -477,7 +485,8 @@ class OracleSim:
         dKE, stopped = couple(v, self.mass, self.A, self.T, self.chi, mode=p["couple_mode"],
                               frozen=p["frozen"], seed=p["seed"], md_step=self.md_step,
                               dt_md=dt_md, gamma_fs=self.gamma_L, VC=self.VC,
-                              stop_beta=p.get("stop_beta", 0.0), stop_ecut=p.get("stop_ecut", 10.0))
+                              stop_beta=p.get("stop_beta", 0.0), stop_ecut=p.get("stop_ecut", 10.0),
+                              rng_id=self.rng_ids)
         if local:
             # a stopped atom's unpaid energy returns to its own electrons: U_i += (A_i - dKE_i) / V
             idx = np.nonzero(self.T != Tb)[0]

@@ -641,11 +641,14 @@ void oracle_gauss3(uint64_t id, uint64_t step, uint64_t seed, double g[3]) {
  * integrated over the MD step: the atom's kinetic energy K loses
  * K (1 - exp(-2 beta dt_md)), and its own electrons gain that energy, through the
  * same exact hand-over as A_i (the target kinetic energy is K + A_i minus the
- * stopping loss; whatever the lattice does not take goes back to T_i). */
+ * stopping loss; whatever the lattice does not take goes back to T_i).
+ * rng_id (may be NULL): the id that keys atom i's Gaussian numbers in mode 1
+ * (NULL: i itself); a slab domain of a decomposed system passes its atoms'
+ * global ids, so that they draw what the undivided system draws. */
 int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *A, double *T,
                       const uint8_t *chi, int mode, int frozen, uint64_t seed, uint64_t md_step,
                       double dt_md, double gamma_fs, double VC, double *dKE, double stop_beta,
-                      double stop_ecut) {
+                      double stop_ecut, const int64_t *rng_id) {
   const double mvv = o_mvv_ev();
   int64_t stopped = 0;
 #pragma omp parallel for schedule(static) reduction(+ : stopped)
@@ -663,7 +666,7 @@ int64_t oracle_couple(int64_t n, double *v, const double *mass_of_atom, double *
     double w[3] = {vi[0], vi[1], vi[2]};
     if (mode == 1) {
       double g[3];
-      oracle_gauss3((uint64_t)i, md_step, seed, g);
+      oracle_gauss3(rng_id ? (uint64_t)rng_id[i] : (uint64_t)i, md_step, seed, g);
       double e1 = exp(-gamma_fs * dt_md);
       double e2 = exp(-2.0 * gamma_fs * dt_md);
       double sig = sqrt(O_KB * T[i] * (1.0 - e2) / (m * mvv));

@@ -87,6 +87,7 @@ _SIGS = {
     "ehc_get_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
     "ehc_set_te_at": (_I, [_P, _P, ctypes.c_int64, _P]),
     "ehc_set_step_means": (_I, [_P, ctypes.c_double, ctypes.c_double]),
+    "ehc_set_rng_ids": (_I, [_P, _P, ctypes.c_int64]),
     "ehc_sums_at": (_I, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "ehc_md_step_host": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]),
     "ehc_energy": (_I, [_P, ctypes.POINTER(ehc_energy_t)]),
@@ -364,6 +365,18 @@ class Ehc:
 
     def set_step_means(self, Te_mean: float, Tlat: float):
         _check(self._lib.ehc_set_step_means(self._h, float(Te_mean), float(Tlat)), "ehc_set_step_means")
+
+    def set_rng_ids(self, ids, md_step: int):
+        """Key the Langevin stream of the caller-order atoms by ids (int64 device
+        tensor of n ids, or None for the caller index) and set the MD step counter."""
+        if ids is not None:
+            import torch
+            ids = torch.as_tensor(ids).to(device=self.device, dtype=torch.int64).contiguous()
+            if ids.numel() != self.n:
+                raise ValueError("one id per atom")
+        self._rng_ids = ids   # kept alive until the asynchronous copy has run
+        _check(self._lib.ehc_set_rng_ids(self._h, _ptr(ids) if ids is not None else None, int(md_step)),
+               "ehc_set_rng_ids")
 
     def probe_wait(self, polls: int, complete: bool) -> int:
         """Return code of the bounded-wait probe (EHC_E_TIMEOUT when it ran out)."""

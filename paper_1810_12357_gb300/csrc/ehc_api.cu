@@ -69,7 +69,7 @@ void free_all(Ctx &c) {
                  c.pulse, c.dKE, c.partials, c.scal, c.err, c.coef, c.x_dev, c.v_dev, c.T_out,
                  c.pidx, c.row_nbr, c.dlo, c.uTl, c.pulse_f, c.rrange[0], c.rrange[1], c.srcw_d, c.reps,
                  c.work, c.wgt, c.tfix_orig, c.bmask, c.bres, c.bnd_part, c.uhi, c.md_part, c.ldmax,
-                 c.cand, c.ccnt, c.q_ref, c.perm_raw, c.wgt_d};
+                 c.cand, c.ccnt, c.q_ref, c.perm_raw, c.wgt_d, c.rng_id};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c.pulse_host) cudaFreeHost(c.pulse_host);
@@ -921,6 +921,26 @@ int ehc_set_step_means(ehc_ctx *h, double Te_mean, double Tlat) {
   Ctx &c = h->c;
   if (!c.built) return EHC_E_STATE;
   return step_coefficients(c, Te_mean, Tlat);
+}
+
+int ehc_set_rng_ids(ehc_ctx *h, const int64_t *ids_dev, int64_t md_step) {
+  if (!h || md_step < 0) return EHC_E_INVAL;
+  Ctx &c = h->c;
+  c.md_step = md_step;
+  if (!ids_dev) {
+    if (c.rng_id) CK(cudaStreamSynchronize(c.stream));   // a hand-over in flight may still read it
+    if (c.rng_id) cudaFree(c.rng_id);
+    c.rng_id = nullptr;
+    return EHC_OK;
+  }
+  if (!c.rng_id && c.n > 0 && cudaMalloc((void **)&c.rng_id, sizeof(int64_t) * (size_t)c.n) != cudaSuccess) {
+    cudaGetLastError();
+    c.rng_id = nullptr;
+    return EHC_E_NOMEM;
+  }
+  if (c.n > 0)
+    CK(cudaMemcpyAsync(c.rng_id, ids_dev, sizeof(int64_t) * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
+  return EHC_OK;
 }
 
 int ehc_probe_wait(ehc_ctx *h, uint32_t polls, int32_t complete) {

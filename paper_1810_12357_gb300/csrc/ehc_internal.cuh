@@ -523,6 +523,9 @@ struct Ctx {
   int32_t *cand = nullptr;
   uint8_t *ccnt = nullptr;
   int4 *q_ref = nullptr;
+  // ids keying each caller-order atom's Langevin stream (null: the caller index);
+  // set by ehc_set_rng_ids, allocated there on first use
+  int64_t *rng_id = nullptr;
   int32_t staged_max = 0;
   int32_t row_max = 0;
   int32_t tile_floats = 0;       // floats per tile buffer of the row-tile kernel (0: not set up)
@@ -551,7 +554,7 @@ struct Ctx {
   bool ff_valid = false;         // float-float substep state holds the current temperatures
   bool t_stale = false;          // T[tcur] is behind the float-float state
   int parity = 0;                // mirror buffer holding the current snapshot
-  int64_t md_step = 0;
+  int64_t md_step = 0;           // counter of the Langevin stream (ehc_set_rng_ids may set it)
   int64_t builds = 0;            // neighbour builds so far
   int64_t t_version = 0;         // bumped by everything that changes or reorders T
   int32_t n_max = 0;             // largest neighbour count this MD step

@@ -184,7 +184,7 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
                               double *__restrict__ A, double *__restrict__ T, double *__restrict__ v,
                               double *__restrict__ dKE, int mode, int frozen, uint64_t seed, uint64_t md_step,
                               double inv_VC, unsigned long long *__restrict__ n_stopped, double thc,
-                              double inv_Tmax) {
+                              double inv_Tmax, const int64_t *__restrict__ rng_id) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   // every load that does not depend on another is issued first: two waits on
@@ -207,7 +207,9 @@ __global__ void couple_kernel(int64_t n, const int32_t *__restrict__ perm, const
   double *vi = v + 3 * o;
   const double v0 = vi[0], v1 = vi[1], v2 = vi[2];
   float g[3] = {0.0f, 0.0f, 0.0f};
-  if (mode == 1) gauss3((uint64_t)o, md_step, seed, g);
+  // the Langevin stream of the atom: keyed by its caller index, or by the id the
+  // caller set for it (a domain of a decomposed system: the global id)
+  if (mode == 1) gauss3(rng_id ? (uint64_t)rng_id[o] : (uint64_t)o, md_step, seed, g);
   const FF hk = ct.hk[ty];
   const FF x0 = d2ff(v0), x1 = d2ff(v1), x2 = d2ff(v2);
   const FF K0 = ff_mul(hk, ff_sqr3(x0, x1, x2));
@@ -358,7 +360,7 @@ cudaError_t launch_couple(Ctx &c, double *v, double dt_md) {
         c.p.frozen, c.p.seed, (uint64_t)c.md_step,
         c.local ? kEVJ / (c.vatom * 1e-30 * c.p.gamma_Ce * c.p.Tmax_K * c.p.Tmax_K) : 1.0 / c.VC,
         reinterpret_cast<unsigned long long *>(c.scal + 9), c.local ? c.coef_host->thc : 0.0,
-        c.local ? 1.0 / c.p.Tmax_K : 0.0);
+        c.local ? 1.0 / c.p.Tmax_K : 0.0, c.rng_id);
   sum_partial<<<kRedBlocks, kRedThreads, 0, c.stream>>>(c.n, c.dKE, c.partials);
   sum_final_accumulate<<<1, kRedThreads, 0, c.stream>>>(kRedBlocks, c.partials, c.scal + 8);
   return cudaGetLastError();

@@ -378,7 +378,7 @@ class SlabDomain:
         self.ids, self.x, self.v, self.T = loc.ids[k], x[k].clone(), v[k].clone(), T[k].clone()
 
 
-def run_domains(domains: list, comm, params: dict, n_md: int, n_sub: int, t0: float = 0.0):
+def run_domains(domains: list, comm, params: dict, n_md: int, n_sub: int, t0: float = 0.0, md_step0: int = 0):
     """Advance the domains of this process by n_md MD steps of the whole path on
     the CUDA library, one context per domain and MD step: migration, ghosts,
     neighbour build from the local positions, the system means all-reduced from
@@ -387,7 +387,10 @@ def run_domains(domains: list, comm, params: dict, n_md: int, n_sub: int, t0: fl
     unpacked (ehc_set_te_at), then the hand-over and the drift.  comm: DistComm
     (one domain per process, tensors on this rank's GPU) or LocalComm (all
     domains of the system in this process).  params must fix vatom (the system's
-    volume per atom): a domain's own volume per atom is not the system's."""
+    volume per atom): a domain's own volume per atom is not the system's.  The
+    Langevin hand-over draws each atom's numbers by its global id and the system's
+    MD step (md_step0 + the step of this call; ehc_set_rng_ids), as the undivided
+    run does."""
     import torch
     from . import Ehc
     if not params.get("vatom"):
@@ -419,6 +422,7 @@ def run_domains(domains: list, comm, params: dict, n_md: int, n_sub: int, t0: fl
             g = Ehc(params, n=n, box=d.box, periodic=d.periodic, mass_amu=d.mass_amu,
                     types=np.zeros(n, dtype=np.int32))
             g.set_te(loc.T)
+            g.set_rng_ids(loc.ids, md_step0 + step)
             g.build_neighbors(loc.x, loc.v)
             st, ke = g.sums_at(loc.owned_idx.to(torch.int32))
             sums.append(torch.tensor([st, ke, float(loc.owned_idx.shape[0])], dtype=torch.float64,

@@ -114,8 +114,8 @@ def test_domain_means_from_owned_sums():
     assert err < 1e-12, err
 
 
-@pytest.mark.parametrize("flux_prec", [1, 0])
-def test_domains_rebuilt_every_md_step_on_one_gpu(flux_prec):
+@pytest.mark.parametrize("flux_prec,couple_mode", [(1, 0), (0, 0), (1, 1)])
+def test_domains_rebuilt_every_md_step_on_one_gpu(flux_prec, couple_mode):
     """halo.run_domains on one GPU: 2 and 3 slab domains of a system, each MD step
     rebuilt from its owned atoms and the ghosts within r_c of its slab (no global
     neighbour list), atoms migrating between domains, the means all-reduced from
@@ -124,12 +124,14 @@ def test_domains_rebuilt_every_md_step_on_one_gpu(flux_prec):
     1e-11, positions and velocities 1e-12 (the all-reduced means differ from the
     undivided sums in the last bits); single-precision flux: T_e within 1e-7 (an
     overwritten ghost makes the next substep take the full series, where the
-    undivided run takes each tile's own order)."""
+    undivided run takes each tile's own order).  couple_mode 1: the Langevin
+    hand-over, each domain atom's numbers keyed by its global id and the system's
+    MD step (ehc_set_rng_ids), as the undivided context draws them."""
     import torch
     import test_halo as TH
     from paper_1810_12357_gb300 import halo
     from _drive import run_gpu
-    s, p = TH._md_system()
+    s, p = TH._md_system(couple_mode)
     p = dict(p, flux_prec=flux_prec)
     tol = 1e-11 if flux_prec == 1 else 1e-7
     g, xg, vg = run_gpu(s, p, TH.N_MD, TH.N_SUB_MD)
@@ -145,8 +147,53 @@ def test_domains_rebuilt_every_md_step_on_one_gpu(flux_prec):
             assert np.all(np.isnan(T[ids]))
             T[ids], x[ids], v[ids] = d.T.cpu().numpy(), d.x.cpu().numpy(), d.v.cpu().numpy()
         err = float(np.max(np.abs(T - Tr) / Tr))
-        print(f"{nd} domains rebuilt every MD step (flux_prec {flux_prec}): T_e max rel err {err:.2e}, "
+        print(f"{nd} domains rebuilt every MD step (flux_prec {flux_prec}, couple_mode {couple_mode}): "
+              f"T_e max rel err {err:.2e}, "
               f"x {np.max(np.abs(x - xr)):.1e} A, v {np.max(np.abs(v - vr)):.1e} A/fs")
         assert err < tol
         assert float(np.max(np.abs(x - xr))) < 1e3 * tol
         assert float(np.max(np.abs(v - vr))) < tol * float(np.abs(vr).max())
+
+
+def test_rng_ids_key_the_langevin_stream():
+    """ehc_set_rng_ids: ids equal to the caller index reproduce the default
+    Langevin hand-over bit for bit; other ids or another MD step draw other
+    numbers; the oracle keyed by the same ids agrees (velocities within 1e-6 of
+    the largest: the GPU's Box-Muller runs in single precision); null ids return
+    to the index."""
+    import torch
+    from paper_1810_12357_gb300 import Ehc
+    s = I.track_system(6, 3, r0=5.0)
+    p = dict(I.params_track(), couple_mode=1)
+    n_sub, dt_md = 10, 10 * p["dt_sub"]
+    ids_shift = np.arange(s.n, dtype=np.int64)[::-1].copy() + 1000
+
+    def hand_over(ids, md_step):
+        g = Ehc(p, s)
+        g.set_te(s.Te)
+        if ids is not False:
+            g.set_rng_ids(None if ids is None else torch.as_tensor(ids, device="cuda"), md_step)
+        x = torch.as_tensor(s.x, device="cuda").contiguous()
+        v = torch.as_tensor(s.v, device="cuda").contiguous()
+        g.build_neighbors(x, v)
+        g.substep(n_sub, 0.0)
+        g.couple(v, dt_md)
+        torch.cuda.synchronize()
+        return v.cpu().numpy()
+
+    v_def = hand_over(False, 0)
+    assert np.array_equal(hand_over(np.arange(s.n, dtype=np.int64), 0), v_def)
+    assert np.array_equal(hand_over(None, 0), v_def)
+    v_ids = hand_over(ids_shift, 0)
+    v_step = hand_over(None, 3)
+    assert not np.array_equal(v_ids, v_def) and not np.array_equal(v_step, v_def)
+    # the oracle with the same ids and step
+    for ids, step, vg in ((ids_shift, 0, v_ids), (None, 3, v_step)):
+        sim = oracle.OracleSim(p, s.box, s.periodic, s.mass_amu, s.type)
+        sim.set_te(s.Te)
+        sim.rng_ids, sim.md_step = ids, step
+        x, v = s.x.copy(), s.v.copy()
+        sim.build(x, v)
+        sim.substeps(n_sub, 0.0)
+        sim.couple(v, dt_md)
+        assert float(np.max(np.abs(v - vg))) < 1e-6 * float(np.abs(v).max())

@@ -9,6 +9,7 @@ import socket
 import sys
 
 import numpy as np
+import pytest
 
 import oracle
 from paper_1810_12357_gb300 import halo
@@ -119,12 +120,12 @@ def test_two_gloo_ranks_equal_the_whole_system():
 N_MD, N_SUB_MD = 3, 20
 
 
-def _md_system():
+def _md_system(couple_mode=0):
     # a hot track on a lattice displaced by 0.1 A with 2,000 K velocities; the
     # slab faces of 2 and 3 domains (12 cells) lie on lattice planes, so atoms
     # cross them within the run
     s = I.track_system(12, 5, peak=20000.0, r0=6.0, disp_sigma=0.1, T_lat=2000.0)
-    p = dict(I.params_track(), couple_mode=0, frozen=0, dt_sub=5e-3, kappa0=40.0,
+    p = dict(I.params_track(), couple_mode=couple_mode, frozen=0, dt_sub=5e-3, kappa0=40.0,
              vatom=float(np.prod(s.box)) / s.n)
     return s, p
 
@@ -133,7 +134,8 @@ def oracle_domains(domains, exchange, allreduce, p, n_md, n_sub):
     """The oracle's MD steps on slab domains: the same sequence as
     halo.run_domains (migration, ghosts, build on the local positions, means of
     the owned atoms summed over the domains, ghost temperatures before every
-    substep, damping hand-over, free flight); exchange / allreduce act on all of
+    substep, hand-over with each atom's Langevin numbers keyed by its global id
+    and the system's MD step, free flight); exchange / allreduce act on all of
     this process's domains at once."""
     import torch
     dt_md = n_sub * p["dt_sub"]
@@ -148,6 +150,7 @@ def oracle_domains(domains, exchange, allreduce, p, n_md, n_sub):
             n = int(loc.ids.shape[0])
             sim = oracle.OracleSim(p, d.box, d.periodic, d.mass_amu, np.zeros(n, dtype=np.int32))
             sim.set_te(loc.T.numpy())
+            sim.rng_ids, sim.md_step = loc.ids.numpy(), step
             x, v = loc.x.numpy().copy(), loc.v.numpy().copy()
             sim.build(x, v)
             k = loc.owned_idx.numpy()
@@ -194,8 +197,10 @@ def _compare(T, x, v, Tr, xr, vr):
     assert float(np.max(np.abs(x - xr))) < 1e-12
 
 
-def test_three_domains_rebuilt_every_md_step_equal_the_whole_system():
-    s, p = _md_system()
+@pytest.mark.parametrize("couple_mode", [0, 1])
+def test_three_domains_rebuilt_every_md_step_equal_the_whole_system(couple_mode):
+    # couple_mode 1: the Langevin hand-over, its numbers keyed by global ids
+    s, p = _md_system(couple_mode)
     Tr, xr, vr = _undivided(s, p)
     reach = p["rc"] + 1e-5
     domains = [halo.SlabDomain.from_system(r, 3, s, reach) for r in range(3)]
