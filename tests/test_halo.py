@@ -213,7 +213,7 @@ def test_three_domains_rebuilt_every_md_step_equal_the_whole_system(couple_mode)
     _compare(*_collect(domains, s.n), Tr, xr, vr)
 
 
-def _rank_md(rank, ws, port, q):
+def _rank_md(rank, ws, port, q, couple_mode=0):
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -221,7 +221,7 @@ def _rank_md(rank, ws, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     import test_halo as TH
-    s, p = TH._md_system()
+    s, p = TH._md_system(couple_mode)
     comm = halo.DistComm(dist)
     d = halo.SlabDomain.from_system(rank, ws, s, p["rc"] + 1e-5)
     TH.oracle_domains([d], lambda outs: [comm.exchange(outs[0])], lambda ts: [comm.allreduce_sum(ts[0])], p,
@@ -230,13 +230,14 @@ def _rank_md(rank, ws, port, q):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_with_domains_rebuilt_every_md_step():
-    s, p = _md_system()
+@pytest.mark.parametrize("couple_mode", [0, 1])
+def test_two_gloo_ranks_with_domains_rebuilt_every_md_step(couple_mode):
+    s, p = _md_system(couple_mode)
     Tr, xr, vr = _undivided(s, p)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_md, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_md, args=(r, 2, port, q, couple_mode)) for r in range(2)]
     for pr in procs:
         pr.start()
     res = [q.get(timeout=300) for _ in procs]
