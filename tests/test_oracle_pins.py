@@ -282,6 +282,37 @@ def test_langevin_mode_moves_directions_not_energies():
     assert np.median(cosang) > 0.95
 
 
+def test_langevin_stream_follows_the_atom_id():
+    # The Langevin numbers of an atom are keyed by its id (default: its index):
+    # ids equal to the indices change nothing; identical atoms labelled with
+    # reversed ids come out reversed; two atoms with one id draw one set of
+    # numbers; another MD step draws others.
+    n = 64
+    rng = np.random.default_rng(5)
+    v1 = rng.normal(0.0, 0.03, 3)
+    mass = np.full(n, 63.546)
+    kw = dict(mode=1, frozen=0, seed=77, dt_md=0.1, gamma_fs=0.02, VC=2e-6)
+
+    def run(ids, md_step=4, same=True):
+        v = np.tile(v1, (n, 1)) if same else rng.normal(0.0, 0.03, (n, 3))
+        A = np.full(n, 1e-4)
+        T = np.full(n, 5000.0)
+        chi = np.ones(n, dtype=np.uint8)
+        dKE, _ = oracle.couple(v, mass, A, T, chi, md_step=md_step, rng_id=ids, **kw)
+        return v, dKE
+
+    v_def, d_def = run(None)
+    v_idx, d_idx = run(np.arange(n))
+    assert np.array_equal(v_def, v_idx) and np.array_equal(d_def, d_idx)
+    v_rev, _ = run(np.arange(n)[::-1])
+    assert np.array_equal(v_rev, v_def[::-1])
+    assert not np.array_equal(v_rev, v_def)
+    v_one, _ = run(np.full(n, 9))
+    assert np.all(v_one == v_one[0]) and np.array_equal(v_one[0], v_def[9])
+    v_step, _ = run(None, md_step=5)
+    assert not np.any(np.all(v_step == v_def, axis=1))
+
+
 # ------------------------------------------------------------- stability bound
 
 def test_stability_bound_at_the_l_point():
