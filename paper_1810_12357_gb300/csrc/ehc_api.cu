@@ -1939,8 +1939,10 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
   // the F(Y_0) term of the later stages (second order, or trained coefficients)
   bool use_f0 = false;
   for (int j = 2; j <= w->s; ++j) use_f0 = use_f0 || w->gam[j] != 0.0;
+  // the window's coupling factor 1 - (1 - dt G/C_e)^n_w, applied by the last stage
+  const double fin = 1.0 - std::pow(1.0 - c.p.dt_sub_fs * c.cG, (double)w->n_w);
   for (int j = 1; j <= w->s; ++j) {
-    StageArgs sa;
+    StageArgs sa{};
     sa.yin = j == 1 ? Y0 : rot[(j - 2) % 3];
     sa.y0 = Y0;
     sa.zin = j >= 2 ? w->z[(j - 2) % 3] : nullptr;
@@ -1955,23 +1957,30 @@ int ehc_cheb_step(ehc_cheb *w, ehc_ctx *hc, double tau, double t_fs, int32_t *fe
     sa.mt = (float)(w->mut[j] * tauw * c.K);
     sa.kap = (float)w->kap[j];
     sa.gt = (float)(w->gam[j] * tauw * c.K);
+    if (j == w->s) {
+      // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
+      sa.T0 = T0;
+      sa.T1 = T1;
+      sa.dTc = w->dTc;
+      sa.fin = (float)fin;
+      sa.Tref_f = (float)c.p.Tref_K;
+      sa.invTmax_f = (float)(1.0 / c.p.Tmax_K);
+      sa.Tmax = c.p.Tmax_K;
+    }
     CK(launch_cheb_stage(c, sa, par, c.stream));
     par ^= 1;
   }
   float *ys = rot[(w->s - 1) % 3];
-  const float *zs = w->z[(w->s - 1) % 3];
   int bs = 0;
   for (int k = 0; k < 4; ++k)
     if (w->y[k] == ys) bs = k;
-  // back to FP64 with the electron-phonon coupling of the window (kept in dTc until accepted)
-  CK(cheb_finish(c, T0, zs, ys, T1, w->dTc, w->n_w));
   // the learned corrector's pair flux on the window's result (T1 and its mirror)
   if (w->corr) {
     const int rc = gnn_correct_window(w->corr, c, tauw * c.K, ys, T1);
     if (rc) return rc;
   }
   // pair flux of the end state for the residual
-  StageArgs sf;
+  StageArgs sf{};
   sf.yin = ys;
   sf.y0 = ys;
   sf.zin = nullptr;

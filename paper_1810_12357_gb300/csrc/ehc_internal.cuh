@@ -309,6 +309,13 @@ struct StageArgs {
   float *Fout;          // the pair-flux sum F(Y_{j-1}) per atom, or null
   float *rr[2];         // row value ranges of the stage values (read [parity], write [parity ^ 1])
   float nu, mt, kap, gt;   // nu_j, mut_j tau K, 1 - mu_j - nu_j, gam_j tau K
+  // the window's last stage (T1 non-null) also ends the window in FP64:
+  // T1 = T0 + Tmax z - dT with the coupling of the window dT = fin (T0 - T_l)
+  // (single precision, also into dTc), and Y_j lowered by dT / Tmax
+  const double *T0;
+  double *T1, *dTc;
+  float fin, Tref_f, invTmax_f;
+  double Tmax;
 };
 
 // Deterministic block-partial reductions.
@@ -354,7 +361,6 @@ cudaError_t launch_tile_worklist(const RepArgs *reps, const int2 *work, int32_t 
 cudaError_t launch_cheb_stage(Ctx &c, const StageArgs &sa, int parity, cudaStream_t st);
 // kernels_window.cu (Chebyshev window propagator)
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y);
-cudaError_t cheb_finish(Ctx &c, const double *T0, const float *z, float *y, double *T1, double *dTc, int n_w);
 cudaError_t cheb_accept(Ctx &c, const double *dTc);
 cudaError_t cheb_residual(Ctx &c, const double *T0, const double *T1, const float *F0, const float *F1, double tau,
                           float *part, float *out);

@@ -461,9 +461,20 @@ __device__ __forceinline__ float row_atom(const RepArgs &ra, const StepCoef *cf,
     const float inc = fmaf(sa.gt, si.F0, fmaf(-sa.kap, si.zm1, sa.mt * F));
     const float z = si.zm1 + fmaf(sa.nu, si.zm2 - si.zm1, inc);
     const float h = si.y0 + z;
+    float hw = h;
+    if (sa.T1) {   // the last stage: the window's end in FP64 and its coupling
+      const double t0 = sa.T0[s];
+      const float ui = ra.uTl[s];
+      float dT = 0.0f;
+      if (ui == ui) dT = sa.fin * ((d2f_rn(t0) - sa.Tref_f) + ui);   // fin (T0 - T_l), T_l = Tref - ui
+      const double dTd = f2d(dT);
+      sa.T1[s] = fma(sa.Tmax, f2d(z), t0) - dTd;
+      sa.dTc[s] = dTd;
+      if (dT != 0.0f) hw = fmaf(-dT, sa.invTmax_f, h);
+    }
     if (sa.zout) {   // null: a flux pass, whose stage values are not kept
       sa.zout[s] = z;
-      sa.yout[s] = h;
+      sa.yout[s] = hw;
     }
     if (sa.Fout) sa.Fout[s] = F;
     return h;

@@ -1,6 +1,7 @@
 // kernels_window.cu -- element-wise parts of the Chebyshev window propagator:
-// the state as delta = (T - Tref)/Tmax for the stage launches, the stage result
-// back to FP64 temperatures, and the a-posteriori residual of a window.
+// the state as delta = (T - Tref)/Tmax for the stage launches, the accepted
+// window's coupling energy, and the a-posteriori residual of a window (the
+// stage result goes back to FP64 temperatures in the last stage itself).
 //
 // A window of n_w substeps of Eq. HeatTransport (pair-flux part) is advanced by
 // s stages of the first-order damped Chebyshev recurrence (RKC family):
@@ -91,34 +92,6 @@ int cheb_blocks(int64_t n) {
 cudaError_t cheb_mirror(Ctx &c, const double *T, float *y) {
   if (c.n > 0)
     mirror_kernel<<<nblk(c.n, kWinThreads), kWinThreads, 0, c.stream>>>(c.n, T, c.p.Tref_K, 1.0 / c.p.Tmax_K, y);
-  return cudaGetLastError();
-}
-
-// T1 = T0 + Tmax z (the window's change, so the start values' rounding does not
-// enter) minus the coupling of the window, f (T0 - T_l) with
-// f = 1 - (1 - dt G/C_e)^n_w; the decrement (single precision, the same value
-// in T1 and in the ledger) goes to dTc, handed to the lattice ledger only if the
-// window is accepted, and y (the stage values) follows T1
-__global__ void finish_kernel(int64_t n, const double *__restrict__ T0, const float *__restrict__ z,
-                              float *__restrict__ y, const float *__restrict__ uTl, float f, float Tref,
-                              float invTmax, double Tmax_d, double *__restrict__ T1, double *__restrict__ dTc) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const double t0 = T0[s];
-  const float ui = uTl[s];
-  float dT = 0.0f;
-  if (ui == ui) dT = f * ((d2f_rn(t0) - Tref) + ui);   // f (T0 - T_l), T_l = Tref - ui
-  const double dTd = f2d(dT);                            // conversions on the integer pipes
-  T1[s] = fma(Tmax_d, f2d(z[s]), t0) - dTd;
-  dTc[s] = dTd;
-  if (dT != 0.0f) y[s] = fmaf(-dT, invTmax, y[s]);
-}
-
-cudaError_t cheb_finish(Ctx &c, const double *T0, const float *z, float *y, double *T1, double *dTc, int n_w) {
-  if (c.n == 0) return cudaSuccess;
-  const double f = 1.0 - std::pow(1.0 - c.p.dt_sub_fs * c.cG, (double)n_w);
-  finish_kernel<<<nblk(c.n, kWinThreads), kWinThreads, 0, c.stream>>>(
-      c.n, T0, z, y, c.uTl, (float)f, (float)c.p.Tref_K, (float)(1.0 / c.p.Tmax_K), c.p.Tmax_K, T1, dTc);
   return cudaGetLastError();
 }
 
